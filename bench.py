@@ -1,0 +1,380 @@
+#!/usr/bin/env python
+"""Throughput of the source-to-waveform path on GB300: ruptures/s to 64
+observation waveforms.
+
+One step = one pass of the whole path (slip rFFT, stage-1 per-bin
+contraction, retransform with D_t, stage-2 contraction, reduction + IFFT) over
+one batch of ruptures.  The default workload is the paper-shaped plain case:
+963 subfaults, 20,000 grid points, 64 observations, 256 steps, one rupture per
+step, FP32 spectra (Ghat ~40 GB, streamed from HBM every step, so every step
+reads far more than the 129 MB L2).
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle instead (rank 0 only), on a bounded sample of the same workload.
+
+Multi-GPU (torchrun, one process per GPU): independent replicas, each with its
+own resident operators and its own ruptures; no collective on the data path
+(weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+from paper_2608_21763_gb300 import layout  # noqa: E402
+
+METRIC = "ruptures/sec to 64-obs waveforms at 1 GB300 (+HBM GB/s, tensor %) at stated rel-L2 error"
+UNIT = "ruptures/s"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+COMPLEX_BYTES = {"fp32": 8, "bf16": 4, "bf16_hilo": 8, "fp8": 2}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="plain", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--prec-g", default="fp32", choices=["fp32", "bf16", "bf16_hilo", "fp8"])
+    ap.add_argument("--prec-p", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--batch", type=int, default=None, help="ruptures per step (default: the workload's)")
+    ap.add_argument("--grid", type=int, default=None,
+                    help="override the number of grid points (small cases for profiling)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-check", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+    FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_index):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.out = os.path.join("/tmp", f"s2w_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.out, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={','.join(self.FIELDS)}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu_index)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.out):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) != len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.out)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ setup
+def load_context(s2w, wl, geom, prec_g, prec_p, B, device, chunk=1024):
+    ctx = s2w.Context(wl.Ns, wl.Ng, wl.No, wl.Nt, prec_g=prec_g, prec_p=prec_p,
+                      max_batch=B, device=device)
+    for g0 in range(0, wl.Ng, chunk):
+        g1 = min(wl.Ng, g0 + chunk)
+        ctx.load_greens(g0, geom.greens_rows(g0, g1, wl.Nt, np.float32))
+        ctx.load_adjoint(g0, geom.adjoint_cols(g0, g1, wl.Nt, np.float32))
+    return ctx
+
+
+def stage1_algorithmic_bytes(wl, prec_g, B):
+    """Bytes one stage-1 contraction launch must move: the unpadded operator
+    spectrum once, the slip spectra, and the seafloor spectra it writes."""
+    Nb = wl.Nt + 1
+    op = Nb * wl.Ng * wl.Ns * COMPLEX_BYTES[prec_g]
+    if prec_g == "fp8":
+        op += Nb * ((wl.Ng + 255) // 256) * 4
+    return op + Nb * wl.Ns * 8 * B + Nb * wl.Ng * 8 * B
+
+
+# ------------------------------------------------------------------ oracle legs
+def oracle_rows_rate(wl, geom, slip, budget_s, chunk=512, start=0):
+    """Time the FP64 oracle (stage 1, D_t, stage 2) on consecutive chunks of
+    grid rows of rupture 0 until `budget_s` of oracle time; returns (rows,
+    seconds).  Operator generation is not timed."""
+    import oracle
+    rows, secs, g0 = 0, 0.0, start
+    s = slip[:1].astype(np.float64)
+    while secs < budget_s and rows < wl.Ng:
+        g1 = min(wl.Ng, g0 + chunk)
+        G = geom.greens_rows(g0, g1, wl.Nt)
+        P = geom.adjoint_cols(g0, g1, wl.Nt)
+        t = time.perf_counter()
+        oracle.bltt_apply(P, oracle.dt_apply(oracle.bltt_apply(G, s)))
+        secs += time.perf_counter() - t
+        rows += g1 - g0
+        g0 = g1 % wl.Ng
+    return rows, secs
+
+
+def cpu_cores():
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+def sampled_accuracy(wl, geom, slip, q, n_obs=2):
+    """Whole waveforms of a few observations, rupture 0, against the FP64
+    oracle.  P[o, i, :] is exactly zero in FP64 beyond ~68 km (the Ricker
+    envelope underflows), so q_o only needs the grid rows where it is not;
+    the oracle sums exactly those terms."""
+    import oracle
+    errs = []
+    s = slip[:1].astype(np.float64)
+    for o in range(wl.No):
+        if len(errs) >= n_obs:
+            break
+        Po = synth.response(geom.obs[o:o + 1], geom.grid, wl.Nt, synth.ADJ_VEL_KMS)[0]
+        idx = np.nonzero(np.any(Po != 0, axis=1))[0]
+        if idx.size == 0:
+            continue
+        G = synth.response(geom.grid[idx], geom.sub, wl.Nt, synth.GREEN_VEL_KMS)
+        m = oracle.bltt_apply(G, s)
+        qo = oracle.bltt_apply(Po[idx][None], oracle.dt_apply(m))[0, 0]
+        errs.append(float(np.linalg.norm(q[0, o] - qo) / np.linalg.norm(qo)))
+    return {"max": max(errs), "observations": len(errs), "rupture": 0} if errs else None
+
+
+# ------------------------------------------------------------------ arms
+def workload(args):
+    import dataclasses
+    wl = synth.WORKLOADS[args.workload]
+    if args.grid:
+        wl = dataclasses.replace(wl, name=f"{wl.name}-grid{args.grid}", Ng=args.grid)
+    return wl
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_2608_21763_gb300 as s2w
+
+    wl = workload(args)
+    B = args.batch or wl.B
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    geom = wl.geometry_obj()
+    pool = 8
+    slip_np = wl.slip(geom, B=pool * B).astype(np.float32)
+    if rank > 0:  # replicas get their own ruptures
+        slip_np = np.roll(slip_np, rank, axis=0)
+    slip_np = slip_np.reshape(pool, B, wl.Ns, wl.Nt)
+
+    t_setup = time.perf_counter()
+    ctx = load_context(s2w, wl, geom, args.prec_g, args.prec_p, B, local_rank)
+    setup_s = time.perf_counter() - t_setup
+    slip_d = torch.tensor(slip_np, device=dev)
+    q_d = torch.empty((pool, B, wl.No, wl.Nt), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for k in range(args.warmup):
+        ctx.waveforms(slip_d[k % pool], q=q_d[k % pool], stream=stream)
+    torch.cuda.synchronize(dev)
+    ctx.sync()
+
+    # ---- device-timed region: inputs resident in HBM
+    barrier()
+    torch.cuda.synchronize(dev)
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    gpu_index = int(vis.split(",")[local_rank]) if vis and vis.split(",")[0].isdigit() else local_rank
+    sampler = ClockSampler(gpu_index)
+    ctx.profile_enable(True)
+    _, launches0 = ctx.profile_read()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    sampler.start()
+    e0.record(stream)
+    for k in range(args.steps):
+        ctx.waveforms(slip_d[k % pool], q=q_d[k % pool], stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    barrier()
+    elapsed_ms = e0.elapsed_time(e1)
+    stages, launches1 = ctx.profile_read()
+    ctx.profile_enable(False)
+    ctx.sync()
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    value = world * B * args.steps / (elapsed_ms / 1e3)
+
+    # ---- end to end through the public API with host buffers
+    import torch as _t
+    slip_h = _t.tensor(slip_np).pin_memory()
+    q_h = _t.empty((pool, B, wl.No, wl.Nt), dtype=_t.float32).pin_memory()
+    for k in range(2):
+        ctx.waveforms(slip_h[k % pool], q=q_h[k % pool], stream=stream)
+    barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        ctx.waveforms(slip_h[k % pool], q=q_h[k % pool], stream=stream)   # H2D + D2H + sync inside
+    torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * B * args.steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": B * wl.Ns * wl.Nt * 4, "d2h_bytes_per_step": B * wl.No * wl.Nt * 4}
+
+    if rank != 0:
+        return None
+
+    # ---- roofline of the dominant kernel (stage-1 contraction)
+    pk, pk_kind = peaks()
+    ms1, n1 = stages["contract_stage1"]
+    per_launch_s = ms1 / max(n1, 1) / 1e3
+    alg = stage1_algorithmic_bytes(wl, args.prec_g, 1)
+    achieved = alg / per_launch_s / 1e9
+    roof = {"kernel": "k_stream_dot (stage-1 per-bin contraction)", "bound": "hbm",
+            "achieved": round(achieved, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": round(achieved / pk["hbm_gbs"], 4), "peak_source": pk_kind,
+            "traffic": None, "algorithmic_bytes_per_launch": alg,
+            "launch_ms": round(per_launch_s * 1e3, 4)}
+    total_stage_ms = sum(v[0] for v in stages.values())
+    stage_report = {k: {"ms_per_step": round(v[0] / args.steps, 4), "share": round(v[0] / total_stage_ms, 4)}
+                    for k, v in stages.items() if v[1] > 0}
+
+    out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(elapsed_ms / args.steps, 4), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": wl.name, "Ns": wl.Ns, "Ng": wl.Ng, "No": wl.No, "Nt": wl.Nt,
+                      "ruptures_per_step": B, "prec_g": args.prec_g, "prec_p": args.prec_p,
+                      "l2": "inputs larger than L2 (every step streams the full operator spectra)",
+                      "parallelism": f"replicas{world}",
+                      "operator_gb": round(sum(ctx.operator_bytes()) / 1e9, 2),
+                      "setup_s": round(setup_s, 1)},
+           "roofline": roof, "stages": stage_report, "clocks": clocks, "e2e": e2e,
+           "gpu_launches": int(launches1 - launches0)}
+    q0 = q_d[0].cpu().numpy()
+    if not args.no_check:
+        out["rel_l2"] = sampled_accuracy(wl, geom, slip_np[0], q0)
+    if not args.no_cpu_baseline:
+        rows, secs = oracle_rows_rate(wl, geom, slip_np[0], budget_s=10.0)
+        out["cpu_baseline"] = {"value": round(rows / (secs * wl.Ng), 6), "unit": UNIT, "cores": cpu_cores(),
+                               "kind": "oracle",
+                               "sample": f"FP64 direct oracle on {rows} of {wl.Ng} grid rows of one rupture "
+                                         f"({secs:.1f} s), scaled to the full grid"}
+    return out
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return None
+    wl = workload(args)
+    geom = wl.geometry_obj()
+    slip = wl.slip(geom, B=1)
+    # calibrate the rows per step so the whole run stays within ~3 minutes
+    rows, secs = oracle_rows_rate(wl, geom, slip, budget_s=0.5, chunk=256)
+    rate = rows / secs
+    per_step = max(0.05, min(2.0, 150.0 / max(1, args.steps + args.warmup)))
+    chunk = int(max(8, min(wl.Ng, rate * per_step)))
+    import oracle
+    G = geom.greens_rows(0, chunk, wl.Nt)
+    P = geom.adjoint_cols(0, chunk, wl.Nt)
+    s = slip.astype(np.float64)
+    for _ in range(args.warmup):
+        oracle.bltt_apply(P, oracle.dt_apply(oracle.bltt_apply(G, s)))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.bltt_apply(P, oracle.dt_apply(oracle.bltt_apply(G, s)))
+    dt = time.perf_counter() - t0
+    value = args.steps * chunk / (dt * wl.Ng)
+    cb = {"value": round(value, 6), "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+          "sample": f"each step: FP64 direct oracle on {chunk} of {wl.Ng} grid rows of one rupture, "
+                    f"scaled to the full grid"}
+    return {"metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": wl.name, "Ns": wl.Ns, "Ng": wl.Ng, "No": wl.No, "Nt": wl.Nt,
+                       "ruptures_per_step": 1, "prec_g": args.prec_g, "prec_p": args.prec_p,
+                       "parallelism": "host cores"},
+            "cpu_baseline": cb,
+            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank)
+    else:
+        if world > 1:
+            import torch
+            import torch.distributed as dist
+            torch.cuda.set_device(local_rank)
+            dist.init_process_group("nccl")
+        out = run_ours(args, rank, world, local_rank)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,170 @@
+/*
+ * s2w.h - C ABI of libs2w, the GB300 (sm_103a) source-to-waveform library.
+ *
+ * The library evaluates the two-stage linear time-invariant map of the paper
+ * (arXiv 2608.21763, Sec. II):
+ *
+ *     m_n = sum_{k=0}^{n} F_{G,k} s_{n-k}       Eq. (elastic-response)
+ *     v   = D_t m                               Sec. II-B.2
+ *     q_n = sum_{k=0}^{n} F_{q,k} v_{n-k}       Eq. (waveform-response)
+ *
+ * i.e. q = F_q D_t F_G s (Alg. 1 steps 2-4, on one GPU, with the sum over
+ * grid partitions of Eq. (distributed-composition) done inside the device),
+ * with each block-Toeplitz matvec evaluated by FFT along time (Alg. 2):
+ * zero-pad to L = 2 Nt, real FFT, per-bin complex contraction over bins
+ * l = 0..Nt, inverse FFT, keep the first Nt samples.
+ *
+ * Notation: Ns = subfaults (N_f), Ng = seafloor grid points (N_m), No =
+ * observations (N_q), Nt = time steps, Nb = Nt + 1 bins, B = ruptures per call.
+ *
+ * Conventions shared by every entry point:
+ *  - Arrays are row-major float32 with the time index fastest.
+ *  - Pointer arguments may be host or device memory; the library tells them
+ *    apart with cudaPointerGetAttributes.  Device pointers must belong to the
+ *    context's device.  The caller owns every array it passes; the library
+ *    never keeps a pointer past the call.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *    enqueued on it.  When an output is host memory, the call copies the
+ *    result back and synchronises `stream` before returning; when all outputs
+ *    are device memory, the call returns once the work is enqueued and the
+ *    caller must keep inputs alive until the stream has passed the work.
+ *  - Every call returns an s2w_status.  A message for the last failure is
+ *    available from s2w_last_error.  Nothing aborts or prints.
+ *  - Kernel-side failures (a bounded wait that expired) are latched in a
+ *    device status word and reported by the next s2w_sync as S2W_ERR_TIMEOUT.
+ */
+#ifndef S2W_H
+#define S2W_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct s2w_ctx s2w_ctx;
+
+typedef enum {
+  S2W_OK = 0,
+  S2W_ERR_ARG = -1,         /* invalid argument (size, pointer, alignment) */
+  S2W_ERR_OOM = -2,         /* device allocation failed */
+  S2W_ERR_STATE = -3,       /* call out of order (e.g. operators not loaded) */
+  S2W_ERR_CUDA = -4,        /* a CUDA runtime call failed */
+  S2W_ERR_TIMEOUT = -5,     /* a kernel-side bounded wait expired */
+  S2W_ERR_UNSUPPORTED = -6  /* valid request outside what this build supports */
+} s2w_status;
+
+/* Storage of a resident operator spectrum.  Products always accumulate in
+ * FP32.  BF16: round-to-nearest-even bf16 complex.  BF16_HILO: two bf16
+ * arrays hi = bf16(x), lo = bf16(x - hi), used as hi + lo.  FP8_E4M3: e4m3
+ * complex with one FP32 scale per (bin, 256 consecutive grid rows),
+ * scale = amax / 448 computed in FP64 (stage-1 operator only). */
+typedef enum {
+  S2W_PREC_FP32 = 0,
+  S2W_PREC_BF16 = 1,
+  S2W_PREC_BF16_HILO = 2,
+  S2W_PREC_FP8_E4M3 = 3
+} s2w_prec;
+
+/* D_t between the stages.  The paper (Sec. II-B.2) names "a discrete
+ * temporal-difference stencil" without printing it; BACKWARD is the
+ * first-order backward difference v[n] = (m[n] - m[n-1]) / dt, m[-1] = 0.
+ * NONE gives v = m (two plain consecutive convolutions). */
+typedef enum { S2W_DT_BACKWARD = 0, S2W_DT_NONE = 1 } s2w_dt_mode;
+
+typedef struct {
+  int prec_g;     /* s2w_prec of the stage-1 spectrum Ghat (default FP32) */
+  int prec_p;     /* s2w_prec of the stage-2 spectrum Phat: FP32 or BF16 */
+  int dt_mode;    /* s2w_dt_mode (default BACKWARD) */
+  double dt;      /* time step of D_t in seconds (default 1.0, Sec. II-A) */
+  int max_batch;  /* largest B accepted by s2w_waveforms (sizes workspaces) */
+  int device;     /* CUDA device ordinal (default 0) */
+} s2w_opts;
+
+/* Fill *o with the defaults listed above (max_batch = 1). */
+void s2w_default_opts(s2w_opts *o);
+
+/* Create a context for Ns x Ng x No operators over Nt steps.  Allocates the
+ * resident spectra (sizes: s2w_operator_bytes) and workspaces on
+ * opts->device.  Supported: Nt in {32, 64, 128, 256, 512}; 1 <= Ns <= 1024;
+ * Ng >= 1; 1 <= No.  *out is NULL on failure.  opts may be NULL (defaults). */
+int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts *opts, s2w_ctx **out);
+
+/* Release every device allocation of the context.  NULL is accepted. */
+int s2w_destroy(s2w_ctx *ctx);
+
+/* Bytes of the resident stage-1 and stage-2 spectra of a context. */
+int s2w_operator_bytes(const s2w_ctx *ctx, size_t *g_bytes, size_t *p_bytes);
+
+/* Load grid rows g0 .. g0+ng-1 of the stage-1 operator from its time-domain
+ * impulse responses G[r][j][k] = [F_{G,k}]_{g0+r, j} (Sec. II-B.1), layout
+ * [ng][Ns][Nt].  The library zero-pads each response to L = 2 Nt, takes its
+ * real FFT with FP64-generated twiddles (Sec. II-C.1: spectra computed once
+ * at setup and kept resident), and stores bins 0..Nt in the context's
+ * precision.  Rows may be loaded in any order and in any number of calls;
+ * s2w_waveforms requires every row to have been loaded once.  FP8 storage
+ * requires g0 to be a multiple of 256 and ng a multiple of 256 unless the
+ * chunk ends at Ng.  Synchronises `stream` before returning. */
+int s2w_load_greens(s2w_ctx *ctx, int g0, int ng, const float *G, void *stream);
+
+/* Load grid columns g0 .. g0+ng-1 of the stage-2 operator from its
+ * time-domain responses P[o][r][k] = [F_{q,k}]_{o, g0+r} (Sec. II-B.2,
+ * adjoint acoustic-gravity responses), layout [No][ng][Nt].  Same transform
+ * and rules as s2w_load_greens (no alignment rule). */
+int s2w_load_adjoint(s2w_ctx *ctx, int g0, int ng, const float *P, void *stream);
+
+/* Waveforms for B ruptures: q[b] = F_q D_t F_G slip[b].
+ *   slip      [B][Ns][Nt]  slip-rate histories s_j[n]          (input)
+ *   q         [B][No][Nt]  observation waveforms q_o[n]        (output)
+ *   seafloor  [B][Ng][Nt]  seafloor motion m_i[n], or NULL     (output)
+ * 0 <= B <= max_batch (B = 0 does nothing).  Requires both operators fully
+ * loaded (else S2W_ERR_STATE). */
+int s2w_waveforms(s2w_ctx *ctx, const float *slip, int B, float *q, float *seafloor, void *stream);
+
+/* Zero-padded real FFT of `rows` signals of Nt samples (the transform of
+ * Alg. 2 steps 1-2): X[r][l] = sum_{n<Nt} x[r][n] exp(-2 pi i n l / (2 Nt)),
+ * l = 0..Nt, X as interleaved (re, im) float pairs [rows][Nt+1][2].
+ * x and X must be device pointers. */
+int s2w_rfft(s2w_ctx *ctx, const float *x, long long rows, float *X, void *stream);
+
+/* Inverse of the above with truncation (Alg. 2 steps 4-5): from bins
+ * X[r][0..Nt] of a real length-2Nt signal, x[r][n] for n < Nt.  Device
+ * pointers only. */
+int s2w_irfft(s2w_ctx *ctx, const float *X, long long rows, float *x, void *stream);
+
+/* Per-stage CUDA-event timers (the per-stage timing of Sec. III-B).
+ * Stages: 0 rfft of slip, 1 stage-1 contraction, 2 retransform (IFFT,
+ * Truncate, D_t, ZeroPad, FFT), 3 stage-2 contraction, 4 partial reduction +
+ * IFFT + Truncate, 5 host<->device copies made by s2w_waveforms. */
+#define S2W_NUM_STAGES 6
+typedef struct {
+  double ms[S2W_NUM_STAGES];           /* summed event-timed durations */
+  long long count[S2W_NUM_STAGES];     /* timed launches per stage */
+  long long launches;                  /* kernel launches by the library (always counted) */
+} s2w_profile;
+
+/* on != 0: clear the totals and start recording a CUDA event before and after
+ * every stage launch, on the stream the stage runs on.  on == 0: stop. */
+int s2w_profile_enable(s2w_ctx *ctx, int on);
+
+/* Synchronise the recorded events and return the totals since enable.
+ * `launches` counts every kernel the library launched since the context was
+ * created (recording on or off). */
+int s2w_profile_read(s2w_ctx *ctx, s2w_profile *out);
+
+/* Wait for all work of the context's device, then report and clear the
+ * device status word (S2W_ERR_TIMEOUT if a kernel-side wait expired). */
+int s2w_sync(s2w_ctx *ctx);
+
+/* Message of the last failing call on ctx (or of the last failing
+ * s2w_create when ctx is NULL).  Valid until the next call on ctx. */
+const char *s2w_last_error(const s2w_ctx *ctx);
+
+/* Static name of a status code. */
+const char *s2w_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* S2W_H */

@@ -1,0 +1,342 @@
+// Transform kernels of the pipeline (everything except the per-bin
+// contractions): twiddle table, batched zero-padded real FFT (Alg. 2, steps
+// 1-2), the stage-1 -> stage-2 retransform (Alg. 2 steps 4-5 for F_G, the
+// D_t stencil of Sec. II-B.2, then steps 1-2 for F_q), the split-K reduction
+// of stage-2 partials fused with the final IFFT + Truncate, and the load-time
+// conversion of FP32 spectra into the resident storage types.
+#include "fft.cuh"
+
+namespace s2w {
+
+namespace {
+
+constexpr int kWarps = 8;
+constexpr int kThreads = 32 * kWarps;
+
+// tw[m] = exp(-2 pi i m / L), m < L, evaluated in FP64 and stored as FP32.
+__global__ void k_twiddles(float2* tw, int L) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= L) return;
+  double s, c;
+  sincospi(2.0 * static_cast<double>(m) / static_cast<double>(L), &s, &c);
+  tw[m] = make_float2(static_cast<float>(c), static_cast<float>(-s));
+}
+
+template <int P>
+__device__ __forceinline__ void load_twiddles(float2* tw, const float2* __restrict__ twg) {
+  for (int m = threadIdx.x; m < 64 * P; m += blockDim.x) tw[m] = twg[m];
+}
+
+// One warp per row: x[row][0..n_in) zero-padded to L = 2N, bins 0..N to
+// X[l * ld_l + (row / rows_a) * ld_a + row % rows_a].
+template <int P>
+__global__ void __launch_bounds__(kThreads) k_rfft_rows(const float* __restrict__ x, long long rows, int n_in,
+                                                        const float2* __restrict__ twg, float2* __restrict__ X,
+                                                        long long ld_l, long long rows_a, long long ld_a) {
+  constexpr int N = 32 * P;
+  constexpr int L = 2 * N;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* tw = reinterpret_cast<float2*>(smraw);
+  float2* zs = tw + L + (threadIdx.x >> 5) * N;
+  load_twiddles<P>(tw, twg);
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const long long row = static_cast<long long>(blockIdx.x) * kWarps + (threadIdx.x >> 5);
+  if (row >= rows) return;
+  const float* xr = x + row * n_in;
+  warp_rfft_stage<P>([&](int n) { return n < n_in ? __ldg(xr + n) : 0.f; }, zs, tw, lane);
+  float2* out = X + (row / rows_a) * ld_a + (row % rows_a);
+  for (int k = lane; k <= N; k += 32) out[k * ld_l] = rfft_bin<P>(zs, tw, k);
+}
+
+// One warp per row: bins X[row][0..N] -> first N samples x[row][0..N).
+template <int P>
+__global__ void __launch_bounds__(kThreads) k_irfft_rows(const float2* __restrict__ X, long long rows,
+                                                         const float2* __restrict__ twg, float* __restrict__ x) {
+  constexpr int N = 32 * P;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* tw = reinterpret_cast<float2*>(smraw);
+  load_twiddles<P>(tw, twg);
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const long long row = static_cast<long long>(blockIdx.x) * kWarps + (threadIdx.x >> 5);
+  if (row >= rows) return;
+  const float2* xr = X + row * (N + 1);
+  float* out = x + row * N;
+  warp_irfft_head<P>([&](int k) { return xr[k]; }, [&](int n, float v) { out[n] = v; }, tw, lane);
+}
+
+// Retransform of 32 consecutive grid points per CTA:
+//   mhat[l][i] (bins 0..N)  -> IFFT, keep n < N (Truncate)  -> m
+//   v = D_t m  (backward difference; or v = m when dt_mode is NONE)
+//   v zero-padded to 2N -> FFT -> vhat[l][i].
+// Optionally writes m to seafloor[i][0..N).
+template <int P>
+__global__ void __launch_bounds__(kThreads) k_retransform(const float2* __restrict__ mhat, long long Ng, long long ld_m,
+                                                          const float2* __restrict__ twg, float inv_dt, int dt_mode,
+                                                          float2* __restrict__ vhat, long long ld_v,
+                                                          float* __restrict__ seafloor) {
+  constexpr int N = 32 * P;
+  constexpr int L = 2 * N;
+  constexpr int NB = N + 1;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* tw = reinterpret_cast<float2*>(smraw);
+  float2* tile = tw + L;                                 // [32][NB]
+  float2* zs = tile + 32 * NB + (threadIdx.x >> 5) * N;  // per warp [N]
+  float* mb = reinterpret_cast<float*>(tile + 32 * NB + kWarps * N) + (threadIdx.x >> 5) * N;
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const long long i0 = static_cast<long long>(blockIdx.x) * 32;
+  load_twiddles<P>(tw, twg);
+  for (int e = threadIdx.x; e < NB * 32; e += kThreads) {
+    const int l = e >> 5, c = e & 31;
+    const long long i = i0 + c;
+    tile[c * NB + l] = (i < Ng) ? mhat[l * ld_m + i] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  for (int c = warp; c < 32; c += kWarps) {
+    const long long i = i0 + c;
+    if (i >= Ng) break;
+    float2* X = tile + c * NB;
+    warp_irfft_head<P>([&](int k) { return X[k]; }, [&](int n, float v) { mb[n] = v; }, tw, lane);
+    __syncwarp();
+    if (seafloor != nullptr)
+      for (int n = lane; n < N; n += 32) seafloor[i * N + n] = mb[n];
+    if (dt_mode == S2W_DT_NONE) {
+      warp_rfft_stage<P>([&](int n) { return n < N ? mb[n] : 0.f; }, zs, tw, lane);
+    } else {
+      warp_rfft_stage<P>(
+          [&](int n) { return n < N ? (mb[n] - (n > 0 ? mb[n - 1] : 0.f)) * inv_dt : 0.f; }, zs, tw, lane);
+    }
+    for (int k = lane; k <= N; k += 32) X[k] = rfft_bin<P>(zs, tw, k);
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < NB * 32; e += kThreads) {
+    const int l = e >> 5, c = e & 31;
+    const long long i = i0 + c;
+    if (i < Ng) vhat[l * ld_v + i] = tile[c * NB + l];
+  }
+}
+
+// Split-K reduction + output transform.  For rupture b and observation o:
+//   Qhat[l] = sum_{s < nseg} part[b][l][s][o]   (fixed order: deterministic)
+//   q[b][o][n] = IFFT(Qhat)[n], n < N.
+template <int P>
+__global__ void __launch_bounds__(kThreads) k_reduce_irfft(const float2* __restrict__ part, int B, int No, int nseg,
+                                                           long long ld_b, const float2* __restrict__ twg,
+                                                           float* __restrict__ q) {
+  constexpr int N = 32 * P;
+  constexpr int L = 2 * N;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* tw = reinterpret_cast<float2*>(smraw);
+  float2* xs = tw + L + (threadIdx.x >> 5) * (N + 1);
+  load_twiddles<P>(tw, twg);
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const long long id = static_cast<long long>(blockIdx.x) * kWarps + (threadIdx.x >> 5);
+  if (id >= static_cast<long long>(B) * No) return;
+  const int b = static_cast<int>(id / No), o = static_cast<int>(id % No);
+  const float2* pb = part + b * ld_b;
+  for (int k = lane; k <= N; k += 32) {
+    float2 acc = make_float2(0.f, 0.f);
+    for (int s = 0; s < nseg; ++s) acc = cadd(acc, pb[(static_cast<long long>(k) * nseg + s) * No + o]);
+    xs[k] = acc;
+  }
+  __syncwarp();
+  float* out = q + id * N;
+  warp_irfft_head<P>([&](int k) { return xs[k]; }, [&](int n, float v) { out[n] = v; }, tw, lane);
+}
+
+// FP32 spectra -> resident storage (FP32 / BF16 / BF16 hi+lo), block copy:
+// dst[l * ld_dst_l + dst_off + r] = convert(src[l * n_per_l + r]).
+__global__ void k_store_blocks(const float2* __restrict__ src, int Nb, long long n_per_l, int el, void* dst,
+                               void* dst_lo, long long ld_dst_l, long long dst_off) {
+  const long long total = static_cast<long long>(Nb) * n_per_l;
+  for (long long e = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long l = e / n_per_l, r = e % n_per_l;
+    const float2 v = src[e];
+    const long long d = l * ld_dst_l + dst_off + r;
+    if (el == EL_FP32) {
+      static_cast<float2*>(dst)[d] = v;
+    } else {
+      const __nv_bfloat162 hi = __floats2bfloat162_rn(v.x, v.y);
+      static_cast<__nv_bfloat162*>(dst)[d] = hi;
+      if (el == EL_BF16_HILO) {
+        const float2 h = __bfloat1622float2(hi);
+        static_cast<__nv_bfloat162*>(dst_lo)[d] = __floats2bfloat162_rn(v.x - h.x, v.y - h.y);
+      }
+    }
+  }
+}
+
+// Stage-2 spectra, staging [l][o][nc] -> resident [l][seg][o][RL] at grid
+// column i = c0 + c (seg = i / RL).
+__global__ void k_store_adjoint(const float2* __restrict__ src, int Nb, int No, long long nc, long long c0, int RL,
+                                int nseg, int el, void* dst) {
+  const long long total = static_cast<long long>(Nb) * No * nc;
+  for (long long e = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long l = e / (No * nc);
+    const long long rem = e % (No * nc);
+    const long long o = rem / nc, c = rem % nc;
+    const long long i = c0 + c;
+    const long long d = ((l * nseg + i / RL) * No + o) * RL + (i % RL);
+    const float2 v = src[e];
+    if (el == EL_FP32)
+      static_cast<float2*>(dst)[d] = v;
+    else
+      static_cast<__nv_bfloat162*>(dst)[d] = __floats2bfloat162_rn(v.x, v.y);
+  }
+}
+
+// FP8 scales: one CTA per (bin l, 256-row block) of the staging chunk
+// [l][rows][Ns_pad]; amax over |Re|, |Im| of the block, then, in FP64,
+// scale = amax / 448 (448 = largest finite e4m3).
+__global__ void k_fp8_scales(const float2* __restrict__ spec, long long rows, int Ns_pad, long long row0, float* scale,
+                             int nblk) {
+  const int l = blockIdx.y;
+  const long long rb = static_cast<long long>(blockIdx.x) * 256;
+  const long long re = min(rows, rb + 256);
+  const float2* base = spec + (static_cast<long long>(l) * rows + rb) * Ns_pad;
+  const long long n = (re - rb) * Ns_pad;
+  float m = 0.f;
+  for (long long e = threadIdx.x; e < n; e += blockDim.x) {
+    const float2 v = base[e];
+    m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+  }
+  __shared__ float red[32];
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float mm = 0.f;
+    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) mm = fmaxf(mm, red[w]);
+    const double s = static_cast<double>(mm) / 448.0;
+    scale[static_cast<long long>(l) * nblk + (row0 + rb) / 256] = static_cast<float>(s);
+  }
+}
+
+// FP8 quantisation with round-to-nearest-even and saturation:
+// dst[l][row0 + r][j] = e4m3(spec[l][r][j] / scale[l][(row0 + r) / 256]).
+__global__ void k_fp8_quantize(const float2* __restrict__ spec, int Nb, long long rows, int Ns_pad, long long row0,
+                               long long Ng, const float* __restrict__ scale, int nblk,
+                               __nv_fp8x2_storage_t* __restrict__ dst) {
+  const long long per_l = rows * Ns_pad;
+  const long long total = static_cast<long long>(Nb) * per_l;
+  for (long long e = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long l = e / per_l, rem = e % per_l;
+    const long long r = rem / Ns_pad;
+    const float sc = scale[l * nblk + (row0 + r) / 256];
+    const float inv = sc > 0.f ? static_cast<float>(1.0 / static_cast<double>(sc)) : 0.f;
+    const float2 v = spec[e];
+    dst[l * Ng * Ns_pad + row0 * Ns_pad + rem] =
+        __nv_cvt_float2_to_fp8x2(make_float2(v.x * inv, v.y * inv), __NV_SATFINITE, __NV_E4M3);
+  }
+}
+
+int grid_for(long long n, int threads) {
+  long long g = (n + threads - 1) / threads;
+  if (g > 152LL * 32) g = 152LL * 32;
+  if (g < 1) g = 1;
+  return static_cast<int>(g);
+}
+
+template <int P>
+size_t smem_retransform() {
+  constexpr int N = 32 * P;
+  return sizeof(float2) * (2 * N + 32 * (N + 1) + kWarps * N) + sizeof(float) * kWarps * N;
+}
+
+}  // namespace
+
+#define S2W_DISPATCH_P(Nt, ...)                               \
+  switch (Nt) {                                               \
+    case 32: { constexpr int P = 1; __VA_ARGS__; } break;     \
+    case 64: { constexpr int P = 2; __VA_ARGS__; } break;     \
+    case 128: { constexpr int P = 4; __VA_ARGS__; } break;    \
+    case 256: { constexpr int P = 8; __VA_ARGS__; } break;    \
+    case 512: { constexpr int P = 16; __VA_ARGS__; } break;   \
+    default: return cudaErrorInvalidValue;                    \
+  }
+
+cudaError_t launch_twiddles(float2* tw, int L, cudaStream_t st) {
+  k_twiddles<<<(L + 255) / 256, 256, 0, st>>>(tw, L);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rfft_rows(const float* x, long long rows, int n_in, int Nt, const float2* tw, float2* X,
+                             long long ld_l, long long rows_a, long long ld_a, cudaStream_t st) {
+  if (rows <= 0) return cudaSuccess;
+  const unsigned grid = static_cast<unsigned>((rows + kWarps - 1) / kWarps);
+  S2W_DISPATCH_P(Nt, {
+    const size_t sm = sizeof(float2) * (64 * P + kWarps * 32 * P);
+    k_rfft_rows<P><<<grid, kThreads, sm, st>>>(x, rows, n_in, tw, X, ld_l, rows_a, ld_a);
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_irfft_rows(const float2* X, long long rows, int Nt, const float2* tw, float* x, cudaStream_t st) {
+  if (rows <= 0) return cudaSuccess;
+  const unsigned grid = static_cast<unsigned>((rows + kWarps - 1) / kWarps);
+  S2W_DISPATCH_P(Nt, {
+    const size_t sm = sizeof(float2) * 64 * P;
+    k_irfft_rows<P><<<grid, kThreads, sm, st>>>(X, rows, tw, x);
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_retransform(const float2* mhat, long long Ng, long long ld_m, int Nt, const float2* tw,
+                               float inv_dt, int dt_mode, float2* vhat, long long ld_v, float* seafloor,
+                               cudaStream_t st) {
+  if (Ng <= 0) return cudaSuccess;
+  const unsigned grid = static_cast<unsigned>((Ng + 31) / 32);
+  S2W_DISPATCH_P(Nt, {
+    const size_t sm = smem_retransform<P>();
+    cudaError_t e = cudaFuncSetAttribute(k_retransform<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(sm));
+    if (e != cudaSuccess) return e;
+    k_retransform<P><<<grid, kThreads, sm, st>>>(mhat, Ng, ld_m, tw, inv_dt, dt_mode, vhat, ld_v, seafloor);
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_irfft(const float2* part, int B, int No, int nseg, int Nt, long long ld_b, const float2* tw,
+                                float* q, cudaStream_t st) {
+  const long long n = static_cast<long long>(B) * No;
+  if (n <= 0) return cudaSuccess;
+  const unsigned grid = static_cast<unsigned>((n + kWarps - 1) / kWarps);
+  S2W_DISPATCH_P(Nt, {
+    const size_t sm = sizeof(float2) * (64 * P + kWarps * (32 * P + 1));
+    k_reduce_irfft<P><<<grid, kThreads, sm, st>>>(part, B, No, nseg, ld_b, tw, q);
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_store_blocks(const float2* src, int Nb, long long n_per_l, int el, void* dst, void* dst_lo,
+                                long long ld_dst_l, long long dst_off, cudaStream_t st) {
+  k_store_blocks<<<grid_for(Nb * n_per_l, 256), 256, 0, st>>>(src, Nb, n_per_l, el, dst, dst_lo, ld_dst_l, dst_off);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_store_adjoint(const float2* src, int Nb, int No, long long nc, long long c0, int RL, int nseg,
+                                 int el, void* dst, cudaStream_t st) {
+  k_store_adjoint<<<grid_for(static_cast<long long>(Nb) * No * nc, 256), 256, 0, st>>>(src, Nb, No, nc, c0, RL, nseg,
+                                                                                        el, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fp8_store(const float2* spec, int Nb, long long rows, int Ns_pad, long long row0, long long Ng,
+                             float* scale, int nblk, void* dst, cudaStream_t st) {
+  dim3 g(static_cast<unsigned>((rows + 255) / 256), static_cast<unsigned>(Nb));
+  k_fp8_scales<<<g, 256, 0, st>>>(spec, rows, Ns_pad, row0, scale, nblk);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_fp8_quantize<<<grid_for(Nb * rows * Ns_pad, 256), 256, 0, st>>>(spec, Nb, rows, Ns_pad, row0, Ng, scale, nblk,
+                                                                     static_cast<__nv_fp8x2_storage_t*>(dst));
+  return cudaGetLastError();
+}
+
+}  // namespace s2w

@@ -1,0 +1,237 @@
+// Per-bin complex contractions on the HBM-streaming path (Alg. 2 step 3,
+// yhat_l = Fhat_l xhat_l, for a small rupture batch).
+//
+// Both stages are one kernel.  The resident spectrum is a sequence of F
+// contiguous rows of `row_len` complex entries; row f is dotted with the
+// vector x_vec(f) = x + (f / rows_per_vec) * x_stride:
+//   stage 1: rows (l, i) of Ghat [l][i][Ns_pad], x_vec = shat_l     -> mhat[l][i]
+//   stage 2: rows (l, seg, o) of Phat [l][seg][o][RL],
+//            x_vec = vhat_l[seg * RL ..]                           -> partial[l][seg][o]
+//
+// Each CTA owns one contiguous range of rows (balanced to the row) and streams
+// it through a 3-stage shared-memory ring filled by cp.async.bulk (one bulk
+// copy per stage, L2 evict-first: every operator byte is read exactly once).
+// Eight consumer warps take one row each per pass; lane l handles the 16-byte
+// chunks l, l + 32, ... of the row, so a warp reads 512 contiguous bytes per
+// step, and keeps the matching slice of x_vec in registers across rows that
+// share it.  Products accumulate in FP32; FP8 rows are rescaled by their
+// per-(bin, 256-row block) scale after the dot product.
+#include "s2w_internal.cuh"
+
+namespace s2w {
+
+namespace {
+
+constexpr int kConsumerWarps = 8;
+constexpr int kStages = 3;
+constexpr int kThreads = 32 * (kConsumerWarps + 1);
+constexpr int kMaxRowLen = 1024;
+
+template <int EL>
+struct Chunk;  // complex entries per 16-byte chunk and how to unpack them
+
+template <>
+struct Chunk<EL_FP32> {
+  static constexpr int C = 2;
+  __device__ __forceinline__ static void unpack(const uint4& u, float2 (&g)[C]) {
+    g[0] = make_float2(__uint_as_float(u.x), __uint_as_float(u.y));
+    g[1] = make_float2(__uint_as_float(u.z), __uint_as_float(u.w));
+  }
+};
+
+__device__ __forceinline__ float2 bf2_to_f2(unsigned w) {
+  // bf16 -> f32 is exact: the 16 bits move to the top of the word
+  return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+}
+
+template <>
+struct Chunk<EL_BF16> {
+  static constexpr int C = 4;
+  __device__ __forceinline__ static void unpack(const uint4& u, float2 (&g)[C]) {
+    g[0] = bf2_to_f2(u.x);
+    g[1] = bf2_to_f2(u.y);
+    g[2] = bf2_to_f2(u.z);
+    g[3] = bf2_to_f2(u.w);
+  }
+};
+
+__device__ __forceinline__ float2 fp8x2_to_f2(unsigned short s) {
+  const __half2_raw h = __nv_cvt_fp8x2_to_halfraw2(static_cast<__nv_fp8x2_storage_t>(s), __NV_E4M3);
+  return __half22float2(*reinterpret_cast<const __half2*>(&h));
+}
+
+template <>
+struct Chunk<EL_FP8> {
+  static constexpr int C = 8;
+  __device__ __forceinline__ static void unpack(const uint4& u, float2 (&g)[C]) {
+    const unsigned w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      g[2 * k] = fp8x2_to_f2(static_cast<unsigned short>(w[k] & 0xffffu));
+      g[2 * k + 1] = fp8x2_to_f2(static_cast<unsigned short>(w[k] >> 16));
+    }
+  }
+};
+
+// EL selects the unpacker (EL_BF16 also serves the hi/lo pair when HILO).
+template <int EL, bool HILO>
+__global__ void __launch_bounds__(kThreads, 1) k_stream_dot(const StreamArgs a, int stage_rows) {
+  using CH = Chunk<EL>;
+  constexpr int C = CH::C;
+  constexpr int T = kMaxRowLen / (32 * C);  // chunk slots per lane
+  extern __shared__ __align__(128) unsigned char sm[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm);
+  uint64_t* empty = full + kStages;
+  unsigned char* buf = sm + 128;
+  const int row_bytes = a.row_len * (16 / C);
+  const int stage_bytes = stage_rows * row_bytes;
+  unsigned char* buf_lo = buf + kStages * stage_bytes;
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const long long r0 = a.F * blockIdx.x / gridDim.x;
+  const long long r1 = a.F * (blockIdx.x + 1) / gridDim.x;
+  const int nst = static_cast<int>((r1 - r0 + stage_rows - 1) / stage_rows);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(empty + s, kConsumerWarps);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  if (warp == kConsumerWarps) {  // producer warp: one elected lane issues the copies
+    if (lane == 0) {
+      const uint64_t pol = l2_policy_evict_first();
+      int k = 0;
+      for (; k < nst; ++k) {
+        const int s = k % kStages;
+        if (k >= kStages &&
+            !mbar_wait_bounded(empty + s, ((k / kStages) - 1) & 1, a.status, DEV_ERR_TIMEOUT_EMPTY))
+          break;
+        const long long rs = r0 + static_cast<long long>(k) * stage_rows;
+        const int nr = static_cast<int>(min(static_cast<long long>(stage_rows), r1 - rs));
+        const uint32_t bytes = static_cast<uint32_t>(nr) * row_bytes;
+        mbar_arrive_expect_tx(full + s, HILO ? 2 * bytes : bytes);
+        bulk_g2s(buf + s * stage_bytes, static_cast<const unsigned char*>(a.rows) + rs * row_bytes, bytes, full + s,
+                 pol);
+        if (HILO)
+          bulk_g2s(buf_lo + s * stage_bytes, static_cast<const unsigned char*>(a.rows_lo) + rs * row_bytes, bytes,
+                   full + s, pol);
+      }
+      // Never leave the CTA with copies in flight: wait for the last stages issued.
+      for (int kk = (k > kStages ? k - kStages : 0); kk < k; ++kk)
+        mbar_wait_bounded(full + kk % kStages, (kk / kStages) & 1, a.status, DEV_ERR_TIMEOUT_FULL);
+    }
+    return;
+  }
+
+  // consumer warps
+  const int nchunk = row_bytes / 16;
+  float2 xr[T][C];
+  long long cur_vec = -1;
+  for (int k = 0; k < nst; ++k) {
+    const int s = k % kStages;
+    if (!mbar_wait_bounded(full + s, (k / kStages) & 1, a.status, DEV_ERR_TIMEOUT_FULL)) return;
+    const long long rs = r0 + static_cast<long long>(k) * stage_rows;
+    const int nr = static_cast<int>(min(static_cast<long long>(stage_rows), r1 - rs));
+    for (int lr = warp; lr < nr; lr += kConsumerWarps) {
+      const long long f = rs + lr;
+      const long long vec = f / a.rows_per_vec;
+      if (vec != cur_vec) {
+        const float4* xv = reinterpret_cast<const float4*>(a.x + vec * a.x_stride);
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+          const int c = lane + 32 * t;
+#pragma unroll
+          for (int q = 0; q < C / 2; ++q) {
+            const float4 v = (c < nchunk) ? __ldg(xv + c * (C / 2) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+            xr[t][2 * q] = make_float2(v.x, v.y);
+            xr[t][2 * q + 1] = make_float2(v.z, v.w);
+          }
+        }
+        cur_vec = vec;
+      }
+      const uint4* row = reinterpret_cast<const uint4*>(buf + s * stage_bytes + lr * row_bytes);
+      const uint4* row_lo = reinterpret_cast<const uint4*>(buf_lo + s * stage_bytes + lr * row_bytes);
+      float ar0 = 0.f, ai0 = 0.f, ar1 = 0.f, ai1 = 0.f;
+#pragma unroll
+      for (int t = 0; t < T; ++t) {
+        const int c = lane + 32 * t;
+        if (c < nchunk) {
+          float2 g[C];
+          CH::unpack(row[c], g);
+          if (HILO) {
+            float2 gl[C];
+            CH::unpack(row_lo[c], gl);
+#pragma unroll
+            for (int q = 0; q < C; ++q) g[q] = cadd(g[q], gl[q]);
+          }
+#pragma unroll
+          for (int q = 0; q < C; q += 2) {
+            ar0 = fmaf(g[q].x, xr[t][q].x, ar0);
+            ar0 = fmaf(-g[q].y, xr[t][q].y, ar0);
+            ai0 = fmaf(g[q].x, xr[t][q].y, ai0);
+            ai0 = fmaf(g[q].y, xr[t][q].x, ai0);
+            ar1 = fmaf(g[q + 1].x, xr[t][q + 1].x, ar1);
+            ar1 = fmaf(-g[q + 1].y, xr[t][q + 1].y, ar1);
+            ai1 = fmaf(g[q + 1].x, xr[t][q + 1].y, ai1);
+            ai1 = fmaf(g[q + 1].y, xr[t][q + 1].x, ai1);
+          }
+        }
+      }
+      float ar = ar0 + ar1, ai = ai0 + ai1;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        ar += __shfl_xor_sync(0xffffffffu, ar, o);
+        ai += __shfl_xor_sync(0xffffffffu, ai, o);
+      }
+      if (lane == 0) {
+        if (EL == EL_FP8) {
+          const float sc = a.scale[vec * a.nblk + (f % a.rows_per_vec) / 256];
+          ar *= sc;
+          ai *= sc;
+        }
+        a.y[f] = make_float2(ar, ai);
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(empty + s);
+  }
+}
+
+template <int EL, bool HILO>
+cudaError_t launch_t(const StreamArgs& a, int num_sms, cudaStream_t st) {
+  constexpr int C = Chunk<EL>::C;
+  const int row_bytes = a.row_len * (16 / C);
+  const int budget = HILO ? 32 * 1024 : 64 * 1024;
+  int stage_rows = budget / row_bytes;
+  if (stage_rows >= kConsumerWarps) stage_rows -= stage_rows % kConsumerWarps;
+  if (stage_rows < 1) stage_rows = 1;
+  const size_t smem = 128 + static_cast<size_t>(kStages) * stage_rows * row_bytes * (HILO ? 2 : 1);
+  cudaError_t e = cudaFuncSetAttribute(k_stream_dot<EL, HILO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  long long grid = num_sms;
+  if (grid > a.F) grid = a.F;
+  if (grid < 1) grid = 1;
+  k_stream_dot<EL, HILO><<<static_cast<unsigned>(grid), kThreads, smem, st>>>(a, stage_rows);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_stream_dot(const StreamArgs& a, int num_sms, cudaStream_t st) {
+  if (a.F <= 0) return cudaSuccess;
+  if (a.row_len <= 0 || a.row_len > kMaxRowLen || (a.row_len % 8) != 0) return cudaErrorInvalidValue;
+  switch (a.el) {
+    case EL_FP32: return launch_t<EL_FP32, false>(a, num_sms, st);
+    case EL_BF16: return launch_t<EL_BF16, false>(a, num_sms, st);
+    case EL_BF16_HILO: return launch_t<EL_BF16, true>(a, num_sms, st);
+    case EL_FP8: return launch_t<EL_FP8, false>(a, num_sms, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace s2w

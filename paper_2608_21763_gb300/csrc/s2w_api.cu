@@ -1,0 +1,573 @@
+// C ABI of libs2w (include/s2w.h): context, operator loading, and the
+// waveform pipeline q = F_q D_t F_G s on one GPU.
+//
+// Pipeline of one s2w_waveforms call (Alg. 1 steps 2-4, each matvec by
+// Alg. 2):
+//   K1  rfft of every slip row, zero-padded to 2 Nt      -> shat [l][b][Ns_pad]
+//   per rupture b:
+//     K2  stage-1 per-bin contraction (HBM stream of Ghat) -> mhat [l][Ng]
+//     K3  IFFT + Truncate, D_t, ZeroPad + FFT              -> vhat [l][nseg*RL]
+//     K4  stage-2 per-bin contraction over grid segments   -> partial [b][l][seg][o]
+//   K5  sum of segment partials (the in-device ReduceSum of Alg. 1 step 5)
+//       fused with IFFT + Truncate                        -> q [b][o][Nt]
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "s2w_internal.cuh"
+
+using namespace s2w;
+
+struct s2w_ctx {
+  int Ns, Ng, No, Nt, Nb, L, Ns_pad;
+  int RL, nseg;  // stage-2 grid segments: nseg segments of RL columns
+  s2w_opts opts;
+  int device, num_sms;
+  // resident operators
+  void* G = nullptr;
+  void* G_lo = nullptr;
+  float* G_scale = nullptr;
+  int nblk = 0;
+  void* P = nullptr;
+  size_t g_bytes = 0, p_bytes = 0;
+  float2* tw = nullptr;
+  // workspaces
+  float* ws_slip = nullptr;
+  float2* ws_shat = nullptr;
+  float2* ws_mhat = nullptr;
+  float2* ws_vhat = nullptr;
+  float2* ws_part = nullptr;
+  float* ws_q = nullptr;
+  float* ws_seafloor = nullptr;
+  int* d_status = nullptr;
+  std::vector<unsigned char> g_loaded, p_loaded;
+  long long g_count = 0, p_count = 0;
+  // per-stage event timers
+  struct Pending {
+    int stage;
+    cudaEvent_t a, b;
+  };
+  bool prof_on = false;
+  std::vector<cudaEvent_t> ev_free;
+  std::vector<Pending> pending;
+  double prof_ms[S2W_NUM_STAGES] = {0};
+  long long prof_cnt[S2W_NUM_STAGES] = {0};
+  long long launches = 0;
+  char err[512] = {0};
+};
+
+namespace {
+
+thread_local char g_create_err[512];
+
+int fail(s2w_ctx* c, int code, const char* fmt, ...) {
+  char* dst = c ? c->err : g_create_err;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(dst, 512, fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+#define CK(call)                                                                                    \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess)                                                                          \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? S2W_ERR_OOM : S2W_ERR_CUDA, "%s: %s (%s:%d)", \
+                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                               \
+  } while (0)
+
+template <class T>
+cudaError_t dalloc(T** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return cudaSuccess;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), bytes);
+  if (e != cudaSuccess) return e;
+  return cudaMemset(*p, 0, bytes);
+}
+
+// 1 = device memory of `device`, 0 = host memory, -1 = device memory of
+// another device.
+int pointer_kind(const void* p, int device) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return at.device == device ? 1 : -1;
+  return 0;
+}
+
+bool supported_nt(int Nt) { return Nt == 32 || Nt == 64 || Nt == 128 || Nt == 256 || Nt == 512; }
+
+long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
+
+cudaEvent_t take_event(s2w_ctx* c) {
+  if (!c->ev_free.empty()) {
+    cudaEvent_t e = c->ev_free.back();
+    c->ev_free.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+// Brackets one stage launch with CUDA events on its stream when the profiler
+// is on; counts `n` kernel launches either way.
+struct StageTimer {
+  s2w_ctx* c;
+  int stage;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr, b = nullptr;
+  StageTimer(s2w_ctx* c_, int stage_, cudaStream_t st_, int n = 1) : c(c_), stage(stage_), st(st_) {
+    c->launches += n;
+    if (c->prof_on) {
+      a = take_event(c);
+      b = take_event(c);
+      if (a && b) cudaEventRecord(a, st);
+    }
+  }
+  ~StageTimer() {
+    if (a && b) {
+      cudaEventRecord(b, st);
+      c->pending.push_back({stage, a, b});
+    } else {
+      if (a) c->ev_free.push_back(a);
+      if (b) c->ev_free.push_back(b);
+    }
+  }
+};
+
+void free_all(s2w_ctx* c) {
+  for (auto& p : c->pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (auto e : c->ev_free) cudaEventDestroy(e);
+  c->pending.clear();
+  c->ev_free.clear();
+  void* ps[] = {c->G, c->G_lo, c->G_scale, c->P, c->tw, c->ws_slip, c->ws_shat, c->ws_mhat,
+                c->ws_vhat, c->ws_part, c->ws_q, c->ws_seafloor, c->d_status};
+  for (void* p : ps)
+    if (p) cudaFree(p);
+}
+
+}  // namespace
+
+extern "C" {
+
+void s2w_default_opts(s2w_opts* o) {
+  if (!o) return;
+  o->prec_g = S2W_PREC_FP32;
+  o->prec_p = S2W_PREC_FP32;
+  o->dt_mode = S2W_DT_BACKWARD;
+  o->dt = 1.0;
+  o->max_batch = 1;
+  o->device = 0;
+}
+
+const char* s2w_status_string(int s) {
+  switch (s) {
+    case S2W_OK: return "S2W_OK";
+    case S2W_ERR_ARG: return "S2W_ERR_ARG";
+    case S2W_ERR_OOM: return "S2W_ERR_OOM";
+    case S2W_ERR_STATE: return "S2W_ERR_STATE";
+    case S2W_ERR_CUDA: return "S2W_ERR_CUDA";
+    case S2W_ERR_TIMEOUT: return "S2W_ERR_TIMEOUT";
+    case S2W_ERR_UNSUPPORTED: return "S2W_ERR_UNSUPPORTED";
+    default: return "S2W_ERR_UNKNOWN";
+  }
+}
+
+const char* s2w_last_error(const s2w_ctx* ctx) { return ctx ? ctx->err : g_create_err; }
+
+int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** out) {
+  s2w_ctx* ctx = nullptr;
+  if (!out) return fail(nullptr, S2W_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  s2w_opts o;
+  s2w_default_opts(&o);
+  if (opts) o = *opts;
+  if (Ns < 1 || Ng < 1 || No < 1) return fail(nullptr, S2W_ERR_ARG, "Ns, Ng, No must be >= 1");
+  if (!supported_nt(Nt)) return fail(nullptr, S2W_ERR_UNSUPPORTED, "Nt=%d: supported 32, 64, 128, 256, 512", Nt);
+  if (Ns > 1024) return fail(nullptr, S2W_ERR_UNSUPPORTED, "Ns=%d > 1024", Ns);
+  if (o.prec_g < S2W_PREC_FP32 || o.prec_g > S2W_PREC_FP8_E4M3)
+    return fail(nullptr, S2W_ERR_ARG, "prec_g=%d", o.prec_g);
+  if (o.prec_p != S2W_PREC_FP32 && o.prec_p != S2W_PREC_BF16)
+    return fail(nullptr, S2W_ERR_UNSUPPORTED, "prec_p=%d: FP32 or BF16", o.prec_p);
+  if (o.dt_mode != S2W_DT_BACKWARD && o.dt_mode != S2W_DT_NONE)
+    return fail(nullptr, S2W_ERR_ARG, "dt_mode=%d", o.dt_mode);
+  if (!(o.dt > 0.0)) return fail(nullptr, S2W_ERR_ARG, "dt must be > 0");
+  if (o.max_batch < 1) return fail(nullptr, S2W_ERR_ARG, "max_batch must be >= 1");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || o.device < 0 || o.device >= ndev) {
+    cudaGetLastError();
+    return fail(nullptr, S2W_ERR_CUDA, "no CUDA device %d", o.device);
+  }
+  DeviceGuard guard(o.device);
+  ctx = new s2w_ctx();
+  ctx->Ns = Ns;
+  ctx->Ng = Ng;
+  ctx->No = No;
+  ctx->Nt = Nt;
+  ctx->Nb = Nt + 1;
+  ctx->L = 2 * Nt;
+  ctx->Ns_pad = static_cast<int>(round_up(Ns, 8));
+  ctx->nseg = static_cast<int>((Ng + 1023) / 1024);
+  ctx->RL = static_cast<int>(round_up((Ng + ctx->nseg - 1) / ctx->nseg, 8));
+  ctx->opts = o;
+  ctx->device = o.device;
+  cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, o.device);
+  ctx->g_loaded.assign(Ng, 0);
+  ctx->p_loaded.assign(Ng, 0);
+
+  const long long Nb = ctx->Nb, B = o.max_batch;
+  const size_t gcb = elem_complex_bytes(o.prec_g);
+  ctx->nblk = static_cast<int>((Ng + 255) / 256);
+  ctx->g_bytes = static_cast<size_t>(Nb) * Ng * ctx->Ns_pad * gcb;
+  if (o.prec_g == S2W_PREC_BF16_HILO) ctx->g_bytes *= 2;
+  if (o.prec_g == S2W_PREC_FP8_E4M3) ctx->g_bytes += static_cast<size_t>(Nb) * ctx->nblk * sizeof(float);
+  ctx->p_bytes = static_cast<size_t>(Nb) * ctx->nseg * No * ctx->RL * elem_complex_bytes(o.prec_p);
+
+  auto bad = [&](cudaError_t e, const char* what) {
+    fail(nullptr, e == cudaErrorMemoryAllocation ? S2W_ERR_OOM : S2W_ERR_CUDA, "%s: %s", what,
+         cudaGetErrorString(e));
+    free_all(ctx);
+    delete ctx;
+    return e == cudaErrorMemoryAllocation ? S2W_ERR_OOM : S2W_ERR_CUDA;
+  };
+  cudaError_t e;
+  const size_t gsz = static_cast<size_t>(Nb) * Ng * ctx->Ns_pad * gcb;
+  if ((e = dalloc(&ctx->G, gsz)) != cudaSuccess) return bad(e, "Ghat");
+  if (o.prec_g == S2W_PREC_BF16_HILO && (e = dalloc(&ctx->G_lo, gsz)) != cudaSuccess) return bad(e, "Ghat lo");
+  if (o.prec_g == S2W_PREC_FP8_E4M3 &&
+      (e = dalloc(&ctx->G_scale, static_cast<size_t>(Nb) * ctx->nblk * sizeof(float))) != cudaSuccess)
+    return bad(e, "Ghat scales");
+  if ((e = dalloc(&ctx->P, ctx->p_bytes)) != cudaSuccess) return bad(e, "Phat");
+  if ((e = dalloc(&ctx->tw, sizeof(float2) * ctx->L)) != cudaSuccess) return bad(e, "twiddles");
+  if ((e = dalloc(&ctx->ws_slip, sizeof(float) * B * Ns * Nt)) != cudaSuccess) return bad(e, "slip workspace");
+  if ((e = dalloc(&ctx->ws_shat, sizeof(float2) * Nb * B * ctx->Ns_pad)) != cudaSuccess)
+    return bad(e, "slip spectra");
+  if ((e = dalloc(&ctx->ws_mhat, sizeof(float2) * Nb * Ng)) != cudaSuccess) return bad(e, "seafloor spectra");
+  if ((e = dalloc(&ctx->ws_vhat, sizeof(float2) * Nb * ctx->nseg * ctx->RL)) != cudaSuccess)
+    return bad(e, "velocity spectra");
+  if ((e = dalloc(&ctx->ws_part, sizeof(float2) * B * Nb * ctx->nseg * No)) != cudaSuccess)
+    return bad(e, "stage-2 partials");
+  if ((e = dalloc(&ctx->ws_q, sizeof(float) * B * No * Nt)) != cudaSuccess) return bad(e, "waveform workspace");
+  if ((e = dalloc(&ctx->ws_seafloor, sizeof(float) * static_cast<size_t>(Ng) * Nt)) != cudaSuccess)
+    return bad(e, "seafloor workspace");
+  if ((e = dalloc(&ctx->d_status, sizeof(int))) != cudaSuccess) return bad(e, "status word");
+  if ((e = launch_twiddles(ctx->tw, ctx->L, nullptr)) != cudaSuccess) return bad(e, "twiddles");
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bad(e, "create sync");
+  *out = ctx;
+  return S2W_OK;
+}
+
+int s2w_destroy(s2w_ctx* ctx) {
+  if (!ctx) return S2W_OK;
+  DeviceGuard guard(ctx->device);
+  cudaDeviceSynchronize();
+  free_all(ctx);
+  delete ctx;
+  return S2W_OK;
+}
+
+int s2w_operator_bytes(const s2w_ctx* ctx, size_t* g_bytes, size_t* p_bytes) {
+  if (!ctx) return S2W_ERR_ARG;
+  if (g_bytes) *g_bytes = ctx->g_bytes;
+  if (p_bytes) *p_bytes = ctx->p_bytes;
+  return S2W_OK;
+}
+
+int s2w_load_greens(s2w_ctx* ctx, int g0, int ng, const float* G, void* stream) {
+  if (!ctx) return S2W_ERR_ARG;
+  if (!G || g0 < 0 || ng < 1 || static_cast<long long>(g0) + ng > ctx->Ng)
+    return fail(ctx, S2W_ERR_ARG, "load_greens: rows [%d, %d) outside [0, %d) or G is NULL", g0, g0 + ng, ctx->Ng);
+  const bool fp8 = ctx->opts.prec_g == S2W_PREC_FP8_E4M3;
+  if (fp8 && (g0 % 256 != 0 || (ng % 256 != 0 && g0 + ng != ctx->Ng)))
+    return fail(ctx, S2W_ERR_ARG, "load_greens: FP8 storage needs 256-row aligned chunks (g0=%d, ng=%d)", g0, ng);
+  DeviceGuard guard(ctx->device);
+  if (pointer_kind(G, ctx->device) < 0) return fail(ctx, S2W_ERR_ARG, "load_greens: G is on another device");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const long long Ns = ctx->Ns, Nt = ctx->Nt, Nb = ctx->Nb, Ns_pad = ctx->Ns_pad;
+  const long long RC = 256;
+  float* stage_t = nullptr;
+  float2* stage_s = nullptr;
+  CK(cudaMalloc(&stage_t, sizeof(float) * RC * Ns * Nt));
+  cudaError_t e = cudaMalloc(&stage_s, sizeof(float2) * Nb * RC * Ns_pad);
+  if (e != cudaSuccess) {
+    cudaFree(stage_t);
+    CK(e);
+  }
+  int rc_status = S2W_OK;
+  for (long long r = 0; r < ng && rc_status == S2W_OK; r += RC) {
+    const long long rc = std::min(RC, static_cast<long long>(ng) - r);
+    const long long row0 = g0 + r;
+    auto step = [&]() -> int {
+      CK(cudaMemcpyAsync(stage_t, G + r * Ns * Nt, sizeof(float) * rc * Ns * Nt, cudaMemcpyDefault, st));
+      CK(cudaMemsetAsync(stage_s, 0, sizeof(float2) * Nb * rc * Ns_pad, st));
+      ctx->launches += fp8 ? 3 : 2;
+      CK(launch_rfft_rows(stage_t, rc * Ns, static_cast<int>(Nt), static_cast<int>(Nt), ctx->tw, stage_s,
+                          rc * Ns_pad, Ns, Ns_pad, st));
+      if (fp8) {
+        CK(launch_fp8_store(stage_s, static_cast<int>(Nb), rc, static_cast<int>(Ns_pad), row0, ctx->Ng,
+                            ctx->G_scale, ctx->nblk, ctx->G, st));
+      } else {
+        CK(launch_store_blocks(stage_s, static_cast<int>(Nb), rc * Ns_pad, ctx->opts.prec_g, ctx->G, ctx->G_lo,
+                               static_cast<long long>(ctx->Ng) * Ns_pad, row0 * Ns_pad, st));
+      }
+      return S2W_OK;
+    };
+    rc_status = step();
+  }
+  if (rc_status == S2W_OK) {
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc_status = fail(ctx, S2W_ERR_CUDA, "load_greens: %s", cudaGetErrorString(e));
+  }
+  cudaStreamSynchronize(st);
+  cudaFree(stage_t);
+  cudaFree(stage_s);
+  if (rc_status != S2W_OK) return rc_status;
+  for (int r = 0; r < ng; ++r) {
+    if (!ctx->g_loaded[g0 + r]) ++ctx->g_count;
+    ctx->g_loaded[g0 + r] = 1;
+  }
+  return S2W_OK;
+}
+
+int s2w_load_adjoint(s2w_ctx* ctx, int g0, int ng, const float* P, void* stream) {
+  if (!ctx) return S2W_ERR_ARG;
+  if (!P || g0 < 0 || ng < 1 || static_cast<long long>(g0) + ng > ctx->Ng)
+    return fail(ctx, S2W_ERR_ARG, "load_adjoint: columns [%d, %d) outside [0, %d) or P is NULL", g0, g0 + ng,
+                ctx->Ng);
+  DeviceGuard guard(ctx->device);
+  if (pointer_kind(P, ctx->device) < 0) return fail(ctx, S2W_ERR_ARG, "load_adjoint: P is on another device");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const long long No = ctx->No, Nt = ctx->Nt, Nb = ctx->Nb;
+  const long long RC = 2048;
+  float* stage_t = nullptr;
+  float2* stage_s = nullptr;
+  CK(cudaMalloc(&stage_t, sizeof(float) * No * RC * Nt));
+  cudaError_t e = cudaMalloc(&stage_s, sizeof(float2) * Nb * No * RC);
+  if (e != cudaSuccess) {
+    cudaFree(stage_t);
+    CK(e);
+  }
+  int rc_status = S2W_OK;
+  for (long long c = 0; c < ng && rc_status == S2W_OK; c += RC) {
+    const long long rc = std::min(RC, static_cast<long long>(ng) - c);
+    auto step = [&]() -> int {
+      CK(cudaMemcpy2DAsync(stage_t, sizeof(float) * rc * Nt, P + c * Nt, sizeof(float) * ng * Nt,
+                           sizeof(float) * rc * Nt, No, cudaMemcpyDefault, st));
+      ctx->launches += 2;
+      CK(launch_rfft_rows(stage_t, No * rc, static_cast<int>(Nt), static_cast<int>(Nt), ctx->tw, stage_s, No * rc,
+                          rc, rc, st));
+      CK(launch_store_adjoint(stage_s, static_cast<int>(Nb), static_cast<int>(No), rc, g0 + c, ctx->RL, ctx->nseg,
+                              ctx->opts.prec_p, ctx->P, st));
+      return S2W_OK;
+    };
+    rc_status = step();
+  }
+  if (rc_status == S2W_OK) {
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc_status = fail(ctx, S2W_ERR_CUDA, "load_adjoint: %s", cudaGetErrorString(e));
+  }
+  cudaStreamSynchronize(st);
+  cudaFree(stage_t);
+  cudaFree(stage_s);
+  if (rc_status != S2W_OK) return rc_status;
+  for (int r = 0; r < ng; ++r) {
+    if (!ctx->p_loaded[g0 + r]) ++ctx->p_count;
+    ctx->p_loaded[g0 + r] = 1;
+  }
+  return S2W_OK;
+}
+
+int s2w_waveforms(s2w_ctx* ctx, const float* slip, int B, float* q, float* seafloor, void* stream) {
+  if (!ctx) return S2W_ERR_ARG;
+  if (B < 0 || B > ctx->opts.max_batch)
+    return fail(ctx, S2W_ERR_ARG, "waveforms: B=%d outside [0, max_batch=%d]", B, ctx->opts.max_batch);
+  if (B == 0) return S2W_OK;
+  if (!slip || !q) return fail(ctx, S2W_ERR_ARG, "waveforms: slip and q must not be NULL");
+  if (ctx->g_count != ctx->Ng || ctx->p_count != ctx->Ng)
+    return fail(ctx, S2W_ERR_STATE, "waveforms: operators not fully loaded (%lld/%d Green rows, %lld/%d adjoint cols)",
+                ctx->g_count, ctx->Ng, ctx->p_count, ctx->Ng);
+  DeviceGuard guard(ctx->device);
+  const int ks = pointer_kind(slip, ctx->device), kq = pointer_kind(q, ctx->device);
+  const int kf = seafloor ? pointer_kind(seafloor, ctx->device) : 1;
+  if (ks < 0 || kq < 0 || kf < 0) return fail(ctx, S2W_ERR_ARG, "waveforms: pointer on another device");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const long long Ns = ctx->Ns, Ng = ctx->Ng, No = ctx->No, Nt = ctx->Nt, Nb = ctx->Nb, Ns_pad = ctx->Ns_pad;
+  const float* slip_d = slip;
+  if (ks == 0) {
+    StageTimer t(ctx, 5, st, 0);
+    CK(cudaMemcpyAsync(ctx->ws_slip, slip, sizeof(float) * B * Ns * Nt, cudaMemcpyHostToDevice, st));
+    slip_d = ctx->ws_slip;
+  }
+  float* q_d = kq == 1 ? q : ctx->ws_q;
+  // K1
+  {
+  StageTimer t(ctx, 0, st);
+  CK(launch_rfft_rows(slip_d, B * Ns, static_cast<int>(Nt), static_cast<int>(Nt), ctx->tw, ctx->ws_shat,
+                      B * Ns_pad, Ns, Ns_pad, st));
+  }
+  const long long part_b = Nb * ctx->nseg * No;
+  for (int b = 0; b < B; ++b) {
+    // K2
+    StreamArgs a1{};
+    a1.rows = ctx->G;
+    a1.rows_lo = ctx->G_lo;
+    a1.F = Nb * Ng;
+    a1.row_len = static_cast<int>(Ns_pad);
+    a1.el = ctx->opts.prec_g;
+    a1.x = ctx->ws_shat + b * Ns_pad;
+    a1.x_stride = B * Ns_pad;
+    a1.rows_per_vec = Ng;
+    a1.scale = ctx->G_scale;
+    a1.nblk = ctx->nblk;
+    a1.y = ctx->ws_mhat;
+    a1.status = ctx->d_status;
+    {
+      StageTimer t(ctx, 1, st);
+      CK(launch_stream_dot(a1, ctx->num_sms, st));
+    }
+    // K3
+    float* sf = nullptr;
+    if (seafloor) sf = kf == 1 ? seafloor + b * Ng * Nt : ctx->ws_seafloor;
+    {
+    StageTimer t(ctx, 2, st);
+    CK(launch_retransform(ctx->ws_mhat, Ng, Ng, static_cast<int>(Nt), ctx->tw,
+                          static_cast<float>(1.0 / ctx->opts.dt), ctx->opts.dt_mode, ctx->ws_vhat,
+                          static_cast<long long>(ctx->nseg) * ctx->RL, sf, st));
+    }
+    if (seafloor && kf == 0)
+      CK(cudaMemcpyAsync(seafloor + b * Ng * Nt, ctx->ws_seafloor, sizeof(float) * Ng * Nt, cudaMemcpyDeviceToHost,
+                         st));
+    // K4
+    StreamArgs a2{};
+    a2.rows = ctx->P;
+    a2.F = Nb * ctx->nseg * No;
+    a2.row_len = ctx->RL;
+    a2.el = ctx->opts.prec_p;
+    a2.x = ctx->ws_vhat;
+    a2.x_stride = ctx->RL;
+    a2.rows_per_vec = No;
+    a2.y = ctx->ws_part + b * part_b;
+    a2.status = ctx->d_status;
+    {
+      StageTimer t(ctx, 3, st);
+      CK(launch_stream_dot(a2, ctx->num_sms, st));
+    }
+  }
+  // K5
+  {
+  StageTimer t(ctx, 4, st);
+  CK(launch_reduce_irfft(ctx->ws_part, B, static_cast<int>(No), ctx->nseg, static_cast<int>(Nt), part_b, ctx->tw,
+                         q_d, st));
+  }
+  if (kq == 0) {
+    StageTimer t(ctx, 5, st, 0);
+    CK(cudaMemcpyAsync(q, q_d, sizeof(float) * B * No * Nt, cudaMemcpyDeviceToHost, st));
+  }
+  if (kq == 0 || (seafloor && kf == 0)) CK(cudaStreamSynchronize(st));
+  return S2W_OK;
+}
+
+int s2w_rfft(s2w_ctx* ctx, const float* x, long long rows, float* X, void* stream) {
+  if (!ctx) return S2W_ERR_ARG;
+  if (rows < 0 || (rows > 0 && (!x || !X))) return fail(ctx, S2W_ERR_ARG, "rfft: bad arguments");
+  if (rows == 0) return S2W_OK;
+  DeviceGuard guard(ctx->device);
+  if (pointer_kind(x, ctx->device) != 1 || pointer_kind(X, ctx->device) != 1)
+    return fail(ctx, S2W_ERR_ARG, "rfft: x and X must be device pointers");
+  ctx->launches += 1;
+  CK(launch_rfft_rows(x, rows, ctx->Nt, ctx->Nt, ctx->tw, reinterpret_cast<float2*>(X), 1, 1, ctx->Nb,
+                      static_cast<cudaStream_t>(stream)));
+  return S2W_OK;
+}
+
+int s2w_irfft(s2w_ctx* ctx, const float* X, long long rows, float* x, void* stream) {
+  if (!ctx) return S2W_ERR_ARG;
+  if (rows < 0 || (rows > 0 && (!x || !X))) return fail(ctx, S2W_ERR_ARG, "irfft: bad arguments");
+  if (rows == 0) return S2W_OK;
+  DeviceGuard guard(ctx->device);
+  if (pointer_kind(x, ctx->device) != 1 || pointer_kind(X, ctx->device) != 1)
+    return fail(ctx, S2W_ERR_ARG, "irfft: x and X must be device pointers");
+  ctx->launches += 1;
+  CK(launch_irfft_rows(reinterpret_cast<const float2*>(X), rows, ctx->Nt, ctx->tw, x,
+                       static_cast<cudaStream_t>(stream)));
+  return S2W_OK;
+}
+
+int s2w_profile_enable(s2w_ctx* ctx, int on) {
+  if (!ctx) return S2W_ERR_ARG;
+  DeviceGuard guard(ctx->device);
+  for (auto& p : ctx->pending) {
+    cudaEventSynchronize(p.b);
+    ctx->ev_free.push_back(p.a);
+    ctx->ev_free.push_back(p.b);
+  }
+  ctx->pending.clear();
+  for (int i = 0; i < S2W_NUM_STAGES; ++i) {
+    ctx->prof_ms[i] = 0.0;
+    ctx->prof_cnt[i] = 0;
+  }
+  ctx->prof_on = on != 0;
+  return S2W_OK;
+}
+
+int s2w_profile_read(s2w_ctx* ctx, s2w_profile* out) {
+  if (!ctx || !out) return S2W_ERR_ARG;
+  DeviceGuard guard(ctx->device);
+  for (auto& p : ctx->pending) {
+    CK(cudaEventSynchronize(p.b));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, p.a, p.b));
+    ctx->prof_ms[p.stage] += ms;
+    ctx->prof_cnt[p.stage] += 1;
+    ctx->ev_free.push_back(p.a);
+    ctx->ev_free.push_back(p.b);
+  }
+  ctx->pending.clear();
+  for (int i = 0; i < S2W_NUM_STAGES; ++i) {
+    out->ms[i] = ctx->prof_ms[i];
+    out->count[i] = ctx->prof_cnt[i];
+  }
+  out->launches = ctx->launches;
+  return S2W_OK;
+}
+
+int s2w_sync(s2w_ctx* ctx) {
+  if (!ctx) return S2W_ERR_ARG;
+  DeviceGuard guard(ctx->device);
+  CK(cudaDeviceSynchronize());
+  int h = 0;
+  CK(cudaMemcpy(&h, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h != 0) {
+    CK(cudaMemset(ctx->d_status, 0, sizeof(int)));
+    return fail(ctx, S2W_ERR_TIMEOUT, "a kernel-side wait expired (status bits 0x%x)", h);
+  }
+  return S2W_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,160 @@
+// Internal declarations shared by the CUDA translation units of libs2w.
+// Nothing here is part of the public C ABI (include/s2w.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <stdint.h>
+
+#include "../../include/s2w.h"
+
+namespace s2w {
+
+// Device status bits (latched in a device word, read back by s2w_sync).
+enum : int {
+  DEV_ERR_TIMEOUT_FULL = 1 << 0,   // consumer gave up waiting for a TMA stage
+  DEV_ERR_TIMEOUT_EMPTY = 1 << 1,  // producer gave up waiting for a free stage
+  DEV_ERR_TIMEOUT_MMA = 1 << 2,    // tensor-core pipeline wait gave up
+  DEV_ERR_SHAPE = 1 << 3,          // a kernel saw an argument outside its limits
+};
+
+// Wall-clock bound on every spin-wait inside a kernel (nanoseconds).
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;
+
+// Storage codes of the resident spectra (same values as S2W_PREC_*).
+enum Elem : int { EL_FP32 = 0, EL_BF16 = 1, EL_BF16_HILO = 2, EL_FP8 = 3 };
+
+__host__ __device__ inline int elem_complex_bytes(int el) {
+  return el == EL_FP32 ? 8 : (el == EL_FP8 ? 2 : 4);
+}
+
+// ---------------------------------------------------------------------------
+// complex helpers (float2 = re, im)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+
+// ---------------------------------------------------------------------------
+// PTX wrappers: shared-memory addresses, mbarriers, bulk async copies
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for phase `parity` of `bar` to complete, for at most kWaitLimitNs.
+// On timeout, latch `code` into the device status word and return false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* status, int code) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 0u && globaltimer() - t0 > kWaitLimitNs) {
+      atomicOr(status, code);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
+// Bulk (non-tensor) asynchronous copy global -> this CTA's shared memory,
+// completing `bytes` of transaction count on `bar`.  Both addresses must be
+// 16-byte aligned and `bytes` a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* sdst, const void* gsrc, uint32_t bytes, uint64_t* bar,
+                                         uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          smem_u32(sdst)),
+      "l"(gsrc), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+      : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers implemented in the kernel translation units.
+// All return cudaError_t of the launch (cudaGetLastError()).
+// ---------------------------------------------------------------------------
+// k_fft.cu
+cudaError_t launch_twiddles(float2* tw, int L, cudaStream_t st);
+// Rows x[row][0..n_in) zero-padded to L = 2 Nt; bins l = 0..Nt of row `row`
+// go to X[l * ld_l + (row / rows_a) * ld_a + row % rows_a].
+cudaError_t launch_rfft_rows(const float* x, long long rows, int n_in, int Nt, const float2* tw, float2* X,
+                             long long ld_l, long long rows_a, long long ld_a, cudaStream_t st);
+// Rows X[row][0..Nt] -> first Nt samples x[row][0..Nt) of the length-2Nt IFFT.
+cudaError_t launch_irfft_rows(const float2* X, long long rows, int Nt, const float2* tw, float* x, cudaStream_t st);
+cudaError_t launch_retransform(const float2* mhat, long long Ng, long long ld_m, int Nt, const float2* tw,
+                               float inv_dt, int dt_mode, float2* vhat, long long ld_v, float* seafloor,
+                               cudaStream_t st);
+cudaError_t launch_reduce_irfft(const float2* part, int B, int No, int nseg, int Nt, long long ld_b, const float2* tw,
+                                float* q, cudaStream_t st);
+cudaError_t launch_store_blocks(const float2* src, int Nb, long long n_per_l, int el, void* dst, void* dst_lo,
+                                long long ld_dst_l, long long dst_off, cudaStream_t st);
+cudaError_t launch_store_adjoint(const float2* src, int Nb, int No, long long nc, long long c0, int RL, int nseg,
+                                 int el, void* dst, cudaStream_t st);
+cudaError_t launch_fp8_store(const float2* spec, int Nb, long long rows, int Ns_pad, long long row0, long long Ng,
+                             float* scale, int nblk, void* dst, cudaStream_t st);
+
+// k_stream.cu: y[f] = sum_c rows[f][c] * x_vec(f)[c] for f < F, with
+// x_vec(f) = x + (f / rows_per_vec) * x_stride.  Rows are contiguous,
+// row_len complex entries each, row_len a multiple of 8 and <= 1024.
+struct StreamArgs {
+  const void* rows;
+  const void* rows_lo;        // BF16 hi/lo: the lo array (same layout), else nullptr
+  long long F;
+  int row_len;
+  int el;                     // Elem
+  const float2* x;
+  long long x_stride;         // complex entries between consecutive x vectors
+  long long rows_per_vec;
+  const float* scale;         // FP8: scale[(f / rows_per_vec) * nblk + (f % rows_per_vec) / 256]
+  int nblk;
+  float2* y;
+  int* status;
+};
+cudaError_t launch_stream_dot(const StreamArgs& a, int num_sms, cudaStream_t st);
+
+}  // namespace s2w

@@ -1,0 +1,66 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, and exports
+every entry point that include/s2w.h declares.  No kernel is launched."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_2608_21763_gb300 as s2w
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                      "include", "s2w.h")
+
+
+def declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(s2w_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_binding_exports():
+    assert declared() == sorted(s2w.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol():
+    path = s2w.lib()._name
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True,
+                         text=True, check=True).stdout
+    syms = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    missing = [f for f in declared() if f not in syms]
+    assert not missing, missing
+
+
+def test_library_is_built_for_sm_103a():
+    out = subprocess.run(["cuobjdump", "--list-elf", s2w.lib()._name],
+                         capture_output=True, text=True)
+    if out.returncode != 0:
+        pytest.skip("cuobjdump unavailable")
+    assert "sm_103a" in out.stdout
+
+
+def test_status_strings_and_default_opts():
+    L = s2w.lib()
+    assert L.s2w_status_string(0) == b"S2W_OK"
+    assert L.s2w_status_string(-5) == b"S2W_ERR_TIMEOUT"
+    o = s2w.Opts()
+    L.s2w_default_opts(ctypes.byref(o))
+    assert (o.prec_g, o.prec_p, o.dt_mode, o.dt, o.max_batch, o.device) == (0, 0, 0, 1.0, 1, 0)
+
+
+def test_create_rejects_bad_shapes_before_touching_a_device():
+    L = s2w.lib()
+    h = ctypes.c_void_p()
+    assert L.s2w_create(16, 64, 4, 48, None, ctypes.byref(h)) == -6   # Nt unsupported
+    assert h.value is None
+    assert b"Nt=48" in L.s2w_last_error(None)
+    assert L.s2w_create(0, 64, 4, 32, None, ctypes.byref(h)) == -1
+    assert L.s2w_create(2000, 64, 4, 32, None, ctypes.byref(h)) == -6  # Ns > 1024
+
+
+def test_null_context_is_an_argument_error():
+    L = s2w.lib()
+    assert L.s2w_waveforms(None, None, 1, None, None, None) == -1
+    assert L.s2w_sync(None) == -1
+    assert L.s2w_destroy(None) == 0

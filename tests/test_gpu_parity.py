@@ -1,0 +1,210 @@
+"""CUDA path against the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (relative L2 over all No x Nt samples of a rupture):
+  FP32 storage        1e-5  (the stated target for the FP32 path)
+  BF16 hi/lo storage  1e-5
+  BF16 storage        2e-3  (bf16 keeps 8 significant bits: ~2e-3 per entry)
+  FP8 e4m3 storage    3e-2  (3 mantissa bits with per-block scales)
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import make_context, oracle_reference, rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2608_21763_gb300 as s2w  # noqa: E402
+
+TOL = {"fp32": 1e-5, "bf16_hilo": 1e-5, "bf16": 2e-3, "fp8": 3e-2}
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    wl = synth.WORKLOADS["tiny"]
+    geom = wl.geometry_obj()
+    slip = wl.slip(geom, B=3)
+    q_ref, m_ref = oracle_reference(geom, wl.Nt, slip, seafloor=True)
+    return wl, geom, slip, q_ref, m_ref
+
+
+# ---------------------------------------------------------------- transforms
+@pytest.mark.parametrize("Nt", [32, 64, 128, 256, 512])
+def test_rfft_matches_oracle_dft(Nt):
+    ctx = s2w.Context(4, 8, 2, Nt)
+    x = np.random.default_rng(Nt).standard_normal((37, Nt))
+    X = ctx.rfft(torch.tensor(x, dtype=torch.float32, device="cuda")).cpu().numpy()
+    ref = oracle.dft_real(x.astype(np.float32), 2 * Nt)
+    assert rel_l2(X.real, ref.real) < 1e-6 and rel_l2(X.imag, ref.imag) < 1e-6
+
+
+@pytest.mark.parametrize("Nt", [32, 256, 512])
+def test_irfft_truncates_and_inverts(Nt):
+    ctx = s2w.Context(4, 8, 2, Nt)
+    rng = np.random.default_rng(Nt + 1)
+    X = rng.standard_normal((19, Nt + 1)) + 1j * rng.standard_normal((19, Nt + 1))
+    X[:, 0] = X[:, 0].real
+    X[:, -1] = X[:, -1].real
+    x = ctx.irfft(torch.tensor(X, dtype=torch.complex64, device="cuda")).cpu().numpy()
+    ref = np.fft.irfft(X, n=2 * Nt)[:, :Nt]
+    assert x.shape == (19, Nt)
+    assert rel_l2(x, ref) < 1e-6
+    # round trip on a signal supported on [0, Nt)
+    s = rng.standard_normal((5, Nt))
+    st = torch.tensor(s, dtype=torch.float32, device="cuda")
+    back = ctx.irfft(ctx.rfft(st)).cpu().numpy()
+    assert rel_l2(back, s) < 1e-6
+
+
+# ---------------------------------------------------------------- end to end
+@pytest.mark.parametrize("prec", ["fp32", "bf16_hilo", "bf16", "fp8"])
+def test_tiny_workload_against_oracle(tiny, prec):
+    wl, geom, slip, q_ref, _ = tiny
+    ctx = make_context(s2w, geom, wl.Nt, prec_g=prec, max_batch=3, chunk=256)
+    q = ctx.waveforms(torch.tensor(slip, dtype=torch.float32, device="cuda")).cpu().numpy()
+    err = rel_l2(q, q_ref)
+    print(f"tiny {prec}: rel-L2 per rupture {err}")
+    assert np.all(err <= TOL[prec]), err
+
+
+def test_seafloor_field_against_oracle(tiny):
+    wl, geom, slip, _, m_ref = tiny
+    ctx = make_context(s2w, geom, wl.Nt, max_batch=3)
+    s = torch.tensor(slip, dtype=torch.float32, device="cuda")
+    sf = torch.empty((3, geom.Ng, wl.Nt), dtype=torch.float32, device="cuda")
+    ctx.waveforms(s, seafloor=sf)
+    assert np.all(rel_l2(sf.cpu().numpy(), m_ref) <= 1e-5)
+
+
+def test_bf16_p_storage(tiny):
+    wl, geom, slip, q_ref, _ = tiny
+    ctx = make_context(s2w, geom, wl.Nt, prec_p="bf16", max_batch=3)
+    q = ctx.waveforms(torch.tensor(slip, dtype=torch.float32, device="cuda")).cpu().numpy()
+    assert np.all(rel_l2(q, q_ref) <= TOL["bf16"])
+
+
+def test_impulse_returns_green_column_and_composed_response(tiny):
+    """An impulse on subfault j returns column j of the Green's function as the
+    seafloor field, and (P * G)[:, j] as the waveforms when D_t is off."""
+    wl, geom, _, _, _ = tiny
+    j = 5
+    s = np.zeros((1, geom.Ns, wl.Nt))
+    s[0, j, 0] = 1.0
+    ctx = make_context(s2w, geom, wl.Nt, dt_mode="none")
+    sf = torch.empty((1, geom.Ng, wl.Nt), dtype=torch.float32, device="cuda")
+    q = ctx.waveforms(torch.tensor(s, dtype=torch.float32, device="cuda"), seafloor=sf).cpu().numpy()
+    G = geom.greens_rows(0, geom.Ng, wl.Nt)
+    P = geom.adjoint_cols(0, geom.Ng, wl.Nt)
+    assert rel_l2(sf.cpu().numpy()[0], G[:, j, :]) < 1e-5
+    q_ref = oracle.bltt_apply(P, G[:, j, :])
+    assert rel_l2(q[0], q_ref) < 1e-5
+
+
+def test_linearity_and_causality(tiny):
+    wl, geom, slip, _, _ = tiny
+    ctx = make_context(s2w, geom, wl.Nt)
+    dev = lambda a: torch.tensor(a[None], dtype=torch.float32, device="cuda")
+    s1, s2 = slip[0], slip[1]
+    q1 = ctx.waveforms(dev(s1)).cpu().numpy()[0].astype(np.float64)
+    q2 = ctx.waveforms(dev(s2)).cpu().numpy()[0].astype(np.float64)
+    q12 = ctx.waveforms(dev(2.0 * s1 - 0.5 * s2)).cpu().numpy()[0]
+    assert rel_l2(q12, 2.0 * q1 - 0.5 * q2) < 1e-5
+    n0 = 12
+    s3 = s1.copy()
+    s3[:, n0:] += np.random.default_rng(3).standard_normal(s3[:, n0:].shape)
+    q3 = ctx.waveforms(dev(s3)).cpu().numpy()[0]
+    d = q3 - q1
+    assert np.linalg.norm(d[:, :n0]) <= 1e-5 * np.linalg.norm(d)
+
+
+def test_time_shift(tiny):
+    wl, geom, slip, _, _ = tiny
+    ctx = make_context(s2w, geom, wl.Nt)
+    tau = 4
+    s = slip[0]
+    sh = np.zeros_like(s)
+    sh[:, tau:] = s[:, :-tau]
+    dev = lambda a: torch.tensor(a[None], dtype=torch.float32, device="cuda")
+    q = ctx.waveforms(dev(s)).cpu().numpy()[0]
+    qs = ctx.waveforms(dev(sh)).cpu().numpy()[0]
+    assert rel_l2(qs[:, tau:], q[:, :-tau]) < 1e-5
+    assert np.abs(qs[:, :tau]).max() <= 1e-5 * np.abs(q).max()
+
+
+def test_host_device_batch_and_chunking_agree_bitwise(tiny):
+    wl, geom, slip, _, _ = tiny
+    ctx = make_context(s2w, geom, wl.Nt, max_batch=3, chunk=1024)
+    ctx2 = make_context(s2w, geom, wl.Nt, max_batch=3, chunk=96, order=list(range(10, -1, -1)))
+    s32 = slip.astype(np.float32)
+    q_host = ctx.waveforms(s32)                                        # numpy: host path
+    q_dev = ctx.waveforms(torch.tensor(s32, device="cuda")).cpu().numpy()
+    q_ch = ctx2.waveforms(torch.tensor(s32, device="cuda")).cpu().numpy()
+    q_one = np.stack([ctx.waveforms(s32[b:b + 1])[0] for b in range(3)])
+    assert np.array_equal(q_host, q_dev)
+    assert np.array_equal(q_dev, q_ch)
+    assert np.array_equal(q_dev, q_one)
+
+
+@pytest.mark.parametrize("Ns,Ng,No,Nt", [(5, 1000, 3, 64), (1, 37, 1, 32), (1024, 300, 2, 32),
+                                         (7, 2100, 5, 128)])
+def test_ragged_shapes(Ns, Ng, No, Nt):
+    geom = synth.geometry_box(Ns, Ng, No, seed=Ns + Ng)
+    slip = np.random.default_rng(1).standard_normal((2, Ns, Nt))
+    slip[:, :, Nt // 2:] = 0
+    ctx = make_context(s2w, geom, Nt, max_batch=2, chunk=512)
+    q = ctx.waveforms(torch.tensor(slip, dtype=torch.float32, device="cuda")).cpu().numpy()
+    q_ref = oracle_reference(geom, Nt, slip)
+    assert np.all(rel_l2(q, q_ref) <= 1e-5)
+
+
+def test_errors_and_empty_batch(tiny):
+    wl, geom, slip, _, _ = tiny
+    ctx = s2w.Context(geom.Ns, geom.Ng, geom.No, wl.Nt, max_batch=2)
+    s = torch.tensor(slip[:1], dtype=torch.float32, device="cuda")
+    with pytest.raises(s2w.S2WError) as e:
+        ctx.waveforms(s)
+    assert e.value.status == -3          # operators not loaded
+    ctx.load_greens(0, geom.greens_rows(0, geom.Ng, wl.Nt, np.float32))
+    with pytest.raises(s2w.S2WError):
+        ctx.waveforms(s)                 # adjoint still missing
+    ctx.load_adjoint(0, geom.adjoint_cols(0, geom.Ng, wl.Nt, np.float32))
+    ctx.waveforms(s)
+    q = torch.empty((0, geom.No, wl.Nt), device="cuda")
+    ctx.waveforms(torch.empty((0, geom.Ns, wl.Nt), device="cuda"), q=q)   # B = 0
+    with pytest.raises(s2w.S2WError) as e:
+        ctx.waveforms(torch.zeros((3, geom.Ns, wl.Nt), device="cuda"))
+    assert e.value.status == -1          # B > max_batch
+    with pytest.raises(s2w.S2WError):
+        ctx.load_greens(geom.Ng - 2, geom.greens_rows(0, 4, wl.Nt, np.float32))
+    fp8 = s2w.Context(geom.Ns, geom.Ng, geom.No, wl.Nt, prec_g="fp8")
+    with pytest.raises(s2w.S2WError):
+        fp8.load_greens(100, geom.greens_rows(100, 356, wl.Nt, np.float32))  # unaligned
+    ctx.sync()
+
+
+# ---------------------------------------------------------------- full size
+def test_plain_workload_full_size_fp32():
+    """Paper-shaped plain workload (963 subfaults, 20,000 grid points, 64
+    observations, 256 steps), FP32, one rupture: the whole waveform set
+    against the FP64 oracle (Eq. distributed-composition over grid chunks)."""
+    wl = synth.WORKLOADS["plain"]
+    geom = wl.geometry_obj()
+    slip = wl.slip(geom, B=1)
+    ctx = s2w.Context(wl.Ns, wl.Ng, wl.No, wl.Nt)
+    q_ref = None
+    chunk = 1024
+    for g0 in range(0, wl.Ng, chunk):
+        g1 = min(wl.Ng, g0 + chunk)
+        G = geom.greens_rows(g0, g1, wl.Nt)
+        P = geom.adjoint_cols(g0, g1, wl.Nt)
+        ctx.load_greens(g0, G.astype(np.float32))
+        ctx.load_adjoint(g0, np.ascontiguousarray(P.astype(np.float32)))
+        q_r = oracle.bltt_apply(P, oracle.dt_apply(oracle.bltt_apply(G, slip)))
+        q_ref = q_r if q_ref is None else q_ref + q_r
+    q = ctx.waveforms(torch.tensor(slip, dtype=torch.float32, device="cuda")).cpu().numpy()
+    err = rel_l2(q, q_ref)
+    print(f"plain fp32 full size: rel-L2 {err}")
+    assert np.all(err <= 1e-5), err
+    ctx.sync()
