@@ -138,6 +138,25 @@ def stage1_algorithmic_bytes(wl, prec_g, B):
     return op + Nb * wl.Ns * 8 * B + Nb * wl.Ng * 8 * B
 
 
+def measured_traffic(wl, prec_g):
+    """DRAM bytes of one stage-1 launch from the committed ncu capture
+    (profiles/traffic.json), scaled by the grid rows; None when the kernel
+    source changed since the capture or no capture exists for prec_g."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    src = os.path.join(ROOT, "paper_2608_21763_gb300", "csrc", "k_stream.cu")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    with open(src, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    per_row = d.get("stage1_bytes_per_grid_row", {}).get(prec_g)
+    if sha != d.get("k_stream_cu_sha256_16") or per_row is None or wl.Ns != 963 or wl.Nt != 256:
+        return None
+    return int(per_row * wl.Ng)
+
+
 # ------------------------------------------------------------------ oracle legs
 def oracle_rows_rate(wl, geom, slip, budget_s, chunk=512, start=0):
     """Time the FP64 oracle (stage 1, D_t, stage 2) on consecutive chunks of
@@ -287,7 +306,7 @@ def run_ours(args, rank, world, local_rank):
     roof = {"kernel": "k_stream_dot (stage-1 per-bin contraction)", "bound": "hbm",
             "achieved": round(achieved, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": round(achieved / pk["hbm_gbs"], 4), "peak_source": pk_kind,
-            "traffic": None, "algorithmic_bytes_per_launch": alg,
+            "traffic": measured_traffic(wl, args.prec_g), "algorithmic_bytes_per_launch": alg,
             "launch_ms": round(per_launch_s * 1e3, 4)}
     total_stage_ms = sum(v[0] for v in stages.values())
     stage_report = {k: {"ms_per_step": round(v[0] / args.steps, 4), "share": round(v[0] / total_stage_ms, 4)}

@@ -207,6 +207,24 @@ def gradient_partitioned(chunks_fn, s, d, dt_mode: str = "backward",
     return loss, g
 
 
+def fft_window(G, P, s, dt_mode: str = "backward", dt: float = 1.0):
+    """The 2 Nt-sample stage-2 output window that Alg. 2 forms before its
+    final Truncate: with the seafloor motion truncated to Nt samples (Alg. 2
+    step 5 of stage 1) and v = D_t m zero-padded to 2 Nt,
+    ``q_win[n] = sum_i sum_k P[o,i,k] v_i[n-k]`` for n < 2 Nt, written as
+    ``bltt_apply`` on zero-extended arrays.  Its first Nt samples are q.
+
+    A finite-precision FFT evaluation is accurate relative to this window,
+    not to its first Nt samples alone: when most of the window's energy lies
+    past Nt (signals arriving at the end of the record), the kept head is
+    small next to the rounding of the whole window."""
+    G, P, s = _f64(G), _f64(P), _f64(s)
+    m = bltt_apply(G, s)
+    v = _stage_dt(m, dt_mode, dt)
+    ext = lambda a: np.concatenate([a, np.zeros_like(a)], axis=-1)
+    return bltt_apply(ext(P), ext(v))
+
+
 def rel_l2(a, ref) -> np.ndarray:
     """Relative L2 error per leading index: ||a - ref||_2 / ||ref||_2."""
     a = np.asarray(a, dtype=np.float64)

@@ -39,3 +39,35 @@ def oracle_reference(geom, Nt, slip, dt_mode="backward", chunk=1024, seafloor=Fa
 
 def rel_l2(a, ref):
     return oracle.rel_l2(np.asarray(a, dtype=np.float64), ref)
+
+
+def window_norms(G, P, slip, dt_mode="backward"):
+    """Per-rupture norm of the oracle's 2 Nt-sample FFT window (oracle.fft_window)
+    and the window/head energy ratio kappa."""
+    qw = oracle.fft_window(G, P, slip, dt_mode)
+    if qw.ndim == 2:
+        qw = qw[None]
+    Nt = qw.shape[-1] // 2
+    wn = np.linalg.norm(qw.reshape(qw.shape[0], -1), axis=1)
+    hn = np.linalg.norm(qw[..., :Nt].reshape(qw.shape[0], -1), axis=1)
+    return wn, wn / np.maximum(hn, 1e-300)
+
+
+def assert_parity(q, q_ref, wnorm, kappa, tol, strict=1e-5, kappa_max=10.0, label=""):
+    """Two bars, per rupture:
+    (1) ||q - q_ref|| <= tol * ||q_win||  (accuracy on the FFT window's scale);
+    (2) for FP32-class paths (tol <= 1e-5) on well-conditioned windows
+        (kappa <= kappa_max): the plain rel-L2 <= strict."""
+    q = np.asarray(q, dtype=np.float64)
+    q_ref = np.asarray(q_ref, dtype=np.float64)
+    if q.ndim == 2:
+        q, q_ref = q[None], q_ref[None]
+    err = np.linalg.norm((q - q_ref).reshape(q.shape[0], -1), axis=1)
+    rel = err / np.maximum(np.linalg.norm(q_ref.reshape(q.shape[0], -1), axis=1), 1e-300)
+    win = err / np.maximum(wnorm, 1e-300)
+    print(f"{label}: rel-L2 {rel}, error / window norm {win}, kappa {kappa}")
+    assert np.all(win <= tol), (label, win, tol)
+    if tol <= 1e-5:
+        good = kappa <= kappa_max
+        assert np.all(rel[good] <= strict), (label, rel, kappa)
+    return rel, win

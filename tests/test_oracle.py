@@ -264,3 +264,20 @@ def test_oracle_on_tiny_workload_is_finite_and_nonzero():
     q = oracle.waveforms(G, P, s)
     assert q.shape == (1, wl.No, wl.Nt)
     assert np.all(np.isfinite(q)) and np.abs(q).max() > 0
+
+
+def test_fft_window_head_is_q_and_tail_is_linear_convolution(small):
+    """oracle.fft_window: first Nt samples are q; the whole window is the
+    linear convolution of P with the Nt-truncated v (numpy.convolve)."""
+    G, P, s = small
+    Nt = s.shape[1]
+    qw = oracle.fft_window(G, P, s[None])
+    assert qw.shape == (1, P.shape[0], 2 * Nt)
+    assert np.allclose(qw[0, :, :Nt], oracle.waveforms(G, P, s), rtol=0, atol=1e-13)
+    v = oracle.dt_apply(oracle.bltt_apply(G, s))
+    ref = np.zeros((P.shape[0], 2 * Nt))
+    for o in range(P.shape[0]):
+        for i in range(P.shape[1]):
+            # full linear convolution has 2 Nt - 1 samples; the last one is 0
+            ref[o, :2 * Nt - 1] += np.convolve(P[o, i], v[i])
+    assert np.allclose(qw[0], ref, rtol=0, atol=1e-12 * np.abs(ref).max())
