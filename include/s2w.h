@@ -121,6 +121,27 @@ int s2w_load_adjoint(s2w_ctx *ctx, int g0, int ng, const float *P, void *stream)
  * loaded (else S2W_ERR_STATE). */
 int s2w_waveforms(s2w_ctx *ctx, const float *slip, int B, float *q, float *seafloor, void *stream);
 
+/* Waveforms for ONE rupture without allocating any memory (the paper has no
+ * counterpart; this serves callers that cannot let a library allocate device
+ * memory: applications whose device memory all comes from their own pool,
+ * code inside a CUDA stream capture, latency-bound loops that must not wait on
+ * the allocator).  Same result as s2w_waveforms with B = 1 and no seafloor
+ * output; the intermediates live in a static 32 MiB device array that every
+ * GPU which loads libs2w holds until the process exits.
+ *   slip [Ns][Nt], q [No][Nt]: device pointers of the context's device.
+ * Limits: the problem's scratch (slip, seafloor and velocity spectra, stage-2
+ * partials: about 16 (Nt + 1) Ng bytes plus small terms) must fit in 32 MiB,
+ * e.g. Ng <= ~7,700 at Ns = 963, Nt = 256; larger problems get
+ * S2W_ERR_UNSUPPORTED with the required size in s2w_last_error.
+ * The first call on a device looks up the array's device address (one
+ * cudaGetSymbolAddress per device); make that first call before any stream
+ * capture.  All calls in the process share the array, which keeps the last
+ * call's contents (the call clears what must start at zero): calls that can
+ * overlap on the GPU (different streams, contexts or threads without
+ * ordering) race on it and must be serialised by the caller.  Returns once
+ * the work is enqueued on `stream`. */
+int s2w_waveforms_noalloc(s2w_ctx *ctx, const float *slip, float *q, void *stream);
+
 /* Zero-padded real FFT of `rows` signals of Nt samples (the transform of
  * Alg. 2 steps 1-2): X[r][l] = sum_{n<Nt} x[r][n] exp(-2 pi i n l / (2 Nt)),
  * l = 0..Nt, X as interleaved (re, im) float pairs [rows][Nt+1][2].

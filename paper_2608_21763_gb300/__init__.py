@@ -28,7 +28,7 @@ STATUS = {0: "S2W_OK", -1: "S2W_ERR_ARG", -2: "S2W_ERR_OOM", -3: "S2W_ERR_STATE"
 
 # every entry point declared in include/s2w.h
 EXPORTS = ("s2w_default_opts", "s2w_create", "s2w_destroy", "s2w_operator_bytes",
-           "s2w_load_greens", "s2w_load_adjoint", "s2w_waveforms", "s2w_rfft",
+           "s2w_load_greens", "s2w_load_adjoint", "s2w_waveforms", "s2w_waveforms_noalloc", "s2w_rfft",
            "s2w_irfft", "s2w_profile_enable", "s2w_profile_read", "s2w_sync",
            "s2w_last_error", "s2w_status_string")
 NUM_STAGES = 6
@@ -75,6 +75,7 @@ def lib():
     L.s2w_load_greens.argtypes = [V, I, I, P, V]
     L.s2w_load_adjoint.argtypes = [V, I, I, P, V]
     L.s2w_waveforms.argtypes = [V, P, I, P, P, V]
+    L.s2w_waveforms_noalloc.argtypes = [V, P, P, V]
     L.s2w_rfft.argtypes = [V, P, LL, P, V]
     L.s2w_irfft.argtypes = [V, P, LL, P, V]
     L.s2w_profile_enable.argtypes = [V, I]
@@ -85,7 +86,7 @@ def lib():
     L.s2w_status_string.argtypes = [I]
     L.s2w_status_string.restype = ctypes.c_char_p
     for name in ("s2w_create", "s2w_destroy", "s2w_operator_bytes", "s2w_load_greens",
-                 "s2w_load_adjoint", "s2w_waveforms", "s2w_rfft", "s2w_irfft", "s2w_sync",
+                 "s2w_load_adjoint", "s2w_waveforms", "s2w_waveforms_noalloc", "s2w_rfft", "s2w_irfft", "s2w_sync",
                  "s2w_profile_enable", "s2w_profile_read"):
         getattr(L, name).restype = I
     _lib = L

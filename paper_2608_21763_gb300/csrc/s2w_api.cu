@@ -571,3 +571,120 @@ int s2w_sync(s2w_ctx* ctx) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Waveforms without allocating: scratch in a fixed static device array.
+//
+// s2w_waveforms keeps its intermediates (slip spectra, seafloor spectra,
+// velocity spectra, stage-2 partials) in workspaces that s2w_create allocates.
+// Some callers cannot let a library allocate device memory on their behalf:
+// a host application whose device memory all comes from its own pool, code
+// that runs inside a CUDA stream capture (where a cudaMalloc would break the
+// capture), or a latency-bound warning loop that must never wait on the
+// allocator.  s2w_waveforms_noalloc evaluates one rupture with the same
+// kernels but takes every intermediate from kNoAllocScratchBytes of static
+// device memory, so the call itself allocates nothing.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+constexpr size_t kNoAllocScratchBytes = 32ull << 20;  // 32 MiB per device
+constexpr int kMaxDevices = 256;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kMaxDevices] = {};
+}  // namespace
+
+// Every GPU that loads libs2w holds this array until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+
+size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+
+// Device address of g_noalloc_scratch on the current device (== `device`).
+// The symbol's name in host code is only a host-side stand-in; the real
+// address comes from cudaGetSymbolAddress, taken once per device.
+int noalloc_scratch(s2w_ctx* ctx, void** out) {
+  if (ctx->device < 0 || ctx->device >= kMaxDevices)
+    return fail(ctx, S2W_ERR_UNSUPPORTED, "waveforms_noalloc: device ordinal %d", ctx->device);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (g_noalloc_addr[ctx->device] == nullptr) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr)
+      return fail(ctx, S2W_ERR_CUDA, "waveforms_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    g_noalloc_addr[ctx->device] = p;
+  }
+  *out = g_noalloc_addr[ctx->device];
+  return S2W_OK;
+}
+
+}  // namespace
+
+extern "C" int s2w_waveforms_noalloc(s2w_ctx* ctx, const float* slip, float* q, void* stream) {
+  if (!ctx) return S2W_ERR_ARG;
+  if (!slip || !q) return fail(ctx, S2W_ERR_ARG, "waveforms_noalloc: slip and q must not be NULL");
+  const long long Ns = ctx->Ns, Ng = ctx->Ng, No = ctx->No, Nt = ctx->Nt, Nb = ctx->Nb, Ns_pad = ctx->Ns_pad;
+  const long long seg_cols = static_cast<long long>(ctx->nseg) * ctx->RL;
+  const size_t off_s = 0;
+  const size_t off_m = align256(off_s + sizeof(float2) * Nb * Ns_pad);
+  const size_t off_v = align256(off_m + sizeof(float2) * Nb * Ng);
+  const size_t off_p = align256(off_v + sizeof(float2) * Nb * seg_cols);
+  const size_t need = off_p + sizeof(float2) * Nb * ctx->nseg * No;
+  if (need > kNoAllocScratchBytes)
+    return fail(ctx, S2W_ERR_UNSUPPORTED,
+                "waveforms_noalloc: this problem needs %zu bytes of scratch, more than the static %zu bytes "
+                "(Ns=%lld, Ng=%lld, No=%lld, Nt=%lld); use s2w_waveforms",
+                need, kNoAllocScratchBytes, Ns, Ng, No, Nt);
+  if (ctx->g_count != ctx->Ng || ctx->p_count != ctx->Ng)
+    return fail(ctx, S2W_ERR_STATE, "waveforms_noalloc: operators not fully loaded");
+  DeviceGuard guard(ctx->device);
+  if (pointer_kind(slip, ctx->device) != 1 || pointer_kind(q, ctx->device) != 1)
+    return fail(ctx, S2W_ERR_ARG, "waveforms_noalloc: slip and q must be device pointers of the context's device");
+  void* base = nullptr;
+  const int rs = noalloc_scratch(ctx, &base);
+  if (rs != S2W_OK) return rs;
+  unsigned char* sc = static_cast<unsigned char*>(base);
+  float2* shat = reinterpret_cast<float2*>(sc + off_s);
+  float2* mhat = reinterpret_cast<float2*>(sc + off_m);
+  float2* vhat = reinterpret_cast<float2*>(sc + off_v);
+  float2* part = reinterpret_cast<float2*>(sc + off_p);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // The array keeps the previous call's contents: zero the regions whose
+  // padding entries are read (slip spectra columns >= Ns, velocity spectra
+  // columns >= Ng); mhat and the partials are overwritten in full.
+  CK(cudaMemsetAsync(shat, 0, sizeof(float2) * Nb * Ns_pad, st));
+  CK(cudaMemsetAsync(vhat, 0, sizeof(float2) * Nb * seg_cols, st));
+  CK(launch_rfft_rows(slip, Ns, static_cast<int>(Nt), static_cast<int>(Nt), ctx->tw, shat, Ns_pad, Ns, Ns_pad, st));
+  StreamArgs a1{};
+  a1.rows = ctx->G;
+  a1.rows_lo = ctx->G_lo;
+  a1.F = Nb * Ng;
+  a1.row_len = static_cast<int>(Ns_pad);
+  a1.el = ctx->opts.prec_g;
+  a1.x = shat;
+  a1.x_stride = Ns_pad;
+  a1.rows_per_vec = Ng;
+  a1.scale = ctx->G_scale;
+  a1.nblk = ctx->nblk;
+  a1.y = mhat;
+  a1.status = ctx->d_status;
+  CK(launch_stream_dot(a1, ctx->num_sms, st));
+  CK(launch_retransform(mhat, Ng, Ng, static_cast<int>(Nt), ctx->tw, static_cast<float>(1.0 / ctx->opts.dt),
+                        ctx->opts.dt_mode, vhat, seg_cols, nullptr, st));
+  StreamArgs a2{};
+  a2.rows = ctx->P;
+  a2.F = Nb * ctx->nseg * No;
+  a2.row_len = ctx->RL;
+  a2.el = ctx->opts.prec_p;
+  a2.x = vhat;
+  a2.x_stride = ctx->RL;
+  a2.rows_per_vec = No;
+  a2.y = part;
+  a2.status = ctx->d_status;
+  CK(launch_stream_dot(a2, ctx->num_sms, st));
+  CK(launch_reduce_irfft(part, 1, static_cast<int>(No), ctx->nseg, static_cast<int>(Nt), Nb * ctx->nseg * No,
+                         ctx->tw, q, st));
+  ctx->launches += 5;
+  return S2W_OK;
+}
