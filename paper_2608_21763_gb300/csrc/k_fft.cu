@@ -119,33 +119,33 @@ __global__ void __launch_bounds__(kThreads) k_retransform(const float2* __restri
   }
 }
 
-// Split-K reduction + output transform.  For rupture b and observation o:
-//   Qhat[l] = sum_{s < nseg} part[b][l][s][o]   (fixed order: deterministic)
+// Split-K reduction + output transform, one CTA per (rupture b, observation o):
+//   Qhat[l] = sum_{s < nseg} part[b][l][s][o]   (fixed order: deterministic),
+// all bins in parallel over the CTA's threads, then one warp forms
 //   q[b][o][n] = IFFT(Qhat)[n], n < N.
 template <int P>
-__global__ void __launch_bounds__(kThreads) k_reduce_irfft(const float2* __restrict__ part, int B, int No, int nseg,
+__global__ void __launch_bounds__(kThreads) k_reduce_irfft(const float2* __restrict__ part, int No, int nseg,
                                                            long long ld_b, const float2* __restrict__ twg,
                                                            float* __restrict__ q) {
   constexpr int N = 32 * P;
   constexpr int L = 2 * N;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* tw = reinterpret_cast<float2*>(smraw);
-  float2* xs = tw + L + (threadIdx.x >> 5) * (N + 1);
+  float2* xs = tw + L;
   load_twiddles<P>(tw, twg);
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const long long id = static_cast<long long>(blockIdx.x) * kWarps + (threadIdx.x >> 5);
-  if (id >= static_cast<long long>(B) * No) return;
-  const int b = static_cast<int>(id / No), o = static_cast<int>(id % No);
-  const float2* pb = part + b * ld_b;
-  for (int k = lane; k <= N; k += 32) {
+  const int b = blockIdx.x / No, o = blockIdx.x % No;
+  const float2* pb = part + b * ld_b + o;
+  for (int k = threadIdx.x; k <= N; k += kThreads) {
+    const float2* pk = pb + static_cast<long long>(k) * nseg * No;
     float2 acc = make_float2(0.f, 0.f);
-    for (int s = 0; s < nseg; ++s) acc = cadd(acc, pb[(static_cast<long long>(k) * nseg + s) * No + o]);
+#pragma unroll 4
+    for (int s = 0; s < nseg; ++s) acc = cadd(acc, pk[static_cast<long long>(s) * No]);
     xs[k] = acc;
   }
-  __syncwarp();
-  float* out = q + id * N;
-  warp_irfft_head<P>([&](int k) { return xs[k]; }, [&](int n, float v) { out[n] = v; }, tw, lane);
+  __syncthreads();
+  if (threadIdx.x >= 32) return;
+  float* out = q + static_cast<long long>(blockIdx.x) * N;
+  warp_irfft_head<P>([&](int k) { return xs[k]; }, [&](int n, float v) { out[n] = v; }, tw, threadIdx.x);
 }
 
 // FP32 spectra -> resident storage (FP32 / BF16 / BF16 hi+lo), block copy:
@@ -307,10 +307,9 @@ cudaError_t launch_reduce_irfft(const float2* part, int B, int No, int nseg, int
                                 float* q, cudaStream_t st) {
   const long long n = static_cast<long long>(B) * No;
   if (n <= 0) return cudaSuccess;
-  const unsigned grid = static_cast<unsigned>((n + kWarps - 1) / kWarps);
   S2W_DISPATCH_P(Nt, {
-    const size_t sm = sizeof(float2) * (64 * P + kWarps * (32 * P + 1));
-    k_reduce_irfft<P><<<grid, kThreads, sm, st>>>(part, B, No, nseg, ld_b, tw, q);
+    const size_t sm = sizeof(float2) * (64 * P + 32 * P + 1);
+    k_reduce_irfft<P><<<static_cast<unsigned>(n), kThreads, sm, st>>>(part, No, nseg, ld_b, tw, q);
   });
   return cudaGetLastError();
 }

@@ -208,26 +208,40 @@ def test_errors_and_empty_batch(tiny):
 
 
 # ---------------------------------------------------------------- full size
-def test_plain_workload_full_size_fp32():
+@pytest.fixture(scope="module")
+def plain_reference():
     """Paper-shaped plain workload (963 subfaults, 20,000 grid points, 64
-    observations, 256 steps), FP32, one rupture: the whole waveform set
-    against the FP64 oracle (Eq. distributed-composition over grid chunks)."""
+    observations, 256 steps), one rupture: the FP64 oracle over grid chunks
+    (Eq. distributed-composition), plus the norm of its 2 Nt-sample window."""
     wl = synth.WORKLOADS["plain"]
     geom = wl.geometry_obj()
     slip = wl.slip(geom, B=1)
-    ctx = s2w.Context(wl.Ns, wl.Ng, wl.No, wl.Nt)
-    q_ref = None
-    chunk = 1024
-    for g0 in range(0, wl.Ng, chunk):
-        g1 = min(wl.Ng, g0 + chunk)
+    q_ref, q_win = None, None
+    for g0 in range(0, wl.Ng, 1024):
+        g1 = min(wl.Ng, g0 + 1024)
         G = geom.greens_rows(g0, g1, wl.Nt)
         P = geom.adjoint_cols(g0, g1, wl.Nt)
-        ctx.load_greens(g0, G.astype(np.float32))
-        ctx.load_adjoint(g0, np.ascontiguousarray(P.astype(np.float32)))
-        q_r = oracle.bltt_apply(P, oracle.dt_apply(oracle.bltt_apply(G, slip)))
-        q_ref = q_r if q_ref is None else q_ref + q_r
+        w = oracle.fft_window(G, P, slip)
+        q_win = w if q_win is None else q_win + w
+    q_ref = q_win[..., :wl.Nt]
+    wn = np.linalg.norm(q_win.reshape(1, -1), axis=1)
+    kappa = wn / np.linalg.norm(q_ref.reshape(1, -1), axis=1)
+    return wl, geom, slip, q_ref, wn, kappa
+
+
+@pytest.mark.parametrize("prec_g,prec_p", [("fp32", "fp32"), ("bf16_hilo", "fp32"), ("bf16", "bf16"),
+                                           ("fp8", "bf16")])
+def test_plain_workload_full_size(plain_reference, prec_g, prec_p):
+    """The whole waveform set of the plain workload against the FP64 oracle,
+    in every storage precision, at the size and launch configuration that
+    bench.py times (one rupture per call)."""
+    wl, geom, slip, q_ref, wn, kappa = plain_reference
+    ctx = s2w.Context(wl.Ns, wl.Ng, wl.No, wl.Nt, prec_g=prec_g, prec_p=prec_p)
+    for g0 in range(0, wl.Ng, 4096):
+        g1 = min(wl.Ng, g0 + 4096)
+        ctx.load_greens(g0, geom.greens_rows(g0, g1, wl.Nt, np.float32))
+        ctx.load_adjoint(g0, geom.adjoint_cols(g0, g1, wl.Nt, np.float32))
     q = ctx.waveforms(torch.tensor(slip, dtype=torch.float32, device="cuda")).cpu().numpy()
-    err = rel_l2(q, q_ref)
-    print(f"plain fp32 full size: rel-L2 {err}")
-    assert np.all(err <= 1e-5), err
+    tol = max(TOL[prec_g], TOL[prec_p])
+    assert_parity(q, q_ref, wn, kappa, tol=tol, label=f"plain {prec_g}/{prec_p}")
     ctx.sync()
