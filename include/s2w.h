@@ -72,6 +72,15 @@ typedef enum {
  * NONE gives v = m (two plain consecutive convolutions). */
 typedef enum { S2W_DT_BACKWARD = 0, S2W_DT_NONE = 1 } s2w_dt_mode;
 
+/* Contraction engine for s2w_waveforms.  STREAM: CUDA-core kernels that
+ * stream the resident spectra once per rupture (any storage precision).
+ * TENSOR: tcgen05 tensor-core GEMMs over the whole rupture batch (one pass
+ * over the spectra per batch of up to 256 ruptures); needs prec_g = BF16;
+ * the activations (slip and velocity spectra) are rounded to BF16 and the
+ * stage-2 operator is kept in BF16.  AUTO: TENSOR for calls with B >= 2 when
+ * prec_g is BF16, STREAM otherwise. */
+typedef enum { S2W_ENGINE_AUTO = 0, S2W_ENGINE_STREAM = 1, S2W_ENGINE_TENSOR = 2 } s2w_engine;
+
 typedef struct {
   int prec_g;     /* s2w_prec of the stage-1 spectrum Ghat (default FP32) */
   int prec_p;     /* s2w_prec of the stage-2 spectrum Phat: FP32 or BF16 */
@@ -79,6 +88,7 @@ typedef struct {
   double dt;      /* time step of D_t in seconds (default 1.0, Sec. II-A) */
   int max_batch;  /* largest B accepted by s2w_waveforms (sizes workspaces) */
   int device;     /* CUDA device ordinal (default 0) */
+  int engine;     /* s2w_engine (default AUTO) */
 } s2w_opts;
 
 /* Fill *o with the defaults listed above (max_batch = 1). */

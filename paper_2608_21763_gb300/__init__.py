@@ -22,6 +22,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _lib = None
 
 PREC = {"fp32": 0, "bf16": 1, "bf16_hilo": 2, "fp8": 3}
+ENGINE = {"auto": 0, "stream": 1, "tensor": 2}
 DT_MODE = {"backward": 0, "none": 1}
 STATUS = {0: "S2W_OK", -1: "S2W_ERR_ARG", -2: "S2W_ERR_OOM", -3: "S2W_ERR_STATE",
           -4: "S2W_ERR_CUDA", -5: "S2W_ERR_TIMEOUT", -6: "S2W_ERR_UNSUPPORTED"}
@@ -51,7 +52,8 @@ class Profile(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("prec_g", ctypes.c_int), ("prec_p", ctypes.c_int),
                 ("dt_mode", ctypes.c_int), ("dt", ctypes.c_double),
-                ("max_batch", ctypes.c_int), ("device", ctypes.c_int)]
+                ("max_batch", ctypes.c_int), ("device", ctypes.c_int),
+                ("engine", ctypes.c_int)]
 
 
 def lib_path() -> str:
@@ -123,19 +125,20 @@ class Context:
     """One resident operator pair (Ghat, Phat) on one GPU.
 
     ``Context(Ns, Ng, No, Nt, prec_g="fp32", prec_p="fp32", dt_mode="backward",
-    dt=1.0, max_batch=1, device=0)``; load the operators with
+    dt=1.0, max_batch=1, device=0, engine="auto")``; load the operators with
     ``load_greens``/``load_adjoint`` (time-domain responses, any row chunking),
     then call ``waveforms``.
     """
 
     def __init__(self, Ns, Ng, No, Nt, prec_g="fp32", prec_p="fp32",
-                 dt_mode="backward", dt=1.0, max_batch=1, device=0):
+                 dt_mode="backward", dt=1.0, max_batch=1, device=0, engine="auto"):
         L = lib()
         o = Opts()
         L.s2w_default_opts(ctypes.byref(o))
         o.prec_g, o.prec_p = PREC[prec_g], PREC[prec_p]
         o.dt_mode, o.dt = DT_MODE[dt_mode], float(dt)
         o.max_batch, o.device = int(max_batch), int(device)
+        o.engine = ENGINE[engine]
         h = ctypes.c_void_p()
         st = L.s2w_create(Ns, Ng, No, Nt, ctypes.byref(o), ctypes.byref(h))
         if st != 0:
@@ -144,6 +147,7 @@ class Context:
         self.Ns, self.Ng, self.No, self.Nt = Ns, Ng, No, Nt
         self.Nb = Nt + 1
         self.prec_g, self.prec_p, self.max_batch, self.device = prec_g, prec_p, max_batch, device
+        self.engine = engine
 
     def _check(self, st):
         if st != 0:

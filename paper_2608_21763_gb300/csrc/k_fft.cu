@@ -66,16 +66,17 @@ __global__ void __launch_bounds__(kThreads) k_irfft_rows(const float2* __restric
   warp_irfft_head<P>([&](int k) { return xr[k]; }, [&](int n, float v) { out[n] = v; }, tw, lane);
 }
 
-// Retransform of 32 consecutive grid points per CTA:
+// Retransform of 32 consecutive grid points per CTA, rupture blockIdx.y:
 //   mhat[l][i] (bins 0..N)  -> IFFT, keep n < N (Truncate)  -> m
 //   v = D_t m  (backward difference; or v = m when dt_mode is NONE)
-//   v zero-padded to 2N -> FFT -> vhat[l][i].
+//   v zero-padded to 2N -> FFT -> vhat[l][i]  (FP32, or BF16 pairs when BF16OUT).
 // Optionally writes m to seafloor[i][0..N).
-template <int P>
+template <int P, bool BF16OUT>
 __global__ void __launch_bounds__(kThreads) k_retransform(const float2* __restrict__ mhat, long long Ng, long long ld_m,
                                                           const float2* __restrict__ twg, float inv_dt, int dt_mode,
-                                                          float2* __restrict__ vhat, long long ld_v,
-                                                          float* __restrict__ seafloor) {
+                                                          void* __restrict__ vout, long long ld_v,
+                                                          float* __restrict__ seafloor, long long mhat_ld_b,
+                                                          long long vhat_ld_b) {
   constexpr int N = 32 * P;
   constexpr int L = 2 * N;
   constexpr int NB = N + 1;
@@ -87,6 +88,8 @@ __global__ void __launch_bounds__(kThreads) k_retransform(const float2* __restri
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const long long i0 = static_cast<long long>(blockIdx.x) * 32;
+  mhat += blockIdx.y * mhat_ld_b;
+  if (seafloor != nullptr) seafloor += static_cast<long long>(blockIdx.y) * Ng * N;
   load_twiddles<P>(tw, twg);
   for (int e = threadIdx.x; e < NB * 32; e += kThreads) {
     const int l = e >> 5, c = e & 31;
@@ -115,18 +118,23 @@ __global__ void __launch_bounds__(kThreads) k_retransform(const float2* __restri
   for (int e = threadIdx.x; e < NB * 32; e += kThreads) {
     const int l = e >> 5, c = e & 31;
     const long long i = i0 + c;
-    if (i < Ng) vhat[l * ld_v + i] = tile[c * NB + l];
+    if (i >= Ng) continue;
+    const float2 v = tile[c * NB + l];
+    if (BF16OUT)
+      (static_cast<__nv_bfloat162*>(vout) + blockIdx.y * vhat_ld_b)[l * ld_v + i] = __floats2bfloat162_rn(v.x, v.y);
+    else
+      (static_cast<float2*>(vout) + blockIdx.y * vhat_ld_b)[l * ld_v + i] = v;
   }
 }
 
 // Split-K reduction + output transform, one CTA per (rupture b, observation o):
-//   Qhat[l] = sum_{s < nseg} part[b][l][s][o]   (fixed order: deterministic),
-// all bins in parallel over the CTA's threads, then one warp forms
-//   q[b][o][n] = IFFT(Qhat)[n], n < N.
+//   Qhat[l] = sum_{s < nseg} part[b*s_b + l*s_l + s*s_s + o]   (fixed order:
+// deterministic), all bins in parallel over the CTA's threads, then one warp
+// forms q[b][o][n] = IFFT(Qhat)[n], n < N.
 template <int P>
 __global__ void __launch_bounds__(kThreads) k_reduce_irfft(const float2* __restrict__ part, int No, int nseg,
-                                                           long long ld_b, const float2* __restrict__ twg,
-                                                           float* __restrict__ q) {
+                                                           long long s_b, long long s_l, long long s_s,
+                                                           const float2* __restrict__ twg, float* __restrict__ q) {
   constexpr int N = 32 * P;
   constexpr int L = 2 * N;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -134,12 +142,12 @@ __global__ void __launch_bounds__(kThreads) k_reduce_irfft(const float2* __restr
   float2* xs = tw + L;
   load_twiddles<P>(tw, twg);
   const int b = blockIdx.x / No, o = blockIdx.x % No;
-  const float2* pb = part + b * ld_b + o;
+  const float2* pb = part + b * s_b + o;
   for (int k = threadIdx.x; k <= N; k += kThreads) {
-    const float2* pk = pb + static_cast<long long>(k) * nseg * No;
+    const float2* pk = pb + static_cast<long long>(k) * s_l;
     float2 acc = make_float2(0.f, 0.f);
 #pragma unroll 4
-    for (int s = 0; s < nseg; ++s) acc = cadd(acc, pk[static_cast<long long>(s) * No]);
+    for (int s = 0; s < nseg; ++s) acc = cadd(acc, pk[static_cast<long long>(s) * s_s]);
     xs[k] = acc;
   }
   __syncthreads();
@@ -290,26 +298,36 @@ cudaError_t launch_irfft_rows(const float2* X, long long rows, int Nt, const flo
 
 cudaError_t launch_retransform(const float2* mhat, long long Ng, long long ld_m, int Nt, const float2* tw,
                                float inv_dt, int dt_mode, float2* vhat, long long ld_v, float* seafloor,
-                               cudaStream_t st) {
-  if (Ng <= 0) return cudaSuccess;
-  const unsigned grid = static_cast<unsigned>((Ng + 31) / 32);
+                               cudaStream_t st, int nb, long long mhat_ld_b, long long vhat_ld_b,
+                               __nv_bfloat162* vhat_bf) {
+  if (Ng <= 0 || nb <= 0) return cudaSuccess;
+  const dim3 grid(static_cast<unsigned>((Ng + 31) / 32), static_cast<unsigned>(nb));
   S2W_DISPATCH_P(Nt, {
     const size_t sm = smem_retransform<P>();
-    cudaError_t e = cudaFuncSetAttribute(k_retransform<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(sm));
-    if (e != cudaSuccess) return e;
-    k_retransform<P><<<grid, kThreads, sm, st>>>(mhat, Ng, ld_m, tw, inv_dt, dt_mode, vhat, ld_v, seafloor);
+    if (vhat_bf != nullptr) {
+      cudaError_t e = cudaFuncSetAttribute(k_retransform<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           static_cast<int>(sm));
+      if (e != cudaSuccess) return e;
+      k_retransform<P, true><<<grid, kThreads, sm, st>>>(mhat, Ng, ld_m, tw, inv_dt, dt_mode, vhat_bf, ld_v, seafloor,
+                                                         mhat_ld_b, vhat_ld_b);
+    } else {
+      cudaError_t e = cudaFuncSetAttribute(k_retransform<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           static_cast<int>(sm));
+      if (e != cudaSuccess) return e;
+      k_retransform<P, false><<<grid, kThreads, sm, st>>>(mhat, Ng, ld_m, tw, inv_dt, dt_mode, vhat, ld_v, seafloor,
+                                                          mhat_ld_b, vhat_ld_b);
+    }
   });
   return cudaGetLastError();
 }
 
-cudaError_t launch_reduce_irfft(const float2* part, int B, int No, int nseg, int Nt, long long ld_b, const float2* tw,
-                                float* q, cudaStream_t st) {
+cudaError_t launch_reduce_irfft(const float2* part, int B, int No, int nseg, int Nt, long long s_b, long long s_l,
+                                long long s_s, const float2* tw, float* q, cudaStream_t st) {
   const long long n = static_cast<long long>(B) * No;
   if (n <= 0) return cudaSuccess;
   S2W_DISPATCH_P(Nt, {
     const size_t sm = sizeof(float2) * (64 * P + 32 * P + 1);
-    k_reduce_irfft<P><<<static_cast<unsigned>(n), kThreads, sm, st>>>(part, No, nseg, ld_b, tw, q);
+    k_reduce_irfft<P><<<static_cast<unsigned>(n), kThreads, sm, st>>>(part, No, nseg, s_b, s_l, s_s, tw, q);
   });
   return cudaGetLastError();
 }

@@ -1,0 +1,370 @@
+// Tensor-core per-bin contractions for rupture batches (Alg. 2 step 3 with
+// many right-hand sides): tcgen05.mma (kind::f16, BF16 operands, FP32
+// accumulators in tensor memory), operands staged by TMA with 128-byte
+// swizzle.
+//
+// Complex products run as one real GEMM per bin through a real embedding that
+// never duplicates the streamed operand A:
+//   A[r][2c] = Re a_rc, A[r][2c+1] = Im a_rc                  (K-major, as stored)
+//   B[2t][2c] = Re x_ct,  B[2t][2c+1] = -Im x_ct               (row 2t: real part)
+//   B[2t+1][2c] = Im x_ct, B[2t+1][2c+1] = Re x_ct             (row 2t+1: imaginary part)
+//   D = A B^T  =>  D[r][2t] + i D[r][2t+1] = sum_c a_rc x_ct.
+// Stage 1: A = Ghat_l (rows = grid points, c = subfault), x = shat_l over the
+//          batch (t = rupture);  D -> mhat[l][b][i].
+// Stage 2: A = vhat_l (rows = ruptures, c = grid point), B built from Phat_l
+//          (t = observation);  split over chunks of grid points, D -> partials.
+//
+// Warp roles (192 threads, one CTA per SM, persistent over work units):
+//   warp 0  one lane issues TMA loads into a ring of K-block stages;
+//   warp 1  allocates tensor memory; one lane issues tcgen05.mma and commits;
+//   warps 2-5  epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
+//              lanes 32 (w % 4) .. +31, i.e. tile rows), scale, store.
+// Every mbarrier wait is bounded (s2w_internal.cuh); on expiry a status bit
+// is latched and the CTA drains and exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "s2w_internal.cuh"
+
+namespace s2w {
+
+namespace {
+
+constexpr int kTcThreads = 192;
+constexpr int kBlockM = 128;
+constexpr int kBlockK = 64;  // bf16 elements per 128-byte swizzle row
+constexpr int kABytes = kBlockM * kBlockK * 2;
+constexpr int kSmemBudget = 200 * 1024;
+
+__device__ __forceinline__ void tma_load_3d(void* sdst, const CUtensorMap* tm, int c0, int c1, int c2,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+          "r"(smem_u32(sdst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* holder, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(holder)), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// Arrive once on `bar` when every tcgen05.mma issued so far by this thread
+// has completed.
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                            uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// 32 lanes x 16 columns of 32-bit accumulators: thread t of the warp gets
+// columns [col, col + 16) of TMEM lane (lane base + t).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+// Shared-memory matrix descriptor of a K-major tile written by TMA with
+// 128-byte swizzle: rows of 128 bytes, 8-row core-matrix groups 1024 bytes
+// apart (stride byte offset), tile base 1024-byte aligned; advancing along K
+// inside the swizzle row is a plain byte offset of the start address.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= static_cast<uint64_t>(1) << 16;                  // leading byte offset (unused here)
+  d |= static_cast<uint64_t>(1024 >> 4) << 32;          // stride byte offset
+  d |= static_cast<uint64_t>(1) << 46;                  // descriptor version (tcgen05)
+  d |= static_cast<uint64_t>(2) << 61;                  // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: BF16 A and B, FP32 D, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+  const int N = a.N;
+  const int b_bytes = N * kBlockK * 2;
+  const int stage_bytes = kABytes + b_bytes;
+  const int S = a.stages;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * stage_bytes);
+  uint64_t* empty = full + S;
+  uint64_t* acc_full = empty + S;
+  uint64_t* acc_empty = acc_full + 1;
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(acc_empty + 1);
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int nk_total = (a.K + kBlockK - 1) / kBlockK;
+  const long long units = static_cast<long long>(a.Nb) * a.m_tiles * a.n_kchunks;
+  const int n_mma = N > 256 ? N / 256 : 1;
+  const int n_mma_cols = N > 256 ? 256 : N;
+  const uint32_t idesc = idesc_bf16(kBlockM, n_mma_cols);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(empty + s, 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, 4);
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_holder, a.tmem_cols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_holder;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int it = 0;
+      bool ok = true;
+      for (long long u = blockIdx.x; u < units && ok; u += gridDim.x) {
+        const int kc = static_cast<int>(u % a.n_kchunks);
+        const long long r = u / a.n_kchunks;
+        const int mt = static_cast<int>(r % a.m_tiles);
+        const int l = static_cast<int>(r / a.m_tiles);
+        const int kb0 = kc * a.kblocks_per_chunk;
+        const int kb1 = min(nk_total, kb0 + a.kblocks_per_chunk);
+        for (int kb = kb0; kb < kb1; ++kb, ++it) {
+          const int s = it % S;
+          if (it >= S && !mbar_wait_bounded(empty + s, ((it / S) - 1) & 1, a.status, DEV_ERR_TIMEOUT_EMPTY)) {
+            ok = false;
+            break;
+          }
+          unsigned char* sa = smem + s * stage_bytes;
+          mbar_arrive_expect_tx(full + s, stage_bytes);
+          tma_load_3d(sa, &tmA, kb * kBlockK, mt * kBlockM, l, full + s);
+          for (int c = 0; c < n_mma; ++c)
+            tma_load_3d(sa + kABytes + c * n_mma_cols * kBlockK * 2, &tmB, kb * kBlockK, c * n_mma_cols, l, full + s);
+        }
+      }
+      for (int kk = (it > S ? it - S : 0); kk < it; ++kk)
+        mbar_wait_bounded(full + kk % S, (kk / S) & 1, a.status, DEV_ERR_TIMEOUT_FULL);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int it = 0, acc_it = 0;
+      bool ok = true;
+      for (long long u = blockIdx.x; u < units && ok; u += gridDim.x) {
+        const int kc = static_cast<int>(u % a.n_kchunks);
+        const int kb0 = kc * a.kblocks_per_chunk;
+        const int kb1 = min(nk_total, kb0 + a.kblocks_per_chunk);
+        if (acc_it > 0 && !mbar_wait_bounded(acc_empty, (acc_it - 1) & 1, a.status, DEV_ERR_TIMEOUT_MMA)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        for (int kb = kb0; kb < kb1; ++kb, ++it) {
+          const int s = it % S;
+          if (!mbar_wait_bounded(full + s, (it / S) & 1, a.status, DEV_ERR_TIMEOUT_FULL)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(smem + s * stage_bytes);
+          const uint32_t sb = sa + kABytes;
+#pragma unroll
+          for (int k = 0; k < kBlockK / 16; ++k) {
+            const uint64_t ad = sdesc_sw128(sa + k * 32);
+            for (int c = 0; c < n_mma; ++c) {
+              const uint64_t bd = sdesc_sw128(sb + c * n_mma_cols * kBlockK * 2 + k * 32);
+              tc_mma_bf16(tmem + c * n_mma_cols, ad, bd, idesc, (kb > kb0 || k > 0) ? 1u : 0u);
+            }
+          }
+          tc_commit(empty + s);
+        }
+        if (!ok) break;
+        tc_commit(acc_full);
+        ++acc_it;
+      }
+      // the epilogue consumes the last accumulator; wait for it before teardown
+      if (acc_it > 0) mbar_wait_bounded(acc_empty, (acc_it - 1) & 1, a.status, DEV_ERR_TIMEOUT_MMA);
+    }
+  } else {
+    // epilogue warps 2..5
+    const int q = warp & 3;  // TMEM lane quadrant this warp may access
+    int acc_it = 0;
+    for (long long u = blockIdx.x; u < units; u += gridDim.x) {
+      const int kc = static_cast<int>(u % a.n_kchunks);
+      const long long r = u / a.n_kchunks;
+      const int mt = static_cast<int>(r % a.m_tiles);
+      const int l = static_cast<int>(r / a.m_tiles);
+      if (!mbar_wait_bounded(acc_full, acc_it & 1, a.status, DEV_ERR_TIMEOUT_MMA)) break;
+      tc_fence_after();
+      const int row = mt * kBlockM + q * 32 + lane;
+      const uint32_t tbase = tmem + (static_cast<uint32_t>(q * 32) << 16);
+      const bool live = row < a.M_total;
+      float scale = 1.f;
+      if (a.row_scale != nullptr && live) scale = a.row_scale[static_cast<long long>(l) * a.nblk + row / 256];
+      for (int c0 = 0; c0 < N; c0 += 16) {
+        float v[16];
+        tmem_ld16(tbase + c0, v);
+        if (!live) continue;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int t = c0 / 2 + k;  // complex column (rupture or observation)
+          if (t < a.T) {
+            const float2 z = make_float2(v[2 * k] * scale, v[2 * k + 1] * scale);
+            if (a.epi == 0)
+              a.out[static_cast<long long>(l) * a.ld_l + static_cast<long long>(t) * a.ld_t + row] = z;
+            else
+              a.out[((static_cast<long long>(l) * a.n_kchunks + kc) * a.M_total + row) * a.T + t] = z;
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acc_empty);
+      ++acc_it;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, a.tmem_cols);
+  }
+}
+
+// Stage-1 B operand from the slip spectra shat[l][b][Ns_pad] (complex FP32):
+// rows 2b / 2b+1 of Bp[l][N_alloc][2 Ns_pad] (BF16, round to nearest even).
+__global__ void k_pack_stage1_b(const float2* __restrict__ shat, int B, int Ns_pad, int Nb, int N_alloc,
+                                __nv_bfloat162* __restrict__ Bp) {
+  const long long total = static_cast<long long>(Nb) * B * Ns_pad;
+  for (long long e = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long j = e % Ns_pad;
+    const long long b = (e / Ns_pad) % B;
+    const long long l = e / (static_cast<long long>(Ns_pad) * B);
+    const float2 v = shat[e];
+    __nv_bfloat162* row = Bp + (l * N_alloc + 2 * b) * Ns_pad;  // Ns_pad bf16 pairs per row
+    row[j] = __floats2bfloat162_rn(v.x, -v.y);
+    row[Ns_pad + j] = __floats2bfloat162_rn(v.y, v.x);
+  }
+}
+
+// Stage-2 B operand from the adjoint spectra, staging [l][o][nc] (complex
+// FP32) at grid columns c0 .. c0+nc-1: rows 2o / 2o+1 of
+// Pp[l][2 No][Kpad] with Kpad/2 complex columns.
+__global__ void k_pack_stage2_b(const float2* __restrict__ src, int Nb, int No, long long nc, long long c0,
+                                long long Kc, __nv_bfloat162* __restrict__ Pp) {
+  const long long total = static_cast<long long>(Nb) * No * nc;
+  for (long long e = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long c = e % nc;
+    const long long o = (e / nc) % No;
+    const long long l = e / (nc * No);
+    const float2 v = src[e];
+    __nv_bfloat162* row = Pp + (l * 2 * No + 2 * o) * Kc;
+    row[c0 + c] = __floats2bfloat162_rn(v.x, -v.y);
+    row[Kc + c0 + c] = __floats2bfloat162_rn(v.y, v.x);
+  }
+}
+
+int grid_for_tc(long long n) {
+  long long g = (n + 255) / 256;
+  if (g > 152LL * 32) g = 152LL * 32;
+  return static_cast<int>(g < 1 ? 1 : g);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+}  // namespace
+
+cudaError_t tc_encode_3d(CUtensorMap* out, const void* base, long long K, long long rows, long long nbatch,
+                         long long row_pitch_elems, int box_rows) {
+  if (g_encode == nullptr) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || fn == nullptr) return cudaErrorNotSupported;
+    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t dims[3] = {static_cast<cuuint64_t>(K), static_cast<cuuint64_t>(rows),
+                              static_cast<cuuint64_t>(nbatch)};
+  const cuuint64_t strides[2] = {static_cast<cuuint64_t>(row_pitch_elems) * 2,
+                                 static_cast<cuuint64_t>(row_pitch_elems) * 2 * static_cast<cuuint64_t>(rows)};
+  const cuuint32_t box[3] = {static_cast<cuuint32_t>(kBlockK), static_cast<cuuint32_t>(box_rows), 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = g_encode(out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+int tc_stages_for(int N) {
+  const int stage = kABytes + N * kBlockK * 2;
+  int s = kSmemBudget / stage;
+  if (s > 8) s = 8;
+  return s;
+}
+
+size_t tc_smem_bytes(int N, int stages) {
+  return 1024 + static_cast<size_t>(stages) * (kABytes + N * kBlockK * 2) + 8 * (2 * stages + 2) + 16;
+}
+
+cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const TcArgs& a, int num_sms,
+                           cudaStream_t st) {
+  const long long units = static_cast<long long>(a.Nb) * a.m_tiles * a.n_kchunks;
+  if (units <= 0) return cudaSuccess;
+  if (a.N < 16 || a.N > 512 || a.N % 16 != 0 || (a.N > 256 && a.N % 256 != 0) || a.stages < 2)
+    return cudaErrorInvalidValue;
+  const size_t smem = tc_smem_bytes(a.N, a.stages);
+  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  const long long grid = units < num_sms ? units : num_sms;
+  k_tc_gemm<<<static_cast<unsigned>(grid), kTcThreads, smem, st>>>(tmA, tmB, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_stage1_b(const float2* shat, int B, int Ns_pad, int Nb, int N_alloc, void* Bp,
+                                 cudaStream_t st) {
+  k_pack_stage1_b<<<grid_for_tc(static_cast<long long>(Nb) * B * Ns_pad), 256, 0, st>>>(
+      shat, B, Ns_pad, Nb, N_alloc, static_cast<__nv_bfloat162*>(Bp));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_stage2_b(const float2* src, int Nb, int No, long long nc, long long c0, long long Kc, void* Pp,
+                                 cudaStream_t st) {
+  k_pack_stage2_b<<<grid_for_tc(static_cast<long long>(Nb) * No * nc), 256, 0, st>>>(
+      src, Nb, No, nc, c0, Kc, static_cast<__nv_bfloat162*>(Pp));
+  return cudaGetLastError();
+}
+
+}  // namespace s2w

@@ -44,6 +44,19 @@ struct s2w_ctx {
   float* ws_q = nullptr;
   float* ws_seafloor = nullptr;
   int* d_status = nullptr;
+  // tensor-core engine (BF16 storage, rupture batches)
+  bool tc_on = false;
+  int tc_bsub = 0;       // largest sub-batch per tensor pass (<= 256)
+  int tc_n1max = 0;      // B-operand rows of stage 1 (2 x sub-batch, padded)
+  int tc_n2 = 0;         // B-operand rows of stage 2 (2 x No, padded)
+  long long Ng_pad2 = 0; // complex columns per row of the stage-2 operands
+  int tc_kbpc = 64;      // 64-element K blocks per stage-2 chunk
+  int tc_nkc = 1;        // stage-2 K chunks
+  void* tc_bp1 = nullptr;   // [Nb][tc_n1max][2 Ns_pad] bf16
+  float2* tc_mhat = nullptr;  // [Nb][b][Ng] complex FP32
+  void* tc_vhat = nullptr;  // [Nb][tc_bsub][Ng_pad2] bf16 pairs
+  float2* tc_part = nullptr;  // [Nb][nkc][b][No] complex FP32
+  void* tc_p2 = nullptr;    // [Nb][tc_n2][Ng_pad2] bf16 pairs
   std::vector<unsigned char> g_loaded, p_loaded;
   long long g_count = 0, p_count = 0;
   // per-stage event timers
@@ -167,9 +180,92 @@ void free_all(s2w_ctx* c) {
   c->pending.clear();
   c->ev_free.clear();
   void* ps[] = {c->G, c->G_lo, c->G_scale, c->P, c->tw, c->ws_slip, c->ws_shat, c->ws_mhat,
-                c->ws_vhat, c->ws_part, c->ws_q, c->ws_seafloor, c->d_status};
+                c->ws_vhat, c->ws_part, c->ws_q, c->ws_seafloor, c->d_status, c->tc_bp1,
+                c->tc_mhat, c->tc_vhat, c->tc_part, c->tc_p2};
   for (void* p : ps)
     if (p) cudaFree(p);
+}
+
+// Tensor-core pipeline for a batch of ruptures (slip and q device pointers),
+// in sub-batches of at most tc_bsub ruptures:
+//   rfft slip -> pack stage-1 B operand -> tcgen05 stage 1 -> mhat[l][b][Ng]
+//   -> retransform (BF16 velocity spectra, the stage-2 A operand)
+//   -> tcgen05 stage 2 over grid chunks -> partials -> reduce + IFFT -> q.
+int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, float* seafloor, cudaStream_t st) {
+  const long long Ns = ctx->Ns, Ng = ctx->Ng, No = ctx->No, Nt = ctx->Nt, Nb = ctx->Nb, Ns_pad = ctx->Ns_pad;
+  const int K1 = static_cast<int>(2 * Ns_pad);
+  const long long K2 = 2 * ctx->Ng_pad2;
+  for (int b0 = 0; b0 < B; b0 += ctx->tc_bsub) {
+    const int Bs = std::min(ctx->tc_bsub, B - b0);
+    int N1 = static_cast<int>(round_up(2 * Bs, 16));
+    if (N1 > 256) N1 = 512;
+    {
+      StageTimer t(ctx, 0, st);
+      CK(launch_rfft_rows(slip_d + static_cast<long long>(b0) * Ns * Nt, Bs * Ns, static_cast<int>(Nt),
+                          static_cast<int>(Nt), ctx->tw, ctx->ws_shat, Bs * Ns_pad, Ns, Ns_pad, st));
+    }
+    {
+      StageTimer t(ctx, 1, st, 2);
+      CK(launch_pack_stage1_b(ctx->ws_shat, Bs, static_cast<int>(Ns_pad), static_cast<int>(Nb), ctx->tc_n1max,
+                              ctx->tc_bp1, st));
+      CUtensorMap ta, tb;
+      CK(tc_encode_3d(&ta, ctx->G, K1, Ng, Nb, K1, 128));
+      CK(tc_encode_3d(&tb, ctx->tc_bp1, K1, ctx->tc_n1max, Nb, K1, N1 > 256 ? 256 : N1));
+      TcArgs a{};
+      a.N = N1;
+      a.K = K1;
+      a.M_total = static_cast<int>(Ng);
+      a.Nb = static_cast<int>(Nb);
+      a.m_tiles = static_cast<int>((Ng + 127) / 128);
+      a.n_kchunks = 1;
+      a.kblocks_per_chunk = (K1 + 63) / 64;
+      a.stages = tc_stages_for(N1);
+      a.tmem_cols = N1 <= 32 ? 32 : (N1 <= 64 ? 64 : (N1 <= 128 ? 128 : (N1 <= 256 ? 256 : 512)));
+      a.epi = 0;
+      a.T = Bs;
+      a.out = ctx->tc_mhat;
+      a.ld_l = static_cast<long long>(Bs) * Ng;
+      a.ld_t = Ng;
+      a.status = ctx->d_status;
+      CK(launch_tc_gemm(ta, tb, a, ctx->num_sms, st));
+    }
+    {
+      StageTimer t(ctx, 2, st);
+      float* sf = seafloor ? seafloor + static_cast<long long>(b0) * Ng * Nt : nullptr;
+      CK(launch_retransform(ctx->tc_mhat, Ng, static_cast<long long>(Bs) * Ng, static_cast<int>(Nt), ctx->tw,
+                            static_cast<float>(1.0 / ctx->opts.dt), ctx->opts.dt_mode, nullptr,
+                            static_cast<long long>(ctx->tc_bsub) * ctx->Ng_pad2, sf, st, Bs, Ng, ctx->Ng_pad2,
+                            static_cast<__nv_bfloat162*>(ctx->tc_vhat)));
+    }
+    {
+      StageTimer t(ctx, 3, st);
+      CUtensorMap ta, tb;
+      CK(tc_encode_3d(&ta, ctx->tc_vhat, K2, ctx->tc_bsub, Nb, K2, 128));
+      CK(tc_encode_3d(&tb, ctx->tc_p2, K2, ctx->tc_n2, Nb, K2, ctx->tc_n2));
+      TcArgs a{};
+      a.N = ctx->tc_n2;
+      a.K = static_cast<int>(K2);
+      a.M_total = Bs;
+      a.Nb = static_cast<int>(Nb);
+      a.m_tiles = (Bs + 127) / 128;
+      a.n_kchunks = ctx->tc_nkc;
+      a.kblocks_per_chunk = ctx->tc_kbpc;
+      a.stages = tc_stages_for(ctx->tc_n2);
+      a.tmem_cols = ctx->tc_n2 <= 32 ? 32 : (ctx->tc_n2 <= 64 ? 64 : (ctx->tc_n2 <= 128 ? 128 : 256));
+      a.epi = 1;
+      a.T = static_cast<int>(No);
+      a.out = ctx->tc_part;
+      a.status = ctx->d_status;
+      CK(launch_tc_gemm(ta, tb, a, ctx->num_sms, st));
+    }
+    {
+      StageTimer t(ctx, 4, st);
+      CK(launch_reduce_irfft(ctx->tc_part, Bs, static_cast<int>(No), ctx->tc_nkc, static_cast<int>(Nt), No,
+                             static_cast<long long>(ctx->tc_nkc) * Bs * No, static_cast<long long>(Bs) * No, ctx->tw,
+                             q_d + static_cast<long long>(b0) * No * Nt, st));
+    }
+  }
+  return S2W_OK;
 }
 
 }  // namespace
@@ -184,6 +280,7 @@ void s2w_default_opts(s2w_opts* o) {
   o->dt = 1.0;
   o->max_batch = 1;
   o->device = 0;
+  o->engine = S2W_ENGINE_AUTO;
 }
 
 const char* s2w_status_string(int s) {
@@ -219,6 +316,11 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
     return fail(nullptr, S2W_ERR_ARG, "dt_mode=%d", o.dt_mode);
   if (!(o.dt > 0.0)) return fail(nullptr, S2W_ERR_ARG, "dt must be > 0");
   if (o.max_batch < 1) return fail(nullptr, S2W_ERR_ARG, "max_batch must be >= 1");
+  if (o.engine < S2W_ENGINE_AUTO || o.engine > S2W_ENGINE_TENSOR) return fail(nullptr, S2W_ERR_ARG, "engine=%d", o.engine);
+  if (o.engine == S2W_ENGINE_TENSOR && o.prec_g != S2W_PREC_BF16)
+    return fail(nullptr, S2W_ERR_UNSUPPORTED, "the tensor engine needs prec_g = BF16");
+  if (o.engine == S2W_ENGINE_TENSOR && 2 * No > 256)
+    return fail(nullptr, S2W_ERR_UNSUPPORTED, "the tensor engine needs No <= 128");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || o.device < 0 || o.device >= ndev) {
     cudaGetLastError();
@@ -277,6 +379,28 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
   if ((e = dalloc(&ctx->ws_seafloor, sizeof(float) * static_cast<size_t>(Ng) * Nt)) != cudaSuccess)
     return bad(e, "seafloor workspace");
   if ((e = dalloc(&ctx->d_status, sizeof(int))) != cudaSuccess) return bad(e, "status word");
+  ctx->tc_on = o.prec_g == S2W_PREC_BF16 && 2 * No <= 256 &&
+               (o.engine == S2W_ENGINE_TENSOR || (o.engine == S2W_ENGINE_AUTO && o.max_batch >= 2));
+  if (ctx->tc_on) {
+    ctx->tc_bsub = static_cast<int>(std::min<long long>(B, 256));
+    ctx->tc_n1max = static_cast<int>(round_up(2 * ctx->tc_bsub, 16));
+    if (ctx->tc_n1max > 256) ctx->tc_n1max = 512;
+    ctx->tc_n2 = static_cast<int>(round_up(2 * No, 16));
+    ctx->Ng_pad2 = round_up(Ng, 8);
+    const long long nk2 = (2 * ctx->Ng_pad2 + 63) / 64;
+    ctx->tc_nkc = static_cast<int>((nk2 + ctx->tc_kbpc - 1) / ctx->tc_kbpc);
+    const long long bs = ctx->tc_bsub;
+    if ((e = dalloc(&ctx->tc_bp1, 2ull * Nb * ctx->tc_n1max * 2 * ctx->Ns_pad)) != cudaSuccess)
+      return bad(e, "tensor stage-1 operand");
+    if ((e = dalloc(&ctx->tc_mhat, sizeof(float2) * Nb * bs * Ng)) != cudaSuccess)
+      return bad(e, "tensor seafloor spectra");
+    if ((e = dalloc(&ctx->tc_vhat, 4ull * Nb * bs * ctx->Ng_pad2)) != cudaSuccess)
+      return bad(e, "tensor velocity spectra");
+    if ((e = dalloc(&ctx->tc_part, sizeof(float2) * Nb * ctx->tc_nkc * bs * No)) != cudaSuccess)
+      return bad(e, "tensor stage-2 partials");
+    if ((e = dalloc(&ctx->tc_p2, 4ull * Nb * ctx->tc_n2 * ctx->Ng_pad2)) != cudaSuccess)
+      return bad(e, "tensor stage-2 operand");
+  }
   if ((e = launch_twiddles(ctx->tw, ctx->L, nullptr)) != cudaSuccess) return bad(e, "twiddles");
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bad(e, "create sync");
   *out = ctx;
@@ -384,6 +508,11 @@ int s2w_load_adjoint(s2w_ctx* ctx, int g0, int ng, const float* P, void* stream)
                           rc, rc, st));
       CK(launch_store_adjoint(stage_s, static_cast<int>(Nb), static_cast<int>(No), rc, g0 + c, ctx->RL, ctx->nseg,
                               ctx->opts.prec_p, ctx->P, st));
+      if (ctx->tc_on) {
+        ctx->launches += 1;
+        CK(launch_pack_stage2_b(stage_s, static_cast<int>(Nb), static_cast<int>(No), rc, g0 + c, ctx->Ng_pad2,
+                                ctx->tc_p2, st));
+      }
       return S2W_OK;
     };
     rc_status = step();
@@ -425,6 +554,18 @@ int s2w_waveforms(s2w_ctx* ctx, const float* slip, int B, float* q, float* seafl
     slip_d = ctx->ws_slip;
   }
   float* q_d = kq == 1 ? q : ctx->ws_q;
+  const bool use_tc = ctx->tc_on && (seafloor == nullptr || kf == 1) &&
+                      (ctx->opts.engine == S2W_ENGINE_TENSOR || B >= 2);
+  if (use_tc) {
+    int rc = waveforms_tensor(ctx, slip_d, B, q_d, seafloor, st);
+    if (rc != S2W_OK) return rc;
+    if (kq == 0) {
+      StageTimer t(ctx, 5, st, 0);
+      CK(cudaMemcpyAsync(q, q_d, sizeof(float) * B * No * Nt, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+    }
+    return S2W_OK;
+  }
   // K1
   {
   StageTimer t(ctx, 0, st);
@@ -482,8 +623,8 @@ int s2w_waveforms(s2w_ctx* ctx, const float* slip, int B, float* q, float* seafl
   // K5
   {
   StageTimer t(ctx, 4, st);
-  CK(launch_reduce_irfft(ctx->ws_part, B, static_cast<int>(No), ctx->nseg, static_cast<int>(Nt), part_b, ctx->tw,
-                         q_d, st));
+  CK(launch_reduce_irfft(ctx->ws_part, B, static_cast<int>(No), ctx->nseg, static_cast<int>(Nt), part_b,
+                         static_cast<long long>(ctx->nseg) * No, No, ctx->tw, q_d, st));
   }
   if (kq == 0) {
     StageTimer t(ctx, 5, st, 0);
@@ -684,7 +825,7 @@ extern "C" int s2w_waveforms_noalloc(s2w_ctx* ctx, const float* slip, float* q, 
   a2.status = ctx->d_status;
   CK(launch_stream_dot(a2, ctx->num_sms, st));
   CK(launch_reduce_irfft(part, 1, static_cast<int>(No), ctx->nseg, static_cast<int>(Nt), Nb * ctx->nseg * No,
-                         ctx->tw, q, st));
+                         static_cast<long long>(ctx->nseg) * No, No, ctx->tw, q, st));
   ctx->launches += 5;
   return S2W_OK;
 }

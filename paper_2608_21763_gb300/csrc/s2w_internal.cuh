@@ -2,6 +2,7 @@
 // Nothing here is part of the public C ABI (include/s2w.h).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
@@ -126,11 +127,17 @@ cudaError_t launch_rfft_rows(const float* x, long long rows, int n_in, int Nt, c
                              long long ld_l, long long rows_a, long long ld_a, cudaStream_t st);
 // Rows X[row][0..Nt] -> first Nt samples x[row][0..Nt) of the length-2Nt IFFT.
 cudaError_t launch_irfft_rows(const float2* X, long long rows, int Nt, const float2* tw, float* x, cudaStream_t st);
+// Retransform of `nb` ruptures (grid y): rupture y reads mhat + y * mhat_ld_b
+// ([l][i] with bin stride ld_m) and writes either vhat + y * vhat_ld_b (FP32
+// complex, bin stride ld_v) or, when vhat_bf is given, vhat_bf + y * vhat_ld_b
+// (BF16 complex pairs, bin stride ld_v); seafloor (optional) + y * Ng * Nt.
 cudaError_t launch_retransform(const float2* mhat, long long Ng, long long ld_m, int Nt, const float2* tw,
                                float inv_dt, int dt_mode, float2* vhat, long long ld_v, float* seafloor,
-                               cudaStream_t st);
-cudaError_t launch_reduce_irfft(const float2* part, int B, int No, int nseg, int Nt, long long ld_b, const float2* tw,
-                                float* q, cudaStream_t st);
+                               cudaStream_t st, int nb = 1, long long mhat_ld_b = 0, long long vhat_ld_b = 0,
+                               __nv_bfloat162* vhat_bf = nullptr);
+// q[b][o][n] from partials: Qhat[l] = sum_{s < nseg} part[b*s_b + l*s_l + s*s_s + o].
+cudaError_t launch_reduce_irfft(const float2* part, int B, int No, int nseg, int Nt, long long s_b, long long s_l,
+                                long long s_s, const float2* tw, float* q, cudaStream_t st);
 cudaError_t launch_store_blocks(const float2* src, int Nb, long long n_per_l, int el, void* dst, void* dst_lo,
                                 long long ld_dst_l, long long dst_off, cudaStream_t st);
 cudaError_t launch_store_adjoint(const float2* src, int Nb, int No, long long nc, long long c0, int RL, int nseg,
@@ -156,5 +163,34 @@ struct StreamArgs {
   int* status;
 };
 cudaError_t launch_stream_dot(const StreamArgs& a, int num_sms, cudaStream_t st);
+
+// k_tc.cu: D = A B^T per bin on tensor cores (see the file comment).
+struct TcArgs {
+  int N;                  // MMA columns (multiple of 16; 256 or 512 above 256)
+  int K;                  // reduction extent in BF16 elements
+  int M_total;            // live rows of A per bin
+  int Nb;                 // bins
+  int m_tiles;            // ceil(M_total / 128)
+  int n_kchunks;          // split of the K blocks into chunks (stage 2)
+  int kblocks_per_chunk;  // 64-element K blocks per chunk
+  int stages;             // shared-memory ring depth
+  int tmem_cols;          // power of two >= max(32, N)
+  int epi;                // 0: out[l*ld_l + t*ld_t + row]; 1: out[((l*n_kchunks + kc)*M_total + row)*T + t]
+  int T;                  // complex output columns (N / 2 live)
+  float2* out;
+  long long ld_l, ld_t;
+  const float* row_scale;  // optional per-(bin, 256-row block) scale
+  int nblk;
+  int* status;
+};
+cudaError_t tc_encode_3d(CUtensorMap* out, const void* base, long long K, long long rows, long long nbatch,
+                         long long row_pitch_elems, int box_rows);
+int tc_stages_for(int N);
+cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const TcArgs& a, int num_sms,
+                           cudaStream_t st);
+cudaError_t launch_pack_stage1_b(const float2* shat, int B, int Ns_pad, int Nb, int N_alloc, void* Bp,
+                                 cudaStream_t st);
+cudaError_t launch_pack_stage2_b(const float2* src, int Nb, int No, long long nc, long long c0, long long Kc, void* Pp,
+                                 cudaStream_t st);
 
 }  // namespace s2w

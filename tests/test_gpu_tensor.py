@@ -1,0 +1,103 @@
+"""Tensor-core engine (tcgen05, BF16 operands, FP32 accumulation) against the
+FP64 oracle, through the C ABI.
+
+Bar: ||q - q_ref|| <= TOL_TC * ||q_win|| per rupture (q_win: the 2 Nt-sample
+FFT window, oracle.fft_window).  The engine rounds the operator spectra AND
+the activations (slip and velocity spectra) to BF16 (8 significant bits,
+<= 2^-9 relative per entry), so its bar is twice the BF16-storage bar.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import assert_parity, make_context, window_norms
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2608_21763_gb300 as s2w  # noqa: E402
+
+TOL_TC = 1e-2
+
+
+def compact_box(Ns, Ng, No, seed, scale=0.1):
+    g = synth.geometry_box(Ns, Ng, No, seed)
+    return synth.Geometry(g.sub * scale, g.grid * scale, g.obs * scale,
+                          g.strike * scale, g.dip * scale, "box")
+
+
+def run_case(geom, Nt, B, seed=5, engine="tensor", chunk=4096):
+    rng = np.random.default_rng(seed)
+    slip = rng.standard_normal((B, geom.Ns, Nt))
+    slip[:, :, Nt // 2:] = 0
+    ctx = make_context(s2w, geom, Nt, prec_g="bf16", max_batch=B, chunk=chunk, engine=engine)
+    q = ctx.waveforms(torch.tensor(slip, dtype=torch.float32, device="cuda")).cpu().numpy()
+    ctx.sync()
+    G = geom.greens_rows(0, geom.Ng, Nt)
+    P = geom.adjoint_cols(0, geom.Ng, Nt)
+    q_ref = oracle.waveforms(G, P, slip)
+    return q, q_ref, window_norms(G, P, slip), ctx, slip
+
+
+def test_tiny_workload_tensor_engine():
+    wl = synth.WORKLOADS["tiny"]
+    geom = wl.geometry_obj()
+    slip = wl.slip(geom, B=3)
+    ctx = s2w.Context(wl.Ns, wl.Ng, wl.No, wl.Nt, prec_g="bf16", max_batch=3, engine="tensor")
+    ctx.load_greens(0, geom.greens_rows(0, wl.Ng, wl.Nt, np.float32))
+    ctx.load_adjoint(0, geom.adjoint_cols(0, wl.Ng, wl.Nt, np.float32))
+    q = ctx.waveforms(torch.tensor(slip, dtype=torch.float32, device="cuda")).cpu().numpy()
+    ctx.sync()
+    G = geom.greens_rows(0, wl.Ng, wl.Nt)
+    P = geom.adjoint_cols(0, wl.Ng, wl.Nt)
+    assert_parity(q, oracle.waveforms(G, P, slip), *window_norms(G, P, slip), tol=TOL_TC, label="tiny tensor")
+
+
+@pytest.mark.parametrize("B", [1, 7])
+def test_small_batches_tensor_engine(B):
+    geom = compact_box(24, 700, 6, seed=3)
+    q, q_ref, wn, _, _ = run_case(geom, 64, B)
+    assert_parity(q, q_ref, *wn, tol=TOL_TC, label=f"tensor B={B}")
+
+
+def test_full_width_batch_and_sub_batches():
+    """B = 300: one sub-batch of 256 ruptures (N = 512, two MMAs per K step)
+    and one of 44 (N = 96); 700 grid rows = 5 full M tiles + 60."""
+    geom = compact_box(24, 700, 6, seed=4)
+    q, q_ref, wn, ctx, slip = run_case(geom, 64, 300)
+    assert_parity(q, q_ref, *wn, tol=TOL_TC, label="tensor B=300")
+    # deterministic: same inputs, same bits
+    q2 = ctx.waveforms(torch.tensor(slip, dtype=torch.float32, device="cuda")).cpu().numpy()
+    assert np.array_equal(q, q2)
+
+
+def test_split_k_over_grid_chunks():
+    """5,000 grid points: the stage-2 reduction dimension (2 x 5,000) spans
+    three 4,096-element chunks whose partials are summed in fixed order."""
+    geom = compact_box(16, 5000, 4, seed=6)
+    q, q_ref, wn, _, _ = run_case(geom, 32, 20, chunk=2048)
+    assert_parity(q, q_ref, *wn, tol=TOL_TC, label="tensor split-K")
+
+
+def test_auto_engine_uses_tensor_path_for_batches_only():
+    """AUTO: one rupture goes through the streaming kernels (activations kept
+    FP32), a batch through the tensor engine; both meet their bars."""
+    geom = compact_box(24, 700, 6, seed=7)
+    Nt, B = 64, 5
+    rng = np.random.default_rng(9)
+    slip = rng.standard_normal((B, geom.Ns, Nt))
+    slip[:, :, Nt // 2:] = 0
+    ctx = make_context(s2w, geom, Nt, prec_g="bf16", max_batch=B)
+    st = torch.tensor(slip, dtype=torch.float32, device="cuda")
+    ctx.profile_enable(True)
+    q_batch = ctx.waveforms(st).cpu().numpy()
+    q_one = ctx.waveforms(st[:1]).cpu().numpy()
+    stages, _ = ctx.profile_read()
+    G = geom.greens_rows(0, geom.Ng, Nt)
+    P = geom.adjoint_cols(0, geom.Ng, Nt)
+    q_ref = oracle.waveforms(G, P, slip)
+    wn, kappa = window_norms(G, P, slip)
+    assert_parity(q_batch, q_ref, wn, kappa, tol=TOL_TC, label="auto batch")
+    assert_parity(q_one, q_ref[:1], wn[:1], kappa[:1], tol=5e-3, label="auto single")
+    assert stages["contract_stage1"][1] == 2  # one tensor pass + one streaming pass
