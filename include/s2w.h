@@ -166,8 +166,9 @@ int s2w_irfft(s2w_ctx *ctx, const float *X, long long rows, float *x, void *stre
 /* Per-stage CUDA-event timers (the per-stage timing of Sec. III-B).
  * Stages: 0 rfft of slip, 1 stage-1 contraction, 2 retransform (IFFT,
  * Truncate, D_t, ZeroPad, FFT), 3 stage-2 contraction, 4 partial reduction +
- * IFFT + Truncate, 5 host<->device copies made by s2w_waveforms. */
-#define S2W_NUM_STAGES 6
+ * IFFT + Truncate, 5 host<->device copies made by s2w_waveforms, 6 packing
+ * of tensor-engine operands (slip spectra into the stage-1 B operand). */
+#define S2W_NUM_STAGES 7
 typedef struct {
   double ms[S2W_NUM_STAGES];           /* summed event-timed durations */
   long long count[S2W_NUM_STAGES];     /* timed launches per stage */

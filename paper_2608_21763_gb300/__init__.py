@@ -32,9 +32,9 @@ EXPORTS = ("s2w_default_opts", "s2w_create", "s2w_destroy", "s2w_operator_bytes"
            "s2w_load_greens", "s2w_load_adjoint", "s2w_waveforms", "s2w_waveforms_noalloc", "s2w_rfft",
            "s2w_irfft", "s2w_profile_enable", "s2w_profile_read", "s2w_sync",
            "s2w_last_error", "s2w_status_string")
-NUM_STAGES = 6
+NUM_STAGES = 7
 STAGE_NAMES = ("rfft_slip", "contract_stage1", "retransform", "contract_stage2",
-               "reduce_irfft", "copies")
+               "reduce_irfft", "copies", "pack_operands")
 
 
 class S2WError(RuntimeError):

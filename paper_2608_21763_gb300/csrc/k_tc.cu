@@ -281,9 +281,9 @@ __global__ void k_pack_stage1_b(const float2* __restrict__ shat, int B, int Ns_p
 
 // Stage-2 B operand from the adjoint spectra, staging [l][o][nc] (complex
 // FP32) at grid columns c0 .. c0+nc-1: rows 2o / 2o+1 of
-// Pp[l][2 No][Kpad] with Kpad/2 complex columns.
+// Pp[l][N_alloc][Kc] (Kc complex columns = 2 Kc BF16 per row).
 __global__ void k_pack_stage2_b(const float2* __restrict__ src, int Nb, int No, long long nc, long long c0,
-                                long long Kc, __nv_bfloat162* __restrict__ Pp) {
+                                long long Kc, int N_alloc, __nv_bfloat162* __restrict__ Pp) {
   const long long total = static_cast<long long>(Nb) * No * nc;
   for (long long e = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
        e += static_cast<long long>(gridDim.x) * blockDim.x) {
@@ -291,7 +291,7 @@ __global__ void k_pack_stage2_b(const float2* __restrict__ src, int Nb, int No, 
     const long long o = (e / nc) % No;
     const long long l = e / (nc * No);
     const float2 v = src[e];
-    __nv_bfloat162* row = Pp + (l * 2 * No + 2 * o) * Kc;
+    __nv_bfloat162* row = Pp + (l * N_alloc + 2 * o) * Kc;
     row[c0 + c] = __floats2bfloat162_rn(v.x, -v.y);
     row[Kc + c0 + c] = __floats2bfloat162_rn(v.y, v.x);
   }
@@ -360,10 +360,10 @@ cudaError_t launch_pack_stage1_b(const float2* shat, int B, int Ns_pad, int Nb, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_pack_stage2_b(const float2* src, int Nb, int No, long long nc, long long c0, long long Kc, void* Pp,
-                                 cudaStream_t st) {
+cudaError_t launch_pack_stage2_b(const float2* src, int Nb, int No, long long nc, long long c0, long long Kc,
+                                 int N_alloc, void* Pp, cudaStream_t st) {
   k_pack_stage2_b<<<grid_for_tc(static_cast<long long>(Nb) * No * nc), 256, 0, st>>>(
-      src, Nb, No, nc, c0, Kc, static_cast<__nv_bfloat162*>(Pp));
+      src, Nb, No, nc, c0, Kc, N_alloc, static_cast<__nv_bfloat162*>(Pp));
   return cudaGetLastError();
 }
 

@@ -205,9 +205,12 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, float
                           static_cast<int>(Nt), ctx->tw, ctx->ws_shat, Bs * Ns_pad, Ns, Ns_pad, st));
     }
     {
-      StageTimer t(ctx, 1, st, 2);
+      StageTimer t(ctx, 6, st);
       CK(launch_pack_stage1_b(ctx->ws_shat, Bs, static_cast<int>(Ns_pad), static_cast<int>(Nb), ctx->tc_n1max,
                               ctx->tc_bp1, st));
+    }
+    {
+      StageTimer t(ctx, 1, st);
       CUtensorMap ta, tb;
       CK(tc_encode_3d(&ta, ctx->G, K1, Ng, Nb, K1, 128));
       CK(tc_encode_3d(&tb, ctx->tc_bp1, K1, ctx->tc_n1max, Nb, K1, N1 > 256 ? 256 : N1));
@@ -511,7 +514,7 @@ int s2w_load_adjoint(s2w_ctx* ctx, int g0, int ng, const float* P, void* stream)
       if (ctx->tc_on) {
         ctx->launches += 1;
         CK(launch_pack_stage2_b(stage_s, static_cast<int>(Nb), static_cast<int>(No), rc, g0 + c, ctx->Ng_pad2,
-                                ctx->tc_p2, st));
+                                ctx->tc_n2, ctx->tc_p2, st));
       }
       return S2W_OK;
     };

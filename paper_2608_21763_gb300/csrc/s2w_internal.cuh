@@ -190,7 +190,7 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
                            cudaStream_t st);
 cudaError_t launch_pack_stage1_b(const float2* shat, int B, int Ns_pad, int Nb, int N_alloc, void* Bp,
                                  cudaStream_t st);
-cudaError_t launch_pack_stage2_b(const float2* src, int Nb, int No, long long nc, long long c0, long long Kc, void* Pp,
-                                 cudaStream_t st);
+cudaError_t launch_pack_stage2_b(const float2* src, int Nb, int No, long long nc, long long c0, long long Kc,
+                                 int N_alloc, void* Pp, cudaStream_t st);
 
 }  // namespace s2w
