@@ -297,6 +297,225 @@ __global__ void k_pack_stage2_b(const float2* __restrict__ src, int Nb, int No, 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Retransform as a GEMM (tensor-engine path).  For one signal (grid point i,
+// rupture b) the stage-1 -> stage-2 step of the pipeline
+//   vhat = FFT( ZeroPad( D_t( Truncate( IFFT(mhat) ) ) ) )
+// is a fixed real-linear map of its Nt + 1 bins.  Bins 0 and Nt of a real
+// signal are real, so both sides have exactly K = 2 Nt real degrees of
+// freedom, ordered  k = 0: Re bin 0,  k = 1: Re bin Nt,  k = 2l, 2l+1:
+// Re, Im of bin l (0 < l < Nt).  With T[n][k] (built on the host in FP64 from
+// the definitions, rounded to BF16) every tile of 128 signals is
+//   V (128 x K) = M (128 x K) T^T,
+// one tcgen05 GEMM per tile.  The M tile is written into shared memory by
+// eight fill warps (coalesced loads of mhat[l][b][i0..i0+127], BF16
+// conversion, 128-byte swizzled K-major layout), T streams through a ring by
+// TMA (it stays in L2), the accumulator rows go back out as BF16 velocity
+// spectra in the stage-2 operand layout.
+// Warps: 0 TMA (T), 1 TMEM + MMA, 2-5 epilogue, 6-13 fill.
+// ---------------------------------------------------------------------------
+constexpr int kRtThreads = 448;
+constexpr int kRtFillWarps = 8;
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(kRtThreads, 1)
+    k_tc_retransform(const __grid_constant__ CUtensorMap tmT, const TcRtArgs a) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+  const int Nt = a.Nt;
+  const int K = 2 * Nt;           // = N
+  const int KB = K / kBlockK;     // k-blocks per tile (A slots)
+  const int n_mma = K > 256 ? 2 : 1;
+  const int ncols = K > 256 ? 256 : K;
+  const int t_bytes = ncols * kBlockK * 2;
+  unsigned char* sA = smem;                               // KB slots of 16 KB
+  unsigned char* sT = smem + KB * kABytes;                // 2 stages of t_bytes
+  uint64_t* afull = reinterpret_cast<uint64_t*>(sT + 2 * t_bytes);
+  uint64_t* afree = afull + KB;
+  uint64_t* tfull = afree + KB;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* acc_full = tempty + 2;
+  uint64_t* acc_empty = acc_full + 1;
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(acc_empty + 1);
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int mtiles = (a.Ng + kBlockM - 1) / kBlockM;
+  const long long tiles = static_cast<long long>(a.Bs) * mtiles;
+  const uint32_t idesc = idesc_bf16(kBlockM, ncols);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < KB; ++s) {
+      mbar_init(afull + s, kRtFillWarps);
+      mbar_init(afree + s, 1);
+    }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(tfull + s, 1);
+      mbar_init(tempty + s, 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, 4);
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_holder, K > 256 ? 512 : (K > 128 ? 256 : (K > 64 ? 128 : 64)));
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_holder;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int it = 0;
+      bool ok = true;
+      for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+        for (int kb = 0; kb < KB && ok; ++kb) {
+          for (int h = 0; h < n_mma; ++h, ++it) {
+            const int s = it & 1;
+            if (it >= 2 && !mbar_wait_bounded(tempty + s, ((it >> 1) - 1) & 1, a.status, DEV_ERR_TIMEOUT_EMPTY)) {
+              ok = false;
+              break;
+            }
+            mbar_arrive_expect_tx(tfull + s, t_bytes);
+            tma_load_3d(sT + s * t_bytes, &tmT, kb * kBlockK, h * ncols, 0, tfull + s);
+          }
+        }
+      }
+      for (int kk = (it > 2 ? it - 2 : 0); kk < it; ++kk)
+        mbar_wait_bounded(tfull + (kk & 1), (kk >> 1) & 1, a.status, DEV_ERR_TIMEOUT_FULL);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int it = 0, tl = 0;
+      bool ok = true;
+      for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++tl) {
+        if (tl > 0 && !mbar_wait_bounded(acc_empty, (tl - 1) & 1, a.status, DEV_ERR_TIMEOUT_MMA)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        for (int kb = 0; kb < KB && ok; ++kb) {
+          if (!mbar_wait_bounded(afull + kb, tl & 1, a.status, DEV_ERR_TIMEOUT_FULL)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(sA + kb * kABytes);
+          for (int h = 0; h < n_mma; ++h, ++it) {
+            const int s = it & 1;
+            if (!mbar_wait_bounded(tfull + s, (it >> 1) & 1, a.status, DEV_ERR_TIMEOUT_FULL)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t sb = smem_u32(sT + s * t_bytes);
+#pragma unroll
+            for (int k = 0; k < kBlockK / 16; ++k)
+              tc_mma_bf16(tmem + h * ncols, sdesc_sw128(sa + k * 32), sdesc_sw128(sb + k * 32), idesc,
+                          (kb > 0 || k > 0) ? 1u : 0u);
+            tc_commit(tempty + s);
+          }
+          tc_commit(afree + kb);
+        }
+        if (!ok) break;
+        tc_commit(acc_full);
+      }
+      if (tl > 0) mbar_wait_bounded(acc_empty, (tl - 1) & 1, a.status, DEV_ERR_TIMEOUT_MMA);
+    }
+  } else if (warp < 6) {
+    // epilogue: accumulator row = signal, columns = output degrees of freedom
+    const int q = warp & 3;
+    int tl = 0;
+    for (long long t = blockIdx.x; t < tiles; t += gridDim.x, ++tl) {
+      const int b = static_cast<int>(t / mtiles);
+      const int i = static_cast<int>(t % mtiles) * kBlockM + q * 32 + lane;
+      if (!mbar_wait_bounded(acc_full, tl & 1, a.status, DEV_ERR_TIMEOUT_MMA)) break;
+      tc_fence_after();
+      const uint32_t tbase = tmem + (static_cast<uint32_t>(q * 32) << 16);
+      __nv_bfloat162* out = a.vhat + static_cast<long long>(b) * a.vld_b + i;
+      for (int c0 = 0; c0 < K; c0 += 16) {
+        float v[16];
+        tmem_ld16(tbase + c0, v);
+        if (i >= a.Ng) continue;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int l = c0 / 2 + k;
+          if (l == 0) {
+            out[0] = __floats2bfloat162_rn(v[0], 0.f);
+            out[static_cast<long long>(Nt) * a.vld_l] = __floats2bfloat162_rn(v[1], 0.f);
+          } else {
+            out[static_cast<long long>(l) * a.vld_l] = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acc_empty);
+    }
+  } else {
+    // fill warps: M tile k-block kb holds bins 32 kb .. 32 kb + 31 for 128 signals
+    const int f = warp - 6;
+    int tl = 0;
+    bool ok = true;
+    for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++tl) {
+      const int b = static_cast<int>(t / mtiles);
+      const int i0 = static_cast<int>(t % mtiles) * kBlockM;
+      const float2* mb = a.mhat + static_cast<long long>(b) * a.ld_b;
+      for (int kb = 0; kb < KB; ++kb) {
+        if (tl > 0 && !mbar_wait_bounded(afree + kb, (tl - 1) & 1, a.status, DEV_ERR_TIMEOUT_EMPTY)) {
+          ok = false;
+          break;
+        }
+        unsigned char* slot = sA + kb * kABytes;
+        float2 v[4][4];
+        float2 vn[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {        // bins: l_local = f + 8 j
+          const int l = kb * 32 + f + 8 * j;
+#pragma unroll
+          for (int g = 0; g < 4; ++g) {      // signals: row = 32 g + lane
+            const int i = i0 + 32 * g + lane;
+            v[j][g] = (i < a.Ng) ? __ldg(mb + static_cast<long long>(l) * a.ld_l + i) : make_float2(0.f, 0.f);
+          }
+        }
+        if (kb == 0 && f == 0) {
+#pragma unroll
+          for (int g = 0; g < 4; ++g) {
+            const int i = i0 + 32 * g + lane;
+            vn[g] = (i < a.Ng) ? __ldg(mb + static_cast<long long>(Nt) * a.ld_l + i) : make_float2(0.f, 0.f);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int ll = f + 8 * j;          // local bin -> k_local = 2 ll, 2 ll + 1
+#pragma unroll
+          for (int g = 0; g < 4; ++g) {
+            const int row = 32 * g + lane;
+            float2 z = v[j][g];
+            if (kb == 0 && ll == 0) z.y = vn[g].x;  // slot k = 1 carries Re(bin Nt)
+            const int byte = ll * 4;                 // (2 ll) bf16 * 2 bytes
+            const int off = row * 128 + ((((byte >> 4) ^ (row & 7)) << 4) | (byte & 15));
+            *reinterpret_cast<__nv_bfloat162*>(slot + off) = __floats2bfloat162_rn(z.x, z.y);
+          }
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(afull + kb);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, K > 256 ? 512 : (K > 128 ? 256 : (K > 64 ? 128 : 64)));
+  }
+}
+
 int grid_for_tc(long long n) {
   long long g = (n + 255) / 256;
   if (g > 152LL * 32) g = 152LL * 32;
@@ -350,6 +569,22 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
   if (e != cudaSuccess) return e;
   const long long grid = units < num_sms ? units : num_sms;
   k_tc_gemm<<<static_cast<unsigned>(grid), kTcThreads, smem, st>>>(tmA, tmB, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_retransform(const CUtensorMap& tmT, const TcRtArgs& a, int num_sms, cudaStream_t st) {
+  if (a.Nt < 32 || a.Nt > 256) return cudaErrorInvalidValue;
+  const long long tiles = static_cast<long long>(a.Bs) * ((a.Ng + kBlockM - 1) / kBlockM);
+  if (tiles <= 0) return cudaSuccess;
+  const int K = 2 * a.Nt;
+  const int ncols = K > 256 ? 256 : K;
+  const size_t smem = 1024 + static_cast<size_t>(K / kBlockK) * kABytes + 2ull * ncols * kBlockK * 2 +
+                      8 * (2 * (K / kBlockK) + 6) + 16;
+  cudaError_t e =
+      cudaFuncSetAttribute(k_tc_retransform, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  const long long grid = tiles < num_sms ? tiles : num_sms;
+  k_tc_retransform<<<static_cast<unsigned>(grid), kRtThreads, smem, st>>>(tmT, a);
   return cudaGetLastError();
 }
 

@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -57,6 +58,8 @@ struct s2w_ctx {
   void* tc_vhat = nullptr;  // [Nb][tc_bsub][Ng_pad2] bf16 pairs
   float2* tc_part = nullptr;  // [Nb][nkc][b][No] complex FP32
   void* tc_p2 = nullptr;    // [Nb][tc_n2][Ng_pad2] bf16 pairs
+  void* tc_T = nullptr;     // [2 Nt][2 Nt] bf16: retransform as a real-linear map
+  CUtensorMap tc_tmT;
   std::vector<unsigned char> g_loaded, p_loaded;
   long long g_count = 0, p_count = 0;
   // per-stage event timers
@@ -181,9 +184,52 @@ void free_all(s2w_ctx* c) {
   c->ev_free.clear();
   void* ps[] = {c->G, c->G_lo, c->G_scale, c->P, c->tw, c->ws_slip, c->ws_shat, c->ws_mhat,
                 c->ws_vhat, c->ws_part, c->ws_q, c->ws_seafloor, c->d_status, c->tc_bp1,
-                c->tc_mhat, c->tc_vhat, c->tc_part, c->tc_p2};
+                c->tc_mhat, c->tc_vhat, c->tc_part, c->tc_p2, c->tc_T};
   for (void* p : ps)
     if (p) cudaFree(p);
+}
+
+// The retransform of one signal, vhat = FFT(ZeroPad(D_t(Truncate(IFFT(mhat))))),
+// as a real 2 Nt x 2 Nt matrix T[n][k] over the degrees of freedom
+// k = 0: Re bin 0, k = 1: Re bin Nt, k = 2l / 2l+1: Re / Im bin l (0 < l < Nt),
+// the same ordering for the outputs n.  Column k is the map applied to basis
+// spectrum k, evaluated in FP64 from the definitions (inverse DFT head,
+// backward difference, zero-padded DFT), then rounded to BF16.
+std::vector<__nv_bfloat16> retransform_matrix(int Nt, int dt_mode, double dt) {
+  const int L = 2 * Nt, K = 2 * Nt;
+  std::vector<double> c(L), sn(L);
+  for (int m = 0; m < L; ++m) {
+    const double ang = 2.0 * 3.14159265358979323846 * m / L;
+    c[m] = std::cos(ang);
+    sn[m] = std::sin(ang);
+  }
+  std::vector<double> T(static_cast<size_t>(K) * K, 0.0), x(Nt), v(Nt);
+  for (int k = 0; k < K; ++k) {
+    for (int n = 0; n < Nt; ++n) {
+      if (k == 0) x[n] = 1.0 / L;
+      else if (k == 1) x[n] = (n % 2 == 0 ? 1.0 : -1.0) / L;
+      else if (k % 2 == 0) x[n] = 2.0 / L * c[(static_cast<long long>(k / 2) * n) % L];
+      else x[n] = -2.0 / L * sn[(static_cast<long long>(k / 2) * n) % L];
+    }
+    for (int n = 0; n < Nt; ++n) v[n] = dt_mode == S2W_DT_NONE ? x[n] : (x[n] - (n > 0 ? x[n - 1] : 0.0)) / dt;
+    for (int l = 0; l <= Nt; ++l) {
+      double re = 0.0, im = 0.0;
+      for (int n = 0; n < Nt; ++n) {
+        const long long m = (static_cast<long long>(n) * l) % L;
+        re += v[n] * c[m];
+        im -= v[n] * sn[m];
+      }
+      if (l == 0) T[0 * K + k] = re;
+      else if (l == Nt) T[1 * K + k] = re;
+      else {
+        T[static_cast<size_t>(2 * l) * K + k] = re;
+        T[static_cast<size_t>(2 * l + 1) * K + k] = im;
+      }
+    }
+  }
+  std::vector<__nv_bfloat16> out(T.size());
+  for (size_t e = 0; e < T.size(); ++e) out[e] = __float2bfloat16_rn(static_cast<float>(T[e]));
+  return out;
 }
 
 // Tensor-core pipeline for a batch of ruptures (slip and q device pointers),
@@ -234,11 +280,26 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, float
     }
     {
       StageTimer t(ctx, 2, st);
-      float* sf = seafloor ? seafloor + static_cast<long long>(b0) * Ng * Nt : nullptr;
-      CK(launch_retransform(ctx->tc_mhat, Ng, static_cast<long long>(Bs) * Ng, static_cast<int>(Nt), ctx->tw,
-                            static_cast<float>(1.0 / ctx->opts.dt), ctx->opts.dt_mode, nullptr,
-                            static_cast<long long>(ctx->tc_bsub) * ctx->Ng_pad2, sf, st, Bs, Ng, ctx->Ng_pad2,
-                            static_cast<__nv_bfloat162*>(ctx->tc_vhat)));
+      if (seafloor == nullptr && ctx->tc_T != nullptr) {
+        TcRtArgs r{};
+        r.mhat = ctx->tc_mhat;
+        r.ld_l = static_cast<long long>(Bs) * Ng;
+        r.ld_b = Ng;
+        r.Ng = static_cast<int>(Ng);
+        r.Bs = Bs;
+        r.Nt = static_cast<int>(Nt);
+        r.vhat = static_cast<__nv_bfloat162*>(ctx->tc_vhat);
+        r.vld_l = static_cast<long long>(ctx->tc_bsub) * ctx->Ng_pad2;
+        r.vld_b = ctx->Ng_pad2;
+        r.status = ctx->d_status;
+        CK(launch_tc_retransform(ctx->tc_tmT, r, ctx->num_sms, st));
+      } else {
+        float* sf = seafloor ? seafloor + static_cast<long long>(b0) * Ng * Nt : nullptr;
+        CK(launch_retransform(ctx->tc_mhat, Ng, static_cast<long long>(Bs) * Ng, static_cast<int>(Nt), ctx->tw,
+                              static_cast<float>(1.0 / ctx->opts.dt), ctx->opts.dt_mode, nullptr,
+                              static_cast<long long>(ctx->tc_bsub) * ctx->Ng_pad2, sf, st, Bs, Ng, ctx->Ng_pad2,
+                              static_cast<__nv_bfloat162*>(ctx->tc_vhat)));
+      }
     }
     {
       StageTimer t(ctx, 3, st);
@@ -403,6 +464,17 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
       return bad(e, "tensor stage-2 partials");
     if ((e = dalloc(&ctx->tc_p2, 4ull * Nb * ctx->tc_n2 * ctx->Ng_pad2)) != cudaSuccess)
       return bad(e, "tensor stage-2 operand");
+    if (Nt <= 256) {
+      const std::vector<__nv_bfloat16> T = retransform_matrix(Nt, o.dt_mode, o.dt);
+      if ((e = dalloc(&ctx->tc_T, sizeof(__nv_bfloat16) * T.size())) != cudaSuccess)
+        return bad(e, "retransform matrix");
+      if ((e = cudaMemcpy(ctx->tc_T, T.data(), sizeof(__nv_bfloat16) * T.size(), cudaMemcpyHostToDevice)) !=
+          cudaSuccess)
+        return bad(e, "retransform matrix");
+      const int K = 2 * Nt;
+      if ((e = tc_encode_3d(&ctx->tc_tmT, ctx->tc_T, K, K, 1, K, K > 256 ? 256 : K)) != cudaSuccess)
+        return bad(e, "retransform tensor map");
+    }
   }
   if ((e = launch_twiddles(ctx->tw, ctx->L, nullptr)) != cudaSuccess) return bad(e, "twiddles");
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bad(e, "create sync");

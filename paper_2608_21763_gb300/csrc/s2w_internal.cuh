@@ -190,6 +190,18 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
                            cudaStream_t st);
 cudaError_t launch_pack_stage1_b(const float2* shat, int B, int Ns_pad, int Nb, int N_alloc, void* Bp,
                                  cudaStream_t st);
+// Retransform of Bs ruptures as one GEMM per 128-signal tile (see k_tc.cu):
+// reads mhat[l*ld_l + b*ld_b + i], writes vhat[l*vld_l + b*vld_b + i] (BF16
+// pairs); tmT: T[n][k], 2 Nt x 2 Nt BF16, K-major.  32 <= Nt <= 256.
+struct TcRtArgs {
+  const float2* mhat;
+  long long ld_l, ld_b;
+  int Ng, Bs, Nt;
+  __nv_bfloat162* vhat;
+  long long vld_l, vld_b;
+  int* status;
+};
+cudaError_t launch_tc_retransform(const CUtensorMap& tmT, const TcRtArgs& a, int num_sms, cudaStream_t st);
 cudaError_t launch_pack_stage2_b(const float2* src, int Nb, int No, long long nc, long long c0, long long Kc,
                                  int N_alloc, void* Pp, cudaStream_t st);
 

@@ -101,3 +101,35 @@ def test_auto_engine_uses_tensor_path_for_batches_only():
     assert_parity(q_batch, q_ref, wn, kappa, tol=TOL_TC, label="auto batch")
     assert_parity(q_one, q_ref[:1], wn[:1], kappa[:1], tol=5e-3, label="auto single")
     assert stages["contract_stage1"][1] == 2  # one tensor pass + one streaming pass
+
+
+def test_tensor_engine_with_seafloor_output():
+    """With a seafloor field requested the tensor path forms m by the FFT
+    retransform (the GEMM retransform never materialises m); both outputs
+    meet the tensor-engine bar."""
+    geom = compact_box(24, 700, 6, seed=8)
+    Nt, B = 64, 6
+    rng = np.random.default_rng(10)
+    slip = rng.standard_normal((B, geom.Ns, Nt))
+    slip[:, :, Nt // 2:] = 0
+    ctx = make_context(s2w, geom, Nt, prec_g="bf16", max_batch=B, engine="tensor")
+    st = torch.tensor(slip, dtype=torch.float32, device="cuda")
+    sf = torch.empty((B, geom.Ng, Nt), dtype=torch.float32, device="cuda")
+    q_sf = ctx.waveforms(st, seafloor=sf).cpu().numpy()
+    q = ctx.waveforms(st).cpu().numpy()
+    G = geom.greens_rows(0, geom.Ng, Nt)
+    P = geom.adjoint_cols(0, geom.Ng, Nt)
+    q_ref, m_ref = oracle.waveforms(G, P, slip, return_seafloor=True)
+    wn, kappa = window_norms(G, P, slip)
+    assert_parity(q, q_ref, wn, kappa, tol=TOL_TC, label="tensor, GEMM retransform")
+    assert_parity(q_sf, q_ref, wn, kappa, tol=TOL_TC, label="tensor, FFT retransform")
+    m = sf.cpu().numpy()
+    err = np.linalg.norm((m - m_ref).reshape(B, -1), axis=1) / np.linalg.norm(m_ref.reshape(B, -1), axis=1)
+    assert np.all(err <= TOL_TC), err
+
+
+@pytest.mark.parametrize("Nt", [32, 128, 256])
+def test_gemm_retransform_record_lengths(Nt):
+    geom = compact_box(12, 300, 3, seed=Nt)
+    q, q_ref, wn, _, _ = run_case(geom, Nt, 4)
+    assert_parity(q, q_ref, *wn, tol=TOL_TC, label=f"tensor Nt={Nt}")
