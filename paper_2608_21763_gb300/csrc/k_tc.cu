@@ -95,15 +95,20 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 // 128-byte swizzle: rows of 128 bytes, 8-row core-matrix groups 1024 bytes
 // apart (stride byte offset), tile base 1024-byte aligned; advancing along K
 // inside the swizzle row is a plain byte offset of the start address.
-__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+template <int BK>
+__device__ __forceinline__ uint64_t sdesc_sw(uint32_t saddr) {
+  // BK = 64: rows of 128 B, 128-byte swizzle; BK = 32: rows of 64 B, 64-byte swizzle
+  constexpr uint32_t sbo = 8 * BK * 2;
+  constexpr uint64_t layout = BK == 64 ? 2 : 4;
   uint64_t d = 0;
   d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);  // start address
   d |= static_cast<uint64_t>(1) << 16;                  // leading byte offset (unused here)
-  d |= static_cast<uint64_t>(1024 >> 4) << 32;          // stride byte offset
+  d |= static_cast<uint64_t>(sbo >> 4) << 32;           // stride byte offset (8-row groups)
   d |= static_cast<uint64_t>(1) << 46;                  // descriptor version (tcgen05)
-  d |= static_cast<uint64_t>(2) << 61;                  // 128-byte swizzle
+  d |= layout << 61;                                    // swizzle mode
   return d;
 }
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) { return sdesc_sw<64>(saddr); }
 
 // Instruction descriptor, kind::f16: BF16 A and B, FP32 D, both K-major.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
@@ -111,13 +116,15 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
          (static_cast<uint32_t>(M >> 4) << 24);
 }
 
+template <int BK>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
+  constexpr int kA = kBlockM * BK * 2;
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
   const int N = a.N;
-  const int b_bytes = N * kBlockK * 2;
-  const int stage_bytes = kABytes + b_bytes;
+  const int b_bytes = N * BK * 2;
+  const int stage_bytes = kA + b_bytes;
   const int S = a.stages;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * stage_bytes);
   uint64_t* empty = full + S;
@@ -126,7 +133,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(acc_empty + 1);
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int nk_total = (a.K + kBlockK - 1) / kBlockK;
+  const int nk_total = (a.K + BK - 1) / BK;
   const long long units = static_cast<long long>(a.Nb) * a.m_tiles * a.n_kchunks;
   const int n_mma = N > 256 ? N / 256 : 1;
   const int n_mma_cols = N > 256 ? 256 : N;
@@ -169,9 +176,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           }
           unsigned char* sa = smem + s * stage_bytes;
           mbar_arrive_expect_tx(full + s, stage_bytes);
-          tma_load_3d(sa, &tmA, kb * kBlockK, mt * kBlockM, l, full + s);
+          tma_load_3d(sa, &tmA, kb * BK, mt * kBlockM, l, full + s);
           for (int c = 0; c < n_mma; ++c)
-            tma_load_3d(sa + kABytes + c * n_mma_cols * kBlockK * 2, &tmB, kb * kBlockK, c * n_mma_cols, l, full + s);
+            tma_load_3d(sa + kA + c * n_mma_cols * BK * 2, &tmB, kb * BK, c * n_mma_cols, l, full + s);
         }
       }
       for (int kk = (it > S ? it - S : 0); kk < it; ++kk)
@@ -198,12 +205,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           }
           tc_fence_after();
           const uint32_t sa = smem_u32(smem + s * stage_bytes);
-          const uint32_t sb = sa + kABytes;
+          const uint32_t sb = sa + kA;
 #pragma unroll
-          for (int k = 0; k < kBlockK / 16; ++k) {
-            const uint64_t ad = sdesc_sw128(sa + k * 32);
+          for (int k = 0; k < BK / 16; ++k) {
+            const uint64_t ad = sdesc_sw<BK>(sa + k * 32);
             for (int c = 0; c < n_mma; ++c) {
-              const uint64_t bd = sdesc_sw128(sb + c * n_mma_cols * kBlockK * 2 + k * 32);
+              const uint64_t bd = sdesc_sw<BK>(sb + c * n_mma_cols * BK * 2 + k * 32);
               tc_mma_bf16(tmem + c * n_mma_cols, ad, bd, idesc, (kb > kb0 || k > 0) ? 1u : 0u);
             }
           }
@@ -241,7 +248,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           const int t = c0 / 2 + k;  // complex column (rupture or observation)
           if (t < a.T) {
             const float2 z = make_float2(v[2 * k] * scale, v[2 * k + 1] * scale);
-            if (a.epi == 0)
+            if (a.epi == 0 && a.out_bf != nullptr)
+              a.out_bf[static_cast<long long>(l) * a.ld_l + static_cast<long long>(t) * a.ld_t + row] =
+                  __floats2bfloat162_rn(z.x, z.y);
+            else if (a.epi == 0)
               a.out[static_cast<long long>(l) * a.ld_l + static_cast<long long>(t) * a.ld_t + row] = z;
             else
               a.out[((static_cast<long long>(l) * a.n_kchunks + kc) * a.M_total + row) * a.T + t] = z;
@@ -321,6 +331,7 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+template <bool BF16IN>
 __global__ void __launch_bounds__(kRtThreads, 1)
     k_tc_retransform(const __grid_constant__ CUtensorMap tmT, const TcRtArgs a) {
   extern __shared__ __align__(1024) unsigned char smraw[];
@@ -464,7 +475,7 @@ __global__ void __launch_bounds__(kRtThreads, 1)
     for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++tl) {
       const int b = static_cast<int>(t / mtiles);
       const int i0 = static_cast<int>(t % mtiles) * kBlockM;
-      const float2* mb = a.mhat + static_cast<long long>(b) * a.ld_b;
+      const float2* mb = a.mhat + static_cast<long long>(b) * a.ld_b;  // unused when mhat_bf is set
       for (int kb = 0; kb < KB; ++kb) {
         if (tl > 0 && !mbar_wait_bounded(afree + kb, (tl - 1) & 1, a.status, DEV_ERR_TIMEOUT_EMPTY)) {
           ok = false;
@@ -473,20 +484,46 @@ __global__ void __launch_bounds__(kRtThreads, 1)
         unsigned char* slot = sA + kb * kABytes;
         float2 v[4][4];
         float2 vn[4];
+        // all loads of the k-block first (16 per lane), then convert and store
+        if (BF16IN) {
+          const unsigned* mbb = reinterpret_cast<const unsigned*>(a.mhat_bf) + static_cast<long long>(b) * a.ld_b;
+          unsigned raw[4][4], rawn[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {        // bins: l_local = f + 8 j
-          const int l = kb * 32 + f + 8 * j;
+          for (int j = 0; j < 4; ++j) {      // bins: l_local = f + 8 j
+            const long long lo = static_cast<long long>(kb * 32 + f + 8 * j) * a.ld_l;
 #pragma unroll
-          for (int g = 0; g < 4; ++g) {      // signals: row = 32 g + lane
-            const int i = i0 + 32 * g + lane;
-            v[j][g] = (i < a.Ng) ? __ldg(mb + static_cast<long long>(l) * a.ld_l + i) : make_float2(0.f, 0.f);
+            for (int g = 0; g < 4; ++g) {    // signals: row = 32 g + lane
+              const int i = i0 + 32 * g + lane;
+              raw[j][g] = i < a.Ng ? __ldg(mbb + lo + i) : 0u;
+            }
           }
-        }
-        if (kb == 0 && f == 0) {
 #pragma unroll
           for (int g = 0; g < 4; ++g) {
             const int i = i0 + 32 * g + lane;
-            vn[g] = (i < a.Ng) ? __ldg(mb + static_cast<long long>(Nt) * a.ld_l + i) : make_float2(0.f, 0.f);
+            rawn[g] = (kb == 0 && f == 0 && i < a.Ng) ? __ldg(mbb + static_cast<long long>(Nt) * a.ld_l + i) : 0u;
+          }
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int g = 0; g < 4; ++g)
+              v[j][g] = make_float2(__uint_as_float(raw[j][g] << 16), __uint_as_float(raw[j][g] & 0xffff0000u));
+#pragma unroll
+          for (int g = 0; g < 4; ++g) vn[g] = make_float2(__uint_as_float(rawn[g] << 16), 0.f);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const long long lo = static_cast<long long>(kb * 32 + f + 8 * j) * a.ld_l;
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+              const int i = i0 + 32 * g + lane;
+              v[j][g] = i < a.Ng ? __ldg(mb + lo + i) : make_float2(0.f, 0.f);
+            }
+          }
+#pragma unroll
+          for (int g = 0; g < 4; ++g) {
+            const int i = i0 + 32 * g + lane;
+            vn[g] = (kb == 0 && f == 0 && i < a.Ng) ? __ldg(mb + static_cast<long long>(Nt) * a.ld_l + i)
+                                                    : make_float2(0.f, 0.f);
           }
         }
 #pragma unroll
@@ -527,7 +564,7 @@ PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 }  // namespace
 
 cudaError_t tc_encode_3d(CUtensorMap* out, const void* base, long long K, long long rows, long long nbatch,
-                         long long row_pitch_elems, int box_rows) {
+                         long long row_pitch_elems, int box_rows, int bk) {
   if (g_encode == nullptr) {
     void* fn = nullptr;
     cudaDriverEntryPointQueryResult q;
@@ -539,23 +576,28 @@ cudaError_t tc_encode_3d(CUtensorMap* out, const void* base, long long K, long l
                               static_cast<cuuint64_t>(nbatch)};
   const cuuint64_t strides[2] = {static_cast<cuuint64_t>(row_pitch_elems) * 2,
                                  static_cast<cuuint64_t>(row_pitch_elems) * 2 * static_cast<cuuint64_t>(rows)};
-  const cuuint32_t box[3] = {static_cast<cuuint32_t>(kBlockK), static_cast<cuuint32_t>(box_rows), 1};
+  const cuuint32_t box[3] = {static_cast<cuuint32_t>(bk), static_cast<cuuint32_t>(box_rows), 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = g_encode(out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+int tc_block_k(int N) { return N > 256 ? 32 : 64; }
+
 int tc_stages_for(int N) {
-  const int stage = kABytes + N * kBlockK * 2;
+  const int bk = tc_block_k(N);
+  const int stage = kBlockM * bk * 2 + N * bk * 2;
   int s = kSmemBudget / stage;
   if (s > 8) s = 8;
   return s;
 }
 
 size_t tc_smem_bytes(int N, int stages) {
-  return 1024 + static_cast<size_t>(stages) * (kABytes + N * kBlockK * 2) + 8 * (2 * stages + 2) + 16;
+  const int bk = tc_block_k(N);
+  return 1024 + static_cast<size_t>(stages) * (kBlockM * bk * 2 + N * bk * 2) + 8 * (2 * stages + 2) + 16;
 }
 
 cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const TcArgs& a, int num_sms,
@@ -565,10 +607,18 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
   if (a.N < 16 || a.N > 512 || a.N % 16 != 0 || (a.N > 256 && a.N % 256 != 0) || a.stages < 2)
     return cudaErrorInvalidValue;
   const size_t smem = tc_smem_bytes(a.N, a.stages);
-  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-  if (e != cudaSuccess) return e;
   const long long grid = units < num_sms ? units : num_sms;
-  k_tc_gemm<<<static_cast<unsigned>(grid), kTcThreads, smem, st>>>(tmA, tmB, a);
+  if (tc_block_k(a.N) == 64) {
+    cudaError_t e =
+        cudaFuncSetAttribute(k_tc_gemm<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    k_tc_gemm<64><<<static_cast<unsigned>(grid), kTcThreads, smem, st>>>(tmA, tmB, a);
+  } else {
+    cudaError_t e =
+        cudaFuncSetAttribute(k_tc_gemm<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    k_tc_gemm<32><<<static_cast<unsigned>(grid), kTcThreads, smem, st>>>(tmA, tmB, a);
+  }
   return cudaGetLastError();
 }
 
@@ -580,11 +630,18 @@ cudaError_t launch_tc_retransform(const CUtensorMap& tmT, const TcRtArgs& a, int
   const int ncols = K > 256 ? 256 : K;
   const size_t smem = 1024 + static_cast<size_t>(K / kBlockK) * kABytes + 2ull * ncols * kBlockK * 2 +
                       8 * (2 * (K / kBlockK) + 6) + 16;
-  cudaError_t e =
-      cudaFuncSetAttribute(k_tc_retransform, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-  if (e != cudaSuccess) return e;
   const long long grid = tiles < num_sms ? tiles : num_sms;
-  k_tc_retransform<<<static_cast<unsigned>(grid), kRtThreads, smem, st>>>(tmT, a);
+  if (a.mhat_bf != nullptr) {
+    cudaError_t e = cudaFuncSetAttribute(k_tc_retransform<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    k_tc_retransform<true><<<static_cast<unsigned>(grid), kRtThreads, smem, st>>>(tmT, a);
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(k_tc_retransform<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    k_tc_retransform<false><<<static_cast<unsigned>(grid), kRtThreads, smem, st>>>(tmT, a);
+  }
   return cudaGetLastError();
 }
 

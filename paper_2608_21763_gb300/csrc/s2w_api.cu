@@ -258,8 +258,9 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, float
     {
       StageTimer t(ctx, 1, st);
       CUtensorMap ta, tb;
-      CK(tc_encode_3d(&ta, ctx->G, K1, Ng, Nb, K1, 128));
-      CK(tc_encode_3d(&tb, ctx->tc_bp1, K1, ctx->tc_n1max, Nb, K1, N1 > 256 ? 256 : N1));
+      const int bk = tc_block_k(N1);
+      CK(tc_encode_3d(&ta, ctx->G, K1, Ng, Nb, K1, 128, bk));
+      CK(tc_encode_3d(&tb, ctx->tc_bp1, K1, ctx->tc_n1max, Nb, K1, N1 > 256 ? 256 : N1, bk));
       TcArgs a{};
       a.N = N1;
       a.K = K1;
@@ -267,12 +268,15 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, float
       a.Nb = static_cast<int>(Nb);
       a.m_tiles = static_cast<int>((Ng + 127) / 128);
       a.n_kchunks = 1;
-      a.kblocks_per_chunk = (K1 + 63) / 64;
+      a.kblocks_per_chunk = (K1 + bk - 1) / bk;
       a.stages = tc_stages_for(N1);
       a.tmem_cols = N1 <= 32 ? 32 : (N1 <= 64 ? 64 : (N1 <= 128 ? 128 : (N1 <= 256 ? 256 : 512)));
       a.epi = 0;
       a.T = Bs;
       a.out = ctx->tc_mhat;
+      // the GEMM retransform rounds the seafloor spectra to BF16 anyway
+      const bool gemm_rt = seafloor == nullptr && ctx->tc_T != nullptr;
+      a.out_bf = gemm_rt ? reinterpret_cast<__nv_bfloat162*>(ctx->tc_mhat) : nullptr;
       a.ld_l = static_cast<long long>(Bs) * Ng;
       a.ld_t = Ng;
       a.status = ctx->d_status;
@@ -283,6 +287,7 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, float
       if (seafloor == nullptr && ctx->tc_T != nullptr) {
         TcRtArgs r{};
         r.mhat = ctx->tc_mhat;
+        r.mhat_bf = reinterpret_cast<const __nv_bfloat162*>(ctx->tc_mhat);
         r.ld_l = static_cast<long long>(Bs) * Ng;
         r.ld_b = Ng;
         r.Ng = static_cast<int>(Ng);

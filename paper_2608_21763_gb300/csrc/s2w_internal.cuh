@@ -178,13 +178,16 @@ struct TcArgs {
   int epi;                // 0: out[l*ld_l + t*ld_t + row]; 1: out[((l*n_kchunks + kc)*M_total + row)*T + t]
   int T;                  // complex output columns (N / 2 live)
   float2* out;
+  __nv_bfloat162* out_bf;  // epi 0: write BF16 pairs here instead of `out`
   long long ld_l, ld_t;
   const float* row_scale;  // optional per-(bin, 256-row block) scale
   int nblk;
   int* status;
 };
+// bk = 64: 128-byte swizzle, K boxes of 64 BF16; bk = 32: 64-byte swizzle.
 cudaError_t tc_encode_3d(CUtensorMap* out, const void* base, long long K, long long rows, long long nbatch,
-                         long long row_pitch_elems, int box_rows);
+                         long long row_pitch_elems, int box_rows, int bk = 64);
+int tc_block_k(int N);
 int tc_stages_for(int N);
 cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const TcArgs& a, int num_sms,
                            cudaStream_t st);
@@ -195,6 +198,7 @@ cudaError_t launch_pack_stage1_b(const float2* shat, int B, int Ns_pad, int Nb, 
 // pairs); tmT: T[n][k], 2 Nt x 2 Nt BF16, K-major.  32 <= Nt <= 256.
 struct TcRtArgs {
   const float2* mhat;
+  const __nv_bfloat162* mhat_bf;  // when set, mhat is read as BF16 pairs from here
   long long ld_l, ld_b;
   int Ng, Bs, Nt;
   __nv_bfloat162* vhat;
