@@ -131,6 +131,18 @@ int s2w_load_adjoint(s2w_ctx *ctx, int g0, int ng, const float *P, void *stream)
  * loaded (else S2W_ERR_STATE). */
 int s2w_waveforms(s2w_ctx *ctx, const float *slip, int B, float *q, float *seafloor, void *stream);
 
+/* Adjoint of s2w_waveforms (the paper has no adjoint of the pipeline; this is
+ * the transpose of the same map): for B residual sets r[b] ([No][Nt]),
+ *   grad_s[b] = F_G^T D_t^T F_q^T r[b]     ([Ns][Nt]),
+ * i.e. the gradient of 0.5 ||q(s) - d||^2 with respect to the slip-rate
+ * histories when r = q(s) - d.  Each transpose is a correlation with the
+ * conjugate spectra, (F^T y)_j[n] = sum_i sum_{k <= Nt-1-n} f_ij[k] y_i[n+k],
+ * evaluated as conj(Fhat_l) yhat_l per bin with zero padding to 2 Nt (no
+ * wrap reaches the kept samples), and D_t^T w[n] = (w[n] - w[n+1]) / dt with
+ * w[Nt] = 0.  Uses the streaming kernels, one rupture at a time, for every
+ * storage precision.  Pointer and stream rules as s2w_waveforms. */
+int s2w_adjoint(s2w_ctx *ctx, const float *r, int B, float *grad_s, void *stream);
+
 /* Waveforms for ONE rupture without allocating any memory (the paper has no
  * counterpart; this serves callers that cannot let a library allocate device
  * memory: applications whose device memory all comes from their own pool,

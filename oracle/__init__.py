@@ -225,6 +225,23 @@ def fft_window(G, P, s, dt_mode: str = "backward", dt: float = 1.0):
     return bltt_apply(ext(P), ext(v))
 
 
+def fft_window_adjoint(G, P, r, dt_mode: str = "backward", dt: float = 1.0):
+    """Adjoint analogue of ``fft_window``: the full correlation window that
+    an FFT evaluation of ``F_G^T D_t^T F_q^T r`` forms before its final
+    Truncate, lags -Nt..Nt-1 (index n' = n + Nt):
+    ``g_full[j][n] = sum_i sum_k G[i,j,k] u_i[n+k]`` with ``u = D_t^T w`` and
+    ``w`` the kept (n >= 0) part of the stage-2 correlation.  Written as
+    ``bltt_transpose`` on arrays extended by Nt leading zeros.  Its second
+    half (n >= 0) is the gradient."""
+    G, P, r = _f64(G), _f64(P), _f64(r)
+    Nt = G.shape[2]
+    pad_lag = lambda F: np.concatenate([F, np.zeros_like(F)], axis=-1)
+    lead = lambda y: np.concatenate([np.zeros_like(y), y], axis=-1)
+    w = bltt_transpose(P, r)
+    u = _stage_dt_t(w, dt_mode, dt)
+    return bltt_transpose(pad_lag(G), lead(u))
+
+
 def rel_l2(a, ref) -> np.ndarray:
     """Relative L2 error per leading index: ||a - ref||_2 / ||ref||_2."""
     a = np.asarray(a, dtype=np.float64)

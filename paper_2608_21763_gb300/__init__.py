@@ -29,7 +29,8 @@ STATUS = {0: "S2W_OK", -1: "S2W_ERR_ARG", -2: "S2W_ERR_OOM", -3: "S2W_ERR_STATE"
 
 # every entry point declared in include/s2w.h
 EXPORTS = ("s2w_default_opts", "s2w_create", "s2w_destroy", "s2w_operator_bytes",
-           "s2w_load_greens", "s2w_load_adjoint", "s2w_waveforms", "s2w_waveforms_noalloc", "s2w_rfft",
+           "s2w_load_greens", "s2w_load_adjoint", "s2w_waveforms", "s2w_waveforms_noalloc",
+           "s2w_adjoint", "s2w_rfft",
            "s2w_irfft", "s2w_profile_enable", "s2w_profile_read", "s2w_sync",
            "s2w_last_error", "s2w_status_string")
 NUM_STAGES = 7
@@ -78,6 +79,7 @@ def lib():
     L.s2w_load_adjoint.argtypes = [V, I, I, P, V]
     L.s2w_waveforms.argtypes = [V, P, I, P, P, V]
     L.s2w_waveforms_noalloc.argtypes = [V, P, P, V]
+    L.s2w_adjoint.argtypes = [V, P, I, P, V]
     L.s2w_rfft.argtypes = [V, P, LL, P, V]
     L.s2w_irfft.argtypes = [V, P, LL, P, V]
     L.s2w_profile_enable.argtypes = [V, I]
@@ -88,7 +90,8 @@ def lib():
     L.s2w_status_string.argtypes = [I]
     L.s2w_status_string.restype = ctypes.c_char_p
     for name in ("s2w_create", "s2w_destroy", "s2w_operator_bytes", "s2w_load_greens",
-                 "s2w_load_adjoint", "s2w_waveforms", "s2w_waveforms_noalloc", "s2w_rfft", "s2w_irfft", "s2w_sync",
+                 "s2w_load_adjoint", "s2w_waveforms", "s2w_waveforms_noalloc", "s2w_adjoint", "s2w_rfft",
+                 "s2w_irfft", "s2w_sync",
                  "s2w_profile_enable", "s2w_profile_read"):
         getattr(L, name).restype = I
     _lib = L
@@ -202,6 +205,20 @@ class Context:
         self._check(lib().s2w_waveforms(self._h, _ptr(slip), int(B), _ptr(q), _ptr(seafloor),
                                         _stream(stream, slip, q, seafloor)))
         return q
+
+    def adjoint(self, r, grad=None, stream=None):
+        """grad[b] = F_G^T D_t^T F_q^T r[b]: the gradient of 0.5 ||q - d||^2
+        with respect to slip when r = q - d.  r: float32 [B][No][Nt]."""
+        B = r.shape[0]
+        assert r.shape[1:] == (self.No, self.Nt), r.shape
+        if grad is None:
+            if isinstance(r, np.ndarray):
+                grad = np.empty((B, self.Ns, self.Nt), np.float32)
+            else:
+                import torch
+                grad = torch.empty((B, self.Ns, self.Nt), dtype=torch.float32, device=r.device)
+        self._check(lib().s2w_adjoint(self._h, _ptr(r), int(B), _ptr(grad), _stream(stream, r, grad)))
+        return grad
 
     def rfft(self, x, X=None, stream=None):
         """Zero-padded real FFT of device rows x [..., Nt] -> complex64 [..., Nt+1]."""

@@ -107,6 +107,10 @@ __global__ void __launch_bounds__(kThreads) k_retransform(const float2* __restri
       for (int n = lane; n < N; n += 32) seafloor[i * N + n] = mb[n];
     if (dt_mode == S2W_DT_NONE) {
       warp_rfft_stage<P>([&](int n) { return n < N ? mb[n] : 0.f; }, zs, tw, lane);
+    } else if (dt_mode == kDtTranspose) {
+      // D_t^T: u[n] = (w[n] - w[n+1]) / dt, w[N] = 0
+      warp_rfft_stage<P>(
+          [&](int n) { return n < N ? (mb[n] - (n + 1 < N ? mb[n + 1] : 0.f)) * inv_dt : 0.f; }, zs, tw, lane);
     } else {
       warp_rfft_stage<P>(
           [&](int n) { return n < N ? (mb[n] - (n > 0 ? mb[n - 1] : 0.f)) * inv_dt : 0.f; }, zs, tw, lane);

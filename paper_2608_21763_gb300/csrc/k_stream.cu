@@ -26,6 +26,7 @@ constexpr int kConsumerWarps = 8;
 constexpr int kStages = 3;
 constexpr int kThreads = 32 * (kConsumerWarps + 1);
 constexpr int kMaxRowLen = 1024;
+constexpr int kStagesT = 2;  // ring depth of the transposed kernel (its reduction buffer needs the room)
 
 template <int EL>
 struct Chunk;  // complex entries per 16-byte chunk and how to unpack them
@@ -201,6 +202,178 @@ __global__ void __launch_bounds__(kThreads, 1) k_stream_dot(const StreamArgs a, 
   }
 }
 
+// Transposed contraction (the adjoint, a correlation with the conjugate
+// spectra):  y[u][c] = sum_{f in unit u} conj(rows[f][c]) * w_f.
+// A unit is `Rc` consecutive rows of one group of G1 rows (chunk u % nchunk
+// of group u / nchunk); the row weight is w[w_base + (g / wa) * wb + (f - g G1)]
+// with g = f / G1, times the FP8 row scale when the rows are FP8.
+// One CTA per unit at a time; the 8 consumer warps accumulate their rows
+// column-wise in registers, then sum across warps through shared memory.
+template <int EL, bool HILO>
+__global__ void __launch_bounds__(kThreads, 1) k_stream_tdot(const StreamTArgs a, int stage_rows) {
+  using CH = Chunk<EL>;
+  constexpr int C = CH::C;
+  constexpr int T = kMaxRowLen / (32 * C);
+  extern __shared__ __align__(128) unsigned char sm[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm);
+  uint64_t* empty = full + kStagesT;
+  unsigned char* buf = sm + 128;
+  const int row_bytes = a.row_len * (16 / C);
+  const int stage_bytes = stage_rows * row_bytes;
+  unsigned char* buf_lo = buf + kStagesT * stage_bytes;
+  float2* red = reinterpret_cast<float2*>(buf + (HILO ? 2 : 1) * kStagesT * stage_bytes);  // [8][row_len]
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStagesT; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(empty + s, kConsumerWarps);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  auto unit_rows = [&](long long u, long long& f0, long long& f1) {
+    const long long g = u / a.nchunk;
+    const long long c = u % a.nchunk;
+    f0 = g * a.G1 + c * a.Rc;
+    f1 = g * a.G1 + min(static_cast<long long>(c + 1) * a.Rc, a.G1);
+  };
+
+  if (warp == kConsumerWarps) {
+    if (lane == 0) {
+      const uint64_t pol = l2_policy_evict_first();
+      int it = 0;
+      bool ok = true;
+      for (long long u = blockIdx.x; u < a.n_units && ok; u += gridDim.x) {
+        long long f0, f1;
+        unit_rows(u, f0, f1);
+        for (long long rs = f0; rs < f1; rs += stage_rows, ++it) {
+          const int s = it % kStagesT;
+          if (it >= kStagesT &&
+              !mbar_wait_bounded(empty + s, ((it / kStagesT) - 1) & 1, a.status, DEV_ERR_TIMEOUT_EMPTY)) {
+            ok = false;
+            break;
+          }
+          const int nr = static_cast<int>(min(static_cast<long long>(stage_rows), f1 - rs));
+          const uint32_t bytes = static_cast<uint32_t>(nr) * row_bytes;
+          mbar_arrive_expect_tx(full + s, HILO ? 2 * bytes : bytes);
+          bulk_g2s(buf + s * stage_bytes, static_cast<const unsigned char*>(a.rows) + rs * row_bytes, bytes,
+                   full + s, pol);
+          if (HILO)
+            bulk_g2s(buf_lo + s * stage_bytes, static_cast<const unsigned char*>(a.rows_lo) + rs * row_bytes, bytes,
+                     full + s, pol);
+        }
+      }
+      for (int kk = (it > kStagesT ? it - kStagesT : 0); kk < it; ++kk)
+        mbar_wait_bounded(full + kk % kStagesT, (kk / kStagesT) & 1, a.status, DEV_ERR_TIMEOUT_FULL);
+    }
+    return;
+  }
+
+  const int nchunk = row_bytes / 16;
+  int it = 0;
+  for (long long u = blockIdx.x; u < a.n_units; u += gridDim.x) {
+    long long f0, f1;
+    unit_rows(u, f0, f1);
+    float2 acc[T][C];
+#pragma unroll
+    for (int t = 0; t < T; ++t)
+#pragma unroll
+      for (int q = 0; q < C; ++q) acc[t][q] = make_float2(0.f, 0.f);
+    bool ok = true;
+    for (long long rs = f0; rs < f1; rs += stage_rows, ++it) {
+      const int s = it % kStagesT;
+      if (!mbar_wait_bounded(full + s, (it / kStagesT) & 1, a.status, DEV_ERR_TIMEOUT_FULL)) {
+        ok = false;
+        break;
+      }
+      const int nr = static_cast<int>(min(static_cast<long long>(stage_rows), f1 - rs));
+      for (int lr = warp; lr < nr; lr += kConsumerWarps) {
+        const long long f = rs + lr;
+        const long long g = f / a.G1;
+        const long long within = f - g * a.G1;
+        float2 w = a.w[a.w_base + (g / a.wa) * a.wb + within];
+        if (EL == EL_FP8) {
+          const float sc = a.scale[g * a.nblk + within / 256];
+          w.x *= sc;
+          w.y *= sc;
+        }
+        const uint4* row = reinterpret_cast<const uint4*>(buf + s * stage_bytes + lr * row_bytes);
+        const uint4* row_lo = reinterpret_cast<const uint4*>(buf_lo + s * stage_bytes + lr * row_bytes);
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+          const int c = lane + 32 * t;
+          if (c < nchunk) {
+            float2 gv[C];
+            CH::unpack(row[c], gv);
+            if (HILO) {
+              float2 gl[C];
+              CH::unpack(row_lo[c], gl);
+#pragma unroll
+              for (int q = 0; q < C; ++q) gv[q] = cadd(gv[q], gl[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < C; ++q) {  // conj(g) * w
+              acc[t][q].x = fmaf(gv[q].x, w.x, fmaf(gv[q].y, w.y, acc[t][q].x));
+              acc[t][q].y = fmaf(gv[q].x, w.y, fmaf(-gv[q].y, w.x, acc[t][q].y));
+            }
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(empty + s);
+    }
+    // cross-warp sum of the unit's column accumulators, in fixed warp order
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+      const int c = lane + 32 * t;
+      if (c < nchunk)
+#pragma unroll
+        for (int q = 0; q < C; ++q) red[warp * a.row_len + c * C + q] = acc[t][q];
+    }
+    asm volatile("bar.sync 1, %0;" ::"r"(kConsumerWarps * 32) : "memory");
+    for (int col = threadIdx.x; col < a.row_len; col += kConsumerWarps * 32) {
+      float2 sum = red[col];
+      for (int w2 = 1; w2 < kConsumerWarps; ++w2) sum = cadd(sum, red[w2 * a.row_len + col]);
+      a.y[u * a.row_len + col] = sum;
+    }
+    // second barrier doubles as a vote: if any consumer warp gave up on a
+    // wait, all of them leave together (none is left behind on this barrier)
+    int any_failed;
+    asm volatile(
+        "{\n\t.reg .pred pin, pout;\n\t"
+        "setp.eq.u32 pin, %1, 0;\n\t"
+        "bar.red.or.pred pout, 1, %2, pin;\n\t"
+        "selp.u32 %0, 1, 0, pout;\n\t}"
+        : "=r"(any_failed)
+        : "r"(ok ? 1u : 0u), "r"(kConsumerWarps * 32)
+        : "memory");
+    if (any_failed) return;
+  }
+}
+
+template <int EL, bool HILO>
+cudaError_t launch_tt(const StreamTArgs& a, int num_sms, cudaStream_t st) {
+  constexpr int C = Chunk<EL>::C;
+  const int row_bytes = a.row_len * (16 / C);
+  const int budget = HILO ? 32 * 1024 : 64 * 1024;
+  int stage_rows = budget / row_bytes;
+  if (stage_rows >= kConsumerWarps) stage_rows -= stage_rows % kConsumerWarps;
+  if (stage_rows < 1) stage_rows = 1;
+  const size_t smem = 128 + static_cast<size_t>(kStagesT) * stage_rows * row_bytes * (HILO ? 2 : 1) +
+                      sizeof(float2) * kConsumerWarps * a.row_len;
+  cudaError_t e = cudaFuncSetAttribute(k_stream_tdot<EL, HILO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  long long grid = num_sms;
+  if (grid > a.n_units) grid = a.n_units;
+  if (grid < 1) grid = 1;
+  k_stream_tdot<EL, HILO><<<static_cast<unsigned>(grid), kThreads, smem, st>>>(a, stage_rows);
+  return cudaGetLastError();
+}
+
 template <int EL, bool HILO>
 cudaError_t launch_t(const StreamArgs& a, int num_sms, cudaStream_t st) {
   constexpr int C = Chunk<EL>::C;
@@ -230,6 +403,23 @@ cudaError_t launch_stream_dot(const StreamArgs& a, int num_sms, cudaStream_t st)
     case EL_BF16: return launch_t<EL_BF16, false>(a, num_sms, st);
     case EL_BF16_HILO: return launch_t<EL_BF16, true>(a, num_sms, st);
     case EL_FP8: return launch_t<EL_FP8, false>(a, num_sms, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace s2w
+
+namespace s2w {
+
+cudaError_t launch_stream_tdot(const StreamTArgs& a, int num_sms, cudaStream_t st) {
+  if (a.n_units <= 0) return cudaSuccess;
+  if (a.row_len <= 0 || a.row_len > kMaxRowLen || (a.row_len % 8) != 0 || a.Rc < 1 || a.nchunk < 1)
+    return cudaErrorInvalidValue;
+  switch (a.el) {
+    case EL_FP32: return launch_tt<EL_FP32, false>(a, num_sms, st);
+    case EL_BF16: return launch_tt<EL_BF16, false>(a, num_sms, st);
+    case EL_BF16_HILO: return launch_tt<EL_BF16, true>(a, num_sms, st);
+    case EL_FP8: return launch_tt<EL_FP8, false>(a, num_sms, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -44,6 +44,10 @@ struct s2w_ctx {
   float2* ws_part = nullptr;
   float* ws_q = nullptr;
   float* ws_seafloor = nullptr;
+  float2* ws_rhat = nullptr;   // adjoint: residual spectra [l][b][No]
+  float2* ws_gpart = nullptr;  // adjoint: stage-1 chunk partials [l][chunk][Ns_pad]
+  int adj_rc = 512;            // adjoint: grid rows per stage-1 chunk
+  int adj_nchunk = 1;
   int* d_status = nullptr;
   // tensor-core engine (BF16 storage, rupture batches)
   bool tc_on = false;
@@ -183,7 +187,7 @@ void free_all(s2w_ctx* c) {
   c->pending.clear();
   c->ev_free.clear();
   void* ps[] = {c->G, c->G_lo, c->G_scale, c->P, c->tw, c->ws_slip, c->ws_shat, c->ws_mhat,
-                c->ws_vhat, c->ws_part, c->ws_q, c->ws_seafloor, c->d_status, c->tc_bp1,
+                c->ws_vhat, c->ws_part, c->ws_q, c->ws_seafloor, c->d_status, c->tc_bp1, c->ws_rhat, c->ws_gpart,
                 c->tc_mhat, c->tc_vhat, c->tc_part, c->tc_p2, c->tc_T};
   for (void* p : ps)
     if (p) cudaFree(p);
@@ -448,6 +452,10 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
   if ((e = dalloc(&ctx->ws_seafloor, sizeof(float) * static_cast<size_t>(Ng) * Nt)) != cudaSuccess)
     return bad(e, "seafloor workspace");
   if ((e = dalloc(&ctx->d_status, sizeof(int))) != cudaSuccess) return bad(e, "status word");
+  ctx->adj_nchunk = static_cast<int>((Ng + ctx->adj_rc - 1) / ctx->adj_rc);
+  if ((e = dalloc(&ctx->ws_rhat, sizeof(float2) * Nb * B * No)) != cudaSuccess) return bad(e, "residual spectra");
+  if ((e = dalloc(&ctx->ws_gpart, sizeof(float2) * Nb * ctx->adj_nchunk * ctx->Ns_pad)) != cudaSuccess)
+    return bad(e, "adjoint partials");
   ctx->tc_on = o.prec_g == S2W_PREC_BF16 && 2 * No <= 256 &&
                (o.engine == S2W_ENGINE_TENSOR || (o.engine == S2W_ENGINE_AUTO && o.max_batch >= 2));
   if (ctx->tc_on) {
@@ -711,6 +719,92 @@ int s2w_waveforms(s2w_ctx* ctx, const float* slip, int B, float* q, float* seafl
     CK(cudaMemcpyAsync(q, q_d, sizeof(float) * B * No * Nt, cudaMemcpyDeviceToHost, st));
   }
   if (kq == 0 || (seafloor && kf == 0)) CK(cudaStreamSynchronize(st));
+  return S2W_OK;
+}
+
+int s2w_adjoint(s2w_ctx* ctx, const float* r, int B, float* grad_s, void* stream) {
+  if (!ctx) return S2W_ERR_ARG;
+  if (B < 0 || B > ctx->opts.max_batch)
+    return fail(ctx, S2W_ERR_ARG, "adjoint: B=%d outside [0, max_batch=%d]", B, ctx->opts.max_batch);
+  if (B == 0) return S2W_OK;
+  if (!r || !grad_s) return fail(ctx, S2W_ERR_ARG, "adjoint: r and grad_s must not be NULL");
+  if (ctx->g_count != ctx->Ng || ctx->p_count != ctx->Ng)
+    return fail(ctx, S2W_ERR_STATE, "adjoint: operators not fully loaded");
+  DeviceGuard guard(ctx->device);
+  const int kr = pointer_kind(r, ctx->device), kg = pointer_kind(grad_s, ctx->device);
+  if (kr < 0 || kg < 0) return fail(ctx, S2W_ERR_ARG, "adjoint: pointer on another device");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const long long Ns = ctx->Ns, Ng = ctx->Ng, No = ctx->No, Nt = ctx->Nt, Nb = ctx->Nb, Ns_pad = ctx->Ns_pad;
+  const float* r_d = r;
+  if (kr == 0) {
+    StageTimer t(ctx, 5, st, 0);
+    CK(cudaMemcpyAsync(ctx->ws_q, r, sizeof(float) * B * No * Nt, cudaMemcpyHostToDevice, st));
+    r_d = ctx->ws_q;
+  }
+  float* g_d = kg == 1 ? grad_s : ctx->ws_slip;
+  {
+    StageTimer t(ctx, 0, st);
+    CK(launch_rfft_rows(r_d, B * No, static_cast<int>(Nt), static_cast<int>(Nt), ctx->tw, ctx->ws_rhat, B * No, No,
+                        No, st));
+  }
+  const int dt_t = ctx->opts.dt_mode == S2W_DT_NONE ? S2W_DT_NONE : kDtTranspose;
+  for (int b = 0; b < B; ++b) {
+    {  // stage-2 adjoint: what_l[i] = sum_o conj(Phat_l[o][i]) rhat_l[o]
+      StageTimer t(ctx, 3, st);
+      StreamTArgs a{};
+      a.rows = ctx->P;
+      a.el = ctx->opts.prec_p;
+      a.row_len = ctx->RL;
+      a.n_units = Nb * ctx->nseg;
+      a.G1 = No;
+      a.Rc = static_cast<int>(No);
+      a.nchunk = 1;
+      a.w = ctx->ws_rhat;
+      a.w_base = static_cast<long long>(b) * No;
+      a.wa = ctx->nseg;
+      a.wb = static_cast<long long>(B) * No;
+      a.y = ctx->ws_vhat;
+      a.status = ctx->d_status;
+      CK(launch_stream_tdot(a, ctx->num_sms, st));
+    }
+    {  // IFFT + Truncate, D_t^T, ZeroPad + FFT
+      StageTimer t(ctx, 2, st);
+      CK(launch_retransform(ctx->ws_vhat, Ng, static_cast<long long>(ctx->nseg) * ctx->RL, static_cast<int>(Nt),
+                            ctx->tw, static_cast<float>(1.0 / ctx->opts.dt), dt_t, ctx->ws_mhat, Ng, nullptr, st));
+    }
+    {  // stage-1 adjoint: ghat_l[j] = sum_i conj(Ghat_l[i][j]) uhat_l[i], in row chunks
+      StageTimer t(ctx, 1, st);
+      StreamTArgs a{};
+      a.rows = ctx->G;
+      a.rows_lo = ctx->G_lo;
+      a.el = ctx->opts.prec_g;
+      a.row_len = static_cast<int>(Ns_pad);
+      a.n_units = Nb * ctx->adj_nchunk;
+      a.G1 = Ng;
+      a.Rc = ctx->adj_rc;
+      a.nchunk = ctx->adj_nchunk;
+      a.w = ctx->ws_mhat;
+      a.w_base = 0;
+      a.wa = 1;
+      a.wb = Ng;
+      a.scale = ctx->G_scale;
+      a.nblk = ctx->nblk;
+      a.y = ctx->ws_gpart;
+      a.status = ctx->d_status;
+      CK(launch_stream_tdot(a, ctx->num_sms, st));
+    }
+    {  // chunk reduction + IFFT + Truncate -> grad_s[b]
+      StageTimer t(ctx, 4, st);
+      CK(launch_reduce_irfft(ctx->ws_gpart, 1, static_cast<int>(Ns), ctx->adj_nchunk, static_cast<int>(Nt), 0,
+                             static_cast<long long>(ctx->adj_nchunk) * Ns_pad, Ns_pad, ctx->tw,
+                             g_d + static_cast<long long>(b) * Ns * Nt, st));
+    }
+  }
+  if (kg == 0) {
+    StageTimer t(ctx, 5, st, 0);
+    CK(cudaMemcpyAsync(grad_s, g_d, sizeof(float) * B * Ns * Nt, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  }
   return S2W_OK;
 }
 

@@ -23,6 +23,10 @@ enum : int {
 // Wall-clock bound on every spin-wait inside a kernel (nanoseconds).
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;
 
+// Retransform stencil code for the adjoint (beside S2W_DT_BACKWARD / NONE):
+// the transpose of the backward difference, u[n] = (w[n] - w[n+1]) / dt.
+constexpr int kDtTranspose = 2;
+
 // Storage codes of the resident spectra (same values as S2W_PREC_*).
 enum Elem : int { EL_FP32 = 0, EL_BF16 = 1, EL_BF16_HILO = 2, EL_FP8 = 3 };
 
@@ -163,6 +167,27 @@ struct StreamArgs {
   int* status;
 };
 cudaError_t launch_stream_dot(const StreamArgs& a, int num_sms, cudaStream_t st);
+
+// k_stream.cu, transposed: y[u][c] = sum_{f in unit u} conj(rows[f][c]) w_f,
+// unit u = chunk (u % nchunk) of Rc rows of group (u / nchunk) of G1 rows,
+// w_f = w[w_base + (g / wa) * wb + (f - g G1)], g = f / G1 (times the FP8
+// scale[g * nblk + (f - g G1) / 256] for FP8 rows).
+struct StreamTArgs {
+  const void* rows;
+  const void* rows_lo;
+  int el;
+  int row_len;
+  long long n_units;
+  long long G1;
+  int Rc, nchunk;
+  const float2* w;
+  long long w_base, wa, wb;
+  const float* scale;
+  int nblk;
+  float2* y;
+  int* status;
+};
+cudaError_t launch_stream_tdot(const StreamTArgs& a, int num_sms, cudaStream_t st);
 
 // k_tc.cu: D = A B^T per bin on tensor cores (see the file comment).
 struct TcArgs {

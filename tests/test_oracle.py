@@ -281,3 +281,24 @@ def test_fft_window_head_is_q_and_tail_is_linear_convolution(small):
             # full linear convolution has 2 Nt - 1 samples; the last one is 0
             ref[o, :2 * Nt - 1] += np.convolve(P[o, i], v[i])
     assert np.allclose(qw[0], ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+def test_fft_window_adjoint_tail_is_gradient_and_full_correlation(small):
+    """oracle.fft_window_adjoint: lags n >= 0 are F_G^T D_t^T F_q^T r; the
+    whole window is the full cross-correlation (numpy.correlate) of the
+    Green's functions with u = D_t^T F_q^T r."""
+    G, P, _ = small
+    Nt = G.shape[2]
+    r = np.random.default_rng(21).standard_normal((1, P.shape[0], Nt))
+    gw = oracle.fft_window_adjoint(G, P, r)
+    assert gw.shape == (1, G.shape[1], 2 * Nt)
+    g = oracle.bltt_transpose(G, oracle.dt_transpose(oracle.bltt_transpose(P, r)))
+    assert np.allclose(gw[..., Nt:], g, rtol=0, atol=1e-13 * np.abs(g).max())
+    u = oracle.dt_transpose(oracle.bltt_transpose(P, r))[0]
+    ref = np.zeros((G.shape[1], 2 * Nt))
+    for j in range(G.shape[1]):
+        for i in range(G.shape[0]):
+            # c[m] = sum_k G[k] u[m + k], m = -(Nt-1)..Nt-1  ->  index m + Nt
+            c = np.correlate(u[i], G[i, j], mode="full")  # lags -(Nt-1)..(Nt-1)
+            ref[j, 1:] += c
+    assert np.allclose(gw[0], ref, rtol=0, atol=1e-12 * np.abs(ref).max())
