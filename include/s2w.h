@@ -143,6 +143,14 @@ int s2w_waveforms(s2w_ctx *ctx, const float *slip, int B, float *q, float *seafl
  * storage precision.  Pointer and stream rules as s2w_waveforms. */
 int s2w_adjoint(s2w_ctx *ctx, const float *r, int B, float *grad_s, void *stream);
 
+/* Gradient of the waveform misfit L_b = 0.5 ||q(slip[b]) - d[b]||^2 for B
+ * ruptures: forward waveforms, residual r = q - d, then s2w_adjoint(r).
+ *   slip [B][Ns][Nt], d [B][No][Nt] (inputs); grad_s [B][Ns][Nt] (output);
+ *   loss [B] (output, may be NULL; same memory kind as grad_s).
+ * Pointer and stream rules as s2w_waveforms. */
+int s2w_misfit_gradient(s2w_ctx *ctx, const float *slip, const float *d, int B, float *grad_s, float *loss,
+                        void *stream);
+
 /* Waveforms for ONE rupture without allocating any memory (the paper has no
  * counterpart; this serves callers that cannot let a library allocate device
  * memory: applications whose device memory all comes from their own pool,

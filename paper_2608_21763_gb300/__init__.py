@@ -30,7 +30,7 @@ STATUS = {0: "S2W_OK", -1: "S2W_ERR_ARG", -2: "S2W_ERR_OOM", -3: "S2W_ERR_STATE"
 # every entry point declared in include/s2w.h
 EXPORTS = ("s2w_default_opts", "s2w_create", "s2w_destroy", "s2w_operator_bytes",
            "s2w_load_greens", "s2w_load_adjoint", "s2w_waveforms", "s2w_waveforms_noalloc",
-           "s2w_adjoint", "s2w_rfft",
+           "s2w_adjoint", "s2w_misfit_gradient", "s2w_rfft",
            "s2w_irfft", "s2w_profile_enable", "s2w_profile_read", "s2w_sync",
            "s2w_last_error", "s2w_status_string")
 NUM_STAGES = 7
@@ -80,6 +80,7 @@ def lib():
     L.s2w_waveforms.argtypes = [V, P, I, P, P, V]
     L.s2w_waveforms_noalloc.argtypes = [V, P, P, V]
     L.s2w_adjoint.argtypes = [V, P, I, P, V]
+    L.s2w_misfit_gradient.argtypes = [V, P, P, I, P, P, V]
     L.s2w_rfft.argtypes = [V, P, LL, P, V]
     L.s2w_irfft.argtypes = [V, P, LL, P, V]
     L.s2w_profile_enable.argtypes = [V, I]
@@ -90,7 +91,7 @@ def lib():
     L.s2w_status_string.argtypes = [I]
     L.s2w_status_string.restype = ctypes.c_char_p
     for name in ("s2w_create", "s2w_destroy", "s2w_operator_bytes", "s2w_load_greens",
-                 "s2w_load_adjoint", "s2w_waveforms", "s2w_waveforms_noalloc", "s2w_adjoint", "s2w_rfft",
+                 "s2w_load_adjoint", "s2w_waveforms", "s2w_waveforms_noalloc", "s2w_adjoint", "s2w_misfit_gradient", "s2w_rfft",
                  "s2w_irfft", "s2w_sync",
                  "s2w_profile_enable", "s2w_profile_read"):
         getattr(L, name).restype = I
@@ -219,6 +220,24 @@ class Context:
                 grad = torch.empty((B, self.Ns, self.Nt), dtype=torch.float32, device=r.device)
         self._check(lib().s2w_adjoint(self._h, _ptr(r), int(B), _ptr(grad), _stream(stream, r, grad)))
         return grad
+
+    def misfit_gradient(self, slip, d, grad=None, loss=None, stream=None):
+        """Gradient of 0.5 ||q(slip[b]) - d[b]||^2 per rupture; returns
+        (grad [B][Ns][Nt], loss [B])."""
+        B = slip.shape[0]
+        assert slip.shape[1:] == (self.Ns, self.Nt) and d.shape == (B, self.No, self.Nt)
+        if isinstance(slip, np.ndarray):
+            grad = np.empty((B, self.Ns, self.Nt), np.float32) if grad is None else grad
+            loss = np.empty((B,), np.float32) if loss is None else loss
+        else:
+            import torch
+            if grad is None:
+                grad = torch.empty((B, self.Ns, self.Nt), dtype=torch.float32, device=slip.device)
+            if loss is None:
+                loss = torch.empty((B,), dtype=torch.float32, device=grad.device)
+        self._check(lib().s2w_misfit_gradient(self._h, _ptr(slip), _ptr(d), int(B), _ptr(grad), _ptr(loss),
+                                              _stream(stream, slip, d, grad)))
+        return grad, loss
 
     def rfft(self, x, X=None, stream=None):
         """Zero-padded real FFT of device rows x [..., Nt] -> complex64 [..., Nt+1]."""

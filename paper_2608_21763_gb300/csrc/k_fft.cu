@@ -249,6 +249,28 @@ __global__ void k_fp8_quantize(const float2* __restrict__ spec, int Nb, long lon
   }
 }
 
+// Residual and misfit: r = q - d in place of q, loss[b] = 0.5 sum r^2 over the
+// rupture's No x Nt samples (one CTA per rupture, fixed summation order).
+__global__ void __launch_bounds__(kThreads) k_residual(float* __restrict__ q, const float* __restrict__ d,
+                                                       long long n_per_b, float* __restrict__ loss) {
+  const long long base = static_cast<long long>(blockIdx.x) * n_per_b;
+  float acc = 0.f;
+  for (long long e = threadIdx.x; e < n_per_b; e += kThreads) {
+    const float r = q[base + e] - d[base + e];
+    q[base + e] = r;
+    acc = fmaf(r, r, acc);
+  }
+  __shared__ float red[kWarps];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0 && loss != nullptr) {
+    float t = 0.f;
+    for (int w = 0; w < kWarps; ++w) t += red[w];
+    loss[blockIdx.x] = 0.5f * t;
+  }
+}
+
 int grid_for(long long n, int threads) {
   long long g = (n + threads - 1) / threads;
   if (g > 152LL * 32) g = 152LL * 32;
@@ -273,6 +295,12 @@ size_t smem_retransform() {
     case 512: { constexpr int P = 16; __VA_ARGS__; } break;   \
     default: return cudaErrorInvalidValue;                    \
   }
+
+cudaError_t launch_residual(float* q, const float* d, int B, long long n_per_b, float* loss, cudaStream_t st) {
+  if (B <= 0) return cudaSuccess;
+  k_residual<<<B, kThreads, 0, st>>>(q, d, n_per_b, loss);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_twiddles(float2* tw, int L, cudaStream_t st) {
   k_twiddles<<<(L + 255) / 256, 256, 0, st>>>(tw, L);

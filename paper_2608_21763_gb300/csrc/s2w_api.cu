@@ -45,6 +45,9 @@ struct s2w_ctx {
   float* ws_q = nullptr;
   float* ws_seafloor = nullptr;
   float2* ws_rhat = nullptr;   // adjoint: residual spectra [l][b][No]
+  float* ws_resid = nullptr;   // misfit gradient: q then r = q - d, [b][No][Nt]
+  float* ws_d = nullptr;       // misfit gradient: staged targets, [b][No][Nt]
+  float* ws_loss = nullptr;    // misfit gradient: per-rupture loss
   float2* ws_gpart = nullptr;  // adjoint: stage-1 chunk partials [l][chunk][Ns_pad]
   int adj_rc = 512;            // adjoint: grid rows per stage-1 chunk
   int adj_nchunk = 1;
@@ -187,7 +190,7 @@ void free_all(s2w_ctx* c) {
   c->pending.clear();
   c->ev_free.clear();
   void* ps[] = {c->G, c->G_lo, c->G_scale, c->P, c->tw, c->ws_slip, c->ws_shat, c->ws_mhat,
-                c->ws_vhat, c->ws_part, c->ws_q, c->ws_seafloor, c->d_status, c->tc_bp1, c->ws_rhat, c->ws_gpart,
+                c->ws_vhat, c->ws_part, c->ws_q, c->ws_seafloor, c->d_status, c->tc_bp1, c->ws_rhat, c->ws_gpart, c->ws_resid, c->ws_d, c->ws_loss,
                 c->tc_mhat, c->tc_vhat, c->tc_part, c->tc_p2, c->tc_T};
   for (void* p : ps)
     if (p) cudaFree(p);
@@ -454,6 +457,9 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
   if ((e = dalloc(&ctx->d_status, sizeof(int))) != cudaSuccess) return bad(e, "status word");
   ctx->adj_nchunk = static_cast<int>((Ng + ctx->adj_rc - 1) / ctx->adj_rc);
   if ((e = dalloc(&ctx->ws_rhat, sizeof(float2) * Nb * B * No)) != cudaSuccess) return bad(e, "residual spectra");
+  if ((e = dalloc(&ctx->ws_resid, sizeof(float) * B * No * Nt)) != cudaSuccess) return bad(e, "residuals");
+  if ((e = dalloc(&ctx->ws_d, sizeof(float) * B * No * Nt)) != cudaSuccess) return bad(e, "targets");
+  if ((e = dalloc(&ctx->ws_loss, sizeof(float) * B)) != cudaSuccess) return bad(e, "losses");
   if ((e = dalloc(&ctx->ws_gpart, sizeof(float2) * Nb * ctx->adj_nchunk * ctx->Ns_pad)) != cudaSuccess)
     return bad(e, "adjoint partials");
   ctx->tc_on = o.prec_g == S2W_PREC_BF16 && 2 * No <= 256 &&
@@ -803,6 +809,40 @@ int s2w_adjoint(s2w_ctx* ctx, const float* r, int B, float* grad_s, void* stream
   if (kg == 0) {
     StageTimer t(ctx, 5, st, 0);
     CK(cudaMemcpyAsync(grad_s, g_d, sizeof(float) * B * Ns * Nt, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  return S2W_OK;
+}
+
+int s2w_misfit_gradient(s2w_ctx* ctx, const float* slip, const float* d, int B, float* grad_s, float* loss,
+                        void* stream) {
+  if (!ctx) return S2W_ERR_ARG;
+  if (B < 0 || B > ctx->opts.max_batch)
+    return fail(ctx, S2W_ERR_ARG, "misfit_gradient: B=%d outside [0, max_batch=%d]", B, ctx->opts.max_batch);
+  if (B == 0) return S2W_OK;
+  if (!slip || !d || !grad_s) return fail(ctx, S2W_ERR_ARG, "misfit_gradient: slip, d, grad_s must not be NULL");
+  DeviceGuard guard(ctx->device);
+  const int kd = pointer_kind(d, ctx->device), kg = pointer_kind(grad_s, ctx->device);
+  const int kl = loss ? pointer_kind(loss, ctx->device) : kg;
+  if (kd < 0 || kg < 0 || kl < 0) return fail(ctx, S2W_ERR_ARG, "misfit_gradient: pointer on another device");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const long long n_per_b = static_cast<long long>(ctx->No) * ctx->Nt;
+  int rc = s2w_waveforms(ctx, slip, B, ctx->ws_resid, nullptr, stream);
+  if (rc != S2W_OK) return rc;
+  const float* d_d = d;
+  if (kd == 0) {
+    StageTimer t(ctx, 5, st, 0);
+    CK(cudaMemcpyAsync(ctx->ws_d, d, sizeof(float) * B * n_per_b, cudaMemcpyHostToDevice, st));
+    d_d = ctx->ws_d;
+  }
+  {
+    StageTimer t(ctx, 4, st);
+    CK(launch_residual(ctx->ws_resid, d_d, B, n_per_b, loss && kl == 1 ? loss : ctx->ws_loss, st));
+  }
+  rc = s2w_adjoint(ctx, ctx->ws_resid, B, grad_s, stream);
+  if (rc != S2W_OK) return rc;
+  if (loss && kl == 0) {
+    CK(cudaMemcpyAsync(loss, ctx->ws_loss, sizeof(float) * B, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
   }
   return S2W_OK;

@@ -142,6 +142,8 @@ cudaError_t launch_retransform(const float2* mhat, long long Ng, long long ld_m,
 // q[b][o][n] from partials: Qhat[l] = sum_{s < nseg} part[b*s_b + l*s_l + s*s_s + o].
 cudaError_t launch_reduce_irfft(const float2* part, int B, int No, int nseg, int Nt, long long s_b, long long s_l,
                                 long long s_s, const float2* tw, float* q, cudaStream_t st);
+// r = q - d in place (B blocks of n_per_b floats); loss[b] = 0.5 sum r^2 (optional).
+cudaError_t launch_residual(float* q, const float* d, int B, long long n_per_b, float* loss, cudaStream_t st);
 cudaError_t launch_store_blocks(const float2* src, int Nb, long long n_per_l, int el, void* dst, void* dst_lo,
                                 long long ld_dst_l, long long dst_off, cudaStream_t st);
 cudaError_t launch_store_adjoint(const float2* src, int Nb, int No, long long nc, long long c0, int RL, int nseg,

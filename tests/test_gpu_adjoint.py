@@ -162,3 +162,20 @@ def test_adjoint_plain_workload_full_size():
     print(f"adjoint plain full size: rel-L2 {err}, error / window norm {win}")
     assert win <= 1e-5 and err <= 1e-5 * max(1.0, np.linalg.norm(g_win) / np.linalg.norm(g_ref)), (err, win)
     ctx.sync()
+
+
+def test_misfit_gradient_entry_point(tiny_ops):
+    """s2w_misfit_gradient (forward, residual, adjoint in the library)
+    against the FP64 oracle misfit and gradient."""
+    wl, geom, G, P = tiny_ops
+    s = wl.slip(geom, B=3)
+    d = synth.random_waveforms(3, wl.No, wl.Nt, seed=12)
+    ctx = make_context(s2w, geom, wl.Nt, max_batch=3)
+    g, loss = ctx.misfit_gradient(torch.tensor(s, dtype=torch.float32, device="cuda"),
+                                  torch.tensor(d, dtype=torch.float32, device="cuda"))
+    loss_ref, g_ref = oracle.gradient(G, P, s, d)
+    assert np.allclose(loss.cpu().numpy(), loss_ref, rtol=1e-5)
+    r = oracle.waveforms(G, P, s) - d
+    adjoint_bars(g.cpu().numpy(), G, P, r, 2e-5, "misfit gradient")
+    g_h, loss_h = ctx.misfit_gradient(s.astype(np.float32), d.astype(np.float32))
+    assert np.array_equal(g_h, g.cpu().numpy()) and np.array_equal(loss_h, loss.cpu().numpy())
