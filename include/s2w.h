@@ -77,8 +77,10 @@ typedef enum { S2W_DT_BACKWARD = 0, S2W_DT_NONE = 1 } s2w_dt_mode;
  * TENSOR: tcgen05 tensor-core GEMMs over the whole rupture batch (one pass
  * over the spectra per batch of up to 256 ruptures); needs prec_g = BF16;
  * the activations (slip and velocity spectra) are rounded to BF16 and the
- * stage-2 operator is kept in BF16.  AUTO: TENSOR for calls with B >= 2 when
- * prec_g is BF16, STREAM otherwise. */
+ * stage-2 operator is kept in BF16; Nt <= 256.  A call that asks for the
+ * seafloor field runs on the stream kernels.  AUTO: TENSOR for calls with
+ * B >= 2 when prec_g is BF16, STREAM otherwise.  The stream engine handles
+ * the ruptures of a call in groups of up to 64. */
 typedef enum { S2W_ENGINE_AUTO = 0, S2W_ENGINE_STREAM = 1, S2W_ENGINE_TENSOR = 2 } s2w_engine;
 
 typedef struct {

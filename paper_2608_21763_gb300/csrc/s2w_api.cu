@@ -137,6 +137,10 @@ int pointer_kind(const void* p, int device) {
   return 0;
 }
 
+// The stream engine handles ruptures in groups of at most this many (its
+// per-call workspaces are sized for one group).
+constexpr int kStreamGroup = 64;
+
 bool supported_nt(int Nt) { return Nt == 32 || Nt == 64 || Nt == 128 || Nt == 256 || Nt == 512; }
 
 long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
@@ -244,7 +248,7 @@ std::vector<__nv_bfloat16> retransform_matrix(int Nt, int dt_mode, double dt) {
 //   rfft slip -> pack stage-1 B operand -> tcgen05 stage 1 -> mhat[l][b][Ng]
 //   -> retransform (BF16 velocity spectra, the stage-2 A operand)
 //   -> tcgen05 stage 2 over grid chunks -> partials -> reduce + IFFT -> q.
-int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, float* seafloor, cudaStream_t st) {
+int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaStream_t st) {
   const long long Ns = ctx->Ns, Ng = ctx->Ng, No = ctx->No, Nt = ctx->Nt, Nb = ctx->Nb, Ns_pad = ctx->Ns_pad;
   const int K1 = static_cast<int>(2 * Ns_pad);
   const long long K2 = 2 * ctx->Ng_pad2;
@@ -280,10 +284,9 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, float
       a.tmem_cols = N1 <= 32 ? 32 : (N1 <= 64 ? 64 : (N1 <= 128 ? 128 : (N1 <= 256 ? 256 : 512)));
       a.epi = 0;
       a.T = Bs;
-      a.out = ctx->tc_mhat;
+      a.out = nullptr;
       // the GEMM retransform rounds the seafloor spectra to BF16 anyway
-      const bool gemm_rt = seafloor == nullptr && ctx->tc_T != nullptr;
-      a.out_bf = gemm_rt ? reinterpret_cast<__nv_bfloat162*>(ctx->tc_mhat) : nullptr;
+      a.out_bf = reinterpret_cast<__nv_bfloat162*>(ctx->tc_mhat);
       a.ld_l = static_cast<long long>(Bs) * Ng;
       a.ld_t = Ng;
       a.status = ctx->d_status;
@@ -291,27 +294,19 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, float
     }
     {
       StageTimer t(ctx, 2, st);
-      if (seafloor == nullptr && ctx->tc_T != nullptr) {
-        TcRtArgs r{};
-        r.mhat = ctx->tc_mhat;
-        r.mhat_bf = reinterpret_cast<const __nv_bfloat162*>(ctx->tc_mhat);
-        r.ld_l = static_cast<long long>(Bs) * Ng;
-        r.ld_b = Ng;
-        r.Ng = static_cast<int>(Ng);
-        r.Bs = Bs;
-        r.Nt = static_cast<int>(Nt);
-        r.vhat = static_cast<__nv_bfloat162*>(ctx->tc_vhat);
-        r.vld_l = static_cast<long long>(ctx->tc_bsub) * ctx->Ng_pad2;
-        r.vld_b = ctx->Ng_pad2;
-        r.status = ctx->d_status;
-        CK(launch_tc_retransform(ctx->tc_tmT, r, ctx->num_sms, st));
-      } else {
-        float* sf = seafloor ? seafloor + static_cast<long long>(b0) * Ng * Nt : nullptr;
-        CK(launch_retransform(ctx->tc_mhat, Ng, static_cast<long long>(Bs) * Ng, static_cast<int>(Nt), ctx->tw,
-                              static_cast<float>(1.0 / ctx->opts.dt), ctx->opts.dt_mode, nullptr,
-                              static_cast<long long>(ctx->tc_bsub) * ctx->Ng_pad2, sf, st, Bs, Ng, ctx->Ng_pad2,
-                              static_cast<__nv_bfloat162*>(ctx->tc_vhat)));
-      }
+      TcRtArgs r{};
+      r.mhat = nullptr;
+      r.mhat_bf = reinterpret_cast<const __nv_bfloat162*>(ctx->tc_mhat);
+      r.ld_l = static_cast<long long>(Bs) * Ng;
+      r.ld_b = Ng;
+      r.Ng = static_cast<int>(Ng);
+      r.Bs = Bs;
+      r.Nt = static_cast<int>(Nt);
+      r.vhat = static_cast<__nv_bfloat162*>(ctx->tc_vhat);
+      r.vld_l = static_cast<long long>(ctx->tc_bsub) * ctx->Ng_pad2;
+      r.vld_b = ctx->Ng_pad2;
+      r.status = ctx->d_status;
+      CK(launch_tc_retransform(ctx->tc_tmT, r, ctx->num_sms, st));
     }
     {
       StageTimer t(ctx, 3, st);
@@ -444,12 +439,14 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
   if ((e = dalloc(&ctx->P, ctx->p_bytes)) != cudaSuccess) return bad(e, "Phat");
   if ((e = dalloc(&ctx->tw, sizeof(float2) * ctx->L)) != cudaSuccess) return bad(e, "twiddles");
   if ((e = dalloc(&ctx->ws_slip, sizeof(float) * B * Ns * Nt)) != cudaSuccess) return bad(e, "slip workspace");
-  if ((e = dalloc(&ctx->ws_shat, sizeof(float2) * Nb * B * ctx->Ns_pad)) != cudaSuccess)
+  const long long Bsh = std::min<long long>(B, 256);  // slip spectra serve one group / sub-batch at a time
+  if ((e = dalloc(&ctx->ws_shat, sizeof(float2) * Nb * Bsh * ctx->Ns_pad)) != cudaSuccess)
     return bad(e, "slip spectra");
   if ((e = dalloc(&ctx->ws_mhat, sizeof(float2) * Nb * Ng)) != cudaSuccess) return bad(e, "seafloor spectra");
   if ((e = dalloc(&ctx->ws_vhat, sizeof(float2) * Nb * ctx->nseg * ctx->RL)) != cudaSuccess)
     return bad(e, "velocity spectra");
-  if ((e = dalloc(&ctx->ws_part, sizeof(float2) * B * Nb * ctx->nseg * No)) != cudaSuccess)
+  if ((e = dalloc(&ctx->ws_part, sizeof(float2) * std::min<long long>(B, kStreamGroup) * Nb * ctx->nseg * No)) !=
+      cudaSuccess)
     return bad(e, "stage-2 partials");
   if ((e = dalloc(&ctx->ws_q, sizeof(float) * B * No * Nt)) != cudaSuccess) return bad(e, "waveform workspace");
   if ((e = dalloc(&ctx->ws_seafloor, sizeof(float) * static_cast<size_t>(Ng) * Nt)) != cudaSuccess)
@@ -475,7 +472,7 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
     const long long bs = ctx->tc_bsub;
     if ((e = dalloc(&ctx->tc_bp1, 2ull * Nb * ctx->tc_n1max * 2 * ctx->Ns_pad)) != cudaSuccess)
       return bad(e, "tensor stage-1 operand");
-    if ((e = dalloc(&ctx->tc_mhat, sizeof(float2) * Nb * bs * Ng)) != cudaSuccess)
+    if ((e = dalloc(&ctx->tc_mhat, sizeof(__nv_bfloat162) * Nb * bs * Ng)) != cudaSuccess)
       return bad(e, "tensor seafloor spectra");
     if ((e = dalloc(&ctx->tc_vhat, 4ull * Nb * bs * ctx->Ng_pad2)) != cudaSuccess)
       return bad(e, "tensor velocity spectra");
@@ -648,10 +645,10 @@ int s2w_waveforms(s2w_ctx* ctx, const float* slip, int B, float* q, float* seafl
     slip_d = ctx->ws_slip;
   }
   float* q_d = kq == 1 ? q : ctx->ws_q;
-  const bool use_tc = ctx->tc_on && (seafloor == nullptr || kf == 1) &&
+  const bool use_tc = ctx->tc_on && seafloor == nullptr && ctx->tc_T != nullptr &&
                       (ctx->opts.engine == S2W_ENGINE_TENSOR || B >= 2);
   if (use_tc) {
-    int rc = waveforms_tensor(ctx, slip_d, B, q_d, seafloor, st);
+    int rc = waveforms_tensor(ctx, slip_d, B, q_d, st);
     if (rc != S2W_OK) return rc;
     if (kq == 0) {
       StageTimer t(ctx, 5, st, 0);
@@ -660,65 +657,70 @@ int s2w_waveforms(s2w_ctx* ctx, const float* slip, int B, float* q, float* seafl
     }
     return S2W_OK;
   }
-  // K1
-  {
-  StageTimer t(ctx, 0, st);
-  CK(launch_rfft_rows(slip_d, B * Ns, static_cast<int>(Nt), static_cast<int>(Nt), ctx->tw, ctx->ws_shat,
-                      B * Ns_pad, Ns, Ns_pad, st));
-  }
-  const long long part_b = Nb * ctx->nseg * No;
-  for (int b = 0; b < B; ++b) {
-    // K2
-    StreamArgs a1{};
-    a1.rows = ctx->G;
-    a1.rows_lo = ctx->G_lo;
-    a1.F = Nb * Ng;
-    a1.row_len = static_cast<int>(Ns_pad);
-    a1.el = ctx->opts.prec_g;
-    a1.x = ctx->ws_shat + b * Ns_pad;
-    a1.x_stride = B * Ns_pad;
-    a1.rows_per_vec = Ng;
-    a1.scale = ctx->G_scale;
-    a1.nblk = ctx->nblk;
-    a1.y = ctx->ws_mhat;
-    a1.status = ctx->d_status;
+  for (int g0 = 0; g0 < B; g0 += kStreamGroup) {
+    const int Bg = std::min(kStreamGroup, B - g0);
+    // K1
     {
-      StageTimer t(ctx, 1, st);
-      CK(launch_stream_dot(a1, ctx->num_sms, st));
+      StageTimer t(ctx, 0, st);
+      CK(launch_rfft_rows(slip_d + static_cast<long long>(g0) * Ns * Nt, Bg * Ns, static_cast<int>(Nt),
+                          static_cast<int>(Nt), ctx->tw, ctx->ws_shat, Bg * Ns_pad, Ns, Ns_pad, st));
     }
-    // K3
-    float* sf = nullptr;
-    if (seafloor) sf = kf == 1 ? seafloor + b * Ng * Nt : ctx->ws_seafloor;
+    const long long part_b = Nb * ctx->nseg * No;
+    for (int b = 0; b < Bg; ++b) {
+      const long long bg = g0 + b;  // rupture index in the call
+      // K2
+      StreamArgs a1{};
+      a1.rows = ctx->G;
+      a1.rows_lo = ctx->G_lo;
+      a1.F = Nb * Ng;
+      a1.row_len = static_cast<int>(Ns_pad);
+      a1.el = ctx->opts.prec_g;
+      a1.x = ctx->ws_shat + b * Ns_pad;
+      a1.x_stride = Bg * Ns_pad;
+      a1.rows_per_vec = Ng;
+      a1.scale = ctx->G_scale;
+      a1.nblk = ctx->nblk;
+      a1.y = ctx->ws_mhat;
+      a1.status = ctx->d_status;
+      {
+        StageTimer t(ctx, 1, st);
+        CK(launch_stream_dot(a1, ctx->num_sms, st));
+      }
+      // K3
+      float* sf = nullptr;
+      if (seafloor) sf = kf == 1 ? seafloor + bg * Ng * Nt : ctx->ws_seafloor;
+      {
+        StageTimer t(ctx, 2, st);
+        CK(launch_retransform(ctx->ws_mhat, Ng, Ng, static_cast<int>(Nt), ctx->tw,
+                              static_cast<float>(1.0 / ctx->opts.dt), ctx->opts.dt_mode, ctx->ws_vhat,
+                              static_cast<long long>(ctx->nseg) * ctx->RL, sf, st));
+      }
+      if (seafloor && kf == 0)
+        CK(cudaMemcpyAsync(seafloor + bg * Ng * Nt, ctx->ws_seafloor, sizeof(float) * Ng * Nt,
+                           cudaMemcpyDeviceToHost, st));
+      // K4
+      StreamArgs a2{};
+      a2.rows = ctx->P;
+      a2.F = Nb * ctx->nseg * No;
+      a2.row_len = ctx->RL;
+      a2.el = ctx->opts.prec_p;
+      a2.x = ctx->ws_vhat;
+      a2.x_stride = ctx->RL;
+      a2.rows_per_vec = No;
+      a2.y = ctx->ws_part + b * part_b;
+      a2.status = ctx->d_status;
+      {
+        StageTimer t(ctx, 3, st);
+        CK(launch_stream_dot(a2, ctx->num_sms, st));
+      }
+    }
+    // K5
     {
-    StageTimer t(ctx, 2, st);
-    CK(launch_retransform(ctx->ws_mhat, Ng, Ng, static_cast<int>(Nt), ctx->tw,
-                          static_cast<float>(1.0 / ctx->opts.dt), ctx->opts.dt_mode, ctx->ws_vhat,
-                          static_cast<long long>(ctx->nseg) * ctx->RL, sf, st));
+      StageTimer t(ctx, 4, st);
+      CK(launch_reduce_irfft(ctx->ws_part, Bg, static_cast<int>(No), ctx->nseg, static_cast<int>(Nt), part_b,
+                             static_cast<long long>(ctx->nseg) * No, No, ctx->tw,
+                             q_d + static_cast<long long>(g0) * No * Nt, st));
     }
-    if (seafloor && kf == 0)
-      CK(cudaMemcpyAsync(seafloor + b * Ng * Nt, ctx->ws_seafloor, sizeof(float) * Ng * Nt, cudaMemcpyDeviceToHost,
-                         st));
-    // K4
-    StreamArgs a2{};
-    a2.rows = ctx->P;
-    a2.F = Nb * ctx->nseg * No;
-    a2.row_len = ctx->RL;
-    a2.el = ctx->opts.prec_p;
-    a2.x = ctx->ws_vhat;
-    a2.x_stride = ctx->RL;
-    a2.rows_per_vec = No;
-    a2.y = ctx->ws_part + b * part_b;
-    a2.status = ctx->d_status;
-    {
-      StageTimer t(ctx, 3, st);
-      CK(launch_stream_dot(a2, ctx->num_sms, st));
-    }
-  }
-  // K5
-  {
-  StageTimer t(ctx, 4, st);
-  CK(launch_reduce_irfft(ctx->ws_part, B, static_cast<int>(No), ctx->nseg, static_cast<int>(Nt), part_b,
-                         static_cast<long long>(ctx->nseg) * No, No, ctx->tw, q_d, st));
   }
   if (kq == 0) {
     StageTimer t(ctx, 5, st, 0);

@@ -58,7 +58,7 @@ def tiny_ops():
 def test_adjoint_against_oracle(tiny_ops, prec):
     wl, geom, G, P = tiny_ops
     r = synth.random_waveforms(3, wl.No, wl.Nt, seed=4)
-    ctx = make_context(s2w, geom, wl.Nt, prec_g=prec, max_batch=3, chunk=256)
+    ctx = make_context(s2w, geom, wl.Nt, prec_g=prec, max_batch=3, chunk=256, engine="stream")
     g = ctx.adjoint(torch.tensor(r, dtype=torch.float32, device="cuda")).cpu().numpy()
     ctx.sync()
     adjoint_bars(g, G, P, r, TOL[prec], f"adjoint tiny {prec}")

@@ -84,7 +84,8 @@ def test_irfft_truncates_and_inverts(Nt):
 @pytest.mark.parametrize("prec", ["fp32", "bf16_hilo", "bf16", "fp8"])
 def test_tiny_workload_against_oracle(tiny, tiny_window, prec):
     wl, geom, slip, q_ref, _ = tiny
-    ctx = make_context(s2w, geom, wl.Nt, prec_g=prec, max_batch=3, chunk=256)
+    # stream engine: these bars are for the storage precisions alone
+    ctx = make_context(s2w, geom, wl.Nt, prec_g=prec, max_batch=3, chunk=256, engine="stream")
     q = ctx.waveforms(torch.tensor(slip, dtype=torch.float32, device="cuda")).cpu().numpy()
     assert_parity(q, q_ref, *tiny_window, tol=TOL[prec], label=f"tiny {prec}")
 
@@ -100,7 +101,7 @@ def test_seafloor_field_against_oracle(tiny):
 
 def test_bf16_p_storage(tiny, tiny_window):
     wl, geom, slip, q_ref, _ = tiny
-    ctx = make_context(s2w, geom, wl.Nt, prec_p="bf16", max_batch=3)
+    ctx = make_context(s2w, geom, wl.Nt, prec_p="bf16", max_batch=3, engine="stream")
     q = ctx.waveforms(torch.tensor(slip, dtype=torch.float32, device="cuda")).cpu().numpy()
     assert_parity(q, q_ref, *tiny_window, tol=TOL["bf16"], label="tiny P bf16")
 
@@ -166,6 +167,22 @@ def test_host_device_batch_and_chunking_agree_bitwise(tiny):
     assert np.array_equal(q_host, q_dev)
     assert np.array_equal(q_dev, q_ch)
     assert np.array_equal(q_dev, q_one)
+
+
+def test_stream_groups_of_ruptures():
+    """The stream engine handles a call's ruptures in groups of 64; a
+    70-rupture call equals the same ruptures one by one, bit for bit."""
+    geom = compact_box(6, 500, 3, seed=70)
+    Nt, B = 32, 70
+    slip = np.random.default_rng(70).standard_normal((B, 6, Nt)).astype(np.float32)
+    ctx = make_context(s2w, geom, Nt, max_batch=B)
+    st = torch.tensor(slip, device="cuda")
+    q = ctx.waveforms(st).cpu().numpy()
+    q1 = np.stack([ctx.waveforms(st[b:b + 1]).cpu().numpy()[0] for b in (0, 63, 64, 69)])
+    assert np.array_equal(q[[0, 63, 64, 69]], q1)
+    G = geom.greens_rows(0, geom.Ng, Nt)
+    P = geom.adjoint_cols(0, geom.Ng, Nt)
+    assert_parity(q, oracle.waveforms(G, P, slip), *window_norms(G, P, slip), tol=1e-5, label="stream groups")
 
 
 @pytest.mark.parametrize("Ns,Ng,No,Nt", [(5, 1000, 3, 64), (1, 37, 1, 32), (1024, 300, 2, 32),
