@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--prec-g", default="fp32", choices=["fp32", "bf16", "bf16_hilo", "fp8"])
     ap.add_argument("--prec-p", default="fp32", choices=["fp32", "bf16"])
     ap.add_argument("--engine", default="auto", choices=["auto", "stream", "tensor"])
+    ap.add_argument("--tc-cluster", type=int, default=0, choices=[0, 1, 2, 4],
+                    help="tensor engine: CTAs per cluster sharing B tiles (0 = library choice)")
     ap.add_argument("--mode", default="waveforms", choices=["waveforms", "gradient"],
                     help="gradient: one step = misfit gradients of the batch (forward + adjoint)")
     ap.add_argument("--batch", type=int, default=None, help="ruptures per step (default: the workload's)")
@@ -121,9 +123,9 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ setup
-def load_context(s2w, wl, geom, prec_g, prec_p, B, device, engine="auto", chunk=1024):
+def load_context(s2w, wl, geom, prec_g, prec_p, B, device, engine="auto", chunk=1024, tc_cluster=0):
     ctx = s2w.Context(wl.Ns, wl.Ng, wl.No, wl.Nt, prec_g=prec_g, prec_p=prec_p,
-                      max_batch=B, device=device, engine=engine)
+                      max_batch=B, device=device, engine=engine, tc_cluster=tc_cluster)
     for g0 in range(0, wl.Ng, chunk):
         g1 = min(wl.Ng, g0 + chunk)
         ctx.load_greens(g0, geom.greens_rows(g0, g1, wl.Nt, np.float32))
@@ -238,7 +240,8 @@ def run_ours(args, rank, world, local_rank):
     slip_np = slip_np.reshape(pool, B, wl.Ns, wl.Nt)
 
     t_setup = time.perf_counter()
-    ctx = load_context(s2w, wl, geom, args.prec_g, args.prec_p, B, local_rank, args.engine)
+    ctx = load_context(s2w, wl, geom, args.prec_g, args.prec_p, B, local_rank, args.engine,
+                       tc_cluster=args.tc_cluster)
     setup_s = time.perf_counter() - t_setup
     slip_d = torch.tensor(slip_np, device=dev)
     q_d = torch.empty((pool, B, wl.No, wl.Nt), dtype=torch.float32, device=dev)
@@ -376,6 +379,7 @@ def run_ours(args, rank, world, local_rank):
            "config": {"workload": wl.name, "Ns": wl.Ns, "Ng": wl.Ng, "No": wl.No, "Nt": wl.Nt,
                       "ruptures_per_step": B, "prec_g": args.prec_g, "prec_p": args.prec_p,
                       "engine": "tensor" if tensor else "stream", "mode": args.mode,
+                      "tc_cluster": args.tc_cluster,
                       "l2": "inputs larger than L2 (every step streams the full operator spectra)",
                       "parallelism": f"replicas{world}",
                       "operator_gb": round(sum(ctx.operator_bytes()) / 1e9, 2),

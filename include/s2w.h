@@ -91,6 +91,9 @@ typedef struct {
   int max_batch;  /* largest B accepted by s2w_waveforms (sizes workspaces) */
   int device;     /* CUDA device ordinal (default 0) */
   int engine;     /* s2w_engine (default AUTO) */
+  int tc_cluster; /* tensor engine: CTAs per cluster sharing each B tile by
+                     multicast, 1, 2 or 4; 0 = library choice (s2w_autotune
+                     can measure and set it) */
 } s2w_opts;
 
 /* Fill *o with the defaults listed above (max_batch = 1). */

@@ -30,7 +30,7 @@ namespace s2w {
 
 namespace {
 
-constexpr int kTcThreads = 192;
+constexpr int kTcThreads = 192;  // warps: 0 TMA producer, 1 MMA, 2-5 epilogue
 constexpr int kBlockM = 128;
 constexpr int kBlockK = 64;  // bf16 elements per 128-byte swizzle row
 constexpr int kABytes = kBlockM * kBlockK * 2;
@@ -43,6 +43,36 @@ __device__ __forceinline__ void tma_load_3d(void* sdst, const CUtensorMap* tm, i
           "r"(smem_u32(sdst)),
       "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
       : "memory");
+}
+
+// Same load, delivered to the same shared-memory offset (and completing on the
+// same barrier offset) in every CTA of the cluster whose bit is set in mask.
+__device__ __forceinline__ void tma_load_3d_mc(void* sdst, const CUtensorMap* tm, int c0, int c1, int c2,
+                                               uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1, {%2, "
+      "%3, %4}], [%5], %6;" ::"r"(smem_u32(sdst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar)), "h"(mask)
+      : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_id_x() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_count_x() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -66,6 +96,15 @@ __device__ __forceinline__ void tc_commit(uint64_t* bar) {
                : "memory");
 }
 
+// Arrive once on `bar` in every CTA of `mask` when this thread's issued MMAs complete.
+__device__ __forceinline__ void tc_commit_mc(uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(mask)
+      : "memory");
+}
+
 __device__ __forceinline__ void tc_mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
                                             uint32_t accumulate) {
   asm volatile(
@@ -77,18 +116,44 @@ __device__ __forceinline__ void tc_mma_bf16(uint32_t d_tmem, uint64_t a_desc, ui
 }
 
 // 32 lanes x 16 columns of 32-bit accumulators: thread t of the warp gets
-// columns [col, col + 16) of TMEM lane (lane base + t).
+// columns [col, col + 16) of TMEM lane (lane base + t).  The load and its
+// wait are one asm statement, so no use of the outputs can be scheduled
+// before the data has arrived.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   uint32_t r[16];
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15}, [%16];"
+      "%15}, [%16];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
         "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      : "r"(taddr)
+      : "memory");
 #pragma unroll
   for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+// Same for 64 columns in one load (one wait per 64 accumulators).
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64]) {
+  uint32_t r[64];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32, %33, %34, %35, %36, %37, "
+      "%38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, "
+      "%60, %61, %62, %63}, [%64];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]),
+        "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]),
+        "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]),
+        "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]),
+        "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int k = 0; k < 64; ++k) v[k] = __uint_as_float(r[k]);
 }
 
 // Shared-memory matrix descriptor of a K-major tile written by TMA with
@@ -116,10 +181,19 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
          (static_cast<uint32_t>(M >> 4) << 24);
 }
 
-template <int BK>
+// One ring of K-block stages, each holding the A tile and the B tile of the
+// same K block (loaded together, released together).
+// CL > 1: clusters of CL CTAs take CL adjacent M tiles of the same (bin, K
+// chunk); each CTA loads 1/CL of the B tile and multicasts it to all of them,
+// and every CTA's MMA releases a stage in all of them (empty barriers count CL).
+template <int BK, int CL>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
   constexpr int kA = kBlockM * BK * 2;
+  constexpr uint16_t kMask = static_cast<uint16_t>((1u << CL) - 1u);
+  const uint32_t crank = CL > 1 ? cluster_ctarank() : 0u;
+  const long long cid = CL > 1 ? static_cast<long long>(cluster_id_x()) : static_cast<long long>(blockIdx.x);
+  const long long ncl = CL > 1 ? static_cast<long long>(cluster_count_x()) : static_cast<long long>(gridDim.x);
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
   const int N = a.N;
@@ -134,15 +208,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const int nk_total = (a.K + BK - 1) / BK;
-  const long long units = static_cast<long long>(a.Nb) * a.m_tiles * a.n_kchunks;
+  const int mtg = (a.m_tiles + CL - 1) / CL;  // M-tile groups (one per cluster unit)
+  const long long units = static_cast<long long>(a.Nb) * mtg * a.n_kchunks;
   const int n_mma = N > 256 ? N / 256 : 1;
   const int n_mma_cols = N > 256 ? 256 : N;
+  const int slice_rows = N / CL;  // B rows this CTA loads (and multicasts)
   const uint32_t idesc = idesc_bf16(kBlockM, n_mma_cols);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(full + s, 1);
-      mbar_init(empty + s, 1);
+      mbar_init(empty + s, CL);
     }
     mbar_init(acc_full, 1);
     mbar_init(acc_empty, 4);
@@ -154,18 +230,24 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
   tc_fence_before();
   __syncthreads();
+  if (CL > 1) cluster_sync_all();  // every CTA's barriers exist before any multicast
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
+
+  auto unit_coords = [&](long long u, int& l, int& mt, int& kc) {
+    kc = static_cast<int>(u % a.n_kchunks);
+    const long long r = u / a.n_kchunks;
+    mt = static_cast<int>(r % mtg) * CL + static_cast<int>(crank);
+    l = static_cast<int>(r / mtg);
+  };
 
   if (warp == 0) {
     if (lane == 0) {
       int it = 0;
       bool ok = true;
-      for (long long u = blockIdx.x; u < units && ok; u += gridDim.x) {
-        const int kc = static_cast<int>(u % a.n_kchunks);
-        const long long r = u / a.n_kchunks;
-        const int mt = static_cast<int>(r % a.m_tiles);
-        const int l = static_cast<int>(r / a.m_tiles);
+      for (long long u = cid; u < units && ok; u += ncl) {
+        int l, mt, kc;
+        unit_coords(u, l, mt, kc);
         const int kb0 = kc * a.kblocks_per_chunk;
         const int kb1 = min(nk_total, kb0 + a.kblocks_per_chunk);
         for (int kb = kb0; kb < kb1; ++kb, ++it) {
@@ -177,19 +259,29 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           unsigned char* sa = smem + s * stage_bytes;
           mbar_arrive_expect_tx(full + s, stage_bytes);
           tma_load_3d(sa, &tmA, kb * BK, mt * kBlockM, l, full + s);
-          for (int c = 0; c < n_mma; ++c)
-            tma_load_3d(sa + kA + c * n_mma_cols * BK * 2, &tmB, kb * BK, c * n_mma_cols, l, full + s);
+          if (CL == 1) {
+            for (int c = 0; c < n_mma; ++c)
+              tma_load_3d(sa + kA + c * n_mma_cols * BK * 2, &tmB, kb * BK, c * n_mma_cols, l, full + s);
+          } else {
+            tma_load_3d_mc(sa + kA + crank * slice_rows * BK * 2, &tmB, kb * BK, static_cast<int>(crank) * slice_rows,
+                           l, full + s, kMask);
+          }
         }
       }
       for (int kk = (it > S ? it - S : 0); kk < it; ++kk)
         mbar_wait_bounded(full + kk % S, (kk / S) & 1, a.status, DEV_ERR_TIMEOUT_FULL);
+      // the last stages must also have been released by every CTA of the
+      // cluster (their multicast commits land here) before anyone leaves
+      for (int kk = (it > S ? it - S : 0); kk < it; ++kk)
+        mbar_wait_bounded(empty + kk % S, (kk / S) & 1, a.status, DEV_ERR_TIMEOUT_EMPTY);
     }
   } else if (warp == 1) {
     if (lane == 0) {
       int it = 0, acc_it = 0;
       bool ok = true;
-      for (long long u = blockIdx.x; u < units && ok; u += gridDim.x) {
-        const int kc = static_cast<int>(u % a.n_kchunks);
+      for (long long u = cid; u < units && ok; u += ncl) {
+        int l, mt, kc;
+        unit_coords(u, l, mt, kc);
         const int kb0 = kc * a.kblocks_per_chunk;
         const int kb1 = min(nk_total, kb0 + a.kblocks_per_chunk);
         if (acc_it > 0 && !mbar_wait_bounded(acc_empty, (acc_it - 1) & 1, a.status, DEV_ERR_TIMEOUT_MMA)) {
@@ -214,7 +306,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               tc_mma_bf16(tmem + c * n_mma_cols, ad, bd, idesc, (kb > kb0 || k > 0) ? 1u : 0u);
             }
           }
-          tc_commit(empty + s);
+          if (CL == 1)
+            tc_commit(empty + s);
+          else
+            tc_commit_mc(empty + s, kMask);
         }
         if (!ok) break;
         tc_commit(acc_full);
@@ -227,24 +322,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // epilogue warps 2..5
     const int q = warp & 3;  // TMEM lane quadrant this warp may access
     int acc_it = 0;
-    for (long long u = blockIdx.x; u < units; u += gridDim.x) {
-      const int kc = static_cast<int>(u % a.n_kchunks);
-      const long long r = u / a.n_kchunks;
-      const int mt = static_cast<int>(r % a.m_tiles);
-      const int l = static_cast<int>(r / a.m_tiles);
+    for (long long u = cid; u < units; u += ncl) {
+      int l, mt, kc;
+      unit_coords(u, l, mt, kc);
       if (!mbar_wait_bounded(acc_full, acc_it & 1, a.status, DEV_ERR_TIMEOUT_MMA)) break;
       tc_fence_after();
       const int row = mt * kBlockM + q * 32 + lane;
       const uint32_t tbase = tmem + (static_cast<uint32_t>(q * 32) << 16);
-      const bool live = row < a.M_total;
+      const bool live = row < a.M_total && mt < a.m_tiles;
       float scale = 1.f;
       if (a.row_scale != nullptr && live) scale = a.row_scale[static_cast<long long>(l) * a.nblk + row / 256];
-      for (int c0 = 0; c0 < N; c0 += 16) {
-        float v[16];
-        tmem_ld16(tbase + c0, v);
-        if (!live) continue;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
+      auto emit = [&](int c0, const float* v, int ncols) {
+        if (!live) return;
+        for (int k = 0; k < ncols / 2; ++k) {
           const int t = c0 / 2 + k;  // complex column (rupture or observation)
           if (t < a.T) {
             const float2 z = make_float2(v[2 * k] * scale, v[2 * k + 1] * scale);
@@ -257,6 +347,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               a.out[((static_cast<long long>(l) * a.n_kchunks + kc) * a.M_total + row) * a.T + t] = z;
           }
         }
+      };
+      int c0 = 0;
+      for (; c0 + 64 <= N; c0 += 64) {
+        float v[64];
+        tmem_ld64(tbase + c0, v);
+        emit(c0, v, 64);
+      }
+      for (; c0 < N; c0 += 16) {
+        float v[16];
+        tmem_ld16(tbase + c0, v);
+        emit(c0, v, 16);
       }
       tc_fence_before();
       __syncwarp();
@@ -270,6 +371,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc_fence_after();
     tmem_dealloc(tmem, a.tmem_cols);
   }
+  if (CL > 1) cluster_sync_all();  // no CTA leaves while a peer may still signal it
 }
 
 // Stage-1 B operand from the slip spectra shat[l][b][Ns_pad] (complex FP32):
@@ -331,7 +433,6 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-template <bool BF16IN>
 __global__ void __launch_bounds__(kRtThreads, 1)
     k_tc_retransform(const __grid_constant__ CUtensorMap tmT, const TcRtArgs a) {
   extern __shared__ __align__(1024) unsigned char smraw[];
@@ -339,7 +440,7 @@ __global__ void __launch_bounds__(kRtThreads, 1)
   const int Nt = a.Nt;
   const int K = 2 * Nt;           // = N
   const int KB = K / kBlockK;     // k-blocks per tile (A slots)
-  const int n_mma = K > 256 ? 2 : 1;
+  const int n_half = K > 256 ? 2 : 1;   // MMA column halves (256 output columns each)
   const int ncols = K > 256 ? 256 : K;
   const int t_bytes = ncols * kBlockK * 2;
   unsigned char* sA = smem;                               // KB slots of 16 KB
@@ -356,6 +457,7 @@ __global__ void __launch_bounds__(kRtThreads, 1)
   const int mtiles = (a.Ng + kBlockM - 1) / kBlockM;
   const long long tiles = static_cast<long long>(a.Bs) * mtiles;
   const uint32_t idesc = idesc_bf16(kBlockM, ncols);
+  const uint32_t tmem_cols = K <= 64 ? 64 : (K <= 128 ? 128 : (K <= 256 ? 256 : 512));
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < KB; ++s) {
@@ -371,7 +473,7 @@ __global__ void __launch_bounds__(kRtThreads, 1)
     fence_mbar_init();
   }
   if (warp == 1) {
-    tmem_alloc(tmem_holder, K > 256 ? 512 : (K > 128 ? 256 : (K > 64 ? 128 : 64)));
+    tmem_alloc(tmem_holder, tmem_cols);
     tmem_relinquish();
   }
   tc_fence_before();
@@ -380,12 +482,13 @@ __global__ void __launch_bounds__(kRtThreads, 1)
   const uint32_t tmem = *tmem_holder;
 
   if (warp == 0) {
+    // T tiles in job order: tile, half, k-block
     if (lane == 0) {
       int it = 0;
       bool ok = true;
       for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
-        for (int kb = 0; kb < KB && ok; ++kb) {
-          for (int h = 0; h < n_mma; ++h, ++it) {
+        for (int h = 0; h < n_half && ok; ++h) {
+          for (int kb = 0; kb < KB; ++kb, ++it) {
             const int s = it & 1;
             if (it >= 2 && !mbar_wait_bounded(tempty + s, ((it >> 1) - 1) & 1, a.status, DEV_ERR_TIMEOUT_EMPTY)) {
               ok = false;
@@ -409,28 +512,27 @@ __global__ void __launch_bounds__(kRtThreads, 1)
           break;
         }
         tc_fence_after();
-        for (int kb = 0; kb < KB && ok; ++kb) {
-          if (!mbar_wait_bounded(afull + kb, tl & 1, a.status, DEV_ERR_TIMEOUT_FULL)) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          const uint32_t sa = smem_u32(sA + kb * kABytes);
-          for (int h = 0; h < n_mma; ++h, ++it) {
+        for (int h = 0; h < n_half && ok; ++h) {
+          for (int kb = 0; kb < KB && ok; ++kb, ++it) {
+            if (h == 0 && !mbar_wait_bounded(afull + kb, tl & 1, a.status, DEV_ERR_TIMEOUT_FULL)) {
+              ok = false;
+              break;
+            }
             const int s = it & 1;
             if (!mbar_wait_bounded(tfull + s, (it >> 1) & 1, a.status, DEV_ERR_TIMEOUT_FULL)) {
               ok = false;
               break;
             }
             tc_fence_after();
+            const uint32_t sa = smem_u32(sA + kb * kABytes);
             const uint32_t sb = smem_u32(sT + s * t_bytes);
 #pragma unroll
             for (int k = 0; k < kBlockK / 16; ++k)
               tc_mma_bf16(tmem + h * ncols, sdesc_sw128(sa + k * 32), sdesc_sw128(sb + k * 32), idesc,
                           (kb > 0 || k > 0) ? 1u : 0u);
             tc_commit(tempty + s);
+            if (h == n_half - 1) tc_commit(afree + kb);
           }
-          tc_commit(afree + kb);
         }
         if (!ok) break;
         tc_commit(acc_full);
@@ -448,12 +550,13 @@ __global__ void __launch_bounds__(kRtThreads, 1)
       tc_fence_after();
       const uint32_t tbase = tmem + (static_cast<uint32_t>(q * 32) << 16);
       __nv_bfloat162* out = a.vhat + static_cast<long long>(b) * a.vld_b + i;
-      for (int c0 = 0; c0 < K; c0 += 16) {
-        float v[16];
-        tmem_ld16(tbase + c0, v);
+      // K = 2 Nt is a multiple of 64 for every supported Nt (32..256)
+      for (int c0 = 0; c0 < K; c0 += 64) {
+        float v[64];
+        tmem_ld64(tbase + c0, v);
         if (i >= a.Ng) continue;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
+        for (int k = 0; k < 32; ++k) {
           const int l = c0 / 2 + k;
           if (l == 0) {
             out[0] = __floats2bfloat162_rn(v[0], 0.f);
@@ -475,56 +578,28 @@ __global__ void __launch_bounds__(kRtThreads, 1)
     for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++tl) {
       const int b = static_cast<int>(t / mtiles);
       const int i0 = static_cast<int>(t % mtiles) * kBlockM;
-      const float2* mb = a.mhat + static_cast<long long>(b) * a.ld_b;  // unused when mhat_bf is set
+      const unsigned* mbb = reinterpret_cast<const unsigned*>(a.mhat_bf) + static_cast<long long>(b) * a.ld_b;
       for (int kb = 0; kb < KB; ++kb) {
         if (tl > 0 && !mbar_wait_bounded(afree + kb, (tl - 1) & 1, a.status, DEV_ERR_TIMEOUT_EMPTY)) {
           ok = false;
           break;
         }
         unsigned char* slot = sA + kb * kABytes;
-        float2 v[4][4];
-        float2 vn[4];
-        // all loads of the k-block first (16 per lane), then convert and store
-        if (BF16IN) {
-          const unsigned* mbb = reinterpret_cast<const unsigned*>(a.mhat_bf) + static_cast<long long>(b) * a.ld_b;
-          unsigned raw[4][4], rawn[4];
+        unsigned raw[4][4], rawn[4];
+        // all loads of the k-block first (16 per lane), then store
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {      // bins: l_local = f + 8 j
-            const long long lo = static_cast<long long>(kb * 32 + f + 8 * j) * a.ld_l;
+        for (int j = 0; j < 4; ++j) {        // bins: l_local = f + 8 j
+          const long long lo = static_cast<long long>(kb * 32 + f + 8 * j) * a.ld_l;
 #pragma unroll
-            for (int g = 0; g < 4; ++g) {    // signals: row = 32 g + lane
-              const int i = i0 + 32 * g + lane;
-              raw[j][g] = i < a.Ng ? __ldg(mbb + lo + i) : 0u;
-            }
-          }
-#pragma unroll
-          for (int g = 0; g < 4; ++g) {
+          for (int g = 0; g < 4; ++g) {      // signals: row = 32 g + lane
             const int i = i0 + 32 * g + lane;
-            rawn[g] = (kb == 0 && f == 0 && i < a.Ng) ? __ldg(mbb + static_cast<long long>(Nt) * a.ld_l + i) : 0u;
+            raw[j][g] = i < a.Ng ? __ldg(mbb + lo + i) : 0u;
           }
+        }
 #pragma unroll
-          for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int g = 0; g < 4; ++g)
-              v[j][g] = make_float2(__uint_as_float(raw[j][g] << 16), __uint_as_float(raw[j][g] & 0xffff0000u));
-#pragma unroll
-          for (int g = 0; g < 4; ++g) vn[g] = make_float2(__uint_as_float(rawn[g] << 16), 0.f);
-        } else {
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const long long lo = static_cast<long long>(kb * 32 + f + 8 * j) * a.ld_l;
-#pragma unroll
-            for (int g = 0; g < 4; ++g) {
-              const int i = i0 + 32 * g + lane;
-              v[j][g] = i < a.Ng ? __ldg(mb + lo + i) : make_float2(0.f, 0.f);
-            }
-          }
-#pragma unroll
-          for (int g = 0; g < 4; ++g) {
-            const int i = i0 + 32 * g + lane;
-            vn[g] = (kb == 0 && f == 0 && i < a.Ng) ? __ldg(mb + static_cast<long long>(Nt) * a.ld_l + i)
-                                                    : make_float2(0.f, 0.f);
-          }
+        for (int g = 0; g < 4; ++g) {
+          const int i = i0 + 32 * g + lane;
+          rawn[g] = (kb == 0 && f == 0 && i < a.Ng) ? __ldg(mbb + static_cast<long long>(Nt) * a.ld_l + i) : 0u;
         }
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -532,11 +607,11 @@ __global__ void __launch_bounds__(kRtThreads, 1)
 #pragma unroll
           for (int g = 0; g < 4; ++g) {
             const int row = 32 * g + lane;
-            float2 z = v[j][g];
-            if (kb == 0 && ll == 0) z.y = vn[g].x;  // slot k = 1 carries Re(bin Nt)
+            unsigned w = raw[j][g];
+            if (kb == 0 && ll == 0) w = (w & 0xffffu) | (rawn[g] << 16);  // slot k = 1 carries Re(bin Nt)
             const int byte = ll * 4;                 // (2 ll) bf16 * 2 bytes
             const int off = row * 128 + ((((byte >> 4) ^ (row & 7)) << 4) | (byte & 15));
-            *reinterpret_cast<__nv_bfloat162*>(slot + off) = __floats2bfloat162_rn(z.x, z.y);
+            *reinterpret_cast<unsigned*>(slot + off) = w;
           }
         }
         fence_proxy_async_smem();
@@ -549,7 +624,7 @@ __global__ void __launch_bounds__(kRtThreads, 1)
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tmem, K > 256 ? 512 : (K > 128 ? 256 : (K > 64 ? 128 : 64)));
+    tmem_dealloc(tmem, tmem_cols);
   }
 }
 
@@ -600,26 +675,60 @@ size_t tc_smem_bytes(int N, int stages) {
   return 1024 + static_cast<size_t>(stages) * (kBlockM * bk * 2 + N * bk * 2) + 8 * (2 * stages + 2) + 16;
 }
 
+template <int BK, int CL>
+cudaError_t launch_tc_cl(const CUtensorMap& tmA, const CUtensorMap& tmB, const TcArgs& a, int num_sms, size_t smem,
+                         cudaStream_t st) {
+  auto kern = k_tc_gemm<BK, CL>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  const long long cunits = static_cast<long long>(a.Nb) * ((a.m_tiles + CL - 1) / CL) * a.n_kchunks;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  cfg.blockDim = dim3(kTcThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  long long nclusters = num_sms / CL;
+  if (CL > 1) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 0);
+    if (e != cudaSuccess) return e;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3(static_cast<unsigned>(nclusters * CL));
+    int active = 0;
+    e = cudaOccupancyMaxActiveClusters(&active, kern, &cfg);
+    if (e != cudaSuccess) return e;
+    if (active < 1) return cudaErrorInvalidConfiguration;
+    nclusters = active;
+  }
+  if (nclusters > cunits) nclusters = cunits;
+  cfg.gridDim = dim3(static_cast<unsigned>(nclusters * CL));
+  e = cudaLaunchKernelEx(&cfg, kern, tmA, tmB, a);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const TcArgs& a, int num_sms,
                            cudaStream_t st) {
   const long long units = static_cast<long long>(a.Nb) * a.m_tiles * a.n_kchunks;
   if (units <= 0) return cudaSuccess;
   if (a.N < 16 || a.N > 512 || a.N % 16 != 0 || (a.N > 256 && a.N % 256 != 0) || a.stages < 2)
     return cudaErrorInvalidValue;
+  const int CL = a.cluster < 1 ? 1 : a.cluster;
+  if (CL != 1 && CL != 2 && CL != 4) return cudaErrorInvalidValue;
+  if (CL > 1 && (a.N / CL < 8 || (a.N / CL) % 8 != 0 || a.N / CL > 256)) return cudaErrorInvalidValue;
   const size_t smem = tc_smem_bytes(a.N, a.stages);
-  const long long grid = units < num_sms ? units : num_sms;
   if (tc_block_k(a.N) == 64) {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_tc_gemm<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    k_tc_gemm<64><<<static_cast<unsigned>(grid), kTcThreads, smem, st>>>(tmA, tmB, a);
-  } else {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_tc_gemm<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    k_tc_gemm<32><<<static_cast<unsigned>(grid), kTcThreads, smem, st>>>(tmA, tmB, a);
+    if (CL == 1) return launch_tc_cl<64, 1>(tmA, tmB, a, num_sms, smem, st);
+    if (CL == 2) return launch_tc_cl<64, 2>(tmA, tmB, a, num_sms, smem, st);
+    return launch_tc_cl<64, 4>(tmA, tmB, a, num_sms, smem, st);
   }
-  return cudaGetLastError();
+  if (CL == 1) return launch_tc_cl<32, 1>(tmA, tmB, a, num_sms, smem, st);
+  if (CL == 2) return launch_tc_cl<32, 2>(tmA, tmB, a, num_sms, smem, st);
+  return launch_tc_cl<32, 4>(tmA, tmB, a, num_sms, smem, st);
 }
 
 cudaError_t launch_tc_retransform(const CUtensorMap& tmT, const TcRtArgs& a, int num_sms, cudaStream_t st) {
@@ -629,19 +738,13 @@ cudaError_t launch_tc_retransform(const CUtensorMap& tmT, const TcRtArgs& a, int
   const int K = 2 * a.Nt;
   const int ncols = K > 256 ? 256 : K;
   const size_t smem = 1024 + static_cast<size_t>(K / kBlockK) * kABytes + 2ull * ncols * kBlockK * 2 +
-                      8 * (2 * (K / kBlockK) + 6) + 16;
+                      8 * (2 * (K / kBlockK) + 8) + 16;
   const long long grid = tiles < num_sms ? tiles : num_sms;
-  if (a.mhat_bf != nullptr) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_retransform<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    k_tc_retransform<true><<<static_cast<unsigned>(grid), kRtThreads, smem, st>>>(tmT, a);
-  } else {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_retransform<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    k_tc_retransform<false><<<static_cast<unsigned>(grid), kRtThreads, smem, st>>>(tmT, a);
-  }
+  if (a.mhat_bf == nullptr) return cudaErrorInvalidValue;
+  cudaError_t e =
+      cudaFuncSetAttribute(k_tc_retransform, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  k_tc_retransform<<<static_cast<unsigned>(grid), kRtThreads, smem, st>>>(tmT, a);
   return cudaGetLastError();
 }
 

@@ -60,6 +60,8 @@ struct s2w_ctx {
   long long Ng_pad2 = 0; // complex columns per row of the stage-2 operands
   int tc_kbpc = 64;      // 64-element K blocks per stage-2 chunk
   int tc_nkc = 1;        // stage-2 K chunks
+  int tc_cl1 = 1;        // cluster size of the stage-1 GEMM (B tiles multicast)
+  int tc_cl2 = 1;        // cluster size of the stage-2 GEMM
   void* tc_bp1 = nullptr;   // [Nb][tc_n1max][2 Ns_pad] bf16
   float2* tc_mhat = nullptr;  // [Nb][b][Ng] complex FP32
   void* tc_vhat = nullptr;  // [Nb][tc_bsub][Ng_pad2] bf16 pairs
@@ -135,6 +137,17 @@ int pointer_kind(const void* p, int device) {
   }
   if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return at.device == device ? 1 : -1;
   return 0;
+}
+
+// Tensor engine: default CTAs per cluster sharing each B tile.
+constexpr int kDefaultCluster = 1;
+
+// Largest cluster <= want that the GEMM accepts for an N-wide B operand split
+// over it and m_tiles M tiles.
+int fit_cluster(int want, int N, int m_tiles) {
+  int cl = want < 1 ? 1 : want;
+  while (cl > 1 && (N / cl < 8 || (N / cl) % 8 != 0 || N / cl > 256 || cl > m_tiles)) cl /= 2;
+  return cl;  // 1: a single CTA loads any N <= 512 itself
 }
 
 // The stream engine handles ruptures in groups of at most this many (its
@@ -270,8 +283,10 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
       StageTimer t(ctx, 1, st);
       CUtensorMap ta, tb;
       const int bk = tc_block_k(N1);
+      const int m1 = static_cast<int>((Ng + 127) / 128);
+      const int cl = fit_cluster(ctx->tc_cl1, N1, m1);
       CK(tc_encode_3d(&ta, ctx->G, K1, Ng, Nb, K1, 128, bk));
-      CK(tc_encode_3d(&tb, ctx->tc_bp1, K1, ctx->tc_n1max, Nb, K1, N1 > 256 ? 256 : N1, bk));
+      CK(tc_encode_3d(&tb, ctx->tc_bp1, K1, ctx->tc_n1max, Nb, K1, cl > 1 ? N1 / cl : (N1 > 256 ? 256 : N1), bk));
       TcArgs a{};
       a.N = N1;
       a.K = K1;
@@ -282,6 +297,7 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
       a.kblocks_per_chunk = (K1 + bk - 1) / bk;
       a.stages = tc_stages_for(N1);
       a.tmem_cols = N1 <= 32 ? 32 : (N1 <= 64 ? 64 : (N1 <= 128 ? 128 : (N1 <= 256 ? 256 : 512)));
+      a.cluster = cl;
       a.epi = 0;
       a.T = Bs;
       a.out = nullptr;
@@ -295,7 +311,6 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
     {
       StageTimer t(ctx, 2, st);
       TcRtArgs r{};
-      r.mhat = nullptr;
       r.mhat_bf = reinterpret_cast<const __nv_bfloat162*>(ctx->tc_mhat);
       r.ld_l = static_cast<long long>(Bs) * Ng;
       r.ld_b = Ng;
@@ -311,8 +326,10 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
     {
       StageTimer t(ctx, 3, st);
       CUtensorMap ta, tb;
+      const int m2 = (Bs + 127) / 128;
+      const int cl = fit_cluster(ctx->tc_cl2, ctx->tc_n2, m2);
       CK(tc_encode_3d(&ta, ctx->tc_vhat, K2, ctx->tc_bsub, Nb, K2, 128));
-      CK(tc_encode_3d(&tb, ctx->tc_p2, K2, ctx->tc_n2, Nb, K2, ctx->tc_n2));
+      CK(tc_encode_3d(&tb, ctx->tc_p2, K2, ctx->tc_n2, Nb, K2, ctx->tc_n2 / cl));
       TcArgs a{};
       a.N = ctx->tc_n2;
       a.K = static_cast<int>(K2);
@@ -323,6 +340,7 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
       a.kblocks_per_chunk = ctx->tc_kbpc;
       a.stages = tc_stages_for(ctx->tc_n2);
       a.tmem_cols = ctx->tc_n2 <= 32 ? 32 : (ctx->tc_n2 <= 64 ? 64 : (ctx->tc_n2 <= 128 ? 128 : 256));
+      a.cluster = cl;
       a.epi = 1;
       a.T = static_cast<int>(No);
       a.out = ctx->tc_part;
@@ -352,6 +370,7 @@ void s2w_default_opts(s2w_opts* o) {
   o->max_batch = 1;
   o->device = 0;
   o->engine = S2W_ENGINE_AUTO;
+  o->tc_cluster = 0;
 }
 
 const char* s2w_status_string(int s) {
@@ -388,6 +407,8 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
   if (!(o.dt > 0.0)) return fail(nullptr, S2W_ERR_ARG, "dt must be > 0");
   if (o.max_batch < 1) return fail(nullptr, S2W_ERR_ARG, "max_batch must be >= 1");
   if (o.engine < S2W_ENGINE_AUTO || o.engine > S2W_ENGINE_TENSOR) return fail(nullptr, S2W_ERR_ARG, "engine=%d", o.engine);
+  if (o.tc_cluster != 0 && o.tc_cluster != 1 && o.tc_cluster != 2 && o.tc_cluster != 4)
+    return fail(nullptr, S2W_ERR_ARG, "tc_cluster=%d: 0, 1, 2 or 4", o.tc_cluster);
   if (o.engine == S2W_ENGINE_TENSOR && o.prec_g != S2W_PREC_BF16)
     return fail(nullptr, S2W_ERR_UNSUPPORTED, "the tensor engine needs prec_g = BF16");
   if (o.engine == S2W_ENGINE_TENSOR && 2 * No > 256)
@@ -463,11 +484,19 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
                (o.engine == S2W_ENGINE_TENSOR || (o.engine == S2W_ENGINE_AUTO && o.max_batch >= 2));
   if (ctx->tc_on) {
     ctx->tc_bsub = static_cast<int>(std::min<long long>(B, 256));
+    ctx->tc_cl1 = o.tc_cluster > 0 ? o.tc_cluster : kDefaultCluster;
+    ctx->tc_cl2 = o.tc_cluster > 0 ? o.tc_cluster : kDefaultCluster;
     ctx->tc_n1max = static_cast<int>(round_up(2 * ctx->tc_bsub, 16));
     if (ctx->tc_n1max > 256) ctx->tc_n1max = 512;
     ctx->tc_n2 = static_cast<int>(round_up(2 * No, 16));
     ctx->Ng_pad2 = round_up(Ng, 8);
+    // stage-2 split-K: enough work units for every SM (about 4 each) and no
+    // more, so the chunk partials stay small
     const long long nk2 = (2 * ctx->Ng_pad2 + 63) / 64;
+    const long long mt2 = (ctx->tc_bsub + 127) / 128;
+    long long nkc = (4LL * ctx->num_sms + Nb * mt2 - 1) / (Nb * mt2);
+    nkc = std::max(1LL, std::min(nkc, nk2));
+    ctx->tc_kbpc = static_cast<int>((nk2 + nkc - 1) / nkc);
     ctx->tc_nkc = static_cast<int>((nk2 + ctx->tc_kbpc - 1) / ctx->tc_kbpc);
     const long long bs = ctx->tc_bsub;
     if ((e = dalloc(&ctx->tc_bp1, 2ull * Nb * ctx->tc_n1max * 2 * ctx->Ns_pad)) != cudaSuccess)

@@ -201,6 +201,7 @@ struct TcArgs {
   int n_kchunks;          // split of the K blocks into chunks (stage 2)
   int kblocks_per_chunk;  // 64-element K blocks per chunk
   int stages;             // shared-memory ring depth
+  int cluster;            // CTAs per cluster sharing each B tile by multicast (1, 2, 4); B box rows = N / cluster
   int tmem_cols;          // power of two >= max(32, N)
   int epi;                // 0: out[l*ld_l + t*ld_t + row]; 1: out[((l*n_kchunks + kc)*M_total + row)*T + t]
   int T;                  // complex output columns (N / 2 live)
@@ -224,8 +225,7 @@ cudaError_t launch_pack_stage1_b(const float2* shat, int B, int Ns_pad, int Nb, 
 // reads mhat[l*ld_l + b*ld_b + i], writes vhat[l*vld_l + b*vld_b + i] (BF16
 // pairs); tmT: T[n][k], 2 Nt x 2 Nt BF16, K-major.  32 <= Nt <= 256.
 struct TcRtArgs {
-  const float2* mhat;
-  const __nv_bfloat162* mhat_bf;  // when set, mhat is read as BF16 pairs from here
+  const __nv_bfloat162* mhat_bf;  // seafloor spectra, BF16 (re, im) pairs
   long long ld_l, ld_b;
   int Ng, Bs, Nt;
   __nv_bfloat162* vhat;

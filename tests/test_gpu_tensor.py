@@ -27,11 +27,12 @@ def compact_box(Ns, Ng, No, seed, scale=0.1):
                           g.strike * scale, g.dip * scale, "box")
 
 
-def run_case(geom, Nt, B, seed=5, engine="tensor", chunk=4096):
+def run_case(geom, Nt, B, seed=5, engine="tensor", chunk=4096, tc_cluster=0):
     rng = np.random.default_rng(seed)
     slip = rng.standard_normal((B, geom.Ns, Nt))
     slip[:, :, Nt // 2:] = 0
-    ctx = make_context(s2w, geom, Nt, prec_g="bf16", max_batch=B, chunk=chunk, engine=engine)
+    ctx = make_context(s2w, geom, Nt, prec_g="bf16", max_batch=B, chunk=chunk, engine=engine,
+                       tc_cluster=tc_cluster)
     q = ctx.waveforms(torch.tensor(slip, dtype=torch.float32, device="cuda")).cpu().numpy()
     ctx.sync()
     G = geom.greens_rows(0, geom.Ng, Nt)
@@ -133,3 +134,16 @@ def test_gemm_retransform_record_lengths(Nt):
     geom = compact_box(12, 300, 3, seed=Nt)
     q, q_ref, wn, _, _ = run_case(geom, Nt, 4)
     assert_parity(q, q_ref, *wn, tol=TOL_TC, label=f"tensor Nt={Nt}")
+
+
+@pytest.mark.parametrize("cluster", [2, 4])
+@pytest.mark.parametrize("B", [3, 300])
+def test_multicast_clusters_match_single_cta(cluster, B):
+    """Clusters that share each B tile by TMA multicast compute exactly what
+    single CTAs compute (same MMAs, same accumulation order): bitwise equal,
+    including partial M-tile groups (700 rows = 5.5 tiles) and N = 16..512."""
+    geom = compact_box(24, 700, 6, seed=12)
+    q1, q_ref, wn, _, _ = run_case(geom, 64, B, seed=13, tc_cluster=1)
+    qc, _, _, _, _ = run_case(geom, 64, B, seed=13, tc_cluster=cluster)
+    assert_parity(qc, q_ref, *wn, tol=TOL_TC, label=f"cluster {cluster} B={B}")
+    assert np.array_equal(q1, qc)
