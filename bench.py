@@ -57,6 +57,10 @@ def parse():
     ap.add_argument("--batch", type=int, default=None, help="ruptures per step (default: the workload's)")
     ap.add_argument("--grid", type=int, default=None,
                     help="override the number of grid points (small cases for profiling)")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="time direct calls instead of replayed CUDA graphs of the pipeline")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default tensor-engine cluster size and AUTO batch threshold")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true")
     return ap.parse_args()
@@ -131,13 +135,6 @@ def load_context(s2w, wl, geom, prec_g, prec_p, B, device, engine="auto", chunk=
         ctx.load_greens(g0, geom.greens_rows(g0, g1, wl.Nt, np.float32))
         ctx.load_adjoint(g0, geom.adjoint_cols(g0, g1, wl.Nt, np.float32))
     return ctx
-
-
-def uses_tensor_engine(args, B):
-    """Mirror of the library's engine choice for s2w_waveforms."""
-    if args.prec_g != "bf16" or args.engine == "stream":
-        return False
-    return args.engine == "tensor" or B >= 2
 
 
 def stage1_algorithmic_bytes(wl, prec_g, B):
@@ -259,7 +256,21 @@ def run_ours(args, rank, world, local_rank):
         g_d = torch.empty_like(slip_d)
         loss_d = torch.empty((pool, B), dtype=torch.float32, device=dev)
 
-    def step(k, host=False):
+    # tensor-engine choices measured on the loaded operators
+    tuning = None
+    if not gradient and args.prec_g == "bf16" and args.engine == "auto" and args.tc_cluster == 0 \
+            and not args.no_autotune:
+        tuning = ctx.autotune(B, stream=stream)
+    # one CUDA graph of the pipeline per input buffer, captured during setup
+    use_graph = not gradient and not args.no_graph
+    if use_graph:
+        for k in range(pool):
+            ctx.waveforms_graph(slip_d[k], q_d[k], stream=stream)
+        torch.cuda.synchronize(dev)
+
+    def step(k, host=False, direct=False):
+        if use_graph and not host and not direct:
+            return ctx.waveforms_graph(slip_d[k % pool], q_d[k % pool], stream=stream)
         if gradient:
             if host:
                 return ctx.misfit_gradient(slip_h[k % pool], d_h[k % pool], grad=g_h[k % pool],
@@ -302,6 +313,19 @@ def run_ours(args, rank, world, local_rank):
     stages, launches1 = ctx.profile_read()
     ctx.profile_enable(False)
     ctx.sync()
+    # per-stage kernel times: a short profiled pass of direct calls (a
+    # replayed graph is timed as a whole)
+    n_prof = args.steps
+    if use_graph:
+        n_prof = max(3, min(args.steps, 20))
+        ctx.profile_enable(True)
+        ctx.profile_read()
+        for k in range(n_prof):
+            step(k, direct=True)
+        torch.cuda.synchronize(dev)
+        stages, _ = ctx.profile_read()
+        ctx.profile_enable(False)
+        ctx.sync()
     if world > 1:
         import torch.distributed as dist
         t = torch.tensor([elapsed_ms], device=dev)
@@ -345,7 +369,7 @@ def run_ours(args, rank, world, local_rank):
     pk, pk_kind = peaks()
     ms1, n1 = stages["contract_stage1"]
     per_launch_s = ms1 / max(n1, 1) / 1e3
-    tensor = uses_tensor_engine(args, B) and not gradient
+    tensor = stages["pack_operands"][1] > 0  # the tensor engine packs its operands
     if tensor:
         # per launch: one sub-batch of up to 256 ruptures; 8 real flops per
         # complex multiply-add of Ghat (Nb x Ng x Ns) with every rupture
@@ -366,8 +390,9 @@ def run_ours(args, rank, world, local_rank):
                 "frac": round(achieved / pk["hbm_gbs"], 4), "peak_source": pk_kind,
                 "traffic": measured_traffic(wl, args.prec_g), "algorithmic_bytes_per_launch": alg,
                 "launch_ms": round(per_launch_s * 1e3, 4)}
+    stages = {k: v for k, v in stages.items() if k != "graph"}
     total_stage_ms = sum(v[0] for v in stages.values())
-    stage_report = {k: {"ms_per_step": round(v[0] / args.steps, 4), "share": round(v[0] / total_stage_ms, 4)}
+    stage_report = {k: {"ms_per_step": round(v[0] / n_prof, 4), "share": round(v[0] / total_stage_ms, 4)}
                     for k, v in stages.items() if v[1] > 0}
 
     metric = METRIC if not gradient else \
@@ -379,7 +404,8 @@ def run_ours(args, rank, world, local_rank):
            "config": {"workload": wl.name, "Ns": wl.Ns, "Ng": wl.Ng, "No": wl.No, "Nt": wl.Nt,
                       "ruptures_per_step": B, "prec_g": args.prec_g, "prec_p": args.prec_p,
                       "engine": "tensor" if tensor else "stream", "mode": args.mode,
-                      "tc_cluster": args.tc_cluster,
+                      "tc_cluster": tuning["tc_cluster"] if tuning else args.tc_cluster,
+                      "autotune": tuning, "cuda_graph": use_graph,
                       "l2": "inputs larger than L2 (every step streams the full operator spectra)",
                       "parallelism": f"replicas{world}",
                       "operator_gb": round(sum(ctx.operator_bytes()) / 1e9, 2),

@@ -177,6 +177,34 @@ int s2w_misfit_gradient(s2w_ctx *ctx, const float *slip, const float *d, int B, 
  * the work is enqueued on `stream`. */
 int s2w_waveforms_noalloc(s2w_ctx *ctx, const float *slip, float *q, void *stream);
 
+/* s2w_waveforms for device pointers, run as a CUDA graph: the first call
+ * with a given (slip, q, B) captures the whole launch sequence once (on an
+ * internal stream, after synchronising `stream`) and instantiates it; later
+ * calls with the same arguments replay it on `stream` with one graph launch
+ * and no per-kernel host work.  Up to 8 graphs are kept per context (least
+ * recently replayed evicted).  No seafloor output.  Results equal those of
+ * s2w_waveforms bit for bit.  The graphs use the context's workspaces:
+ * replays on different streams must not overlap, as for s2w_waveforms.
+ * S2W_ERR_ARG for host pointers or pointers of another device. */
+int s2w_waveforms_graph(s2w_ctx *ctx, const float *slip, int B, float *q, void *stream);
+
+/* Measured choices of the tensor engine, from s2w_autotune. */
+typedef struct {
+  int tc_cluster;               /* chosen CTAs per cluster (1, 2, 4) */
+  int tc_min_batch;             /* smallest B that ENGINE_AUTO sends to the tensor engine */
+  int probe_batch;              /* batch size of the cluster probes */
+  float ms_stream_per_rupture;  /* stream engine, one rupture */
+  float ms_tensor_cluster[3];   /* tensor engine at probe_batch, clusters 1, 2, 4 (0 = not run) */
+  float ms_tensor_batch[6];     /* tensor engine at B = 2, 4, 8, 16, 32, 64 (0 = not run) */
+} s2w_tuning;
+
+/* Time the engines on the loaded operators (data-independent timings, dummy
+ * inputs) and set the context's tensor-engine cluster size and the batch
+ * size above which AUTO uses the tensor engine.  Uses up to B ruptures
+ * (<= max_batch).  Without the tensor engine only ms_stream_per_rupture is
+ * measured.  `out` may be NULL. */
+int s2w_autotune(s2w_ctx *ctx, int B, s2w_tuning *out, void *stream);
+
 /* Zero-padded real FFT of `rows` signals of Nt samples (the transform of
  * Alg. 2 steps 1-2): X[r][l] = sum_{n<Nt} x[r][n] exp(-2 pi i n l / (2 Nt)),
  * l = 0..Nt, X as interleaved (re, im) float pairs [rows][Nt+1][2].
@@ -192,8 +220,9 @@ int s2w_irfft(s2w_ctx *ctx, const float *X, long long rows, float *x, void *stre
  * Stages: 0 rfft of slip, 1 stage-1 contraction, 2 retransform (IFFT,
  * Truncate, D_t, ZeroPad, FFT), 3 stage-2 contraction, 4 partial reduction +
  * IFFT + Truncate, 5 host<->device copies made by s2w_waveforms, 6 packing
- * of tensor-engine operands (slip spectra into the stage-1 B operand). */
-#define S2W_NUM_STAGES 7
+ * of tensor-engine operands (slip spectra into the stage-1 B operand), 7 a
+ * whole replayed graph (s2w_waveforms_graph). */
+#define S2W_NUM_STAGES 8
 typedef struct {
   double ms[S2W_NUM_STAGES];           /* summed event-timed durations */
   long long count[S2W_NUM_STAGES];     /* timed launches per stage */

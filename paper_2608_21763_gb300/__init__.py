@@ -30,12 +30,12 @@ STATUS = {0: "S2W_OK", -1: "S2W_ERR_ARG", -2: "S2W_ERR_OOM", -3: "S2W_ERR_STATE"
 # every entry point declared in include/s2w.h
 EXPORTS = ("s2w_default_opts", "s2w_create", "s2w_destroy", "s2w_operator_bytes",
            "s2w_load_greens", "s2w_load_adjoint", "s2w_waveforms", "s2w_waveforms_noalloc",
-           "s2w_adjoint", "s2w_misfit_gradient", "s2w_rfft",
+           "s2w_adjoint", "s2w_misfit_gradient", "s2w_waveforms_graph", "s2w_autotune", "s2w_rfft",
            "s2w_irfft", "s2w_profile_enable", "s2w_profile_read", "s2w_sync",
            "s2w_last_error", "s2w_status_string")
-NUM_STAGES = 7
+NUM_STAGES = 8
 STAGE_NAMES = ("rfft_slip", "contract_stage1", "retransform", "contract_stage2",
-               "reduce_irfft", "copies", "pack_operands")
+               "reduce_irfft", "copies", "pack_operands", "graph")
 
 
 class S2WError(RuntimeError):
@@ -48,6 +48,12 @@ class Profile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * NUM_STAGES),
                 ("count", ctypes.c_longlong * NUM_STAGES),
                 ("launches", ctypes.c_longlong)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("tc_cluster", ctypes.c_int), ("tc_min_batch", ctypes.c_int), ("probe_batch", ctypes.c_int),
+                ("ms_stream_per_rupture", ctypes.c_float), ("ms_tensor_cluster", ctypes.c_float * 3),
+                ("ms_tensor_batch", ctypes.c_float * 6)]
 
 
 class Opts(ctypes.Structure):
@@ -81,6 +87,8 @@ def lib():
     L.s2w_waveforms_noalloc.argtypes = [V, P, P, V]
     L.s2w_adjoint.argtypes = [V, P, I, P, V]
     L.s2w_misfit_gradient.argtypes = [V, P, P, I, P, P, V]
+    L.s2w_waveforms_graph.argtypes = [V, P, I, P, V]
+    L.s2w_autotune.argtypes = [V, I, ctypes.POINTER(Tuning), V]
     L.s2w_rfft.argtypes = [V, P, LL, P, V]
     L.s2w_irfft.argtypes = [V, P, LL, P, V]
     L.s2w_profile_enable.argtypes = [V, I]
@@ -91,7 +99,8 @@ def lib():
     L.s2w_status_string.argtypes = [I]
     L.s2w_status_string.restype = ctypes.c_char_p
     for name in ("s2w_create", "s2w_destroy", "s2w_operator_bytes", "s2w_load_greens",
-                 "s2w_load_adjoint", "s2w_waveforms", "s2w_waveforms_noalloc", "s2w_adjoint", "s2w_misfit_gradient", "s2w_rfft",
+                 "s2w_load_adjoint", "s2w_waveforms", "s2w_waveforms_noalloc", "s2w_adjoint", "s2w_misfit_gradient", "s2w_waveforms_graph",
+                 "s2w_autotune", "s2w_rfft",
                  "s2w_irfft", "s2w_sync",
                  "s2w_profile_enable", "s2w_profile_read"):
         getattr(L, name).restype = I
@@ -221,6 +230,26 @@ class Context:
                 grad = torch.empty((B, self.Ns, self.Nt), dtype=torch.float32, device=r.device)
         self._check(lib().s2w_adjoint(self._h, _ptr(r), int(B), _ptr(grad), _stream(stream, r, grad)))
         return grad
+
+    def waveforms_graph(self, slip, q, stream=None):
+        """s2w_waveforms as a replayed CUDA graph (device tensors only; the
+        first call with these buffers captures, later calls replay)."""
+        self._check(lib().s2w_waveforms_graph(self._h, _ptr(slip), int(slip.shape[0]), _ptr(q),
+                                              _stream(stream, slip, q)))
+        return q
+
+    def autotune(self, B, stream=None):
+        """Measure the engines on the loaded operators; sets the tensor-engine
+        cluster size and the AUTO batch threshold.  Returns the measurements."""
+        t = Tuning()
+        st = stream
+        if st is None:
+            import torch
+            st = torch.cuda.current_stream(self.device)
+        self._check(lib().s2w_autotune(self._h, int(B), ctypes.byref(t), _stream(st)))
+        return {"tc_cluster": t.tc_cluster, "tc_min_batch": t.tc_min_batch, "probe_batch": t.probe_batch,
+                "ms_stream_per_rupture": t.ms_stream_per_rupture,
+                "ms_tensor_cluster": list(t.ms_tensor_cluster), "ms_tensor_batch": list(t.ms_tensor_batch)}
 
     def misfit_gradient(self, slip, d, grad=None, loss=None, stream=None):
         """Gradient of 0.5 ||q(slip[b]) - d[b]||^2 per rupture; returns

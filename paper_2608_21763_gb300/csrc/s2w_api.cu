@@ -62,6 +62,20 @@ struct s2w_ctx {
   int tc_nkc = 1;        // stage-2 K chunks
   int tc_cl1 = 1;        // cluster size of the stage-1 GEMM (B tiles multicast)
   int tc_cl2 = 1;        // cluster size of the stage-2 GEMM
+  int tc_min_batch = 2;  // AUTO: smallest B on the tensor engine
+  // CUDA graphs of the waveform pipeline, one per (slip, q, B), least
+  // recently used evicted beyond kGraphCache entries
+  struct GraphEntry {
+    const float* slip;
+    float* q;
+    int B;
+    cudaGraphExec_t exec;
+    long long launches;
+    unsigned long long last_use;
+  };
+  cudaStream_t cap_stream = nullptr;
+  std::vector<GraphEntry> graphs;
+  unsigned long long graph_clock = 0;
   void* tc_bp1 = nullptr;   // [Nb][tc_n1max][2 Ns_pad] bf16
   float2* tc_mhat = nullptr;  // [Nb][b][Ng] complex FP32
   void* tc_vhat = nullptr;  // [Nb][tc_bsub][Ng_pad2] bf16 pairs
@@ -199,6 +213,10 @@ struct StageTimer {
 };
 
 void free_all(s2w_ctx* c) {
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+  c->graphs.clear();
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  c->cap_stream = nullptr;
   for (auto& p : c->pending) {
     cudaEventDestroy(p.a);
     cudaEventDestroy(p.b);
@@ -675,7 +693,7 @@ int s2w_waveforms(s2w_ctx* ctx, const float* slip, int B, float* q, float* seafl
   }
   float* q_d = kq == 1 ? q : ctx->ws_q;
   const bool use_tc = ctx->tc_on && seafloor == nullptr && ctx->tc_T != nullptr &&
-                      (ctx->opts.engine == S2W_ENGINE_TENSOR || B >= 2);
+                      (ctx->opts.engine == S2W_ENGINE_TENSOR || B >= ctx->tc_min_batch);
   if (use_tc) {
     int rc = waveforms_tensor(ctx, slip_d, B, q_d, st);
     if (rc != S2W_OK) return rc;
@@ -902,6 +920,142 @@ int s2w_irfft(s2w_ctx* ctx, const float* X, long long rows, float* x, void* stre
   ctx->launches += 1;
   CK(launch_irfft_rows(reinterpret_cast<const float2*>(X), rows, ctx->Nt, ctx->tw, x,
                        static_cast<cudaStream_t>(stream)));
+  return S2W_OK;
+}
+
+// Graphs kept per context; a call with a new (slip, q, B) beyond this evicts
+// the least recently replayed one.
+constexpr size_t kGraphCache = 8;
+
+int s2w_waveforms_graph(s2w_ctx* ctx, const float* slip, int B, float* q, void* stream) {
+  if (!ctx) return S2W_ERR_ARG;
+  if (B < 0 || B > ctx->opts.max_batch)
+    return fail(ctx, S2W_ERR_ARG, "waveforms_graph: B=%d outside [0, max_batch=%d]", B, ctx->opts.max_batch);
+  if (B == 0) return S2W_OK;
+  if (!slip || !q) return fail(ctx, S2W_ERR_ARG, "waveforms_graph: slip and q must not be NULL");
+  if (ctx->g_count != ctx->Ng || ctx->p_count != ctx->Ng)
+    return fail(ctx, S2W_ERR_STATE, "waveforms_graph: operators not fully loaded");
+  DeviceGuard guard(ctx->device);
+  if (pointer_kind(slip, ctx->device) != 1 || pointer_kind(q, ctx->device) != 1)
+    return fail(ctx, S2W_ERR_ARG, "waveforms_graph: slip and q must be device pointers of the context's device");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  s2w_ctx::GraphEntry* ge = nullptr;
+  for (auto& g : ctx->graphs)
+    if (g.slip == slip && g.q == q && g.B == B) ge = &g;
+  if (ge == nullptr) {
+    if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    // the captured work must come after earlier work on `stream` (operators
+    // loaded, inputs written): capture happens on a separate stream
+    CK(cudaStreamSynchronize(st));
+    const bool prof = ctx->prof_on;
+    ctx->prof_on = false;
+    const long long l0 = ctx->launches;
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed));
+    const int rc = s2w_waveforms(ctx, slip, B, q, nullptr, ctx->cap_stream);
+    const cudaError_t ec = cudaStreamEndCapture(ctx->cap_stream, &graph);
+    ctx->prof_on = prof;
+    const long long n_launch = ctx->launches - l0;
+    ctx->launches = l0;
+    if (rc != S2W_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    CK(ec);
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(ei);
+    if (ctx->graphs.size() >= kGraphCache) {
+      size_t old = 0;
+      for (size_t k = 1; k < ctx->graphs.size(); ++k)
+        if (ctx->graphs[k].last_use < ctx->graphs[old].last_use) old = k;
+      cudaGraphExecDestroy(ctx->graphs[old].exec);
+      ctx->graphs.erase(ctx->graphs.begin() + static_cast<long>(old));
+    }
+    ctx->graphs.push_back({slip, q, B, exec, n_launch, 0});
+    ge = &ctx->graphs.back();
+  }
+  ge->last_use = ++ctx->graph_clock;
+  StageTimer t(ctx, 7, st, static_cast<int>(ge->launches));
+  CK(cudaGraphLaunch(ge->exec, st));
+  return S2W_OK;
+}
+
+int s2w_autotune(s2w_ctx* ctx, int B, s2w_tuning* out, void* stream) {
+  if (!ctx) return S2W_ERR_ARG;
+  if (B < 1 || B > ctx->opts.max_batch)
+    return fail(ctx, S2W_ERR_ARG, "autotune: B=%d outside [1, max_batch=%d]", B, ctx->opts.max_batch);
+  if (ctx->g_count != ctx->Ng || ctx->p_count != ctx->Ng)
+    return fail(ctx, S2W_ERR_STATE, "autotune: operators not fully loaded");
+  DeviceGuard guard(ctx->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // captured graphs hold the old engine choices
+  CK(cudaStreamSynchronize(st));
+  for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.exec);
+  ctx->graphs.clear();
+  s2w_tuning r{};
+  const bool prof = ctx->prof_on;
+  ctx->prof_on = false;
+  const long long l0 = ctx->launches;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  // dummy inputs: the slip workspace (any values; the timings do not depend on them)
+  auto timed = [&](int nb, int engine, float* ms) -> int {
+    const int saved = ctx->opts.engine;
+    ctx->opts.engine = engine;
+    int rc = s2w_waveforms(ctx, ctx->ws_slip, nb, ctx->ws_q, nullptr, st);  // warm-up
+    float best = 1e30f;
+    for (int rep = 0; rep < 2 && rc == S2W_OK; ++rep) {
+      cudaEventRecord(e0, st);
+      rc = s2w_waveforms(ctx, ctx->ws_slip, nb, ctx->ws_q, nullptr, st);
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      float m = 0.f;
+      cudaEventElapsedTime(&m, e0, e1);
+      best = std::min(best, m);
+    }
+    ctx->opts.engine = saved;
+    *ms = best;
+    return rc;
+  };
+  int rc = timed(1, S2W_ENGINE_STREAM, &r.ms_stream_per_rupture);
+  r.tc_cluster = ctx->tc_cl1;
+  r.tc_min_batch = ctx->tc_min_batch;
+  if (rc == S2W_OK && ctx->tc_on && ctx->tc_T != nullptr) {
+    r.probe_batch = std::min(B, ctx->tc_bsub);
+    const int cls[3] = {1, 2, 4};
+    float best = 1e30f;
+    int best_cl = ctx->tc_cl1;
+    for (int c = 0; c < 3 && rc == S2W_OK; ++c) {
+      ctx->tc_cl1 = ctx->tc_cl2 = cls[c];
+      rc = timed(r.probe_batch, S2W_ENGINE_TENSOR, &r.ms_tensor_cluster[c]);
+      if (rc == S2W_OK && r.ms_tensor_cluster[c] < best) {
+        best = r.ms_tensor_cluster[c];
+        best_cl = cls[c];
+      }
+    }
+    ctx->tc_cl1 = ctx->tc_cl2 = best_cl;
+    r.tc_cluster = best_cl;
+    // smallest batch whose tensor pass beats that many stream passes
+    const int sizes[6] = {2, 4, 8, 16, 32, 64};
+    int min_b = 0;
+    for (int k = 0; k < 6 && rc == S2W_OK; ++k) {
+      if (sizes[k] > B || sizes[k] > ctx->tc_bsub) break;
+      rc = timed(sizes[k], S2W_ENGINE_TENSOR, &r.ms_tensor_batch[k]);
+      if (rc == S2W_OK && min_b == 0 && r.ms_tensor_batch[k] < sizes[k] * r.ms_stream_per_rupture) min_b = sizes[k];
+    }
+    if (min_b == 0) min_b = r.ms_tensor_batch[0] > 0.f ? ctx->tc_bsub + 1 : ctx->tc_min_batch;
+    ctx->tc_min_batch = min_b;
+    r.tc_min_batch = min_b;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->prof_on = prof;
+  ctx->launches = l0;
+  if (rc != S2W_OK) return rc;
+  if (out) *out = r;
   return S2W_OK;
 }
 
