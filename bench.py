@@ -45,7 +45,11 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference", "torch_conv"],
+                    help="torch_conv: the paper's comparison method (two direct convolutions with "
+                         "torch.nn.functional.conv_transpose1d on the GPU), as context")
+    ap.add_argument("--torch-dtype", default="fp32", choices=["fp32", "fp64"],
+                    help="torch_conv arithmetic type")
     ap.add_argument("--workload", default="plain", choices=sorted(synth.WORKLOADS))
     ap.add_argument("--prec-g", default="fp32", choices=["fp32", "bf16", "bf16_hilo", "fp8"])
     ap.add_argument("--prec-p", default="fp32", choices=["fp32", "bf16"])
@@ -371,16 +375,20 @@ def run_ours(args, rank, world, local_rank):
     per_launch_s = ms1 / max(n1, 1) / 1e3
     tensor = stages["pack_operands"][1] > 0  # the tensor engine packs its operands
     if tensor:
-        # per launch: one sub-batch of up to 256 ruptures; 8 real flops per
-        # complex multiply-add of Ghat (Nb x Ng x Ns) with every rupture
-        bsub = min(B, 256)
+        # per launch: one sub-batch (up to 256 ruptures, 128 with hi/lo
+        # splits); 8 real flops per complex multiply-add of Ghat (Nb x Ng x Ns)
+        # with every rupture; the hi/lo split issues three BF16 MMAs (hi*hi,
+        # hi*lo, lo*hi) per product, so the tensor pipe executes 3x those flops
+        split = args.prec_g == "bf16_hilo"
+        bsub = min(B, 128 if split else 256)
         flops = 8.0 * (wl.Nt + 1) * wl.Ng * wl.Ns * bsub
-        achieved = flops / per_launch_s / 1e12
+        terms = 3 if split else 1
+        achieved = terms * flops / per_launch_s / 1e12
         peak = pk["bf16_tflops_sustained"]
         roof = {"kernel": "k_tc_gemm (stage-1 per-bin GEMM, tcgen05 kind::f16)", "bound": "tensor",
                 "achieved": round(achieved, 1), "peak": peak, "unit": "TFLOP/s",
                 "frac": round(achieved / peak, 4), "peak_source": pk_kind + " (bf16 sustained)",
-                "traffic": None, "algorithmic_flops_per_launch": flops,
+                "traffic": None, "algorithmic_flops_per_launch": flops, "mma_terms": terms,
                 "launch_ms": round(per_launch_s * 1e3, 4)}
     else:
         alg = stage1_algorithmic_bytes(wl, args.prec_g, 1)
@@ -400,7 +408,8 @@ def run_ours(args, rank, world, local_rank):
     out = {"metric": metric, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": round(elapsed_ms / args.steps, 4), "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if tensor else "f32", "data": "synthetic",
+           "scaling": "weak", "vs_baseline": None, "dtype": ("bf16x3" if args.prec_g == "bf16_hilo" else "bf16") if tensor else "f32",
+           "data": "synthetic",
            "config": {"workload": wl.name, "Ns": wl.Ns, "Ng": wl.Ng, "No": wl.No, "Nt": wl.Nt,
                       "ruptures_per_step": B, "prec_g": args.prec_g, "prec_p": args.prec_p,
                       "engine": "tensor" if tensor else "stream", "mode": args.mode,
@@ -462,6 +471,85 @@ def run_reference(args, rank):
                     "d2h_bytes_per_step": 0}}
 
 
+def run_torch_conv(args, rank, local_rank):
+    """Eq. time-domain-conv evaluated twice with conv_transpose1d (cuDNN), D_t
+    between, as the paper's direct baseline does: m = G * s, v = D_t m,
+    q = P * v, each convolution truncated to Nt samples.  The grid dimension
+    is split into the largest power-of-two tile the backend accepts (fixed
+    once), as the paper describes: here the largest power of two that keeps
+    every operand and result below 2^30 elements.  TF32 is disabled so FP32
+    means FP32."""
+    if rank != 0:
+        return None
+    import torch
+    import torch.nn.functional as F
+    torch.backends.cudnn.allow_tf32 = False
+    torch.backends.cuda.matmul.allow_tf32 = False
+    wl = workload(args)
+    B = args.batch or wl.B
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dtype = torch.float64 if args.torch_dtype == "fp64" else torch.float32
+    geom = wl.geometry_obj()
+    Ns, Ng, No, Nt = wl.Ns, wl.Ng, wl.No, wl.Nt
+    t_setup = time.perf_counter()
+    W1 = torch.empty((Ns, Ng, Nt), dtype=dtype, device=dev)   # conv_transpose1d weight [C_in][C_out][K]
+    W2 = torch.empty((Ng, No, Nt), dtype=dtype, device=dev)
+    for g0 in range(0, Ng, 2048):
+        g1 = min(Ng, g0 + 2048)
+        W1[:, g0:g1] = torch.from_numpy(geom.greens_rows(g0, g1, Nt)).to(dev, dtype).permute(1, 0, 2)
+        W2[g0:g1] = torch.from_numpy(np.ascontiguousarray(geom.adjoint_cols(g0, g1, Nt))).to(dev, dtype).permute(1, 0, 2)
+    setup_s = time.perf_counter() - t_setup
+    slip_np = wl.slip(geom, B=B)
+    x = torch.tensor(slip_np, dtype=dtype, device=dev)
+
+    def forward(x, tile):
+        m = torch.empty((x.shape[0], Ng, Nt), dtype=dtype, device=dev)
+        for g0 in range(0, Ng, tile):
+            g1 = min(Ng, g0 + tile)
+            m[:, g0:g1] = F.conv_transpose1d(x, W1[:, g0:g1])[..., :Nt]
+        v = m - F.pad(m, (1, 0))[..., :Nt]                      # D_t, dt = 1
+        q = torch.zeros((x.shape[0], No, Nt), dtype=dtype, device=dev)
+        for g0 in range(0, Ng, tile):
+            g1 = min(Ng, g0 + tile)
+            q += F.conv_transpose1d(v[:, g0:g1], W2[g0:g1])[..., :Nt]
+        return q
+
+    # every tensor handed to the backend stays below 2^30 elements (half its int32
+    # indexing limit: a weight above it faulted inside the library instead of
+    # raising), so the grid tile is fixed from the shapes before any call
+    limit = 2 ** 30
+    tile = 1 << (Ng - 1).bit_length()
+    while tile > 1 and max(Ns * tile * Nt, B * tile * (2 * Nt - 1), tile * No * Nt) > limit:
+        tile //= 2
+    try:
+        q = forward(x, tile)
+        torch.cuda.synchronize(dev)
+    except RuntimeError as e:  # report once; no further GPU work after a backend error
+        return {"impl": "torch_conv", "unavailable": f"conv_transpose1d failed at grid tile {tile}: "
+                f"{str(e).splitlines()[0]}"}
+    for _ in range(args.warmup):
+        forward(x, tile)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        q = forward(x, tile)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / args.steps
+    out = {"metric": METRIC, "value": round(B / (ms / 1e3), 3), "unit": UNIT, "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64" if dtype == torch.float64 else "f32", "data": "synthetic", "impl": "torch_conv",
+           "config": {"workload": wl.name, "Ns": Ns, "Ng": Ng, "No": No, "Nt": Nt, "ruptures_per_step": B,
+                      "grid_tile": min(tile, Ng), "cudnn_tf32": False, "setup_s": round(setup_s, 1)}}
+    if not args.no_check:
+        out["rel_l2"] = sampled_accuracy(wl, geom, slip_np, q.float().cpu().numpy())
+    return out
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -469,6 +557,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         out = run_reference(args, rank)
+    elif args.impl == "torch_conv":
+        out = run_torch_conv(args, rank, local_rank)
     else:
         if world > 1:
             import torch

@@ -75,12 +75,17 @@ typedef enum { S2W_DT_BACKWARD = 0, S2W_DT_NONE = 1 } s2w_dt_mode;
 /* Contraction engine for s2w_waveforms.  STREAM: CUDA-core kernels that
  * stream the resident spectra once per rupture (any storage precision).
  * TENSOR: tcgen05 tensor-core GEMMs over the whole rupture batch (one pass
- * over the spectra per batch of up to 256 ruptures); needs prec_g = BF16;
- * the activations (slip and velocity spectra) are rounded to BF16 and the
- * stage-2 operator is kept in BF16; Nt <= 256.  A call that asks for the
- * seafloor field runs on the stream kernels.  AUTO: TENSOR for calls with
- * B >= 2 when prec_g is BF16, STREAM otherwise.  The stream engine handles
- * the ruptures of a call in groups of up to 64. */
+ * over the spectra per sub-batch); needs prec_g = BF16 or BF16_HILO, Nt <=
+ * 256, No <= 128.  With BF16 the activations (slip and velocity spectra) and
+ * the stage-2 operator are rounded to BF16 and the retransform runs as a
+ * GEMM (sub-batches of up to 256 ruptures).  With BF16_HILO every operand
+ * (both operators and both activations) is split into hi + lo BF16 parts,
+ * each K step issues three MMAs (hi hi, hi lo, lo hi) into FP32
+ * accumulators, and the retransform is the FP32 FFT (sub-batches of up to
+ * 128).  A call that asks for the seafloor field runs on the stream
+ * kernels.  AUTO: TENSOR for calls with B >= the batch threshold (2, or what
+ * s2w_autotune measured) when prec_g allows it, STREAM otherwise.  The
+ * stream engine handles the ruptures of a call in groups of up to 64. */
 typedef enum { S2W_ENGINE_AUTO = 0, S2W_ENGINE_STREAM = 1, S2W_ENGINE_TENSOR = 2 } s2w_engine;
 
 typedef struct {

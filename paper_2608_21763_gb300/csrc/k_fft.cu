@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(kThreads) k_retransform(const float2* __restri
                                                           const float2* __restrict__ twg, float inv_dt, int dt_mode,
                                                           void* __restrict__ vout, long long ld_v,
                                                           float* __restrict__ seafloor, long long mhat_ld_b,
-                                                          long long vhat_ld_b) {
+                                                          long long vhat_ld_b, __nv_bfloat162* __restrict__ vout_lo) {
   constexpr int N = 32 * P;
   constexpr int L = 2 * N;
   constexpr int NB = N + 1;
@@ -91,10 +91,23 @@ __global__ void __launch_bounds__(kThreads) k_retransform(const float2* __restri
   mhat += blockIdx.y * mhat_ld_b;
   if (seafloor != nullptr) seafloor += static_cast<long long>(blockIdx.y) * Ng * N;
   load_twiddles<P>(tw, twg);
-  for (int e = threadIdx.x; e < NB * 32; e += kThreads) {
-    const int l = e >> 5, c = e & 31;
-    const long long i = i0 + c;
-    tile[c * NB + l] = (i < Ng) ? mhat[l * ld_m + i] : make_float2(0.f, 0.f);
+  // 16 independent loads in flight per thread (a warp reads 256 contiguous
+  // bytes of one bin per load)
+  constexpr int kU = 16;
+  for (int e0 = threadIdx.x; e0 < NB * 32; e0 += kThreads * kU) {
+    float2 v[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int e = e0 + u * kThreads;
+      const int l = e >> 5, c = e & 31;
+      const long long i = i0 + c;
+      v[u] = (e < NB * 32 && i < Ng) ? __ldg(mhat + l * ld_m + i) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int e = e0 + u * kThreads;
+      if (e < NB * 32) tile[(e & 31) * NB + (e >> 5)] = v[u];
+    }
   }
   __syncthreads();
   for (int c = warp; c < 32; c += kWarps) {
@@ -124,9 +137,13 @@ __global__ void __launch_bounds__(kThreads) k_retransform(const float2* __restri
     const long long i = i0 + c;
     if (i >= Ng) continue;
     const float2 v = tile[c * NB + l];
-    if (BF16OUT)
-      (static_cast<__nv_bfloat162*>(vout) + blockIdx.y * vhat_ld_b)[l * ld_v + i] = __floats2bfloat162_rn(v.x, v.y);
-    else
+    if (BF16OUT) {
+      const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
+      (static_cast<__nv_bfloat162*>(vout) + blockIdx.y * vhat_ld_b)[l * ld_v + i] = h;
+      if (vout_lo != nullptr)  // low-order part: v - hi, rounded again
+        (vout_lo + blockIdx.y * vhat_ld_b)[l * ld_v + i] =
+            __floats2bfloat162_rn(v.x - __low2float(h), v.y - __high2float(h));
+    } else
       (static_cast<float2*>(vout) + blockIdx.y * vhat_ld_b)[l * ld_v + i] = v;
   }
 }
@@ -331,7 +348,7 @@ cudaError_t launch_irfft_rows(const float2* X, long long rows, int Nt, const flo
 cudaError_t launch_retransform(const float2* mhat, long long Ng, long long ld_m, int Nt, const float2* tw,
                                float inv_dt, int dt_mode, float2* vhat, long long ld_v, float* seafloor,
                                cudaStream_t st, int nb, long long mhat_ld_b, long long vhat_ld_b,
-                               __nv_bfloat162* vhat_bf) {
+                               __nv_bfloat162* vhat_bf, __nv_bfloat162* vhat_bf_lo) {
   if (Ng <= 0 || nb <= 0) return cudaSuccess;
   const dim3 grid(static_cast<unsigned>((Ng + 31) / 32), static_cast<unsigned>(nb));
   S2W_DISPATCH_P(Nt, {
@@ -341,13 +358,13 @@ cudaError_t launch_retransform(const float2* mhat, long long Ng, long long ld_m,
                                            static_cast<int>(sm));
       if (e != cudaSuccess) return e;
       k_retransform<P, true><<<grid, kThreads, sm, st>>>(mhat, Ng, ld_m, tw, inv_dt, dt_mode, vhat_bf, ld_v, seafloor,
-                                                         mhat_ld_b, vhat_ld_b);
+                                                         mhat_ld_b, vhat_ld_b, vhat_bf_lo);
     } else {
       cudaError_t e = cudaFuncSetAttribute(k_retransform<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            static_cast<int>(sm));
       if (e != cudaSuccess) return e;
       k_retransform<P, false><<<grid, kThreads, sm, st>>>(mhat, Ng, ld_m, tw, inv_dt, dt_mode, vhat, ld_v, seafloor,
-                                                          mhat_ld_b, vhat_ld_b);
+                                                          mhat_ld_b, vhat_ld_b, nullptr);
     }
   });
   return cudaGetLastError();

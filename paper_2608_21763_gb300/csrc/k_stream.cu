@@ -11,10 +11,11 @@
 // Each CTA owns one contiguous range of rows (balanced to the row) and streams
 // it through a 3-stage shared-memory ring filled by cp.async.bulk (one bulk
 // copy per stage, L2 evict-first: every operator byte is read exactly once).
-// Eight consumer warps take one row each per pass; lane l handles the 16-byte
-// chunks l, l + 32, ... of the row, so a warp reads 512 contiguous bytes per
-// step, and keeps the matching slice of x_vec in registers across rows that
-// share it.  Products accumulate in FP32; FP8 rows are rescaled by their
+// Eight consumer warps take rows in passes: a long row gets a whole warp (lane
+// l handles the 16-byte chunks l, l + 32, ..., so a warp reads 512 contiguous
+// bytes per step); a short row (a few subfaults) gets a power-of-two group of
+// lanes with about four chunks each, several rows per warp pass.  Each lane
+// keeps its slice of x_vec in registers across rows that share it.  Products accumulate in FP32; FP8 rows are rescaled by their
 // per-(bin, 256-row block) scale after the dot product.
 #include "s2w_internal.cuh"
 
@@ -61,9 +62,27 @@ __device__ __forceinline__ float2 fp8x2_to_f2(unsigned short s) {
   return __half22float2(*reinterpret_cast<const __half2*>(&h));
 }
 
+// e4m3 -> f32 by moving bits: the sign to bit 31 and the 7 exponent+mantissa
+// bits to bits 26..20 gives an f32 whose value is the e4m3 value times
+// 2^-120 (exponent bias 127 - 7 = 120), exactly, subnormals included (the
+// e4m3 subnormals land on f32 subnormals).  The caller undoes the 2^-120:
+// 2^64 on the vector it multiplies, 2^56 on the sum.
+__device__ __forceinline__ float2 e4m3x2_scaled(unsigned w) {  // bytes 0 and 1 of w
+  return make_float2(__uint_as_float(((w << 24) & 0x80000000u) | ((w << 20) & 0x07f00000u)),
+                     __uint_as_float(((w << 16) & 0x80000000u) | ((w << 12) & 0x07f00000u)));
+}
+
 template <>
 struct Chunk<EL_FP8> {
   static constexpr int C = 8;
+  __device__ __forceinline__ static void unpack_scaled(const uint4& u, float2 (&g)[C]) {
+    const unsigned w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      g[2 * k] = e4m3x2_scaled(w[k]);
+      g[2 * k + 1] = e4m3x2_scaled(w[k] >> 16);
+    }
+  }
   __device__ __forceinline__ static void unpack(const uint4& u, float2 (&g)[C]) {
     const unsigned w[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
@@ -74,12 +93,14 @@ struct Chunk<EL_FP8> {
   }
 };
 
-// EL selects the unpacker (EL_BF16 also serves the hi/lo pair when HILO).
-template <int EL, bool HILO>
+// EL selects the unpacker (EL_BF16 also serves the hi/lo pair when HILO);
+// SHORT: rows of at most 64 chunks, shared by lane groups.
+template <int EL, bool HILO, bool SHORT>
 __global__ void __launch_bounds__(kThreads, 1) k_stream_dot(const StreamArgs a, int stage_rows) {
   using CH = Chunk<EL>;
   constexpr int C = CH::C;
-  constexpr int T = kMaxRowLen / (32 * C);  // chunk slots per lane
+  // chunk slots per lane: a short row gives each lane at most four chunks
+  constexpr int T = SHORT ? 4 : kMaxRowLen / (32 * C);
   extern __shared__ __align__(128) unsigned char sm[];
   uint64_t* full = reinterpret_cast<uint64_t*>(sm);
   uint64_t* empty = full + kStages;
@@ -128,41 +149,59 @@ __global__ void __launch_bounds__(kThreads, 1) k_stream_dot(const StreamArgs a, 
     return;
   }
 
-  // consumer warps
+  // consumer warps: a row is shared by `lpr` lanes (a power of two, chosen so
+  // a lane takes about four chunks of a short row), so a warp takes 32 / lpr
+  // rows per pass and the row sums need log2(lpr) shuffle steps
   const int nchunk = row_bytes / 16;
+  int lpr = 32;
+  if (SHORT)
+    while (lpr > 1 && 4 * (lpr / 2) >= nchunk) lpr >>= 1;
+  const int rpp = 32 / lpr;     // rows per warp pass
+  const int sub = lane % lpr;   // lane within its row group
+  const int grp = lane / lpr;   // row group within the warp
   float2 xr[T][C];
-  long long cur_vec = -1;
+  long long vec = -1, vec_end = 0;  // x_vec of rows [vec_end - rows_per_vec, vec_end); rows rise per lane
   for (int k = 0; k < nst; ++k) {
     const int s = k % kStages;
     if (!mbar_wait_bounded(full + s, (k / kStages) & 1, a.status, DEV_ERR_TIMEOUT_FULL)) return;
     const long long rs = r0 + static_cast<long long>(k) * stage_rows;
     const int nr = static_cast<int>(min(static_cast<long long>(stage_rows), r1 - rs));
-    for (int lr = warp; lr < nr; lr += kConsumerWarps) {
-      const long long f = rs + lr;
-      const long long vec = f / a.rows_per_vec;
-      if (vec != cur_vec) {
+    for (int base = warp * rpp; base < nr; base += kConsumerWarps * rpp) {
+      const int lr = base + grp;
+      const bool valid = lr < nr;
+      const long long f = rs + (valid ? lr : base);
+      if (f >= vec_end) {
+        vec = f / a.rows_per_vec;
+        vec_end = (vec + 1) * a.rows_per_vec;
         const float4* xv = reinterpret_cast<const float4*>(a.x + vec * a.x_stride);
 #pragma unroll
         for (int t = 0; t < T; ++t) {
-          const int c = lane + 32 * t;
+          const int c = sub + lpr * t;
 #pragma unroll
           for (int q = 0; q < C / 2; ++q) {
-            const float4 v = (c < nchunk) ? __ldg(xv + c * (C / 2) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 v = (c < nchunk) ? __ldg(xv + c * (C / 2) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (EL == EL_FP8) {  // 2^64: see e4m3x2_scaled
+              const float k64 = __uint_as_float((127u + 64u) << 23);
+              v = make_float4(v.x * k64, v.y * k64, v.z * k64, v.w * k64);
+            }
             xr[t][2 * q] = make_float2(v.x, v.y);
             xr[t][2 * q + 1] = make_float2(v.z, v.w);
           }
         }
-        cur_vec = vec;
       }
-      const uint4* row = reinterpret_cast<const uint4*>(buf + s * stage_bytes + lr * row_bytes);
-      const uint4* row_lo = reinterpret_cast<const uint4*>(buf_lo + s * stage_bytes + lr * row_bytes);
+      const int rrow = valid ? lr : base;
+      const uint4* row = reinterpret_cast<const uint4*>(buf + s * stage_bytes + rrow * row_bytes);
+      const uint4* row_lo = reinterpret_cast<const uint4*>(buf_lo + s * stage_bytes + rrow * row_bytes);
       float ar0 = 0.f, ai0 = 0.f, ar1 = 0.f, ai1 = 0.f;
 #pragma unroll
       for (int t = 0; t < T; ++t) {
-        const int c = lane + 32 * t;
-        if (c < nchunk) {
+        const int c = sub + lpr * t;
+        if (valid && c < nchunk) {
           float2 g[C];
-          CH::unpack(row[c], g);
+          if constexpr (EL == EL_FP8)
+            CH::unpack_scaled(row[c], g);
+          else
+            CH::unpack(row[c], g);
           if (HILO) {
             float2 gl[C];
             CH::unpack(row_lo[c], gl);
@@ -183,14 +222,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_stream_dot(const StreamArgs a, 
         }
       }
       float ar = ar0 + ar1, ai = ai0 + ai1;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
+      for (int o = lpr / 2; o > 0; o >>= 1) {
         ar += __shfl_xor_sync(0xffffffffu, ar, o);
         ai += __shfl_xor_sync(0xffffffffu, ai, o);
       }
-      if (lane == 0) {
+      if (valid && sub == 0) {
         if (EL == EL_FP8) {
-          const float sc = a.scale[vec * a.nblk + (f % a.rows_per_vec) / 256];
+          const float sc = a.scale[vec * a.nblk + (f - (vec_end - a.rows_per_vec)) / 256] *
+                           __uint_as_float((127u + 56u) << 23);  // 2^56: see e4m3x2_scaled
           ar *= sc;
           ai *= sc;
         }
@@ -374,7 +413,7 @@ cudaError_t launch_tt(const StreamTArgs& a, int num_sms, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <int EL, bool HILO>
+template <int EL, bool HILO, bool SHORT>
 cudaError_t launch_t(const StreamArgs& a, int num_sms, cudaStream_t st) {
   constexpr int C = Chunk<EL>::C;
   const int row_bytes = a.row_len * (16 / C);
@@ -383,15 +422,19 @@ cudaError_t launch_t(const StreamArgs& a, int num_sms, cudaStream_t st) {
   if (stage_rows >= kConsumerWarps) stage_rows -= stage_rows % kConsumerWarps;
   if (stage_rows < 1) stage_rows = 1;
   const size_t smem = 128 + static_cast<size_t>(kStages) * stage_rows * row_bytes * (HILO ? 2 : 1);
-  cudaError_t e = cudaFuncSetAttribute(k_stream_dot<EL, HILO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_stream_dot<EL, HILO, SHORT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   long long grid = num_sms;
   if (grid > a.F) grid = a.F;
   if (grid < 1) grid = 1;
-  k_stream_dot<EL, HILO><<<static_cast<unsigned>(grid), kThreads, smem, st>>>(a, stage_rows);
+  k_stream_dot<EL, HILO, SHORT><<<static_cast<unsigned>(grid), kThreads, smem, st>>>(a, stage_rows);
   return cudaGetLastError();
 }
+
+// Rows of at most 64 16-byte chunks (C complex entries each) take the
+// lane-group variant.
+bool short_rows(const StreamArgs& a, int C) { return a.row_len / C <= 64; }
 
 }  // namespace
 
@@ -399,10 +442,18 @@ cudaError_t launch_stream_dot(const StreamArgs& a, int num_sms, cudaStream_t st)
   if (a.F <= 0) return cudaSuccess;
   if (a.row_len <= 0 || a.row_len > kMaxRowLen || (a.row_len % 8) != 0) return cudaErrorInvalidValue;
   switch (a.el) {
-    case EL_FP32: return launch_t<EL_FP32, false>(a, num_sms, st);
-    case EL_BF16: return launch_t<EL_BF16, false>(a, num_sms, st);
-    case EL_BF16_HILO: return launch_t<EL_BF16, true>(a, num_sms, st);
-    case EL_FP8: return launch_t<EL_FP8, false>(a, num_sms, st);
+    case EL_FP32:
+      return short_rows(a, 2) ? launch_t<EL_FP32, false, true>(a, num_sms, st)
+                              : launch_t<EL_FP32, false, false>(a, num_sms, st);
+    case EL_BF16:
+      return short_rows(a, 4) ? launch_t<EL_BF16, false, true>(a, num_sms, st)
+                              : launch_t<EL_BF16, false, false>(a, num_sms, st);
+    case EL_BF16_HILO:
+      return short_rows(a, 4) ? launch_t<EL_BF16, true, true>(a, num_sms, st)
+                              : launch_t<EL_BF16, true, false>(a, num_sms, st);
+    case EL_FP8:
+      return short_rows(a, 8) ? launch_t<EL_FP8, false, true>(a, num_sms, st)
+                              : launch_t<EL_FP8, false, false>(a, num_sms, st);
     default: return cudaErrorInvalidValue;
   }
 }

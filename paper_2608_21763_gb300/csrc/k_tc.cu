@@ -186,9 +186,14 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
 // CL > 1: clusters of CL CTAs take CL adjacent M tiles of the same (bin, K
 // chunk); each CTA loads 1/CL of the B tile and multicasts it to all of them,
 // and every CTA's MMA releases a stage in all of them (empty barriers count CL).
+// Split precision (a_lo / b_lo): an operand stored as hi + lo BF16 parts has
+// both parts in every stage, and each K step issues A B, then A B_lo and/or
+// A_lo B into the same FP32 accumulator (the A_lo B_lo term, ~2^-18
+// relative, is dropped).
 template <int BK, int CL>
 __global__ void __launch_bounds__(kTcThreads, 1)
-    k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
+    k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB2, const TcArgs a) {
   constexpr int kA = kBlockM * BK * 2;
   constexpr uint16_t kMask = static_cast<uint16_t>((1u << CL) - 1u);
   const uint32_t crank = CL > 1 ? cluster_ctarank() : 0u;
@@ -198,7 +203,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
   const int N = a.N;
   const int b_bytes = N * BK * 2;
-  const int stage_bytes = kA + b_bytes;
+  const int a_all = kA * (1 + a.a_lo);                 // A (+ A_lo) bytes per stage
+  const int stage_bytes = a_all + b_bytes * (1 + a.b_lo);
   const int S = a.stages;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * stage_bytes);
   uint64_t* empty = full + S;
@@ -259,12 +265,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           unsigned char* sa = smem + s * stage_bytes;
           mbar_arrive_expect_tx(full + s, stage_bytes);
           tma_load_3d(sa, &tmA, kb * BK, mt * kBlockM, l, full + s);
-          if (CL == 1) {
-            for (int c = 0; c < n_mma; ++c)
-              tma_load_3d(sa + kA + c * n_mma_cols * BK * 2, &tmB, kb * BK, c * n_mma_cols, l, full + s);
-          } else {
-            tma_load_3d_mc(sa + kA + crank * slice_rows * BK * 2, &tmB, kb * BK, static_cast<int>(crank) * slice_rows,
-                           l, full + s, kMask);
+          if (a.a_lo) tma_load_3d(sa + kA, &tmA2, kb * BK, mt * kBlockM, l, full + s);
+          for (int h = 0; h <= a.b_lo; ++h) {
+            const CUtensorMap* tb = h ? &tmB2 : &tmB;
+            unsigned char* sb = sa + a_all + h * b_bytes;
+            if (CL == 1) {
+              for (int c = 0; c < n_mma; ++c)
+                tma_load_3d(sb + c * n_mma_cols * BK * 2, tb, kb * BK, c * n_mma_cols, l, full + s);
+            } else {
+              tma_load_3d_mc(sb + crank * slice_rows * BK * 2, tb, kb * BK, static_cast<int>(crank) * slice_rows, l,
+                             full + s, kMask);
+            }
           }
         }
       }
@@ -297,13 +308,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           }
           tc_fence_after();
           const uint32_t sa = smem_u32(smem + s * stage_bytes);
-          const uint32_t sb = sa + kA;
+          const uint32_t sb = sa + a_all;
 #pragma unroll
           for (int k = 0; k < BK / 16; ++k) {
             const uint64_t ad = sdesc_sw<BK>(sa + k * 32);
             for (int c = 0; c < n_mma; ++c) {
-              const uint64_t bd = sdesc_sw<BK>(sb + c * n_mma_cols * BK * 2 + k * 32);
+              const uint32_t boff = c * n_mma_cols * BK * 2 + k * 32;
+              const uint64_t bd = sdesc_sw<BK>(sb + boff);
               tc_mma_bf16(tmem + c * n_mma_cols, ad, bd, idesc, (kb > kb0 || k > 0) ? 1u : 0u);
+              if (a.b_lo) tc_mma_bf16(tmem + c * n_mma_cols, ad, sdesc_sw<BK>(sb + b_bytes + boff), idesc, 1u);
+              if (a.a_lo) tc_mma_bf16(tmem + c * n_mma_cols, sdesc_sw<BK>(sa + kA + k * 32), bd, idesc, 1u);
             }
           }
           if (CL == 1)
@@ -374,38 +388,54 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (CL > 1) cluster_sync_all();  // no CTA leaves while a peer may still signal it
 }
 
-// Stage-1 B operand from the slip spectra shat[l][b][Ns_pad] (complex FP32):
-// rows 2b / 2b+1 of Bp[l][N_alloc][2 Ns_pad] (BF16, round to nearest even).
-__global__ void k_pack_stage1_b(const float2* __restrict__ shat, int B, int Ns_pad, int Nb, int N_alloc,
-                                __nv_bfloat162* __restrict__ Bp) {
-  const long long total = static_cast<long long>(Nb) * B * Ns_pad;
-  for (long long e = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
-       e += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const long long j = e % Ns_pad;
-    const long long b = (e / Ns_pad) % B;
-    const long long l = e / (static_cast<long long>(Ns_pad) * B);
-    const float2 v = shat[e];
-    __nv_bfloat162* row = Bp + (l * N_alloc + 2 * b) * Ns_pad;  // Ns_pad bf16 pairs per row
-    row[j] = __floats2bfloat162_rn(v.x, -v.y);
-    row[Ns_pad + j] = __floats2bfloat162_rn(v.y, v.x);
-  }
-}
-
-// Stage-2 B operand from the adjoint spectra, staging [l][o][nc] (complex
-// FP32) at grid columns c0 .. c0+nc-1: rows 2o / 2o+1 of
-// Pp[l][N_alloc][Kc] (Kc complex columns = 2 Kc BF16 per row).
-__global__ void k_pack_stage2_b(const float2* __restrict__ src, int Nb, int No, long long nc, long long c0,
-                                long long Kc, int N_alloc, __nv_bfloat162* __restrict__ Pp) {
-  const long long total = static_cast<long long>(Nb) * No * nc;
+// B operand of the real embedding from complex FP32 x[l][t][c] (element
+// src[l*s_l + t*s_t + c], c < nc): rows 2t / 2t+1 of dst[l][N_alloc][2 Kc]
+// (BF16, round to nearest even) at complex columns c0 + c:
+//   plain (D = A x):        row 2t = (Re x, -Im x),  row 2t+1 = (Im x,  Re x)
+//   conj  (D = conj(A) x):  row 2t = (Re x,  Im x),  row 2t+1 = (Im x, -Re x)
+// With `lo`, lo = bf16(v - hi) holds the low-order part of every entry.
+__global__ void k_pack_b(const float2* __restrict__ src, int Nb, int T, long long nc, long long s_l, long long s_t,
+                         long long c0, long long Kc, int N_alloc, int conj, __nv_bfloat162* __restrict__ hi,
+                         __nv_bfloat162* __restrict__ lo) {
+  const long long total = static_cast<long long>(Nb) * T * nc;
   for (long long e = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
        e += static_cast<long long>(gridDim.x) * blockDim.x) {
     const long long c = e % nc;
-    const long long o = (e / nc) % No;
-    const long long l = e / (nc * No);
-    const float2 v = src[e];
-    __nv_bfloat162* row = Pp + (l * N_alloc + 2 * o) * Kc;
-    row[c0 + c] = __floats2bfloat162_rn(v.x, -v.y);
-    row[Kc + c0 + c] = __floats2bfloat162_rn(v.y, v.x);
+    const long long t = (e / nc) % T;
+    const long long l = e / (nc * T);
+    const float2 v = src[l * s_l + t * s_t + c];
+    const float2 r0 = conj ? make_float2(v.x, v.y) : make_float2(v.x, -v.y);
+    const float2 r1 = conj ? make_float2(v.y, -v.x) : make_float2(v.y, v.x);
+    const long long o0 = (l * N_alloc + 2 * t) * Kc + c0 + c;
+    const __nv_bfloat162 h0 = __floats2bfloat162_rn(r0.x, r0.y);
+    const __nv_bfloat162 h1 = __floats2bfloat162_rn(r1.x, r1.y);
+    hi[o0] = h0;
+    hi[o0 + Kc] = h1;
+    if (lo != nullptr) {
+      lo[o0] = __floats2bfloat162_rn(r0.x - __low2float(h0), r0.y - __high2float(h0));
+      lo[o0 + Kc] = __floats2bfloat162_rn(r1.x - __low2float(h1), r1.y - __high2float(h1));
+    }
+  }
+}
+
+// A operand (K-major, complex pairs interleaved along K) from complex FP32
+// x[l][r][c] (src[l*s_l + r*s_r + c*s_c], r < rows, c < nc):
+// dst[(l*rows_total + r0 + r)*Kc + c0 + c] hi (and lo) BF16 pairs.  With
+// s_r = 1 and s_c = the source row pitch this is a transposing copy.
+__global__ void k_pack_a(const float2* __restrict__ src, int Nb, int rows, long long nc, long long s_l,
+                         long long s_r, long long s_c, long long rows_total, long long r0, long long c0, long long Kc,
+                         __nv_bfloat162* __restrict__ hi, __nv_bfloat162* __restrict__ lo) {
+  const long long total = static_cast<long long>(Nb) * rows * nc;
+  for (long long e = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long c = e % nc;
+    const long long r = (e / nc) % rows;
+    const long long l = e / (nc * rows);
+    const float2 v = src[l * s_l + r * s_r + c * s_c];
+    const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
+    const long long o = (l * rows_total + r0 + r) * Kc + c0 + c;
+    hi[o] = h;
+    if (lo != nullptr) lo[o] = __floats2bfloat162_rn(v.x - __low2float(h), v.y - __high2float(h));
   }
 }
 
@@ -660,24 +690,28 @@ cudaError_t tc_encode_3d(CUtensorMap* out, const void* base, long long K, long l
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-int tc_block_k(int N) { return N > 256 ? 32 : 64; }
+int tc_block_k(int N, int split) { return (N > 256 || (split && N > 128)) ? 32 : 64; }
 
-int tc_stages_for(int N) {
-  const int bk = tc_block_k(N);
-  const int stage = kBlockM * bk * 2 + N * bk * 2;
-  int s = kSmemBudget / stage;
+namespace {
+int tc_stage_bytes(int N, int a_lo, int b_lo) {
+  const int bk = tc_block_k(N, a_lo | b_lo);
+  return kBlockM * bk * 2 * (1 + a_lo) + N * bk * 2 * (1 + b_lo);
+}
+}  // namespace
+
+int tc_stages_for(int N, int a_lo, int b_lo) {
+  int s = kSmemBudget / tc_stage_bytes(N, a_lo, b_lo);
   if (s > 8) s = 8;
   return s;
 }
 
-size_t tc_smem_bytes(int N, int stages) {
-  const int bk = tc_block_k(N);
-  return 1024 + static_cast<size_t>(stages) * (kBlockM * bk * 2 + N * bk * 2) + 8 * (2 * stages + 2) + 16;
+size_t tc_smem_bytes(int N, int stages, int a_lo, int b_lo) {
+  return 1024 + static_cast<size_t>(stages) * tc_stage_bytes(N, a_lo, b_lo) + 8 * (2 * stages + 2) + 16;
 }
 
 template <int BK, int CL>
-cudaError_t launch_tc_cl(const CUtensorMap& tmA, const CUtensorMap& tmB, const TcArgs& a, int num_sms, size_t smem,
-                         cudaStream_t st) {
+cudaError_t launch_tc_cl(const CUtensorMap& tmA, const CUtensorMap& tmB, const CUtensorMap& tmA2,
+                         const CUtensorMap& tmB2, const TcArgs& a, int num_sms, size_t smem, cudaStream_t st) {
   auto kern = k_tc_gemm<BK, CL>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
@@ -706,29 +740,34 @@ cudaError_t launch_tc_cl(const CUtensorMap& tmA, const CUtensorMap& tmB, const T
   }
   if (nclusters > cunits) nclusters = cunits;
   cfg.gridDim = dim3(static_cast<unsigned>(nclusters * CL));
-  e = cudaLaunchKernelEx(&cfg, kern, tmA, tmB, a);
+  e = cudaLaunchKernelEx(&cfg, kern, tmA, tmB, tmA2, tmB2, a);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
 cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const TcArgs& a, int num_sms,
-                           cudaStream_t st) {
+                           cudaStream_t st, const CUtensorMap* tmA2, const CUtensorMap* tmB2) {
   const long long units = static_cast<long long>(a.Nb) * a.m_tiles * a.n_kchunks;
   if (units <= 0) return cudaSuccess;
   if (a.N < 16 || a.N > 512 || a.N % 16 != 0 || (a.N > 256 && a.N % 256 != 0) || a.stages < 2)
     return cudaErrorInvalidValue;
+  if ((a.a_lo != 0 && a.a_lo != 1) || (a.b_lo != 0 && a.b_lo != 1) || (a.a_lo && !tmA2) || (a.b_lo && !tmB2))
+    return cudaErrorInvalidValue;
   const int CL = a.cluster < 1 ? 1 : a.cluster;
   if (CL != 1 && CL != 2 && CL != 4) return cudaErrorInvalidValue;
   if (CL > 1 && (a.N / CL < 8 || (a.N / CL) % 8 != 0 || a.N / CL > 256)) return cudaErrorInvalidValue;
-  const size_t smem = tc_smem_bytes(a.N, a.stages);
-  if (tc_block_k(a.N) == 64) {
-    if (CL == 1) return launch_tc_cl<64, 1>(tmA, tmB, a, num_sms, smem, st);
-    if (CL == 2) return launch_tc_cl<64, 2>(tmA, tmB, a, num_sms, smem, st);
-    return launch_tc_cl<64, 4>(tmA, tmB, a, num_sms, smem, st);
+  const size_t smem = tc_smem_bytes(a.N, a.stages, a.a_lo, a.b_lo);
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  const CUtensorMap& a2 = a.a_lo ? *tmA2 : tmA;  // unused unless a_lo / b_lo
+  const CUtensorMap& b2 = a.b_lo ? *tmB2 : tmB;
+  if (tc_block_k(a.N, a.a_lo | a.b_lo) == 64) {
+    if (CL == 1) return launch_tc_cl<64, 1>(tmA, tmB, a2, b2, a, num_sms, smem, st);
+    if (CL == 2) return launch_tc_cl<64, 2>(tmA, tmB, a2, b2, a, num_sms, smem, st);
+    return launch_tc_cl<64, 4>(tmA, tmB, a2, b2, a, num_sms, smem, st);
   }
-  if (CL == 1) return launch_tc_cl<32, 1>(tmA, tmB, a, num_sms, smem, st);
-  if (CL == 2) return launch_tc_cl<32, 2>(tmA, tmB, a, num_sms, smem, st);
-  return launch_tc_cl<32, 4>(tmA, tmB, a, num_sms, smem, st);
+  if (CL == 1) return launch_tc_cl<32, 1>(tmA, tmB, a2, b2, a, num_sms, smem, st);
+  if (CL == 2) return launch_tc_cl<32, 2>(tmA, tmB, a2, b2, a, num_sms, smem, st);
+  return launch_tc_cl<32, 4>(tmA, tmB, a2, b2, a, num_sms, smem, st);
 }
 
 cudaError_t launch_tc_retransform(const CUtensorMap& tmT, const TcRtArgs& a, int num_sms, cudaStream_t st) {
@@ -748,17 +787,22 @@ cudaError_t launch_tc_retransform(const CUtensorMap& tmT, const TcRtArgs& a, int
   return cudaGetLastError();
 }
 
-cudaError_t launch_pack_stage1_b(const float2* shat, int B, int Ns_pad, int Nb, int N_alloc, void* Bp,
-                                 cudaStream_t st) {
-  k_pack_stage1_b<<<grid_for_tc(static_cast<long long>(Nb) * B * Ns_pad), 256, 0, st>>>(
-      shat, B, Ns_pad, Nb, N_alloc, static_cast<__nv_bfloat162*>(Bp));
+cudaError_t launch_pack_b(const float2* src, int Nb, int T, long long nc, long long s_l, long long s_t, long long c0,
+                          long long Kc, int N_alloc, int conj, void* hi, void* lo, cudaStream_t st) {
+  const long long total = static_cast<long long>(Nb) * T * nc;
+  if (total <= 0) return cudaSuccess;
+  k_pack_b<<<grid_for_tc(total), 256, 0, st>>>(src, Nb, T, nc, s_l, s_t, c0, Kc, N_alloc, conj,
+                                               static_cast<__nv_bfloat162*>(hi), static_cast<__nv_bfloat162*>(lo));
   return cudaGetLastError();
 }
 
-cudaError_t launch_pack_stage2_b(const float2* src, int Nb, int No, long long nc, long long c0, long long Kc,
-                                 int N_alloc, void* Pp, cudaStream_t st) {
-  k_pack_stage2_b<<<grid_for_tc(static_cast<long long>(Nb) * No * nc), 256, 0, st>>>(
-      src, Nb, No, nc, c0, Kc, N_alloc, static_cast<__nv_bfloat162*>(Pp));
+cudaError_t launch_pack_a(const float2* src, int Nb, int rows, long long nc, long long s_l, long long s_r,
+                          long long s_c, long long rows_total, long long r0, long long c0, long long Kc, void* hi,
+                          void* lo, cudaStream_t st) {
+  const long long total = static_cast<long long>(Nb) * rows * nc;
+  if (total <= 0) return cudaSuccess;
+  k_pack_a<<<grid_for_tc(total), 256, 0, st>>>(src, Nb, rows, nc, s_l, s_r, s_c, rows_total, r0, c0, Kc,
+                                               static_cast<__nv_bfloat162*>(hi), static_cast<__nv_bfloat162*>(lo));
   return cudaGetLastError();
 }
 

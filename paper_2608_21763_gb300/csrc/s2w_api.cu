@@ -58,7 +58,7 @@ struct s2w_ctx {
   int tc_n1max = 0;      // B-operand rows of stage 1 (2 x sub-batch, padded)
   int tc_n2 = 0;         // B-operand rows of stage 2 (2 x No, padded)
   long long Ng_pad2 = 0; // complex columns per row of the stage-2 operands
-  int tc_kbpc = 64;      // 64-element K blocks per stage-2 chunk
+  int tc_kbpc = 64;      // K blocks per stage-2 chunk
   int tc_nkc = 1;        // stage-2 K chunks
   int tc_cl1 = 1;        // cluster size of the stage-1 GEMM (B tiles multicast)
   int tc_cl2 = 1;        // cluster size of the stage-2 GEMM
@@ -76,8 +76,12 @@ struct s2w_ctx {
   cudaStream_t cap_stream = nullptr;
   std::vector<GraphEntry> graphs;
   unsigned long long graph_clock = 0;
+  bool tc_split = false;    // BF16 hi/lo operands and activations (three MMAs per K step)
+  void* tc_bp1_lo = nullptr;  // split: low-order parts of tc_bp1, tc_vhat, tc_p2
+  void* tc_vhat_lo = nullptr;
+  void* tc_p2_lo = nullptr;
   void* tc_bp1 = nullptr;   // [Nb][tc_n1max][2 Ns_pad] bf16
-  float2* tc_mhat = nullptr;  // [Nb][b][Ng] complex FP32
+  void* tc_mhat = nullptr;  // [Nb][b][Ng] BF16 pairs (complex FP32 when split)
   void* tc_vhat = nullptr;  // [Nb][tc_bsub][Ng_pad2] bf16 pairs
   float2* tc_part = nullptr;  // [Nb][nkc][b][No] complex FP32
   void* tc_p2 = nullptr;    // [Nb][tc_n2][Ng_pad2] bf16 pairs
@@ -226,7 +230,7 @@ void free_all(s2w_ctx* c) {
   c->ev_free.clear();
   void* ps[] = {c->G, c->G_lo, c->G_scale, c->P, c->tw, c->ws_slip, c->ws_shat, c->ws_mhat,
                 c->ws_vhat, c->ws_part, c->ws_q, c->ws_seafloor, c->d_status, c->tc_bp1, c->ws_rhat, c->ws_gpart, c->ws_resid, c->ws_d, c->ws_loss,
-                c->tc_mhat, c->tc_vhat, c->tc_part, c->tc_p2, c->tc_T};
+                c->tc_mhat, c->tc_vhat, c->tc_part, c->tc_p2, c->tc_T, c->tc_bp1_lo, c->tc_vhat_lo, c->tc_p2_lo};
   for (void* p : ps)
     if (p) cudaFree(p);
 }
@@ -292,19 +296,25 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
       CK(launch_rfft_rows(slip_d + static_cast<long long>(b0) * Ns * Nt, Bs * Ns, static_cast<int>(Nt),
                           static_cast<int>(Nt), ctx->tw, ctx->ws_shat, Bs * Ns_pad, Ns, Ns_pad, st));
     }
+    const int sp = ctx->tc_split ? 1 : 0;
     {
       StageTimer t(ctx, 6, st);
-      CK(launch_pack_stage1_b(ctx->ws_shat, Bs, static_cast<int>(Ns_pad), static_cast<int>(Nb), ctx->tc_n1max,
-                              ctx->tc_bp1, st));
+      CK(launch_pack_b(ctx->ws_shat, static_cast<int>(Nb), Bs, Ns_pad, static_cast<long long>(Bs) * Ns_pad, Ns_pad, 0,
+                       Ns_pad, ctx->tc_n1max, 0, ctx->tc_bp1, ctx->tc_bp1_lo, st));
     }
     {
       StageTimer t(ctx, 1, st);
-      CUtensorMap ta, tb;
-      const int bk = tc_block_k(N1);
+      CUtensorMap ta, tb, ta2, tb2;
+      const int bk = tc_block_k(N1, sp);
       const int m1 = static_cast<int>((Ng + 127) / 128);
       const int cl = fit_cluster(ctx->tc_cl1, N1, m1);
+      const int brows = cl > 1 ? N1 / cl : (N1 > 256 ? 256 : N1);
       CK(tc_encode_3d(&ta, ctx->G, K1, Ng, Nb, K1, 128, bk));
-      CK(tc_encode_3d(&tb, ctx->tc_bp1, K1, ctx->tc_n1max, Nb, K1, cl > 1 ? N1 / cl : (N1 > 256 ? 256 : N1), bk));
+      CK(tc_encode_3d(&tb, ctx->tc_bp1, K1, ctx->tc_n1max, Nb, K1, brows, bk));
+      if (sp) {
+        CK(tc_encode_3d(&ta2, ctx->G_lo, K1, Ng, Nb, K1, 128, bk));
+        CK(tc_encode_3d(&tb2, ctx->tc_bp1_lo, K1, ctx->tc_n1max, Nb, K1, brows, bk));
+      }
       TcArgs a{};
       a.N = N1;
       a.K = K1;
@@ -313,20 +323,30 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
       a.m_tiles = static_cast<int>((Ng + 127) / 128);
       a.n_kchunks = 1;
       a.kblocks_per_chunk = (K1 + bk - 1) / bk;
-      a.stages = tc_stages_for(N1);
+      a.stages = tc_stages_for(N1, sp, sp);
+      a.a_lo = sp;
+      a.b_lo = sp;
       a.tmem_cols = N1 <= 32 ? 32 : (N1 <= 64 ? 64 : (N1 <= 128 ? 128 : (N1 <= 256 ? 256 : 512)));
       a.cluster = cl;
       a.epi = 0;
       a.T = Bs;
-      a.out = nullptr;
-      // the GEMM retransform rounds the seafloor spectra to BF16 anyway
-      a.out_bf = reinterpret_cast<__nv_bfloat162*>(ctx->tc_mhat);
+      // the GEMM retransform rounds the seafloor spectra to BF16 anyway; the
+      // split path keeps them in FP32 for the FFT retransform
+      a.out = sp ? static_cast<float2*>(ctx->tc_mhat) : nullptr;
+      a.out_bf = sp ? nullptr : static_cast<__nv_bfloat162*>(ctx->tc_mhat);
       a.ld_l = static_cast<long long>(Bs) * Ng;
       a.ld_t = Ng;
       a.status = ctx->d_status;
-      CK(launch_tc_gemm(ta, tb, a, ctx->num_sms, st));
+      CK(launch_tc_gemm(ta, tb, a, ctx->num_sms, st, sp ? &ta2 : nullptr, sp ? &tb2 : nullptr));
     }
-    {
+    if (sp) {
+      StageTimer t(ctx, 2, st);
+      CK(launch_retransform(static_cast<const float2*>(ctx->tc_mhat), Ng, static_cast<long long>(Bs) * Ng,
+                            static_cast<int>(Nt), ctx->tw, static_cast<float>(1.0 / ctx->opts.dt), ctx->opts.dt_mode,
+                            nullptr, static_cast<long long>(ctx->tc_bsub) * ctx->Ng_pad2, nullptr, st, Bs, Ng,
+                            ctx->Ng_pad2, static_cast<__nv_bfloat162*>(ctx->tc_vhat),
+                            static_cast<__nv_bfloat162*>(ctx->tc_vhat_lo)));
+    } else {
       StageTimer t(ctx, 2, st);
       TcRtArgs r{};
       r.mhat_bf = reinterpret_cast<const __nv_bfloat162*>(ctx->tc_mhat);
@@ -343,11 +363,16 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
     }
     {
       StageTimer t(ctx, 3, st);
-      CUtensorMap ta, tb;
+      CUtensorMap ta, tb, ta2, tb2;
       const int m2 = (Bs + 127) / 128;
       const int cl = fit_cluster(ctx->tc_cl2, ctx->tc_n2, m2);
-      CK(tc_encode_3d(&ta, ctx->tc_vhat, K2, ctx->tc_bsub, Nb, K2, 128));
-      CK(tc_encode_3d(&tb, ctx->tc_p2, K2, ctx->tc_n2, Nb, K2, ctx->tc_n2 / cl));
+      const int bk = tc_block_k(ctx->tc_n2, sp);
+      CK(tc_encode_3d(&ta, ctx->tc_vhat, K2, ctx->tc_bsub, Nb, K2, 128, bk));
+      CK(tc_encode_3d(&tb, ctx->tc_p2, K2, ctx->tc_n2, Nb, K2, ctx->tc_n2 / cl, bk));
+      if (sp) {
+        CK(tc_encode_3d(&ta2, ctx->tc_vhat_lo, K2, ctx->tc_bsub, Nb, K2, 128, bk));
+        CK(tc_encode_3d(&tb2, ctx->tc_p2_lo, K2, ctx->tc_n2, Nb, K2, ctx->tc_n2 / cl, bk));
+      }
       TcArgs a{};
       a.N = ctx->tc_n2;
       a.K = static_cast<int>(K2);
@@ -356,14 +381,16 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
       a.m_tiles = (Bs + 127) / 128;
       a.n_kchunks = ctx->tc_nkc;
       a.kblocks_per_chunk = ctx->tc_kbpc;
-      a.stages = tc_stages_for(ctx->tc_n2);
+      a.stages = tc_stages_for(ctx->tc_n2, sp, sp);
+      a.a_lo = sp;
+      a.b_lo = sp;
       a.tmem_cols = ctx->tc_n2 <= 32 ? 32 : (ctx->tc_n2 <= 64 ? 64 : (ctx->tc_n2 <= 128 ? 128 : 256));
       a.cluster = cl;
       a.epi = 1;
       a.T = static_cast<int>(No);
       a.out = ctx->tc_part;
       a.status = ctx->d_status;
-      CK(launch_tc_gemm(ta, tb, a, ctx->num_sms, st));
+      CK(launch_tc_gemm(ta, tb, a, ctx->num_sms, st, sp ? &ta2 : nullptr, sp ? &tb2 : nullptr));
     }
     {
       StageTimer t(ctx, 4, st);
@@ -427,8 +454,8 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
   if (o.engine < S2W_ENGINE_AUTO || o.engine > S2W_ENGINE_TENSOR) return fail(nullptr, S2W_ERR_ARG, "engine=%d", o.engine);
   if (o.tc_cluster != 0 && o.tc_cluster != 1 && o.tc_cluster != 2 && o.tc_cluster != 4)
     return fail(nullptr, S2W_ERR_ARG, "tc_cluster=%d: 0, 1, 2 or 4", o.tc_cluster);
-  if (o.engine == S2W_ENGINE_TENSOR && o.prec_g != S2W_PREC_BF16)
-    return fail(nullptr, S2W_ERR_UNSUPPORTED, "the tensor engine needs prec_g = BF16");
+  if (o.engine == S2W_ENGINE_TENSOR && o.prec_g != S2W_PREC_BF16 && o.prec_g != S2W_PREC_BF16_HILO)
+    return fail(nullptr, S2W_ERR_UNSUPPORTED, "the tensor engine needs prec_g = BF16 or BF16_HILO");
   if (o.engine == S2W_ENGINE_TENSOR && 2 * No > 256)
     return fail(nullptr, S2W_ERR_UNSUPPORTED, "the tensor engine needs No <= 128");
   int ndev = 0;
@@ -498,10 +525,12 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
   if ((e = dalloc(&ctx->ws_loss, sizeof(float) * B)) != cudaSuccess) return bad(e, "losses");
   if ((e = dalloc(&ctx->ws_gpart, sizeof(float2) * Nb * ctx->adj_nchunk * ctx->Ns_pad)) != cudaSuccess)
     return bad(e, "adjoint partials");
-  ctx->tc_on = o.prec_g == S2W_PREC_BF16 && 2 * No <= 256 &&
+  ctx->tc_on = (o.prec_g == S2W_PREC_BF16 || o.prec_g == S2W_PREC_BF16_HILO) && 2 * No <= 256 &&
                (o.engine == S2W_ENGINE_TENSOR || (o.engine == S2W_ENGINE_AUTO && o.max_batch >= 2));
+  ctx->tc_split = ctx->tc_on && o.prec_g == S2W_PREC_BF16_HILO;
   if (ctx->tc_on) {
-    ctx->tc_bsub = static_cast<int>(std::min<long long>(B, 256));
+    // split operands double the B tiles: sub-batches of up to 128 ruptures
+    ctx->tc_bsub = static_cast<int>(std::min<long long>(B, ctx->tc_split ? 128 : 256));
     ctx->tc_cl1 = o.tc_cluster > 0 ? o.tc_cluster : kDefaultCluster;
     ctx->tc_cl2 = o.tc_cluster > 0 ? o.tc_cluster : kDefaultCluster;
     ctx->tc_n1max = static_cast<int>(round_up(2 * ctx->tc_bsub, 16));
@@ -510,16 +539,18 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
     ctx->Ng_pad2 = round_up(Ng, 8);
     // stage-2 split-K: enough work units for every SM (about 4 each) and no
     // more, so the chunk partials stay small
-    const long long nk2 = (2 * ctx->Ng_pad2 + 63) / 64;
+    const int bk2 = tc_block_k(ctx->tc_n2, ctx->tc_split ? 1 : 0);
+    const long long nk2 = (2 * ctx->Ng_pad2 + bk2 - 1) / bk2;
     const long long mt2 = (ctx->tc_bsub + 127) / 128;
     long long nkc = (4LL * ctx->num_sms + Nb * mt2 - 1) / (Nb * mt2);
     nkc = std::max(1LL, std::min(nkc, nk2));
     ctx->tc_kbpc = static_cast<int>((nk2 + nkc - 1) / nkc);
     ctx->tc_nkc = static_cast<int>((nk2 + ctx->tc_kbpc - 1) / ctx->tc_kbpc);
     const long long bs = ctx->tc_bsub;
+    const bool sp = ctx->tc_split;
     if ((e = dalloc(&ctx->tc_bp1, 2ull * Nb * ctx->tc_n1max * 2 * ctx->Ns_pad)) != cudaSuccess)
       return bad(e, "tensor stage-1 operand");
-    if ((e = dalloc(&ctx->tc_mhat, sizeof(__nv_bfloat162) * Nb * bs * Ng)) != cudaSuccess)
+    if ((e = dalloc(&ctx->tc_mhat, (sp ? sizeof(float2) : sizeof(__nv_bfloat162)) * Nb * bs * Ng)) != cudaSuccess)
       return bad(e, "tensor seafloor spectra");
     if ((e = dalloc(&ctx->tc_vhat, 4ull * Nb * bs * ctx->Ng_pad2)) != cudaSuccess)
       return bad(e, "tensor velocity spectra");
@@ -527,7 +558,17 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
       return bad(e, "tensor stage-2 partials");
     if ((e = dalloc(&ctx->tc_p2, 4ull * Nb * ctx->tc_n2 * ctx->Ng_pad2)) != cudaSuccess)
       return bad(e, "tensor stage-2 operand");
-    if (Nt <= 256) {
+    if (sp) {
+      if ((e = dalloc(&ctx->tc_bp1_lo, 2ull * Nb * ctx->tc_n1max * 2 * ctx->Ns_pad)) != cudaSuccess)
+        return bad(e, "tensor stage-1 operand (lo)");
+      if ((e = dalloc(&ctx->tc_vhat_lo, 4ull * Nb * bs * ctx->Ng_pad2)) != cudaSuccess)
+        return bad(e, "tensor velocity spectra (lo)");
+      if ((e = dalloc(&ctx->tc_p2_lo, 4ull * Nb * ctx->tc_n2 * ctx->Ng_pad2)) != cudaSuccess)
+        return bad(e, "tensor stage-2 operand (lo)");
+    }
+    // the GEMM retransform serves BF16 activations; the split path keeps the
+    // FFT retransform in FP32
+    if (Nt <= 256 && !sp) {
       const std::vector<__nv_bfloat16> T = retransform_matrix(Nt, o.dt_mode, o.dt);
       if ((e = dalloc(&ctx->tc_T, sizeof(__nv_bfloat16) * T.size())) != cudaSuccess)
         return bad(e, "retransform matrix");
@@ -648,8 +689,8 @@ int s2w_load_adjoint(s2w_ctx* ctx, int g0, int ng, const float* P, void* stream)
                               ctx->opts.prec_p, ctx->P, st));
       if (ctx->tc_on) {
         ctx->launches += 1;
-        CK(launch_pack_stage2_b(stage_s, static_cast<int>(Nb), static_cast<int>(No), rc, g0 + c, ctx->Ng_pad2,
-                                ctx->tc_n2, ctx->tc_p2, st));
+        CK(launch_pack_b(stage_s, static_cast<int>(Nb), static_cast<int>(No), rc, No * rc, rc, g0 + c, ctx->Ng_pad2,
+                         ctx->tc_n2, 0, ctx->tc_p2, ctx->tc_p2_lo, st));
       }
       return S2W_OK;
     };
@@ -692,7 +733,7 @@ int s2w_waveforms(s2w_ctx* ctx, const float* slip, int B, float* q, float* seafl
     slip_d = ctx->ws_slip;
   }
   float* q_d = kq == 1 ? q : ctx->ws_q;
-  const bool use_tc = ctx->tc_on && seafloor == nullptr && ctx->tc_T != nullptr &&
+  const bool use_tc = ctx->tc_on && seafloor == nullptr && (ctx->tc_split || ctx->tc_T != nullptr) &&
                       (ctx->opts.engine == S2W_ENGINE_TENSOR || B >= ctx->tc_min_batch);
   if (use_tc) {
     int rc = waveforms_tensor(ctx, slip_d, B, q_d, st);
@@ -1023,7 +1064,7 @@ int s2w_autotune(s2w_ctx* ctx, int B, s2w_tuning* out, void* stream) {
   int rc = timed(1, S2W_ENGINE_STREAM, &r.ms_stream_per_rupture);
   r.tc_cluster = ctx->tc_cl1;
   r.tc_min_batch = ctx->tc_min_batch;
-  if (rc == S2W_OK && ctx->tc_on && ctx->tc_T != nullptr) {
+  if (rc == S2W_OK && ctx->tc_on && (ctx->tc_split || ctx->tc_T != nullptr)) {
     r.probe_batch = std::min(B, ctx->tc_bsub);
     const int cls[3] = {1, 2, 4};
     float best = 1e30f;

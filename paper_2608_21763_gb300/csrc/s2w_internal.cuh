@@ -138,7 +138,7 @@ cudaError_t launch_irfft_rows(const float2* X, long long rows, int Nt, const flo
 cudaError_t launch_retransform(const float2* mhat, long long Ng, long long ld_m, int Nt, const float2* tw,
                                float inv_dt, int dt_mode, float2* vhat, long long ld_v, float* seafloor,
                                cudaStream_t st, int nb = 1, long long mhat_ld_b = 0, long long vhat_ld_b = 0,
-                               __nv_bfloat162* vhat_bf = nullptr);
+                               __nv_bfloat162* vhat_bf = nullptr, __nv_bfloat162* vhat_bf_lo = nullptr);
 // q[b][o][n] from partials: Qhat[l] = sum_{s < nseg} part[b*s_b + l*s_l + s*s_s + o].
 cudaError_t launch_reduce_irfft(const float2* part, int B, int No, int nseg, int Nt, long long s_b, long long s_l,
                                 long long s_s, const float2* tw, float* q, cudaStream_t st);
@@ -210,17 +210,30 @@ struct TcArgs {
   long long ld_l, ld_t;
   const float* row_scale;  // optional per-(bin, 256-row block) scale
   int nblk;
+  int a_lo;                // 1: A has a low-order BF16 part (second tensor map): adds A_lo B
+  int b_lo;                // 1: B has a low-order BF16 part: adds A B_lo
   int* status;
 };
 // bk = 64: 128-byte swizzle, K boxes of 64 BF16; bk = 32: 64-byte swizzle.
 cudaError_t tc_encode_3d(CUtensorMap* out, const void* base, long long K, long long rows, long long nbatch,
                          long long row_pitch_elems, int box_rows, int bk = 64);
-int tc_block_k(int N);
-int tc_stages_for(int N);
+// K block (BF16 elements per swizzle row) and ring depth for N MMA columns
+// with `terms` = 1 + a_lo + b_lo operand tiles beyond the first A and B
+int tc_block_k(int N, int split = 0);
+int tc_stages_for(int N, int a_lo = 0, int b_lo = 0);
+// tmA2 / tmB2: tensor maps of the low-order parts when a.a_lo / a.b_lo
 cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const TcArgs& a, int num_sms,
-                           cudaStream_t st);
-cudaError_t launch_pack_stage1_b(const float2* shat, int B, int Ns_pad, int Nb, int N_alloc, void* Bp,
-                                 cudaStream_t st);
+                           cudaStream_t st, const CUtensorMap* tmA2 = nullptr, const CUtensorMap* tmB2 = nullptr);
+// B operand rows 2t / 2t+1 of dst[l][N_alloc][2 Kc] (BF16 pairs, hi and
+// optional lo) from complex FP32 src[l*s_l + t*s_t + c], t < T, c < nc, at
+// complex columns c0 + c; conj selects the embedding of conj(A) x.
+cudaError_t launch_pack_b(const float2* src, int Nb, int T, long long nc, long long s_l, long long s_t, long long c0,
+                          long long Kc, int N_alloc, int conj, void* hi, void* lo, cudaStream_t st);
+// A operand dst[(l*rows_total + r0 + r)*Kc + c0 + c] (BF16 pairs, hi and
+// optional lo) from complex FP32 src[l*s_l + r*s_r + c*s_c], r < rows, c < nc.
+cudaError_t launch_pack_a(const float2* src, int Nb, int rows, long long nc, long long s_l, long long s_r,
+                          long long s_c, long long rows_total, long long r0, long long c0, long long Kc, void* hi,
+                          void* lo, cudaStream_t st);
 // Retransform of Bs ruptures as one GEMM per 128-signal tile (see k_tc.cu):
 // reads mhat[l*ld_l + b*ld_b + i], writes vhat[l*vld_l + b*vld_b + i] (BF16
 // pairs); tmT: T[n][k], 2 Nt x 2 Nt BF16, K-major.  32 <= Nt <= 256.
@@ -233,7 +246,6 @@ struct TcRtArgs {
   int* status;
 };
 cudaError_t launch_tc_retransform(const CUtensorMap& tmT, const TcRtArgs& a, int num_sms, cudaStream_t st);
-cudaError_t launch_pack_stage2_b(const float2* src, int Nb, int No, long long nc, long long c0, long long Kc,
-                                 int N_alloc, void* Pp, cudaStream_t st);
+
 
 }  // namespace s2w

@@ -315,6 +315,16 @@ WORKLOADS = {
     # 150,000-point grid, 1024 ruptures
     "largest": Workload("largest", 963, 150000, 64, 256, 1024, "plane", 40, 41,
                         "von_karman", (7.0, 9.2)),
+    # per-GPU shapes of the paper's runs (Table I, Table II), one rupture:
+    # weak scaling, 480 subfaults x 37,758 grid points x 32 observations
+    "paper_weak": Workload("paper_weak", 480, 37758, 32, 256, 1, "plane", 50, 51,
+                           "von_karman", (8.0, 9.0)),
+    # strong scaling on 8 GPUs, 60 x (2,416,530 / 8) x 4
+    "paper_strong8": Workload("paper_strong8", 60, 302066, 4, 256, 1, "plane", 60, 61,
+                              "von_karman", (8.0, 9.0)),
+    # full Cascadia operator on 64 GPUs, 963 x (2,416,530 / 64) x 64
+    "paper_csz64": Workload("paper_csz64", 963, 37758, 64, 256, 1, "plane", 70, 71,
+                            "von_karman", (8.0, 9.0)),
 }
 
 

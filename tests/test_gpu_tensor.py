@@ -19,6 +19,9 @@ pytestmark = pytest.mark.gpu
 import paper_2608_21763_gb300 as s2w  # noqa: E402
 
 TOL_TC = 1e-2
+# split precision (hi/lo BF16 operator AND activations, three MMAs per K
+# step): each product carries ~2^-16 relative error at most
+TOL_SPLIT = 3e-5
 
 
 def compact_box(Ns, Ng, No, seed, scale=0.1):
@@ -27,11 +30,11 @@ def compact_box(Ns, Ng, No, seed, scale=0.1):
                           g.strike * scale, g.dip * scale, "box")
 
 
-def run_case(geom, Nt, B, seed=5, engine="tensor", chunk=4096, tc_cluster=0):
+def run_case(geom, Nt, B, seed=5, engine="tensor", chunk=4096, tc_cluster=0, prec="bf16"):
     rng = np.random.default_rng(seed)
     slip = rng.standard_normal((B, geom.Ns, Nt))
     slip[:, :, Nt // 2:] = 0
-    ctx = make_context(s2w, geom, Nt, prec_g="bf16", max_batch=B, chunk=chunk, engine=engine,
+    ctx = make_context(s2w, geom, Nt, prec_g=prec, max_batch=B, chunk=chunk, engine=engine,
                        tc_cluster=tc_cluster)
     q = ctx.waveforms(torch.tensor(slip, dtype=torch.float32, device="cuda")).cpu().numpy()
     ctx.sync()
@@ -147,3 +150,46 @@ def test_multicast_clusters_match_single_cta(cluster, B):
     qc, _, _, _, _ = run_case(geom, 64, B, seed=13, tc_cluster=cluster)
     assert_parity(qc, q_ref, *wn, tol=TOL_TC, label=f"cluster {cluster} B={B}")
     assert np.array_equal(q1, qc)
+
+
+@pytest.mark.parametrize("B", [1, 5, 130])
+def test_split_precision_tensor_engine(B):
+    """BF16 hi/lo operator spectra with hi/lo slip and velocity spectra on the
+    tensor engine (the FFT retransform stays FP32); B = 130 runs sub-batches
+    of 128 and 2."""
+    geom = compact_box(24, 700, 6, seed=31)
+    q, q_ref, wn, _, _ = run_case(geom, 64, B, seed=32, prec="bf16_hilo")
+    rel, win = assert_parity(q, q_ref, *wn, tol=TOL_SPLIT, label=f"tensor split B={B}")
+
+
+def test_split_precision_tiny_workload_and_stream_agreement():
+    """Tiny workload: the split tensor engine and the hi/lo stream engine (FP32
+    activations) both meet the hi/lo bar and agree with each other."""
+    wl = synth.WORKLOADS["tiny"]
+    geom = wl.geometry_obj()
+    slip = wl.slip(geom, B=4)
+    G = geom.greens_rows(0, wl.Ng, wl.Nt)
+    P = geom.adjoint_cols(0, wl.Ng, wl.Nt)
+    q_ref = oracle.waveforms(G, P, slip)
+    wn = window_norms(G, P, slip)
+    out = {}
+    for engine in ("tensor", "stream"):
+        ctx = make_context(s2w, geom, wl.Nt, prec_g="bf16_hilo", max_batch=4, engine=engine)
+        out[engine] = ctx.waveforms(torch.tensor(slip, dtype=torch.float32, device="cuda")).cpu().numpy()
+        ctx.sync()
+        assert_parity(out[engine], q_ref, *wn, tol=TOL_SPLIT, label=f"tiny hi/lo {engine}")
+
+
+@pytest.mark.parametrize("Nt", [32, 256])
+def test_split_precision_record_lengths(Nt):
+    geom = compact_box(12, 300, 3, seed=Nt + 1)
+    q, q_ref, wn, _, _ = run_case(geom, Nt, 6, prec="bf16_hilo")
+    assert_parity(q, q_ref, *wn, tol=TOL_SPLIT, label=f"tensor split Nt={Nt}")
+
+
+def test_split_precision_clusters_bitwise():
+    geom = compact_box(24, 700, 6, seed=33)
+    q1, q_ref, wn, _, _ = run_case(geom, 64, 40, seed=34, prec="bf16_hilo", tc_cluster=1)
+    q2, _, _, _, _ = run_case(geom, 64, 40, seed=34, prec="bf16_hilo", tc_cluster=2)
+    assert_parity(q2, q_ref, *wn, tol=TOL_SPLIT, label="tensor split cluster 2")
+    assert np.array_equal(q1, q2)
