@@ -131,9 +131,10 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ setup
-def load_context(s2w, wl, geom, prec_g, prec_p, B, device, engine="auto", chunk=1024, tc_cluster=0):
+def load_context(s2w, wl, geom, prec_g, prec_p, B, device, engine="auto", chunk=1024, tc_cluster=0,
+                 tc_adjoint=False):
     ctx = s2w.Context(wl.Ns, wl.Ng, wl.No, wl.Nt, prec_g=prec_g, prec_p=prec_p,
-                      max_batch=B, device=device, engine=engine, tc_cluster=tc_cluster)
+                      max_batch=B, device=device, engine=engine, tc_cluster=tc_cluster, tc_adjoint=tc_adjoint)
     for g0 in range(0, wl.Ng, chunk):
         g1 = min(wl.Ng, g0 + chunk)
         ctx.load_greens(g0, geom.greens_rows(g0, g1, wl.Nt, np.float32))
@@ -241,8 +242,11 @@ def run_ours(args, rank, world, local_rank):
     slip_np = slip_np.reshape(pool, B, wl.Ns, wl.Nt)
 
     t_setup = time.perf_counter()
+    # gradient steps on a tensor-capable storage keep the transposed spectra
+    # so the adjoint runs on the tensor engine as well
+    tc_adj = args.mode == "gradient" and args.prec_g in ("bf16", "bf16_hilo") and args.engine != "stream"
     ctx = load_context(s2w, wl, geom, args.prec_g, args.prec_p, B, local_rank, args.engine,
-                       tc_cluster=args.tc_cluster)
+                       tc_cluster=args.tc_cluster, tc_adjoint=tc_adj)
     setup_s = time.perf_counter() - t_setup
     slip_d = torch.tensor(slip_np, device=dev)
     q_d = torch.empty((pool, B, wl.No, wl.Nt), dtype=torch.float32, device=dev)

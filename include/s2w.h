@@ -99,6 +99,12 @@ typedef struct {
   int tc_cluster; /* tensor engine: CTAs per cluster sharing each B tile by
                      multicast, 1, 2 or 4; 0 = library choice (s2w_autotune
                      can measure and set it) */
+  int tc_adjoint; /* 1: also keep transposed copies of both operator spectra
+                     (K-major along the grid) so that s2w_adjoint and
+                     s2w_misfit_gradient run on the tensor engine for
+                     batches (same rules as s2w_waveforms); doubles the
+                     stage-1 operator memory.  0 (default): the adjoint
+                     streams the spectra once per rupture. */
 } s2w_opts;
 
 /* Fill *o with the defaults listed above (max_batch = 1). */
@@ -149,8 +155,13 @@ int s2w_waveforms(s2w_ctx *ctx, const float *slip, int B, float *q, float *seafl
  * conjugate spectra, (F^T y)_j[n] = sum_i sum_{k <= Nt-1-n} f_ij[k] y_i[n+k],
  * evaluated as conj(Fhat_l) yhat_l per bin with zero padding to 2 Nt (no
  * wrap reaches the kept samples), and D_t^T w[n] = (w[n] - w[n+1]) / dt with
- * w[Nt] = 0.  Uses the streaming kernels, one rupture at a time, for every
- * storage precision.  Pointer and stream rules as s2w_waveforms. */
+ * w[Nt] = 0.  Without opts.tc_adjoint: the streaming kernels, one rupture at
+ * a time, for every storage precision.  With opts.tc_adjoint (BF16 or
+ * BF16_HILO storage) and B >= the AUTO batch threshold (or ENGINE_TENSOR):
+ * both correlations run as tcgen05 GEMMs over the sub-batch against the
+ * transposed spectra, with the same hi/lo splitting as the forward tensor
+ * path and the FP32 FFT retransform with D_t^T between them.  Pointer and
+ * stream rules as s2w_waveforms. */
 int s2w_adjoint(s2w_ctx *ctx, const float *r, int B, float *grad_s, void *stream);
 
 /* Gradient of the waveform misfit L_b = 0.5 ||q(slip[b]) - d[b]||^2 for B

@@ -60,7 +60,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("prec_g", ctypes.c_int), ("prec_p", ctypes.c_int),
                 ("dt_mode", ctypes.c_int), ("dt", ctypes.c_double),
                 ("max_batch", ctypes.c_int), ("device", ctypes.c_int),
-                ("engine", ctypes.c_int), ("tc_cluster", ctypes.c_int)]
+                ("engine", ctypes.c_int), ("tc_cluster", ctypes.c_int), ("tc_adjoint", ctypes.c_int)]
 
 
 def lib_path() -> str:
@@ -144,7 +144,8 @@ class Context:
     """
 
     def __init__(self, Ns, Ng, No, Nt, prec_g="fp32", prec_p="fp32",
-                 dt_mode="backward", dt=1.0, max_batch=1, device=0, engine="auto", tc_cluster=0):
+                 dt_mode="backward", dt=1.0, max_batch=1, device=0, engine="auto", tc_cluster=0,
+                 tc_adjoint=False):
         L = lib()
         o = Opts()
         L.s2w_default_opts(ctypes.byref(o))
@@ -153,6 +154,7 @@ class Context:
         o.max_batch, o.device = int(max_batch), int(device)
         o.engine = ENGINE[engine]
         o.tc_cluster = int(tc_cluster)
+        o.tc_adjoint = int(bool(tc_adjoint))
         h = ctypes.c_void_p()
         st = L.s2w_create(Ns, Ng, No, Nt, ctypes.byref(o), ctypes.byref(h))
         if st != 0:

@@ -76,7 +76,8 @@ __global__ void __launch_bounds__(kThreads) k_retransform(const float2* __restri
                                                           const float2* __restrict__ twg, float inv_dt, int dt_mode,
                                                           void* __restrict__ vout, long long ld_v,
                                                           float* __restrict__ seafloor, long long mhat_ld_b,
-                                                          long long vhat_ld_b, __nv_bfloat162* __restrict__ vout_lo) {
+                                                          long long vhat_ld_b, __nv_bfloat162* __restrict__ vout_lo,
+                                                          int n_alloc) {
   constexpr int N = 32 * P;
   constexpr int L = 2 * N;
   constexpr int NB = N + 1;
@@ -137,7 +138,19 @@ __global__ void __launch_bounds__(kThreads) k_retransform(const float2* __restri
     const long long i = i0 + c;
     if (i >= Ng) continue;
     const float2 v = tile[c * NB + l];
-    if (BF16OUT) {
+    if (BF16OUT && n_alloc > 0) {
+      // B operand of the conjugate embedding (tensor-engine adjoint): rows
+      // 2b = (Re v, Im v) and 2b+1 = (Im v, -Re v) of [l][n_alloc][ld_v]
+      const long long o0 = (static_cast<long long>(l) * n_alloc + 2 * blockIdx.y) * ld_v + i;
+      const float2 r[2] = {make_float2(v.x, v.y), make_float2(v.y, -v.x)};
+#pragma unroll
+      for (int h2 = 0; h2 < 2; ++h2) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(r[h2].x, r[h2].y);
+        static_cast<__nv_bfloat162*>(vout)[o0 + h2 * ld_v] = h;
+        if (vout_lo != nullptr)
+          vout_lo[o0 + h2 * ld_v] = __floats2bfloat162_rn(r[h2].x - __low2float(h), r[h2].y - __high2float(h));
+      }
+    } else if (BF16OUT) {
       const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
       (static_cast<__nv_bfloat162*>(vout) + blockIdx.y * vhat_ld_b)[l * ld_v + i] = h;
       if (vout_lo != nullptr)  // low-order part: v - hi, rounded again
@@ -348,7 +361,7 @@ cudaError_t launch_irfft_rows(const float2* X, long long rows, int Nt, const flo
 cudaError_t launch_retransform(const float2* mhat, long long Ng, long long ld_m, int Nt, const float2* tw,
                                float inv_dt, int dt_mode, float2* vhat, long long ld_v, float* seafloor,
                                cudaStream_t st, int nb, long long mhat_ld_b, long long vhat_ld_b,
-                               __nv_bfloat162* vhat_bf, __nv_bfloat162* vhat_bf_lo) {
+                               __nv_bfloat162* vhat_bf, __nv_bfloat162* vhat_bf_lo, int n_alloc) {
   if (Ng <= 0 || nb <= 0) return cudaSuccess;
   const dim3 grid(static_cast<unsigned>((Ng + 31) / 32), static_cast<unsigned>(nb));
   S2W_DISPATCH_P(Nt, {
@@ -358,13 +371,13 @@ cudaError_t launch_retransform(const float2* mhat, long long Ng, long long ld_m,
                                            static_cast<int>(sm));
       if (e != cudaSuccess) return e;
       k_retransform<P, true><<<grid, kThreads, sm, st>>>(mhat, Ng, ld_m, tw, inv_dt, dt_mode, vhat_bf, ld_v, seafloor,
-                                                         mhat_ld_b, vhat_ld_b, vhat_bf_lo);
+                                                         mhat_ld_b, vhat_ld_b, vhat_bf_lo, n_alloc);
     } else {
       cudaError_t e = cudaFuncSetAttribute(k_retransform<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            static_cast<int>(sm));
       if (e != cudaSuccess) return e;
       k_retransform<P, false><<<grid, kThreads, sm, st>>>(mhat, Ng, ld_m, tw, inv_dt, dt_mode, vhat, ld_v, seafloor,
-                                                          mhat_ld_b, vhat_ld_b, nullptr);
+                                                          mhat_ld_b, vhat_ld_b, nullptr, 0);
     }
   });
   return cudaGetLastError();

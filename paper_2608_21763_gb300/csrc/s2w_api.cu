@@ -76,6 +76,18 @@ struct s2w_ctx {
   cudaStream_t cap_stream = nullptr;
   std::vector<GraphEntry> graphs;
   unsigned long long graph_clock = 0;
+  // tensor-engine adjoint: transposed spectra, K-major along the grid
+  bool tc_adj = false;
+  int NoP = 0;                // complex columns per row of Phat^T (No padded to 32)
+  void* tc_gT = nullptr;      // [Nb][Ns][Ng_pad2] bf16 pairs: Ghat_l^T
+  void* tc_gT_lo = nullptr;
+  void* tc_pT = nullptr;      // [Nb][Ng][NoP] bf16 pairs: Phat_l^T
+  void* tc_pT_lo = nullptr;
+  void* tc_rb = nullptr;      // [Nb][tc_n1max][2 NoP] bf16: residual spectra, conjugate embedding
+  void* tc_rb_lo = nullptr;
+  void* tc_ub = nullptr;      // [Nb][tc_n1max][2 Ng_pad2] bf16: D_t^T-retransformed spectra, conjugate embedding
+  void* tc_ub_lo = nullptr;
+  float2* tc_ghat = nullptr;  // [Nb][tc_bsub][Ns] complex FP32
   bool tc_split = false;    // BF16 hi/lo operands and activations (three MMAs per K step)
   void* tc_bp1_lo = nullptr;  // split: low-order parts of tc_bp1, tc_vhat, tc_p2
   void* tc_vhat_lo = nullptr;
@@ -230,7 +242,9 @@ void free_all(s2w_ctx* c) {
   c->ev_free.clear();
   void* ps[] = {c->G, c->G_lo, c->G_scale, c->P, c->tw, c->ws_slip, c->ws_shat, c->ws_mhat,
                 c->ws_vhat, c->ws_part, c->ws_q, c->ws_seafloor, c->d_status, c->tc_bp1, c->ws_rhat, c->ws_gpart, c->ws_resid, c->ws_d, c->ws_loss,
-                c->tc_mhat, c->tc_vhat, c->tc_part, c->tc_p2, c->tc_T, c->tc_bp1_lo, c->tc_vhat_lo, c->tc_p2_lo};
+                c->tc_mhat, c->tc_vhat, c->tc_part, c->tc_p2, c->tc_T, c->tc_bp1_lo, c->tc_vhat_lo, c->tc_p2_lo,
+                c->tc_gT, c->tc_gT_lo, c->tc_pT, c->tc_pT_lo, c->tc_rb, c->tc_rb_lo, c->tc_ub, c->tc_ub_lo,
+                c->tc_ghat};
   for (void* p : ps)
     if (p) cudaFree(p);
 }
@@ -283,6 +297,101 @@ std::vector<__nv_bfloat16> retransform_matrix(int Nt, int dt_mode, double dt) {
 //   rfft slip -> pack stage-1 B operand -> tcgen05 stage 1 -> mhat[l][b][Ng]
 //   -> retransform (BF16 velocity spectra, the stage-2 A operand)
 //   -> tcgen05 stage 2 over grid chunks -> partials -> reduce + IFFT -> q.
+// One tcgen05 GEMM (epilogue 0: FP32 out[l][t][row]) over A [Nb][M][K]
+// and the B operand rows [Nb][n_alloc][K] (BF16; lo parts when split).
+int tc_gemm_epi0(s2w_ctx* ctx, const void* A, const void* A_lo, long long M, long long K, const void* Bop,
+                 const void* B_lo, int n_alloc, int N, int T, float2* out, long long ld_l, long long ld_t, int cl_want,
+                 cudaStream_t st) {
+  const int sp = A_lo != nullptr ? 1 : 0;
+  CUtensorMap ta, tb, ta2, tb2;
+  const int bk = tc_block_k(N, sp);
+  const int mt = static_cast<int>((M + 127) / 128);
+  const int cl = fit_cluster(cl_want, N, mt);
+  const int brows = cl > 1 ? N / cl : (N > 256 ? 256 : N);
+  CK(tc_encode_3d(&ta, A, K, M, ctx->Nb, K, 128, bk));
+  CK(tc_encode_3d(&tb, Bop, K, n_alloc, ctx->Nb, K, brows, bk));
+  if (sp) {
+    CK(tc_encode_3d(&ta2, A_lo, K, M, ctx->Nb, K, 128, bk));
+    CK(tc_encode_3d(&tb2, B_lo, K, n_alloc, ctx->Nb, K, brows, bk));
+  }
+  TcArgs a{};
+  a.N = N;
+  a.K = static_cast<int>(K);
+  a.M_total = static_cast<int>(M);
+  a.Nb = static_cast<int>(ctx->Nb);
+  a.m_tiles = mt;
+  a.n_kchunks = 1;
+  a.kblocks_per_chunk = static_cast<int>((K + bk - 1) / bk);
+  a.stages = tc_stages_for(N, sp, sp);
+  a.a_lo = sp;
+  a.b_lo = sp;
+  a.tmem_cols = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : (N <= 256 ? 256 : 512)));
+  a.cluster = cl;
+  a.epi = 0;
+  a.T = T;
+  a.out = out;
+  a.ld_l = ld_l;
+  a.ld_t = ld_t;
+  a.status = ctx->d_status;
+  CK(launch_tc_gemm(ta, tb, a, ctx->num_sms, st, sp ? &ta2 : nullptr, sp ? &tb2 : nullptr));
+  return S2W_OK;
+}
+
+// Adjoint of the waveform map on the tensor engine, per sub-batch (same
+// steps as the streaming adjoint, each contraction one GEMM per bin):
+//   rhat = rFFT(ZeroPad(r));  what_l = Phat_l^H rhat_l  (A = Phat_l^T, B = conj. embedding of rhat)
+//   uhat = FFT(ZeroPad(D_t^T(Truncate(IFFT(what)))))      (FP32 FFT retransform, writes B directly)
+//   ghat_l = Ghat_l^H uhat_l  (A = Ghat_l^T, K = grid);   g = Truncate(IFFT(ghat))
+int adjoint_tensor(s2w_ctx* ctx, const float* r_d, int B, float* g_d, cudaStream_t st) {
+  const long long Ns = ctx->Ns, Ng = ctx->Ng, No = ctx->No, Nt = ctx->Nt, Nb = ctx->Nb;
+  const int sp = ctx->tc_split ? 1 : 0;
+  const int dt_t = ctx->opts.dt_mode == S2W_DT_NONE ? S2W_DT_NONE : kDtTranspose;
+  for (int b0 = 0; b0 < B; b0 += ctx->tc_bsub) {
+    const int Bs = std::min(ctx->tc_bsub, B - b0);
+    int N1 = static_cast<int>(round_up(2 * Bs, 16));
+    if (N1 > 256) N1 = 512;
+    {
+      StageTimer t(ctx, 0, st);
+      CK(launch_rfft_rows(r_d + static_cast<long long>(b0) * No * Nt, Bs * No, static_cast<int>(Nt),
+                          static_cast<int>(Nt), ctx->tw, ctx->ws_rhat, Bs * No, No, No, st));
+    }
+    {
+      StageTimer t(ctx, 6, st);
+      CK(launch_pack_b(ctx->ws_rhat, static_cast<int>(Nb), Bs, No, static_cast<long long>(Bs) * No, No, 0, ctx->NoP,
+                       ctx->tc_n1max, 1, ctx->tc_rb, ctx->tc_rb_lo, st));
+    }
+    float2* what = static_cast<float2*>(ctx->tc_mhat);
+    {
+      StageTimer t(ctx, 3, st);
+      int rc = tc_gemm_epi0(ctx, ctx->tc_pT, sp ? ctx->tc_pT_lo : nullptr, Ng, 2LL * ctx->NoP, ctx->tc_rb,
+                            sp ? ctx->tc_rb_lo : nullptr, ctx->tc_n1max, N1, Bs, what,
+                            static_cast<long long>(Bs) * Ng, Ng, ctx->tc_cl1, st);
+      if (rc != S2W_OK) return rc;
+    }
+    {
+      StageTimer t(ctx, 2, st);
+      CK(launch_retransform(what, Ng, static_cast<long long>(Bs) * Ng, static_cast<int>(Nt), ctx->tw,
+                            static_cast<float>(1.0 / ctx->opts.dt), dt_t, nullptr, ctx->Ng_pad2, nullptr, st, Bs, Ng, 0,
+                            static_cast<__nv_bfloat162*>(ctx->tc_ub), static_cast<__nv_bfloat162*>(ctx->tc_ub_lo),
+                            ctx->tc_n1max));
+    }
+    {
+      StageTimer t(ctx, 1, st);
+      int rc = tc_gemm_epi0(ctx, ctx->tc_gT, sp ? ctx->tc_gT_lo : nullptr, Ns, 2 * ctx->Ng_pad2, ctx->tc_ub,
+                            sp ? ctx->tc_ub_lo : nullptr, ctx->tc_n1max, N1, Bs, ctx->tc_ghat,
+                            static_cast<long long>(Bs) * Ns, Ns, ctx->tc_cl1, st);
+      if (rc != S2W_OK) return rc;
+    }
+    {
+      StageTimer t(ctx, 4, st);
+      CK(launch_reduce_irfft(ctx->tc_ghat, Bs, static_cast<int>(Ns), 1, static_cast<int>(Nt), Ns,
+                             static_cast<long long>(Bs) * Ns, 0, ctx->tw, g_d + static_cast<long long>(b0) * Ns * Nt,
+                             st));
+    }
+  }
+  return S2W_OK;
+}
+
 int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaStream_t st) {
   const long long Ns = ctx->Ns, Ng = ctx->Ng, No = ctx->No, Nt = ctx->Nt, Nb = ctx->Nb, Ns_pad = ctx->Ns_pad;
   const int K1 = static_cast<int>(2 * Ns_pad);
@@ -416,6 +525,7 @@ void s2w_default_opts(s2w_opts* o) {
   o->device = 0;
   o->engine = S2W_ENGINE_AUTO;
   o->tc_cluster = 0;
+  o->tc_adjoint = 0;
 }
 
 const char* s2w_status_string(int s) {
@@ -456,6 +566,7 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
     return fail(nullptr, S2W_ERR_ARG, "tc_cluster=%d: 0, 1, 2 or 4", o.tc_cluster);
   if (o.engine == S2W_ENGINE_TENSOR && o.prec_g != S2W_PREC_BF16 && o.prec_g != S2W_PREC_BF16_HILO)
     return fail(nullptr, S2W_ERR_UNSUPPORTED, "the tensor engine needs prec_g = BF16 or BF16_HILO");
+  if (o.tc_adjoint != 0 && o.tc_adjoint != 1) return fail(nullptr, S2W_ERR_ARG, "tc_adjoint=%d: 0 or 1", o.tc_adjoint);
   if (o.engine == S2W_ENGINE_TENSOR && 2 * No > 256)
     return fail(nullptr, S2W_ERR_UNSUPPORTED, "the tensor engine needs No <= 128");
   int ndev = 0;
@@ -550,8 +661,32 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
     const bool sp = ctx->tc_split;
     if ((e = dalloc(&ctx->tc_bp1, 2ull * Nb * ctx->tc_n1max * 2 * ctx->Ns_pad)) != cudaSuccess)
       return bad(e, "tensor stage-1 operand");
-    if ((e = dalloc(&ctx->tc_mhat, (sp ? sizeof(float2) : sizeof(__nv_bfloat162)) * Nb * bs * Ng)) != cudaSuccess)
+    ctx->tc_adj = o.tc_adjoint != 0;
+    // FP32 seafloor spectra for the split path, and for the adjoint's what
+    const bool mhat32 = sp || ctx->tc_adj;
+    if ((e = dalloc(&ctx->tc_mhat, (mhat32 ? sizeof(float2) : sizeof(__nv_bfloat162)) * Nb * bs * Ng)) !=
+        cudaSuccess)
       return bad(e, "tensor seafloor spectra");
+    if (ctx->tc_adj) {
+      ctx->NoP = static_cast<int>(round_up(No, 32));
+      const size_t gT = 4ull * Nb * Ns * round_up(Ng, 8), pT = 4ull * Nb * Ng * ctx->NoP;
+      const size_t rb = 2ull * Nb * ctx->tc_n1max * 2 * ctx->NoP;
+      const size_t ub = 2ull * Nb * ctx->tc_n1max * 2 * round_up(Ng, 8);
+      if ((e = dalloc(&ctx->tc_gT, gT)) != cudaSuccess) return bad(e, "transposed Ghat");
+      if ((e = dalloc(&ctx->tc_pT, pT)) != cudaSuccess) return bad(e, "transposed Phat");
+      if ((e = dalloc(&ctx->tc_rb, rb)) != cudaSuccess) return bad(e, "adjoint residual operand");
+      if ((e = dalloc(&ctx->tc_ub, ub)) != cudaSuccess) return bad(e, "adjoint stage-1 operand");
+      if (sp) {
+        if ((e = dalloc(&ctx->tc_gT_lo, gT)) != cudaSuccess) return bad(e, "transposed Ghat (lo)");
+        if ((e = dalloc(&ctx->tc_pT_lo, pT)) != cudaSuccess) return bad(e, "transposed Phat (lo)");
+        if ((e = dalloc(&ctx->tc_rb_lo, rb)) != cudaSuccess) return bad(e, "adjoint residual operand (lo)");
+        if ((e = dalloc(&ctx->tc_ub_lo, ub)) != cudaSuccess) return bad(e, "adjoint stage-1 operand (lo)");
+      }
+      if ((e = dalloc(&ctx->tc_ghat, sizeof(float2) * Nb * bs * Ns)) != cudaSuccess)
+        return bad(e, "adjoint slip spectra");
+      ctx->g_bytes += gT * (sp ? 2 : 1);
+      ctx->p_bytes += pT * (sp ? 2 : 1);
+    }
     if ((e = dalloc(&ctx->tc_vhat, 4ull * Nb * bs * ctx->Ng_pad2)) != cudaSuccess)
       return bad(e, "tensor velocity spectra");
     if ((e = dalloc(&ctx->tc_part, sizeof(float2) * Nb * ctx->tc_nkc * bs * No)) != cudaSuccess)
@@ -639,6 +774,11 @@ int s2w_load_greens(s2w_ctx* ctx, int g0, int ng, const float* G, void* stream) 
         CK(launch_store_blocks(stage_s, static_cast<int>(Nb), rc * Ns_pad, ctx->opts.prec_g, ctx->G, ctx->G_lo,
                                static_cast<long long>(ctx->Ng) * Ns_pad, row0 * Ns_pad, st));
       }
+      if (ctx->tc_adj) {  // Ghat_l^T[j][row0 + r] (transposing copy; grid along K)
+        ctx->launches += 1;
+        CK(launch_pack_a(stage_s, static_cast<int>(Nb), static_cast<int>(Ns), rc, rc * Ns_pad, 1, Ns_pad, Ns, 0, row0,
+                         ctx->Ng_pad2, ctx->tc_gT, ctx->tc_gT_lo, st));
+      }
       return S2W_OK;
     };
     rc_status = step();
@@ -691,6 +831,11 @@ int s2w_load_adjoint(s2w_ctx* ctx, int g0, int ng, const float* P, void* stream)
         ctx->launches += 1;
         CK(launch_pack_b(stage_s, static_cast<int>(Nb), static_cast<int>(No), rc, No * rc, rc, g0 + c, ctx->Ng_pad2,
                          ctx->tc_n2, 0, ctx->tc_p2, ctx->tc_p2_lo, st));
+      }
+      if (ctx->tc_adj) {  // Phat_l^T[g0 + c + r][o] (transposing copy; observations along K)
+        ctx->launches += 1;
+        CK(launch_pack_a(stage_s, static_cast<int>(Nb), static_cast<int>(rc), No, No * rc, 1, rc, ctx->Ng, g0 + c, 0,
+                         ctx->NoP, ctx->tc_pT, ctx->tc_pT_lo, st));
       }
       return S2W_OK;
     };
@@ -838,6 +983,16 @@ int s2w_adjoint(s2w_ctx* ctx, const float* r, int B, float* grad_s, void* stream
     r_d = ctx->ws_q;
   }
   float* g_d = kg == 1 ? grad_s : ctx->ws_slip;
+  if (ctx->tc_adj && (ctx->opts.engine == S2W_ENGINE_TENSOR || B >= ctx->tc_min_batch)) {
+    const int rc = adjoint_tensor(ctx, r_d, B, g_d, st);
+    if (rc != S2W_OK) return rc;
+    if (kg == 0) {
+      StageTimer t(ctx, 5, st, 0);
+      CK(cudaMemcpyAsync(grad_s, g_d, sizeof(float) * B * Ns * Nt, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+    }
+    return S2W_OK;
+  }
   {
     StageTimer t(ctx, 0, st);
     CK(launch_rfft_rows(r_d, B * No, static_cast<int>(Nt), static_cast<int>(Nt), ctx->tw, ctx->ws_rhat, B * No, No,

@@ -134,11 +134,15 @@ cudaError_t launch_irfft_rows(const float2* X, long long rows, int Nt, const flo
 // Retransform of `nb` ruptures (grid y): rupture y reads mhat + y * mhat_ld_b
 // ([l][i] with bin stride ld_m) and writes either vhat + y * vhat_ld_b (FP32
 // complex, bin stride ld_v) or, when vhat_bf is given, vhat_bf + y * vhat_ld_b
-// (BF16 complex pairs, bin stride ld_v); seafloor (optional) + y * Ng * Nt.
+// (BF16 complex pairs, bin stride ld_v; with vhat_bf_lo also the low-order
+// parts v - hi); seafloor (optional) + y * Ng * Nt.  n_alloc > 0 (with
+// vhat_bf): rupture y writes rows 2y, 2y+1 of the conjugate-embedding B
+// operand [l][n_alloc][ld_v] instead (vhat_ld_b unused).
 cudaError_t launch_retransform(const float2* mhat, long long Ng, long long ld_m, int Nt, const float2* tw,
                                float inv_dt, int dt_mode, float2* vhat, long long ld_v, float* seafloor,
                                cudaStream_t st, int nb = 1, long long mhat_ld_b = 0, long long vhat_ld_b = 0,
-                               __nv_bfloat162* vhat_bf = nullptr, __nv_bfloat162* vhat_bf_lo = nullptr);
+                               __nv_bfloat162* vhat_bf = nullptr, __nv_bfloat162* vhat_bf_lo = nullptr,
+                               int n_alloc = 0);
 // q[b][o][n] from partials: Qhat[l] = sum_{s < nseg} part[b*s_b + l*s_l + s*s_s + o].
 cudaError_t launch_reduce_irfft(const float2* part, int B, int No, int nseg, int Nt, long long s_b, long long s_l,
                                 long long s_s, const float2* tw, float* q, cudaStream_t st);

@@ -179,3 +179,77 @@ def test_misfit_gradient_entry_point(tiny_ops):
     adjoint_bars(g.cpu().numpy(), G, P, r, 2e-5, "misfit gradient")
     g_h, loss_h = ctx.misfit_gradient(s.astype(np.float32), d.astype(np.float32))
     assert np.array_equal(g_h, g.cpu().numpy()) and np.array_equal(loss_h, loss.cpu().numpy())
+
+
+# tensor-engine adjoint (transposed operator copies, tcgen05 GEMMs)
+TOL_TC_ADJ = {"bf16": 1e-2, "bf16_hilo": 3e-5}
+
+
+@pytest.mark.parametrize("prec", ["bf16", "bf16_hilo"])
+def test_tensor_adjoint_against_oracle(tiny_ops, prec):
+    wl, geom, G, P = tiny_ops
+    r = synth.random_waveforms(5, wl.No, wl.Nt, seed=21)
+    ctx = make_context(s2w, geom, wl.Nt, prec_g=prec, max_batch=5, engine="tensor", tc_adjoint=True)
+    g = ctx.adjoint(torch.tensor(r, dtype=torch.float32, device="cuda")).cpu().numpy()
+    ctx.sync()
+    adjoint_bars(g, G, P, r, TOL_TC_ADJ[prec], f"tensor adjoint tiny {prec}")
+
+
+@pytest.mark.parametrize("Ns,Ng,No,Nt,B", [(5, 1000, 3, 64, 2), (24, 700, 6, 32, 130), (7, 2100, 5, 128, 9)])
+def test_tensor_adjoint_shapes(Ns, Ng, No, Nt, B):
+    """Ragged shapes: partial M tiles of the transposed operators, No far
+    below its 32-column padding, and (B = 130) two sub-batches."""
+    geom = compact_box(Ns, Ng, No, seed=Ns + Ng + 3)
+    r = np.random.default_rng(3).standard_normal((B, No, Nt))
+    ctx = make_context(s2w, geom, Nt, prec_g="bf16_hilo", max_batch=B, chunk=512, engine="tensor",
+                       tc_adjoint=True)
+    g = ctx.adjoint(torch.tensor(r, dtype=torch.float32, device="cuda")).cpu().numpy()
+    ctx.sync()
+    G = geom.greens_rows(0, Ng, Nt)
+    P = geom.adjoint_cols(0, Ng, Nt)
+    adjoint_bars(g, G, P, r, TOL_TC_ADJ["bf16_hilo"], f"tensor adjoint {Ns}x{Ng}x{No}x{Nt} B={B}")
+
+
+def test_tensor_adjoint_identity_and_stream_agreement(tiny_ops):
+    """<W s, r> = <s, W^T r> with both sides from the split tensor engine,
+    and the tensor adjoint against the streaming adjoint of the same
+    hi/lo operator."""
+    wl, geom, G, P = tiny_ops
+    s = wl.slip(geom, B=4)
+    r = synth.random_waveforms(4, wl.No, wl.Nt, seed=22)
+    ctx = make_context(s2w, geom, wl.Nt, prec_g="bf16_hilo", max_batch=4, engine="tensor", tc_adjoint=True)
+    q = ctx.waveforms(torch.tensor(s, dtype=torch.float32, device="cuda")).cpu().numpy().astype(np.float64)
+    g = ctx.adjoint(torch.tensor(r, dtype=torch.float32, device="cuda")).cpu().numpy().astype(np.float64)
+    # each side carries its engine error on the scale of its FFT window
+    qn = np.linalg.norm(oracle.fft_window(G, P, s).reshape(4, -1), axis=1)
+    gw = oracle.fft_window_adjoint(G, P, r)
+    wn = np.linalg.norm(gw.reshape(4, -1), axis=1)
+    for b in range(4):
+        lhs, rhs = np.sum(q[b] * r[b]), np.sum(s[b] * g[b])
+        bound = 3e-5 * (qn[b] * np.linalg.norm(r[b]) + np.linalg.norm(s[b]) * wn[b])
+        assert abs(lhs - rhs) <= bound, (b, lhs, rhs, bound)
+    cs = make_context(s2w, geom, wl.Nt, prec_g="bf16_hilo", max_batch=4, engine="stream")
+    g_s = cs.adjoint(torch.tensor(r, dtype=torch.float32, device="cuda")).cpu().numpy()
+    assert np.all(np.linalg.norm((g - g_s).reshape(4, -1), axis=1) <= 6e-5 * wn)
+    ctx.sync()
+
+
+def test_tensor_misfit_gradient(tiny_ops):
+    """s2w_misfit_gradient with forward and adjoint on the split tensor
+    engine against the FP64 oracle misfit and gradient, and autograd through
+    the same context."""
+    wl, geom, G, P = tiny_ops
+    s = wl.slip(geom, B=3)
+    d = synth.random_waveforms(3, wl.No, wl.Nt, seed=23)
+    ctx = make_context(s2w, geom, wl.Nt, prec_g="bf16_hilo", max_batch=3, engine="tensor", tc_adjoint=True)
+    g, loss = ctx.misfit_gradient(torch.tensor(s, dtype=torch.float32, device="cuda"),
+                                  torch.tensor(d, dtype=torch.float32, device="cuda"))
+    loss_ref, g_ref = oracle.gradient(G, P, s, d)
+    assert np.allclose(loss.cpu().numpy(), loss_ref, rtol=5e-5)
+    r = oracle.waveforms(G, P, s) - d
+    adjoint_bars(g.cpu().numpy(), G, P, r, 6e-5, "tensor misfit gradient")
+    st = torch.tensor(s, dtype=torch.float32, device="cuda", requires_grad=True)
+    lt = s2w_autograd.misfit(ctx, st, torch.tensor(d, dtype=torch.float32, device="cuda"))
+    lt.backward()
+    assert torch.allclose(st.grad, g, rtol=0, atol=1e-6 * float(g.abs().max()))
+    ctx.sync()
