@@ -44,7 +44,8 @@ __global__ void __launch_bounds__(kThreads) k_rfft_rows(const float* __restrict_
   const long long row = static_cast<long long>(blockIdx.x) * kWarps + (threadIdx.x >> 5);
   if (row >= rows) return;
   const float* xr = x + row * n_in;
-  warp_rfft_stage<P>([&](int n) { return n < n_in ? __ldg(xr + n) : 0.f; }, zs, tw, lane);
+  const FftLane<P> fl = fft_lane<P>(tw, lane);
+  warp_rfft_stage<P>([&](int n) { return n < n_in ? __ldg(xr + n) : 0.f; }, zs, tw, fl, lane);
   float2* out = X + (row / rows_a) * ld_a + (row % rows_a);
   for (int k = lane; k <= N; k += 32) out[k * ld_l] = rfft_bin<P>(zs, tw, k);
 }
@@ -56,6 +57,7 @@ __global__ void __launch_bounds__(kThreads) k_irfft_rows(const float2* __restric
   constexpr int N = 32 * P;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* tw = reinterpret_cast<float2*>(smraw);
+  float2* scr = tw + 2 * N + (threadIdx.x >> 5) * N;
   load_twiddles<P>(tw, twg);
   __syncthreads();
   const int lane = threadIdx.x & 31;
@@ -63,7 +65,8 @@ __global__ void __launch_bounds__(kThreads) k_irfft_rows(const float2* __restric
   if (row >= rows) return;
   const float2* xr = X + row * (N + 1);
   float* out = x + row * N;
-  warp_irfft_head<P>([&](int k) { return xr[k]; }, [&](int n, float v) { out[n] = v; }, tw, lane);
+  const FftLane<P> fl = fft_lane<P>(tw, lane);
+  warp_irfft_head<P>([&](int k) { return xr[k]; }, [&](int n, float v) { out[n] = v; }, tw, fl, lane, scr);
 }
 
 // Retransform of 32 consecutive grid points per CTA, rupture blockIdx.y:
@@ -111,23 +114,30 @@ __global__ void __launch_bounds__(kThreads) k_retransform(const float2* __restri
     }
   }
   __syncthreads();
+  const FftLane<P> fl = fft_lane<P>(tw, lane);
   for (int c = warp; c < 32; c += kWarps) {
     const long long i = i0 + c;
     if (i >= Ng) break;
     float2* X = tile + c * NB;
-    warp_irfft_head<P>([&](int k) { return X[k]; }, [&](int n, float v) { mb[n] = v; }, tw, lane);
+    // m[n] lives at mb[msw(n)]: the IFFT hands the lanes samples 2 fft_out
+    // (+1) in a strided pattern; the XOR swizzle inside blocks of 32 floats
+    // spreads those stores (and the later natural-order reads) over the banks
+    auto msw = [](int n) { return n ^ (((n >> 5) ^ (n >> 7)) & 31); };
+    warp_irfft_head<P>([&](int k) { return X[k]; }, [&](int n, float v) { mb[msw(n)] = v; }, tw, fl, lane, zs);
     __syncwarp();
     if (seafloor != nullptr)
-      for (int n = lane; n < N; n += 32) seafloor[i * N + n] = mb[n];
+      for (int n = lane; n < N; n += 32) seafloor[i * N + n] = mb[msw(n)];
     if (dt_mode == S2W_DT_NONE) {
-      warp_rfft_stage<P>([&](int n) { return n < N ? mb[n] : 0.f; }, zs, tw, lane);
+      warp_rfft_stage<P>([&](int n) { return n < N ? mb[msw(n)] : 0.f; }, zs, tw, fl, lane);
     } else if (dt_mode == kDtTranspose) {
       // D_t^T: u[n] = (w[n] - w[n+1]) / dt, w[N] = 0
       warp_rfft_stage<P>(
-          [&](int n) { return n < N ? (mb[n] - (n + 1 < N ? mb[n + 1] : 0.f)) * inv_dt : 0.f; }, zs, tw, lane);
+          [&](int n) { return n < N ? (mb[msw(n)] - (n + 1 < N ? mb[msw(n + 1)] : 0.f)) * inv_dt : 0.f; }, zs, tw,
+          fl, lane);
     } else {
       warp_rfft_stage<P>(
-          [&](int n) { return n < N ? (mb[n] - (n > 0 ? mb[n - 1] : 0.f)) * inv_dt : 0.f; }, zs, tw, lane);
+          [&](int n) { return n < N ? (mb[msw(n)] - (n > 0 ? mb[msw(n - 1)] : 0.f)) * inv_dt : 0.f; }, zs, tw, fl,
+          lane);
     }
     for (int k = lane; k <= N; k += 32) X[k] = rfft_bin<P>(zs, tw, k);
     __syncwarp();
@@ -174,6 +184,7 @@ __global__ void __launch_bounds__(kThreads) k_reduce_irfft(const float2* __restr
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* tw = reinterpret_cast<float2*>(smraw);
   float2* xs = tw + L;
+  float2* scr = xs + N + 1;
   load_twiddles<P>(tw, twg);
   const int b = blockIdx.x / No, o = blockIdx.x % No;
   const float2* pb = part + b * s_b + o;
@@ -187,7 +198,8 @@ __global__ void __launch_bounds__(kThreads) k_reduce_irfft(const float2* __restr
   __syncthreads();
   if (threadIdx.x >= 32) return;
   float* out = q + static_cast<long long>(blockIdx.x) * N;
-  warp_irfft_head<P>([&](int k) { return xs[k]; }, [&](int n, float v) { out[n] = v; }, tw, threadIdx.x);
+  const FftLane<P> fl = fft_lane<P>(tw, threadIdx.x);
+  warp_irfft_head<P>([&](int k) { return xs[k]; }, [&](int n, float v) { out[n] = v; }, tw, fl, threadIdx.x, scr);
 }
 
 // FP32 spectra -> resident storage (FP32 / BF16 / BF16 hi+lo), block copy:
@@ -352,7 +364,7 @@ cudaError_t launch_irfft_rows(const float2* X, long long rows, int Nt, const flo
   if (rows <= 0) return cudaSuccess;
   const unsigned grid = static_cast<unsigned>((rows + kWarps - 1) / kWarps);
   S2W_DISPATCH_P(Nt, {
-    const size_t sm = sizeof(float2) * 64 * P;
+    const size_t sm = sizeof(float2) * (64 * P + kWarps * 32 * P);
     k_irfft_rows<P><<<grid, kThreads, sm, st>>>(X, rows, tw, x);
   });
   return cudaGetLastError();
@@ -388,7 +400,7 @@ cudaError_t launch_reduce_irfft(const float2* part, int B, int No, int nseg, int
   const long long n = static_cast<long long>(B) * No;
   if (n <= 0) return cudaSuccess;
   S2W_DISPATCH_P(Nt, {
-    const size_t sm = sizeof(float2) * (64 * P + 32 * P + 1);
+    const size_t sm = sizeof(float2) * (64 * P + 32 * P + 1 + 32 * P);
     k_reduce_irfft<P><<<static_cast<unsigned>(n), kThreads, sm, st>>>(part, No, nseg, s_b, s_l, s_s, tw, q);
   });
   return cudaGetLastError();
