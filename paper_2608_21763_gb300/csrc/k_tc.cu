@@ -24,6 +24,8 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <type_traits>
+
 #include "s2w_internal.cuh"
 
 namespace s2w {
@@ -190,10 +192,11 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
 // both parts in every stage, and each K step issues A B, then A B_lo and/or
 // A_lo B into the same FP32 accumulator (the A_lo B_lo term, ~2^-18
 // relative, is dropped).
-template <int BK, int CL>
-__global__ void __launch_bounds__(kTcThreads, 1)
-    k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-              const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB2, const TcArgs a) {
+// SPLIT is a separate instantiation (and kernel) so that the plain BF16 kernel
+// carries none of the split path's code.
+template <int BK, int CL, bool SPLIT>
+__device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUtensorMap* tmB, const CUtensorMap* tmA2,
+                                             const CUtensorMap* tmB2, const TcArgs& a) {
   constexpr int kA = kBlockM * BK * 2;
   constexpr uint16_t kMask = static_cast<uint16_t>((1u << CL) - 1u);
   const uint32_t crank = CL > 1 ? cluster_ctarank() : 0u;
@@ -203,8 +206,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
   const int N = a.N;
   const int b_bytes = N * BK * 2;
-  const int a_all = kA * (1 + a.a_lo);                 // A (+ A_lo) bytes per stage
-  const int stage_bytes = a_all + b_bytes * (1 + a.b_lo);
+  constexpr int a_all = kA * (SPLIT ? 2 : 1);          // A (+ A_lo) bytes per stage
+  const int stage_bytes = a_all + b_bytes * (SPLIT ? 2 : 1);
   const int S = a.stages;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * stage_bytes);
   uint64_t* empty = full + S;
@@ -264,11 +267,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           }
           unsigned char* sa = smem + s * stage_bytes;
           mbar_arrive_expect_tx(full + s, stage_bytes);
-          tma_load_3d(sa, &tmA, kb * BK, mt * kBlockM, l, full + s);
-          if (a.a_lo) tma_load_3d(sa + kA, &tmA2, kb * BK, mt * kBlockM, l, full + s);
-          for (int h = 0; h <= a.b_lo; ++h) {
-            const CUtensorMap* tb = h ? &tmB2 : &tmB;
-            unsigned char* sb = sa + a_all + h * b_bytes;
+          tma_load_3d(sa, tmA, kb * BK, mt * kBlockM, l, full + s);
+          if constexpr (SPLIT) tma_load_3d(sa + kA, tmA2, kb * BK, mt * kBlockM, l, full + s);
+          auto load_b = [&](const CUtensorMap* tb, unsigned char* sb) {
             if (CL == 1) {
               for (int c = 0; c < n_mma; ++c)
                 tma_load_3d(sb + c * n_mma_cols * BK * 2, tb, kb * BK, c * n_mma_cols, l, full + s);
@@ -276,7 +277,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               tma_load_3d_mc(sb + crank * slice_rows * BK * 2, tb, kb * BK, static_cast<int>(crank) * slice_rows, l,
                              full + s, kMask);
             }
-          }
+          };
+          load_b(tmB, sa + a_all);
+          if constexpr (SPLIT) load_b(tmB2, sa + a_all + b_bytes);
         }
       }
       for (int kk = (it > S ? it - S : 0); kk < it; ++kk)
@@ -316,8 +319,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               const uint32_t boff = c * n_mma_cols * BK * 2 + k * 32;
               const uint64_t bd = sdesc_sw<BK>(sb + boff);
               tc_mma_bf16(tmem + c * n_mma_cols, ad, bd, idesc, (kb > kb0 || k > 0) ? 1u : 0u);
-              if (a.b_lo) tc_mma_bf16(tmem + c * n_mma_cols, ad, sdesc_sw<BK>(sb + b_bytes + boff), idesc, 1u);
-              if (a.a_lo) tc_mma_bf16(tmem + c * n_mma_cols, sdesc_sw<BK>(sa + kA + k * 32), bd, idesc, 1u);
+              if constexpr (SPLIT) {
+                tc_mma_bf16(tmem + c * n_mma_cols, ad, sdesc_sw<BK>(sb + b_bytes + boff), idesc, 1u);
+                tc_mma_bf16(tmem + c * n_mma_cols, sdesc_sw<BK>(sa + kA + k * 32), bd, idesc, 1u);
+              }
             }
           }
           if (CL == 1)
@@ -386,6 +391,20 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tmem_dealloc(tmem, a.tmem_cols);
   }
   if (CL > 1) cluster_sync_all();  // no CTA leaves while a peer may still signal it
+}
+
+template <int BK, int CL>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
+  tc_gemm_body<BK, CL, false>(&tmA, &tmB, nullptr, nullptr, a);
+}
+
+template <int BK, int CL>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_tc_gemm_split(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                    const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB2,
+                    const TcArgs a) {
+  tc_gemm_body<BK, CL, true>(&tmA, &tmB, &tmA2, &tmB2, a);
 }
 
 // B operand of the real embedding from complex FP32 x[l][t][c] (element
@@ -709,11 +728,13 @@ size_t tc_smem_bytes(int N, int stages, int a_lo, int b_lo) {
   return 1024 + static_cast<size_t>(stages) * tc_stage_bytes(N, a_lo, b_lo) + 8 * (2 * stages + 2) + 16;
 }
 
-template <int BK, int CL>
+template <int BK, int CL, bool SPLIT>
 cudaError_t launch_tc_cl(const CUtensorMap& tmA, const CUtensorMap& tmB, const CUtensorMap& tmA2,
                          const CUtensorMap& tmB2, const TcArgs& a, int num_sms, size_t smem, cudaStream_t st) {
   auto kern = k_tc_gemm<BK, CL>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  auto kern_s = k_tc_gemm_split<BK, CL>;
+  const void* kfn = SPLIT ? reinterpret_cast<const void*>(kern_s) : reinterpret_cast<const void*>(kern);
+  cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   const long long cunits = static_cast<long long>(a.Nb) * ((a.m_tiles + CL - 1) / CL) * a.n_kchunks;
   cudaLaunchConfig_t cfg = {};
@@ -723,7 +744,7 @@ cudaError_t launch_tc_cl(const CUtensorMap& tmA, const CUtensorMap& tmB, const C
   cfg.stream = st;
   long long nclusters = num_sms / CL;
   if (CL > 1) {
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 0);
+    e = cudaFuncSetAttribute(kfn, cudaFuncAttributeNonPortableClusterSizeAllowed, 0);
     if (e != cudaSuccess) return e;
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = CL;
@@ -733,14 +754,17 @@ cudaError_t launch_tc_cl(const CUtensorMap& tmA, const CUtensorMap& tmB, const C
     cfg.numAttrs = 1;
     cfg.gridDim = dim3(static_cast<unsigned>(nclusters * CL));
     int active = 0;
-    e = cudaOccupancyMaxActiveClusters(&active, kern, &cfg);
+    e = cudaOccupancyMaxActiveClusters(&active, kfn, &cfg);
     if (e != cudaSuccess) return e;
     if (active < 1) return cudaErrorInvalidConfiguration;
     nclusters = active;
   }
   if (nclusters > cunits) nclusters = cunits;
   cfg.gridDim = dim3(static_cast<unsigned>(nclusters * CL));
-  e = cudaLaunchKernelEx(&cfg, kern, tmA, tmB, tmA2, tmB2, a);
+  if (SPLIT)
+    e = cudaLaunchKernelEx(&cfg, kern_s, tmA, tmB, tmA2, tmB2, a);
+  else
+    e = cudaLaunchKernelEx(&cfg, kern, tmA, tmB, a);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
@@ -751,8 +775,8 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
   if (units <= 0) return cudaSuccess;
   if (a.N < 16 || a.N > 512 || a.N % 16 != 0 || (a.N > 256 && a.N % 256 != 0) || a.stages < 2)
     return cudaErrorInvalidValue;
-  if ((a.a_lo != 0 && a.a_lo != 1) || (a.b_lo != 0 && a.b_lo != 1) || (a.a_lo && !tmA2) || (a.b_lo && !tmB2))
-    return cudaErrorInvalidValue;
+  // split operands come in pairs: both A and B carry lo parts, or neither
+  if (a.a_lo != a.b_lo || (a.a_lo != 0 && a.a_lo != 1) || (a.a_lo && (!tmA2 || !tmB2))) return cudaErrorInvalidValue;
   const int CL = a.cluster < 1 ? 1 : a.cluster;
   if (CL != 1 && CL != 2 && CL != 4) return cudaErrorInvalidValue;
   if (CL > 1 && (a.N / CL < 8 || (a.N / CL) % 8 != 0 || a.N / CL > 256)) return cudaErrorInvalidValue;
@@ -760,14 +784,19 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   const CUtensorMap& a2 = a.a_lo ? *tmA2 : tmA;  // unused unless a_lo / b_lo
   const CUtensorMap& b2 = a.b_lo ? *tmB2 : tmB;
-  if (tc_block_k(a.N, a.a_lo | a.b_lo) == 64) {
-    if (CL == 1) return launch_tc_cl<64, 1>(tmA, tmB, a2, b2, a, num_sms, smem, st);
-    if (CL == 2) return launch_tc_cl<64, 2>(tmA, tmB, a2, b2, a, num_sms, smem, st);
-    return launch_tc_cl<64, 4>(tmA, tmB, a2, b2, a, num_sms, smem, st);
-  }
-  if (CL == 1) return launch_tc_cl<32, 1>(tmA, tmB, a2, b2, a, num_sms, smem, st);
-  if (CL == 2) return launch_tc_cl<32, 2>(tmA, tmB, a2, b2, a, num_sms, smem, st);
-  return launch_tc_cl<32, 4>(tmA, tmB, a2, b2, a, num_sms, smem, st);
+  auto go = [&](auto bk_tag, auto split_tag) -> cudaError_t {
+    constexpr int BK = decltype(bk_tag)::value;
+    constexpr bool SP = decltype(split_tag)::value;
+    if (CL == 1) return launch_tc_cl<BK, 1, SP>(tmA, tmB, a2, b2, a, num_sms, smem, st);
+    if (CL == 2) return launch_tc_cl<BK, 2, SP>(tmA, tmB, a2, b2, a, num_sms, smem, st);
+    return launch_tc_cl<BK, 4, SP>(tmA, tmB, a2, b2, a, num_sms, smem, st);
+  };
+  using bk64 = std::integral_constant<int, 64>;
+  using bk32 = std::integral_constant<int, 32>;
+  const bool sp = a.a_lo != 0;
+  if (tc_block_k(a.N, sp ? 1 : 0) == 64)
+    return sp ? go(bk64{}, std::true_type{}) : go(bk64{}, std::false_type{});
+  return sp ? go(bk32{}, std::true_type{}) : go(bk32{}, std::false_type{});
 }
 
 cudaError_t launch_tc_retransform(const CUtensorMap& tmT, const TcRtArgs& a, int num_sms, cudaStream_t st) {
