@@ -226,6 +226,30 @@ def workload(args):
     return wl
 
 
+# ------------------------------------------------------------------ replicas
+def replica_ruptures(slip, rank):
+    """Replicas evaluate their own ruptures: the pool rotated by the rank."""
+    return np.roll(slip, rank, axis=0) if rank > 0 else slip
+
+
+def max_over_ranks(x, world, device=None):
+    """Max of a per-rank scalar over the job (the slowest replica sets the
+    time); the identity on one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, units_per_rank, seconds):
+    """Whole-job throughput: the units every rank processed over the
+    max-over-ranks time."""
+    return world * units_per_rank / seconds
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_2608_21763_gb300 as s2w
@@ -236,9 +260,7 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     geom = wl.geometry_obj()
     pool = 8 if B <= 16 else 2
-    slip_np = wl.slip(geom, B=pool * B).astype(np.float32)
-    if rank > 0:  # replicas get their own ruptures
-        slip_np = np.roll(slip_np, rank, axis=0)
+    slip_np = replica_ruptures(wl.slip(geom, B=pool * B).astype(np.float32), rank)
     slip_np = slip_np.reshape(pool, B, wl.Ns, wl.Nt)
 
     t_setup = time.perf_counter()
@@ -334,12 +356,8 @@ def run_ours(args, rank, world, local_rank):
         stages, _ = ctx.profile_read()
         ctx.profile_enable(False)
         ctx.sync()
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-    value = world * B * args.steps / (elapsed_ms / 1e3)
+    elapsed_ms = max_over_ranks(elapsed_ms, world, dev)
+    value = job_rate(world, B * args.steps, elapsed_ms / 1e3)
 
     # ---- end to end through the public API with host buffers
     import torch as _t
@@ -358,16 +376,12 @@ def run_ours(args, rank, world, local_rank):
         step(k, host=True)   # H2D + D2H + sync inside the library call
     torch.cuda.synchronize(dev)
     e2e_s = time.perf_counter() - t0
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, world, dev)
     if gradient:
-        e2e = {"value": world * B * args.steps / e2e_s, "unit": UNIT,
+        e2e = {"value": job_rate(world, B * args.steps, e2e_s), "unit": UNIT,
                "h2d_bytes_per_step": B * (wl.Ns + wl.No) * wl.Nt * 4, "d2h_bytes_per_step": B * (wl.Ns * wl.Nt + 1) * 4}
     else:
-        e2e = {"value": world * B * args.steps / e2e_s, "unit": UNIT,
+        e2e = {"value": job_rate(world, B * args.steps, e2e_s), "unit": UNIT,
                "h2d_bytes_per_step": B * wl.Ns * wl.Nt * 4, "d2h_bytes_per_step": B * wl.No * wl.Nt * 4}
 
     if rank != 0:

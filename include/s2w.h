@@ -139,6 +139,18 @@ int s2w_load_greens(s2w_ctx *ctx, int g0, int ng, const float *G, void *stream);
  * and rules as s2w_load_greens (no alignment rule). */
 int s2w_load_adjoint(s2w_ctx *ctx, int g0, int ng, const float *P, void *stream);
 
+/* Load operator spectra directly (the form the paper keeps resident, Sec.
+ * II-C.1: the blocks' zero-padded DFTs, bins l = 0..Nt of length 2 Nt):
+ *   Ghat[l][r][j] = sum_{k<Nt} G[g0+r][j][k] exp(-2 pi i k l / (2 Nt)),
+ * complex64 (re, im interleaved), layout [Nt+1][ng][Ns].  Same storage
+ * conversion (precision, FP8 scales, 256-row chunk rule), transposed copies
+ * and pointer rules as s2w_load_greens; rows of both loaders may be mixed. */
+int s2w_load_greens_spectra(s2w_ctx *ctx, int g0, int ng, const float *Ghat, void *stream);
+
+/* Phat[l][o][r] = sum_{k<Nt} P[o][g0+r][k] exp(-2 pi i k l / (2 Nt)),
+ * complex64, layout [Nt+1][No][ng].  Rules as s2w_load_adjoint. */
+int s2w_load_adjoint_spectra(s2w_ctx *ctx, int g0, int ng, const float *Phat, void *stream);
+
 /* Waveforms for B ruptures: q[b] = F_q D_t F_G slip[b].
  *   slip      [B][Ns][Nt]  slip-rate histories s_j[n]          (input)
  *   q         [B][No][Nt]  observation waveforms q_o[n]        (output)
@@ -146,6 +158,16 @@ int s2w_load_adjoint(s2w_ctx *ctx, int g0, int ng, const float *P, void *stream)
  * 0 <= B <= max_batch (B = 0 does nothing).  Requires both operators fully
  * loaded (else S2W_ERR_STATE). */
 int s2w_waveforms(s2w_ctx *ctx, const float *slip, int B, float *q, float *seafloor, void *stream);
+
+/* s2w_waveforms for ruptures with uneven active durations: rupture b's
+ * slip-rate histories are taken as zero from sample active_len[b] on (those
+ * samples are never read, so they may hold anything).  active_len: host
+ * array of B ints in [0, Nt] (S2W_ERR_ARG otherwise); NULL = all Nt.  The
+ * frequency-domain contractions stay dense in the bins, so the cost is that
+ * of s2w_waveforms; results equal s2w_waveforms on zero-filled tails, bit for
+ * bit. */
+int s2w_waveforms_active(s2w_ctx *ctx, const float *slip, const int *active_len, int B, float *q,
+                         float *seafloor, void *stream);
 
 /* Adjoint of s2w_waveforms (the paper has no adjoint of the pipeline; this is
  * the transpose of the same map): for B residual sets r[b] ([No][Nt]),

@@ -29,7 +29,8 @@ STATUS = {0: "S2W_OK", -1: "S2W_ERR_ARG", -2: "S2W_ERR_OOM", -3: "S2W_ERR_STATE"
 
 # every entry point declared in include/s2w.h
 EXPORTS = ("s2w_default_opts", "s2w_create", "s2w_destroy", "s2w_operator_bytes",
-           "s2w_load_greens", "s2w_load_adjoint", "s2w_waveforms", "s2w_waveforms_noalloc",
+           "s2w_load_greens", "s2w_load_adjoint", "s2w_load_greens_spectra", "s2w_load_adjoint_spectra",
+           "s2w_waveforms", "s2w_waveforms_active", "s2w_waveforms_noalloc",
            "s2w_adjoint", "s2w_misfit_gradient", "s2w_waveforms_graph", "s2w_autotune", "s2w_rfft",
            "s2w_irfft", "s2w_profile_enable", "s2w_profile_read", "s2w_sync",
            "s2w_last_error", "s2w_status_string")
@@ -83,7 +84,10 @@ def lib():
     L.s2w_operator_bytes.argtypes = [V, ctypes.POINTER(SZ), ctypes.POINTER(SZ)]
     L.s2w_load_greens.argtypes = [V, I, I, P, V]
     L.s2w_load_adjoint.argtypes = [V, I, I, P, V]
+    L.s2w_load_greens_spectra.argtypes = [V, I, I, P, V]
+    L.s2w_load_adjoint_spectra.argtypes = [V, I, I, P, V]
     L.s2w_waveforms.argtypes = [V, P, I, P, P, V]
+    L.s2w_waveforms_active.argtypes = [V, P, P, I, P, P, V]
     L.s2w_waveforms_noalloc.argtypes = [V, P, P, V]
     L.s2w_adjoint.argtypes = [V, P, I, P, V]
     L.s2w_misfit_gradient.argtypes = [V, P, P, I, P, P, V]
@@ -99,7 +103,7 @@ def lib():
     L.s2w_status_string.argtypes = [I]
     L.s2w_status_string.restype = ctypes.c_char_p
     for name in ("s2w_create", "s2w_destroy", "s2w_operator_bytes", "s2w_load_greens",
-                 "s2w_load_adjoint", "s2w_waveforms", "s2w_waveforms_noalloc", "s2w_adjoint", "s2w_misfit_gradient", "s2w_waveforms_graph",
+                 "s2w_load_adjoint", "s2w_load_greens_spectra", "s2w_load_adjoint_spectra", "s2w_waveforms_active", "s2w_waveforms", "s2w_waveforms_noalloc", "s2w_adjoint", "s2w_misfit_gradient", "s2w_waveforms_graph",
                  "s2w_autotune", "s2w_rfft",
                  "s2w_irfft", "s2w_sync",
                  "s2w_profile_enable", "s2w_profile_read"):
@@ -120,6 +124,16 @@ def _ptr(a):
         assert a.dtype == torch.float32 and a.is_contiguous(), "need contiguous float32"
         return a.data_ptr()
     raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _as_float(a):
+    """complex64 array / tensor viewed as interleaved float32 (no copy)."""
+    if isinstance(a, np.ndarray):
+        assert a.dtype == np.complex64 and a.flags.c_contiguous, "need C-contiguous complex64"
+        return a.view(np.float32)
+    import torch
+    assert a.dtype == torch.complex64 and a.is_contiguous(), "need contiguous complex64"
+    return torch.view_as_real(a)
 
 
 def _stream(stream, *arrays):
@@ -203,6 +217,20 @@ class Context:
         self._check(lib().s2w_load_adjoint(self._h, int(g0), int(P.shape[1]), _ptr(P),
                                            _stream(stream, P)))
 
+    def load_greens_spectra(self, g0, Ghat, stream=None):
+        """Ghat: complex64 [Nt+1][ng][Ns], the zero-padded DFTs (length 2 Nt) of
+        rows g0..g0+ng-1 of the stage-1 blocks (host or device)."""
+        assert Ghat.shape[0] == self.Nb and Ghat.shape[2] == self.Ns, Ghat.shape
+        self._check(lib().s2w_load_greens_spectra(self._h, int(g0), int(Ghat.shape[1]), _ptr(_as_float(Ghat)),
+                                                  _stream(stream, Ghat)))
+
+    def load_adjoint_spectra(self, g0, Phat, stream=None):
+        """Phat: complex64 [Nt+1][No][ng], the zero-padded DFTs of columns
+        g0..g0+ng-1 of the stage-2 blocks."""
+        assert Phat.shape[0] == self.Nb and Phat.shape[1] == self.No, Phat.shape
+        self._check(lib().s2w_load_adjoint_spectra(self._h, int(g0), int(Phat.shape[2]), _ptr(_as_float(Phat)),
+                                                   _stream(stream, Phat)))
+
     def waveforms(self, slip, q=None, seafloor=None, stream=None):
         """q[b] = F_q D_t F_G slip[b].  slip: float32 [B][Ns][Nt] (torch CUDA
         tensor, or numpy for the host path).  Returns q (allocated like slip
@@ -232,6 +260,22 @@ class Context:
                 grad = torch.empty((B, self.Ns, self.Nt), dtype=torch.float32, device=r.device)
         self._check(lib().s2w_adjoint(self._h, _ptr(r), int(B), _ptr(grad), _stream(stream, r, grad)))
         return grad
+
+    def waveforms_active(self, slip, active_len, q=None, seafloor=None, stream=None):
+        """s2w_waveforms with per-rupture active durations: slip[b][:, n] for
+        n >= active_len[b] is taken as zero (never read)."""
+        B = slip.shape[0]
+        lens = np.ascontiguousarray(np.asarray(active_len, dtype=np.int32))
+        assert lens.shape == (B,), lens.shape
+        if q is None:
+            if isinstance(slip, np.ndarray):
+                q = np.empty((B, self.No, self.Nt), np.float32)
+            else:
+                import torch
+                q = torch.empty((B, self.No, self.Nt), dtype=torch.float32, device=slip.device)
+        self._check(lib().s2w_waveforms_active(self._h, _ptr(slip), lens.ctypes.data, int(B), _ptr(q),
+                                               _ptr(seafloor), _stream(stream, slip, q, seafloor)))
+        return q
 
     def waveforms_graph(self, slip, q, stream=None):
         """s2w_waveforms as a replayed CUDA graph (device tensors only; the

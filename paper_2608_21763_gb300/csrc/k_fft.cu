@@ -32,7 +32,8 @@ __device__ __forceinline__ void load_twiddles(float2* tw, const float2* __restri
 template <int P>
 __global__ void __launch_bounds__(kThreads) k_rfft_rows(const float* __restrict__ x, long long rows, int n_in,
                                                         const float2* __restrict__ twg, float2* __restrict__ X,
-                                                        long long ld_l, long long rows_a, long long ld_a) {
+                                                        long long ld_l, long long rows_a, long long ld_a,
+                                                        const int* __restrict__ lens) {
   constexpr int N = 32 * P;
   constexpr int L = 2 * N;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -44,8 +45,10 @@ __global__ void __launch_bounds__(kThreads) k_rfft_rows(const float* __restrict_
   const long long row = static_cast<long long>(blockIdx.x) * kWarps + (threadIdx.x >> 5);
   if (row >= rows) return;
   const float* xr = x + row * n_in;
+  // lens: active samples per group of rows_a rows (later samples read as 0)
+  const int n_act = lens != nullptr ? min(n_in, max(0, __ldg(lens + row / rows_a))) : n_in;
   const FftLane<P> fl = fft_lane<P>(tw, lane);
-  warp_rfft_stage<P>([&](int n) { return n < n_in ? __ldg(xr + n) : 0.f; }, zs, tw, fl, lane);
+  warp_rfft_stage<P>([&](int n) { return n < n_act ? __ldg(xr + n) : 0.f; }, zs, tw, fl, lane);
   float2* out = X + (row / rows_a) * ld_a + (row % rows_a);
   for (int k = lane; k <= N; k += 32) out[k * ld_l] = rfft_bin<P>(zs, tw, k);
 }
@@ -350,12 +353,12 @@ cudaError_t launch_twiddles(float2* tw, int L, cudaStream_t st) {
 }
 
 cudaError_t launch_rfft_rows(const float* x, long long rows, int n_in, int Nt, const float2* tw, float2* X,
-                             long long ld_l, long long rows_a, long long ld_a, cudaStream_t st) {
+                             long long ld_l, long long rows_a, long long ld_a, cudaStream_t st, const int* lens) {
   if (rows <= 0) return cudaSuccess;
   const unsigned grid = static_cast<unsigned>((rows + kWarps - 1) / kWarps);
   S2W_DISPATCH_P(Nt, {
     const size_t sm = sizeof(float2) * (64 * P + kWarps * 32 * P);
-    k_rfft_rows<P><<<grid, kThreads, sm, st>>>(x, rows, n_in, tw, X, ld_l, rows_a, ld_a);
+    k_rfft_rows<P><<<grid, kThreads, sm, st>>>(x, rows, n_in, tw, X, ld_l, rows_a, ld_a, lens);
   });
   return cudaGetLastError();
 }

@@ -88,6 +88,8 @@ struct s2w_ctx {
   void* tc_ub = nullptr;      // [Nb][tc_n1max][2 Ng_pad2] bf16: D_t^T-retransformed spectra, conjugate embedding
   void* tc_ub_lo = nullptr;
   float2* tc_ghat = nullptr;  // [Nb][tc_bsub][Ns] complex FP32
+  int* ws_lens = nullptr;       // active samples per rupture (s2w_waveforms_active), [max_batch]
+  const int* cur_lens = nullptr;  // set for the duration of an s2w_waveforms_active call
   bool tc_split = false;    // BF16 hi/lo operands and activations (three MMAs per K step)
   void* tc_bp1_lo = nullptr;  // split: low-order parts of tc_bp1, tc_vhat, tc_p2
   void* tc_vhat_lo = nullptr;
@@ -244,7 +246,7 @@ void free_all(s2w_ctx* c) {
                 c->ws_vhat, c->ws_part, c->ws_q, c->ws_seafloor, c->d_status, c->tc_bp1, c->ws_rhat, c->ws_gpart, c->ws_resid, c->ws_d, c->ws_loss,
                 c->tc_mhat, c->tc_vhat, c->tc_part, c->tc_p2, c->tc_T, c->tc_bp1_lo, c->tc_vhat_lo, c->tc_p2_lo,
                 c->tc_gT, c->tc_gT_lo, c->tc_pT, c->tc_pT_lo, c->tc_rb, c->tc_rb_lo, c->tc_ub, c->tc_ub_lo,
-                c->tc_ghat};
+                c->tc_ghat, c->ws_lens};
   for (void* p : ps)
     if (p) cudaFree(p);
 }
@@ -403,7 +405,8 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
     {
       StageTimer t(ctx, 0, st);
       CK(launch_rfft_rows(slip_d + static_cast<long long>(b0) * Ns * Nt, Bs * Ns, static_cast<int>(Nt),
-                          static_cast<int>(Nt), ctx->tw, ctx->ws_shat, Bs * Ns_pad, Ns, Ns_pad, st));
+                          static_cast<int>(Nt), ctx->tw, ctx->ws_shat, Bs * Ns_pad, Ns, Ns_pad, st,
+                          ctx->cur_lens ? ctx->cur_lens + b0 : nullptr));
     }
     const int sp = ctx->tc_split ? 1 : 0;
     {
@@ -634,6 +637,7 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
   if ((e = dalloc(&ctx->ws_resid, sizeof(float) * B * No * Nt)) != cudaSuccess) return bad(e, "residuals");
   if ((e = dalloc(&ctx->ws_d, sizeof(float) * B * No * Nt)) != cudaSuccess) return bad(e, "targets");
   if ((e = dalloc(&ctx->ws_loss, sizeof(float) * B)) != cudaSuccess) return bad(e, "losses");
+  if ((e = dalloc(&ctx->ws_lens, sizeof(int) * B)) != cudaSuccess) return bad(e, "active lengths");
   if ((e = dalloc(&ctx->ws_gpart, sizeof(float2) * Nb * ctx->adj_nchunk * ctx->Ns_pad)) != cudaSuccess)
     return bad(e, "adjoint partials");
   ctx->tc_on = (o.prec_g == S2W_PREC_BF16 || o.prec_g == S2W_PREC_BF16_HILO) && 2 * No <= 256 &&
@@ -737,7 +741,11 @@ int s2w_operator_bytes(const s2w_ctx* ctx, size_t* g_bytes, size_t* p_bytes) {
   return S2W_OK;
 }
 
-int s2w_load_greens(s2w_ctx* ctx, int g0, int ng, const float* G, void* stream) {
+namespace {
+
+// Shared by the time-domain and the spectral loaders: spectra == true takes
+// complex64 Ghat[l][r][j] ([Nb][ng][Ns]) instead of time-domain rows.
+int load_greens_impl(s2w_ctx* ctx, int g0, int ng, const float* G, bool spectra, void* stream) {
   if (!ctx) return S2W_ERR_ARG;
   if (!G || g0 < 0 || ng < 1 || static_cast<long long>(g0) + ng > ctx->Ng)
     return fail(ctx, S2W_ERR_ARG, "load_greens: rows [%d, %d) outside [0, %d) or G is NULL", g0, g0 + ng, ctx->Ng);
@@ -762,11 +770,20 @@ int s2w_load_greens(s2w_ctx* ctx, int g0, int ng, const float* G, void* stream) 
     const long long rc = std::min(RC, static_cast<long long>(ng) - r);
     const long long row0 = g0 + r;
     auto step = [&]() -> int {
-      CK(cudaMemcpyAsync(stage_t, G + r * Ns * Nt, sizeof(float) * rc * Ns * Nt, cudaMemcpyDefault, st));
       CK(cudaMemsetAsync(stage_s, 0, sizeof(float2) * Nb * rc * Ns_pad, st));
-      ctx->launches += fp8 ? 3 : 2;
-      CK(launch_rfft_rows(stage_t, rc * Ns, static_cast<int>(Nt), static_cast<int>(Nt), ctx->tw, stage_s,
-                          rc * Ns_pad, Ns, Ns_pad, st));
+      if (spectra) {  // bin l: rows r .. r+rc of Ghat_l, re-pitched to Ns_pad
+        ctx->launches += fp8 ? 1 : 0;
+        for (long long l = 0; l < Nb; ++l)
+          CK(cudaMemcpy2DAsync(stage_s + l * rc * Ns_pad, sizeof(float2) * Ns_pad,
+                               G + 2 * ((l * ng + r) * Ns), sizeof(float2) * Ns, sizeof(float2) * Ns, rc,
+                               cudaMemcpyDefault, st));
+      } else {
+        CK(cudaMemcpyAsync(stage_t, G + r * Ns * Nt, sizeof(float) * rc * Ns * Nt, cudaMemcpyDefault, st));
+        ctx->launches += fp8 ? 2 : 1;
+        CK(launch_rfft_rows(stage_t, rc * Ns, static_cast<int>(Nt), static_cast<int>(Nt), ctx->tw, stage_s,
+                            rc * Ns_pad, Ns, Ns_pad, st));
+      }
+      ctx->launches += 1;
       if (fp8) {
         CK(launch_fp8_store(stage_s, static_cast<int>(Nb), rc, static_cast<int>(Ns_pad), row0, ctx->Ng,
                             ctx->G_scale, ctx->nblk, ctx->G, st));
@@ -798,7 +815,8 @@ int s2w_load_greens(s2w_ctx* ctx, int g0, int ng, const float* G, void* stream) 
   return S2W_OK;
 }
 
-int s2w_load_adjoint(s2w_ctx* ctx, int g0, int ng, const float* P, void* stream) {
+// spectra == true takes complex64 Phat[l][o][r] ([Nb][No][ng]).
+int load_adjoint_impl(s2w_ctx* ctx, int g0, int ng, const float* P, bool spectra, void* stream) {
   if (!ctx) return S2W_ERR_ARG;
   if (!P || g0 < 0 || ng < 1 || static_cast<long long>(g0) + ng > ctx->Ng)
     return fail(ctx, S2W_ERR_ARG, "load_adjoint: columns [%d, %d) outside [0, %d) or P is NULL", g0, g0 + ng,
@@ -820,11 +838,18 @@ int s2w_load_adjoint(s2w_ctx* ctx, int g0, int ng, const float* P, void* stream)
   for (long long c = 0; c < ng && rc_status == S2W_OK; c += RC) {
     const long long rc = std::min(RC, static_cast<long long>(ng) - c);
     auto step = [&]() -> int {
-      CK(cudaMemcpy2DAsync(stage_t, sizeof(float) * rc * Nt, P + c * Nt, sizeof(float) * ng * Nt,
-                           sizeof(float) * rc * Nt, No, cudaMemcpyDefault, st));
-      ctx->launches += 2;
-      CK(launch_rfft_rows(stage_t, No * rc, static_cast<int>(Nt), static_cast<int>(Nt), ctx->tw, stage_s, No * rc,
-                          rc, rc, st));
+      if (spectra) {  // bin l: columns c .. c+rc of every observation's row of Phat_l
+        for (long long l = 0; l < Nb; ++l)
+          CK(cudaMemcpy2DAsync(stage_s + l * No * rc, sizeof(float2) * rc, P + 2 * (l * No * ng + c),
+                               sizeof(float2) * ng, sizeof(float2) * rc, No, cudaMemcpyDefault, st));
+        ctx->launches += 1;
+      } else {
+        CK(cudaMemcpy2DAsync(stage_t, sizeof(float) * rc * Nt, P + c * Nt, sizeof(float) * ng * Nt,
+                             sizeof(float) * rc * Nt, No, cudaMemcpyDefault, st));
+        ctx->launches += 2;
+        CK(launch_rfft_rows(stage_t, No * rc, static_cast<int>(Nt), static_cast<int>(Nt), ctx->tw, stage_s,
+                            No * rc, rc, rc, st));
+      }
       CK(launch_store_adjoint(stage_s, static_cast<int>(Nb), static_cast<int>(No), rc, g0 + c, ctx->RL, ctx->nseg,
                               ctx->opts.prec_p, ctx->P, st));
       if (ctx->tc_on) {
@@ -854,6 +879,24 @@ int s2w_load_adjoint(s2w_ctx* ctx, int g0, int ng, const float* P, void* stream)
     ctx->p_loaded[g0 + r] = 1;
   }
   return S2W_OK;
+}
+
+}  // namespace
+
+int s2w_load_greens(s2w_ctx* ctx, int g0, int ng, const float* G, void* stream) {
+  return load_greens_impl(ctx, g0, ng, G, false, stream);
+}
+
+int s2w_load_greens_spectra(s2w_ctx* ctx, int g0, int ng, const float* Ghat, void* stream) {
+  return load_greens_impl(ctx, g0, ng, Ghat, true, stream);
+}
+
+int s2w_load_adjoint(s2w_ctx* ctx, int g0, int ng, const float* P, void* stream) {
+  return load_adjoint_impl(ctx, g0, ng, P, false, stream);
+}
+
+int s2w_load_adjoint_spectra(s2w_ctx* ctx, int g0, int ng, const float* Phat, void* stream) {
+  return load_adjoint_impl(ctx, g0, ng, Phat, true, stream);
 }
 
 int s2w_waveforms(s2w_ctx* ctx, const float* slip, int B, float* q, float* seafloor, void* stream) {
@@ -896,7 +939,8 @@ int s2w_waveforms(s2w_ctx* ctx, const float* slip, int B, float* q, float* seafl
     {
       StageTimer t(ctx, 0, st);
       CK(launch_rfft_rows(slip_d + static_cast<long long>(g0) * Ns * Nt, Bg * Ns, static_cast<int>(Nt),
-                          static_cast<int>(Nt), ctx->tw, ctx->ws_shat, Bg * Ns_pad, Ns, Ns_pad, st));
+                          static_cast<int>(Nt), ctx->tw, ctx->ws_shat, Bg * Ns_pad, Ns, Ns_pad, st,
+                          ctx->cur_lens ? ctx->cur_lens + g0 : nullptr));
     }
     const long long part_b = Nb * ctx->nseg * No;
     for (int b = 0; b < Bg; ++b) {
@@ -961,6 +1005,28 @@ int s2w_waveforms(s2w_ctx* ctx, const float* slip, int B, float* q, float* seafl
   }
   if (kq == 0 || (seafloor && kf == 0)) CK(cudaStreamSynchronize(st));
   return S2W_OK;
+}
+
+int s2w_waveforms_active(s2w_ctx* ctx, const float* slip, const int* active_len, int B, float* q, float* seafloor,
+                         void* stream) {
+  if (!ctx) return S2W_ERR_ARG;
+  if (B < 0 || B > ctx->opts.max_batch)
+    return fail(ctx, S2W_ERR_ARG, "waveforms_active: B=%d outside [0, max_batch=%d]", B, ctx->opts.max_batch);
+  if (B == 0) return S2W_OK;
+  if (!active_len) return s2w_waveforms(ctx, slip, B, q, seafloor, stream);
+  DeviceGuard guard(ctx->device);
+  if (pointer_kind(active_len, ctx->device) != 0)
+    return fail(ctx, S2W_ERR_ARG, "waveforms_active: active_len must be a host array");
+  for (int b = 0; b < B; ++b)
+    if (active_len[b] < 0 || active_len[b] > ctx->Nt)
+      return fail(ctx, S2W_ERR_ARG, "waveforms_active: active_len[%d] = %d outside [0, Nt=%lld]", b, active_len[b],
+                  ctx->Nt);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CK(cudaMemcpyAsync(ctx->ws_lens, active_len, sizeof(int) * B, cudaMemcpyHostToDevice, st));
+  ctx->cur_lens = ctx->ws_lens;
+  const int rc = s2w_waveforms(ctx, slip, B, q, seafloor, stream);
+  ctx->cur_lens = nullptr;
+  return rc;
 }
 
 int s2w_adjoint(s2w_ctx* ctx, const float* r, int B, float* grad_s, void* stream) {

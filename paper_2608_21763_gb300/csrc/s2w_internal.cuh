@@ -126,9 +126,11 @@ __device__ __forceinline__ void bulk_g2s(void* sdst, const void* gsrc, uint32_t 
 // k_fft.cu
 cudaError_t launch_twiddles(float2* tw, int L, cudaStream_t st);
 // Rows x[row][0..n_in) zero-padded to L = 2 Nt; bins l = 0..Nt of row `row`
-// go to X[l * ld_l + (row / rows_a) * ld_a + row % rows_a].
+// go to X[l * ld_l + (row / rows_a) * ld_a + row % rows_a].  lens (device,
+// optional): row `row` uses only its first lens[row / rows_a] samples.
 cudaError_t launch_rfft_rows(const float* x, long long rows, int n_in, int Nt, const float2* tw, float2* X,
-                             long long ld_l, long long rows_a, long long ld_a, cudaStream_t st);
+                             long long ld_l, long long rows_a, long long ld_a, cudaStream_t st,
+                             const int* lens = nullptr);
 // Rows X[row][0..Nt] -> first Nt samples x[row][0..Nt) of the length-2Nt IFFT.
 cudaError_t launch_irfft_rows(const float2* X, long long rows, int Nt, const float2* tw, float* x, cudaStream_t st);
 // Retransform of `nb` ruptures (grid y): rupture y reads mhat + y * mhat_ld_b

@@ -262,3 +262,81 @@ def test_plain_workload_full_size(plain_reference, prec_g, prec_p):
     tol = max(TOL[prec_g], TOL[prec_p])
     assert_parity(q, q_ref, wn, kappa, tol=tol, label=f"plain {prec_g}/{prec_p}")
     ctx.sync()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_spectra_loaders_match_time_domain_loaders(prec):
+    """s2w_load_greens_spectra / s2w_load_adjoint_spectra with spectra formed
+    by numpy (FP64 zero-padded rfft, rounded to complex64): mixed with the
+    time-domain loader over row chunks, host and device sources; waveforms
+    meet the same bars and agree with a context loaded in the time domain."""
+    Ns, Ng, No, Nt, B = 24, 700, 6, 64, 3
+    geom = compact_box(Ns, Ng, No, seed=41)
+    G = geom.greens_rows(0, Ng, Nt)
+    P = geom.adjoint_cols(0, Ng, Nt)
+    Ghat = np.ascontiguousarray(np.fft.rfft(G, n=2 * Nt, axis=2).transpose(2, 0, 1)).astype(np.complex64)
+    Phat = np.ascontiguousarray(np.fft.rfft(P, n=2 * Nt, axis=2).transpose(2, 0, 1)).astype(np.complex64)
+    ctx = s2w.Context(Ns, Ng, No, Nt, prec_g=prec, max_batch=B, engine="stream")
+    ctx.load_greens_spectra(0, np.ascontiguousarray(Ghat[:, :300]))
+    ctx.load_greens(300, geom.greens_rows(300, Ng, Nt, np.float32))
+    ctx.load_adjoint_spectra(0, torch.tensor(Phat[:, :, :512], device="cuda"))
+    ctx.load_adjoint(512, np.ascontiguousarray(geom.adjoint_cols(512, Ng, Nt, np.float32)))
+    rng = np.random.default_rng(42)
+    slip = rng.standard_normal((B, Ns, Nt))
+    slip[:, :, Nt // 2:] = 0
+    q = ctx.waveforms(torch.tensor(slip, dtype=torch.float32, device="cuda")).cpu().numpy()
+    ctx.sync()
+    q_ref = oracle.waveforms(G, P, slip)
+    tol = {"fp32": 1e-5, "bf16": 5e-3}[prec]
+    assert_parity(q, q_ref, *window_norms(G, P, slip), tol=tol, label=f"spectra loaders {prec}")
+    ct = make_context(s2w, geom, Nt, prec_g=prec, max_batch=B, engine="stream")
+    qt = ct.waveforms(torch.tensor(slip, dtype=torch.float32, device="cuda")).cpu().numpy()
+    wn, _ = window_norms(G, P, slip)
+    assert np.all(np.linalg.norm((q - qt).reshape(B, -1), axis=1) <= 2 * tol * wn)
+
+
+def test_spectra_loaders_feed_the_tensor_adjoint():
+    """Spectra loaded directly also build the transposed copies of the
+    tensor-engine adjoint (split precision)."""
+    Ns, Ng, No, Nt, B = 16, 900, 5, 32, 4
+    geom = compact_box(Ns, Ng, No, seed=43)
+    G = geom.greens_rows(0, Ng, Nt)
+    P = geom.adjoint_cols(0, Ng, Nt)
+    Ghat = np.ascontiguousarray(np.fft.rfft(G, n=2 * Nt, axis=2).transpose(2, 0, 1)).astype(np.complex64)
+    Phat = np.ascontiguousarray(np.fft.rfft(P, n=2 * Nt, axis=2).transpose(2, 0, 1)).astype(np.complex64)
+    ctx = s2w.Context(Ns, Ng, No, Nt, prec_g="bf16_hilo", max_batch=B, engine="tensor", tc_adjoint=True)
+    ctx.load_greens_spectra(0, Ghat)
+    ctx.load_adjoint_spectra(0, Phat)
+    r = np.random.default_rng(44).standard_normal((B, No, Nt))
+    g = ctx.adjoint(torch.tensor(r, dtype=torch.float32, device="cuda")).cpu().numpy()
+    ctx.sync()
+    gw = oracle.fft_window_adjoint(G, P, r)
+    err = np.linalg.norm((g - gw[..., Nt:]).reshape(B, -1), axis=1)
+    assert np.all(err <= 3e-5 * np.linalg.norm(gw.reshape(B, -1), axis=1)), err
+
+
+@pytest.mark.parametrize("engine,prec", [("stream", "fp32"), ("tensor", "bf16"), ("tensor", "bf16_hilo")])
+def test_active_lengths_match_zero_filled_tails(engine, prec):
+    """s2w_waveforms_active: samples past each rupture's active length are
+    never read (they hold NaN here) and the result equals s2w_waveforms on
+    zero-filled tails, bit for bit; lengths 0 and Nt included."""
+    Ns, Ng, No, Nt = 24, 700, 6, 64
+    lens = [0, 1, 17, 32, 63, 64]
+    B = len(lens)
+    geom = compact_box(Ns, Ng, No, seed=51)
+    rng = np.random.default_rng(52)
+    slip = rng.standard_normal((B, Ns, Nt)).astype(np.float32)
+    zeroed, garbage = slip.copy(), slip.copy()
+    for b, n in enumerate(lens):
+        zeroed[b, :, n:] = 0
+        garbage[b, :, n:] = np.nan
+    ctx = make_context(s2w, geom, Nt, prec_g=prec, max_batch=B, engine=engine)
+    q0 = ctx.waveforms(torch.tensor(zeroed, device="cuda")).cpu().numpy()
+    q1 = ctx.waveforms_active(torch.tensor(garbage, device="cuda"), lens).cpu().numpy()
+    assert np.array_equal(q0, q1)
+    assert np.all(q0[0] == 0)
+    q2 = ctx.waveforms_active(garbage, lens)  # host path
+    assert np.array_equal(q0, q2)
+    with pytest.raises(s2w.S2WError):
+        ctx.waveforms_active(torch.tensor(zeroed, device="cuda"), [Nt + 1] + lens[1:])
+    ctx.sync()
