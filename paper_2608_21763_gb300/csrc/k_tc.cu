@@ -33,6 +33,7 @@ namespace s2w {
 namespace {
 
 constexpr int kTcThreads = 192;  // warps: 0 TMA producer, 1 MMA, 2-5 epilogue
+constexpr int kTcThreadsF8 = 320;  // FP8 A: + warps 6-9 widen the A tiles to BF16
 constexpr int kBlockM = 128;
 constexpr int kBlockK = 64;  // bf16 elements per 128-byte swizzle row
 constexpr int kABytes = kBlockM * kBlockK * 2;
@@ -75,6 +76,10 @@ __device__ __forceinline__ uint32_t cluster_count_x() {
 }
 __device__ __forceinline__ void cluster_sync_all() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -192,11 +197,19 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
 // both parts in every stage, and each K step issues A B, then A B_lo and/or
 // A_lo B into the same FP32 accumulator (the A_lo B_lo term, ~2^-18
 // relative, is dropped).
-// SPLIT is a separate instantiation (and kernel) so that the plain BF16 kernel
-// carries none of the split path's code.
-template <int BK, int CL, bool SPLIT>
+// MODE: 0 BF16 operands; 1 split (hi/lo parts of both operands); 2 FP8 e4m3
+// A: TMA brings the FP8 tile (row-major, one byte per K element) into a
+// staging slot of the stage, warps 6-9 widen it exactly to BF16 (e4m3 ->
+// f16 -> f32 -> bf16 loses nothing) into the swizzled A slot and signal
+// `aready`; the per-(bin, 256-row) scale is applied in the epilogue
+// (row_scale).  Each MODE is its own instantiation and kernel, so the plain
+// kernel carries none of the other modes' code.
+template <int BK, int CL, int MODE>
 __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUtensorMap* tmB, const CUtensorMap* tmA2,
                                              const CUtensorMap* tmB2, const TcArgs& a) {
+  constexpr bool SPLIT = MODE == 1;
+  constexpr bool F8 = MODE == 2;
+  constexpr int kStg = F8 ? kBlockM * BK : 0;  // FP8 staging bytes per stage
   constexpr int kA = kBlockM * BK * 2;
   constexpr uint16_t kMask = static_cast<uint16_t>((1u << CL) - 1u);
   const uint32_t crank = CL > 1 ? cluster_ctarank() : 0u;
@@ -207,11 +220,12 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUten
   const int N = a.N;
   const int b_bytes = N * BK * 2;
   constexpr int a_all = kA * (SPLIT ? 2 : 1);          // A (+ A_lo) bytes per stage
-  const int stage_bytes = a_all + b_bytes * (SPLIT ? 2 : 1);
+  const int stage_bytes = a_all + b_bytes * (SPLIT ? 2 : 1) + kStg;
   const int S = a.stages;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * stage_bytes);
   uint64_t* empty = full + S;
-  uint64_t* acc_full = empty + S;
+  uint64_t* aready = empty + S;  // F8: A slot widened (count 4 converter warps)
+  uint64_t* acc_full = aready + (F8 ? S : 0);
   uint64_t* acc_empty = acc_full + 1;
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(acc_empty + 1);
   const int warp = threadIdx.x >> 5;
@@ -228,6 +242,7 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUten
     for (int s = 0; s < S; ++s) {
       mbar_init(full + s, 1);
       mbar_init(empty + s, CL);
+      if (F8) mbar_init(aready + s, 4);
     }
     mbar_init(acc_full, 1);
     mbar_init(acc_empty, 4);
@@ -266,8 +281,11 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUten
             break;
           }
           unsigned char* sa = smem + s * stage_bytes;
-          mbar_arrive_expect_tx(full + s, stage_bytes);
-          tma_load_3d(sa, tmA, kb * BK, mt * kBlockM, l, full + s);
+          mbar_arrive_expect_tx(full + s, stage_bytes - (F8 ? kA : 0));  // F8: the A slot is not TMA's
+          if constexpr (F8)
+            tma_load_3d(sa + a_all + b_bytes, tmA, kb * BK, mt * kBlockM, l, full + s);
+          else
+            tma_load_3d(sa, tmA, kb * BK, mt * kBlockM, l, full + s);
           if constexpr (SPLIT) tma_load_3d(sa + kA, tmA2, kb * BK, mt * kBlockM, l, full + s);
           auto load_b = [&](const CUtensorMap* tb, unsigned char* sb) {
             if (CL == 1) {
@@ -305,7 +323,7 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUten
         tc_fence_after();
         for (int kb = kb0; kb < kb1; ++kb, ++it) {
           const int s = it % S;
-          if (!mbar_wait_bounded(full + s, (it / S) & 1, a.status, DEV_ERR_TIMEOUT_FULL)) {
+          if (!mbar_wait_bounded(F8 ? aready + s : full + s, (it / S) & 1, a.status, DEV_ERR_TIMEOUT_FULL)) {
             ok = false;
             break;
           }
@@ -336,6 +354,56 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUten
       }
       // the epilogue consumes the last accumulator; wait for it before teardown
       if (acc_it > 0) mbar_wait_bounded(acc_empty, (acc_it - 1) & 1, a.status, DEV_ERR_TIMEOUT_MMA);
+    }
+  } else if (F8 && warp >= 6) {
+    // converter warps 6..9: thread t widens row t of each FP8 A tile
+    const int t = threadIdx.x - 192;
+    int it = 0;
+    bool ok = true;
+    for (long long u = cid; u < units && ok; u += ncl) {
+      int l, mt, kc;
+      unit_coords(u, l, mt, kc);
+      const int kb0 = kc * a.kblocks_per_chunk;
+      const int kb1 = min(nk_total, kb0 + a.kblocks_per_chunk);
+      for (int kb = kb0; kb < kb1; ++kb, ++it) {
+        const int s = it % S;
+        if (!mbar_wait_bounded(full + s, (it / S) & 1, a.status, DEV_ERR_TIMEOUT_FULL)) {
+          ok = false;
+          break;
+        }
+        unsigned char* sa = smem + s * stage_bytes;
+        const uint4* src = reinterpret_cast<const uint4*>(sa + a_all + b_bytes + t * BK);
+        unsigned char* dst = sa + t * (BK * 2);
+#pragma unroll
+        for (int c = 0; c < BK / 16; ++c) {  // 16 FP8 in -> two 16-byte BF16 chunks out
+          const uint4 w = src[(c + t) % (BK / 16)];  // staggered start: fewer bank conflicts
+          const int cc = (c + t) % (BK / 16);
+          const unsigned ww[4] = {w.x, w.y, w.z, w.w};
+          unsigned o[8];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2(
+                  static_cast<__nv_fp8x2_storage_t>((ww[k] >> (16 * h)) & 0xffffu), __NV_E4M3);
+              const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&hr));
+              const __nv_bfloat162 b = __floats2bfloat162_rn(f.x, f.y);
+              o[2 * k + h] = *reinterpret_cast<const unsigned*>(&b);
+            }
+          }
+          // 16-byte chunks 2 cc and 2 cc + 1 of the row, placed as the TMA
+          // swizzle would (128 B: chunk ^ (row & 7); 64 B: chunk ^ ((row >> 1) & 3))
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int ch = 2 * cc + h;
+            const int sw = BK == 64 ? (ch ^ (t & 7)) : (ch ^ ((t >> 1) & 3));
+            *reinterpret_cast<uint4*>(dst + (sw << 4)) = make_uint4(o[4 * h], o[4 * h + 1], o[4 * h + 2], o[4 * h + 3]);
+          }
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(aready + s);
+      }
     }
   } else {
     // epilogue warps 2..5
@@ -396,7 +464,13 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUten
 template <int BK, int CL>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
-  tc_gemm_body<BK, CL, false>(&tmA, &tmB, nullptr, nullptr, a);
+  tc_gemm_body<BK, CL, 0>(&tmA, &tmB, nullptr, nullptr, a);
+}
+
+template <int BK, int CL>
+__global__ void __launch_bounds__(kTcThreadsF8, 1)
+    k_tc_gemm_f8(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
+  tc_gemm_body<BK, CL, 2>(&tmA, &tmB, nullptr, nullptr, a);
 }
 
 template <int BK, int CL>
@@ -404,7 +478,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     k_tc_gemm_split(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB2,
                     const TcArgs a) {
-  tc_gemm_body<BK, CL, true>(&tmA, &tmB, &tmA2, &tmB2, a);
+  tc_gemm_body<BK, CL, 1>(&tmA, &tmB, &tmA2, &tmB2, a);
 }
 
 // B operand of the real embedding from complex FP32 x[l][t][c] (element
@@ -478,9 +552,6 @@ __global__ void k_pack_a(const float2* __restrict__ src, int Nb, int rows, long 
 constexpr int kRtThreads = 448;
 constexpr int kRtFillWarps = 8;
 
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
 
 __global__ void __launch_bounds__(kRtThreads, 1)
     k_tc_retransform(const __grid_constant__ CUtensorMap tmT, const TcRtArgs a) {
@@ -687,15 +758,20 @@ PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 }  // namespace
 
+namespace {
+cudaError_t resolve_encode() {
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+  if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || fn == nullptr) return cudaErrorNotSupported;
+  g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  return cudaSuccess;
+}
+}  // namespace
+
 cudaError_t tc_encode_3d(CUtensorMap* out, const void* base, long long K, long long rows, long long nbatch,
                          long long row_pitch_elems, int box_rows, int bk) {
-  if (g_encode == nullptr) {
-    void* fn = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
-    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || fn == nullptr) return cudaErrorNotSupported;
-    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-  }
+  if (g_encode == nullptr && resolve_encode() != cudaSuccess) return cudaErrorNotSupported;
   const cuuint64_t dims[3] = {static_cast<cuuint64_t>(K), static_cast<cuuint64_t>(rows),
                               static_cast<cuuint64_t>(nbatch)};
   const cuuint64_t strides[2] = {static_cast<cuuint64_t>(row_pitch_elems) * 2,
@@ -709,37 +785,54 @@ cudaError_t tc_encode_3d(CUtensorMap* out, const void* base, long long K, long l
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+cudaError_t tc_encode_3d_u8(CUtensorMap* out, const void* base, long long K, long long rows, long long nbatch,
+                            int box_rows, int bk) {
+  if (g_encode == nullptr && resolve_encode() != cudaSuccess) return cudaErrorNotSupported;
+  const cuuint64_t dims[3] = {static_cast<cuuint64_t>(K), static_cast<cuuint64_t>(rows),
+                              static_cast<cuuint64_t>(nbatch)};
+  const cuuint64_t strides[2] = {static_cast<cuuint64_t>(K), static_cast<cuuint64_t>(K) * static_cast<cuuint64_t>(rows)};
+  const cuuint32_t box[3] = {static_cast<cuuint32_t>(bk), static_cast<cuuint32_t>(box_rows), 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = g_encode(out, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<void*>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 int tc_block_k(int N, int split) { return (N > 256 || (split && N > 128)) ? 32 : 64; }
 
 namespace {
-int tc_stage_bytes(int N, int a_lo, int b_lo) {
+int tc_stage_bytes(int N, int a_lo, int b_lo, int fp8) {
   const int bk = tc_block_k(N, a_lo | b_lo);
-  return kBlockM * bk * 2 * (1 + a_lo) + N * bk * 2 * (1 + b_lo);
+  return kBlockM * bk * 2 * (1 + a_lo) + N * bk * 2 * (1 + b_lo) + (fp8 ? kBlockM * bk : 0);
 }
 }  // namespace
 
-int tc_stages_for(int N, int a_lo, int b_lo) {
-  int s = kSmemBudget / tc_stage_bytes(N, a_lo, b_lo);
+int tc_stages_for(int N, int a_lo, int b_lo, int fp8) {
+  int s = kSmemBudget / tc_stage_bytes(N, a_lo, b_lo, fp8);
   if (s > 8) s = 8;
   return s;
 }
 
-size_t tc_smem_bytes(int N, int stages, int a_lo, int b_lo) {
-  return 1024 + static_cast<size_t>(stages) * tc_stage_bytes(N, a_lo, b_lo) + 8 * (2 * stages + 2) + 16;
+size_t tc_smem_bytes(int N, int stages, int a_lo, int b_lo, int fp8) {
+  return 1024 + static_cast<size_t>(stages) * tc_stage_bytes(N, a_lo, b_lo, fp8) + 8 * (3 * stages + 2) + 16;
 }
 
-template <int BK, int CL, bool SPLIT>
+template <int BK, int CL, int MODE>
 cudaError_t launch_tc_cl(const CUtensorMap& tmA, const CUtensorMap& tmB, const CUtensorMap& tmA2,
                          const CUtensorMap& tmB2, const TcArgs& a, int num_sms, size_t smem, cudaStream_t st) {
   auto kern = k_tc_gemm<BK, CL>;
   auto kern_s = k_tc_gemm_split<BK, CL>;
-  const void* kfn = SPLIT ? reinterpret_cast<const void*>(kern_s) : reinterpret_cast<const void*>(kern);
+  auto kern_f = k_tc_gemm_f8<BK, CL>;
+  const void* kfn = MODE == 1   ? reinterpret_cast<const void*>(kern_s)
+                    : MODE == 2 ? reinterpret_cast<const void*>(kern_f)
+                                : reinterpret_cast<const void*>(kern);
   cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   const long long cunits = static_cast<long long>(a.Nb) * ((a.m_tiles + CL - 1) / CL) * a.n_kchunks;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
-  cfg.blockDim = dim3(kTcThreads);
+  cfg.blockDim = dim3(MODE == 2 ? kTcThreadsF8 : kTcThreads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   long long nclusters = num_sms / CL;
@@ -761,8 +854,10 @@ cudaError_t launch_tc_cl(const CUtensorMap& tmA, const CUtensorMap& tmB, const C
   }
   if (nclusters > cunits) nclusters = cunits;
   cfg.gridDim = dim3(static_cast<unsigned>(nclusters * CL));
-  if (SPLIT)
+  if (MODE == 1)
     e = cudaLaunchKernelEx(&cfg, kern_s, tmA, tmB, tmA2, tmB2, a);
+  else if (MODE == 2)
+    e = cudaLaunchKernelEx(&cfg, kern_f, tmA, tmB, a);
   else
     e = cudaLaunchKernelEx(&cfg, kern, tmA, tmB, a);
   if (e != cudaSuccess) return e;
@@ -775,28 +870,37 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
   if (units <= 0) return cudaSuccess;
   if (a.N < 16 || a.N > 512 || a.N % 16 != 0 || (a.N > 256 && a.N % 256 != 0) || a.stages < 2)
     return cudaErrorInvalidValue;
-  // split operands come in pairs: both A and B carry lo parts, or neither
+  // split operands come in pairs: both A and B carry lo parts, or neither;
+  // FP8 A (a_fp8) takes a byte tensor map and excludes the split
   if (a.a_lo != a.b_lo || (a.a_lo != 0 && a.a_lo != 1) || (a.a_lo && (!tmA2 || !tmB2))) return cudaErrorInvalidValue;
+  if ((a.a_fp8 != 0 && a.a_fp8 != 1) || (a.a_fp8 && a.a_lo) || (a.a_fp8 && a.row_scale == nullptr))
+    return cudaErrorInvalidValue;
   const int CL = a.cluster < 1 ? 1 : a.cluster;
   if (CL != 1 && CL != 2 && CL != 4) return cudaErrorInvalidValue;
   if (CL > 1 && (a.N / CL < 8 || (a.N / CL) % 8 != 0 || a.N / CL > 256)) return cudaErrorInvalidValue;
-  const size_t smem = tc_smem_bytes(a.N, a.stages, a.a_lo, a.b_lo);
+  const size_t smem = tc_smem_bytes(a.N, a.stages, a.a_lo, a.b_lo, a.a_fp8);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   const CUtensorMap& a2 = a.a_lo ? *tmA2 : tmA;  // unused unless a_lo / b_lo
   const CUtensorMap& b2 = a.b_lo ? *tmB2 : tmB;
-  auto go = [&](auto bk_tag, auto split_tag) -> cudaError_t {
+  auto go = [&](auto bk_tag, auto mode_tag) -> cudaError_t {
     constexpr int BK = decltype(bk_tag)::value;
-    constexpr bool SP = decltype(split_tag)::value;
-    if (CL == 1) return launch_tc_cl<BK, 1, SP>(tmA, tmB, a2, b2, a, num_sms, smem, st);
-    if (CL == 2) return launch_tc_cl<BK, 2, SP>(tmA, tmB, a2, b2, a, num_sms, smem, st);
-    return launch_tc_cl<BK, 4, SP>(tmA, tmB, a2, b2, a, num_sms, smem, st);
+    constexpr int MD = decltype(mode_tag)::value;
+    if (CL == 1) return launch_tc_cl<BK, 1, MD>(tmA, tmB, a2, b2, a, num_sms, smem, st);
+    if (CL == 2) return launch_tc_cl<BK, 2, MD>(tmA, tmB, a2, b2, a, num_sms, smem, st);
+    return launch_tc_cl<BK, 4, MD>(tmA, tmB, a2, b2, a, num_sms, smem, st);
   };
   using bk64 = std::integral_constant<int, 64>;
   using bk32 = std::integral_constant<int, 32>;
-  const bool sp = a.a_lo != 0;
-  if (tc_block_k(a.N, sp ? 1 : 0) == 64)
-    return sp ? go(bk64{}, std::true_type{}) : go(bk64{}, std::false_type{});
-  return sp ? go(bk32{}, std::true_type{}) : go(bk32{}, std::false_type{});
+  using m0 = std::integral_constant<int, 0>;
+  using m1 = std::integral_constant<int, 1>;
+  using m2 = std::integral_constant<int, 2>;
+  const int mode = a.a_lo ? 1 : (a.a_fp8 ? 2 : 0);
+  if (tc_block_k(a.N, mode == 1 ? 1 : 0) == 64) {
+    if (mode == 1) return go(bk64{}, m1{});
+    return mode == 2 ? go(bk64{}, m2{}) : go(bk64{}, m0{});
+  }
+  if (mode == 1) return go(bk32{}, m1{});
+  return mode == 2 ? go(bk32{}, m2{}) : go(bk32{}, m0{});
 }
 
 cudaError_t launch_tc_retransform(const CUtensorMap& tmT, const TcRtArgs& a, int num_sms, cudaStream_t st) {

@@ -421,7 +421,11 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
       const int m1 = static_cast<int>((Ng + 127) / 128);
       const int cl = fit_cluster(ctx->tc_cl1, N1, m1);
       const int brows = cl > 1 ? N1 / cl : (N1 > 256 ? 256 : N1);
-      CK(tc_encode_3d(&ta, ctx->G, K1, Ng, Nb, K1, 128, bk));
+      const bool f8 = ctx->opts.prec_g == S2W_PREC_FP8_E4M3;
+      if (f8)  // one byte per K element: row pitch 2 Ns_pad bytes
+        CK(tc_encode_3d_u8(&ta, ctx->G, K1, Ng, Nb, 128, bk));
+      else
+        CK(tc_encode_3d(&ta, ctx->G, K1, Ng, Nb, K1, 128, bk));
       CK(tc_encode_3d(&tb, ctx->tc_bp1, K1, ctx->tc_n1max, Nb, K1, brows, bk));
       if (sp) {
         CK(tc_encode_3d(&ta2, ctx->G_lo, K1, Ng, Nb, K1, 128, bk));
@@ -435,9 +439,14 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
       a.m_tiles = static_cast<int>((Ng + 127) / 128);
       a.n_kchunks = 1;
       a.kblocks_per_chunk = (K1 + bk - 1) / bk;
-      a.stages = tc_stages_for(N1, sp, sp);
+      a.stages = tc_stages_for(N1, sp, sp, f8 ? 1 : 0);
       a.a_lo = sp;
       a.b_lo = sp;
+      a.a_fp8 = f8 ? 1 : 0;
+      if (f8) {  // FP8 rows carry one scale per (bin, 256 grid rows)
+        a.row_scale = ctx->G_scale;
+        a.nblk = ctx->nblk;
+      }
       a.tmem_cols = N1 <= 32 ? 32 : (N1 <= 64 ? 64 : (N1 <= 128 ? 128 : (N1 <= 256 ? 256 : 512)));
       a.cluster = cl;
       a.epi = 0;
@@ -567,8 +576,8 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
   if (o.engine < S2W_ENGINE_AUTO || o.engine > S2W_ENGINE_TENSOR) return fail(nullptr, S2W_ERR_ARG, "engine=%d", o.engine);
   if (o.tc_cluster != 0 && o.tc_cluster != 1 && o.tc_cluster != 2 && o.tc_cluster != 4)
     return fail(nullptr, S2W_ERR_ARG, "tc_cluster=%d: 0, 1, 2 or 4", o.tc_cluster);
-  if (o.engine == S2W_ENGINE_TENSOR && o.prec_g != S2W_PREC_BF16 && o.prec_g != S2W_PREC_BF16_HILO)
-    return fail(nullptr, S2W_ERR_UNSUPPORTED, "the tensor engine needs prec_g = BF16 or BF16_HILO");
+  if (o.engine == S2W_ENGINE_TENSOR && o.prec_g == S2W_PREC_FP32)
+    return fail(nullptr, S2W_ERR_UNSUPPORTED, "the tensor engine needs prec_g = BF16, BF16_HILO or FP8_E4M3");
   if (o.tc_adjoint != 0 && o.tc_adjoint != 1) return fail(nullptr, S2W_ERR_ARG, "tc_adjoint=%d: 0 or 1", o.tc_adjoint);
   if (o.engine == S2W_ENGINE_TENSOR && 2 * No > 256)
     return fail(nullptr, S2W_ERR_UNSUPPORTED, "the tensor engine needs No <= 128");
@@ -640,7 +649,7 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
   if ((e = dalloc(&ctx->ws_lens, sizeof(int) * B)) != cudaSuccess) return bad(e, "active lengths");
   if ((e = dalloc(&ctx->ws_gpart, sizeof(float2) * Nb * ctx->adj_nchunk * ctx->Ns_pad)) != cudaSuccess)
     return bad(e, "adjoint partials");
-  ctx->tc_on = (o.prec_g == S2W_PREC_BF16 || o.prec_g == S2W_PREC_BF16_HILO) && 2 * No <= 256 &&
+  ctx->tc_on = o.prec_g != S2W_PREC_FP32 && 2 * No <= 256 &&
                (o.engine == S2W_ENGINE_TENSOR || (o.engine == S2W_ENGINE_AUTO && o.max_batch >= 2));
   ctx->tc_split = ctx->tc_on && o.prec_g == S2W_PREC_BF16_HILO;
   if (ctx->tc_on) {

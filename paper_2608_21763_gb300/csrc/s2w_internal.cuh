@@ -218,6 +218,7 @@ struct TcArgs {
   int nblk;
   int a_lo;                // 1: A has a low-order BF16 part (second tensor map): adds A_lo B
   int b_lo;                // 1: B has a low-order BF16 part: adds A B_lo
+  int a_fp8;               // 1: A is FP8 e4m3 (byte tensor map, row-major), widened in shared memory; needs row_scale
   int* status;
 };
 // bk = 64: 128-byte swizzle, K boxes of 64 BF16; bk = 32: 64-byte swizzle.
@@ -226,7 +227,10 @@ cudaError_t tc_encode_3d(CUtensorMap* out, const void* base, long long K, long l
 // K block (BF16 elements per swizzle row) and ring depth for N MMA columns
 // with `terms` = 1 + a_lo + b_lo operand tiles beyond the first A and B
 int tc_block_k(int N, int split = 0);
-int tc_stages_for(int N, int a_lo = 0, int b_lo = 0);
+int tc_stages_for(int N, int a_lo = 0, int b_lo = 0, int fp8 = 0);
+// Byte tensor map for FP8 A tiles: [nbatch][rows][K] bytes, box bk x box_rows, no swizzle.
+cudaError_t tc_encode_3d_u8(CUtensorMap* out, const void* base, long long K, long long rows, long long nbatch,
+                            int box_rows, int bk);
 // tmA2 / tmB2: tensor maps of the low-order parts when a.a_lo / a.b_lo
 cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const TcArgs& a, int num_sms,
                            cudaStream_t st, const CUtensorMap* tmA2 = nullptr, const CUtensorMap* tmB2 = nullptr);

@@ -193,3 +193,38 @@ def test_split_precision_clusters_bitwise():
     q2, _, _, _, _ = run_case(geom, 64, 40, seed=34, prec="bf16_hilo", tc_cluster=2)
     assert_parity(q2, q_ref, *wn, tol=TOL_SPLIT, label="tensor split cluster 2")
     assert np.array_equal(q1, q2)
+
+
+@pytest.mark.parametrize("B", [3, 7, 300])
+def test_fp8_operator_on_tensor_engine(B):
+    """FP8 e4m3 stage-1 spectra on the tensor engine: tiles widened to BF16
+    in shared memory (128-byte swizzle at N <= 256, 64-byte at N = 512),
+    per-(bin, 256-row) scales in the epilogue.  Against the oracle at the
+    FP8 bar, and against the FP8 stream engine (same quantised operator; they
+    differ by the BF16 rounding of the activations)."""
+    geom = compact_box(24, 700, 6, seed=61)
+    Nt = 64
+    rng = np.random.default_rng(62)
+    slip = rng.standard_normal((B, geom.Ns, Nt))
+    slip[:, :, Nt // 2:] = 0
+    st = torch.tensor(slip, dtype=torch.float32, device="cuda")
+    G = geom.greens_rows(0, geom.Ng, Nt)
+    P = geom.adjoint_cols(0, geom.Ng, Nt)
+    q_ref = oracle.waveforms(G, P, slip)
+    wn, kappa = window_norms(G, P, slip)
+    out = {}
+    for engine in ("tensor", "stream"):
+        ctx = make_context(s2w, geom, Nt, prec_g="fp8", max_batch=B, chunk=256, engine=engine)
+        out[engine] = ctx.waveforms(st).cpu().numpy()
+        ctx.sync()
+        assert_parity(out[engine], q_ref, wn, kappa, tol=1e-1, label=f"fp8 {engine} B={B}")
+    d = np.linalg.norm((out["tensor"] - out["stream"]).reshape(B, -1), axis=1)
+    assert np.all(d <= TOL_TC * wn), d / wn
+
+
+def test_fp8_tensor_clusters_bitwise():
+    geom = compact_box(24, 700, 6, seed=63)
+    q1, q_ref, wn, _, _ = run_case(geom, 64, 40, seed=64, prec="fp8", tc_cluster=1, chunk=256)
+    q2, _, _, _, _ = run_case(geom, 64, 40, seed=64, prec="fp8", tc_cluster=2, chunk=256)
+    assert_parity(q2, q_ref, *wn, tol=1e-1, label="fp8 tensor cluster 2")
+    assert np.array_equal(q1, q2)
