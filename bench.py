@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=None, help="ruptures per step (default: the workload's)")
     ap.add_argument("--grid", type=int, default=None,
                     help="override the number of grid points (small cases for profiling)")
+    ap.add_argument("--single-pass", action="store_true",
+                    help="the single-pass ablation: L = 4 Nt, D_t folded into Phat, no retransform (stream engine)")
     ap.add_argument("--no-graph", action="store_true",
                     help="time direct calls instead of replayed CUDA graphs of the pipeline")
     ap.add_argument("--no-autotune", action="store_true",
@@ -132,9 +134,10 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ setup
 def load_context(s2w, wl, geom, prec_g, prec_p, B, device, engine="auto", chunk=1024, tc_cluster=0,
-                 tc_adjoint=False):
+                 tc_adjoint=False, single_pass=False):
     ctx = s2w.Context(wl.Ns, wl.Ng, wl.No, wl.Nt, prec_g=prec_g, prec_p=prec_p,
-                      max_batch=B, device=device, engine=engine, tc_cluster=tc_cluster, tc_adjoint=tc_adjoint)
+                      max_batch=B, device=device, engine=engine, tc_cluster=tc_cluster, tc_adjoint=tc_adjoint,
+                      single_pass=single_pass)
     for g0 in range(0, wl.Ng, chunk):
         g1 = min(wl.Ng, g0 + chunk)
         ctx.load_greens(g0, geom.greens_rows(g0, g1, wl.Nt, np.float32))
@@ -142,10 +145,11 @@ def load_context(s2w, wl, geom, prec_g, prec_p, B, device, engine="auto", chunk=
     return ctx
 
 
-def stage1_algorithmic_bytes(wl, prec_g, B):
+def stage1_algorithmic_bytes(wl, prec_g, B, single_pass=False):
     """Bytes one stage-1 contraction launch must move: the unpadded operator
-    spectrum once, the slip spectra, and the seafloor spectra it writes."""
-    Nb = wl.Nt + 1
+    spectrum once, the slip spectra, and the seafloor spectra it writes
+    (Nt + 1 bins; 2 Nt + 1 in the single-pass variant)."""
+    Nb = 2 * wl.Nt + 1 if single_pass else wl.Nt + 1
     op = Nb * wl.Ng * wl.Ns * COMPLEX_BYTES[prec_g]
     if prec_g == "fp8":
         op += Nb * ((wl.Ng + 255) // 256) * 4
@@ -268,7 +272,7 @@ def run_ours(args, rank, world, local_rank):
     # so the adjoint runs on the tensor engine as well
     tc_adj = args.mode == "gradient" and args.prec_g in ("bf16", "bf16_hilo") and args.engine != "stream"
     ctx = load_context(s2w, wl, geom, args.prec_g, args.prec_p, B, local_rank, args.engine,
-                       tc_cluster=args.tc_cluster, tc_adjoint=tc_adj)
+                       tc_cluster=args.tc_cluster, tc_adjoint=tc_adj, single_pass=args.single_pass)
     setup_s = time.perf_counter() - t_setup
     slip_d = torch.tensor(slip_np, device=dev)
     q_d = torch.empty((pool, B, wl.No, wl.Nt), dtype=torch.float32, device=dev)
@@ -409,12 +413,13 @@ def run_ours(args, rank, world, local_rank):
                 "traffic": None, "algorithmic_flops_per_launch": flops, "mma_terms": terms,
                 "launch_ms": round(per_launch_s * 1e3, 4)}
     else:
-        alg = stage1_algorithmic_bytes(wl, args.prec_g, 1)
+        alg = stage1_algorithmic_bytes(wl, args.prec_g, 1, args.single_pass)
         achieved = alg / per_launch_s / 1e9
         roof = {"kernel": "k_stream_dot (stage-1 per-bin contraction)", "bound": "hbm",
                 "achieved": round(achieved, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": round(achieved / pk["hbm_gbs"], 4), "peak_source": pk_kind,
-                "traffic": measured_traffic(wl, args.prec_g), "algorithmic_bytes_per_launch": alg,
+                "traffic": None if args.single_pass else measured_traffic(wl, args.prec_g),
+                "algorithmic_bytes_per_launch": alg,
                 "launch_ms": round(per_launch_s * 1e3, 4)}
     stages = {k: v for k, v in stages.items() if k != "graph"}
     total_stage_ms = sum(v[0] for v in stages.values())
@@ -432,7 +437,7 @@ def run_ours(args, rank, world, local_rank):
                       "ruptures_per_step": B, "prec_g": args.prec_g, "prec_p": args.prec_p,
                       "engine": "tensor" if tensor else "stream", "mode": args.mode,
                       "tc_cluster": tuning["tc_cluster"] if tuning else args.tc_cluster,
-                      "autotune": tuning, "cuda_graph": use_graph,
+                      "autotune": tuning, "cuda_graph": use_graph, "single_pass": bool(args.single_pass),
                       "l2": "inputs larger than L2 (every step streams the full operator spectra)",
                       "parallelism": f"replicas{world}",
                       "operator_gb": round(sum(ctx.operator_bytes()) / 1e9, 2),

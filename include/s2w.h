@@ -107,6 +107,18 @@ typedef struct {
                      batches (same rules as s2w_waveforms); doubles the
                      stage-1 operator memory.  0 (default): the adjoint
                      streams the spectra once per rupture. */
+  int single_pass; /* 1: the single-pass variant (an ablation of the
+                      truncate-and-retransform step): both operators are kept
+                      at FFT length L = 4 Nt (2 Nt + 1 bins, twice the bytes),
+                      D_t is folded into the stage-2 spectra as the factor
+                      (1 - exp(-2 pi i l / L)) / dt, and the seafloor spectra
+                      go straight into stage 2 with no IFFT / Truncate / FFT
+                      between the stages.  L >= 3 Nt - 1 keeps the circular
+                      convolution of the three factors free of wrap onto the
+                      kept samples.  Stream engine only; Nt <= 256; no
+                      seafloor output, adjoint or no-alloc path.  The
+                      spectral loaders then take 2 Nt + 1 bins of length-4 Nt
+                      DFTs.  0 (default): L = 2 Nt with the retransform. */
 } s2w_opts;
 
 /* Fill *o with the defaults listed above (max_batch = 1). */

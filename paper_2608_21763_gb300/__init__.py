@@ -61,7 +61,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("prec_g", ctypes.c_int), ("prec_p", ctypes.c_int),
                 ("dt_mode", ctypes.c_int), ("dt", ctypes.c_double),
                 ("max_batch", ctypes.c_int), ("device", ctypes.c_int),
-                ("engine", ctypes.c_int), ("tc_cluster", ctypes.c_int), ("tc_adjoint", ctypes.c_int)]
+                ("engine", ctypes.c_int), ("tc_cluster", ctypes.c_int), ("tc_adjoint", ctypes.c_int),
+                ("single_pass", ctypes.c_int)]
 
 
 def lib_path() -> str:
@@ -159,7 +160,7 @@ class Context:
 
     def __init__(self, Ns, Ng, No, Nt, prec_g="fp32", prec_p="fp32",
                  dt_mode="backward", dt=1.0, max_batch=1, device=0, engine="auto", tc_cluster=0,
-                 tc_adjoint=False):
+                 tc_adjoint=False, single_pass=False):
         L = lib()
         o = Opts()
         L.s2w_default_opts(ctypes.byref(o))
@@ -169,13 +170,14 @@ class Context:
         o.engine = ENGINE[engine]
         o.tc_cluster = int(tc_cluster)
         o.tc_adjoint = int(bool(tc_adjoint))
+        o.single_pass = int(bool(single_pass))
         h = ctypes.c_void_p()
         st = L.s2w_create(Ns, Ng, No, Nt, ctypes.byref(o), ctypes.byref(h))
         if st != 0:
             raise S2WError(st, L.s2w_last_error(None).decode())
         self._h = h
         self.Ns, self.Ng, self.No, self.Nt = Ns, Ng, No, Nt
-        self.Nb = Nt + 1
+        self.Nb = 2 * Nt + 1 if single_pass else Nt + 1
         self.prec_g, self.prec_p, self.max_batch, self.device = prec_g, prec_p, max_batch, device
         self.engine = engine
 

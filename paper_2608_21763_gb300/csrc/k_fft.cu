@@ -181,7 +181,8 @@ __global__ void __launch_bounds__(kThreads) k_retransform(const float2* __restri
 template <int P>
 __global__ void __launch_bounds__(kThreads) k_reduce_irfft(const float2* __restrict__ part, int No, int nseg,
                                                            long long s_b, long long s_l, long long s_s,
-                                                           const float2* __restrict__ twg, float* __restrict__ q) {
+                                                           const float2* __restrict__ twg, float* __restrict__ q,
+                                                           int n_keep) {
   constexpr int N = 32 * P;
   constexpr int L = 2 * N;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -200,9 +201,28 @@ __global__ void __launch_bounds__(kThreads) k_reduce_irfft(const float2* __restr
   }
   __syncthreads();
   if (threadIdx.x >= 32) return;
-  float* out = q + static_cast<long long>(blockIdx.x) * N;
+  float* out = q + static_cast<long long>(blockIdx.x) * n_keep;
   const FftLane<P> fl = fft_lane<P>(tw, threadIdx.x);
-  warp_irfft_head<P>([&](int k) { return xs[k]; }, [&](int n, float v) { out[n] = v; }, tw, fl, threadIdx.x, scr);
+  warp_irfft_head<P>([&](int k) { return xs[k]; },
+                     [&](int n, float v) {
+                       if (n < n_keep) out[n] = v;
+                     },
+                     tw, fl, threadIdx.x, scr);
+}
+
+// X[l][r] *= (1 - W_L^l) / dt for l <= L/2, r < per_bin: the spectrum of the
+// backward difference, folded into the stage-2 spectra of the single-pass
+// variant (no retransform between the stages; L = 4 Nt leaves no wrap).
+__global__ void k_scale_dt(float2* __restrict__ X, int Nb, long long per_bin, const float2* __restrict__ twg,
+                           float inv_dt) {
+  const long long total = static_cast<long long>(Nb) * per_bin;
+  for (long long e = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int l = static_cast<int>(e / per_bin);
+    const float2 w = twg[l];
+    const float2 d = make_float2((1.f - w.x) * inv_dt, -w.y * inv_dt);
+    X[e] = cmul(X[e], d);
+  }
 }
 
 // FP32 spectra -> resident storage (FP32 / BF16 / BF16 hi+lo), block copy:
@@ -399,13 +419,19 @@ cudaError_t launch_retransform(const float2* mhat, long long Ng, long long ld_m,
 }
 
 cudaError_t launch_reduce_irfft(const float2* part, int B, int No, int nseg, int Nt, long long s_b, long long s_l,
-                                long long s_s, const float2* tw, float* q, cudaStream_t st) {
+                                long long s_s, const float2* tw, float* q, cudaStream_t st, int n_keep) {
+  if (n_keep <= 0 || n_keep > Nt) n_keep = Nt;
   const long long n = static_cast<long long>(B) * No;
   if (n <= 0) return cudaSuccess;
   S2W_DISPATCH_P(Nt, {
     const size_t sm = sizeof(float2) * (64 * P + 32 * P + 1 + 32 * P);
-    k_reduce_irfft<P><<<static_cast<unsigned>(n), kThreads, sm, st>>>(part, No, nseg, s_b, s_l, s_s, tw, q);
+    k_reduce_irfft<P><<<static_cast<unsigned>(n), kThreads, sm, st>>>(part, No, nseg, s_b, s_l, s_s, tw, q, n_keep);
   });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_dt(float2* X, int Nb, long long per_bin, const float2* tw, float inv_dt, cudaStream_t st) {
+  k_scale_dt<<<grid_for(Nb * per_bin, 256), 256, 0, st>>>(X, Nb, per_bin, tw, inv_dt);
   return cudaGetLastError();
 }
 

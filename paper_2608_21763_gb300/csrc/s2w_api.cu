@@ -88,6 +88,7 @@ struct s2w_ctx {
   void* tc_ub = nullptr;      // [Nb][tc_n1max][2 Ng_pad2] bf16: D_t^T-retransformed spectra, conjugate embedding
   void* tc_ub_lo = nullptr;
   float2* tc_ghat = nullptr;  // [Nb][tc_bsub][Ns] complex FP32
+  bool single_pass = false;     // L = 4 Nt, D_t folded into Phat, no retransform
   int* ws_lens = nullptr;       // active samples per rupture (s2w_waveforms_active), [max_batch]
   const int* cur_lens = nullptr;  // set for the duration of an s2w_waveforms_active call
   bool tc_split = false;    // BF16 hi/lo operands and activations (three MMAs per K step)
@@ -538,6 +539,7 @@ void s2w_default_opts(s2w_opts* o) {
   o->engine = S2W_ENGINE_AUTO;
   o->tc_cluster = 0;
   o->tc_adjoint = 0;
+  o->single_pass = 0;
 }
 
 const char* s2w_status_string(int s) {
@@ -579,6 +581,10 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
   if (o.engine == S2W_ENGINE_TENSOR && o.prec_g == S2W_PREC_FP32)
     return fail(nullptr, S2W_ERR_UNSUPPORTED, "the tensor engine needs prec_g = BF16, BF16_HILO or FP8_E4M3");
   if (o.tc_adjoint != 0 && o.tc_adjoint != 1) return fail(nullptr, S2W_ERR_ARG, "tc_adjoint=%d: 0 or 1", o.tc_adjoint);
+  if (o.single_pass != 0 && o.single_pass != 1)
+    return fail(nullptr, S2W_ERR_ARG, "single_pass=%d: 0 or 1", o.single_pass);
+  if (o.single_pass && (Nt > 256 || o.engine == S2W_ENGINE_TENSOR || o.tc_adjoint))
+    return fail(nullptr, S2W_ERR_UNSUPPORTED, "single_pass: stream engine only, Nt <= 256, no tc_adjoint");
   if (o.engine == S2W_ENGINE_TENSOR && 2 * No > 256)
     return fail(nullptr, S2W_ERR_UNSUPPORTED, "the tensor engine needs No <= 128");
   int ndev = 0;
@@ -592,8 +598,10 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
   ctx->Ng = Ng;
   ctx->No = No;
   ctx->Nt = Nt;
-  ctx->Nb = Nt + 1;
-  ctx->L = 2 * Nt;
+  // single pass: L = 4 Nt >= 3 Nt - 1 (no wrap without the retransform)
+  ctx->single_pass = o.single_pass != 0;
+  ctx->Nb = ctx->single_pass ? 2 * Nt + 1 : Nt + 1;
+  ctx->L = ctx->single_pass ? 4 * Nt : 2 * Nt;
   ctx->Ns_pad = static_cast<int>(round_up(Ns, 8));
   ctx->nseg = static_cast<int>((Ng + 1023) / 1024);
   ctx->RL = static_cast<int>(round_up((Ng + ctx->nseg - 1) / ctx->nseg, 8));
@@ -649,7 +657,7 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
   if ((e = dalloc(&ctx->ws_lens, sizeof(int) * B)) != cudaSuccess) return bad(e, "active lengths");
   if ((e = dalloc(&ctx->ws_gpart, sizeof(float2) * Nb * ctx->adj_nchunk * ctx->Ns_pad)) != cudaSuccess)
     return bad(e, "adjoint partials");
-  ctx->tc_on = o.prec_g != S2W_PREC_FP32 && 2 * No <= 256 &&
+  ctx->tc_on = !ctx->single_pass && o.prec_g != S2W_PREC_FP32 && 2 * No <= 256 &&
                (o.engine == S2W_ENGINE_TENSOR || (o.engine == S2W_ENGINE_AUTO && o.max_batch >= 2));
   ctx->tc_split = ctx->tc_on && o.prec_g == S2W_PREC_BF16_HILO;
   if (ctx->tc_on) {
@@ -789,7 +797,7 @@ int load_greens_impl(s2w_ctx* ctx, int g0, int ng, const float* G, bool spectra,
       } else {
         CK(cudaMemcpyAsync(stage_t, G + r * Ns * Nt, sizeof(float) * rc * Ns * Nt, cudaMemcpyDefault, st));
         ctx->launches += fp8 ? 2 : 1;
-        CK(launch_rfft_rows(stage_t, rc * Ns, static_cast<int>(Nt), static_cast<int>(Nt), ctx->tw, stage_s,
+        CK(launch_rfft_rows(stage_t, rc * Ns, static_cast<int>(Nt), static_cast<int>(ctx->L / 2), ctx->tw, stage_s,
                             rc * Ns_pad, Ns, Ns_pad, st));
       }
       ctx->launches += 1;
@@ -856,8 +864,13 @@ int load_adjoint_impl(s2w_ctx* ctx, int g0, int ng, const float* P, bool spectra
         CK(cudaMemcpy2DAsync(stage_t, sizeof(float) * rc * Nt, P + c * Nt, sizeof(float) * ng * Nt,
                              sizeof(float) * rc * Nt, No, cudaMemcpyDefault, st));
         ctx->launches += 2;
-        CK(launch_rfft_rows(stage_t, No * rc, static_cast<int>(Nt), static_cast<int>(Nt), ctx->tw, stage_s,
+        CK(launch_rfft_rows(stage_t, No * rc, static_cast<int>(Nt), static_cast<int>(ctx->L / 2), ctx->tw, stage_s,
                             No * rc, rc, rc, st));
+      }
+      if (ctx->single_pass && ctx->opts.dt_mode != S2W_DT_NONE) {  // fold D_t into the stage-2 spectra
+        ctx->launches += 1;
+        CK(launch_scale_dt(stage_s, static_cast<int>(Nb), No * rc, ctx->tw, static_cast<float>(1.0 / ctx->opts.dt),
+                           st));
       }
       CK(launch_store_adjoint(stage_s, static_cast<int>(Nb), static_cast<int>(No), rc, g0 + c, ctx->RL, ctx->nseg,
                               ctx->opts.prec_p, ctx->P, st));
@@ -929,6 +942,8 @@ int s2w_waveforms(s2w_ctx* ctx, const float* slip, int B, float* q, float* seafl
     CK(cudaMemcpyAsync(ctx->ws_slip, slip, sizeof(float) * B * Ns * Nt, cudaMemcpyHostToDevice, st));
     slip_d = ctx->ws_slip;
   }
+  if (ctx->single_pass && seafloor != nullptr)
+    return fail(ctx, S2W_ERR_UNSUPPORTED, "waveforms: no seafloor output in the single-pass variant");
   float* q_d = kq == 1 ? q : ctx->ws_q;
   const bool use_tc = ctx->tc_on && seafloor == nullptr && (ctx->tc_split || ctx->tc_T != nullptr) &&
                       (ctx->opts.engine == S2W_ENGINE_TENSOR || B >= ctx->tc_min_batch);
@@ -948,7 +963,7 @@ int s2w_waveforms(s2w_ctx* ctx, const float* slip, int B, float* q, float* seafl
     {
       StageTimer t(ctx, 0, st);
       CK(launch_rfft_rows(slip_d + static_cast<long long>(g0) * Ns * Nt, Bg * Ns, static_cast<int>(Nt),
-                          static_cast<int>(Nt), ctx->tw, ctx->ws_shat, Bg * Ns_pad, Ns, Ns_pad, st,
+                          static_cast<int>(ctx->L / 2), ctx->tw, ctx->ws_shat, Bg * Ns_pad, Ns, Ns_pad, st,
                           ctx->cur_lens ? ctx->cur_lens + g0 : nullptr));
     }
     const long long part_b = Nb * ctx->nseg * No;
@@ -975,7 +990,11 @@ int s2w_waveforms(s2w_ctx* ctx, const float* slip, int B, float* q, float* seafl
       // K3
       float* sf = nullptr;
       if (seafloor) sf = kf == 1 ? seafloor + bg * Ng * Nt : ctx->ws_seafloor;
-      {
+      if (ctx->single_pass) {  // mhat goes to stage 2 as it is, in the segment layout
+        StageTimer t(ctx, 2, st, 0);
+        CK(cudaMemcpy2DAsync(ctx->ws_vhat, sizeof(float2) * ctx->nseg * ctx->RL, ctx->ws_mhat, sizeof(float2) * Ng,
+                             sizeof(float2) * Ng, Nb, cudaMemcpyDeviceToDevice, st));
+      } else {
         StageTimer t(ctx, 2, st);
         CK(launch_retransform(ctx->ws_mhat, Ng, Ng, static_cast<int>(Nt), ctx->tw,
                               static_cast<float>(1.0 / ctx->opts.dt), ctx->opts.dt_mode, ctx->ws_vhat,
@@ -1003,9 +1022,9 @@ int s2w_waveforms(s2w_ctx* ctx, const float* slip, int B, float* q, float* seafl
     // K5
     {
       StageTimer t(ctx, 4, st);
-      CK(launch_reduce_irfft(ctx->ws_part, Bg, static_cast<int>(No), ctx->nseg, static_cast<int>(Nt), part_b,
+      CK(launch_reduce_irfft(ctx->ws_part, Bg, static_cast<int>(No), ctx->nseg, static_cast<int>(ctx->L / 2), part_b,
                              static_cast<long long>(ctx->nseg) * No, No, ctx->tw,
-                             q_d + static_cast<long long>(g0) * No * Nt, st));
+                             q_d + static_cast<long long>(g0) * No * Nt, st, static_cast<int>(Nt)));
     }
   }
   if (kq == 0) {
@@ -1039,6 +1058,8 @@ int s2w_waveforms_active(s2w_ctx* ctx, const float* slip, const int* active_len,
 }
 
 int s2w_adjoint(s2w_ctx* ctx, const float* r, int B, float* grad_s, void* stream) {
+  if (ctx && ctx->single_pass)
+    return fail(ctx, S2W_ERR_UNSUPPORTED, "adjoint: not available in the single-pass variant");
   if (!ctx) return S2W_ERR_ARG;
   if (B < 0 || B > ctx->opts.max_batch)
     return fail(ctx, S2W_ERR_ARG, "adjoint: B=%d outside [0, max_batch=%d]", B, ctx->opts.max_batch);
@@ -1136,6 +1157,8 @@ int s2w_adjoint(s2w_ctx* ctx, const float* r, int B, float* grad_s, void* stream
 
 int s2w_misfit_gradient(s2w_ctx* ctx, const float* slip, const float* d, int B, float* grad_s, float* loss,
                         void* stream) {
+  if (ctx && ctx->single_pass)
+    return fail(ctx, S2W_ERR_UNSUPPORTED, "misfit_gradient: not available in the single-pass variant");
   if (!ctx) return S2W_ERR_ARG;
   if (B < 0 || B > ctx->opts.max_batch)
     return fail(ctx, S2W_ERR_ARG, "misfit_gradient: B=%d outside [0, max_batch=%d]", B, ctx->opts.max_batch);
@@ -1169,6 +1192,8 @@ int s2w_misfit_gradient(s2w_ctx* ctx, const float* slip, const float* d, int B, 
 }
 
 int s2w_rfft(s2w_ctx* ctx, const float* x, long long rows, float* X, void* stream) {
+  if (ctx && ctx->single_pass)
+    return fail(ctx, S2W_ERR_UNSUPPORTED, "rfft: not available in the single-pass variant");
   if (!ctx) return S2W_ERR_ARG;
   if (rows < 0 || (rows > 0 && (!x || !X))) return fail(ctx, S2W_ERR_ARG, "rfft: bad arguments");
   if (rows == 0) return S2W_OK;
@@ -1182,6 +1207,8 @@ int s2w_rfft(s2w_ctx* ctx, const float* x, long long rows, float* X, void* strea
 }
 
 int s2w_irfft(s2w_ctx* ctx, const float* X, long long rows, float* x, void* stream) {
+  if (ctx && ctx->single_pass)
+    return fail(ctx, S2W_ERR_UNSUPPORTED, "irfft: not available in the single-pass variant");
   if (!ctx) return S2W_ERR_ARG;
   if (rows < 0 || (rows > 0 && (!x || !X))) return fail(ctx, S2W_ERR_ARG, "irfft: bad arguments");
   if (rows == 0) return S2W_OK;
@@ -1433,6 +1460,8 @@ int noalloc_scratch(s2w_ctx* ctx, void** out) {
 }  // namespace
 
 extern "C" int s2w_waveforms_noalloc(s2w_ctx* ctx, const float* slip, float* q, void* stream) {
+  if (ctx && ctx->single_pass)
+    return fail(ctx, S2W_ERR_UNSUPPORTED, "waveforms_noalloc: not available in the single-pass variant");
   if (!ctx) return S2W_ERR_ARG;
   if (!slip || !q) return fail(ctx, S2W_ERR_ARG, "waveforms_noalloc: slip and q must not be NULL");
   const long long Ns = ctx->Ns, Ng = ctx->Ng, No = ctx->No, Nt = ctx->Nt, Nb = ctx->Nb, Ns_pad = ctx->Ns_pad;

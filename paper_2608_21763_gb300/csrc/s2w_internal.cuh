@@ -145,9 +145,12 @@ cudaError_t launch_retransform(const float2* mhat, long long Ng, long long ld_m,
                                cudaStream_t st, int nb = 1, long long mhat_ld_b = 0, long long vhat_ld_b = 0,
                                __nv_bfloat162* vhat_bf = nullptr, __nv_bfloat162* vhat_bf_lo = nullptr,
                                int n_alloc = 0);
-// q[b][o][n] from partials: Qhat[l] = sum_{s < nseg} part[b*s_b + l*s_l + s*s_s + o].
+// q[b][o][n] from partials: Qhat[l] = sum_{s < nseg} part[b*s_b + l*s_l + s*s_s + o];
+// the first n_keep (0: Nt) samples of the length-2Nt IFFT, rows n_keep apart.
 cudaError_t launch_reduce_irfft(const float2* part, int B, int No, int nseg, int Nt, long long s_b, long long s_l,
-                                long long s_s, const float2* tw, float* q, cudaStream_t st);
+                                long long s_s, const float2* tw, float* q, cudaStream_t st, int n_keep = 0);
+// Spectra X[l][r] (l < Nb, r < per_bin) times (1 - W_L^l) / dt, W_L^l = tw[l].
+cudaError_t launch_scale_dt(float2* X, int Nb, long long per_bin, const float2* tw, float inv_dt, cudaStream_t st);
 // r = q - d in place (B blocks of n_per_b floats); loss[b] = 0.5 sum r^2 (optional).
 cudaError_t launch_residual(float* q, const float* d, int B, long long n_per_b, float* loss, cudaStream_t st);
 cudaError_t launch_store_blocks(const float2* src, int Nb, long long n_per_l, int el, void* dst, void* dst_lo,

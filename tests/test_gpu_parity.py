@@ -340,3 +340,54 @@ def test_active_lengths_match_zero_filled_tails(engine, prec):
     with pytest.raises(s2w.S2WError):
         ctx.waveforms_active(torch.tensor(zeroed, device="cuda"), [Nt + 1] + lens[1:])
     ctx.sync()
+
+
+@pytest.mark.parametrize("prec,tol,dt_mode", [("fp32", 1e-5, "backward"), ("bf16_hilo", 2e-5, "backward"),
+                                              ("fp32", 1e-5, "none")])
+def test_single_pass_variant(prec, tol, dt_mode):
+    """The single-pass ablation (L = 4 Nt, D_t folded into Phat, no
+    retransform) meets the same bar as the two-pass path and agrees with it;
+    its operators take (2 Nt + 1) / (Nt + 1) times the bytes."""
+    Ns, Ng, No, Nt, B = 24, 700, 6, 64, 3
+    geom = compact_box(Ns, Ng, No, seed=71)
+    rng = np.random.default_rng(72)
+    slip = rng.standard_normal((B, Ns, Nt))
+    slip[:, :, Nt // 2:] = 0
+    st = torch.tensor(slip, dtype=torch.float32, device="cuda")
+    c1 = make_context(s2w, geom, Nt, prec_g=prec, dt_mode=dt_mode, max_batch=B, engine="stream",
+                      single_pass=True, chunk=256)
+    c2 = make_context(s2w, geom, Nt, prec_g=prec, dt_mode=dt_mode, max_batch=B, engine="stream")
+    q1 = c1.waveforms(st).cpu().numpy()
+    q2 = c2.waveforms(st).cpu().numpy()
+    G = geom.greens_rows(0, Ng, Nt)
+    P = geom.adjoint_cols(0, Ng, Nt)
+    q_ref = oracle.waveforms(G, P, slip, dt_mode=dt_mode)
+    wn, kappa = window_norms(G, P, slip, dt_mode)
+    assert_parity(q1, q_ref, wn, kappa, tol=tol, label=f"single pass {prec} {dt_mode}")
+    assert np.all(np.linalg.norm((q1 - q2).reshape(B, -1), axis=1) <= 2 * tol * wn)
+    g1, _ = c1.operator_bytes()
+    g2, _ = c2.operator_bytes()
+    assert g1 * (Nt + 1) == g2 * (2 * Nt + 1)
+    with pytest.raises(s2w.S2WError):
+        c1.waveforms(st, seafloor=torch.empty((B, Ng, Nt), device="cuda"))
+    with pytest.raises(s2w.S2WError):
+        c1.adjoint(torch.zeros((B, No, Nt), device="cuda"))
+    c1.sync()
+
+
+def test_single_pass_spectral_loads():
+    """Spectra of length 4 Nt handed to the single-pass variant directly."""
+    Ns, Ng, No, Nt, B = 16, 500, 4, 32, 2
+    geom = compact_box(Ns, Ng, No, seed=73)
+    G = geom.greens_rows(0, Ng, Nt)
+    P = geom.adjoint_cols(0, Ng, Nt)
+    Ghat = np.ascontiguousarray(np.fft.rfft(G, n=4 * Nt, axis=2).transpose(2, 0, 1)).astype(np.complex64)
+    Phat = np.ascontiguousarray(np.fft.rfft(P, n=4 * Nt, axis=2).transpose(2, 0, 1)).astype(np.complex64)
+    ctx = s2w.Context(Ns, Ng, No, Nt, max_batch=B, engine="stream", single_pass=True)
+    ctx.load_greens_spectra(0, Ghat)
+    ctx.load_adjoint_spectra(0, Phat)
+    slip = np.random.default_rng(74).standard_normal((B, Ns, Nt))
+    slip[:, :, Nt // 2:] = 0
+    q = ctx.waveforms(torch.tensor(slip, dtype=torch.float32, device="cuda")).cpu().numpy()
+    ctx.sync()
+    assert_parity(q, oracle.waveforms(G, P, slip), *window_norms(G, P, slip), tol=1e-5, label="single pass spectra")
