@@ -292,8 +292,8 @@ def run_ours(args, rank, world, local_rank):
 
     # tensor-engine choices measured on the loaded operators
     tuning = None
-    if not gradient and args.prec_g == "bf16" and args.engine == "auto" and args.tc_cluster == 0 \
-            and not args.no_autotune:
+    if not gradient and args.prec_g in ("bf16", "bf16_hilo", "fp8") and args.engine == "auto" \
+            and args.tc_cluster == 0 and not args.single_pass and not args.no_autotune:
         tuning = ctx.autotune(B, stream=stream)
     # one CUDA graph of the pipeline per input buffer, captured during setup
     use_graph = not gradient and not args.no_graph
