@@ -76,11 +76,13 @@ typedef enum { S2W_DT_BACKWARD = 0, S2W_DT_NONE = 1 } s2w_dt_mode;
  * stream the resident spectra once per rupture (any storage precision).
  * TENSOR: tcgen05 tensor-core GEMMs over the whole rupture batch (one pass
  * over the spectra per sub-batch); needs prec_g = BF16, BF16_HILO or
- * FP8_E4M3, Nt <= 256, No <= 128.  With BF16 (or FP8, whose tiles are widened
- * exactly to BF16 in shared memory and rescaled per (bin, 256 rows) in the
- * epilogue) the activations (slip and velocity spectra) and the stage-2
- * operator are rounded to BF16 and the retransform runs as a GEMM
- * (sub-batches of up to 256 ruptures).  With BF16_HILO every operand
+ * FP8_E4M3, Nt <= 256, No <= 128.  With BF16 the activations (slip and
+ * velocity spectra) and the stage-2 operator are rounded to BF16 and the
+ * retransform runs as a GEMM (sub-batches of up to 256 ruptures).  FP8 works
+ * the same way except in stage 1: its tiles are widened exactly to FP16 in
+ * shared memory and multiplied by the slip spectra packed as FP16 (scaled by a
+ * power of two from their largest magnitude), with the per-(bin, 256 rows)
+ * scales and that power of two undone in the epilogue.  With BF16_HILO every operand
  * (both operators and both activations) is split into hi + lo BF16 parts,
  * each K step issues three MMAs (hi hi, hi lo, lo hi) into FP32
  * accumulators, and the retransform is the FP32 FFT (sub-batches of up to

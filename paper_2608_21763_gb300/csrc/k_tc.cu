@@ -188,6 +188,11 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
          (static_cast<uint32_t>(M >> 4) << 24);
 }
 
+// Same with FP16 A and B (the A / B format fields left at 0 = F16).
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+  return (1u << 4) | (static_cast<uint32_t>(N >> 3) << 17) | (static_cast<uint32_t>(M >> 4) << 24);
+}
+
 // One ring of K-block stages, each holding the A tile and the B tile of the
 // same K block (loaded together, released together).
 // CL > 1: clusters of CL CTAs take CL adjacent M tiles of the same (bin, K
@@ -199,10 +204,10 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
 // relative, is dropped).
 // MODE: 0 BF16 operands; 1 split (hi/lo parts of both operands); 2 FP8 e4m3
 // A: TMA brings the FP8 tile (row-major, one byte per K element) into a
-// staging slot of the stage, warps 6-9 widen it exactly to BF16 (e4m3 ->
-// f16 -> f32 -> bf16 loses nothing) into the swizzled A slot and signal
-// `aready`; the per-(bin, 256-row) scale is applied in the epilogue
-// (row_scale).  Each MODE is its own instantiation and kernel, so the plain
+// staging slot of the stage, warps 6-9 widen it exactly to FP16 (one
+// cvt per pair) into the swizzled A slot and signal `aready`; the MMAs take
+// FP16 A and B (B packed as FP16 with a power-of-two scale from its amax);
+// the per-(bin, 256-row) scale and the B scale are undone in the epilogue.  Each MODE is its own instantiation and kernel, so the plain
 // kernel carries none of the other modes' code.
 template <int BK, int CL, int MODE>
 __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUtensorMap* tmB, const CUtensorMap* tmA2,
@@ -236,7 +241,8 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUten
   const int n_mma = N > 256 ? N / 256 : 1;
   const int n_mma_cols = N > 256 ? 256 : N;
   const int slice_rows = N / CL;  // B rows this CTA loads (and multicasts)
-  const uint32_t idesc = idesc_bf16(kBlockM, n_mma_cols);
+  // FP8 A is widened to FP16 (one conversion per pair, exact); B is FP16 too
+  const uint32_t idesc = F8 ? idesc_f16(kBlockM, n_mma_cols) : idesc_bf16(kBlockM, n_mma_cols);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -386,9 +392,7 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUten
             for (int h = 0; h < 2; ++h) {
               const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2(
                   static_cast<__nv_fp8x2_storage_t>((ww[k] >> (16 * h)) & 0xffffu), __NV_E4M3);
-              const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&hr));
-              const __nv_bfloat162 b = __floats2bfloat162_rn(f.x, f.y);
-              o[2 * k + h] = *reinterpret_cast<const unsigned*>(&b);
+              o[2 * k + h] = static_cast<unsigned>(hr.x) | (static_cast<unsigned>(hr.y) << 16);
             }
           }
           // 16-byte chunks 2 cc and 2 cc + 1 of the row, placed as the TMA
@@ -419,6 +423,7 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUten
       const bool live = row < a.M_total && mt < a.m_tiles;
       float scale = 1.f;
       if (a.row_scale != nullptr && live) scale = a.row_scale[static_cast<long long>(l) * a.nblk + row / 256];
+      if (a.b_amax != nullptr) scale *= f16_unscale(*a.b_amax);  // undo the FP16 B operand's power-of-two scale
       auto emit = [&](int c0, const float* v, int ncols) {
         if (!live) return;
         for (int k = 0; k < ncols / 2; ++k) {
@@ -508,6 +513,38 @@ __global__ void k_pack_b(const float2* __restrict__ src, int Nb, int T, long lon
       lo[o0] = __floats2bfloat162_rn(r0.x - __low2float(h0), r0.y - __high2float(h0));
       lo[o0 + Kc] = __floats2bfloat162_rn(r1.x - __low2float(h1), r1.y - __high2float(h1));
     }
+  }
+}
+
+// Largest |Re|, |Im| of n complex values into *amax (float bits; *amax
+// starts at 0): the range of a B operand packed as FP16.
+__global__ void k_amax_c(const float2* __restrict__ x, long long n, unsigned* __restrict__ amax) {
+  float m = 0.f;
+  for (long long e = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; e < n;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const float2 v = x[e];
+    m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(amax, __float_as_uint(m));  // non-negative floats order as unsigned
+}
+
+// As k_pack_b (plain embedding), FP16 entries scaled by f16_scale(*amax).
+__global__ void k_pack_b_f16(const float2* __restrict__ src, int Nb, int T, long long nc, long long s_l,
+                             long long s_t, long long Kc, int N_alloc, const unsigned* __restrict__ amax,
+                             __half2* __restrict__ dst) {
+  const float sc = f16_scale(*amax);
+  const long long total = static_cast<long long>(Nb) * T * nc;
+  for (long long e = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long c = e % nc;
+    const long long t = (e / nc) % T;
+    const long long l = e / (nc * T);
+    const float2 v = src[l * s_l + t * s_t + c];
+    const long long o0 = (l * N_alloc + 2 * t) * Kc + c;
+    dst[o0] = __floats2half2_rn(v.x * sc, -v.y * sc);
+    dst[o0 + Kc] = __floats2half2_rn(v.y * sc, v.x * sc);
   }
 }
 
@@ -926,6 +963,18 @@ cudaError_t launch_pack_b(const float2* src, int Nb, int T, long long nc, long l
   if (total <= 0) return cudaSuccess;
   k_pack_b<<<grid_for_tc(total), 256, 0, st>>>(src, Nb, T, nc, s_l, s_t, c0, Kc, N_alloc, conj,
                                                static_cast<__nv_bfloat162*>(hi), static_cast<__nv_bfloat162*>(lo));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_b_f16(const float2* src, int Nb, int T, long long nc, long long s_l, long long s_t,
+                              long long Kc, int N_alloc, unsigned* amax, void* dst, cudaStream_t st) {
+  const long long total = static_cast<long long>(Nb) * T * nc;
+  if (total <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(amax, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  k_amax_c<<<grid_for_tc(total), 256, 0, st>>>(src, total, amax);
+  k_pack_b_f16<<<grid_for_tc(total), 256, 0, st>>>(src, Nb, T, nc, s_l, s_t, Kc, N_alloc, amax,
+                                                   static_cast<__half2*>(dst));
   return cudaGetLastError();
 }
 

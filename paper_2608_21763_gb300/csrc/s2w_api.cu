@@ -90,6 +90,7 @@ struct s2w_ctx {
   float2* tc_ghat = nullptr;  // [Nb][tc_bsub][Ns] complex FP32
   bool single_pass = false;     // L = 4 Nt, D_t folded into Phat, no retransform
   int* ws_lens = nullptr;       // active samples per rupture (s2w_waveforms_active), [max_batch]
+  unsigned* d_amax = nullptr;   // FP16 B operand of the FP8 tensor path: its amax (float bits)
   const int* cur_lens = nullptr;  // set for the duration of an s2w_waveforms_active call
   bool tc_split = false;    // BF16 hi/lo operands and activations (three MMAs per K step)
   void* tc_bp1_lo = nullptr;  // split: low-order parts of tc_bp1, tc_vhat, tc_p2
@@ -247,7 +248,7 @@ void free_all(s2w_ctx* c) {
                 c->ws_vhat, c->ws_part, c->ws_q, c->ws_seafloor, c->d_status, c->tc_bp1, c->ws_rhat, c->ws_gpart, c->ws_resid, c->ws_d, c->ws_loss,
                 c->tc_mhat, c->tc_vhat, c->tc_part, c->tc_p2, c->tc_T, c->tc_bp1_lo, c->tc_vhat_lo, c->tc_p2_lo,
                 c->tc_gT, c->tc_gT_lo, c->tc_pT, c->tc_pT_lo, c->tc_rb, c->tc_rb_lo, c->tc_ub, c->tc_ub_lo,
-                c->tc_ghat, c->ws_lens};
+                c->tc_ghat, c->ws_lens, c->d_amax};
   for (void* p : ps)
     if (p) cudaFree(p);
 }
@@ -410,10 +411,15 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
                           ctx->cur_lens ? ctx->cur_lens + b0 : nullptr));
     }
     const int sp = ctx->tc_split ? 1 : 0;
+    const bool f8 = ctx->opts.prec_g == S2W_PREC_FP8_E4M3;
     {
-      StageTimer t(ctx, 6, st);
-      CK(launch_pack_b(ctx->ws_shat, static_cast<int>(Nb), Bs, Ns_pad, static_cast<long long>(Bs) * Ns_pad, Ns_pad, 0,
-                       Ns_pad, ctx->tc_n1max, 0, ctx->tc_bp1, ctx->tc_bp1_lo, st));
+      StageTimer t(ctx, 6, st, f8 ? 2 : 1);
+      if (f8)  // FP16 operand for the FP16 MMAs of the FP8 path, scaled by a power of two from its amax
+        CK(launch_pack_b_f16(ctx->ws_shat, static_cast<int>(Nb), Bs, Ns_pad, static_cast<long long>(Bs) * Ns_pad,
+                             Ns_pad, Ns_pad, ctx->tc_n1max, ctx->d_amax, ctx->tc_bp1, st));
+      else
+        CK(launch_pack_b(ctx->ws_shat, static_cast<int>(Nb), Bs, Ns_pad, static_cast<long long>(Bs) * Ns_pad, Ns_pad,
+                         0, Ns_pad, ctx->tc_n1max, 0, ctx->tc_bp1, ctx->tc_bp1_lo, st));
     }
     {
       StageTimer t(ctx, 1, st);
@@ -422,7 +428,6 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
       const int m1 = static_cast<int>((Ng + 127) / 128);
       const int cl = fit_cluster(ctx->tc_cl1, N1, m1);
       const int brows = cl > 1 ? N1 / cl : (N1 > 256 ? 256 : N1);
-      const bool f8 = ctx->opts.prec_g == S2W_PREC_FP8_E4M3;
       if (f8)  // one byte per K element: row pitch 2 Ns_pad bytes
         CK(tc_encode_3d_u8(&ta, ctx->G, K1, Ng, Nb, 128, bk));
       else
@@ -444,9 +449,10 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
       a.a_lo = sp;
       a.b_lo = sp;
       a.a_fp8 = f8 ? 1 : 0;
-      if (f8) {  // FP8 rows carry one scale per (bin, 256 grid rows)
+      if (f8) {  // FP8 rows carry one scale per (bin, 256 grid rows); B its power-of-two scale
         a.row_scale = ctx->G_scale;
         a.nblk = ctx->nblk;
+        a.b_amax = ctx->d_amax;
       }
       a.tmem_cols = N1 <= 32 ? 32 : (N1 <= 64 ? 64 : (N1 <= 128 ? 128 : (N1 <= 256 ? 256 : 512)));
       a.cluster = cl;
@@ -655,6 +661,7 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
   if ((e = dalloc(&ctx->ws_d, sizeof(float) * B * No * Nt)) != cudaSuccess) return bad(e, "targets");
   if ((e = dalloc(&ctx->ws_loss, sizeof(float) * B)) != cudaSuccess) return bad(e, "losses");
   if ((e = dalloc(&ctx->ws_lens, sizeof(int) * B)) != cudaSuccess) return bad(e, "active lengths");
+  if ((e = dalloc(&ctx->d_amax, sizeof(unsigned))) != cudaSuccess) return bad(e, "operand range word");
   if ((e = dalloc(&ctx->ws_gpart, sizeof(float2) * Nb * ctx->adj_nchunk * ctx->Ns_pad)) != cudaSuccess)
     return bad(e, "adjoint partials");
   ctx->tc_on = !ctx->single_pass && o.prec_g != S2W_PREC_FP32 && 2 * No <= 256 &&

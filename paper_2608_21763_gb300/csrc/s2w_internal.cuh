@@ -221,7 +221,9 @@ struct TcArgs {
   int nblk;
   int a_lo;                // 1: A has a low-order BF16 part (second tensor map): adds A_lo B
   int b_lo;                // 1: B has a low-order BF16 part: adds A B_lo
-  int a_fp8;               // 1: A is FP8 e4m3 (byte tensor map, row-major), widened in shared memory; needs row_scale
+  int a_fp8;               // 1: A is FP8 e4m3 (byte tensor map, row-major), widened to FP16 in shared memory;
+                           //    needs row_scale; B is FP16 (launch_pack_b_f16) with its amax in b_amax
+  const unsigned* b_amax;  // FP16 B operand: amax (float bits) that set its power-of-two scale
   int* status;
 };
 // bk = 64: 128-byte swizzle, K boxes of 64 BF16; bk = 32: 64-byte swizzle.
@@ -242,6 +244,19 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
 // complex columns c0 + c; conj selects the embedding of conj(A) x.
 cudaError_t launch_pack_b(const float2* src, int Nb, int T, long long nc, long long s_l, long long s_t, long long c0,
                           long long Kc, int N_alloc, int conj, void* hi, void* lo, cudaStream_t st);
+// FP16 B operands: the power-of-two scale that keeps |x| * scale <= 2^14
+// (inside the FP16 range with room to spare), and its inverse.
+__device__ __forceinline__ float f16_scale(unsigned amax_bits) {
+  const float amax = __uint_as_float(amax_bits);
+  if (!(amax > 0.f)) return 1.f;
+  return exp2f(static_cast<float>(14 - static_cast<int>(ceilf(log2f(amax)))));
+}
+__device__ __forceinline__ float f16_unscale(unsigned amax_bits) { return 1.f / f16_scale(amax_bits); }
+// Plain-embedding B operand as FP16 (k_pack_b layout, c0 = 0, no lo part):
+// measures amax of the source first (amax: one device word), then packs x *
+// f16_scale(amax).
+cudaError_t launch_pack_b_f16(const float2* src, int Nb, int T, long long nc, long long s_l, long long s_t,
+                              long long Kc, int N_alloc, unsigned* amax, void* dst, cudaStream_t st);
 // A operand dst[(l*rows_total + r0 + r)*Kc + c0 + c] (BF16 pairs, hi and
 // optional lo) from complex FP32 src[l*s_l + r*s_r + c*s_c], r < rows, c < nc.
 cudaError_t launch_pack_a(const float2* src, int Nb, int rows, long long nc, long long s_l, long long s_r,

@@ -228,3 +228,25 @@ def test_fp8_tensor_clusters_bitwise():
     q2, _, _, _, _ = run_case(geom, 64, 40, seed=64, prec="fp8", tc_cluster=2, chunk=256)
     assert_parity(q2, q_ref, *wn, tol=1e-1, label="fp8 tensor cluster 2")
     assert np.array_equal(q1, q2)
+
+
+def test_fp8_tensor_operand_range_is_scaled():
+    """The FP8 path's FP16 B operand carries a power-of-two scale from its
+    amax: slip scaled by 1e6 or 1e-6 (beyond / far inside the FP16 range)
+    gives the scaled waveforms (linearity to the path's accuracy)."""
+    geom = compact_box(24, 700, 6, seed=65)
+    Nt, B = 64, 3
+    rng = np.random.default_rng(66)
+    slip = rng.standard_normal((B, geom.Ns, Nt))
+    slip[:, :, Nt // 2:] = 0
+    ctx = make_context(s2w, geom, Nt, prec_g="fp8", max_batch=B, chunk=256, engine="tensor")
+    q1 = ctx.waveforms(torch.tensor(slip, dtype=torch.float32, device="cuda")).cpu().numpy().astype(np.float64)
+    G = geom.greens_rows(0, geom.Ng, Nt)
+    P = geom.adjoint_cols(0, geom.Ng, Nt)
+    wn, _ = window_norms(G, P, slip)
+    for alpha in (1e6, 1e-6):
+        qa = ctx.waveforms(torch.tensor(slip * alpha, dtype=torch.float32, device="cuda")).cpu().numpy()
+        assert np.all(np.isfinite(qa))
+        d = np.linalg.norm((qa / alpha - q1).reshape(B, -1), axis=1)
+        assert np.all(d <= 1e-3 * wn), (alpha, d / wn)
+    ctx.sync()
