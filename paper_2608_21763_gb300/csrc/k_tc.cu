@@ -580,8 +580,9 @@ __global__ void k_pack_a(const float2* __restrict__ src, int Nb, int rows, long 
 // the definitions, rounded to BF16) every tile of 128 signals is
 //   V (128 x K) = M (128 x K) T^T,
 // one tcgen05 GEMM per tile.  The M tile is written into shared memory by
-// eight fill warps (coalesced loads of mhat[l][b][i0..i0+127], BF16
-// conversion, 128-byte swizzled K-major layout), T streams through a ring by
+// eight fill warps, one k-block each so that all of a tile's loads are in
+// flight together (coalesced loads of mhat[l][b][i0..i0+127], 128-byte
+// swizzled K-major layout, 16-byte stores), T streams through a ring by
 // TMA (it stays in L2), the accumulator rows go back out as BF16 velocity
 // spectra in the stage-2 operand layout.
 // Warps: 0 TMA (T), 1 TMEM + MMA, 2-5 epilogue, 6-13 fill.
@@ -618,7 +619,7 @@ __global__ void __launch_bounds__(kRtThreads, 1)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < KB; ++s) {
-      mbar_init(afull + s, kRtFillWarps);
+      mbar_init(afull + s, 1);  // one fill warp per k-block
       mbar_init(afree + s, 1);
     }
     for (int s = 0; s < 2; ++s) {
@@ -728,7 +729,9 @@ __global__ void __launch_bounds__(kRtThreads, 1)
       if (lane == 0) mbar_arrive(acc_empty);
     }
   } else {
-    // fill warps: M tile k-block kb holds bins 32 kb .. 32 kb + 31 for 128 signals
+    // fill warps: warp f fills k-blocks f, f + 8, ... (k-block kb holds bins
+    // 32 kb .. 32 kb + 31 for 128 signals), so all k-blocks of a tile load
+    // concurrently; 64 loads in flight per lane, 16-byte swizzled stores
     const int f = warp - 6;
     int tl = 0;
     bool ok = true;
@@ -736,39 +739,46 @@ __global__ void __launch_bounds__(kRtThreads, 1)
       const int b = static_cast<int>(t / mtiles);
       const int i0 = static_cast<int>(t % mtiles) * kBlockM;
       const unsigned* mbb = reinterpret_cast<const unsigned*>(a.mhat_bf) + static_cast<long long>(b) * a.ld_b;
-      for (int kb = 0; kb < KB; ++kb) {
+      for (int kb = f; kb < KB && ok; kb += kRtFillWarps) {
         if (tl > 0 && !mbar_wait_bounded(afree + kb, (tl - 1) & 1, a.status, DEV_ERR_TIMEOUT_EMPTY)) {
           ok = false;
           break;
         }
         unsigned char* slot = sA + kb * kABytes;
-        unsigned raw[4][4], rawn[4];
-        // all loads of the k-block first (16 per lane), then store
+        unsigned rawn[4] = {0u, 0u, 0u, 0u};
+        if (kb == 0) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {        // bins: l_local = f + 8 j
-          const long long lo = static_cast<long long>(kb * 32 + f + 8 * j) * a.ld_l;
-#pragma unroll
-          for (int g = 0; g < 4; ++g) {      // signals: row = 32 g + lane
+          for (int g = 0; g < 4; ++g) {
             const int i = i0 + 32 * g + lane;
-            raw[j][g] = i < a.Ng ? __ldg(mbb + lo + i) : 0u;
+            rawn[g] = i < a.Ng ? __ldg(mbb + static_cast<long long>(Nt) * a.ld_l + i) : 0u;
           }
         }
 #pragma unroll
-        for (int g = 0; g < 4; ++g) {
-          const int i = i0 + 32 * g + lane;
-          rawn[g] = (kb == 0 && f == 0 && i < a.Ng) ? __ldg(mbb + static_cast<long long>(Nt) * a.ld_l + i) : 0u;
-        }
+        for (int hh = 0; hh < 2; ++hh) {  // bins 16 hh .. 16 hh + 15 of the k-block
+          unsigned raw[16][4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int ll = f + 8 * j;          // local bin -> k_local = 2 ll, 2 ll + 1
+          for (int j = 0; j < 16; ++j) {
+            const long long lo = static_cast<long long>(kb * 32 + 16 * hh + j) * a.ld_l;
 #pragma unroll
-          for (int g = 0; g < 4; ++g) {
-            const int row = 32 * g + lane;
-            unsigned w = raw[j][g];
-            if (kb == 0 && ll == 0) w = (w & 0xffffu) | (rawn[g] << 16);  // slot k = 1 carries Re(bin Nt)
-            const int byte = ll * 4;                 // (2 ll) bf16 * 2 bytes
-            const int off = row * 128 + ((((byte >> 4) ^ (row & 7)) << 4) | (byte & 15));
-            *reinterpret_cast<unsigned*>(slot + off) = w;
+            for (int g = 0; g < 4; ++g) {  // signals: row = 32 g + lane
+              const int i = i0 + 32 * g + lane;
+              raw[j][g] = i < a.Ng ? __ldg(mbb + lo + i) : 0u;
+            }
+          }
+          if (kb == 0 && hh == 0) {
+#pragma unroll
+            for (int g = 0; g < 4; ++g) raw[0][g] = (raw[0][g] & 0xffffu) | (rawn[g] << 16);  // k = 1: Re(bin Nt)
+          }
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {  // 16-byte chunk 4 hh + c = bins 16 hh + 4 c .. + 3
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+              const int row = 32 * g + lane;
+              const int chunk = 4 * hh + c;
+              const int off = row * 128 + ((chunk ^ (row & 7)) << 4);
+              *reinterpret_cast<uint4*>(slot + off) =
+                  make_uint4(raw[4 * c][g], raw[4 * c + 1][g], raw[4 * c + 2][g], raw[4 * c + 3][g]);
+            }
           }
         }
         fence_proxy_async_smem();

@@ -233,7 +233,9 @@ def test_fp8_tensor_clusters_bitwise():
 def test_fp8_tensor_operand_range_is_scaled():
     """The FP8 path's FP16 B operand carries a power-of-two scale from its
     amax: slip scaled by 1e6 or 1e-6 (beyond / far inside the FP16 range)
-    gives the scaled waveforms (linearity to the path's accuracy)."""
+    gives the scaled waveforms, finite and within the tensor path's bar (a
+    non-power-of-two rescale reshuffles the BF16 rounding of the later
+    stages, ~2e-3 of the window; an overflow or underflow would be O(1))."""
     geom = compact_box(24, 700, 6, seed=65)
     Nt, B = 64, 3
     rng = np.random.default_rng(66)
@@ -248,5 +250,5 @@ def test_fp8_tensor_operand_range_is_scaled():
         qa = ctx.waveforms(torch.tensor(slip * alpha, dtype=torch.float32, device="cuda")).cpu().numpy()
         assert np.all(np.isfinite(qa))
         d = np.linalg.norm((qa / alpha - q1).reshape(B, -1), axis=1)
-        assert np.all(d <= 1e-3 * wn), (alpha, d / wn)
+        assert np.all(d <= TOL_TC * wn), (alpha, d / wn)
     ctx.sync()
