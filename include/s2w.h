@@ -82,11 +82,10 @@ typedef enum { S2W_DT_BACKWARD = 0, S2W_DT_NONE = 1 } s2w_dt_mode;
  * the same way except in stage 1: its tiles are widened exactly to FP16 in
  * shared memory and multiplied by the slip spectra packed as FP16 (scaled by a
  * power of two from their largest magnitude), with the per-(bin, 256 rows)
- * scales and that power of two undone in the epilogue.  With BF16_HILO every operand
- * (both operators and both activations) is split into hi + lo BF16 parts,
- * each K step issues three MMAs (hi hi, hi lo, lo hi) into FP32
- * accumulators, and the retransform is the FP32 FFT (sub-batches of up to
- * 128).  A call that asks for the seafloor field runs on the stream
+ * scales and that power of two undone in the epilogue.  With BF16_HILO every
+ * operand (both operators, both activations and the retransform matrix) is
+ * split into hi + lo BF16 parts and each K step issues three MMAs (hi hi,
+ * hi lo, lo hi) into FP32 accumulators (sub-batches of up to 128).  A call that asks for the seafloor field runs on the stream
  * kernels.  AUTO: TENSOR for calls with B >= the batch threshold (2, or what
  * s2w_autotune measured) when prec_g allows it, STREAM otherwise.  The
  * stream engine handles the ruptures of a call in groups of up to 64. */

@@ -591,23 +591,43 @@ constexpr int kRtThreads = 448;
 constexpr int kRtFillWarps = 8;
 
 
+// K blocks run outer and the (up to two) 256-column output halves inner, so a
+// k-block of the M tile is done once both halves have used it: the M tile
+// lives in a ring of RA k-block slots rather than whole in shared memory.
+// SPLIT: the FP32 seafloor spectra are split by the fill warps into hi + lo
+// BF16 parts, T comes as hi + lo (both from the FP64 matrix), three MMAs per
+// K step (hi hi, hi lo, lo hi), and the epilogue writes hi + lo velocity
+// spectra (the split stage-2 A operand); 32-element K blocks (64-byte
+// swizzle) keep the doubled slots inside shared memory.
+template <bool SPLIT>
 __global__ void __launch_bounds__(kRtThreads, 1)
-    k_tc_retransform(const __grid_constant__ CUtensorMap tmT, const TcRtArgs a) {
+    k_tc_retransform(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmT2,
+                     const TcRtArgs a) {
+  constexpr int BK = SPLIT ? 32 : 64;        // K elements per k-block
+  constexpr int kAs = kBlockM * BK * 2;      // one BF16 part of an M-tile k-block
+  constexpr int a_slot = kAs * (SPLIT ? 2 : 1);
+  constexpr int kBins = BK / 2;              // complex bins per k-block
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
   const int Nt = a.Nt;
   const int K = 2 * Nt;           // = N
-  const int KB = K / kBlockK;     // k-blocks per tile (A slots)
+  const int KB = K / BK;          // k-blocks per tile
   const int n_half = K > 256 ? 2 : 1;   // MMA column halves (256 output columns each)
   const int ncols = K > 256 ? 256 : K;
-  const int t_bytes = ncols * kBlockK * 2;
-  unsigned char* sA = smem;                               // KB slots of 16 KB
-  unsigned char* sT = smem + KB * kABytes;                // 2 stages of t_bytes
-  uint64_t* afull = reinterpret_cast<uint64_t*>(sT + 2 * t_bytes);
-  uint64_t* afree = afull + KB;
-  uint64_t* tfull = afree + KB;
-  uint64_t* tempty = tfull + 2;
-  uint64_t* acc_full = tempty + 2;
+  const int t_part = ncols * BK * 2;
+  const int t_slot = t_part * (SPLIT ? 2 : 1);
+  // one A slot per fill warp: with KB a power of two, slot s = n % RA is only
+  // ever filled by one warp (k-blocks kb = s mod KB, or s when KB >= RA), one
+  // ring lap apart, so no parity wait can run a phase ahead
+  constexpr int RA = kRtFillWarps;
+  const int RT = a.rt;
+  unsigned char* sA = smem;                  // RA k-block slots
+  unsigned char* sT = smem + RA * a_slot;    // RT slots of T
+  uint64_t* afull = reinterpret_cast<uint64_t*>(sT + RT * t_slot);
+  uint64_t* afree = afull + RA;
+  uint64_t* tfull = afree + RA;
+  uint64_t* tempty = tfull + RT;
+  uint64_t* acc_full = tempty + RT;
   uint64_t* acc_empty = acc_full + 1;
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(acc_empty + 1);
   const int warp = threadIdx.x >> 5;
@@ -618,11 +638,11 @@ __global__ void __launch_bounds__(kRtThreads, 1)
   const uint32_t tmem_cols = K <= 64 ? 64 : (K <= 128 ? 128 : (K <= 256 ? 256 : 512));
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < KB; ++s) {
+    for (int s = 0; s < RA; ++s) {
       mbar_init(afull + s, 1);  // one fill warp per k-block
       mbar_init(afree + s, 1);
     }
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < RT; ++s) {
       mbar_init(tfull + s, 1);
       mbar_init(tempty + s, 1);
     }
@@ -640,25 +660,26 @@ __global__ void __launch_bounds__(kRtThreads, 1)
   const uint32_t tmem = *tmem_holder;
 
   if (warp == 0) {
-    // T tiles in job order: tile, half, k-block
+    // T slots in job order: tile, k-block, half
     if (lane == 0) {
       int it = 0;
       bool ok = true;
       for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
-        for (int h = 0; h < n_half && ok; ++h) {
-          for (int kb = 0; kb < KB; ++kb, ++it) {
-            const int s = it & 1;
-            if (it >= 2 && !mbar_wait_bounded(tempty + s, ((it >> 1) - 1) & 1, a.status, DEV_ERR_TIMEOUT_EMPTY)) {
+        for (int kb = 0; kb < KB && ok; ++kb) {
+          for (int h = 0; h < n_half; ++h, ++it) {
+            const int s = it % RT;
+            if (it >= RT && !mbar_wait_bounded(tempty + s, ((it / RT) - 1) & 1, a.status, DEV_ERR_TIMEOUT_EMPTY)) {
               ok = false;
               break;
             }
-            mbar_arrive_expect_tx(tfull + s, t_bytes);
-            tma_load_3d(sT + s * t_bytes, &tmT, kb * kBlockK, h * ncols, 0, tfull + s);
+            mbar_arrive_expect_tx(tfull + s, t_slot);
+            tma_load_3d(sT + s * t_slot, &tmT, kb * BK, h * ncols, 0, tfull + s);
+            if constexpr (SPLIT) tma_load_3d(sT + s * t_slot + t_part, &tmT2, kb * BK, h * ncols, 0, tfull + s);
           }
         }
       }
-      for (int kk = (it > 2 ? it - 2 : 0); kk < it; ++kk)
-        mbar_wait_bounded(tfull + (kk & 1), (kk >> 1) & 1, a.status, DEV_ERR_TIMEOUT_FULL);
+      for (int kk = (it > RT ? it - RT : 0); kk < it; ++kk)
+        mbar_wait_bounded(tfull + kk % RT, (kk / RT) & 1, a.status, DEV_ERR_TIMEOUT_FULL);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -670,27 +691,36 @@ __global__ void __launch_bounds__(kRtThreads, 1)
           break;
         }
         tc_fence_after();
-        for (int h = 0; h < n_half && ok; ++h) {
-          for (int kb = 0; kb < KB && ok; ++kb, ++it) {
-            if (h == 0 && !mbar_wait_bounded(afull + kb, tl & 1, a.status, DEV_ERR_TIMEOUT_FULL)) {
-              ok = false;
-              break;
-            }
-            const int s = it & 1;
-            if (!mbar_wait_bounded(tfull + s, (it >> 1) & 1, a.status, DEV_ERR_TIMEOUT_FULL)) {
+        for (int kb = 0; kb < KB && ok; ++kb) {
+          const long long n = static_cast<long long>(tl) * KB + kb;
+          const int sa = static_cast<int>(n % RA);
+          if (!mbar_wait_bounded(afull + sa, static_cast<int>((n / RA) & 1), a.status, DEV_ERR_TIMEOUT_FULL)) {
+            ok = false;
+            break;
+          }
+          for (int h = 0; h < n_half; ++h, ++it) {
+            const int s = it % RT;
+            if (!mbar_wait_bounded(tfull + s, (it / RT) & 1, a.status, DEV_ERR_TIMEOUT_FULL)) {
               ok = false;
               break;
             }
             tc_fence_after();
-            const uint32_t sa = smem_u32(sA + kb * kABytes);
-            const uint32_t sb = smem_u32(sT + s * t_bytes);
+            const uint32_t ua = smem_u32(sA + sa * a_slot);
+            const uint32_t ub = smem_u32(sT + s * t_slot);
 #pragma unroll
-            for (int k = 0; k < kBlockK / 16; ++k)
-              tc_mma_bf16(tmem + h * ncols, sdesc_sw128(sa + k * 32), sdesc_sw128(sb + k * 32), idesc,
-                          (kb > 0 || k > 0) ? 1u : 0u);
+            for (int k = 0; k < BK / 16; ++k) {
+              const uint64_t ad = sdesc_sw<BK>(ua + k * 32);
+              const uint64_t bd = sdesc_sw<BK>(ub + k * 32);
+              tc_mma_bf16(tmem + h * ncols, ad, bd, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+              if constexpr (SPLIT) {
+                tc_mma_bf16(tmem + h * ncols, ad, sdesc_sw<BK>(ub + t_part + k * 32), idesc, 1u);
+                tc_mma_bf16(tmem + h * ncols, sdesc_sw<BK>(ua + kAs + k * 32), bd, idesc, 1u);
+              }
+            }
             tc_commit(tempty + s);
-            if (h == n_half - 1) tc_commit(afree + kb);
           }
+          if (!ok) break;
+          tc_commit(afree + sa);
         }
         if (!ok) break;
         tc_commit(acc_full);
@@ -708,6 +738,12 @@ __global__ void __launch_bounds__(kRtThreads, 1)
       tc_fence_after();
       const uint32_t tbase = tmem + (static_cast<uint32_t>(q * 32) << 16);
       __nv_bfloat162* out = a.vhat + static_cast<long long>(b) * a.vld_b + i;
+      __nv_bfloat162* out_lo = SPLIT ? a.vhat_lo + static_cast<long long>(b) * a.vld_b + i : nullptr;
+      auto put = [&](long long off, float re, float im) {
+        const __nv_bfloat162 hi = __floats2bfloat162_rn(re, im);
+        out[off] = hi;
+        if constexpr (SPLIT) out_lo[off] = __floats2bfloat162_rn(re - __low2float(hi), im - __high2float(hi));
+      };
       // K = 2 Nt is a multiple of 64 for every supported Nt (32..256)
       for (int c0 = 0; c0 < K; c0 += 64) {
         float v[64];
@@ -717,10 +753,10 @@ __global__ void __launch_bounds__(kRtThreads, 1)
         for (int k = 0; k < 32; ++k) {
           const int l = c0 / 2 + k;
           if (l == 0) {
-            out[0] = __floats2bfloat162_rn(v[0], 0.f);
-            out[static_cast<long long>(Nt) * a.vld_l] = __floats2bfloat162_rn(v[1], 0.f);
+            put(0, v[0], 0.f);
+            put(static_cast<long long>(Nt) * a.vld_l, v[1], 0.f);
           } else {
-            out[static_cast<long long>(l) * a.vld_l] = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+            put(static_cast<long long>(l) * a.vld_l, v[2 * k], v[2 * k + 1]);
           }
         }
       }
@@ -729,61 +765,114 @@ __global__ void __launch_bounds__(kRtThreads, 1)
       if (lane == 0) mbar_arrive(acc_empty);
     }
   } else {
-    // fill warps: warp f fills k-blocks f, f + 8, ... (k-block kb holds bins
-    // 32 kb .. 32 kb + 31 for 128 signals), so all k-blocks of a tile load
-    // concurrently; 64 loads in flight per lane, 16-byte swizzled stores
+    // fill warps: warp f fills k-blocks f, f + 8, ... of every tile (k-block
+    // kb holds bins kBins kb .. kBins kb + kBins - 1 for 128 signals; K slot 1
+    // of bin 0 carries Re(bin Nt)); all of a tile's loads are in flight
+    // together; 16-byte chunks are stored in the TMA swizzle pattern
     const int f = warp - 6;
     int tl = 0;
     bool ok = true;
     for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++tl) {
       const int b = static_cast<int>(t / mtiles);
       const int i0 = static_cast<int>(t % mtiles) * kBlockM;
-      const unsigned* mbb = reinterpret_cast<const unsigned*>(a.mhat_bf) + static_cast<long long>(b) * a.ld_b;
       for (int kb = f; kb < KB && ok; kb += kRtFillWarps) {
-        if (tl > 0 && !mbar_wait_bounded(afree + kb, (tl - 1) & 1, a.status, DEV_ERR_TIMEOUT_EMPTY)) {
+        const long long n = static_cast<long long>(tl) * KB + kb;
+        const int sa = static_cast<int>(n % RA);
+        if (n >= RA &&
+            !mbar_wait_bounded(afree + sa, static_cast<int>(((n / RA) - 1) & 1), a.status, DEV_ERR_TIMEOUT_EMPTY)) {
           ok = false;
           break;
         }
-        unsigned char* slot = sA + kb * kABytes;
-        unsigned rawn[4] = {0u, 0u, 0u, 0u};
-        if (kb == 0) {
-#pragma unroll
-          for (int g = 0; g < 4; ++g) {
-            const int i = i0 + 32 * g + lane;
-            rawn[g] = i < a.Ng ? __ldg(mbb + static_cast<long long>(Nt) * a.ld_l + i) : 0u;
-          }
-        }
-#pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {  // bins 16 hh .. 16 hh + 15 of the k-block
-          unsigned raw[16][4];
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const long long lo = static_cast<long long>(kb * 32 + 16 * hh + j) * a.ld_l;
-#pragma unroll
-            for (int g = 0; g < 4; ++g) {  // signals: row = 32 g + lane
-              const int i = i0 + 32 * g + lane;
-              raw[j][g] = i < a.Ng ? __ldg(mbb + lo + i) : 0u;
-            }
-          }
-          if (kb == 0 && hh == 0) {
-#pragma unroll
-            for (int g = 0; g < 4; ++g) raw[0][g] = (raw[0][g] & 0xffffu) | (rawn[g] << 16);  // k = 1: Re(bin Nt)
-          }
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {  // 16-byte chunk 4 hh + c = bins 16 hh + 4 c .. + 3
+        unsigned char* slot = sA + sa * a_slot;
+        auto chunk_off = [&](int row, int chunk) {  // 16-byte chunk `chunk` of K-major row `row`
+          return BK == 64 ? row * 128 + ((chunk ^ (row & 7)) << 4) : row * 64 + ((chunk ^ ((row >> 1) & 3)) << 4);
+        };
+        if constexpr (!SPLIT) {
+          const unsigned* mbb = reinterpret_cast<const unsigned*>(a.mhat_bf) + static_cast<long long>(b) * a.ld_b;
+          unsigned rawn[4] = {0u, 0u, 0u, 0u};
+          if (kb == 0) {
 #pragma unroll
             for (int g = 0; g < 4; ++g) {
-              const int row = 32 * g + lane;
-              const int chunk = 4 * hh + c;
-              const int off = row * 128 + ((chunk ^ (row & 7)) << 4);
-              *reinterpret_cast<uint4*>(slot + off) =
-                  make_uint4(raw[4 * c][g], raw[4 * c + 1][g], raw[4 * c + 2][g], raw[4 * c + 3][g]);
+              const int i = i0 + 32 * g + lane;
+              rawn[g] = i < a.Ng ? __ldg(mbb + static_cast<long long>(Nt) * a.ld_l + i) : 0u;
+            }
+          }
+#pragma unroll
+          for (int hh = 0; hh < kBins / 16; ++hh) {  // 16 bins per batch, 64 loads in flight
+            unsigned raw[16][4];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const long long lo = static_cast<long long>(kb * kBins + 16 * hh + j) * a.ld_l;
+#pragma unroll
+              for (int g = 0; g < 4; ++g) {
+                const int i = i0 + 32 * g + lane;
+                raw[j][g] = i < a.Ng ? __ldg(mbb + lo + i) : 0u;
+              }
+            }
+            if (kb == 0 && hh == 0) {
+#pragma unroll
+              for (int g = 0; g < 4; ++g) raw[0][g] = (raw[0][g] & 0xffffu) | (rawn[g] << 16);
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+#pragma unroll
+              for (int g = 0; g < 4; ++g) {
+                const int row = 32 * g + lane;
+                *reinterpret_cast<uint4*>(slot + chunk_off(row, 4 * hh + c)) =
+                    make_uint4(raw[4 * c][g], raw[4 * c + 1][g], raw[4 * c + 2][g], raw[4 * c + 3][g]);
+              }
+            }
+          }
+        } else {
+          const float2* mb = a.mhat32 + static_cast<long long>(b) * a.ld_b;
+          float rawn[4] = {0.f, 0.f, 0.f, 0.f};
+          if (kb == 0) {
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+              const int i = i0 + 32 * g + lane;
+              rawn[g] = i < a.Ng ? __ldg(mb + static_cast<long long>(Nt) * a.ld_l + i).x : 0.f;
+            }
+          }
+#pragma unroll
+          for (int hh = 0; hh < kBins / 8; ++hh) {  // 8 bins per batch, 32 float2 loads in flight
+            float2 raw[8][4];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const long long lo = static_cast<long long>(kb * kBins + 8 * hh + j) * a.ld_l;
+#pragma unroll
+              for (int g = 0; g < 4; ++g) {
+                const int i = i0 + 32 * g + lane;
+                raw[j][g] = i < a.Ng ? __ldg(mb + lo + i) : make_float2(0.f, 0.f);
+              }
+            }
+            if (kb == 0 && hh == 0) {
+#pragma unroll
+              for (int g = 0; g < 4; ++g) raw[0][g].y = rawn[g];  // K slot 1: Re(bin Nt)
+            }
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {  // chunk 2 hh + c = bins 8 hh + 4 c .. + 3
+#pragma unroll
+              for (int g = 0; g < 4; ++g) {
+                const int row = 32 * g + lane;
+                unsigned hw[4], lw[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                  const float2 x = raw[4 * c + e][g];
+                  const __nv_bfloat162 h2 = __floats2bfloat162_rn(x.x, x.y);
+                  const __nv_bfloat162 l2 = __floats2bfloat162_rn(x.x - __low2float(h2), x.y - __high2float(h2));
+                  hw[e] = *reinterpret_cast<const unsigned*>(&h2);
+                  lw[e] = *reinterpret_cast<const unsigned*>(&l2);
+                }
+                const int off = chunk_off(row, 2 * hh + c);
+                *reinterpret_cast<uint4*>(slot + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                *reinterpret_cast<uint4*>(slot + kAs + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+              }
             }
           }
         }
         fence_proxy_async_smem();
         __syncwarp();
-        if (lane == 0) mbar_arrive(afull + kb);
+        if (lane == 0) mbar_arrive(afull + sa);
       }
     }
   }
@@ -950,20 +1039,33 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
   return mode == 2 ? go(bk32{}, m2{}) : go(bk32{}, m0{});
 }
 
-cudaError_t launch_tc_retransform(const CUtensorMap& tmT, const TcRtArgs& a, int num_sms, cudaStream_t st) {
+cudaError_t launch_tc_retransform(const CUtensorMap& tmT, const CUtensorMap* tmT2, const TcRtArgs& a, int num_sms,
+                                  cudaStream_t st) {
   if (a.Nt < 32 || a.Nt > 256) return cudaErrorInvalidValue;
   const long long tiles = static_cast<long long>(a.Bs) * ((a.Ng + kBlockM - 1) / kBlockM);
   if (tiles <= 0) return cudaSuccess;
+  const bool split = tmT2 != nullptr;
+  if (split ? (a.mhat32 == nullptr || a.vhat_lo == nullptr) : (a.mhat_bf == nullptr)) return cudaErrorInvalidValue;
+  const int BK = split ? 32 : 64;
   const int K = 2 * a.Nt;
   const int ncols = K > 256 ? 256 : K;
-  const size_t smem = 1024 + static_cast<size_t>(K / kBlockK) * kABytes + 2ull * ncols * kBlockK * 2 +
-                      8 * (2 * (K / kBlockK) + 8) + 16;
+  const size_t a_slot = static_cast<size_t>(kBlockM) * BK * 2 * (split ? 2 : 1);
+  const size_t t_slot = static_cast<size_t>(ncols) * BK * 2 * (split ? 2 : 1);
+  TcRtArgs aa = a;
+  aa.ra = kRtFillWarps;  // one A slot per fill warp (see the kernel)
+  aa.rt = static_cast<int>((kSmemBudget - aa.ra * a_slot) / t_slot);
+  if (aa.rt > 4) aa.rt = 4;
+  if (aa.rt < 2) return cudaErrorInvalidValue;
+  const size_t smem = 1024 + aa.ra * a_slot + aa.rt * t_slot + 8 * (2 * aa.ra + 2 * aa.rt + 2) + 16;
   const long long grid = tiles < num_sms ? tiles : num_sms;
-  if (a.mhat_bf == nullptr) return cudaErrorInvalidValue;
-  cudaError_t e =
-      cudaFuncSetAttribute(k_tc_retransform, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  const void* kfn = split ? reinterpret_cast<const void*>(k_tc_retransform<true>)
+                          : reinterpret_cast<const void*>(k_tc_retransform<false>);
+  cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
-  k_tc_retransform<<<static_cast<unsigned>(grid), kRtThreads, smem, st>>>(tmT, a);
+  if (split)
+    k_tc_retransform<true><<<static_cast<unsigned>(grid), kRtThreads, smem, st>>>(tmT, *tmT2, aa);
+  else
+    k_tc_retransform<false><<<static_cast<unsigned>(grid), kRtThreads, smem, st>>>(tmT, tmT, aa);
   return cudaGetLastError();
 }
 

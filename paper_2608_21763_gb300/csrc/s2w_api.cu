@@ -102,7 +102,8 @@ struct s2w_ctx {
   float2* tc_part = nullptr;  // [Nb][nkc][b][No] complex FP32
   void* tc_p2 = nullptr;    // [Nb][tc_n2][Ng_pad2] bf16 pairs
   void* tc_T = nullptr;     // [2 Nt][2 Nt] bf16: retransform as a real-linear map
-  CUtensorMap tc_tmT;
+  void* tc_T_lo = nullptr;  // split: its low-order part
+  CUtensorMap tc_tmT, tc_tmT2;
   std::vector<unsigned char> g_loaded, p_loaded;
   long long g_count = 0, p_count = 0;
   // per-stage event timers
@@ -248,7 +249,7 @@ void free_all(s2w_ctx* c) {
                 c->ws_vhat, c->ws_part, c->ws_q, c->ws_seafloor, c->d_status, c->tc_bp1, c->ws_rhat, c->ws_gpart, c->ws_resid, c->ws_d, c->ws_loss,
                 c->tc_mhat, c->tc_vhat, c->tc_part, c->tc_p2, c->tc_T, c->tc_bp1_lo, c->tc_vhat_lo, c->tc_p2_lo,
                 c->tc_gT, c->tc_gT_lo, c->tc_pT, c->tc_pT_lo, c->tc_rb, c->tc_rb_lo, c->tc_ub, c->tc_ub_lo,
-                c->tc_ghat, c->ws_lens, c->d_amax};
+                c->tc_ghat, c->ws_lens, c->d_amax, c->tc_T_lo};
   for (void* p : ps)
     if (p) cudaFree(p);
 }
@@ -258,8 +259,9 @@ void free_all(s2w_ctx* c) {
 // k = 0: Re bin 0, k = 1: Re bin Nt, k = 2l / 2l+1: Re / Im bin l (0 < l < Nt),
 // the same ordering for the outputs n.  Column k is the map applied to basis
 // spectrum k, evaluated in FP64 from the definitions (inverse DFT head,
-// backward difference, zero-padded DFT), then rounded to BF16.
-std::vector<__nv_bfloat16> retransform_matrix(int Nt, int dt_mode, double dt) {
+// backward difference, zero-padded DFT); the caller rounds it to BF16 (hi,
+// and lo = the rounded remainder for the split path).
+std::vector<double> retransform_matrix(int Nt, int dt_mode, double dt) {
   const int L = 2 * Nt, K = 2 * Nt;
   std::vector<double> c(L), sn(L);
   for (int m = 0; m < L; ++m) {
@@ -291,9 +293,7 @@ std::vector<__nv_bfloat16> retransform_matrix(int Nt, int dt_mode, double dt) {
       }
     }
   }
-  std::vector<__nv_bfloat16> out(T.size());
-  for (size_t e = 0; e < T.size(); ++e) out[e] = __float2bfloat16_rn(static_cast<float>(T[e]));
-  return out;
+  return T;
 }
 
 // Tensor-core pipeline for a batch of ruptures (slip and q device pointers),
@@ -459,7 +459,7 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
       a.epi = 0;
       a.T = Bs;
       // the GEMM retransform rounds the seafloor spectra to BF16 anyway; the
-      // split path keeps them in FP32 for the FFT retransform
+      // split path keeps them in FP32 and splits them into hi + lo itself
       a.out = sp ? static_cast<float2*>(ctx->tc_mhat) : nullptr;
       a.out_bf = sp ? nullptr : static_cast<__nv_bfloat162*>(ctx->tc_mhat);
       a.ld_l = static_cast<long long>(Bs) * Ng;
@@ -467,17 +467,14 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
       a.status = ctx->d_status;
       CK(launch_tc_gemm(ta, tb, a, ctx->num_sms, st, sp ? &ta2 : nullptr, sp ? &tb2 : nullptr));
     }
-    if (sp) {
-      StageTimer t(ctx, 2, st);
-      CK(launch_retransform(static_cast<const float2*>(ctx->tc_mhat), Ng, static_cast<long long>(Bs) * Ng,
-                            static_cast<int>(Nt), ctx->tw, static_cast<float>(1.0 / ctx->opts.dt), ctx->opts.dt_mode,
-                            nullptr, static_cast<long long>(ctx->tc_bsub) * ctx->Ng_pad2, nullptr, st, Bs, Ng,
-                            ctx->Ng_pad2, static_cast<__nv_bfloat162*>(ctx->tc_vhat),
-                            static_cast<__nv_bfloat162*>(ctx->tc_vhat_lo)));
-    } else {
+    {
       StageTimer t(ctx, 2, st);
       TcRtArgs r{};
-      r.mhat_bf = reinterpret_cast<const __nv_bfloat162*>(ctx->tc_mhat);
+      if (sp)
+        r.mhat32 = static_cast<const float2*>(ctx->tc_mhat);
+      else
+        r.mhat_bf = reinterpret_cast<const __nv_bfloat162*>(ctx->tc_mhat);
+      r.vhat_lo = static_cast<__nv_bfloat162*>(ctx->tc_vhat_lo);
       r.ld_l = static_cast<long long>(Bs) * Ng;
       r.ld_b = Ng;
       r.Ng = static_cast<int>(Ng);
@@ -487,7 +484,7 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
       r.vld_l = static_cast<long long>(ctx->tc_bsub) * ctx->Ng_pad2;
       r.vld_b = ctx->Ng_pad2;
       r.status = ctx->d_status;
-      CK(launch_tc_retransform(ctx->tc_tmT, r, ctx->num_sms, st));
+      CK(launch_tc_retransform(ctx->tc_tmT, sp ? &ctx->tc_tmT2 : nullptr, r, ctx->num_sms, st));
     }
     {
       StageTimer t(ctx, 3, st);
@@ -729,18 +726,29 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
       if ((e = dalloc(&ctx->tc_p2_lo, 4ull * Nb * ctx->tc_n2 * ctx->Ng_pad2)) != cudaSuccess)
         return bad(e, "tensor stage-2 operand (lo)");
     }
-    // the GEMM retransform serves BF16 activations; the split path keeps the
-    // FFT retransform in FP32
-    if (Nt <= 256 && !sp) {
-      const std::vector<__nv_bfloat16> T = retransform_matrix(Nt, o.dt_mode, o.dt);
-      if ((e = dalloc(&ctx->tc_T, sizeof(__nv_bfloat16) * T.size())) != cudaSuccess)
+    // the retransform GEMM's matrix: BF16 (128-byte swizzle boxes), or hi +
+    // lo BF16 for the split path (64-byte swizzle boxes)
+    if (Nt <= 256) {
+      const std::vector<double> T = retransform_matrix(Nt, o.dt_mode, o.dt);
+      std::vector<__nv_bfloat16> hi(T.size()), lo(T.size());
+      for (size_t q = 0; q < T.size(); ++q) {
+        hi[q] = __float2bfloat16_rn(static_cast<float>(T[q]));
+        lo[q] = __float2bfloat16_rn(static_cast<float>(T[q] - static_cast<double>(__bfloat162float(hi[q]))));
+      }
+      const size_t tb = sizeof(__nv_bfloat16) * T.size();
+      if ((e = dalloc(&ctx->tc_T, tb)) != cudaSuccess) return bad(e, "retransform matrix");
+      if ((e = cudaMemcpy(ctx->tc_T, hi.data(), tb, cudaMemcpyHostToDevice)) != cudaSuccess)
         return bad(e, "retransform matrix");
-      if ((e = cudaMemcpy(ctx->tc_T, T.data(), sizeof(__nv_bfloat16) * T.size(), cudaMemcpyHostToDevice)) !=
-          cudaSuccess)
-        return bad(e, "retransform matrix");
-      const int K = 2 * Nt;
-      if ((e = tc_encode_3d(&ctx->tc_tmT, ctx->tc_T, K, K, 1, K, K > 256 ? 256 : K)) != cudaSuccess)
+      const int K = 2 * Nt, box = K > 256 ? 256 : K, bk = sp ? 32 : 64;
+      if ((e = tc_encode_3d(&ctx->tc_tmT, ctx->tc_T, K, K, 1, K, box, bk)) != cudaSuccess)
         return bad(e, "retransform tensor map");
+      if (sp) {
+        if ((e = dalloc(&ctx->tc_T_lo, tb)) != cudaSuccess) return bad(e, "retransform matrix (lo)");
+        if ((e = cudaMemcpy(ctx->tc_T_lo, lo.data(), tb, cudaMemcpyHostToDevice)) != cudaSuccess)
+          return bad(e, "retransform matrix (lo)");
+        if ((e = tc_encode_3d(&ctx->tc_tmT2, ctx->tc_T_lo, K, K, 1, K, box, bk)) != cudaSuccess)
+          return bad(e, "retransform tensor map (lo)");
+      }
     }
   }
   if ((e = launch_twiddles(ctx->tw, ctx->L, nullptr)) != cudaSuccess) return bad(e, "twiddles");

@@ -267,13 +267,19 @@ cudaError_t launch_pack_a(const float2* src, int Nb, int rows, long long nc, lon
 // pairs); tmT: T[n][k], 2 Nt x 2 Nt BF16, K-major.  32 <= Nt <= 256.
 struct TcRtArgs {
   const __nv_bfloat162* mhat_bf;  // seafloor spectra, BF16 (re, im) pairs
+  const float2* mhat32;           // split: seafloor spectra, FP32 (same indexing)
   long long ld_l, ld_b;
   int Ng, Bs, Nt;
   __nv_bfloat162* vhat;
+  __nv_bfloat162* vhat_lo;        // split: low-order parts of vhat
   long long vld_l, vld_b;
+  int ra, rt;                     // ring depths: A (one slot per fill warp) and T (set by the launcher)
   int* status;
 };
-cudaError_t launch_tc_retransform(const CUtensorMap& tmT, const TcRtArgs& a, int num_sms, cudaStream_t st);
+// tmT2 (split): tensor map of T's low-order part; T maps then use 32-element
+// K boxes (64-byte swizzle), else 64 (128-byte swizzle).
+cudaError_t launch_tc_retransform(const CUtensorMap& tmT, const CUtensorMap* tmT2, const TcRtArgs& a, int num_sms,
+                                  cudaStream_t st);
 
 
 }  // namespace s2w
