@@ -85,10 +85,11 @@ typedef enum { S2W_DT_BACKWARD = 0, S2W_DT_NONE = 1 } s2w_dt_mode;
  * scales and that power of two undone in the epilogue.  With BF16_HILO every
  * operand (both operators, both activations and the retransform matrix) is
  * split into hi + lo BF16 parts and each K step issues three MMAs (hi hi,
- * hi lo, lo hi) into FP32 accumulators (sub-batches of up to 128).  A call that asks for the seafloor field runs on the stream
- * kernels.  AUTO: TENSOR for calls with B >= the batch threshold (2, or what
- * s2w_autotune measured) when prec_g allows it, STREAM otherwise.  The
- * stream engine handles the ruptures of a call in groups of up to 64. */
+ * hi lo, lo hi) into FP32 accumulators (sub-batches of up to 128).  A call
+ * that asks for the seafloor field runs on the stream kernels.  AUTO: TENSOR
+ * for calls with B >= the batch threshold (2, or what s2w_autotune measured,
+ * which may be 1) when prec_g allows it, STREAM otherwise.  The stream engine
+ * handles the ruptures of a call in groups of up to 64. */
 typedef enum { S2W_ENGINE_AUTO = 0, S2W_ENGINE_STREAM = 1, S2W_ENGINE_TENSOR = 2 } s2w_engine;
 
 typedef struct {
@@ -248,7 +249,7 @@ typedef struct {
   int probe_batch;              /* batch size of the cluster probes */
   float ms_stream_per_rupture;  /* stream engine, one rupture */
   float ms_tensor_cluster[3];   /* tensor engine at probe_batch, clusters 1, 2, 4 (0 = not run) */
-  float ms_tensor_batch[6];     /* tensor engine at B = 2, 4, 8, 16, 32, 64 (0 = not run) */
+  float ms_tensor_batch[7];     /* tensor engine at B = 1, 2, 4, 8, 16, 32, 64 (0 = not run) */
 } s2w_tuning;
 
 /* Time the engines on the loaded operators (data-independent timings, dummy

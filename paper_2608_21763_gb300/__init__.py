@@ -54,7 +54,7 @@ class Profile(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("tc_cluster", ctypes.c_int), ("tc_min_batch", ctypes.c_int), ("probe_batch", ctypes.c_int),
                 ("ms_stream_per_rupture", ctypes.c_float), ("ms_tensor_cluster", ctypes.c_float * 3),
-                ("ms_tensor_batch", ctypes.c_float * 6)]
+                ("ms_tensor_batch", ctypes.c_float * 7)]
 
 
 class Opts(ctypes.Structure):

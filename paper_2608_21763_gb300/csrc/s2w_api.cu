@@ -661,8 +661,10 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
   if ((e = dalloc(&ctx->d_amax, sizeof(unsigned))) != cudaSuccess) return bad(e, "operand range word");
   if ((e = dalloc(&ctx->ws_gpart, sizeof(float2) * Nb * ctx->adj_nchunk * ctx->Ns_pad)) != cudaSuccess)
     return bad(e, "adjoint partials");
+  // AUTO keeps the tensor engine ready at any max_batch: single ruptures go
+  // to it only if s2w_autotune measured it faster (tc_min_batch = 1)
   ctx->tc_on = !ctx->single_pass && o.prec_g != S2W_PREC_FP32 && 2 * No <= 256 &&
-               (o.engine == S2W_ENGINE_TENSOR || (o.engine == S2W_ENGINE_AUTO && o.max_batch >= 2));
+               (o.engine == S2W_ENGINE_TENSOR || o.engine == S2W_ENGINE_AUTO);
   ctx->tc_split = ctx->tc_on && o.prec_g == S2W_PREC_BF16_HILO;
   if (ctx->tc_on) {
     // split operands double the B tiles: sub-batches of up to 128 ruptures
@@ -1352,9 +1354,9 @@ int s2w_autotune(s2w_ctx* ctx, int B, s2w_tuning* out, void* stream) {
     ctx->tc_cl1 = ctx->tc_cl2 = best_cl;
     r.tc_cluster = best_cl;
     // smallest batch whose tensor pass beats that many stream passes
-    const int sizes[6] = {2, 4, 8, 16, 32, 64};
+    const int sizes[7] = {1, 2, 4, 8, 16, 32, 64};
     int min_b = 0;
-    for (int k = 0; k < 6 && rc == S2W_OK; ++k) {
+    for (int k = 0; k < 7 && rc == S2W_OK; ++k) {
       if (sizes[k] > B || sizes[k] > ctx->tc_bsub) break;
       rc = timed(sizes[k], S2W_ENGINE_TENSOR, &r.ms_tensor_batch[k]);
       if (rc == S2W_OK && min_b == 0 && r.ms_tensor_batch[k] < sizes[k] * r.ms_stream_per_rupture) min_b = sizes[k];
