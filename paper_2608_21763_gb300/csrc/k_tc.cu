@@ -209,13 +209,19 @@ __host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
 // FP16 A and B (B packed as FP16 with a power-of-two scale from its amax);
 // the per-(bin, 256-row) scale and the B scale are undone in the epilogue.  Each MODE is its own instantiation and kernel, so the plain
 // kernel carries none of the other modes' code.
-template <int BK, int CL, int MODE>
+// MT = 2 (N <= 256, no cluster, not FP8): a unit takes two adjacent M tiles
+// that share every B tile, with one accumulator each (2N TMEM columns): A
+// gets two thirds of each stage instead of half at N = 128, and B is read
+// from L2 once per two tiles.
+template <int BK, int CL, int MODE, int MT = 1>
 __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUtensorMap* tmB, const CUtensorMap* tmA2,
                                              const CUtensorMap* tmB2, const TcArgs& a) {
+  static_assert(MT == 1 || (CL == 1 && MODE != 2), "M-tile pairs: no cluster, no FP8");
   constexpr bool SPLIT = MODE == 1;
   constexpr bool F8 = MODE == 2;
   constexpr int kStg = F8 ? kBlockM * BK : 0;  // FP8 staging bytes per stage
   constexpr int kA = kBlockM * BK * 2;
+  constexpr int a_tile = kA * (SPLIT ? 2 : 1);  // one M tile's A (+ A_lo) bytes per stage
   constexpr uint16_t kMask = static_cast<uint16_t>((1u << CL) - 1u);
   const uint32_t crank = CL > 1 ? cluster_ctarank() : 0u;
   const long long cid = CL > 1 ? static_cast<long long>(cluster_id_x()) : static_cast<long long>(blockIdx.x);
@@ -224,7 +230,7 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUten
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
   const int N = a.N;
   const int b_bytes = N * BK * 2;
-  constexpr int a_all = kA * (SPLIT ? 2 : 1);          // A (+ A_lo) bytes per stage
+  constexpr int a_all = a_tile * MT;                   // A (+ A_lo) bytes per stage, all M tiles
   const int stage_bytes = a_all + b_bytes * (SPLIT ? 2 : 1) + kStg;
   const int S = a.stages;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * stage_bytes);
@@ -236,7 +242,7 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUten
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const int nk_total = (a.K + BK - 1) / BK;
-  const int mtg = (a.m_tiles + CL - 1) / CL;  // M-tile groups (one per cluster unit)
+  const int mtg = (a.m_tiles + CL * MT - 1) / (CL * MT);  // M-tile groups (one per cluster unit / pair)
   const long long units = static_cast<long long>(a.Nb) * mtg * a.n_kchunks;
   const int n_mma = N > 256 ? N / 256 : 1;
   const int n_mma_cols = N > 256 ? 256 : N;
@@ -267,7 +273,7 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUten
   auto unit_coords = [&](long long u, int& l, int& mt, int& kc) {
     kc = static_cast<int>(u % a.n_kchunks);
     const long long r = u / a.n_kchunks;
-    mt = static_cast<int>(r % mtg) * CL + static_cast<int>(crank);
+    mt = static_cast<int>(r % mtg) * CL * MT + static_cast<int>(crank);  // first M tile of the unit
     l = static_cast<int>(r / mtg);
   };
 
@@ -288,11 +294,16 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUten
           }
           unsigned char* sa = smem + s * stage_bytes;
           mbar_arrive_expect_tx(full + s, stage_bytes - (F8 ? kA : 0));  // F8: the A slot is not TMA's
-          if constexpr (F8)
+          if constexpr (F8) {
             tma_load_3d(sa + a_all + b_bytes, tmA, kb * BK, mt * kBlockM, l, full + s);
-          else
-            tma_load_3d(sa, tmA, kb * BK, mt * kBlockM, l, full + s);
-          if constexpr (SPLIT) tma_load_3d(sa + kA, tmA2, kb * BK, mt * kBlockM, l, full + s);
+          } else {
+            // rows past the last M tile read as zeros (TMA fill); their outputs are never stored
+#pragma unroll
+            for (int j = 0; j < MT; ++j) {
+              tma_load_3d(sa + j * a_tile, tmA, kb * BK, (mt + j) * kBlockM, l, full + s);
+              if constexpr (SPLIT) tma_load_3d(sa + j * a_tile + kA, tmA2, kb * BK, (mt + j) * kBlockM, l, full + s);
+            }
+          }
           auto load_b = [&](const CUtensorMap* tb, unsigned char* sb) {
             if (CL == 1) {
               for (int c = 0; c < n_mma; ++c)
@@ -338,14 +349,19 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUten
           const uint32_t sb = sa + a_all;
 #pragma unroll
           for (int k = 0; k < BK / 16; ++k) {
-            const uint64_t ad = sdesc_sw<BK>(sa + k * 32);
-            for (int c = 0; c < n_mma; ++c) {
-              const uint32_t boff = c * n_mma_cols * BK * 2 + k * 32;
-              const uint64_t bd = sdesc_sw<BK>(sb + boff);
-              tc_mma_bf16(tmem + c * n_mma_cols, ad, bd, idesc, (kb > kb0 || k > 0) ? 1u : 0u);
-              if constexpr (SPLIT) {
-                tc_mma_bf16(tmem + c * n_mma_cols, ad, sdesc_sw<BK>(sb + b_bytes + boff), idesc, 1u);
-                tc_mma_bf16(tmem + c * n_mma_cols, sdesc_sw<BK>(sa + kA + k * 32), bd, idesc, 1u);
+#pragma unroll
+            for (int j = 0; j < MT; ++j) {  // accumulator j at TMEM columns j N ..
+              const uint32_t aoff = j * a_tile + k * 32;
+              const uint64_t ad = sdesc_sw<BK>(sa + aoff);
+              for (int c = 0; c < n_mma; ++c) {
+                const uint32_t boff = c * n_mma_cols * BK * 2 + k * 32;
+                const uint64_t bd = sdesc_sw<BK>(sb + boff);
+                const uint32_t dcol = tmem + j * N + c * n_mma_cols;
+                tc_mma_bf16(dcol, ad, bd, idesc, (kb > kb0 || k > 0) ? 1u : 0u);
+                if constexpr (SPLIT) {
+                  tc_mma_bf16(dcol, ad, sdesc_sw<BK>(sb + b_bytes + boff), idesc, 1u);
+                  tc_mma_bf16(dcol, sdesc_sw<BK>(sa + aoff + kA), bd, idesc, 1u);
+                }
               }
             }
           }
@@ -418,9 +434,11 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUten
       unit_coords(u, l, mt, kc);
       if (!mbar_wait_bounded(acc_full, acc_it & 1, a.status, DEV_ERR_TIMEOUT_MMA)) break;
       tc_fence_after();
-      const int row = mt * kBlockM + q * 32 + lane;
-      const uint32_t tbase = tmem + (static_cast<uint32_t>(q * 32) << 16);
-      const bool live = row < a.M_total && mt < a.m_tiles;
+#pragma unroll 1
+      for (int j = 0; j < MT; ++j) {
+      const int row = (mt + j) * kBlockM + q * 32 + lane;
+      const uint32_t tbase = tmem + j * N + (static_cast<uint32_t>(q * 32) << 16);
+      const bool live = row < a.M_total && mt + j < a.m_tiles;
       float scale = 1.f;
       if (a.row_scale != nullptr && live) scale = a.row_scale[static_cast<long long>(l) * a.nblk + row / 256];
       if (a.b_amax != nullptr) scale *= f16_unscale(*a.b_amax);  // undo the FP16 B operand's power-of-two scale
@@ -451,6 +469,7 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUten
         tmem_ld16(tbase + c0, v);
         emit(c0, v, 16);
       }
+      }  // M tiles of the unit
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(acc_empty);
@@ -470,6 +489,20 @@ template <int BK, int CL>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
   tc_gemm_body<BK, CL, 0>(&tmA, &tmB, nullptr, nullptr, a);
+}
+
+template <int BK>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_tc_gemm_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
+  tc_gemm_body<BK, 1, 0, 2>(&tmA, &tmB, nullptr, nullptr, a);
+}
+
+template <int BK>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_tc_gemm_split_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                         const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB2,
+                         const TcArgs a) {
+  tc_gemm_body<BK, 1, 1, 2>(&tmA, &tmB, &tmA2, &tmB2, a);
 }
 
 template <int BK, int CL>
@@ -938,20 +971,20 @@ cudaError_t tc_encode_3d_u8(CUtensorMap* out, const void* base, long long K, lon
 int tc_block_k(int N, int split) { return (N > 256 || (split && N > 128)) ? 32 : 64; }
 
 namespace {
-int tc_stage_bytes(int N, int a_lo, int b_lo, int fp8) {
+int tc_stage_bytes(int N, int a_lo, int b_lo, int fp8, int mt) {
   const int bk = tc_block_k(N, a_lo | b_lo);
-  return kBlockM * bk * 2 * (1 + a_lo) + N * bk * 2 * (1 + b_lo) + (fp8 ? kBlockM * bk : 0);
+  return kBlockM * bk * 2 * (1 + a_lo) * mt + N * bk * 2 * (1 + b_lo) + (fp8 ? kBlockM * bk : 0);
 }
 }  // namespace
 
-int tc_stages_for(int N, int a_lo, int b_lo, int fp8) {
-  int s = kSmemBudget / tc_stage_bytes(N, a_lo, b_lo, fp8);
+int tc_stages_for(int N, int a_lo, int b_lo, int fp8, int mt) {
+  int s = kSmemBudget / tc_stage_bytes(N, a_lo, b_lo, fp8, mt);
   if (s > 8) s = 8;
   return s;
 }
 
-size_t tc_smem_bytes(int N, int stages, int a_lo, int b_lo, int fp8) {
-  return 1024 + static_cast<size_t>(stages) * tc_stage_bytes(N, a_lo, b_lo, fp8) + 8 * (3 * stages + 2) + 16;
+size_t tc_smem_bytes(int N, int stages, int a_lo, int b_lo, int fp8, int mt) {
+  return 1024 + static_cast<size_t>(stages) * tc_stage_bytes(N, a_lo, b_lo, fp8, mt) + 8 * (3 * stages + 2) + 16;
 }
 
 template <int BK, int CL, int MODE>
@@ -1014,8 +1047,33 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
   const int CL = a.cluster < 1 ? 1 : a.cluster;
   if (CL != 1 && CL != 2 && CL != 4) return cudaErrorInvalidValue;
   if (CL > 1 && (a.N / CL < 8 || (a.N / CL) % 8 != 0 || a.N / CL > 256)) return cudaErrorInvalidValue;
-  const size_t smem = tc_smem_bytes(a.N, a.stages, a.a_lo, a.b_lo, a.a_fp8);
+  const int mt = a.m_pair ? 2 : 1;
+  if (a.m_pair && (a.N > 256 || CL != 1 || a.a_fp8)) return cudaErrorInvalidValue;
+  const size_t smem = tc_smem_bytes(a.N, a.stages, a.a_lo, a.b_lo, a.a_fp8, mt);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  if (a.m_pair) {  // pairs of M tiles per unit, no cluster
+    const long long pu = static_cast<long long>(a.Nb) * ((a.m_tiles + 1) / 2) * a.n_kchunks;
+    const unsigned grid = static_cast<unsigned>(pu < num_sms ? pu : num_sms);
+    const bool bk64 = tc_block_k(a.N, a.a_lo) == 64;
+    const void* kfn = a.a_lo ? (bk64 ? reinterpret_cast<const void*>(k_tc_gemm_split_pair<64>)
+                                     : reinterpret_cast<const void*>(k_tc_gemm_split_pair<32>))
+                             : (bk64 ? reinterpret_cast<const void*>(k_tc_gemm_pair<64>)
+                                     : reinterpret_cast<const void*>(k_tc_gemm_pair<32>));
+    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    if (a.a_lo) {
+      if (bk64)
+        k_tc_gemm_split_pair<64><<<grid, kTcThreads, smem, st>>>(tmA, tmB, *tmA2, *tmB2, a);
+      else
+        k_tc_gemm_split_pair<32><<<grid, kTcThreads, smem, st>>>(tmA, tmB, *tmA2, *tmB2, a);
+    } else {
+      if (bk64)
+        k_tc_gemm_pair<64><<<grid, kTcThreads, smem, st>>>(tmA, tmB, a);
+      else
+        k_tc_gemm_pair<32><<<grid, kTcThreads, smem, st>>>(tmA, tmB, a);
+    }
+    return cudaGetLastError();
+  }
   const CUtensorMap& a2 = a.a_lo ? *tmA2 : tmA;  // unused unless a_lo / b_lo
   const CUtensorMap& b2 = a.b_lo ? *tmB2 : tmB;
   auto go = [&](auto bk_tag, auto mode_tag) -> cudaError_t {

@@ -185,6 +185,17 @@ int fit_cluster(int want, int N, int m_tiles) {
   return cl;  // 1: a single CTA loads any N <= 512 itself
 }
 
+// Two M tiles per unit sharing each B tile, when the accumulators fit (N <=
+// 256), without a cluster, for non-FP8 A and at least two M tiles; sets the
+// ring depth and TMEM columns of `a` for the chosen form.
+void tc_shape(TcArgs& a, int N, int m_tiles, int cl, int split, int fp8) {
+  a.m_pair = (N <= 256 && cl == 1 && !fp8 && m_tiles >= 2) ? 1 : 0;
+  const int mt = a.m_pair ? 2 : 1;
+  a.stages = tc_stages_for(N, split, split, fp8, mt);
+  const int cols = mt * N;
+  a.tmem_cols = cols <= 32 ? 32 : (cols <= 64 ? 64 : (cols <= 128 ? 128 : (cols <= 256 ? 256 : 512)));
+}
+
 // The stream engine handles ruptures in groups of at most this many (its
 // per-call workspaces are sized for one group).
 constexpr int kStreamGroup = 64;
@@ -326,10 +337,9 @@ int tc_gemm_epi0(s2w_ctx* ctx, const void* A, const void* A_lo, long long M, lon
   a.m_tiles = mt;
   a.n_kchunks = 1;
   a.kblocks_per_chunk = static_cast<int>((K + bk - 1) / bk);
-  a.stages = tc_stages_for(N, sp, sp);
+  tc_shape(a, N, mt, cl, sp, 0);
   a.a_lo = sp;
   a.b_lo = sp;
-  a.tmem_cols = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : (N <= 256 ? 256 : 512)));
   a.cluster = cl;
   a.epi = 0;
   a.T = T;
@@ -445,7 +455,7 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
       a.m_tiles = static_cast<int>((Ng + 127) / 128);
       a.n_kchunks = 1;
       a.kblocks_per_chunk = (K1 + bk - 1) / bk;
-      a.stages = tc_stages_for(N1, sp, sp, f8 ? 1 : 0);
+      tc_shape(a, N1, m1, cl, sp, f8 ? 1 : 0);
       a.a_lo = sp;
       a.b_lo = sp;
       a.a_fp8 = f8 ? 1 : 0;
@@ -454,7 +464,6 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
         a.nblk = ctx->nblk;
         a.b_amax = ctx->d_amax;
       }
-      a.tmem_cols = N1 <= 32 ? 32 : (N1 <= 64 ? 64 : (N1 <= 128 ? 128 : (N1 <= 256 ? 256 : 512)));
       a.cluster = cl;
       a.epi = 0;
       a.T = Bs;
@@ -506,10 +515,9 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
       a.m_tiles = (Bs + 127) / 128;
       a.n_kchunks = ctx->tc_nkc;
       a.kblocks_per_chunk = ctx->tc_kbpc;
-      a.stages = tc_stages_for(ctx->tc_n2, sp, sp);
+      tc_shape(a, ctx->tc_n2, m2, cl, sp, 0);
       a.a_lo = sp;
       a.b_lo = sp;
-      a.tmem_cols = ctx->tc_n2 <= 32 ? 32 : (ctx->tc_n2 <= 64 ? 64 : (ctx->tc_n2 <= 128 ? 128 : 256));
       a.cluster = cl;
       a.epi = 1;
       a.T = static_cast<int>(No);

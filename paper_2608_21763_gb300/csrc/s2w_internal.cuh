@@ -224,6 +224,8 @@ struct TcArgs {
   int a_fp8;               // 1: A is FP8 e4m3 (byte tensor map, row-major), widened to FP16 in shared memory;
                            //    needs row_scale; B is FP16 (launch_pack_b_f16) with its amax in b_amax
   const unsigned* b_amax;  // FP16 B operand: amax (float bits) that set its power-of-two scale
+  int m_pair;              // 1: two M tiles per unit sharing each B tile (N <= 256, cluster 1, not FP8;
+                           //    tmem_cols >= 2 N, stages from tc_stages_for(..., mt = 2))
   int* status;
 };
 // bk = 64: 128-byte swizzle, K boxes of 64 BF16; bk = 32: 64-byte swizzle.
@@ -232,7 +234,7 @@ cudaError_t tc_encode_3d(CUtensorMap* out, const void* base, long long K, long l
 // K block (BF16 elements per swizzle row) and ring depth for N MMA columns
 // with `terms` = 1 + a_lo + b_lo operand tiles beyond the first A and B
 int tc_block_k(int N, int split = 0);
-int tc_stages_for(int N, int a_lo = 0, int b_lo = 0, int fp8 = 0);
+int tc_stages_for(int N, int a_lo = 0, int b_lo = 0, int fp8 = 0, int mt = 1);
 // Byte tensor map for FP8 A tiles: [nbatch][rows][K] bytes, box bk x box_rows, no swizzle.
 cudaError_t tc_encode_3d_u8(CUtensorMap* out, const void* base, long long K, long long rows, long long nbatch,
                             int box_rows, int bk);
