@@ -250,11 +250,14 @@ typedef struct {
   float ms_stream_per_rupture;  /* stream engine, one rupture */
   float ms_tensor_cluster[3];   /* tensor engine at probe_batch, clusters 1, 2, 4 (0 = not run) */
   float ms_tensor_batch[7];     /* tensor engine at B = 1, 2, 4, 8, 16, 32, 64 (0 = not run) */
+  int tc_bsub;                  /* chosen tensor sub-batch size (rupture columns per GEMM pass) */
+  float ms_tensor_half;         /* tensor engine at probe_batch in sub-batches of 128 (0 = not run) */
 } s2w_tuning;
 
 /* Time the engines on the loaded operators (data-independent timings, dummy
- * inputs) and set the context's tensor-engine cluster size and the batch
- * size above which AUTO uses the tensor engine.  Uses up to B ruptures
+ * inputs) and set the context's tensor-engine cluster size, sub-batch size
+ * (256 or 128 ruptures per GEMM pass) and the batch size from which AUTO
+ * uses the tensor engine.  Uses up to B ruptures
  * (<= max_batch).  Without the tensor engine only ms_stream_per_rupture is
  * measured.  `out` may be NULL. */
 int s2w_autotune(s2w_ctx *ctx, int B, s2w_tuning *out, void *stream);

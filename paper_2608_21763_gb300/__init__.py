@@ -54,7 +54,8 @@ class Profile(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("tc_cluster", ctypes.c_int), ("tc_min_batch", ctypes.c_int), ("probe_batch", ctypes.c_int),
                 ("ms_stream_per_rupture", ctypes.c_float), ("ms_tensor_cluster", ctypes.c_float * 3),
-                ("ms_tensor_batch", ctypes.c_float * 7)]
+                ("ms_tensor_batch", ctypes.c_float * 7), ("tc_bsub", ctypes.c_int),
+                ("ms_tensor_half", ctypes.c_float)]
 
 
 class Opts(ctypes.Structure):
@@ -297,7 +298,8 @@ class Context:
         self._check(lib().s2w_autotune(self._h, int(B), ctypes.byref(t), _stream(st)))
         return {"tc_cluster": t.tc_cluster, "tc_min_batch": t.tc_min_batch, "probe_batch": t.probe_batch,
                 "ms_stream_per_rupture": t.ms_stream_per_rupture,
-                "ms_tensor_cluster": list(t.ms_tensor_cluster), "ms_tensor_batch": list(t.ms_tensor_batch)}
+                "ms_tensor_cluster": list(t.ms_tensor_cluster), "ms_tensor_batch": list(t.ms_tensor_batch),
+                "tc_bsub": t.tc_bsub, "ms_tensor_half": t.ms_tensor_half}
 
     def misfit_gradient(self, slip, d, grad=None, loss=None, stream=None):
         """Gradient of 0.5 ||q(slip[b]) - d[b]||^2 per rupture; returns

@@ -1361,6 +1361,23 @@ int s2w_autotune(s2w_ctx* ctx, int B, s2w_tuning* out, void* stream) {
     }
     ctx->tc_cl1 = ctx->tc_cl2 = best_cl;
     r.tc_cluster = best_cl;
+    // sub-batch size: 256 ruptures (N = 512, one M tile per unit) or 128
+    // (N = 256, M-tile pairs; the spectra are streamed twice as often)
+    r.tc_bsub = ctx->tc_bsub;
+    if (rc == S2W_OK && ctx->tc_bsub > 128 && r.probe_batch > 128) {
+      const int full = ctx->tc_bsub;
+      ctx->tc_bsub = 128;
+      ctx->tc_cl1 = ctx->tc_cl2 = 1;  // the M-tile pairs need single CTAs
+      rc = timed(r.probe_batch, S2W_ENGINE_TENSOR, &r.ms_tensor_half);
+      if (rc == S2W_OK && r.ms_tensor_half < best) {
+        best = r.ms_tensor_half;
+        r.tc_cluster = 1;
+      } else {
+        ctx->tc_bsub = full;
+        ctx->tc_cl1 = ctx->tc_cl2 = best_cl;
+      }
+      r.tc_bsub = ctx->tc_bsub;
+    }
     // smallest batch whose tensor pass beats that many stream passes
     const int sizes[7] = {1, 2, 4, 8, 16, 32, 64};
     int min_b = 0;
