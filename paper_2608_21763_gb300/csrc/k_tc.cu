@@ -772,10 +772,14 @@ __global__ void __launch_bounds__(kRtThreads, 1)
       const uint32_t tbase = tmem + (static_cast<uint32_t>(q * 32) << 16);
       __nv_bfloat162* out = a.vhat + static_cast<long long>(b) * a.vld_b + i;
       __nv_bfloat162* out_lo = SPLIT ? a.vhat_lo + static_cast<long long>(b) * a.vld_b + i : nullptr;
-      auto put = [&](long long off, float re, float im) {
+      auto put1 = [&](long long off, float re, float im) {
         const __nv_bfloat162 hi = __floats2bfloat162_rn(re, im);
         out[off] = hi;
         if constexpr (SPLIT) out_lo[off] = __floats2bfloat162_rn(re - __low2float(hi), im - __high2float(hi));
+      };
+      auto put = [&](long long off, float re, float im) {
+        put1(off, re, im);
+        if (a.conj_row > 0) put1(off + a.conj_row, im, -re);  // row 2b + 1 of the conjugate embedding
       };
       // K = 2 Nt is a multiple of 64 for every supported Nt (32..256)
       for (int c0 = 0; c0 < K; c0 += 64) {

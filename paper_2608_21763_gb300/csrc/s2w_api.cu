@@ -104,6 +104,9 @@ struct s2w_ctx {
   void* tc_T = nullptr;     // [2 Nt][2 Nt] bf16: retransform as a real-linear map
   void* tc_T_lo = nullptr;  // split: its low-order part
   CUtensorMap tc_tmT, tc_tmT2;
+  void* tc_Ta = nullptr;    // tc_adjoint: the same map with D_t^T (adjoint retransform), + lo when split
+  void* tc_Ta_lo = nullptr;
+  CUtensorMap tc_tmTa, tc_tmTa2;
   std::vector<unsigned char> g_loaded, p_loaded;
   long long g_count = 0, p_count = 0;
   // per-stage event timers
@@ -260,7 +263,7 @@ void free_all(s2w_ctx* c) {
                 c->ws_vhat, c->ws_part, c->ws_q, c->ws_seafloor, c->d_status, c->tc_bp1, c->ws_rhat, c->ws_gpart, c->ws_resid, c->ws_d, c->ws_loss,
                 c->tc_mhat, c->tc_vhat, c->tc_part, c->tc_p2, c->tc_T, c->tc_bp1_lo, c->tc_vhat_lo, c->tc_p2_lo,
                 c->tc_gT, c->tc_gT_lo, c->tc_pT, c->tc_pT_lo, c->tc_rb, c->tc_rb_lo, c->tc_ub, c->tc_ub_lo,
-                c->tc_ghat, c->ws_lens, c->d_amax, c->tc_T_lo};
+                c->tc_ghat, c->ws_lens, c->d_amax, c->tc_T_lo, c->tc_Ta, c->tc_Ta_lo};
   for (void* p : ps)
     if (p) cudaFree(p);
 }
@@ -270,9 +273,10 @@ void free_all(s2w_ctx* c) {
 // k = 0: Re bin 0, k = 1: Re bin Nt, k = 2l / 2l+1: Re / Im bin l (0 < l < Nt),
 // the same ordering for the outputs n.  Column k is the map applied to basis
 // spectrum k, evaluated in FP64 from the definitions (inverse DFT head,
-// backward difference, zero-padded DFT); the caller rounds it to BF16 (hi,
-// and lo = the rounded remainder for the split path).
-std::vector<double> retransform_matrix(int Nt, int dt_mode, double dt) {
+// backward difference, or its transpose for the adjoint, zero-padded DFT);
+// the caller rounds it to BF16 (hi, and lo = the rounded remainder for the
+// split path).
+std::vector<double> retransform_matrix(int Nt, int dt_mode, double dt, bool transpose = false) {
   const int L = 2 * Nt, K = 2 * Nt;
   std::vector<double> c(L), sn(L);
   for (int m = 0; m < L; ++m) {
@@ -288,7 +292,14 @@ std::vector<double> retransform_matrix(int Nt, int dt_mode, double dt) {
       else if (k % 2 == 0) x[n] = 2.0 / L * c[(static_cast<long long>(k / 2) * n) % L];
       else x[n] = -2.0 / L * sn[(static_cast<long long>(k / 2) * n) % L];
     }
-    for (int n = 0; n < Nt; ++n) v[n] = dt_mode == S2W_DT_NONE ? x[n] : (x[n] - (n > 0 ? x[n - 1] : 0.0)) / dt;
+    for (int n = 0; n < Nt; ++n) {
+      if (dt_mode == S2W_DT_NONE)
+        v[n] = x[n];
+      else if (transpose)  // D_t^T: (w[n] - w[n+1]) / dt, w[Nt] = 0
+        v[n] = (x[n] - (n + 1 < Nt ? x[n + 1] : 0.0)) / dt;
+      else
+        v[n] = (x[n] - (n > 0 ? x[n - 1] : 0.0)) / dt;
+    }
     for (int l = 0; l <= Nt; ++l) {
       double re = 0.0, im = 0.0;
       for (int n = 0; n < Nt; ++n) {
@@ -316,7 +327,7 @@ std::vector<double> retransform_matrix(int Nt, int dt_mode, double dt) {
 // and the B operand rows [Nb][n_alloc][K] (BF16; lo parts when split).
 int tc_gemm_epi0(s2w_ctx* ctx, const void* A, const void* A_lo, long long M, long long K, const void* Bop,
                  const void* B_lo, int n_alloc, int N, int T, float2* out, long long ld_l, long long ld_t, int cl_want,
-                 cudaStream_t st) {
+                 cudaStream_t st, __nv_bfloat162* out_bf = nullptr) {
   const int sp = A_lo != nullptr ? 1 : 0;
   CUtensorMap ta, tb, ta2, tb2;
   const int bk = tc_block_k(N, sp);
@@ -343,7 +354,8 @@ int tc_gemm_epi0(s2w_ctx* ctx, const void* A, const void* A_lo, long long M, lon
   a.cluster = cl;
   a.epi = 0;
   a.T = T;
-  a.out = out;
+  a.out = out_bf ? nullptr : out;
+  a.out_bf = out_bf;
   a.ld_l = ld_l;
   a.ld_t = ld_t;
   a.status = ctx->d_status;
@@ -375,14 +387,37 @@ int adjoint_tensor(s2w_ctx* ctx, const float* r_d, int B, float* g_d, cudaStream
                        ctx->tc_n1max, 1, ctx->tc_rb, ctx->tc_rb_lo, st));
     }
     float2* what = static_cast<float2*>(ctx->tc_mhat);
+    // the GEMM retransform (D_t^T matrix) rounds what to BF16 anyway; the
+    // split path keeps it in FP32 and splits it itself
+    const bool gemm_rt = ctx->tc_Ta != nullptr;
     {
       StageTimer t(ctx, 3, st);
       int rc = tc_gemm_epi0(ctx, ctx->tc_pT, sp ? ctx->tc_pT_lo : nullptr, Ng, 2LL * ctx->NoP, ctx->tc_rb,
                             sp ? ctx->tc_rb_lo : nullptr, ctx->tc_n1max, N1, Bs, what,
-                            static_cast<long long>(Bs) * Ng, Ng, ctx->tc_cl1, st);
+                            static_cast<long long>(Bs) * Ng, Ng, ctx->tc_cl1, st,
+                            gemm_rt && !sp ? reinterpret_cast<__nv_bfloat162*>(what) : nullptr);
       if (rc != S2W_OK) return rc;
     }
-    {
+    if (gemm_rt) {  // uhat as the conjugate-embedding B operand: rows 2b, 2b+1 of [l][n1max][Ng_pad2]
+      StageTimer t(ctx, 2, st);
+      TcRtArgs r{};
+      if (sp)
+        r.mhat32 = what;
+      else
+        r.mhat_bf = reinterpret_cast<const __nv_bfloat162*>(what);
+      r.ld_l = static_cast<long long>(Bs) * Ng;
+      r.ld_b = Ng;
+      r.Ng = static_cast<int>(Ng);
+      r.Bs = Bs;
+      r.Nt = static_cast<int>(Nt);
+      r.vhat = static_cast<__nv_bfloat162*>(ctx->tc_ub);
+      r.vhat_lo = static_cast<__nv_bfloat162*>(ctx->tc_ub_lo);
+      r.vld_l = static_cast<long long>(ctx->tc_n1max) * ctx->Ng_pad2;
+      r.vld_b = 2 * ctx->Ng_pad2;
+      r.conj_row = ctx->Ng_pad2;
+      r.status = ctx->d_status;
+      CK(launch_tc_retransform(ctx->tc_tmTa, sp ? &ctx->tc_tmTa2 : nullptr, r, ctx->num_sms, st));
+    } else {
       StageTimer t(ctx, 2, st);
       CK(launch_retransform(what, Ng, static_cast<long long>(Bs) * Ng, static_cast<int>(Nt), ctx->tw,
                             static_cast<float>(1.0 / ctx->opts.dt), dt_t, nullptr, ctx->Ng_pad2, nullptr, st, Bs, Ng, 0,
@@ -739,26 +774,30 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
     // the retransform GEMM's matrix: BF16 (128-byte swizzle boxes), or hi +
     // lo BF16 for the split path (64-byte swizzle boxes)
     if (Nt <= 256) {
-      const std::vector<double> T = retransform_matrix(Nt, o.dt_mode, o.dt);
-      std::vector<__nv_bfloat16> hi(T.size()), lo(T.size());
-      for (size_t q = 0; q < T.size(); ++q) {
-        hi[q] = __float2bfloat16_rn(static_cast<float>(T[q]));
-        lo[q] = __float2bfloat16_rn(static_cast<float>(T[q] - static_cast<double>(__bfloat162float(hi[q]))));
-      }
-      const size_t tb = sizeof(__nv_bfloat16) * T.size();
-      if ((e = dalloc(&ctx->tc_T, tb)) != cudaSuccess) return bad(e, "retransform matrix");
-      if ((e = cudaMemcpy(ctx->tc_T, hi.data(), tb, cudaMemcpyHostToDevice)) != cudaSuccess)
+      auto upload = [&](bool transpose, void** hi_d, void** lo_d, CUtensorMap* tm, CUtensorMap* tm2) -> cudaError_t {
+        const std::vector<double> T = retransform_matrix(Nt, o.dt_mode, o.dt, transpose);
+        std::vector<__nv_bfloat16> hi(T.size()), lo(T.size());
+        for (size_t q = 0; q < T.size(); ++q) {
+          hi[q] = __float2bfloat16_rn(static_cast<float>(T[q]));
+          lo[q] = __float2bfloat16_rn(static_cast<float>(T[q] - static_cast<double>(__bfloat162float(hi[q]))));
+        }
+        const size_t tb = sizeof(__nv_bfloat16) * T.size();
+        const int K = 2 * Nt, box = K > 256 ? 256 : K, bk = sp ? 32 : 64;
+        cudaError_t r;
+        if ((r = dalloc(hi_d, tb)) != cudaSuccess) return r;
+        if ((r = cudaMemcpy(*hi_d, hi.data(), tb, cudaMemcpyHostToDevice)) != cudaSuccess) return r;
+        if ((r = tc_encode_3d(tm, *hi_d, K, K, 1, K, box, bk)) != cudaSuccess) return r;
+        if (sp) {
+          if ((r = dalloc(lo_d, tb)) != cudaSuccess) return r;
+          if ((r = cudaMemcpy(*lo_d, lo.data(), tb, cudaMemcpyHostToDevice)) != cudaSuccess) return r;
+          if ((r = tc_encode_3d(tm2, *lo_d, K, K, 1, K, box, bk)) != cudaSuccess) return r;
+        }
+        return cudaSuccess;
+      };
+      if ((e = upload(false, &ctx->tc_T, &ctx->tc_T_lo, &ctx->tc_tmT, &ctx->tc_tmT2)) != cudaSuccess)
         return bad(e, "retransform matrix");
-      const int K = 2 * Nt, box = K > 256 ? 256 : K, bk = sp ? 32 : 64;
-      if ((e = tc_encode_3d(&ctx->tc_tmT, ctx->tc_T, K, K, 1, K, box, bk)) != cudaSuccess)
-        return bad(e, "retransform tensor map");
-      if (sp) {
-        if ((e = dalloc(&ctx->tc_T_lo, tb)) != cudaSuccess) return bad(e, "retransform matrix (lo)");
-        if ((e = cudaMemcpy(ctx->tc_T_lo, lo.data(), tb, cudaMemcpyHostToDevice)) != cudaSuccess)
-          return bad(e, "retransform matrix (lo)");
-        if ((e = tc_encode_3d(&ctx->tc_tmT2, ctx->tc_T_lo, K, K, 1, K, box, bk)) != cudaSuccess)
-          return bad(e, "retransform tensor map (lo)");
-      }
+      if (ctx->tc_adj && (e = upload(true, &ctx->tc_Ta, &ctx->tc_Ta_lo, &ctx->tc_tmTa, &ctx->tc_tmTa2)) != cudaSuccess)
+        return bad(e, "adjoint retransform matrix");
     }
   }
   if ((e = launch_twiddles(ctx->tw, ctx->L, nullptr)) != cudaSuccess) return bad(e, "twiddles");

@@ -275,6 +275,8 @@ struct TcRtArgs {
   __nv_bfloat162* vhat;
   __nv_bfloat162* vhat_lo;        // split: low-order parts of vhat
   long long vld_l, vld_b;
+  long long conj_row;             // > 0: write the conjugate-embedding B operand: (Re, Im) at the
+                                  // output position and (Im, -Re) conj_row entries further
   int ra, rt;                     // ring depths: A (one slot per fill warp) and T (set by the launcher)
   int* status;
 };
