@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--engine", default="auto", choices=["auto", "stream", "tensor"])
     ap.add_argument("--tc-cluster", type=int, default=0, choices=[0, 1, 2, 4],
                     help="tensor engine: CTAs per cluster sharing B tiles (0 = library choice)")
+    ap.add_argument("--tc-pair", default="auto", choices=["auto", "on", "off"],
+                    help="tensor engine: two-SM MMAs (a CTA pair per 256-row tile)")
     ap.add_argument("--mode", default="waveforms", choices=["waveforms", "gradient"],
                     help="gradient: one step = misfit gradients of the batch (forward + adjoint)")
     ap.add_argument("--batch", type=int, default=None, help="ruptures per step (default: the workload's)")
@@ -134,10 +136,10 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ setup
 def load_context(s2w, wl, geom, prec_g, prec_p, B, device, engine="auto", chunk=1024, tc_cluster=0,
-                 tc_adjoint=False, single_pass=False):
+                 tc_adjoint=False, single_pass=False, tc_pair="auto"):
     ctx = s2w.Context(wl.Ns, wl.Ng, wl.No, wl.Nt, prec_g=prec_g, prec_p=prec_p,
                       max_batch=B, device=device, engine=engine, tc_cluster=tc_cluster, tc_adjoint=tc_adjoint,
-                      single_pass=single_pass)
+                      single_pass=single_pass, tc_pair=tc_pair)
     for g0 in range(0, wl.Ng, chunk):
         g1 = min(wl.Ng, g0 + chunk)
         ctx.load_greens(g0, geom.greens_rows(g0, g1, wl.Nt, np.float32))
@@ -272,7 +274,8 @@ def run_ours(args, rank, world, local_rank):
     # so the adjoint runs on the tensor engine as well
     tc_adj = args.mode == "gradient" and args.prec_g in ("bf16", "bf16_hilo") and args.engine != "stream"
     ctx = load_context(s2w, wl, geom, args.prec_g, args.prec_p, B, local_rank, args.engine,
-                       tc_cluster=args.tc_cluster, tc_adjoint=tc_adj, single_pass=args.single_pass)
+                       tc_cluster=args.tc_cluster, tc_adjoint=tc_adj, single_pass=args.single_pass,
+                       tc_pair=args.tc_pair)
     setup_s = time.perf_counter() - t_setup
     slip_d = torch.tensor(slip_np, device=dev)
     q_d = torch.empty((pool, B, wl.No, wl.Nt), dtype=torch.float32, device=dev)
@@ -437,6 +440,7 @@ def run_ours(args, rank, world, local_rank):
                       "ruptures_per_step": B, "prec_g": args.prec_g, "prec_p": args.prec_p,
                       "engine": "tensor" if tensor else "stream", "mode": args.mode,
                       "tc_cluster": tuning["tc_cluster"] if tuning else args.tc_cluster,
+                      "tc_pair": args.tc_pair,
                       "autotune": tuning, "cuda_graph": use_graph, "single_pass": bool(args.single_pass),
                       "l2": "inputs larger than L2 (every step streams the full operator spectra)",
                       "parallelism": f"replicas{world}",

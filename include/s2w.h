@@ -121,7 +121,17 @@ typedef struct {
                       seafloor output, adjoint or no-alloc path.  The
                       spectral loaders then take 2 Nt + 1 bins of length-4 Nt
                       DFTs.  0 (default): L = 2 Nt with the retransform. */
+  int tc_pair;     /* tensor engine: S2W_PAIR_ON runs each GEMM whose shape
+                      allows it (cluster 1, BF16 or hi/lo operands, N a
+                      multiple of 32, at least two 128-row M tiles) as
+                      two-SM MMAs: a pair of CTAs computes one 256-row tile
+                      with each CTA staging half of the B tile.  S2W_PAIR_OFF
+                      keeps one CTA per 128-row tile; S2W_PAIR_AUTO (0,
+                      default) takes the two-SM form for the 512-column
+                      GEMMs of BF16 operands (256-rupture sub-batches). */
 } s2w_opts;
+
+enum { S2W_PAIR_AUTO = 0, S2W_PAIR_ON = 1, S2W_PAIR_OFF = 2 };
 
 /* Fill *o with the defaults listed above (max_batch = 1). */
 void s2w_default_opts(s2w_opts *o);

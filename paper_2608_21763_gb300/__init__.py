@@ -24,6 +24,7 @@ _lib = None
 PREC = {"fp32": 0, "bf16": 1, "bf16_hilo": 2, "fp8": 3}
 ENGINE = {"auto": 0, "stream": 1, "tensor": 2}
 DT_MODE = {"backward": 0, "none": 1}
+PAIR = {"auto": 0, "on": 1, "off": 2}
 STATUS = {0: "S2W_OK", -1: "S2W_ERR_ARG", -2: "S2W_ERR_OOM", -3: "S2W_ERR_STATE",
           -4: "S2W_ERR_CUDA", -5: "S2W_ERR_TIMEOUT", -6: "S2W_ERR_UNSUPPORTED"}
 
@@ -63,7 +64,7 @@ class Opts(ctypes.Structure):
                 ("dt_mode", ctypes.c_int), ("dt", ctypes.c_double),
                 ("max_batch", ctypes.c_int), ("device", ctypes.c_int),
                 ("engine", ctypes.c_int), ("tc_cluster", ctypes.c_int), ("tc_adjoint", ctypes.c_int),
-                ("single_pass", ctypes.c_int)]
+                ("single_pass", ctypes.c_int), ("tc_pair", ctypes.c_int)]
 
 
 def lib_path() -> str:
@@ -161,7 +162,7 @@ class Context:
 
     def __init__(self, Ns, Ng, No, Nt, prec_g="fp32", prec_p="fp32",
                  dt_mode="backward", dt=1.0, max_batch=1, device=0, engine="auto", tc_cluster=0,
-                 tc_adjoint=False, single_pass=False):
+                 tc_adjoint=False, single_pass=False, tc_pair="auto"):
         L = lib()
         o = Opts()
         L.s2w_default_opts(ctypes.byref(o))
@@ -172,6 +173,7 @@ class Context:
         o.tc_cluster = int(tc_cluster)
         o.tc_adjoint = int(bool(tc_adjoint))
         o.single_pass = int(bool(single_pass))
+        o.tc_pair = PAIR[tc_pair]
         h = ctypes.c_void_p()
         st = L.s2w_create(Ns, Ng, No, Nt, ctypes.byref(o), ctypes.byref(h))
         if st != 0:

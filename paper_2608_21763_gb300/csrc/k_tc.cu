@@ -14,11 +14,15 @@
 // Stage 2: A = vhat_l (rows = ruptures, c = grid point), B built from Phat_l
 //          (t = observation);  split over chunks of grid points, D -> partials.
 //
-// Warp roles (192 threads, one CTA per SM, persistent over work units):
+// Warp roles (576 threads, one CTA per SM, persistent over work units):
 //   warp 0  one lane issues TMA loads into a ring of K-block stages;
 //   warp 1  allocates tensor memory; one lane issues tcgen05.mma and commits;
-//   warps 2-5  epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
-//              lanes 32 (w % 4) .. +31, i.e. tile rows), scale, store.
+//   warps 2-17 epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
+//              lanes 32 (w % 4) .. +31, i.e. tile rows, and every fourth
+//              64-column chunk), scale, store.  Four warps per lane quadrant
+//              cut the time the MMAs wait for the accumulator to drain
+//              (with N = 512 it fills tensor memory, so it cannot be
+//              double-buffered); FP8 kernels keep two per quadrant.
 // Every mbarrier wait is bounded (s2w_internal.cuh); on expiry a status bit
 // is latched and the CTA drains and exits.
 #include <cuda.h>
@@ -32,8 +36,12 @@ namespace s2w {
 
 namespace {
 
-constexpr int kTcThreads = 192;  // warps: 0 TMA producer, 1 MMA, 2-5 epilogue
-constexpr int kTcThreadsF8 = 320;  // FP8 A: + warps 6-9 widen the A tiles to BF16
+// epilogue warps per TMEM lane quadrant (warps 2 .. 2 + 4 EPW - 1); the FP8
+// kernels keep fewer, their 4 converter warps need the registers
+constexpr int kEpw = 4;
+constexpr int kEpwF8 = 2;
+constexpr int kTcThreads = 32 * (2 + 4 * kEpw);         // warps: 0 TMA producer, 1 MMA, then the epilogue
+constexpr int kTcThreadsF8 = 32 * (2 + 4 * kEpwF8) + 128;  // FP8 A: + 4 warps widen the A tiles to FP16
 constexpr int kBlockM = 128;
 constexpr int kBlockK = 64;  // bf16 elements per 128-byte swizzle row
 constexpr int kABytes = kBlockM * kBlockK * 2;
@@ -193,6 +201,52 @@ __host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
   return (1u << 4) | (static_cast<uint32_t>(N >> 3) << 17) | (static_cast<uint32_t>(M >> 4) << 24);
 }
 
+// Epilogue of one 128 x N accumulator at TMEM address tbase (this warp's lane
+// quadrant): the thread owning tile row `row` scales its columns and stores
+// them, column pair (2t, 2t+1) as complex column t < T, to
+//   epi 0: out[l ld_l + t ld_t + row]  (BF16 pairs when out_bf is set),
+//   epi 1: out[((l n_kchunks + kc) M_total + row) T + t].
+// Epilogue warp group g of EPW takes the 64-column chunks g, g + EPW, ...
+// and the 16-column chunks of the tail likewise.  Every lane runs the
+// tcgen05.ld (warp-collective); rows that are not live store nothing.
+template <int NC>
+__device__ __forceinline__ void tc_store_cols(const TcArgs& a, const float* v, int t0, long long obase, long long ld,
+                                              bool bf, float scale) {
+  const int nt = a.T - t0;  // live complex columns from t0 (all NC when >= NC)
+  if (bf) {
+    __nv_bfloat162* p = a.out_bf + obase + t0 * ld;
+#pragma unroll
+    for (int k = 0; k < NC; ++k)
+      if (k < nt) p[k * ld] = __floats2bfloat162_rn(v[2 * k] * scale, v[2 * k + 1] * scale);
+  } else {
+    float2* p = a.out + obase + t0 * ld;
+#pragma unroll
+    for (int k = 0; k < NC; ++k)
+      if (k < nt) p[k * ld] = make_float2(v[2 * k] * scale, v[2 * k + 1] * scale);
+  }
+}
+
+template <int EPW>
+__device__ __forceinline__ void tc_epilogue_tile(const TcArgs& a, uint32_t tbase, int N, int g, int l, int kc,
+                                                 int row, bool live, float scale) {
+  const bool bf = a.epi == 0 && a.out_bf != nullptr;
+  const long long ld = a.epi == 0 ? a.ld_t : 1;
+  const long long obase = a.epi == 0
+                              ? static_cast<long long>(l) * a.ld_l + row
+                              : ((static_cast<long long>(l) * a.n_kchunks + kc) * a.M_total + row) * a.T;
+  const int n64 = N / 64 * 64;
+  for (int c0 = 64 * g; c0 < n64; c0 += 64 * EPW) {
+    float v[64];
+    tmem_ld64(tbase + c0, v);
+    if (live && c0 / 2 < a.T) tc_store_cols<32>(a, v, c0 / 2, obase, ld, bf, scale);
+  }
+  for (int c0 = n64 + 16 * g; c0 < N; c0 += 16 * EPW) {
+    float v[16];
+    tmem_ld16(tbase + c0, v);
+    if (live && c0 / 2 < a.T) tc_store_cols<8>(a, v, c0 / 2, obase, ld, bf, scale);
+  }
+}
+
 // One ring of K-block stages, each holding the A tile and the B tile of the
 // same K block (loaded together, released together).
 // CL > 1: clusters of CL CTAs take CL adjacent M tiles of the same (bin, K
@@ -219,6 +273,9 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUten
   static_assert(MT == 1 || (CL == 1 && MODE != 2), "M-tile pairs: no cluster, no FP8");
   constexpr bool SPLIT = MODE == 1;
   constexpr bool F8 = MODE == 2;
+  constexpr int EPW = F8 ? kEpwF8 : kEpw;
+  constexpr int kEpiWarps = 4 * EPW;
+  constexpr int kConvWarp0 = 2 + kEpiWarps;  // FP8: first of the 4 converter warps
   constexpr int kStg = F8 ? kBlockM * BK : 0;  // FP8 staging bytes per stage
   constexpr int kA = kBlockM * BK * 2;
   constexpr int a_tile = kA * (SPLIT ? 2 : 1);  // one M tile's A (+ A_lo) bytes per stage
@@ -257,7 +314,7 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUten
       if (F8) mbar_init(aready + s, 4);
     }
     mbar_init(acc_full, 1);
-    mbar_init(acc_empty, 4);
+    mbar_init(acc_empty, kEpiWarps);
     fence_mbar_init();
   }
   if (warp == 1) {
@@ -377,9 +434,9 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUten
       // the epilogue consumes the last accumulator; wait for it before teardown
       if (acc_it > 0) mbar_wait_bounded(acc_empty, (acc_it - 1) & 1, a.status, DEV_ERR_TIMEOUT_MMA);
     }
-  } else if (F8 && warp >= 6) {
-    // converter warps 6..9: thread t widens row t of each FP8 A tile
-    const int t = threadIdx.x - 192;
+  } else if (F8 && warp >= kConvWarp0) {
+    // converter warps: thread t widens row t of each FP8 A tile
+    const int t = threadIdx.x - 32 * kConvWarp0;
     int it = 0;
     bool ok = true;
     for (long long u = cid; u < units && ok; u += ncl) {
@@ -426,8 +483,9 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUten
       }
     }
   } else {
-    // epilogue warps 2..5
-    const int q = warp & 3;  // TMEM lane quadrant this warp may access
+    // epilogue warps 2 .. 2 + kEpiWarps - 1
+    const int q = warp & 3;          // TMEM lane quadrant this warp may access
+    const int g = (warp - 2) >> 2;   // column group of the quadrant
     int acc_it = 0;
     for (long long u = cid; u < units; u += ncl) {
       int l, mt, kc;
@@ -436,39 +494,13 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUten
       tc_fence_after();
 #pragma unroll 1
       for (int j = 0; j < MT; ++j) {
-      const int row = (mt + j) * kBlockM + q * 32 + lane;
-      const uint32_t tbase = tmem + j * N + (static_cast<uint32_t>(q * 32) << 16);
-      const bool live = row < a.M_total && mt + j < a.m_tiles;
-      float scale = 1.f;
-      if (a.row_scale != nullptr && live) scale = a.row_scale[static_cast<long long>(l) * a.nblk + row / 256];
-      if (a.b_amax != nullptr) scale *= f16_unscale(*a.b_amax);  // undo the FP16 B operand's power-of-two scale
-      auto emit = [&](int c0, const float* v, int ncols) {
-        if (!live) return;
-        for (int k = 0; k < ncols / 2; ++k) {
-          const int t = c0 / 2 + k;  // complex column (rupture or observation)
-          if (t < a.T) {
-            const float2 z = make_float2(v[2 * k] * scale, v[2 * k + 1] * scale);
-            if (a.epi == 0 && a.out_bf != nullptr)
-              a.out_bf[static_cast<long long>(l) * a.ld_l + static_cast<long long>(t) * a.ld_t + row] =
-                  __floats2bfloat162_rn(z.x, z.y);
-            else if (a.epi == 0)
-              a.out[static_cast<long long>(l) * a.ld_l + static_cast<long long>(t) * a.ld_t + row] = z;
-            else
-              a.out[((static_cast<long long>(l) * a.n_kchunks + kc) * a.M_total + row) * a.T + t] = z;
-          }
-        }
-      };
-      int c0 = 0;
-      for (; c0 + 64 <= N; c0 += 64) {
-        float v[64];
-        tmem_ld64(tbase + c0, v);
-        emit(c0, v, 64);
-      }
-      for (; c0 < N; c0 += 16) {
-        float v[16];
-        tmem_ld16(tbase + c0, v);
-        emit(c0, v, 16);
-      }
+        const int row = (mt + j) * kBlockM + q * 32 + lane;
+        const uint32_t tbase = tmem + j * N + (static_cast<uint32_t>(q * 32) << 16);
+        const bool live = row < a.M_total && mt + j < a.m_tiles;
+        float scale = 1.f;
+        if (a.row_scale != nullptr && live) scale = a.row_scale[static_cast<long long>(l) * a.nblk + row / 256];
+        if (a.b_amax != nullptr) scale *= f16_unscale(*a.b_amax);  // undo the FP16 B operand's power-of-two scale
+        tc_epilogue_tile<EPW>(a, tbase, N, g, l, kc, row, live, scale);
       }  // M tiles of the unit
       tc_fence_before();
       __syncwarp();
@@ -517,6 +549,284 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB2,
                     const TcArgs a) {
   tc_gemm_body<BK, CL, 1>(&tmA, &tmB, &tmA2, &tmB2, a);
+}
+
+// ---------------------------------------------------------------------------
+// Two-SM form (tcgen05 cta_group::2).  A cluster of two CTAs computes one
+// M = 256 tile: rank 0 holds A rows [0, 128) of it, rank 1 rows [128, 256).
+// Each N <= 256 slice c of the B tile is split between the pair, rank r
+// staging columns [c 256 + r h, + h) with h = slice / 2.  One thread of rank 0
+// issues M = 256 MMAs that read both CTAs' shared memory and leave each
+// CTA's 128 accumulator rows in its own tensor memory.  Per CTA and K step
+// this halves the B bytes staged and read against one CTA per M tile.
+// Barriers: full[s] is used in rank 0 only (the TMA loads of both CTAs
+// complete on it); empty[s] and acc_full exist in both and receive the MMA
+// commits by multicast; acc_empty in rank 0 counts the 4 epilogue warps of
+// each CTA (rank 1's arrive remotely).  Every tcgen05 allocation, MMA and
+// commit of the kernel uses cta_group::2.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t cluster_addr(const void* p, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+  return r;
+}
+
+// TMA load into this CTA's shared memory that completes on the mbarrier at
+// cluster address `bar` (this CTA's or its pair peer's).
+__device__ __forceinline__ void tma_load_3d_pair(void* sdst, const CUtensorMap* tm, int c0, int c1, int c2,
+                                                 uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+      "%4}], [%5];" ::"r"(smem_u32(sdst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// mbar_wait_bounded with cluster-scope acquire (arrivals from the peer CTA).
+__device__ __forceinline__ bool mbar_try_wait_cl(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded_cl(uint64_t* bar, uint32_t parity, int* status, int code) {
+  if (mbar_try_wait_cl(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait_cl(bar, parity)) return true;
+    if ((it & 255u) == 0u && globaltimer() - t0 > kWaitLimitNs) {
+      atomicOr(status, code);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tmem_alloc2(uint32_t* holder, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(holder)), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish2() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc2(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_commit2_mc(uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(mask)
+      : "memory");
+}
+__device__ __forceinline__ void tc_mma2_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                             uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// MODE 0: BF16 operands; 1: split (A, A_lo, B, B_lo; three MMAs per K step).
+// Stage layout per CTA: A [A_lo] B-halves [B_lo-halves].
+template <int BK, int MODE>
+__device__ __forceinline__ void tc_gemm2_body(const CUtensorMap* tmA, const CUtensorMap* tmB, const CUtensorMap* tmA2,
+                                              const CUtensorMap* tmB2, const TcArgs& a) {
+  static_assert(MODE == 0 || MODE == 1, "two-SM form: BF16 or split operands");
+  constexpr bool SPLIT = MODE == 1;
+  constexpr int kEpiWarps = 4 * kEpw;
+  constexpr int kA = kBlockM * BK * 2;
+  const uint32_t crank = cluster_ctarank();
+  const bool lead = crank == 0;
+  const long long cid = static_cast<long long>(cluster_id_x());
+  const long long ncl = static_cast<long long>(cluster_count_x());
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+  const int N = a.N;
+  const int n_mma = N > 256 ? N / 256 : 1;
+  const int n_mma_cols = N > 256 ? 256 : N;
+  const int hrows = n_mma_cols / 2;  // B rows this CTA stages per MMA slice
+  const int hb = hrows * BK * 2;
+  const int bh_bytes = n_mma * hb;
+  const int a_bytes = kA * (SPLIT ? 2 : 1);
+  const int stage_bytes = a_bytes + bh_bytes * (SPLIT ? 2 : 1);
+  const int S = a.stages;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * stage_bytes);
+  uint64_t* empty = full + S;
+  uint64_t* acc_full = empty + S;
+  uint64_t* acc_empty = acc_full + 1;
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(acc_empty + 1);
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int nk_total = (a.K + BK - 1) / BK;
+  const int mpairs = (a.m_tiles + 1) / 2;
+  const long long units = static_cast<long long>(a.Nb) * mpairs * a.n_kchunks;
+  const uint32_t idesc = idesc_bf16(2 * kBlockM, n_mma_cols);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(empty + s, 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, 2 * kEpiWarps);
+    fence_mbar_init();
+  }
+  if (warp == 1) {  // one warp of each CTA allocates the pair's tensor memory together
+    tmem_alloc2(tmem_holder, a.tmem_cols);
+    tmem_relinquish2();
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync_all();  // both CTAs' barriers and tensor memory exist before any load or MMA
+  tc_fence_after();
+  const uint32_t tmem = *tmem_holder;
+
+  auto unit_coords = [&](long long u, int& l, int& mt, int& kc) {
+    kc = static_cast<int>(u % a.n_kchunks);
+    const long long r = u / a.n_kchunks;
+    mt = static_cast<int>(r % mpairs) * 2 + static_cast<int>(crank);  // this CTA's M tile
+    l = static_cast<int>(r / mpairs);
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      const uint32_t full0 = cluster_addr(full, 0);  // rank 0's full[0]
+      int it = 0;
+      bool ok = true;
+      for (long long u = cid; u < units && ok; u += ncl) {
+        int l, mt, kc;
+        unit_coords(u, l, mt, kc);
+        const int kb0 = kc * a.kblocks_per_chunk;
+        const int kb1 = min(nk_total, kb0 + a.kblocks_per_chunk);
+        for (int kb = kb0; kb < kb1; ++kb, ++it) {
+          const int s = it % S;
+          if (it >= S && !mbar_wait_bounded(empty + s, ((it / S) - 1) & 1, a.status, DEV_ERR_TIMEOUT_EMPTY)) {
+            ok = false;
+            break;
+          }
+          unsigned char* sa = smem + s * stage_bytes;
+          if (lead) mbar_arrive_expect_tx(full + s, 2u * static_cast<uint32_t>(stage_bytes));
+          const uint32_t fb = full0 + 8u * static_cast<uint32_t>(s);
+          // rows past the last M tile read as zeros (TMA fill); their outputs are never stored
+          tma_load_3d_pair(sa, tmA, kb * BK, mt * kBlockM, l, fb);
+          if constexpr (SPLIT) tma_load_3d_pair(sa + kA, tmA2, kb * BK, mt * kBlockM, l, fb);
+          unsigned char* sb = sa + a_bytes;
+          for (int c = 0; c < n_mma; ++c) {
+            const int row0 = c * n_mma_cols + static_cast<int>(crank) * hrows;
+            tma_load_3d_pair(sb + c * hb, tmB, kb * BK, row0, l, fb);
+            if constexpr (SPLIT) tma_load_3d_pair(sb + bh_bytes + c * hb, tmB2, kb * BK, row0, l, fb);
+          }
+        }
+      }
+      if (lead)
+        for (int kk = (it > S ? it - S : 0); kk < it; ++kk)
+          mbar_wait_bounded(full + kk % S, (kk / S) & 1, a.status, DEV_ERR_TIMEOUT_FULL);
+      // the MMAs' releases of the last stages land in both CTAs before anyone leaves
+      for (int kk = (it > S ? it - S : 0); kk < it; ++kk)
+        mbar_wait_bounded(empty + kk % S, (kk / S) & 1, a.status, DEV_ERR_TIMEOUT_EMPTY);
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && lead) {
+      int it = 0, acc_it = 0;
+      bool ok = true;
+      for (long long u = cid; u < units && ok; u += ncl) {
+        int l, mt, kc;
+        unit_coords(u, l, mt, kc);
+        const int kb0 = kc * a.kblocks_per_chunk;
+        const int kb1 = min(nk_total, kb0 + a.kblocks_per_chunk);
+        if (acc_it > 0 && !mbar_wait_bounded_cl(acc_empty, (acc_it - 1) & 1, a.status, DEV_ERR_TIMEOUT_MMA)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        for (int kb = kb0; kb < kb1; ++kb, ++it) {
+          const int s = it % S;
+          if (!mbar_wait_bounded(full + s, (it / S) & 1, a.status, DEV_ERR_TIMEOUT_FULL)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(smem + s * stage_bytes);
+          const uint32_t sb = sa + a_bytes;
+#pragma unroll
+          for (int k = 0; k < BK / 16; ++k) {
+            const uint64_t ad = sdesc_sw<BK>(sa + k * 32);
+            for (int c = 0; c < n_mma; ++c) {
+              const uint32_t boff = c * hb + k * 32;
+              const uint64_t bd = sdesc_sw<BK>(sb + boff);
+              const uint32_t dcol = tmem + c * n_mma_cols;
+              tc_mma2_bf16(dcol, ad, bd, idesc, (kb > kb0 || k > 0) ? 1u : 0u);
+              if constexpr (SPLIT) {
+                tc_mma2_bf16(dcol, ad, sdesc_sw<BK>(sb + bh_bytes + boff), idesc, 1u);
+                tc_mma2_bf16(dcol, sdesc_sw<BK>(sa + kA + k * 32), bd, idesc, 1u);
+              }
+            }
+          }
+          tc_commit2_mc(empty + s, 0x3);
+        }
+        if (!ok) break;
+        tc_commit2_mc(acc_full, 0x3);
+        ++acc_it;
+      }
+      // both CTAs' epilogues consume the last accumulator before teardown
+      if (acc_it > 0) mbar_wait_bounded_cl(acc_empty, (acc_it - 1) & 1, a.status, DEV_ERR_TIMEOUT_MMA);
+    }
+  } else {
+    // epilogue warps of both CTAs: this CTA's 128 rows of the M = 256 tile
+    const int q = warp & 3;         // TMEM lane quadrant this warp may access
+    const int g = (warp - 2) >> 2;  // column group of the quadrant
+    const uint32_t acc_empty0 = cluster_addr(acc_empty, 0);
+    int acc_it = 0;
+    for (long long u = cid; u < units; u += ncl) {
+      int l, mt, kc;
+      unit_coords(u, l, mt, kc);
+      if (!mbar_wait_bounded(acc_full, acc_it & 1, a.status, DEV_ERR_TIMEOUT_MMA)) break;
+      tc_fence_after();
+      const int row = mt * kBlockM + q * 32 + lane;
+      const uint32_t tbase = tmem + (static_cast<uint32_t>(q * 32) << 16);
+      const bool live = row < a.M_total && mt < a.m_tiles;
+      float scale = 1.f;
+      if (a.row_scale != nullptr && live) scale = a.row_scale[static_cast<long long>(l) * a.nblk + row / 256];
+      tc_epilogue_tile<kEpw>(a, tbase, N, g, l, kc, row, live, scale);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cluster(acc_empty0);
+      ++acc_it;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync_all();  // neither CTA still reads or writes the pair's tensor memory
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc2(tmem, a.tmem_cols);
+  }
+  cluster_sync_all();  // no CTA leaves while its peer may still signal it
+}
+
+template <int BK>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_tc_gemm2(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
+  tc_gemm2_body<BK, 0>(&tmA, &tmB, nullptr, nullptr, a);
+}
+
+template <int BK>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_tc_gemm2_split(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                     const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB2,
+                     const TcArgs a) {
+  tc_gemm2_body<BK, 1>(&tmA, &tmB, &tmA2, &tmB2, a);
 }
 
 // B operand of the real embedding from complex FP32 x[l][t][c] (element
@@ -972,7 +1282,13 @@ cudaError_t tc_encode_3d_u8(CUtensorMap* out, const void* base, long long K, lon
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-int tc_block_k(int N, int split) { return (N > 256 || (split && N > 128)) ? 32 : 64; }
+int tc_block_k(int N, int split, int pair) {
+  if (pair) {  // half of B per CTA: 128-byte swizzle whenever four such stages fit
+    const int stage64 = (kBlockM + N / 2) * 64 * 2 * (1 + split);
+    return 4 * stage64 <= kSmemBudget ? 64 : 32;
+  }
+  return (N > 256 || (split && N > 128)) ? 32 : 64;
+}
 
 namespace {
 int tc_stage_bytes(int N, int a_lo, int b_lo, int fp8, int mt) {
@@ -989,6 +1305,24 @@ int tc_stages_for(int N, int a_lo, int b_lo, int fp8, int mt) {
 
 size_t tc_smem_bytes(int N, int stages, int a_lo, int b_lo, int fp8, int mt) {
   return 1024 + static_cast<size_t>(stages) * tc_stage_bytes(N, a_lo, b_lo, fp8, mt) + 8 * (3 * stages + 2) + 16;
+}
+
+namespace {
+// Two-SM form: per CTA, one A tile and half of the B tile (each part
+// doubled when split).
+int tc2_stage_bytes(int N, int split) {
+  const int bk = tc_block_k(N, split, 1);
+  return (kBlockM * bk * 2 + (N / 2) * bk * 2) * (1 + split);
+}
+size_t tc2_smem_bytes(int N, int stages, int split) {
+  return 1024 + static_cast<size_t>(stages) * tc2_stage_bytes(N, split) + 8 * (2 * stages + 2) + 16;
+}
+}  // namespace
+
+int tc_stages_pair(int N, int split) {
+  int s = kSmemBudget / tc2_stage_bytes(N, split);
+  if (s > 8) s = 8;
+  return s;
 }
 
 template <int BK, int CL, int MODE>
@@ -1048,6 +1382,52 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
   if (a.a_lo != a.b_lo || (a.a_lo != 0 && a.a_lo != 1) || (a.a_lo && (!tmA2 || !tmB2))) return cudaErrorInvalidValue;
   if ((a.a_fp8 != 0 && a.a_fp8 != 1) || (a.a_fp8 && a.a_lo) || (a.a_fp8 && a.row_scale == nullptr))
     return cudaErrorInvalidValue;
+  if (a.cta2) {  // two-SM MMAs (M = 256 per CTA pair), no cluster multicast, no M-tile pairs, not FP8
+    if (a.a_fp8 || a.m_pair || a.cluster > 1 || a.N % 32 != 0) return cudaErrorInvalidValue;
+    const int sp = a.a_lo;
+    const size_t smem = tc2_smem_bytes(a.N, a.stages, sp);
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    const bool bk64 = tc_block_k(a.N, sp, 1) == 64;
+    const void* kfn = sp ? (bk64 ? reinterpret_cast<const void*>(k_tc_gemm2_split<64>)
+                                 : reinterpret_cast<const void*>(k_tc_gemm2_split<32>))
+                         : (bk64 ? reinterpret_cast<const void*>(k_tc_gemm2<64>)
+                                 : reinterpret_cast<const void*>(k_tc_gemm2<32>));
+    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.blockDim = dim3(kTcThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.gridDim = dim3(static_cast<unsigned>((num_sms / 2) * 2));
+    int active = 0;
+    e = cudaOccupancyMaxActiveClusters(&active, kfn, &cfg);
+    if (e != cudaSuccess) return e;
+    if (active < 1) return cudaErrorInvalidConfiguration;
+    long long nclusters = active;
+    const long long pu = static_cast<long long>(a.Nb) * ((a.m_tiles + 1) / 2) * a.n_kchunks;
+    if (nclusters > pu) nclusters = pu;
+    cfg.gridDim = dim3(static_cast<unsigned>(nclusters * 2));
+    if (sp) {
+      if (bk64)
+        e = cudaLaunchKernelEx(&cfg, k_tc_gemm2_split<64>, tmA, tmB, *tmA2, *tmB2, a);
+      else
+        e = cudaLaunchKernelEx(&cfg, k_tc_gemm2_split<32>, tmA, tmB, *tmA2, *tmB2, a);
+    } else {
+      if (bk64)
+        e = cudaLaunchKernelEx(&cfg, k_tc_gemm2<64>, tmA, tmB, a);
+      else
+        e = cudaLaunchKernelEx(&cfg, k_tc_gemm2<32>, tmA, tmB, a);
+    }
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+  }
   const int CL = a.cluster < 1 ? 1 : a.cluster;
   if (CL != 1 && CL != 2 && CL != 4) return cudaErrorInvalidValue;
   if (CL > 1 && (a.N / CL < 8 || (a.N / CL) % 8 != 0 || a.N / CL > 256)) return cudaErrorInvalidValue;

@@ -62,6 +62,7 @@ struct s2w_ctx {
   int tc_nkc = 1;        // stage-2 K chunks
   int tc_cl1 = 1;        // cluster size of the stage-1 GEMM (B tiles multicast)
   int tc_cl2 = 1;        // cluster size of the stage-2 GEMM
+  int tc_pair = 0;       // 1: two-SM MMAs (CTA pairs per M = 256 tile) where the shape allows; kPairAuto: for N = 512
   int tc_min_batch = 2;  // AUTO: smallest B on the tensor engine
   // CUDA graphs of the waveform pipeline, one per (slip, q, B), least
   // recently used evicted beyond kGraphCache entries
@@ -177,8 +178,14 @@ int pointer_kind(const void* p, int device) {
   return 0;
 }
 
-// Tensor engine: default CTAs per cluster sharing each B tile.
+// Tensor engine: default CTAs per cluster sharing each B tile, and whether
+// GEMMs take the two-SM form by default (kPairAuto: for N = 512, where half
+// of B per CTA lets the ring take 64-element K blocks with 128-byte swizzle;
+// measured 0.86 against 0.75 of the sustained BF16 peak for the 256-rupture
+// stage 1.  At N = 128 the M-tile pairs of one CTA were faster.)
 constexpr int kDefaultCluster = 1;
+constexpr int kPairAuto = 2;
+constexpr int kDefaultPair = kPairAuto;
 
 // Largest cluster <= want that the GEMM accepts for an N-wide B operand split
 // over it and m_tiles M tiles.
@@ -188,15 +195,22 @@ int fit_cluster(int want, int N, int m_tiles) {
   return cl;  // 1: a single CTA loads any N <= 512 itself
 }
 
-// Two M tiles per unit sharing each B tile, when the accumulators fit (N <=
-// 256), without a cluster, for non-FP8 A and at least two M tiles; sets the
-// ring depth and TMEM columns of `a` for the chosen form.
-void tc_shape(TcArgs& a, int N, int m_tiles, int cl, int split, int fp8) {
-  a.m_pair = (N <= 256 && cl == 1 && !fp8 && m_tiles >= 2) ? 1 : 0;
+// Form of one tensor GEMM; sets the ring depth and TMEM columns of `a` and
+// returns the B tensor map's box rows.  With `pair` (1, or kPairAuto and
+// the shape it covers; and no cluster, non-FP8 A, N % 32 == 0, at least two
+// M tiles): two-SM MMAs, a CTA pair per M = 256 tile staging half of B each.  Otherwise two M tiles per unit
+// sharing each B tile when the accumulators fit (N <= 256), without a
+// cluster, for non-FP8 A and at least two M tiles.
+int tc_shape(TcArgs& a, int N, int m_tiles, int cl, int split, int fp8, int pair) {
+  if (pair == kPairAuto) pair = N == 512 && !split;
+  a.cta2 = (pair && cl == 1 && !fp8 && N % 32 == 0 && m_tiles >= 2) ? 1 : 0;
+  a.m_pair = (!a.cta2 && N <= 256 && cl == 1 && !fp8 && m_tiles >= 2) ? 1 : 0;
   const int mt = a.m_pair ? 2 : 1;
-  a.stages = tc_stages_for(N, split, split, fp8, mt);
+  a.stages = a.cta2 ? tc_stages_pair(N, split) : tc_stages_for(N, split, split, fp8, mt);
   const int cols = mt * N;
   a.tmem_cols = cols <= 32 ? 32 : (cols <= 64 ? 64 : (cols <= 128 ? 128 : (cols <= 256 ? 256 : 512)));
+  const int slice = N > 256 ? 256 : N;
+  return a.cta2 ? slice / 2 : (cl > 1 ? N / cl : slice);
 }
 
 // The stream engine handles ruptures in groups of at most this many (its
@@ -330,17 +344,17 @@ int tc_gemm_epi0(s2w_ctx* ctx, const void* A, const void* A_lo, long long M, lon
                  cudaStream_t st, __nv_bfloat162* out_bf = nullptr) {
   const int sp = A_lo != nullptr ? 1 : 0;
   CUtensorMap ta, tb, ta2, tb2;
-  const int bk = tc_block_k(N, sp);
   const int mt = static_cast<int>((M + 127) / 128);
   const int cl = fit_cluster(cl_want, N, mt);
-  const int brows = cl > 1 ? N / cl : (N > 256 ? 256 : N);
+  TcArgs a{};
+  const int brows = tc_shape(a, N, mt, cl, sp, 0, ctx->tc_pair);
+  const int bk = tc_block_k(N, sp, a.cta2);
   CK(tc_encode_3d(&ta, A, K, M, ctx->Nb, K, 128, bk));
   CK(tc_encode_3d(&tb, Bop, K, n_alloc, ctx->Nb, K, brows, bk));
   if (sp) {
     CK(tc_encode_3d(&ta2, A_lo, K, M, ctx->Nb, K, 128, bk));
     CK(tc_encode_3d(&tb2, B_lo, K, n_alloc, ctx->Nb, K, brows, bk));
   }
-  TcArgs a{};
   a.N = N;
   a.K = static_cast<int>(K);
   a.M_total = static_cast<int>(M);
@@ -348,7 +362,6 @@ int tc_gemm_epi0(s2w_ctx* ctx, const void* A, const void* A_lo, long long M, lon
   a.m_tiles = mt;
   a.n_kchunks = 1;
   a.kblocks_per_chunk = static_cast<int>((K + bk - 1) / bk);
-  tc_shape(a, N, mt, cl, sp, 0);
   a.a_lo = sp;
   a.b_lo = sp;
   a.cluster = cl;
@@ -469,10 +482,11 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
     {
       StageTimer t(ctx, 1, st);
       CUtensorMap ta, tb, ta2, tb2;
-      const int bk = tc_block_k(N1, sp);
       const int m1 = static_cast<int>((Ng + 127) / 128);
       const int cl = fit_cluster(ctx->tc_cl1, N1, m1);
-      const int brows = cl > 1 ? N1 / cl : (N1 > 256 ? 256 : N1);
+      TcArgs a{};
+      const int brows = tc_shape(a, N1, m1, cl, sp, f8 ? 1 : 0, ctx->tc_pair);
+      const int bk = tc_block_k(N1, sp, a.cta2);
       if (f8)  // one byte per K element: row pitch 2 Ns_pad bytes
         CK(tc_encode_3d_u8(&ta, ctx->G, K1, Ng, Nb, 128, bk));
       else
@@ -482,7 +496,6 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
         CK(tc_encode_3d(&ta2, ctx->G_lo, K1, Ng, Nb, K1, 128, bk));
         CK(tc_encode_3d(&tb2, ctx->tc_bp1_lo, K1, ctx->tc_n1max, Nb, K1, brows, bk));
       }
-      TcArgs a{};
       a.N = N1;
       a.K = K1;
       a.M_total = static_cast<int>(Ng);
@@ -490,7 +503,6 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
       a.m_tiles = static_cast<int>((Ng + 127) / 128);
       a.n_kchunks = 1;
       a.kblocks_per_chunk = (K1 + bk - 1) / bk;
-      tc_shape(a, N1, m1, cl, sp, f8 ? 1 : 0);
       a.a_lo = sp;
       a.b_lo = sp;
       a.a_fp8 = f8 ? 1 : 0;
@@ -535,14 +547,17 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
       CUtensorMap ta, tb, ta2, tb2;
       const int m2 = (Bs + 127) / 128;
       const int cl = fit_cluster(ctx->tc_cl2, ctx->tc_n2, m2);
-      const int bk = tc_block_k(ctx->tc_n2, sp);
+      TcArgs a{};
+      int brows = tc_shape(a, ctx->tc_n2, m2, cl, sp, 0, ctx->tc_pair);
+      // the chunk length tc_kbpc counts K blocks of the single-CTA size
+      if (tc_block_k(ctx->tc_n2, sp, a.cta2) != tc_block_k(ctx->tc_n2, sp)) brows = tc_shape(a, ctx->tc_n2, m2, cl, sp, 0, 0);
+      const int bk = tc_block_k(ctx->tc_n2, sp, a.cta2);
       CK(tc_encode_3d(&ta, ctx->tc_vhat, K2, ctx->tc_bsub, Nb, K2, 128, bk));
-      CK(tc_encode_3d(&tb, ctx->tc_p2, K2, ctx->tc_n2, Nb, K2, ctx->tc_n2 / cl, bk));
+      CK(tc_encode_3d(&tb, ctx->tc_p2, K2, ctx->tc_n2, Nb, K2, brows, bk));
       if (sp) {
         CK(tc_encode_3d(&ta2, ctx->tc_vhat_lo, K2, ctx->tc_bsub, Nb, K2, 128, bk));
-        CK(tc_encode_3d(&tb2, ctx->tc_p2_lo, K2, ctx->tc_n2, Nb, K2, ctx->tc_n2 / cl, bk));
+        CK(tc_encode_3d(&tb2, ctx->tc_p2_lo, K2, ctx->tc_n2, Nb, K2, brows, bk));
       }
-      TcArgs a{};
       a.N = ctx->tc_n2;
       a.K = static_cast<int>(K2);
       a.M_total = Bs;
@@ -550,7 +565,6 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
       a.m_tiles = (Bs + 127) / 128;
       a.n_kchunks = ctx->tc_nkc;
       a.kblocks_per_chunk = ctx->tc_kbpc;
-      tc_shape(a, ctx->tc_n2, m2, cl, sp, 0);
       a.a_lo = sp;
       a.b_lo = sp;
       a.cluster = cl;
@@ -586,6 +600,7 @@ void s2w_default_opts(s2w_opts* o) {
   o->tc_cluster = 0;
   o->tc_adjoint = 0;
   o->single_pass = 0;
+  o->tc_pair = S2W_PAIR_AUTO;
 }
 
 const char* s2w_status_string(int s) {
@@ -629,6 +644,8 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
   if (o.tc_adjoint != 0 && o.tc_adjoint != 1) return fail(nullptr, S2W_ERR_ARG, "tc_adjoint=%d: 0 or 1", o.tc_adjoint);
   if (o.single_pass != 0 && o.single_pass != 1)
     return fail(nullptr, S2W_ERR_ARG, "single_pass=%d: 0 or 1", o.single_pass);
+  if (o.tc_pair != S2W_PAIR_AUTO && o.tc_pair != S2W_PAIR_ON && o.tc_pair != S2W_PAIR_OFF)
+    return fail(nullptr, S2W_ERR_ARG, "tc_pair=%d: S2W_PAIR_AUTO, _ON or _OFF", o.tc_pair);
   if (o.single_pass && (Nt > 256 || o.engine == S2W_ENGINE_TENSOR || o.tc_adjoint))
     return fail(nullptr, S2W_ERR_UNSUPPORTED, "single_pass: stream engine only, Nt <= 256, no tc_adjoint");
   if (o.engine == S2W_ENGINE_TENSOR && 2 * No > 256)
@@ -714,6 +731,7 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
     ctx->tc_bsub = static_cast<int>(std::min<long long>(B, ctx->tc_split ? 128 : 256));
     ctx->tc_cl1 = o.tc_cluster > 0 ? o.tc_cluster : kDefaultCluster;
     ctx->tc_cl2 = o.tc_cluster > 0 ? o.tc_cluster : kDefaultCluster;
+    ctx->tc_pair = o.tc_pair == S2W_PAIR_ON ? 1 : (o.tc_pair == S2W_PAIR_OFF ? 0 : kDefaultPair);
     ctx->tc_n1max = static_cast<int>(round_up(2 * ctx->tc_bsub, 16));
     if (ctx->tc_n1max > 256) ctx->tc_n1max = 512;
     ctx->tc_n2 = static_cast<int>(round_up(2 * No, 16));

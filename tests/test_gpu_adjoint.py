@@ -195,14 +195,16 @@ def test_tensor_adjoint_against_oracle(tiny_ops, prec):
     adjoint_bars(g, G, P, r, TOL_TC_ADJ[prec], f"tensor adjoint tiny {prec}")
 
 
+@pytest.mark.parametrize("tc_pair", ["off", "on"])
 @pytest.mark.parametrize("Ns,Ng,No,Nt,B", [(5, 1000, 3, 64, 2), (24, 700, 6, 32, 130), (7, 2100, 5, 128, 9)])
-def test_tensor_adjoint_shapes(Ns, Ng, No, Nt, B):
+def test_tensor_adjoint_shapes(Ns, Ng, No, Nt, B, tc_pair):
     """Ragged shapes: partial M tiles of the transposed operators, No far
-    below its 32-column padding, and (B = 130) two sub-batches."""
+    below its 32-column padding, and (B = 130) two sub-batches; with one CTA
+    per 128-row tile and with two-SM CTA pairs where the shape allows."""
     geom = compact_box(Ns, Ng, No, seed=Ns + Ng + 3)
     r = np.random.default_rng(3).standard_normal((B, No, Nt))
     ctx = make_context(s2w, geom, Nt, prec_g="bf16_hilo", max_batch=B, chunk=512, engine="tensor",
-                       tc_adjoint=True)
+                       tc_adjoint=True, tc_pair=tc_pair)
     g = ctx.adjoint(torch.tensor(r, dtype=torch.float32, device="cuda")).cpu().numpy()
     ctx.sync()
     G = geom.greens_rows(0, Ng, Nt)

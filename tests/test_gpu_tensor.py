@@ -30,12 +30,12 @@ def compact_box(Ns, Ng, No, seed, scale=0.1):
                           g.strike * scale, g.dip * scale, "box")
 
 
-def run_case(geom, Nt, B, seed=5, engine="tensor", chunk=4096, tc_cluster=0, prec="bf16"):
+def run_case(geom, Nt, B, seed=5, engine="tensor", chunk=4096, tc_cluster=0, prec="bf16", tc_pair="auto"):
     rng = np.random.default_rng(seed)
     slip = rng.standard_normal((B, geom.Ns, Nt))
     slip[:, :, Nt // 2:] = 0
     ctx = make_context(s2w, geom, Nt, prec_g=prec, max_batch=B, chunk=chunk, engine=engine,
-                       tc_cluster=tc_cluster)
+                       tc_cluster=tc_cluster, tc_pair=tc_pair)
     q = ctx.waveforms(torch.tensor(slip, dtype=torch.float32, device="cuda")).cpu().numpy()
     ctx.sync()
     G = geom.greens_rows(0, geom.Ng, Nt)
@@ -150,6 +150,27 @@ def test_multicast_clusters_match_single_cta(cluster, B):
     qc, _, _, _, _ = run_case(geom, 64, B, seed=13, tc_cluster=cluster)
     assert_parity(qc, q_ref, *wn, tol=TOL_TC, label=f"cluster {cluster} B={B}")
     assert np.array_equal(q1, qc)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "bf16_hilo"])
+@pytest.mark.parametrize("Ng,B", [(700, 48), (600, 300), (5000, 150)])
+def test_two_sm_pairs_match_single_cta(prec, Ng, B):
+    """Two-SM MMAs (a CTA pair per 256-row tile, each CTA staging half of the
+    B tile) against the oracle and against one CTA per 128-row tile: 700 grid
+    rows = 3 pairs with a partial last tile, 600 = 5 tiles (the last pair's
+    second tile empty); B = 48 (N = 96), 300 (sub-batches with N = 512 and 96,
+    and a 256-row stage 2), 150 (a 150-row stage 2 over grid chunks)."""
+    geom = compact_box(24, Ng, 6, seed=Ng + B)
+    chunk = 2048 if Ng > 4096 else 4096
+    tol = TOL_SPLIT if prec == "bf16_hilo" else TOL_TC
+    q1, q_ref, wn, _, _ = run_case(geom, 64, B, seed=B, prec=prec, chunk=chunk, tc_pair="off")
+    q2, _, _, ctx, slip = run_case(geom, 64, B, seed=B, prec=prec, chunk=chunk, tc_pair="on")
+    assert_parity(q2, q_ref, *wn, tol=tol, label=f"pair {prec} Ng={Ng} B={B}")
+    # the same products in the same K order: equal to rounding of the accumulation
+    d = np.linalg.norm((q2 - q1).ravel()) / np.linalg.norm(q1.ravel())
+    assert d < 1e-6, d
+    q3 = ctx.waveforms(torch.tensor(slip, dtype=torch.float32, device="cuda")).cpu().numpy()
+    assert np.array_equal(q2, q3)
 
 
 @pytest.mark.parametrize("B", [1, 5, 130])
