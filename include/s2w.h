@@ -128,7 +128,7 @@ typedef struct {
                       with each CTA staging half of the B tile.  S2W_PAIR_OFF
                       keeps one CTA per 128-row tile; S2W_PAIR_AUTO (0,
                       default) takes the two-SM form for the 512-column
-                      GEMMs of BF16 operands (256-rupture sub-batches). */
+                      GEMMs of BF16 operators (256-rupture sub-batches). */
 } s2w_opts;
 
 enum { S2W_PAIR_AUTO = 0, S2W_PAIR_ON = 1, S2W_PAIR_OFF = 2 };

@@ -247,6 +247,37 @@ __device__ __forceinline__ void tc_epilogue_tile(const TcArgs& a, uint32_t tbase
   }
 }
 
+// Widens row t of an FP8 e4m3 A tile (BK bytes at src, as TMA wrote it
+// without swizzle) exactly to FP16 (one cvt per pair) and stores the BK * 2
+// bytes at dst in the TMA swizzle pattern of a BK-element K-major row
+// (128 B: chunk ^ (row & 7); 64 B: chunk ^ ((row >> 1) & 3)).
+template <int BK>
+__device__ __forceinline__ void widen_fp8_row(const unsigned char* src_row, unsigned char* dst, int t) {
+  const uint4* src = reinterpret_cast<const uint4*>(src_row);
+#pragma unroll
+  for (int c = 0; c < BK / 16; ++c) {  // 16 FP8 in -> two 16-byte FP16 chunks out
+    const int cc = (c + t) % (BK / 16);  // staggered start: fewer bank conflicts
+    const uint4 w = src[cc];
+    const unsigned ww[4] = {w.x, w.y, w.z, w.w};
+    unsigned o[8];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const __half2_raw hr =
+            __nv_cvt_fp8x2_to_halfraw2(static_cast<__nv_fp8x2_storage_t>((ww[k] >> (16 * h)) & 0xffffu), __NV_E4M3);
+        o[2 * k + h] = static_cast<unsigned>(hr.x) | (static_cast<unsigned>(hr.y) << 16);
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int ch = 2 * cc + h;
+      const int sw = BK == 64 ? (ch ^ (t & 7)) : (ch ^ ((t >> 1) & 3));
+      *reinterpret_cast<uint4*>(dst + (sw << 4)) = make_uint4(o[4 * h], o[4 * h + 1], o[4 * h + 2], o[4 * h + 3]);
+    }
+  }
+}
+
 // One ring of K-block stages, each holding the A tile and the B tile of the
 // same K block (loaded together, released together).
 // CL > 1: clusters of CL CTAs take CL adjacent M tiles of the same (bin, K
@@ -451,32 +482,7 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUten
           break;
         }
         unsigned char* sa = smem + s * stage_bytes;
-        const uint4* src = reinterpret_cast<const uint4*>(sa + a_all + b_bytes + t * BK);
-        unsigned char* dst = sa + t * (BK * 2);
-#pragma unroll
-        for (int c = 0; c < BK / 16; ++c) {  // 16 FP8 in -> two 16-byte BF16 chunks out
-          const uint4 w = src[(c + t) % (BK / 16)];  // staggered start: fewer bank conflicts
-          const int cc = (c + t) % (BK / 16);
-          const unsigned ww[4] = {w.x, w.y, w.z, w.w};
-          unsigned o[8];
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2(
-                  static_cast<__nv_fp8x2_storage_t>((ww[k] >> (16 * h)) & 0xffffu), __NV_E4M3);
-              o[2 * k + h] = static_cast<unsigned>(hr.x) | (static_cast<unsigned>(hr.y) << 16);
-            }
-          }
-          // 16-byte chunks 2 cc and 2 cc + 1 of the row, placed as the TMA
-          // swizzle would (128 B: chunk ^ (row & 7); 64 B: chunk ^ ((row >> 1) & 3))
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int ch = 2 * cc + h;
-            const int sw = BK == 64 ? (ch ^ (t & 7)) : (ch ^ ((t >> 1) & 3));
-            *reinterpret_cast<uint4*>(dst + (sw << 4)) = make_uint4(o[4 * h], o[4 * h + 1], o[4 * h + 2], o[4 * h + 3]);
-          }
-        }
+        widen_fp8_row<BK>(sa + a_all + b_bytes + t * BK, sa + t * (BK * 2), t);
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(aready + s);
@@ -637,15 +643,23 @@ __device__ __forceinline__ void tc_mma2_bf16(uint32_t d_tmem, uint64_t a_desc, u
       : "memory");
 }
 
-// MODE 0: BF16 operands; 1: split (A, A_lo, B, B_lo; three MMAs per K step).
-// Stage layout per CTA: A [A_lo] B-halves [B_lo-halves].
+// MODE 0: BF16 operands; 1: split (A, A_lo, B, B_lo; three MMAs per K step);
+// 2: FP8 e4m3 A widened to FP16 in shared memory by 4 converter warps per
+// CTA, FP16 B.  Stage layout per CTA: A [A_lo] B-halves [B_lo-halves]
+// [FP8 staging].  FP8: each CTA's staging load completes on its own full[s]
+// (which rank 0's also expects its own and both CTAs' B halves on); the
+// converters of both CTAs then arrive on rank 0's aready[s], which the MMAs
+// wait for.
 template <int BK, int MODE>
 __device__ __forceinline__ void tc_gemm2_body(const CUtensorMap* tmA, const CUtensorMap* tmB, const CUtensorMap* tmA2,
                                               const CUtensorMap* tmB2, const TcArgs& a) {
-  static_assert(MODE == 0 || MODE == 1, "two-SM form: BF16 or split operands");
   constexpr bool SPLIT = MODE == 1;
-  constexpr int kEpiWarps = 4 * kEpw;
+  constexpr bool F8 = MODE == 2;
+  constexpr int EPW = F8 ? kEpwF8 : kEpw;
+  constexpr int kEpiWarps = 4 * EPW;
+  constexpr int kConvWarp0 = 2 + kEpiWarps;
   constexpr int kA = kBlockM * BK * 2;
+  constexpr int kStg = F8 ? kBlockM * BK : 0;  // FP8 staging bytes per stage
   const uint32_t crank = cluster_ctarank();
   const bool lead = crank == 0;
   const long long cid = static_cast<long long>(cluster_id_x());
@@ -659,11 +673,13 @@ __device__ __forceinline__ void tc_gemm2_body(const CUtensorMap* tmA, const CUte
   const int hb = hrows * BK * 2;
   const int bh_bytes = n_mma * hb;
   const int a_bytes = kA * (SPLIT ? 2 : 1);
-  const int stage_bytes = a_bytes + bh_bytes * (SPLIT ? 2 : 1);
+  const int b_all = bh_bytes * (SPLIT ? 2 : 1);
+  const int stage_bytes = a_bytes + b_all + kStg;
   const int S = a.stages;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * stage_bytes);
   uint64_t* empty = full + S;
-  uint64_t* acc_full = empty + S;
+  uint64_t* aready = empty + S;  // F8, rank 0: both CTAs' A slots widened
+  uint64_t* acc_full = aready + (F8 ? S : 0);
   uint64_t* acc_empty = acc_full + 1;
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(acc_empty + 1);
   const int warp = threadIdx.x >> 5;
@@ -671,12 +687,13 @@ __device__ __forceinline__ void tc_gemm2_body(const CUtensorMap* tmA, const CUte
   const int nk_total = (a.K + BK - 1) / BK;
   const int mpairs = (a.m_tiles + 1) / 2;
   const long long units = static_cast<long long>(a.Nb) * mpairs * a.n_kchunks;
-  const uint32_t idesc = idesc_bf16(2 * kBlockM, n_mma_cols);
+  const uint32_t idesc = F8 ? idesc_f16(2 * kBlockM, n_mma_cols) : idesc_bf16(2 * kBlockM, n_mma_cols);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(full + s, 1);
       mbar_init(empty + s, 1);
+      if (F8) mbar_init(aready + s, 8);  // 4 converter warps of each CTA
     }
     mbar_init(acc_full, 1);
     mbar_init(acc_empty, 2 * kEpiWarps);
@@ -716,11 +733,17 @@ __device__ __forceinline__ void tc_gemm2_body(const CUtensorMap* tmA, const CUte
             break;
           }
           unsigned char* sa = smem + s * stage_bytes;
-          if (lead) mbar_arrive_expect_tx(full + s, 2u * static_cast<uint32_t>(stage_bytes));
           const uint32_t fb = full0 + 8u * static_cast<uint32_t>(s);
-          // rows past the last M tile read as zeros (TMA fill); their outputs are never stored
-          tma_load_3d_pair(sa, tmA, kb * BK, mt * kBlockM, l, fb);
-          if constexpr (SPLIT) tma_load_3d_pair(sa + kA, tmA2, kb * BK, mt * kBlockM, l, fb);
+          if constexpr (F8) {
+            // own staging on own full[s]; rank 0's full[s] also takes both B halves
+            mbar_arrive_expect_tx(full + s, static_cast<uint32_t>(kStg + (lead ? 2 * bh_bytes : 0)));
+            tma_load_3d(sa + a_bytes + b_all, tmA, kb * BK, mt * kBlockM, l, full + s);
+          } else {
+            if (lead) mbar_arrive_expect_tx(full + s, 2u * static_cast<uint32_t>(stage_bytes));
+            // rows past the last M tile read as zeros (TMA fill); their outputs are never stored
+            tma_load_3d_pair(sa, tmA, kb * BK, mt * kBlockM, l, fb);
+            if constexpr (SPLIT) tma_load_3d_pair(sa + kA, tmA2, kb * BK, mt * kBlockM, l, fb);
+          }
           unsigned char* sb = sa + a_bytes;
           for (int c = 0; c < n_mma; ++c) {
             const int row0 = c * n_mma_cols + static_cast<int>(crank) * hrows;
@@ -729,7 +752,7 @@ __device__ __forceinline__ void tc_gemm2_body(const CUtensorMap* tmA, const CUte
           }
         }
       }
-      if (lead)
+      if (lead || F8)
         for (int kk = (it > S ? it - S : 0); kk < it; ++kk)
           mbar_wait_bounded(full + kk % S, (kk / S) & 1, a.status, DEV_ERR_TIMEOUT_FULL);
       // the MMAs' releases of the last stages land in both CTAs before anyone leaves
@@ -752,7 +775,9 @@ __device__ __forceinline__ void tc_gemm2_body(const CUtensorMap* tmA, const CUte
         tc_fence_after();
         for (int kb = kb0; kb < kb1; ++kb, ++it) {
           const int s = it % S;
-          if (!mbar_wait_bounded(full + s, (it / S) & 1, a.status, DEV_ERR_TIMEOUT_FULL)) {
+          const bool got = F8 ? mbar_wait_bounded_cl(aready + s, (it / S) & 1, a.status, DEV_ERR_TIMEOUT_FULL)
+                              : mbar_wait_bounded(full + s, (it / S) & 1, a.status, DEV_ERR_TIMEOUT_FULL);
+          if (!got) {
             ok = false;
             break;
           }
@@ -782,6 +807,30 @@ __device__ __forceinline__ void tc_gemm2_body(const CUtensorMap* tmA, const CUte
       // both CTAs' epilogues consume the last accumulator before teardown
       if (acc_it > 0) mbar_wait_bounded_cl(acc_empty, (acc_it - 1) & 1, a.status, DEV_ERR_TIMEOUT_MMA);
     }
+  } else if (F8 && warp >= kConvWarp0) {
+    // converter warps of both CTAs: thread t widens row t of this CTA's FP8 A tile
+    const int t = threadIdx.x - 32 * kConvWarp0;
+    const uint32_t aready0 = cluster_addr(aready, 0);
+    int it = 0;
+    bool ok = true;
+    for (long long u = cid; u < units && ok; u += ncl) {
+      int l, mt, kc;
+      unit_coords(u, l, mt, kc);
+      const int kb0 = kc * a.kblocks_per_chunk;
+      const int kb1 = min(nk_total, kb0 + a.kblocks_per_chunk);
+      for (int kb = kb0; kb < kb1; ++kb, ++it) {
+        const int s = it % S;
+        if (!mbar_wait_bounded(full + s, (it / S) & 1, a.status, DEV_ERR_TIMEOUT_FULL)) {
+          ok = false;
+          break;
+        }
+        unsigned char* sa = smem + s * stage_bytes;
+        widen_fp8_row<BK>(sa + a_bytes + b_all + t * BK, sa + t * (BK * 2), t);
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive_cluster(aready0 + 8u * static_cast<uint32_t>(s));
+      }
+    }
   } else {
     // epilogue warps of both CTAs: this CTA's 128 rows of the M = 256 tile
     const int q = warp & 3;         // TMEM lane quadrant this warp may access
@@ -798,7 +847,8 @@ __device__ __forceinline__ void tc_gemm2_body(const CUtensorMap* tmA, const CUte
       const bool live = row < a.M_total && mt < a.m_tiles;
       float scale = 1.f;
       if (a.row_scale != nullptr && live) scale = a.row_scale[static_cast<long long>(l) * a.nblk + row / 256];
-      tc_epilogue_tile<kEpw>(a, tbase, N, g, l, kc, row, live, scale);
+      if (a.b_amax != nullptr) scale *= f16_unscale(*a.b_amax);  // undo the FP16 B operand's power-of-two scale
+      tc_epilogue_tile<EPW>(a, tbase, N, g, l, kc, row, live, scale);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive_cluster(acc_empty0);
@@ -819,6 +869,12 @@ template <int BK>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_tc_gemm2(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
   tc_gemm2_body<BK, 0>(&tmA, &tmB, nullptr, nullptr, a);
+}
+
+template <int BK>
+__global__ void __launch_bounds__(kTcThreadsF8, 1)
+    k_tc_gemm2_f8(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
+  tc_gemm2_body<BK, 2>(&tmA, &tmB, nullptr, nullptr, a);
 }
 
 template <int BK>
@@ -928,10 +984,15 @@ __global__ void k_pack_a(const float2* __restrict__ src, int Nb, int rows, long 
 // swizzled K-major layout, 16-byte stores), T streams through a ring by
 // TMA (it stays in L2), the accumulator rows go back out as BF16 velocity
 // spectra in the stage-2 operand layout.
-// Warps: 0 TMA (T), 1 TMEM + MMA, 2-5 epilogue, 6-13 fill.
+// Warps: 0 TMA (T), 1 TMEM + MMA, then 4 RT_EPW epilogue warps (RT_EPW per
+// TMEM lane quadrant, each taking every RT_EPW-th 64-column chunk: the
+// 512-column accumulator fills tensor memory, so the MMAs of the next tile
+// wait for its drain), then 8 fill warps.  The split kernel keeps one
+// epilogue warp per quadrant (its fill warps need the registers).
 // ---------------------------------------------------------------------------
-constexpr int kRtThreads = 448;
 constexpr int kRtFillWarps = 8;
+__host__ __device__ constexpr int rt_epw(bool split) { return split ? 1 : 2; }
+__host__ __device__ constexpr int rt_threads(bool split) { return 32 * (2 + 4 * rt_epw(split) + kRtFillWarps); }
 
 
 // K blocks run outer and the (up to two) 256-column output halves inner, so a
@@ -943,10 +1004,12 @@ constexpr int kRtFillWarps = 8;
 // spectra (the split stage-2 A operand); 32-element K blocks (64-byte
 // swizzle) keep the doubled slots inside shared memory.
 template <bool SPLIT>
-__global__ void __launch_bounds__(kRtThreads, 1)
+__global__ void __launch_bounds__(rt_threads(SPLIT), 1)
     k_tc_retransform(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmT2,
                      const TcRtArgs a) {
   constexpr int BK = SPLIT ? 32 : 64;        // K elements per k-block
+  constexpr int EPW = rt_epw(SPLIT);
+  constexpr int kFill0 = 2 + 4 * EPW;        // first fill warp
   constexpr int kAs = kBlockM * BK * 2;      // one BF16 part of an M-tile k-block
   constexpr int a_slot = kAs * (SPLIT ? 2 : 1);
   constexpr int kBins = BK / 2;              // complex bins per k-block
@@ -990,7 +1053,7 @@ __global__ void __launch_bounds__(kRtThreads, 1)
       mbar_init(tempty + s, 1);
     }
     mbar_init(acc_full, 1);
-    mbar_init(acc_empty, 4);
+    mbar_init(acc_empty, 4 * EPW);
     fence_mbar_init();
   }
   if (warp == 1) {
@@ -1070,9 +1133,10 @@ __global__ void __launch_bounds__(kRtThreads, 1)
       }
       if (tl > 0) mbar_wait_bounded(acc_empty, (tl - 1) & 1, a.status, DEV_ERR_TIMEOUT_MMA);
     }
-  } else if (warp < 6) {
+  } else if (warp < kFill0) {
     // epilogue: accumulator row = signal, columns = output degrees of freedom
     const int q = warp & 3;
+    const int g = (warp - 2) >> 2;  // column group of the quadrant
     int tl = 0;
     for (long long t = blockIdx.x; t < tiles; t += gridDim.x, ++tl) {
       const int b = static_cast<int>(t / mtiles);
@@ -1092,7 +1156,7 @@ __global__ void __launch_bounds__(kRtThreads, 1)
         if (a.conj_row > 0) put1(off + a.conj_row, im, -re);  // row 2b + 1 of the conjugate embedding
       };
       // K = 2 Nt is a multiple of 64 for every supported Nt (32..256)
-      for (int c0 = 0; c0 < K; c0 += 64) {
+      for (int c0 = 64 * g; c0 < K; c0 += 64 * EPW) {
         float v[64];
         tmem_ld64(tbase + c0, v);
         if (i >= a.Ng) continue;
@@ -1116,7 +1180,7 @@ __global__ void __launch_bounds__(kRtThreads, 1)
     // kb holds bins kBins kb .. kBins kb + kBins - 1 for 128 signals; K slot 1
     // of bin 0 carries Re(bin Nt)); all of a tile's loads are in flight
     // together; 16-byte chunks are stored in the TMA swizzle pattern
-    const int f = warp - 6;
+    const int f = warp - kFill0;
     int tl = 0;
     bool ok = true;
     for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++tl) {
@@ -1309,18 +1373,22 @@ size_t tc_smem_bytes(int N, int stages, int a_lo, int b_lo, int fp8, int mt) {
 
 namespace {
 // Two-SM form: per CTA, one A tile and half of the B tile (each part
-// doubled when split).
-int tc2_stage_bytes(int N, int split) {
+// doubled when split), plus the byte staging of an FP8 A tile.
+int tc2_stage_bytes(int N, int split, int fp8) {
   const int bk = tc_block_k(N, split, 1);
-  return (kBlockM * bk * 2 + (N / 2) * bk * 2) * (1 + split);
+  return (kBlockM * bk * 2 + (N / 2) * bk * 2) * (1 + split) + (fp8 ? kBlockM * bk : 0);
 }
-size_t tc2_smem_bytes(int N, int stages, int split) {
-  return 1024 + static_cast<size_t>(stages) * tc2_stage_bytes(N, split) + 8 * (2 * stages + 2) + 16;
+size_t tc2_smem_bytes(int N, int stages, int split, int fp8) {
+  return 1024 + static_cast<size_t>(stages) * tc2_stage_bytes(N, split, fp8) + 8 * (3 * stages + 2) + 16;
 }
+constexpr int kSmemOptIn = 227 * 1024;
 }  // namespace
 
-int tc_stages_pair(int N, int split) {
-  int s = kSmemBudget / tc2_stage_bytes(N, split);
+int tc_stages_pair(int N, int split, int fp8) {
+  // FP8 stages carry the staging too: they may use all of the opt-in shared
+  // memory (four 56 KB stages at N = 512)
+  const int budget = fp8 ? kSmemOptIn - 1024 - 8 * (3 * 8 + 2) - 16 : kSmemBudget;
+  int s = budget / tc2_stage_bytes(N, split, fp8);
   if (s > 8) s = 8;
   return s;
 }
@@ -1382,16 +1450,19 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
   if (a.a_lo != a.b_lo || (a.a_lo != 0 && a.a_lo != 1) || (a.a_lo && (!tmA2 || !tmB2))) return cudaErrorInvalidValue;
   if ((a.a_fp8 != 0 && a.a_fp8 != 1) || (a.a_fp8 && a.a_lo) || (a.a_fp8 && a.row_scale == nullptr))
     return cudaErrorInvalidValue;
-  if (a.cta2) {  // two-SM MMAs (M = 256 per CTA pair), no cluster multicast, no M-tile pairs, not FP8
-    if (a.a_fp8 || a.m_pair || a.cluster > 1 || a.N % 32 != 0) return cudaErrorInvalidValue;
+  if (a.cta2) {  // two-SM MMAs (M = 256 per CTA pair), no cluster multicast, no M-tile pairs
+    if (a.m_pair || a.cluster > 1 || a.N % 32 != 0) return cudaErrorInvalidValue;
     const int sp = a.a_lo;
-    const size_t smem = tc2_smem_bytes(a.N, a.stages, sp);
-    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    const int f8 = a.a_fp8;
+    const size_t smem = tc2_smem_bytes(a.N, a.stages, sp, f8);
+    if (smem > static_cast<size_t>(kSmemOptIn)) return cudaErrorInvalidValue;
     const bool bk64 = tc_block_k(a.N, sp, 1) == 64;
-    const void* kfn = sp ? (bk64 ? reinterpret_cast<const void*>(k_tc_gemm2_split<64>)
-                                 : reinterpret_cast<const void*>(k_tc_gemm2_split<32>))
-                         : (bk64 ? reinterpret_cast<const void*>(k_tc_gemm2<64>)
-                                 : reinterpret_cast<const void*>(k_tc_gemm2<32>));
+    const void* kfn = f8   ? (bk64 ? reinterpret_cast<const void*>(k_tc_gemm2_f8<64>)
+                                   : reinterpret_cast<const void*>(k_tc_gemm2_f8<32>))
+                      : sp ? (bk64 ? reinterpret_cast<const void*>(k_tc_gemm2_split<64>)
+                                   : reinterpret_cast<const void*>(k_tc_gemm2_split<32>))
+                           : (bk64 ? reinterpret_cast<const void*>(k_tc_gemm2<64>)
+                                   : reinterpret_cast<const void*>(k_tc_gemm2<32>));
     cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
@@ -1402,7 +1473,7 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cfg.blockDim = dim3(kTcThreads);
+    cfg.blockDim = dim3(f8 ? kTcThreadsF8 : kTcThreads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cfg.gridDim = dim3(static_cast<unsigned>((num_sms / 2) * 2));
@@ -1414,7 +1485,12 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
     const long long pu = static_cast<long long>(a.Nb) * ((a.m_tiles + 1) / 2) * a.n_kchunks;
     if (nclusters > pu) nclusters = pu;
     cfg.gridDim = dim3(static_cast<unsigned>(nclusters * 2));
-    if (sp) {
+    if (f8) {
+      if (bk64)
+        e = cudaLaunchKernelEx(&cfg, k_tc_gemm2_f8<64>, tmA, tmB, a);
+      else
+        e = cudaLaunchKernelEx(&cfg, k_tc_gemm2_f8<32>, tmA, tmB, a);
+    } else if (sp) {
       if (bk64)
         e = cudaLaunchKernelEx(&cfg, k_tc_gemm2_split<64>, tmA, tmB, *tmA2, *tmB2, a);
       else
@@ -1505,9 +1581,9 @@ cudaError_t launch_tc_retransform(const CUtensorMap& tmT, const CUtensorMap* tmT
   cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   if (split)
-    k_tc_retransform<true><<<static_cast<unsigned>(grid), kRtThreads, smem, st>>>(tmT, *tmT2, aa);
+    k_tc_retransform<true><<<static_cast<unsigned>(grid), rt_threads(true), smem, st>>>(tmT, *tmT2, aa);
   else
-    k_tc_retransform<false><<<static_cast<unsigned>(grid), kRtThreads, smem, st>>>(tmT, tmT, aa);
+    k_tc_retransform<false><<<static_cast<unsigned>(grid), rt_threads(false), smem, st>>>(tmT, tmT, aa);
   return cudaGetLastError();
 }
 

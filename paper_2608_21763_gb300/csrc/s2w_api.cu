@@ -182,7 +182,9 @@ int pointer_kind(const void* p, int device) {
 // GEMMs take the two-SM form by default (kPairAuto: for N = 512, where half
 // of B per CTA lets the ring take 64-element K blocks with 128-byte swizzle;
 // measured 0.86 against 0.75 of the sustained BF16 peak for the 256-rupture
-// stage 1.  At N = 128 the M-tile pairs of one CTA were faster.)
+// stage 1.  At N = 128 the M-tile pairs of one CTA were faster, and so
+// were single CTAs for FP8 A: 0.63 against 0.50, the pair's cross-CTA
+// converter handshake sitting on every stage.)
 constexpr int kDefaultCluster = 1;
 constexpr int kPairAuto = 2;
 constexpr int kDefaultPair = kPairAuto;
@@ -197,16 +199,16 @@ int fit_cluster(int want, int N, int m_tiles) {
 
 // Form of one tensor GEMM; sets the ring depth and TMEM columns of `a` and
 // returns the B tensor map's box rows.  With `pair` (1, or kPairAuto and
-// the shape it covers; and no cluster, non-FP8 A, N % 32 == 0, at least two
-// M tiles): two-SM MMAs, a CTA pair per M = 256 tile staging half of B each.  Otherwise two M tiles per unit
+// the shape it covers; and no cluster, N % 32 == 0, at least two M tiles):
+// two-SM MMAs, a CTA pair per M = 256 tile staging half of B each.  Otherwise two M tiles per unit
 // sharing each B tile when the accumulators fit (N <= 256), without a
 // cluster, for non-FP8 A and at least two M tiles.
 int tc_shape(TcArgs& a, int N, int m_tiles, int cl, int split, int fp8, int pair) {
-  if (pair == kPairAuto) pair = N == 512 && !split;
-  a.cta2 = (pair && cl == 1 && !fp8 && N % 32 == 0 && m_tiles >= 2) ? 1 : 0;
+  if (pair == kPairAuto) pair = N == 512 && !split && !fp8;
+  a.cta2 = (pair && cl == 1 && N % 32 == 0 && m_tiles >= 2) ? 1 : 0;
   a.m_pair = (!a.cta2 && N <= 256 && cl == 1 && !fp8 && m_tiles >= 2) ? 1 : 0;
   const int mt = a.m_pair ? 2 : 1;
-  a.stages = a.cta2 ? tc_stages_pair(N, split) : tc_stages_for(N, split, split, fp8, mt);
+  a.stages = a.cta2 ? tc_stages_pair(N, split, fp8) : tc_stages_for(N, split, split, fp8, mt);
   const int cols = mt * N;
   a.tmem_cols = cols <= 32 ? 32 : (cols <= 64 ? 64 : (cols <= 128 ? 128 : (cols <= 256 ? 256 : 512)));
   const int slice = N > 256 ? 256 : N;

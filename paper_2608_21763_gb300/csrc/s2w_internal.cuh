@@ -227,8 +227,8 @@ struct TcArgs {
   int m_pair;              // 1: two M tiles per unit sharing each B tile (N <= 256, cluster 1, not FP8;
                            //    tmem_cols >= 2 N, stages from tc_stages_for(..., mt = 2))
   int cta2;                // 1: two-SM MMAs, a CTA pair per M = 256 tile, each staging half of B
-                           //    (N % 32 == 0, cluster 1, no m_pair, not FP8; B box rows = min(N, 256) / 2,
-                           //    stages from tc_stages_pair)
+                           //    (N % 32 == 0, cluster 1, no m_pair; B box rows = min(N, 256) / 2,
+                           //    K blocks tc_block_k(N, split, 1), stages from tc_stages_pair)
   int* status;
 };
 // bk = 64: 128-byte swizzle, K boxes of 64 BF16; bk = 32: 64-byte swizzle.
@@ -238,7 +238,7 @@ cudaError_t tc_encode_3d(CUtensorMap* out, const void* base, long long K, long l
 // with `terms` = 1 + a_lo + b_lo operand tiles beyond the first A and B
 int tc_block_k(int N, int split = 0, int pair = 0);
 int tc_stages_for(int N, int a_lo = 0, int b_lo = 0, int fp8 = 0, int mt = 1);
-int tc_stages_pair(int N, int split);
+int tc_stages_pair(int N, int split, int fp8 = 0);
 // Byte tensor map for FP8 A tiles: [nbatch][rows][K] bytes, box bk x box_rows, no swizzle.
 cudaError_t tc_encode_3d_u8(CUtensorMap* out, const void* base, long long K, long long rows, long long nbatch,
                             int box_rows, int bk);

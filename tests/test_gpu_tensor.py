@@ -218,7 +218,7 @@ def test_split_precision_clusters_bitwise():
 
 @pytest.mark.parametrize("B", [3, 7, 300])
 def test_fp8_operator_on_tensor_engine(B):
-    """FP8 e4m3 stage-1 spectra on the tensor engine: tiles widened to BF16
+    """FP8 e4m3 stage-1 spectra on the tensor engine: tiles widened to FP16
     in shared memory (128-byte swizzle at N <= 256, 64-byte at N = 512),
     per-(bin, 256-row) scales in the epilogue.  Against the oracle at the
     FP8 bar, and against the FP8 stream engine (same quantised operator; they
@@ -241,6 +241,23 @@ def test_fp8_operator_on_tensor_engine(B):
         assert_parity(out[engine], q_ref, wn, kappa, tol=1e-1, label=f"fp8 {engine} B={B}")
     d = np.linalg.norm((out["tensor"] - out["stream"]).reshape(B, -1), axis=1)
     assert np.all(d <= TOL_TC * wn), d / wn
+
+
+@pytest.mark.parametrize("Ng,B", [(700, 48), (600, 300)])
+def test_fp8_two_sm_pairs_match_single_cta(Ng, B):
+    """FP8 A on the two-SM form (each CTA widens its own 128 rows; both CTAs'
+    converters release the pair's MMAs) against the oracle at the FP8 bar and
+    against one CTA per 128-row tile (same FP8 products, FP32 accumulation):
+    600 rows leave the last pair's second tile empty, B = 300 runs N = 512
+    and N = 96 sub-batches."""
+    geom = compact_box(24, Ng, 6, seed=Ng + B + 1)
+    q1, q_ref, wn, _, _ = run_case(geom, 64, B, seed=B + 1, prec="fp8", chunk=256, tc_pair="off")
+    q2, _, _, ctx, slip = run_case(geom, 64, B, seed=B + 1, prec="fp8", chunk=256, tc_pair="on")
+    assert_parity(q2, q_ref, *wn, tol=1e-1, label=f"fp8 pair Ng={Ng} B={B}")
+    d = np.linalg.norm((q2 - q1).ravel()) / np.linalg.norm(q1.ravel())
+    assert d < 1e-6, d
+    q3 = ctx.waveforms(torch.tensor(slip, dtype=torch.float32, device="cuda")).cpu().numpy()
+    assert np.array_equal(q2, q3)
 
 
 def test_fp8_tensor_clusters_bitwise():
