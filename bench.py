@@ -410,7 +410,7 @@ def run_ours(args, rank, world, local_rank):
         terms = 3 if split else 1
         achieved = terms * flops / per_launch_s / 1e12
         peak = pk["bf16_tflops_sustained"]
-        roof = {"kernel": "k_tc_gemm (stage-1 per-bin GEMM, tcgen05 kind::f16)", "bound": "tensor",
+        roof = {"kernel": "k_tc_gemm / k_tc_gemm2 (stage-1 per-bin GEMM, tcgen05 kind::f16)", "bound": "tensor",
                 "achieved": round(achieved, 1), "peak": peak, "unit": "TFLOP/s",
                 "frac": round(achieved / peak, 4), "peak_source": pk_kind + " (bf16 sustained)",
                 "traffic": None, "algorithmic_flops_per_launch": flops, "mma_terms": terms,
