@@ -64,7 +64,7 @@ class Opts(ctypes.Structure):
                 ("dt_mode", ctypes.c_int), ("dt", ctypes.c_double),
                 ("max_batch", ctypes.c_int), ("device", ctypes.c_int),
                 ("engine", ctypes.c_int), ("tc_cluster", ctypes.c_int), ("tc_adjoint", ctypes.c_int),
-                ("single_pass", ctypes.c_int), ("tc_pair", ctypes.c_int)]
+                ("single_pass", ctypes.c_int), ("tc_pair", ctypes.c_int), ("tc_fp8_act", ctypes.c_int)]
 
 
 def lib_path() -> str:
@@ -162,7 +162,7 @@ class Context:
 
     def __init__(self, Ns, Ng, No, Nt, prec_g="fp32", prec_p="fp32",
                  dt_mode="backward", dt=1.0, max_batch=1, device=0, engine="auto", tc_cluster=0,
-                 tc_adjoint=False, single_pass=False, tc_pair="auto"):
+                 tc_adjoint=False, single_pass=False, tc_pair="auto", tc_fp8_act=False):
         L = lib()
         o = Opts()
         L.s2w_default_opts(ctypes.byref(o))
@@ -174,6 +174,7 @@ class Context:
         o.tc_adjoint = int(bool(tc_adjoint))
         o.single_pass = int(bool(single_pass))
         o.tc_pair = PAIR[tc_pair]
+        o.tc_fp8_act = int(bool(tc_fp8_act))
         h = ctypes.c_void_p()
         st = L.s2w_create(Ns, Ng, No, Nt, ctypes.byref(o), ctypes.byref(h))
         if st != 0:

@@ -209,20 +209,27 @@ __host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
 // Epilogue warp group g of EPW takes the 64-column chunks g, g + EPW, ...
 // and the 16-column chunks of the tail likewise.  Every lane runs the
 // tcgen05.ld (warp-collective); rows that are not live store nothing.
+// cs: optional per-column scales of this bin (FP8 B operand), cs[t].
 template <int NC>
 __device__ __forceinline__ void tc_store_cols(const TcArgs& a, const float* v, int t0, long long obase, long long ld,
-                                              bool bf, float scale) {
+                                              bool bf, float scale, const float* cs) {
   const int nt = a.T - t0;  // live complex columns from t0 (all NC when >= NC)
   if (bf) {
     __nv_bfloat162* p = a.out_bf + obase + t0 * ld;
 #pragma unroll
     for (int k = 0; k < NC; ++k)
-      if (k < nt) p[k * ld] = __floats2bfloat162_rn(v[2 * k] * scale, v[2 * k + 1] * scale);
+      if (k < nt) {
+        const float sk = cs != nullptr ? scale * cs[t0 + k] : scale;
+        p[k * ld] = __floats2bfloat162_rn(v[2 * k] * sk, v[2 * k + 1] * sk);
+      }
   } else {
     float2* p = a.out + obase + t0 * ld;
 #pragma unroll
     for (int k = 0; k < NC; ++k)
-      if (k < nt) p[k * ld] = make_float2(v[2 * k] * scale, v[2 * k + 1] * scale);
+      if (k < nt) {
+        const float sk = cs != nullptr ? scale * cs[t0 + k] : scale;
+        p[k * ld] = make_float2(v[2 * k] * sk, v[2 * k + 1] * sk);
+      }
   }
 }
 
@@ -234,16 +241,17 @@ __device__ __forceinline__ void tc_epilogue_tile(const TcArgs& a, uint32_t tbase
   const long long obase = a.epi == 0
                               ? static_cast<long long>(l) * a.ld_l + row
                               : ((static_cast<long long>(l) * a.n_kchunks + kc) * a.M_total + row) * a.T;
+  const float* cs = a.col_scale != nullptr ? a.col_scale + static_cast<long long>(l) * a.col_ld : nullptr;
   const int n64 = N / 64 * 64;
   for (int c0 = 64 * g; c0 < n64; c0 += 64 * EPW) {
     float v[64];
     tmem_ld64(tbase + c0, v);
-    if (live && c0 / 2 < a.T) tc_store_cols<32>(a, v, c0 / 2, obase, ld, bf, scale);
+    if (live && c0 / 2 < a.T) tc_store_cols<32>(a, v, c0 / 2, obase, ld, bf, scale, cs);
   }
   for (int c0 = n64 + 16 * g; c0 < N; c0 += 16 * EPW) {
     float v[16];
     tmem_ld16(tbase + c0, v);
-    if (live && c0 / 2 < a.T) tc_store_cols<8>(a, v, c0 / 2, obase, ld, bf, scale);
+    if (live && c0 / 2 < a.T) tc_store_cols<8>(a, v, c0 / 2, obase, ld, bf, scale, cs);
   }
 }
 
@@ -643,22 +651,41 @@ __device__ __forceinline__ void tc_mma2_bf16(uint32_t d_tmem, uint64_t a_desc, u
       : "memory");
 }
 
+// Same with 8-bit operands (kind::f8f6f4; both e4m3 with the f16 instruction
+// descriptor's zero type fields), K = 32 per instruction.
+__device__ __forceinline__ void tc_mma2_f8f8(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                             uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
 // MODE 0: BF16 operands; 1: split (A, A_lo, B, B_lo; three MMAs per K step);
 // 2: FP8 e4m3 A widened to FP16 in shared memory by 4 converter warps per
 // CTA, FP16 B.  Stage layout per CTA: A [A_lo] B-halves [B_lo-halves]
 // [FP8 staging].  FP8: each CTA's staging load completes on its own full[s]
 // (which rank 0's also expects its own and both CTAs' B halves on); the
 // converters of both CTAs then arrive on rank 0's aready[s], which the MMAs
-// wait for.
+// wait for.  3: FP8 e4m3 A and B (kind::f8f6f4, no widening): BK counts
+// bytes = elements, 128-byte rows with 128-byte swizzle, K = 32 per MMA; the
+// per-(bin, 256-row) A scales and per-(bin, column) B scales are applied in
+// the epilogue.
 template <int BK, int MODE>
 __device__ __forceinline__ void tc_gemm2_body(const CUtensorMap* tmA, const CUtensorMap* tmB, const CUtensorMap* tmA2,
                                               const CUtensorMap* tmB2, const TcArgs& a) {
   constexpr bool SPLIT = MODE == 1;
   constexpr bool F8 = MODE == 2;
+  constexpr bool F8F8 = MODE == 3;
+  constexpr int ES = F8F8 ? 1 : 2;        // operand bytes per element in shared memory
+  constexpr int BKB = BK * ES;            // bytes per K-major row of a k-block
+  constexpr int KI = F8F8 ? 32 : 16;      // K per MMA instruction (32 bytes either way)
   constexpr int EPW = F8 ? kEpwF8 : kEpw;
   constexpr int kEpiWarps = 4 * EPW;
   constexpr int kConvWarp0 = 2 + kEpiWarps;
-  constexpr int kA = kBlockM * BK * 2;
+  constexpr int kA = kBlockM * BKB;
   constexpr int kStg = F8 ? kBlockM * BK : 0;  // FP8 staging bytes per stage
   const uint32_t crank = cluster_ctarank();
   const bool lead = crank == 0;
@@ -670,7 +697,7 @@ __device__ __forceinline__ void tc_gemm2_body(const CUtensorMap* tmA, const CUte
   const int n_mma = N > 256 ? N / 256 : 1;
   const int n_mma_cols = N > 256 ? 256 : N;
   const int hrows = n_mma_cols / 2;  // B rows this CTA stages per MMA slice
-  const int hb = hrows * BK * 2;
+  const int hb = hrows * BKB;
   const int bh_bytes = n_mma * hb;
   const int a_bytes = kA * (SPLIT ? 2 : 1);
   const int b_all = bh_bytes * (SPLIT ? 2 : 1);
@@ -687,7 +714,8 @@ __device__ __forceinline__ void tc_gemm2_body(const CUtensorMap* tmA, const CUte
   const int nk_total = (a.K + BK - 1) / BK;
   const int mpairs = (a.m_tiles + 1) / 2;
   const long long units = static_cast<long long>(a.Nb) * mpairs * a.n_kchunks;
-  const uint32_t idesc = F8 ? idesc_f16(2 * kBlockM, n_mma_cols) : idesc_bf16(2 * kBlockM, n_mma_cols);
+  // FP16 (F8) and e4m3 (F8F8, kind::f8f6f4) both encode as type 0
+  const uint32_t idesc = (F8 || F8F8) ? idesc_f16(2 * kBlockM, n_mma_cols) : idesc_bf16(2 * kBlockM, n_mma_cols);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -785,13 +813,17 @@ __device__ __forceinline__ void tc_gemm2_body(const CUtensorMap* tmA, const CUte
           const uint32_t sa = smem_u32(smem + s * stage_bytes);
           const uint32_t sb = sa + a_bytes;
 #pragma unroll
-          for (int k = 0; k < BK / 16; ++k) {
-            const uint64_t ad = sdesc_sw<BK>(sa + k * 32);
+          for (int k = 0; k < BK / KI; ++k) {
+            const uint64_t ad = sdesc_sw<BKB / 2>(sa + k * 32);
             for (int c = 0; c < n_mma; ++c) {
               const uint32_t boff = c * hb + k * 32;
-              const uint64_t bd = sdesc_sw<BK>(sb + boff);
+              const uint64_t bd = sdesc_sw<BKB / 2>(sb + boff);
               const uint32_t dcol = tmem + c * n_mma_cols;
-              tc_mma2_bf16(dcol, ad, bd, idesc, (kb > kb0 || k > 0) ? 1u : 0u);
+              if constexpr (F8F8) {
+                tc_mma2_f8f8(dcol, ad, bd, idesc, (kb > kb0 || k > 0) ? 1u : 0u);
+              } else {
+                tc_mma2_bf16(dcol, ad, bd, idesc, (kb > kb0 || k > 0) ? 1u : 0u);
+              }
               if constexpr (SPLIT) {
                 tc_mma2_bf16(dcol, ad, sdesc_sw<BK>(sb + bh_bytes + boff), idesc, 1u);
                 tc_mma2_bf16(dcol, sdesc_sw<BK>(sa + kA + k * 32), bd, idesc, 1u);
@@ -879,6 +911,12 @@ __global__ void __launch_bounds__(kTcThreadsF8, 1)
 
 template <int BK>
 __global__ void __launch_bounds__(kTcThreads, 1)
+    k_tc_gemm2_f8f8(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
+  tc_gemm2_body<BK, 3>(&tmA, &tmB, nullptr, nullptr, a);
+}
+
+template <int BK>
+__global__ void __launch_bounds__(kTcThreads, 1)
     k_tc_gemm2_split(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                      const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB2,
                      const TcArgs a) {
@@ -944,6 +982,48 @@ __global__ void k_pack_b_f16(const float2* __restrict__ src, int Nb, int T, long
     const long long o0 = (l * N_alloc + 2 * t) * Kc + c;
     dst[o0] = __floats2half2_rn(v.x * sc, -v.y * sc);
     dst[o0 + Kc] = __floats2half2_rn(v.y * sc, v.x * sc);
+  }
+}
+
+// FP8 B operand: one warp per (bin l, complex column t < n_rows / 2); see
+// launch_pack_b_f8.
+__global__ void k_pack_b_f8(const float2* __restrict__ src, int Nb, int T, long long nc, long long s_l,
+                            long long s_t, long long Kc, int N_alloc, int n_rows, float* __restrict__ col_scale,
+                            int col_ld, uint16_t* __restrict__ dst) {
+  const int lane = threadIdx.x & 31;
+  const int nt = n_rows / 2;
+  const long long nw = static_cast<long long>(Nb) * nt;
+  for (long long w = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; w < nw;
+       w += (static_cast<long long>(gridDim.x) * blockDim.x) >> 5) {
+    const long long l = w / nt;
+    const int t = static_cast<int>(w % nt);
+    uint16_t* r0 = dst + (l * N_alloc + 2 * t) * Kc;  // row 2t: (Re, -Im); row 2t + 1: (Im, Re)
+    uint16_t* r1 = r0 + Kc;
+    if (t >= T) {
+      for (long long c = lane; c < Kc; c += 32) r0[c] = r1[c] = 0;
+      if (lane == 0) col_scale[l * col_ld + t] = 0.f;
+      continue;
+    }
+    const float2* x = src + l * s_l + t * s_t;
+    float m = 0.f;
+    for (long long c = lane; c < nc; c += 32) {
+      const float2 v = x[c];
+      m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    // largest power of two sc with m * sc <= 448 (the exponent of 448 / m)
+    float sc = 1.f;
+    if (m > 0.f) {
+      const float r = fmaxf(fminf(448.f / m, 0x1p100f), 0x1p-100f);
+      sc = __uint_as_float(__float_as_uint(r) & 0xff800000u);
+    }
+    for (long long c = lane; c < Kc; c += 32) {
+      const float2 v = c < nc ? x[c] : make_float2(0.f, 0.f);
+      r0[c] = __nv_cvt_float2_to_fp8x2(make_float2(v.x * sc, -v.y * sc), __NV_SATFINITE, __NV_E4M3);
+      r1[c] = __nv_cvt_float2_to_fp8x2(make_float2(v.y * sc, v.x * sc), __NV_SATFINITE, __NV_E4M3);
+    }
+    if (lane == 0) col_scale[l * col_ld + t] = 1.f / sc;
   }
 }
 
@@ -1333,7 +1413,8 @@ cudaError_t tc_encode_3d(CUtensorMap* out, const void* base, long long K, long l
 }
 
 cudaError_t tc_encode_3d_u8(CUtensorMap* out, const void* base, long long K, long long rows, long long nbatch,
-                            int box_rows, int bk) {
+                            int box_rows, int bk, int sw128) {
+  if (sw128 && bk != 128) return cudaErrorInvalidValue;
   if (g_encode == nullptr && resolve_encode() != cudaSuccess) return cudaErrorNotSupported;
   const cuuint64_t dims[3] = {static_cast<cuuint64_t>(K), static_cast<cuuint64_t>(rows),
                               static_cast<cuuint64_t>(nbatch)};
@@ -1341,8 +1422,8 @@ cudaError_t tc_encode_3d_u8(CUtensorMap* out, const void* base, long long K, lon
   const cuuint32_t box[3] = {static_cast<cuuint32_t>(bk), static_cast<cuuint32_t>(box_rows), 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = g_encode(out, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<void*>(base), dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, sw128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
@@ -1374,7 +1455,9 @@ size_t tc_smem_bytes(int N, int stages, int a_lo, int b_lo, int fp8, int mt) {
 namespace {
 // Two-SM form: per CTA, one A tile and half of the B tile (each part
 // doubled when split), plus the byte staging of an FP8 A tile.
+// fp8 = 2: FP8 A and B read directly (128-byte rows of 128 K elements).
 int tc2_stage_bytes(int N, int split, int fp8) {
+  if (fp8 == 2) return (kBlockM + N / 2) * 128;
   const int bk = tc_block_k(N, split, 1);
   return (kBlockM * bk * 2 + (N / 2) * bk * 2) * (1 + split) + (fp8 ? kBlockM * bk : 0);
 }
@@ -1385,9 +1468,9 @@ constexpr int kSmemOptIn = 227 * 1024;
 }  // namespace
 
 int tc_stages_pair(int N, int split, int fp8) {
-  // FP8 stages carry the staging too: they may use all of the opt-in shared
+  // FP8 stages that carry the staging too may use all of the opt-in shared
   // memory (four 56 KB stages at N = 512)
-  const int budget = fp8 ? kSmemOptIn - 1024 - 8 * (3 * 8 + 2) - 16 : kSmemBudget;
+  const int budget = fp8 == 1 ? kSmemOptIn - 1024 - 8 * (3 * 8 + 2) - 16 : kSmemBudget;
   int s = budget / tc2_stage_bytes(N, split, fp8);
   if (s > 8) s = 8;
   return s;
@@ -1454,10 +1537,13 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
     if (a.m_pair || a.cluster > 1 || a.N % 32 != 0) return cudaErrorInvalidValue;
     const int sp = a.a_lo;
     const int f8 = a.a_fp8;
-    const size_t smem = tc2_smem_bytes(a.N, a.stages, sp, f8);
+    const bool f8f8 = a.a_fp8 && a.b_fp8;
+    if (a.b_fp8 && (!a.a_fp8 || a.col_scale == nullptr)) return cudaErrorInvalidValue;
+    const size_t smem = tc2_smem_bytes(a.N, a.stages, sp, f8f8 ? 2 : f8);
     if (smem > static_cast<size_t>(kSmemOptIn)) return cudaErrorInvalidValue;
     const bool bk64 = tc_block_k(a.N, sp, 1) == 64;
-    const void* kfn = f8   ? (bk64 ? reinterpret_cast<const void*>(k_tc_gemm2_f8<64>)
+    const void* kfn = f8f8 ? reinterpret_cast<const void*>(k_tc_gemm2_f8f8<128>)
+                      : f8 ? (bk64 ? reinterpret_cast<const void*>(k_tc_gemm2_f8<64>)
                                    : reinterpret_cast<const void*>(k_tc_gemm2_f8<32>))
                       : sp ? (bk64 ? reinterpret_cast<const void*>(k_tc_gemm2_split<64>)
                                    : reinterpret_cast<const void*>(k_tc_gemm2_split<32>))
@@ -1473,7 +1559,7 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cfg.blockDim = dim3(f8 ? kTcThreadsF8 : kTcThreads);
+    cfg.blockDim = dim3(f8 && !f8f8 ? kTcThreadsF8 : kTcThreads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cfg.gridDim = dim3(static_cast<unsigned>((num_sms / 2) * 2));
@@ -1485,7 +1571,9 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
     const long long pu = static_cast<long long>(a.Nb) * ((a.m_tiles + 1) / 2) * a.n_kchunks;
     if (nclusters > pu) nclusters = pu;
     cfg.gridDim = dim3(static_cast<unsigned>(nclusters * 2));
-    if (f8) {
+    if (f8f8) {
+      e = cudaLaunchKernelEx(&cfg, k_tc_gemm2_f8f8<128>, tmA, tmB, a);
+    } else if (f8) {
       if (bk64)
         e = cudaLaunchKernelEx(&cfg, k_tc_gemm2_f8<64>, tmA, tmB, a);
       else
@@ -1504,6 +1592,7 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
   }
+  if (a.b_fp8) return cudaErrorInvalidValue;  // FP8 B: two-SM form only
   const int CL = a.cluster < 1 ? 1 : a.cluster;
   if (CL != 1 && CL != 2 && CL != 4) return cudaErrorInvalidValue;
   if (CL > 1 && (a.N / CL < 8 || (a.N / CL) % 8 != 0 || a.N / CL > 256)) return cudaErrorInvalidValue;
@@ -1593,6 +1682,20 @@ cudaError_t launch_pack_b(const float2* src, int Nb, int T, long long nc, long l
   if (total <= 0) return cudaSuccess;
   k_pack_b<<<grid_for_tc(total), 256, 0, st>>>(src, Nb, T, nc, s_l, s_t, c0, Kc, N_alloc, conj,
                                                static_cast<__nv_bfloat162*>(hi), static_cast<__nv_bfloat162*>(lo));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_b_f8(const float2* src, int Nb, int T, long long nc, long long s_l, long long s_t,
+                             long long Kc, int N_alloc, int n_rows, float* col_scale, int col_ld, void* dst,
+                             cudaStream_t st) {
+  if (n_rows % 2 != 0 || n_rows > N_alloc || 2 * T > n_rows || nc > Kc || col_ld < n_rows / 2)
+    return cudaErrorInvalidValue;
+  const long long warps = static_cast<long long>(Nb) * (n_rows / 2);
+  if (warps <= 0) return cudaSuccess;
+  long long blocks = (warps + 7) / 8;
+  if (blocks > 152LL * 16) blocks = 152LL * 16;
+  k_pack_b_f8<<<static_cast<unsigned>(blocks), 256, 0, st>>>(src, Nb, T, nc, s_l, s_t, Kc, N_alloc, n_rows,
+                                                                col_scale, col_ld, static_cast<uint16_t*>(dst));
   return cudaGetLastError();
 }
 

@@ -97,7 +97,9 @@ struct s2w_ctx {
   void* tc_bp1_lo = nullptr;  // split: low-order parts of tc_bp1, tc_vhat, tc_p2
   void* tc_vhat_lo = nullptr;
   void* tc_p2_lo = nullptr;
-  void* tc_bp1 = nullptr;   // [Nb][tc_n1max][2 Ns_pad] bf16
+  void* tc_bp1 = nullptr;   // [Nb][tc_n1max][2 Ns_pad] bf16 (FP8 activations: bytes)
+  bool tc_f8act = false;    // FP8 operator x FP8 activations on stage 1 (opts.tc_fp8_act)
+  float* tc_colscale = nullptr;  // [Nb][tc_n1max / 2] per-(bin, rupture) scales of the FP8 B operand
   void* tc_mhat = nullptr;  // [Nb][b][Ng] BF16 pairs (complex FP32 when split)
   void* tc_vhat = nullptr;  // [Nb][tc_bsub][Ng_pad2] bf16 pairs
   float2* tc_part = nullptr;  // [Nb][nkc][b][No] complex FP32
@@ -279,7 +281,7 @@ void free_all(s2w_ctx* c) {
                 c->ws_vhat, c->ws_part, c->ws_q, c->ws_seafloor, c->d_status, c->tc_bp1, c->ws_rhat, c->ws_gpart, c->ws_resid, c->ws_d, c->ws_loss,
                 c->tc_mhat, c->tc_vhat, c->tc_part, c->tc_p2, c->tc_T, c->tc_bp1_lo, c->tc_vhat_lo, c->tc_p2_lo,
                 c->tc_gT, c->tc_gT_lo, c->tc_pT, c->tc_pT_lo, c->tc_rb, c->tc_rb_lo, c->tc_ub, c->tc_ub_lo,
-                c->tc_ghat, c->ws_lens, c->d_amax, c->tc_T_lo, c->tc_Ta, c->tc_Ta_lo};
+                c->tc_ghat, c->ws_lens, c->d_amax, c->tc_T_lo, c->tc_Ta, c->tc_Ta_lo, c->tc_colscale};
   for (void* p : ps)
     if (p) cudaFree(p);
 }
@@ -462,7 +464,12 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
   const long long K2 = 2 * ctx->Ng_pad2;
   for (int b0 = 0; b0 < B; b0 += ctx->tc_bsub) {
     const int Bs = std::min(ctx->tc_bsub, B - b0);
-    int N1 = static_cast<int>(round_up(2 * Bs, 16));
+    const int m1 = static_cast<int>((Ng + 127) / 128);
+    const int sp = ctx->tc_split ? 1 : 0;
+    const bool f8 = ctx->opts.prec_g == S2W_PREC_FP8_E4M3;
+    // FP8 x FP8 stage 1 (two-SM tiles: N % 32, at least two M tiles)
+    const bool f8f8 = f8 && ctx->tc_f8act && m1 >= 2;
+    int N1 = static_cast<int>(round_up(2 * Bs, f8f8 ? 32 : 16));
     if (N1 > 256) N1 = 512;
     {
       StageTimer t(ctx, 0, st);
@@ -470,21 +477,53 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
                           static_cast<int>(Nt), ctx->tw, ctx->ws_shat, Bs * Ns_pad, Ns, Ns_pad, st,
                           ctx->cur_lens ? ctx->cur_lens + b0 : nullptr));
     }
-    const int sp = ctx->tc_split ? 1 : 0;
-    const bool f8 = ctx->opts.prec_g == S2W_PREC_FP8_E4M3;
     {
-      StageTimer t(ctx, 6, st, f8 ? 2 : 1);
-      if (f8)  // FP16 operand for the FP16 MMAs of the FP8 path, scaled by a power of two from its amax
+      StageTimer t(ctx, 6, st, f8 && !f8f8 ? 2 : 1);
+      if (f8f8)  // e4m3 operand, one power-of-two scale per (bin, rupture)
+        CK(launch_pack_b_f8(ctx->ws_shat, static_cast<int>(Nb), Bs, Ns_pad, static_cast<long long>(Bs) * Ns_pad,
+                            Ns_pad, Ns_pad, ctx->tc_n1max, N1, ctx->tc_colscale, ctx->tc_n1max / 2, ctx->tc_bp1,
+                            st));
+      else if (f8)  // FP16 operand for the FP16 MMAs of the FP8 path, scaled by a power of two from its amax
         CK(launch_pack_b_f16(ctx->ws_shat, static_cast<int>(Nb), Bs, Ns_pad, static_cast<long long>(Bs) * Ns_pad,
                              Ns_pad, Ns_pad, ctx->tc_n1max, ctx->d_amax, ctx->tc_bp1, st));
       else
         CK(launch_pack_b(ctx->ws_shat, static_cast<int>(Nb), Bs, Ns_pad, static_cast<long long>(Bs) * Ns_pad, Ns_pad,
                          0, Ns_pad, ctx->tc_n1max, 0, ctx->tc_bp1, ctx->tc_bp1_lo, st));
     }
-    {
+    if (f8f8) {
+      StageTimer t(ctx, 1, st);
+      CUtensorMap ta, tb;
+      // byte maps with 128-byte swizzle: K blocks of 128 e4m3 elements
+      CK(tc_encode_3d_u8(&ta, ctx->G, K1, Ng, Nb, 128, 128, 1));
+      CK(tc_encode_3d_u8(&tb, ctx->tc_bp1, K1, ctx->tc_n1max, Nb, (N1 > 256 ? 256 : N1) / 2, 128, 1));
+      TcArgs a{};
+      a.N = N1;
+      a.K = K1;
+      a.M_total = static_cast<int>(Ng);
+      a.Nb = static_cast<int>(Nb);
+      a.m_tiles = m1;
+      a.n_kchunks = 1;
+      a.kblocks_per_chunk = (K1 + 127) / 128;
+      a.cta2 = 1;
+      a.stages = tc_stages_pair(N1, 0, 2);
+      a.tmem_cols = N1 <= 32 ? 32 : (N1 <= 64 ? 64 : (N1 <= 128 ? 128 : (N1 <= 256 ? 256 : 512)));
+      a.a_fp8 = 1;
+      a.b_fp8 = 1;
+      a.row_scale = ctx->G_scale;
+      a.nblk = ctx->nblk;
+      a.col_scale = ctx->tc_colscale;
+      a.col_ld = ctx->tc_n1max / 2;
+      a.cluster = 1;
+      a.epi = 0;
+      a.T = Bs;
+      a.out_bf = static_cast<__nv_bfloat162*>(ctx->tc_mhat);
+      a.ld_l = static_cast<long long>(Bs) * Ng;
+      a.ld_t = Ng;
+      a.status = ctx->d_status;
+      CK(launch_tc_gemm(ta, tb, a, ctx->num_sms, st));
+    } else {
       StageTimer t(ctx, 1, st);
       CUtensorMap ta, tb, ta2, tb2;
-      const int m1 = static_cast<int>((Ng + 127) / 128);
       const int cl = fit_cluster(ctx->tc_cl1, N1, m1);
       TcArgs a{};
       const int brows = tc_shape(a, N1, m1, cl, sp, f8 ? 1 : 0, ctx->tc_pair);
@@ -603,6 +642,7 @@ void s2w_default_opts(s2w_opts* o) {
   o->tc_adjoint = 0;
   o->single_pass = 0;
   o->tc_pair = S2W_PAIR_AUTO;
+  o->tc_fp8_act = 0;
 }
 
 const char* s2w_status_string(int s) {
@@ -648,6 +688,10 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
     return fail(nullptr, S2W_ERR_ARG, "single_pass=%d: 0 or 1", o.single_pass);
   if (o.tc_pair != S2W_PAIR_AUTO && o.tc_pair != S2W_PAIR_ON && o.tc_pair != S2W_PAIR_OFF)
     return fail(nullptr, S2W_ERR_ARG, "tc_pair=%d: S2W_PAIR_AUTO, _ON or _OFF", o.tc_pair);
+  if (o.tc_fp8_act != 0 && o.tc_fp8_act != 1)
+    return fail(nullptr, S2W_ERR_ARG, "tc_fp8_act=%d: 0 or 1", o.tc_fp8_act);
+  if (o.tc_fp8_act && o.prec_g != S2W_PREC_FP8_E4M3)
+    return fail(nullptr, S2W_ERR_ARG, "tc_fp8_act needs prec_g = S2W_PREC_FP8_E4M3");
   if (o.single_pass && (Nt > 256 || o.engine == S2W_ENGINE_TENSOR || o.tc_adjoint))
     return fail(nullptr, S2W_ERR_UNSUPPORTED, "single_pass: stream engine only, Nt <= 256, no tc_adjoint");
   if (o.engine == S2W_ENGINE_TENSOR && 2 * No > 256)
@@ -734,7 +778,9 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
     ctx->tc_cl1 = o.tc_cluster > 0 ? o.tc_cluster : kDefaultCluster;
     ctx->tc_cl2 = o.tc_cluster > 0 ? o.tc_cluster : kDefaultCluster;
     ctx->tc_pair = o.tc_pair == S2W_PAIR_ON ? 1 : (o.tc_pair == S2W_PAIR_OFF ? 0 : kDefaultPair);
-    ctx->tc_n1max = static_cast<int>(round_up(2 * ctx->tc_bsub, 16));
+    ctx->tc_f8act = o.tc_fp8_act != 0;
+    // FP8 B rows come in multiples of 32 (N % 32 for the two-SM tiles)
+    ctx->tc_n1max = static_cast<int>(round_up(2 * ctx->tc_bsub, ctx->tc_f8act ? 32 : 16));
     if (ctx->tc_n1max > 256) ctx->tc_n1max = 512;
     ctx->tc_n2 = static_cast<int>(round_up(2 * No, 16));
     ctx->Ng_pad2 = round_up(Ng, 8);
@@ -751,6 +797,9 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
     const bool sp = ctx->tc_split;
     if ((e = dalloc(&ctx->tc_bp1, 2ull * Nb * ctx->tc_n1max * 2 * ctx->Ns_pad)) != cudaSuccess)
       return bad(e, "tensor stage-1 operand");
+    if (ctx->tc_f8act &&
+        (e = dalloc(&ctx->tc_colscale, sizeof(float) * Nb * (ctx->tc_n1max / 2))) != cudaSuccess)
+      return bad(e, "FP8 activation scales");
     ctx->tc_adj = o.tc_adjoint != 0;
     // FP32 seafloor spectra for the split path, and for the adjoint's what
     const bool mhat32 = sp || ctx->tc_adj;

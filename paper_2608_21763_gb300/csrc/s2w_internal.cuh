@@ -226,6 +226,10 @@ struct TcArgs {
   const unsigned* b_amax;  // FP16 B operand: amax (float bits) that set its power-of-two scale
   int m_pair;              // 1: two M tiles per unit sharing each B tile (N <= 256, cluster 1, not FP8;
                            //    tmem_cols >= 2 N, stages from tc_stages_for(..., mt = 2))
+  int b_fp8;               // 1 (with a_fp8 and cta2): B is FP8 e4m3 too (launch_pack_b_f8), byte tensor
+                           //    maps with 128-byte swizzle, kind::f8f6f4 MMAs, K blocks of 128 bytes
+  const float* col_scale;  // optional per-(bin, complex column) scale: col_scale[l * col_ld + t]
+  int col_ld;
   int cta2;                // 1: two-SM MMAs, a CTA pair per M = 256 tile, each staging half of B
                            //    (N % 32 == 0, cluster 1, no m_pair; B box rows = min(N, 256) / 2,
                            //    K blocks tc_block_k(N, split, 1), stages from tc_stages_pair)
@@ -239,9 +243,10 @@ cudaError_t tc_encode_3d(CUtensorMap* out, const void* base, long long K, long l
 int tc_block_k(int N, int split = 0, int pair = 0);
 int tc_stages_for(int N, int a_lo = 0, int b_lo = 0, int fp8 = 0, int mt = 1);
 int tc_stages_pair(int N, int split, int fp8 = 0);
-// Byte tensor map for FP8 A tiles: [nbatch][rows][K] bytes, box bk x box_rows, no swizzle.
+// Byte tensor map for FP8 A tiles: [nbatch][rows][K] bytes, box bk x box_rows, no swizzle
+// (sw128: 128-byte swizzle, bk = 128, for operands the MMAs read directly).
 cudaError_t tc_encode_3d_u8(CUtensorMap* out, const void* base, long long K, long long rows, long long nbatch,
-                            int box_rows, int bk);
+                            int box_rows, int bk, int sw128 = 0);
 // tmA2 / tmB2: tensor maps of the low-order parts when a.a_lo / a.b_lo
 cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const TcArgs& a, int num_sms,
                            cudaStream_t st, const CUtensorMap* tmA2 = nullptr, const CUtensorMap* tmB2 = nullptr);
@@ -261,6 +266,14 @@ __device__ __forceinline__ float f16_unscale(unsigned amax_bits) { return 1.f / 
 // Plain-embedding B operand as FP16 (k_pack_b layout, c0 = 0, no lo part):
 // measures amax of the source first (amax: one device word), then packs x *
 // f16_scale(amax).
+// FP8 e4m3 B operand of the plain real embedding, rows 2t / 2t+1 of
+// dst[l][N_alloc][2 Kc] bytes for t < n_rows / 2 (rows of t >= T zero, as is
+// the K padding c >= nc), each pair of rows scaled by the power of two that
+// brings its amax to at most 448 (e4m3's largest finite value), rounded to
+// nearest even with saturation; col_scale[l * col_ld + t] = 1 / that scale.
+cudaError_t launch_pack_b_f8(const float2* src, int Nb, int T, long long nc, long long s_l, long long s_t,
+                             long long Kc, int N_alloc, int n_rows, float* col_scale, int col_ld, void* dst,
+                             cudaStream_t st);
 cudaError_t launch_pack_b_f16(const float2* src, int Nb, int T, long long nc, long long s_l, long long s_t,
                               long long Kc, int N_alloc, unsigned* amax, void* dst, cudaStream_t st);
 // A operand dst[(l*rows_total + r0 + r)*Kc + c0 + c] (BF16 pairs, hi and

@@ -7,13 +7,13 @@ import oracle
 
 def make_context(s2w, geom, Nt, prec_g="fp32", prec_p="fp32", dt_mode="backward",
                  max_batch=1, chunk=4096, order=None, engine="auto", tc_cluster=0, tc_adjoint=False,
-                 single_pass=False, tc_pair="auto"):
+                 single_pass=False, tc_pair="auto", tc_fp8_act=False):
     """Context with both operators loaded from the generator, in row chunks
     (optionally in a permuted chunk order)."""
     Ng = geom.Ng
     ctx = s2w.Context(geom.Ns, Ng, geom.No, Nt, prec_g=prec_g, prec_p=prec_p,
                       dt_mode=dt_mode, max_batch=max_batch, engine=engine, tc_cluster=tc_cluster,
-                      tc_adjoint=tc_adjoint, single_pass=single_pass, tc_pair=tc_pair)
+                      tc_adjoint=tc_adjoint, single_pass=single_pass, tc_pair=tc_pair, tc_fp8_act=tc_fp8_act)
     starts = list(range(0, Ng, chunk))
     if order is not None:
         starts = [starts[i] for i in order]

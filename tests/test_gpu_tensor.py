@@ -260,6 +260,45 @@ def test_fp8_two_sm_pairs_match_single_cta(Ng, B):
     assert np.array_equal(q2, q3)
 
 
+@pytest.mark.parametrize("Ng,B", [(700, 3), (700, 48), (600, 300)])
+def test_fp8_activations_on_tensor_engine(Ng, B):
+    """FP8 operator x FP8 activations (tc_fp8_act: slip spectra rounded to
+    e4m3 with one power-of-two scale per (bin, rupture); kind::f8f6f4 MMAs on
+    two-SM tiles): against the oracle at the FP8 bar, and against the
+    FP16-activation FP8 path within the activation rounding, <= 2^-4 relative
+    per entry, as a fraction of the window norm (measured up to ~4e-2: the
+    products' rounding errors do not cancel like the products do); B = 3 and
+    48 pad N to 32 and 96 columns, B = 300 runs an N = 512 and an N = 96
+    sub-batch."""
+    geom = compact_box(24, Ng, 6, seed=Ng + B + 7)
+    rng = np.random.default_rng(B + 7)
+    Nt = 64
+    slip = rng.standard_normal((B, geom.Ns, Nt))
+    slip[:, :, Nt // 2:] = 0
+    st = torch.tensor(slip, dtype=torch.float32, device="cuda")
+    G = geom.greens_rows(0, geom.Ng, Nt)
+    P = geom.adjoint_cols(0, geom.Ng, Nt)
+    q_ref = oracle.waveforms(G, P, slip)
+    wn, kappa = window_norms(G, P, slip)
+    out = {}
+    for act in (False, True):
+        ctx = make_context(s2w, geom, Nt, prec_g="fp8", max_batch=B, chunk=256, engine="tensor", tc_fp8_act=act)
+        out[act] = ctx.waveforms(st).cpu().numpy()
+        ctx.sync()
+        assert_parity(out[act], q_ref, wn, kappa, tol=1e-1, label=f"fp8 act={act} B={B}")
+    d = np.linalg.norm((out[True] - out[False]).reshape(B, -1), axis=1)
+    assert np.all(d <= 2.0 ** -4 * wn), d / wn
+    # deterministic
+    q2 = ctx.waveforms(st).cpu().numpy()
+    assert np.array_equal(out[True], q2)
+
+
+def test_fp8_activations_reject_other_precisions():
+    geom = compact_box(8, 300, 2, seed=5)
+    with pytest.raises(s2w.S2WError):
+        make_context(s2w, geom, 32, prec_g="bf16", max_batch=4, tc_fp8_act=True)
+
+
 def test_fp8_tensor_clusters_bitwise():
     geom = compact_box(24, 700, 6, seed=63)
     q1, q_ref, wn, _, _ = run_case(geom, 64, 40, seed=64, prec="fp8", tc_cluster=1, chunk=256)
