@@ -209,8 +209,8 @@ __host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
 // Epilogue warp group g of EPW takes the 64-column chunks g, g + EPW, ...
 // and the 16-column chunks of the tail likewise.  Every lane runs the
 // tcgen05.ld (warp-collective); rows that are not live store nothing.
-// cs: optional per-column scales of this bin (FP8 B operand), cs[t].
-template <int NC>
+// CS: per-column scales of this bin (FP8 B operand), cs[t].
+template <int NC, bool CS>
 __device__ __forceinline__ void tc_store_cols(const TcArgs& a, const float* v, int t0, long long obase, long long ld,
                                               bool bf, float scale, const float* cs) {
   const int nt = a.T - t0;  // live complex columns from t0 (all NC when >= NC)
@@ -219,7 +219,7 @@ __device__ __forceinline__ void tc_store_cols(const TcArgs& a, const float* v, i
 #pragma unroll
     for (int k = 0; k < NC; ++k)
       if (k < nt) {
-        const float sk = cs != nullptr ? scale * cs[t0 + k] : scale;
+        const float sk = CS ? scale * cs[t0 + k] : scale;
         p[k * ld] = __floats2bfloat162_rn(v[2 * k] * sk, v[2 * k + 1] * sk);
       }
   } else {
@@ -227,13 +227,13 @@ __device__ __forceinline__ void tc_store_cols(const TcArgs& a, const float* v, i
 #pragma unroll
     for (int k = 0; k < NC; ++k)
       if (k < nt) {
-        const float sk = cs != nullptr ? scale * cs[t0 + k] : scale;
+        const float sk = CS ? scale * cs[t0 + k] : scale;
         p[k * ld] = make_float2(v[2 * k] * sk, v[2 * k + 1] * sk);
       }
   }
 }
 
-template <int EPW>
+template <int EPW, bool CS = false>
 __device__ __forceinline__ void tc_epilogue_tile(const TcArgs& a, uint32_t tbase, int N, int g, int l, int kc,
                                                  int row, bool live, float scale) {
   const bool bf = a.epi == 0 && a.out_bf != nullptr;
@@ -241,17 +241,17 @@ __device__ __forceinline__ void tc_epilogue_tile(const TcArgs& a, uint32_t tbase
   const long long obase = a.epi == 0
                               ? static_cast<long long>(l) * a.ld_l + row
                               : ((static_cast<long long>(l) * a.n_kchunks + kc) * a.M_total + row) * a.T;
-  const float* cs = a.col_scale != nullptr ? a.col_scale + static_cast<long long>(l) * a.col_ld : nullptr;
+  const float* cs = CS ? a.col_scale + static_cast<long long>(l) * a.col_ld : nullptr;
   const int n64 = N / 64 * 64;
   for (int c0 = 64 * g; c0 < n64; c0 += 64 * EPW) {
     float v[64];
     tmem_ld64(tbase + c0, v);
-    if (live && c0 / 2 < a.T) tc_store_cols<32>(a, v, c0 / 2, obase, ld, bf, scale, cs);
+    if (live && c0 / 2 < a.T) tc_store_cols<32, CS>(a, v, c0 / 2, obase, ld, bf, scale, cs);
   }
   for (int c0 = n64 + 16 * g; c0 < N; c0 += 16 * EPW) {
     float v[16];
     tmem_ld16(tbase + c0, v);
-    if (live && c0 / 2 < a.T) tc_store_cols<8>(a, v, c0 / 2, obase, ld, bf, scale, cs);
+    if (live && c0 / 2 < a.T) tc_store_cols<8, CS>(a, v, c0 / 2, obase, ld, bf, scale, cs);
   }
 }
 
@@ -880,7 +880,7 @@ __device__ __forceinline__ void tc_gemm2_body(const CUtensorMap* tmA, const CUte
       float scale = 1.f;
       if (a.row_scale != nullptr && live) scale = a.row_scale[static_cast<long long>(l) * a.nblk + row / 256];
       if (a.b_amax != nullptr) scale *= f16_unscale(*a.b_amax);  // undo the FP16 B operand's power-of-two scale
-      tc_epilogue_tile<EPW>(a, tbase, N, g, l, kc, row, live, scale);
+      tc_epilogue_tile<EPW, F8F8>(a, tbase, N, g, l, kc, row, live, scale);  // F8F8: per-column B scales
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive_cluster(acc_empty0);
@@ -1083,10 +1083,18 @@ __host__ __device__ constexpr int rt_threads(bool split) { return 32 * (2 + 4 * 
 // K step (hi hi, hi lo, lo hi), and the epilogue writes hi + lo velocity
 // spectra (the split stage-2 A operand); 32-element K blocks (64-byte
 // swizzle) keep the doubled slots inside shared memory.
-template <bool SPLIT>
+// PAIR (BF16 only): two-SM tiles as in tc_gemm2_body.  A cluster of two
+// CTAs takes two consecutive 128-signal tiles of one rupture as one M = 256
+// tile; each CTA fills its own signals and stages half of every 256-row
+// slice of T (rank r: rows r 128 .. of the slice), so the T bytes staged and
+// read per CTA halve.  Rank 0 issues the MMAs; both CTAs' fill warps arrive
+// on rank 0's afull, both CTAs' T loads complete on rank 0's tfull, and the
+// MMA commits reach tempty / afree / acc_full of both CTAs by multicast.
+template <bool SPLIT, bool PAIR>
 __global__ void __launch_bounds__(rt_threads(SPLIT), 1)
     k_tc_retransform(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmT2,
                      const TcRtArgs a) {
+  static_assert(!(SPLIT && PAIR), "two-SM retransform: BF16 only");
   constexpr int BK = SPLIT ? 32 : 64;        // K elements per k-block
   constexpr int EPW = rt_epw(SPLIT);
   constexpr int kFill0 = 2 + 4 * EPW;        // first fill warp
@@ -1100,8 +1108,13 @@ __global__ void __launch_bounds__(rt_threads(SPLIT), 1)
   const int KB = K / BK;          // k-blocks per tile
   const int n_half = K > 256 ? 2 : 1;   // MMA column halves (256 output columns each)
   const int ncols = K > 256 ? 256 : K;
-  const int t_part = ncols * BK * 2;
+  const int trows = PAIR ? ncols / 2 : ncols;  // T rows this CTA stages per half
+  const int t_part = trows * BK * 2;
   const int t_slot = t_part * (SPLIT ? 2 : 1);
+  const uint32_t crank = PAIR ? cluster_ctarank() : 0u;
+  const bool lead = crank == 0;
+  const long long cid = PAIR ? static_cast<long long>(cluster_id_x()) : static_cast<long long>(blockIdx.x);
+  const long long ncl = PAIR ? static_cast<long long>(cluster_count_x()) : static_cast<long long>(gridDim.x);
   // one A slot per fill warp: with KB a power of two, slot s = n % RA is only
   // ever filled by one warp (k-blocks kb = s mod KB, or s when KB >= RA), one
   // ring lap apart, so no parity wait can run a phase ahead
@@ -1119,13 +1132,19 @@ __global__ void __launch_bounds__(rt_threads(SPLIT), 1)
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const int mtiles = (a.Ng + kBlockM - 1) / kBlockM;
-  const long long tiles = static_cast<long long>(a.Bs) * mtiles;
-  const uint32_t idesc = idesc_bf16(kBlockM, ncols);
+  const int mgroups = PAIR ? (mtiles + 1) / 2 : mtiles;  // M tiles per unit: 2 (pair) or 1
+  const long long tiles = static_cast<long long>(a.Bs) * mgroups;
+  // unit u -> rupture b and this CTA's first signal i0
+  auto unit_tile = [&](long long u, int& b, int& i0) {
+    b = static_cast<int>(u / mgroups);
+    i0 = (static_cast<int>(u % mgroups) * (PAIR ? 2 : 1) + static_cast<int>(crank)) * kBlockM;
+  };
+  const uint32_t idesc = idesc_bf16(PAIR ? 2 * kBlockM : kBlockM, ncols);
   const uint32_t tmem_cols = K <= 64 ? 64 : (K <= 128 ? 128 : (K <= 256 ? 256 : 512));
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < RA; ++s) {
-      mbar_init(afull + s, 1);  // one fill warp per k-block
+      mbar_init(afull + s, PAIR ? 2 : 1);  // one fill warp per k-block (of each CTA)
       mbar_init(afree + s, 1);
     }
     for (int s = 0; s < RT; ++s) {
@@ -1133,15 +1152,21 @@ __global__ void __launch_bounds__(rt_threads(SPLIT), 1)
       mbar_init(tempty + s, 1);
     }
     mbar_init(acc_full, 1);
-    mbar_init(acc_empty, 4 * EPW);
+    mbar_init(acc_empty, (PAIR ? 2 : 1) * 4 * EPW);
     fence_mbar_init();
   }
   if (warp == 1) {
-    tmem_alloc(tmem_holder, tmem_cols);
-    tmem_relinquish();
+    if constexpr (PAIR) {
+      tmem_alloc2(tmem_holder, tmem_cols);
+      tmem_relinquish2();
+    } else {
+      tmem_alloc(tmem_holder, tmem_cols);
+      tmem_relinquish();
+    }
   }
   tc_fence_before();
   __syncthreads();
+  if constexpr (PAIR) cluster_sync_all();  // both CTAs' barriers and tensor memory exist
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
 
@@ -1150,7 +1175,8 @@ __global__ void __launch_bounds__(rt_threads(SPLIT), 1)
     if (lane == 0) {
       int it = 0;
       bool ok = true;
-      for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+      const uint32_t tfull0 = PAIR ? cluster_addr(tfull, 0) : 0u;
+      for (long long t = cid; t < tiles && ok; t += ncl) {
         for (int kb = 0; kb < KB && ok; ++kb) {
           for (int h = 0; h < n_half; ++h, ++it) {
             const int s = it % RT;
@@ -1158,21 +1184,41 @@ __global__ void __launch_bounds__(rt_threads(SPLIT), 1)
               ok = false;
               break;
             }
-            mbar_arrive_expect_tx(tfull + s, t_slot);
-            tma_load_3d(sT + s * t_slot, &tmT, kb * BK, h * ncols, 0, tfull + s);
-            if constexpr (SPLIT) tma_load_3d(sT + s * t_slot + t_part, &tmT2, kb * BK, h * ncols, 0, tfull + s);
+            if constexpr (PAIR) {
+              if (lead) mbar_arrive_expect_tx(tfull + s, 2u * static_cast<uint32_t>(t_slot));
+              tma_load_3d_pair(sT + s * t_slot, &tmT, kb * BK, h * ncols + static_cast<int>(crank) * trows, 0,
+                               tfull0 + 8u * static_cast<uint32_t>(s));
+            } else {
+              mbar_arrive_expect_tx(tfull + s, t_slot);
+              tma_load_3d(sT + s * t_slot, &tmT, kb * BK, h * ncols, 0, tfull + s);
+              if constexpr (SPLIT) tma_load_3d(sT + s * t_slot + t_part, &tmT2, kb * BK, h * ncols, 0, tfull + s);
+            }
           }
         }
       }
-      for (int kk = (it > RT ? it - RT : 0); kk < it; ++kk)
-        mbar_wait_bounded(tfull + kk % RT, (kk / RT) & 1, a.status, DEV_ERR_TIMEOUT_FULL);
+      if (lead)
+        for (int kk = (it > RT ? it - RT : 0); kk < it; ++kk)
+          mbar_wait_bounded(tfull + kk % RT, (kk / RT) & 1, a.status, DEV_ERR_TIMEOUT_FULL);
+      if constexpr (PAIR)  // the MMAs' releases of the last T slots land in both CTAs before anyone leaves
+        for (int kk = (it > RT ? it - RT : 0); kk < it; ++kk)
+          mbar_wait_bounded(tempty + kk % RT, (kk / RT) & 1, a.status, DEV_ERR_TIMEOUT_EMPTY);
     }
   } else if (warp == 1) {
-    if (lane == 0) {
+    if (lane == 0 && lead) {
+      // arrivals from the peer CTA (PAIR) need cluster-scope acquire
+      auto wait_x = [&](uint64_t* bar, uint32_t parity, int code) {
+        return PAIR ? mbar_wait_bounded_cl(bar, parity, a.status, code) : mbar_wait_bounded(bar, parity, a.status, code);
+      };
+      auto commit = [&](uint64_t* bar) {
+        if constexpr (PAIR)
+          tc_commit2_mc(bar, 0x3);
+        else
+          tc_commit(bar);
+      };
       int it = 0, tl = 0;
       bool ok = true;
-      for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++tl) {
-        if (tl > 0 && !mbar_wait_bounded(acc_empty, (tl - 1) & 1, a.status, DEV_ERR_TIMEOUT_MMA)) {
+      for (long long t = cid; t < tiles && ok; t += ncl, ++tl) {
+        if (tl > 0 && !wait_x(acc_empty, (tl - 1) & 1, DEV_ERR_TIMEOUT_MMA)) {
           ok = false;
           break;
         }
@@ -1180,7 +1226,7 @@ __global__ void __launch_bounds__(rt_threads(SPLIT), 1)
         for (int kb = 0; kb < KB && ok; ++kb) {
           const long long n = static_cast<long long>(tl) * KB + kb;
           const int sa = static_cast<int>(n % RA);
-          if (!mbar_wait_bounded(afull + sa, static_cast<int>((n / RA) & 1), a.status, DEV_ERR_TIMEOUT_FULL)) {
+          if (!wait_x(afull + sa, static_cast<int>((n / RA) & 1), DEV_ERR_TIMEOUT_FULL)) {
             ok = false;
             break;
           }
@@ -1197,30 +1243,35 @@ __global__ void __launch_bounds__(rt_threads(SPLIT), 1)
             for (int k = 0; k < BK / 16; ++k) {
               const uint64_t ad = sdesc_sw<BK>(ua + k * 32);
               const uint64_t bd = sdesc_sw<BK>(ub + k * 32);
-              tc_mma_bf16(tmem + h * ncols, ad, bd, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+              if constexpr (PAIR)
+                tc_mma2_bf16(tmem + h * ncols, ad, bd, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+              else
+                tc_mma_bf16(tmem + h * ncols, ad, bd, idesc, (kb > 0 || k > 0) ? 1u : 0u);
               if constexpr (SPLIT) {
                 tc_mma_bf16(tmem + h * ncols, ad, sdesc_sw<BK>(ub + t_part + k * 32), idesc, 1u);
                 tc_mma_bf16(tmem + h * ncols, sdesc_sw<BK>(ua + kAs + k * 32), bd, idesc, 1u);
               }
             }
-            tc_commit(tempty + s);
+            commit(tempty + s);
           }
           if (!ok) break;
-          tc_commit(afree + sa);
+          commit(afree + sa);
         }
         if (!ok) break;
-        tc_commit(acc_full);
+        commit(acc_full);
       }
-      if (tl > 0) mbar_wait_bounded(acc_empty, (tl - 1) & 1, a.status, DEV_ERR_TIMEOUT_MMA);
+      if (tl > 0) wait_x(acc_empty, (tl - 1) & 1, DEV_ERR_TIMEOUT_MMA);
     }
   } else if (warp < kFill0) {
     // epilogue: accumulator row = signal, columns = output degrees of freedom
     const int q = warp & 3;
     const int g = (warp - 2) >> 2;  // column group of the quadrant
+    const uint32_t acc_empty0 = PAIR ? cluster_addr(acc_empty, 0) : 0u;
     int tl = 0;
-    for (long long t = blockIdx.x; t < tiles; t += gridDim.x, ++tl) {
-      const int b = static_cast<int>(t / mtiles);
-      const int i = static_cast<int>(t % mtiles) * kBlockM + q * 32 + lane;
+    for (long long t = cid; t < tiles; t += ncl, ++tl) {
+      int b, i0;
+      unit_tile(t, b, i0);
+      const int i = i0 + q * 32 + lane;
       if (!mbar_wait_bounded(acc_full, tl & 1, a.status, DEV_ERR_TIMEOUT_MMA)) break;
       tc_fence_after();
       const uint32_t tbase = tmem + (static_cast<uint32_t>(q * 32) << 16);
@@ -1253,7 +1304,12 @@ __global__ void __launch_bounds__(rt_threads(SPLIT), 1)
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(acc_empty);
+      if (lane == 0) {
+        if constexpr (PAIR)
+          mbar_arrive_cluster(acc_empty0);
+        else
+          mbar_arrive(acc_empty);
+      }
     }
   } else {
     // fill warps: warp f fills k-blocks f, f + 8, ... of every tile (k-block
@@ -1261,11 +1317,12 @@ __global__ void __launch_bounds__(rt_threads(SPLIT), 1)
     // of bin 0 carries Re(bin Nt)); all of a tile's loads are in flight
     // together; 16-byte chunks are stored in the TMA swizzle pattern
     const int f = warp - kFill0;
+    const uint32_t afull0 = PAIR ? cluster_addr(afull, 0) : 0u;
     int tl = 0;
     bool ok = true;
-    for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++tl) {
-      const int b = static_cast<int>(t / mtiles);
-      const int i0 = static_cast<int>(t % mtiles) * kBlockM;
+    for (long long t = cid; t < tiles && ok; t += ncl, ++tl) {
+      int b, i0;
+      unit_tile(t, b, i0);
       for (int kb = f; kb < KB && ok; kb += kRtFillWarps) {
         const long long n = static_cast<long long>(tl) * KB + kb;
         const int sa = static_cast<int>(n % RA);
@@ -1363,16 +1420,26 @@ __global__ void __launch_bounds__(rt_threads(SPLIT), 1)
         }
         fence_proxy_async_smem();
         __syncwarp();
-        if (lane == 0) mbar_arrive(afull + sa);
+        if (lane == 0) {
+          if constexpr (PAIR)
+            mbar_arrive_cluster(afull0 + 8u * static_cast<uint32_t>(sa));
+          else
+            mbar_arrive(afull + sa);
+        }
       }
     }
   }
   tc_fence_before();
   __syncthreads();
+  if constexpr (PAIR) cluster_sync_all();  // neither CTA still uses the pair's tensor memory
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tmem, tmem_cols);
+    if constexpr (PAIR)
+      tmem_dealloc2(tmem, tmem_cols);
+    else
+      tmem_dealloc(tmem, tmem_cols);
   }
+  if constexpr (PAIR) cluster_sync_all();  // no CTA leaves while its peer may still signal it
 }
 
 int grid_for_tc(long long n) {
@@ -1647,32 +1714,63 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
 }
 
 cudaError_t launch_tc_retransform(const CUtensorMap& tmT, const CUtensorMap* tmT2, const TcRtArgs& a, int num_sms,
-                                  cudaStream_t st) {
+                                  cudaStream_t st, const CUtensorMap* tmTp) {
   if (a.Nt < 32 || a.Nt > 256) return cudaErrorInvalidValue;
-  const long long tiles = static_cast<long long>(a.Bs) * ((a.Ng + kBlockM - 1) / kBlockM);
+  const int mtiles = (a.Ng + kBlockM - 1) / kBlockM;
+  const long long tiles = static_cast<long long>(a.Bs) * mtiles;
   if (tiles <= 0) return cudaSuccess;
   const bool split = tmT2 != nullptr;
   if (split ? (a.mhat32 == nullptr || a.vhat_lo == nullptr) : (a.mhat_bf == nullptr)) return cudaErrorInvalidValue;
+  // two-SM tiles (BF16 only) when a half-row map of T is given and the grid spans two M tiles
+  const bool pair = !split && tmTp != nullptr && mtiles >= 2;
   const int BK = split ? 32 : 64;
   const int K = 2 * a.Nt;
   const int ncols = K > 256 ? 256 : K;
   const size_t a_slot = static_cast<size_t>(kBlockM) * BK * 2 * (split ? 2 : 1);
-  const size_t t_slot = static_cast<size_t>(ncols) * BK * 2 * (split ? 2 : 1);
+  const size_t t_slot = static_cast<size_t>(pair ? ncols / 2 : ncols) * BK * 2 * (split ? 2 : 1);
   TcRtArgs aa = a;
   aa.ra = kRtFillWarps;  // one A slot per fill warp (see the kernel)
   aa.rt = static_cast<int>((kSmemBudget - aa.ra * a_slot) / t_slot);
   if (aa.rt > 4) aa.rt = 4;
   if (aa.rt < 2) return cudaErrorInvalidValue;
   const size_t smem = 1024 + aa.ra * a_slot + aa.rt * t_slot + 8 * (2 * aa.ra + 2 * aa.rt + 2) + 16;
+  if (pair) {
+    const void* kfn = reinterpret_cast<const void*>(k_tc_retransform<false, true>);
+    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.blockDim = dim3(rt_threads(false));
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.gridDim = dim3(static_cast<unsigned>((num_sms / 2) * 2));
+    int active = 0;
+    e = cudaOccupancyMaxActiveClusters(&active, kfn, &cfg);
+    if (e != cudaSuccess) return e;
+    if (active < 1) return cudaErrorInvalidConfiguration;
+    long long nclusters = active;
+    const long long units = static_cast<long long>(a.Bs) * ((mtiles + 1) / 2);
+    if (nclusters > units) nclusters = units;
+    cfg.gridDim = dim3(static_cast<unsigned>(nclusters * 2));
+    e = cudaLaunchKernelEx(&cfg, k_tc_retransform<false, true>, *tmTp, *tmTp, aa);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+  }
   const long long grid = tiles < num_sms ? tiles : num_sms;
-  const void* kfn = split ? reinterpret_cast<const void*>(k_tc_retransform<true>)
-                          : reinterpret_cast<const void*>(k_tc_retransform<false>);
+  const void* kfn = split ? reinterpret_cast<const void*>(k_tc_retransform<true, false>)
+                          : reinterpret_cast<const void*>(k_tc_retransform<false, false>);
   cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   if (split)
-    k_tc_retransform<true><<<static_cast<unsigned>(grid), rt_threads(true), smem, st>>>(tmT, *tmT2, aa);
+    k_tc_retransform<true, false><<<static_cast<unsigned>(grid), rt_threads(true), smem, st>>>(tmT, *tmT2, aa);
   else
-    k_tc_retransform<false><<<static_cast<unsigned>(grid), rt_threads(false), smem, st>>>(tmT, tmT, aa);
+    k_tc_retransform<false, false><<<static_cast<unsigned>(grid), rt_threads(false), smem, st>>>(tmT, tmT, aa);
   return cudaGetLastError();
 }
 

@@ -63,6 +63,7 @@ struct s2w_ctx {
   int tc_cl1 = 1;        // cluster size of the stage-1 GEMM (B tiles multicast)
   int tc_cl2 = 1;        // cluster size of the stage-2 GEMM
   int tc_pair = 0;       // 1: two-SM MMAs (CTA pairs per M = 256 tile) where the shape allows; kPairAuto: for N = 512
+  bool tc_rtpair = false;  // two-SM tiles for the BF16 retransform GEMM
   int tc_min_batch = 2;  // AUTO: smallest B on the tensor engine
   // CUDA graphs of the waveform pipeline, one per (slip, q, B), least
   // recently used evicted beyond kGraphCache entries
@@ -107,6 +108,7 @@ struct s2w_ctx {
   void* tc_T = nullptr;     // [2 Nt][2 Nt] bf16: retransform as a real-linear map
   void* tc_T_lo = nullptr;  // split: its low-order part
   CUtensorMap tc_tmT, tc_tmT2;
+  CUtensorMap tc_tmTp, tc_tmTap;  // BF16: the same matrices with half-row boxes (two-SM retransform)
   void* tc_Ta = nullptr;    // tc_adjoint: the same map with D_t^T (adjoint retransform), + lo when split
   void* tc_Ta_lo = nullptr;
   CUtensorMap tc_tmTa, tc_tmTa2;
@@ -433,7 +435,8 @@ int adjoint_tensor(s2w_ctx* ctx, const float* r_d, int B, float* g_d, cudaStream
       r.vld_b = 2 * ctx->Ng_pad2;
       r.conj_row = ctx->Ng_pad2;
       r.status = ctx->d_status;
-      CK(launch_tc_retransform(ctx->tc_tmTa, sp ? &ctx->tc_tmTa2 : nullptr, r, ctx->num_sms, st));
+      CK(launch_tc_retransform(ctx->tc_tmTa, sp ? &ctx->tc_tmTa2 : nullptr, r, ctx->num_sms, st,
+                               sp || !ctx->tc_rtpair ? nullptr : &ctx->tc_tmTap));
     } else {
       StageTimer t(ctx, 2, st);
       CK(launch_retransform(what, Ng, static_cast<long long>(Bs) * Ng, static_cast<int>(Nt), ctx->tw,
@@ -581,7 +584,8 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
       r.vld_l = static_cast<long long>(ctx->tc_bsub) * ctx->Ng_pad2;
       r.vld_b = ctx->Ng_pad2;
       r.status = ctx->d_status;
-      CK(launch_tc_retransform(ctx->tc_tmT, sp ? &ctx->tc_tmT2 : nullptr, r, ctx->num_sms, st));
+      CK(launch_tc_retransform(ctx->tc_tmT, sp ? &ctx->tc_tmT2 : nullptr, r, ctx->num_sms, st,
+                               sp || !ctx->tc_rtpair ? nullptr : &ctx->tc_tmTp));
     }
     {
       StageTimer t(ctx, 3, st);
@@ -778,6 +782,9 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
     ctx->tc_cl1 = o.tc_cluster > 0 ? o.tc_cluster : kDefaultCluster;
     ctx->tc_cl2 = o.tc_cluster > 0 ? o.tc_cluster : kDefaultCluster;
     ctx->tc_pair = o.tc_pair == S2W_PAIR_ON ? 1 : (o.tc_pair == S2W_PAIR_OFF ? 0 : kDefaultPair);
+    // the two-SM retransform measured slower (9.0 against 8.4 ms per 256-rupture
+    // batch): only when asked for
+    ctx->tc_rtpair = o.tc_pair == S2W_PAIR_ON;
     ctx->tc_f8act = o.tc_fp8_act != 0;
     // FP8 B rows come in multiples of 32 (N % 32 for the two-SM tiles)
     ctx->tc_n1max = static_cast<int>(round_up(2 * ctx->tc_bsub, ctx->tc_f8act ? 32 : 16));
@@ -843,7 +850,8 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
     // the retransform GEMM's matrix: BF16 (128-byte swizzle boxes), or hi +
     // lo BF16 for the split path (64-byte swizzle boxes)
     if (Nt <= 256) {
-      auto upload = [&](bool transpose, void** hi_d, void** lo_d, CUtensorMap* tm, CUtensorMap* tm2) -> cudaError_t {
+      auto upload = [&](bool transpose, void** hi_d, void** lo_d, CUtensorMap* tm, CUtensorMap* tm2,
+                        CUtensorMap* tmp) -> cudaError_t {
         const std::vector<double> T = retransform_matrix(Nt, o.dt_mode, o.dt, transpose);
         std::vector<__nv_bfloat16> hi(T.size()), lo(T.size());
         for (size_t q = 0; q < T.size(); ++q) {
@@ -856,6 +864,7 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
         if ((r = dalloc(hi_d, tb)) != cudaSuccess) return r;
         if ((r = cudaMemcpy(*hi_d, hi.data(), tb, cudaMemcpyHostToDevice)) != cudaSuccess) return r;
         if ((r = tc_encode_3d(tm, *hi_d, K, K, 1, K, box, bk)) != cudaSuccess) return r;
+        if (!sp && (r = tc_encode_3d(tmp, *hi_d, K, K, 1, K, box / 2, bk)) != cudaSuccess) return r;
         if (sp) {
           if ((r = dalloc(lo_d, tb)) != cudaSuccess) return r;
           if ((r = cudaMemcpy(*lo_d, lo.data(), tb, cudaMemcpyHostToDevice)) != cudaSuccess) return r;
@@ -863,9 +872,10 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
         }
         return cudaSuccess;
       };
-      if ((e = upload(false, &ctx->tc_T, &ctx->tc_T_lo, &ctx->tc_tmT, &ctx->tc_tmT2)) != cudaSuccess)
+      if ((e = upload(false, &ctx->tc_T, &ctx->tc_T_lo, &ctx->tc_tmT, &ctx->tc_tmT2, &ctx->tc_tmTp)) != cudaSuccess)
         return bad(e, "retransform matrix");
-      if (ctx->tc_adj && (e = upload(true, &ctx->tc_Ta, &ctx->tc_Ta_lo, &ctx->tc_tmTa, &ctx->tc_tmTa2)) != cudaSuccess)
+      if (ctx->tc_adj &&
+          (e = upload(true, &ctx->tc_Ta, &ctx->tc_Ta_lo, &ctx->tc_tmTa, &ctx->tc_tmTa2, &ctx->tc_tmTap)) != cudaSuccess)
         return bad(e, "adjoint retransform matrix");
     }
   }

@@ -226,14 +226,14 @@ struct TcArgs {
   const unsigned* b_amax;  // FP16 B operand: amax (float bits) that set its power-of-two scale
   int m_pair;              // 1: two M tiles per unit sharing each B tile (N <= 256, cluster 1, not FP8;
                            //    tmem_cols >= 2 N, stages from tc_stages_for(..., mt = 2))
-  int b_fp8;               // 1 (with a_fp8 and cta2): B is FP8 e4m3 too (launch_pack_b_f8), byte tensor
-                           //    maps with 128-byte swizzle, kind::f8f6f4 MMAs, K blocks of 128 bytes
-  const float* col_scale;  // optional per-(bin, complex column) scale: col_scale[l * col_ld + t]
-  int col_ld;
   int cta2;                // 1: two-SM MMAs, a CTA pair per M = 256 tile, each staging half of B
                            //    (N % 32 == 0, cluster 1, no m_pair; B box rows = min(N, 256) / 2,
                            //    K blocks tc_block_k(N, split, 1), stages from tc_stages_pair)
   int* status;
+  int b_fp8;               // 1 (with a_fp8 and cta2): B is FP8 e4m3 too (launch_pack_b_f8), byte tensor
+                           //    maps with 128-byte swizzle, kind::f8f6f4 MMAs, K blocks of 128 bytes
+  int col_ld;
+  const float* col_scale;  // with b_fp8: per-(bin, complex column) scale col_scale[l * col_ld + t]
 };
 // bk = 64: 128-byte swizzle, K boxes of 64 BF16; bk = 32: 64-byte swizzle.
 cudaError_t tc_encode_3d(CUtensorMap* out, const void* base, long long K, long long rows, long long nbatch,
@@ -298,9 +298,11 @@ struct TcRtArgs {
   int* status;
 };
 // tmT2 (split): tensor map of T's low-order part; T maps then use 32-element
-// K boxes (64-byte swizzle), else 64 (128-byte swizzle).
+// K boxes (64-byte swizzle), else 64 (128-byte swizzle).  tmTp (BF16 only):
+// a map of the same T with boxes of half the rows (min(2 Nt, 256) / 2),
+// which selects two-SM tiles when the grid spans at least two M tiles.
 cudaError_t launch_tc_retransform(const CUtensorMap& tmT, const CUtensorMap* tmT2, const TcRtArgs& a, int num_sms,
-                                  cudaStream_t st);
+                                  cudaStream_t st, const CUtensorMap* tmTp = nullptr);
 
 
 }  // namespace s2w
