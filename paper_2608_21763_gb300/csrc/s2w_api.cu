@@ -791,13 +791,25 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
     if (ctx->tc_n1max > 256) ctx->tc_n1max = 512;
     ctx->tc_n2 = static_cast<int>(round_up(2 * No, 16));
     ctx->Ng_pad2 = round_up(Ng, 8);
-    // stage-2 split-K: enough work units for every SM (about 4 each) and no
-    // more, so the chunk partials stay small
+    // stage-2 split-K: units = bins x M-tile groups (pairs of 128-row tiles
+    // when the GEMM takes them) x K chunks over the persistent CTAs; pick the
+    // chunk count that minimises rounds x chunk length, with a small fixed
+    // cost per unit (pipeline fill and accumulator drain), up to 16 chunks
     const int bk2 = tc_block_k(ctx->tc_n2, ctx->tc_split ? 1 : 0);
     const long long nk2 = (2 * ctx->Ng_pad2 + bk2 - 1) / bk2;
     const long long mt2 = (ctx->tc_bsub + 127) / 128;
-    long long nkc = (4LL * ctx->num_sms + Nb * mt2 - 1) / (Nb * mt2);
-    nkc = std::max(1LL, std::min(nkc, nk2));
+    const long long mg2 = (mt2 >= 2 && ctx->tc_n2 <= 256) ? (mt2 + 1) / 2 : mt2;
+    long long nkc = 1;
+    double best = 1e300;
+    for (long long c = 1; c <= std::min(16LL, nk2); ++c) {
+      const long long units = Nb * mg2 * c;
+      const long long rounds = (units + ctx->num_sms - 1) / ctx->num_sms;
+      const double cost = static_cast<double>(rounds) * (1.0 / static_cast<double>(c) + 0.005);
+      if (cost < best * (1.0 - 1e-9)) {
+        best = cost;
+        nkc = c;
+      }
+    }
     ctx->tc_kbpc = static_cast<int>((nk2 + nkc - 1) / nkc);
     ctx->tc_nkc = static_cast<int>((nk2 + ctx->tc_kbpc - 1) / ctx->tc_kbpc);
     const long long bs = ctx->tc_bsub;
