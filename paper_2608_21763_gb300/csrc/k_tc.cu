@@ -235,13 +235,12 @@ __device__ __forceinline__ void tc_store_cols(const TcArgs& a, const float* v, i
 
 template <int EPW, bool CS = false>
 __device__ __forceinline__ void tc_epilogue_tile(const TcArgs& a, uint32_t tbase, int N, int g, int l, int kc,
-                                                 int row, bool live, float scale) {
+                                                 int row, bool live, float scale, const float* cs = nullptr) {
   const bool bf = a.epi == 0 && a.out_bf != nullptr;
   const long long ld = a.epi == 0 ? a.ld_t : 1;
   const long long obase = a.epi == 0
                               ? static_cast<long long>(l) * a.ld_l + row
                               : ((static_cast<long long>(l) * a.n_kchunks + kc) * a.M_total + row) * a.T;
-  const float* cs = CS ? a.col_scale + static_cast<long long>(l) * a.col_ld : nullptr;
   const int n64 = N / 64 * 64;
   for (int c0 = 64 * g; c0 < n64; c0 += 64 * EPW) {
     float v[64];
@@ -675,7 +674,8 @@ __device__ __forceinline__ void tc_mma2_f8f8(uint32_t d_tmem, uint64_t a_desc, u
 // the epilogue.
 template <int BK, int MODE>
 __device__ __forceinline__ void tc_gemm2_body(const CUtensorMap* tmA, const CUtensorMap* tmB, const CUtensorMap* tmA2,
-                                              const CUtensorMap* tmB2, const TcArgs& a) {
+                                              const CUtensorMap* tmB2, const TcArgs& a,
+                                              const float* col_scale = nullptr, int col_ld = 0) {
   constexpr bool SPLIT = MODE == 1;
   constexpr bool F8 = MODE == 2;
   constexpr bool F8F8 = MODE == 3;
@@ -880,7 +880,8 @@ __device__ __forceinline__ void tc_gemm2_body(const CUtensorMap* tmA, const CUte
       float scale = 1.f;
       if (a.row_scale != nullptr && live) scale = a.row_scale[static_cast<long long>(l) * a.nblk + row / 256];
       if (a.b_amax != nullptr) scale *= f16_unscale(*a.b_amax);  // undo the FP16 B operand's power-of-two scale
-      tc_epilogue_tile<EPW, F8F8>(a, tbase, N, g, l, kc, row, live, scale);  // F8F8: per-column B scales
+      tc_epilogue_tile<EPW, F8F8>(a, tbase, N, g, l, kc, row, live, scale,  // F8F8: per-column B scales
+                                  F8F8 ? col_scale + static_cast<long long>(l) * col_ld : nullptr);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive_cluster(acc_empty0);
@@ -911,8 +912,9 @@ __global__ void __launch_bounds__(kTcThreadsF8, 1)
 
 template <int BK>
 __global__ void __launch_bounds__(kTcThreads, 1)
-    k_tc_gemm2_f8f8(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
-  tc_gemm2_body<BK, 3>(&tmA, &tmB, nullptr, nullptr, a);
+    k_tc_gemm2_f8f8(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcArgs a,
+                    const float* col_scale, int col_ld) {
+  tc_gemm2_body<BK, 3>(&tmA, &tmB, nullptr, nullptr, a, col_scale, col_ld);
 }
 
 template <int BK>
@@ -1590,7 +1592,8 @@ cudaError_t launch_tc_cl(const CUtensorMap& tmA, const CUtensorMap& tmB, const C
 }
 
 cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const TcArgs& a, int num_sms,
-                           cudaStream_t st, const CUtensorMap* tmA2, const CUtensorMap* tmB2) {
+                           cudaStream_t st, const CUtensorMap* tmA2, const CUtensorMap* tmB2, const float* col_scale,
+                           int col_ld) {
   const long long units = static_cast<long long>(a.Nb) * a.m_tiles * a.n_kchunks;
   if (units <= 0) return cudaSuccess;
   if (a.N < 16 || a.N > 512 || a.N % 16 != 0 || (a.N > 256 && a.N % 256 != 0) || a.stages < 2)
@@ -1604,8 +1607,8 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
     if (a.m_pair || a.cluster > 1 || a.N % 32 != 0) return cudaErrorInvalidValue;
     const int sp = a.a_lo;
     const int f8 = a.a_fp8;
-    const bool f8f8 = a.a_fp8 && a.b_fp8;
-    if (a.b_fp8 && (!a.a_fp8 || a.col_scale == nullptr)) return cudaErrorInvalidValue;
+    const bool f8f8 = col_scale != nullptr;
+    if (f8f8 && (!a.a_fp8 || col_ld < a.T)) return cudaErrorInvalidValue;
     const size_t smem = tc2_smem_bytes(a.N, a.stages, sp, f8f8 ? 2 : f8);
     if (smem > static_cast<size_t>(kSmemOptIn)) return cudaErrorInvalidValue;
     const bool bk64 = tc_block_k(a.N, sp, 1) == 64;
@@ -1639,7 +1642,7 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
     if (nclusters > pu) nclusters = pu;
     cfg.gridDim = dim3(static_cast<unsigned>(nclusters * 2));
     if (f8f8) {
-      e = cudaLaunchKernelEx(&cfg, k_tc_gemm2_f8f8<128>, tmA, tmB, a);
+      e = cudaLaunchKernelEx(&cfg, k_tc_gemm2_f8f8<128>, tmA, tmB, a, col_scale, col_ld);
     } else if (f8) {
       if (bk64)
         e = cudaLaunchKernelEx(&cfg, k_tc_gemm2_f8<64>, tmA, tmB, a);
@@ -1659,7 +1662,7 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
   }
-  if (a.b_fp8) return cudaErrorInvalidValue;  // FP8 B: two-SM form only
+  if (col_scale != nullptr) return cudaErrorInvalidValue;  // FP8 B: two-SM form only
   const int CL = a.cluster < 1 ? 1 : a.cluster;
   if (CL != 1 && CL != 2 && CL != 4) return cudaErrorInvalidValue;
   if (CL > 1 && (a.N / CL < 8 || (a.N / CL) % 8 != 0 || a.N / CL > 256)) return cudaErrorInvalidValue;

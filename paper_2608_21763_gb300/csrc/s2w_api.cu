@@ -511,11 +511,8 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
       a.stages = tc_stages_pair(N1, 0, 2);
       a.tmem_cols = N1 <= 32 ? 32 : (N1 <= 64 ? 64 : (N1 <= 128 ? 128 : (N1 <= 256 ? 256 : 512)));
       a.a_fp8 = 1;
-      a.b_fp8 = 1;
       a.row_scale = ctx->G_scale;
       a.nblk = ctx->nblk;
-      a.col_scale = ctx->tc_colscale;
-      a.col_ld = ctx->tc_n1max / 2;
       a.cluster = 1;
       a.epi = 0;
       a.T = Bs;
@@ -523,7 +520,7 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
       a.ld_l = static_cast<long long>(Bs) * Ng;
       a.ld_t = Ng;
       a.status = ctx->d_status;
-      CK(launch_tc_gemm(ta, tb, a, ctx->num_sms, st));
+      CK(launch_tc_gemm(ta, tb, a, ctx->num_sms, st, nullptr, nullptr, ctx->tc_colscale, ctx->tc_n1max / 2));
     } else {
       StageTimer t(ctx, 1, st);
       CUtensorMap ta, tb, ta2, tb2;

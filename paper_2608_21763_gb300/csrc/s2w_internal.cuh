@@ -230,10 +230,6 @@ struct TcArgs {
                            //    (N % 32 == 0, cluster 1, no m_pair; B box rows = min(N, 256) / 2,
                            //    K blocks tc_block_k(N, split, 1), stages from tc_stages_pair)
   int* status;
-  int b_fp8;               // 1 (with a_fp8 and cta2): B is FP8 e4m3 too (launch_pack_b_f8), byte tensor
-                           //    maps with 128-byte swizzle, kind::f8f6f4 MMAs, K blocks of 128 bytes
-  int col_ld;
-  const float* col_scale;  // with b_fp8: per-(bin, complex column) scale col_scale[l * col_ld + t]
 };
 // bk = 64: 128-byte swizzle, K boxes of 64 BF16; bk = 32: 64-byte swizzle.
 cudaError_t tc_encode_3d(CUtensorMap* out, const void* base, long long K, long long rows, long long nbatch,
@@ -247,9 +243,14 @@ int tc_stages_pair(int N, int split, int fp8 = 0);
 // (sw128: 128-byte swizzle, bk = 128, for operands the MMAs read directly).
 cudaError_t tc_encode_3d_u8(CUtensorMap* out, const void* base, long long K, long long rows, long long nbatch,
                             int box_rows, int bk, int sw128 = 0);
-// tmA2 / tmB2: tensor maps of the low-order parts when a.a_lo / a.b_lo
+// tmA2 / tmB2: tensor maps of the low-order parts when a.a_lo / a.b_lo.
+// col_scale (with a.a_fp8 and a.cta2): B is FP8 e4m3 too (launch_pack_b_f8),
+// byte tensor maps with 128-byte swizzle and 128-byte K boxes, kind::f8f6f4
+// MMAs; column t of bin l is scaled by col_scale[l * col_ld + t].  (Kept out
+// of TcArgs: a larger argument block costs every GEMM kernel registers.)
 cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const TcArgs& a, int num_sms,
-                           cudaStream_t st, const CUtensorMap* tmA2 = nullptr, const CUtensorMap* tmB2 = nullptr);
+                           cudaStream_t st, const CUtensorMap* tmA2 = nullptr, const CUtensorMap* tmB2 = nullptr,
+                           const float* col_scale = nullptr, int col_ld = 0);
 // B operand rows 2t / 2t+1 of dst[l][N_alloc][2 Kc] (BF16 pairs, hi and
 // optional lo) from complex FP32 src[l*s_l + t*s_t + c], t < T, c < nc, at
 // complex columns c0 + c; conj selects the embedding of conj(A) x.
