@@ -59,6 +59,35 @@ def test_create_rejects_bad_shapes_before_touching_a_device():
     assert L.s2w_create(2000, 64, 4, 32, None, ctypes.byref(h)) == -6  # Ns > 1024
 
 
+def test_opts_layout_matches_the_header():
+    """s2w_default_opts writes every field of s2w_opts: written into a buffer
+    larger than the binding's Opts, it must stop exactly at Opts' end (a
+    field missing from the binding would be written past it) and leave the
+    defaults of the last fields (two-SM tiles: library choice; FP8
+    activations off)."""
+    L = s2w.lib()
+    n = ctypes.sizeof(s2w.Opts)
+    buf = (ctypes.c_ubyte * (n + 64))(*([0xAB] * (n + 64)))
+    L.s2w_default_opts(ctypes.cast(buf, ctypes.POINTER(s2w.Opts)))
+    assert all(b == 0xAB for b in buf[n:])
+    o = s2w.Opts.from_buffer(buf)
+    assert (o.tc_cluster, o.tc_adjoint, o.single_pass, o.tc_pair, o.tc_fp8_act) == (0, 0, 0, 0, 0)
+
+
+def test_create_rejects_bad_options_before_touching_a_device():
+    L = s2w.lib()
+    h = ctypes.c_void_p()
+    for field, value, prec_g in [("tc_pair", 3, 1), ("tc_pair", -1, 1), ("tc_fp8_act", 2, 3),
+                                 ("tc_fp8_act", 1, 1), ("tc_fp8_act", 1, 0)]:
+        o = s2w.Opts()
+        L.s2w_default_opts(ctypes.byref(o))
+        o.prec_g = prec_g
+        setattr(o, field, value)
+        assert L.s2w_create(16, 64, 4, 32, ctypes.byref(o), ctypes.byref(h)) == -1, (field, value, prec_g)
+        assert h.value is None
+        assert field.encode() in L.s2w_last_error(None)
+
+
 def test_null_context_is_an_argument_error():
     L = s2w.lib()
     assert L.s2w_waveforms(None, None, 1, None, None, None) == -1
