@@ -1,7 +1,11 @@
 // Tensor-core per-bin contractions for rupture batches (Alg. 2 step 3 with
-// many right-hand sides): tcgen05.mma (kind::f16, BF16 operands, FP32
-// accumulators in tensor memory), operands staged by TMA with 128-byte
-// swizzle.
+// many right-hand sides): tcgen05.mma with FP32 accumulators in tensor
+// memory (kind::f16 for BF16 / FP16 operands, kind::f8f6f4 for e4m3 x e4m3),
+// operands staged by TMA with 128-byte (or 64-byte) swizzle.  Two GEMM
+// bodies: tc_gemm_body, one CTA per 128-row tile (optionally two tiles per
+// unit, or clusters sharing B by multicast), and tc_gemm2_body, the two-SM
+// form (cta_group::2: a CTA pair per 256-row tile, each staging half of B).
+// The retransform between the stages is a GEMM too (k_tc_retransform).
 //
 // Complex products run as one real GEMM per bin through a real embedding that
 // never duplicates the streamed operand A:
