@@ -47,8 +47,6 @@ constexpr int kEpwF8 = 2;
 constexpr int kTcThreads = 32 * (2 + 4 * kEpw);         // warps: 0 TMA producer, 1 MMA, then the epilogue
 constexpr int kTcThreadsF8 = 32 * (2 + 4 * kEpwF8) + 128;  // FP8 A: + 4 warps widen the A tiles to FP16
 constexpr int kBlockM = 128;
-constexpr int kBlockK = 64;  // bf16 elements per 128-byte swizzle row
-constexpr int kABytes = kBlockM * kBlockK * 2;
 constexpr int kSmemBudget = 200 * 1024;
 
 __device__ __forceinline__ void tma_load_3d(void* sdst, const CUtensorMap* tm, int c0, int c1, int c2,
@@ -192,7 +190,6 @@ __device__ __forceinline__ uint64_t sdesc_sw(uint32_t saddr) {
   d |= layout << 61;                                    // swizzle mode
   return d;
 }
-__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) { return sdesc_sw<64>(saddr); }
 
 // Instruction descriptor, kind::f16: BF16 A and B, FP32 D, both K-major.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
