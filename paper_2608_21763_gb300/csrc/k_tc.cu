@@ -48,6 +48,7 @@ constexpr int kTcThreads = 32 * (2 + 4 * kEpw);         // warps: 0 TMA producer
 constexpr int kTcThreadsF8 = 32 * (2 + 4 * kEpwF8) + 128;  // FP8 A: + 4 warps widen the A tiles to FP16
 constexpr int kBlockM = 128;
 constexpr int kSmemBudget = 200 * 1024;
+constexpr int kSmemOptInLimit = 227 * 1024;  // opt-in dynamic shared memory per CTA
 
 __device__ __forceinline__ void tma_load_3d(void* sdst, const CUtensorMap* tm, int c0, int c1, int c2,
                                             uint64_t* bar) {
@@ -1513,6 +1514,7 @@ int tc_stage_bytes(int N, int a_lo, int b_lo, int fp8, int mt) {
 }  // namespace
 
 int tc_stages_for(int N, int a_lo, int b_lo, int fp8, int mt) {
+  // (a fifth FP8 stage at N = 512 from the opt-in shared memory measured no gain)
   int s = kSmemBudget / tc_stage_bytes(N, a_lo, b_lo, fp8, mt);
   if (s > 8) s = 8;
   return s;
@@ -1734,7 +1736,10 @@ cudaError_t launch_tc_retransform(const CUtensorMap& tmT, const CUtensorMap* tmT
   const size_t t_slot = static_cast<size_t>(pair ? ncols / 2 : ncols) * BK * 2 * (split ? 2 : 1);
   TcRtArgs aa = a;
   aa.ra = kRtFillWarps;  // one A slot per fill warp (see the kernel)
-  aa.rt = static_cast<int>((kSmemBudget - aa.ra * a_slot) / t_slot);
+  // T slots fill the opt-in shared memory left by the A ring: three at
+  // Nt = 256 (two within 200 KB; the split kernel's 256-rupture batch went
+  // 24.4 -> 20.8 ms, BF16 unchanged)
+  aa.rt = static_cast<int>((kSmemOptInLimit - 1024 - 8 * (2 * 8 + 2 * 4 + 2) - 16 - aa.ra * a_slot) / t_slot);
   if (aa.rt > 4) aa.rt = 4;
   if (aa.rt < 2) return cudaErrorInvalidValue;
   const size_t smem = 1024 + aa.ra * a_slot + aa.rt * t_slot + 8 * (2 * aa.ra + 2 * aa.rt + 2) + 16;
