@@ -137,6 +137,17 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
+def tensor_dtype(args):
+    """Arithmetic type of the tensor engine's stage-1 MMAs: BF16, three BF16
+    MMAs per product (hi/lo split), FP16 (FP8 operator widened, FP16
+    activations) or e4m3 x e4m3 (FP8 activations); FP32 accumulation in all."""
+    if args.prec_g == "bf16_hilo":
+        return "bf16x3"
+    if args.prec_g == "fp8":
+        return "e4m3" if args.fp8_act else "f16"
+    return "bf16"
+
+
 # ------------------------------------------------------------------ setup
 def load_context(s2w, wl, geom, prec_g, prec_p, B, device, engine="auto", chunk=1024, tc_cluster=0,
                  tc_adjoint=False, single_pass=False, tc_pair="auto", tc_fp8_act=False):
@@ -442,7 +453,7 @@ def run_ours(args, rank, world, local_rank):
     out = {"metric": metric, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": round(elapsed_ms / args.steps, 4), "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": ("bf16x3" if args.prec_g == "bf16_hilo" else "bf16") if tensor else "f32",
+           "scaling": "weak", "vs_baseline": None, "dtype": tensor_dtype(args) if tensor else "f32",
            "data": "synthetic",
            "config": {"workload": wl.name, "Ns": wl.Ns, "Ng": wl.Ng, "No": wl.No, "Nt": wl.Nt,
                       "ruptures_per_step": B, "prec_g": args.prec_g, "prec_p": args.prec_p,
