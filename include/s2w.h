@@ -293,6 +293,19 @@ int s2w_rfft(s2w_ctx *ctx, const float *x, long long rows, float *X, void *strea
  * pointers only. */
 int s2w_irfft(s2w_ctx *ctx, const float *X, long long rows, float *x, void *stream);
 
+/* The retransform between the two stages (Alg. 2: IFFT, Truncate to Nt
+ * samples, D_t, ZeroPad to 2 Nt, FFT) of one real signal's Nt + 1 bins,
+ * written as the real 2 Nt x 2 Nt matrix that the tensor engine applies
+ * (rounded to BF16 there): T[n][k] row-major, over the degrees of freedom
+ * k = 0: Re bin 0, k = 1: Re bin Nt, k = 2l / 2l + 1: Re / Im bin l
+ * (0 < l < Nt), the same ordering for the outputs n.  transpose = 1 gives
+ * the adjoint's map (D_t^T in place of D_t).  dt_mode / dt as in s2w_opts.
+ * Evaluated in FP64 on the host; T (caller-owned) receives 4 Nt^2 doubles.
+ * Touches no device.  S2W_ERR_ARG for a NULL T, a bad dt_mode, dt <= 0 or
+ * transpose not 0 / 1; S2W_ERR_UNSUPPORTED for Nt outside 32, 64, 128,
+ * 256. */
+int s2w_retransform_matrix(int Nt, int dt_mode, double dt, int transpose, double *T);
+
 /* Per-stage CUDA-event timers (the per-stage timing of Sec. III-B).
  * Stages: 0 rfft of slip, 1 stage-1 contraction, 2 retransform (IFFT,
  * Truncate, D_t, ZeroPad, FFT), 3 stage-2 contraction, 4 partial reduction +

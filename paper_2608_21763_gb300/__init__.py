@@ -33,7 +33,7 @@ EXPORTS = ("s2w_default_opts", "s2w_create", "s2w_destroy", "s2w_operator_bytes"
            "s2w_load_greens", "s2w_load_adjoint", "s2w_load_greens_spectra", "s2w_load_adjoint_spectra",
            "s2w_waveforms", "s2w_waveforms_active", "s2w_waveforms_noalloc",
            "s2w_adjoint", "s2w_misfit_gradient", "s2w_waveforms_graph", "s2w_autotune", "s2w_rfft",
-           "s2w_irfft", "s2w_profile_enable", "s2w_profile_read", "s2w_sync",
+           "s2w_irfft", "s2w_retransform_matrix", "s2w_profile_enable", "s2w_profile_read", "s2w_sync",
            "s2w_last_error", "s2w_status_string")
 NUM_STAGES = 8
 STAGE_NAMES = ("rfft_slip", "contract_stage1", "retransform", "contract_stage2",
@@ -98,6 +98,7 @@ def lib():
     L.s2w_autotune.argtypes = [V, I, ctypes.POINTER(Tuning), V]
     L.s2w_rfft.argtypes = [V, P, LL, P, V]
     L.s2w_irfft.argtypes = [V, P, LL, P, V]
+    L.s2w_retransform_matrix.argtypes = [I, I, ctypes.c_double, I, ctypes.POINTER(ctypes.c_double)]
     L.s2w_profile_enable.argtypes = [V, I]
     L.s2w_profile_read.argtypes = [V, ctypes.POINTER(Profile)]
     L.s2w_sync.argtypes = [V]

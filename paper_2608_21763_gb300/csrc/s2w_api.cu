@@ -630,6 +630,19 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
 
 extern "C" {
 
+int s2w_retransform_matrix(int Nt, int dt_mode, double dt, int transpose, double* T) {
+  if (T == nullptr) return fail(nullptr, S2W_ERR_ARG, "retransform_matrix: T is NULL");
+  if (Nt != 32 && Nt != 64 && Nt != 128 && Nt != 256)
+    return fail(nullptr, S2W_ERR_UNSUPPORTED, "retransform_matrix: Nt=%d: supported 32, 64, 128, 256", Nt);
+  if (dt_mode != S2W_DT_BACKWARD && dt_mode != S2W_DT_NONE)
+    return fail(nullptr, S2W_ERR_ARG, "retransform_matrix: dt_mode=%d", dt_mode);
+  if (!(dt > 0.0)) return fail(nullptr, S2W_ERR_ARG, "retransform_matrix: dt must be > 0");
+  if (transpose != 0 && transpose != 1) return fail(nullptr, S2W_ERR_ARG, "retransform_matrix: transpose=%d", transpose);
+  const std::vector<double> M = retransform_matrix(Nt, dt_mode, dt, transpose != 0);
+  std::copy(M.begin(), M.end(), T);
+  return S2W_OK;
+}
+
 void s2w_default_opts(s2w_opts* o) {
   if (!o) return;
   o->prec_g = S2W_PREC_FP32;

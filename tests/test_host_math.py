@@ -1,0 +1,77 @@
+"""Host-side FP64 arithmetic of the library, checked on the CPU: the
+retransform matrix that the tensor engine applies between the stages (Alg. 2:
+IFFT, Truncate, D_t, ZeroPad, FFT of one real signal's Nt + 1 bins), through
+the C ABI (s2w_retransform_matrix touches no device).
+
+Pins: the oracle's own D_t / D_t^T and zero-padded DFT, with numpy's inverse
+real FFT as the IFFT step; without D_t the map is the projection
+DFT . ZeroPad . Truncate . IDFT, hence idempotent."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2608_21763_gb300 as s2w
+
+BACKWARD, NONE = 0, 1
+
+
+def lib_matrix(Nt, dt_mode, dt, transpose):
+    T = np.empty(4 * Nt * Nt, dtype=np.float64)
+    st = s2w.lib().s2w_retransform_matrix(Nt, dt_mode, dt, transpose,
+                                         T.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    assert st == 0, s2w.lib().s2w_last_error(None)
+    return T.reshape(2 * Nt, 2 * Nt)
+
+
+def dofs_to_bins(u, Nt):
+    """k = 0: Re bin 0, k = 1: Re bin Nt, k = 2l, 2l + 1: Re, Im bin l."""
+    X = np.zeros(u.shape[:-1] + (Nt + 1,), dtype=np.complex128)
+    X[..., 0] = u[..., 0]
+    X[..., Nt] = u[..., 1]
+    X[..., 1:Nt] = u[..., 2:2 * Nt:2] + 1j * u[..., 3:2 * Nt:2]
+    return X
+
+
+def bins_to_dofs(X, Nt):
+    u = np.empty(X.shape[:-1] + (2 * Nt,))
+    u[..., 0] = X[..., 0].real
+    u[..., 1] = X[..., Nt].real
+    u[..., 2:2 * Nt:2] = X[..., 1:Nt].real
+    u[..., 3:2 * Nt:2] = X[..., 1:Nt].imag
+    return u
+
+
+@pytest.mark.parametrize("Nt", [32, 64, 256])
+@pytest.mark.parametrize("dt_mode,dt", [(BACKWARD, 1.0), (BACKWARD, 0.25), (NONE, 1.0)])
+@pytest.mark.parametrize("transpose", [0, 1])
+def test_retransform_matrix_matches_the_oracle_steps(Nt, dt_mode, dt, transpose):
+    T = lib_matrix(Nt, dt_mode, dt, transpose)
+    L = 2 * Nt
+    u = np.random.default_rng(Nt + transpose).standard_normal((6, 2 * Nt))
+    m = np.fft.irfft(dofs_to_bins(u, Nt), n=L)[:, :Nt]  # IFFT, then Truncate
+    if dt_mode == NONE:
+        v = m
+    else:
+        v = oracle.dt_transpose(m, dt) if transpose else oracle.dt_apply(m, dt)
+    want = bins_to_dofs(oracle.dft_real(v, L), Nt)      # ZeroPad, then FFT
+    got = u @ T.T
+    assert np.max(np.abs(got - want)) <= 1e-11 * np.max(np.abs(want))
+
+
+@pytest.mark.parametrize("Nt", [32, 128])
+def test_without_dt_the_retransform_is_a_projection(Nt):
+    T = lib_matrix(Nt, NONE, 1.0, 0)
+    assert np.allclose(T @ T, T, rtol=0, atol=1e-12 * np.abs(T).max())
+    assert not np.allclose(T, np.eye(2 * Nt))  # truncation discards the tail
+
+
+def test_retransform_matrix_rejects_bad_arguments():
+    L = s2w.lib()
+    T = (ctypes.c_double * 16)()
+    assert L.s2w_retransform_matrix(48, BACKWARD, 1.0, 0, T) == -6
+    assert L.s2w_retransform_matrix(32, 7, 1.0, 0, T) == -1
+    assert L.s2w_retransform_matrix(32, BACKWARD, 0.0, 0, T) == -1
+    assert L.s2w_retransform_matrix(32, BACKWARD, 1.0, 2, T) == -1
+    assert L.s2w_retransform_matrix(32, BACKWARD, 1.0, 0, None) == -1
