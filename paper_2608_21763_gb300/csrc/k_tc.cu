@@ -576,8 +576,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 // this halves the B bytes staged and read against one CTA per M tile.
 // Barriers: full[s] is used in rank 0 only (the TMA loads of both CTAs
 // complete on it); empty[s] and acc_full exist in both and receive the MMA
-// commits by multicast; acc_empty in rank 0 counts the 4 epilogue warps of
-// each CTA (rank 1's arrive remotely).  Every tcgen05 allocation, MMA and
+// commits by multicast; acc_empty in rank 0 counts the epilogue warps of
+// both CTAs (rank 1's arrive remotely).  Every tcgen05 allocation, MMA and
 // commit of the kernel uses cta_group::2.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t cluster_addr(const void* p, uint32_t rank) {
@@ -667,10 +667,9 @@ __device__ __forceinline__ void tc_mma2_f8f8(uint32_t d_tmem, uint64_t a_desc, u
 // MODE 0: BF16 operands; 1: split (A, A_lo, B, B_lo; three MMAs per K step);
 // 2: FP8 e4m3 A widened to FP16 in shared memory by 4 converter warps per
 // CTA, FP16 B.  Stage layout per CTA: A [A_lo] B-halves [B_lo-halves]
-// [FP8 staging].  FP8: each CTA's staging load completes on its own full[s]
-// (which rank 0's also expects its own and both CTAs' B halves on); the
-// converters of both CTAs then arrive on rank 0's aready[s], which the MMAs
-// wait for.  3: FP8 e4m3 A and B (kind::f8f6f4, no widening): BK counts
+// [FP8 staging].  FP8: each CTA's staging load completes on its own full[s],
+// and rank 0's full[s] also takes both CTAs' B halves; the converters of
+// both CTAs then arrive on rank 0's aready[s], which the MMAs wait for.  3: FP8 e4m3 A and B (kind::f8f6f4, no widening): BK counts
 // bytes = elements, 128-byte rows with 128-byte swizzle, K = 32 per MMA; the
 // per-(bin, 256-row) A scales and per-(bin, column) B scales are applied in
 // the epilogue.
