@@ -62,3 +62,16 @@ def test_single_rank_and_job_rate():
     assert np.array_equal(bench.replica_ruptures(pool, 0), pool)
     # two replicas of 256 ruptures per step over 10 steps in 2 s (slowest rank)
     assert bench.job_rate(2, 256 * 10, 2.0) == 2560.0
+
+
+def test_tensor_dtype_names_the_mma_type():
+    """The bench line's dtype is the stage-1 MMA arithmetic: FP8 operators run
+    FP16 MMAs (operator widened) or e4m3 x e4m3 ones (FP8 activations)."""
+    import argparse
+    sys.path.insert(0, ROOT)
+    import bench
+    ns = argparse.Namespace
+    assert bench.tensor_dtype(ns(prec_g="bf16", fp8_act=False)) == "bf16"
+    assert bench.tensor_dtype(ns(prec_g="bf16_hilo", fp8_act=False)) == "bf16x3"
+    assert bench.tensor_dtype(ns(prec_g="fp8", fp8_act=False)) == "f16"
+    assert bench.tensor_dtype(ns(prec_g="fp8", fp8_act=True)) == "e4m3"
