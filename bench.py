@@ -37,7 +37,7 @@ from paper_2608_21763_gb300 import layout  # noqa: E402
 METRIC = "ruptures/sec to 64-obs waveforms at 1 GB300 (+HBM GB/s, tensor %) at stated rel-L2 error"
 UNIT = "ruptures/s"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
-COMPLEX_BYTES = {"fp32": 8, "bf16": 4, "bf16_hilo": 8, "fp8": 2}
+COMPLEX_BYTES = {"fp32": 8, "fp32_hilo": 16, "bf16": 4, "bf16_hilo": 8, "fp8": 2}
 
 
 def parse():
@@ -51,11 +51,9 @@ def parse():
     ap.add_argument("--torch-dtype", default="fp32", choices=["fp32", "fp64"],
                     help="torch_conv arithmetic type")
     ap.add_argument("--workload", default="plain", choices=sorted(synth.WORKLOADS))
-    ap.add_argument("--prec-g", default="fp32", choices=["fp32", "bf16", "bf16_hilo", "fp8"])
-    ap.add_argument("--prec-p", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--prec-g", default="fp32", choices=["fp32", "fp32_hilo", "bf16", "bf16_hilo", "fp8"])
+    ap.add_argument("--prec-p", default="fp32", choices=["fp32", "fp32_hilo", "bf16"])
     ap.add_argument("--engine", default="auto", choices=["auto", "stream", "tensor"])
-    ap.add_argument("--tc-cluster", type=int, default=0, choices=[0, 1, 2, 4],
-                    help="tensor engine: CTAs per cluster sharing B tiles (0 = library choice)")
     ap.add_argument("--tc-pair", default="auto", choices=["auto", "on", "off"],
                     help="tensor engine: two-SM MMAs (a CTA pair per 256-row tile)")
     ap.add_argument("--fp8-act", action="store_true",
@@ -71,7 +69,7 @@ def parse():
     ap.add_argument("--no-graph", action="store_true",
                     help="time direct calls instead of replayed CUDA graphs of the pipeline")
     ap.add_argument("--no-autotune", action="store_true",
-                    help="keep the default tensor-engine cluster size and AUTO batch threshold")
+                    help="keep the library's default tensor-engine schedule and AUTO batch threshold")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true")
     return ap.parse_args()
@@ -149,10 +147,10 @@ def tensor_dtype(args):
 
 
 # ------------------------------------------------------------------ setup
-def load_context(s2w, wl, geom, prec_g, prec_p, B, device, engine="auto", chunk=1024, tc_cluster=0,
+def load_context(s2w, wl, geom, prec_g, prec_p, B, device, engine="auto", chunk=1024,
                  tc_adjoint=False, single_pass=False, tc_pair="auto", tc_fp8_act=False):
     ctx = s2w.Context(wl.Ns, wl.Ng, wl.No, wl.Nt, prec_g=prec_g, prec_p=prec_p,
-                      max_batch=B, device=device, engine=engine, tc_cluster=tc_cluster, tc_adjoint=tc_adjoint,
+                      max_batch=B, device=device, engine=engine, tc_adjoint=tc_adjoint,
                       single_pass=single_pass, tc_pair=tc_pair, tc_fp8_act=tc_fp8_act)
     for g0 in range(0, wl.Ng, chunk):
         g1 = min(wl.Ng, g0 + chunk)
@@ -288,7 +286,7 @@ def run_ours(args, rank, world, local_rank):
     # so the adjoint runs on the tensor engine as well
     tc_adj = args.mode == "gradient" and args.prec_g in ("bf16", "bf16_hilo") and args.engine != "stream"
     ctx = load_context(s2w, wl, geom, args.prec_g, args.prec_p, B, local_rank, args.engine,
-                       tc_cluster=args.tc_cluster, tc_adjoint=tc_adj, single_pass=args.single_pass,
+                       tc_adjoint=tc_adj, single_pass=args.single_pass,
                        tc_pair=args.tc_pair, tc_fp8_act=args.fp8_act)
     setup_s = time.perf_counter() - t_setup
     slip_d = torch.tensor(slip_np, device=dev)
@@ -310,7 +308,7 @@ def run_ours(args, rank, world, local_rank):
     # tensor-engine choices measured on the loaded operators
     tuning = None
     if not gradient and args.prec_g in ("bf16", "bf16_hilo", "fp8") and args.engine == "auto" \
-            and args.tc_cluster == 0 and not args.single_pass and not args.no_autotune:
+            and not args.single_pass and not args.no_autotune:
         tuning = ctx.autotune(B, stream=stream)
     # one CUDA graph of the pipeline per input buffer, captured during setup
     use_graph = not gradient and not args.no_graph
@@ -458,7 +456,6 @@ def run_ours(args, rank, world, local_rank):
            "config": {"workload": wl.name, "Ns": wl.Ns, "Ng": wl.Ng, "No": wl.No, "Nt": wl.Nt,
                       "ruptures_per_step": B, "prec_g": args.prec_g, "prec_p": args.prec_p,
                       "engine": "tensor" if tensor else "stream", "mode": args.mode,
-                      "tc_cluster": tuning["tc_cluster"] if tuning else args.tc_cluster,
                       "tc_pair": args.tc_pair, "fp8_activations": bool(args.fp8_act),
                       "autotune": tuning, "cuda_graph": use_graph, "single_pass": bool(args.single_pass),
                       "l2": "inputs larger than L2 (every step streams the full operator spectra)",

@@ -54,16 +54,30 @@ typedef enum {
   S2W_ERR_UNSUPPORTED = -6  /* valid request outside what this build supports */
 } s2w_status;
 
-/* Storage of a resident operator spectrum.  Products always accumulate in
- * FP32.  BF16: round-to-nearest-even bf16 complex.  BF16_HILO: two bf16
- * arrays hi = bf16(x), lo = bf16(x - hi), used as hi + lo.  FP8_E4M3: e4m3
- * complex with one FP32 scale per (bin, 256 consecutive grid rows),
- * scale = amax / 448 computed in FP64 (stage-1 operator only). */
+/* Storage of a resident operator spectrum.  Products accumulate in FP32
+ * (FP32 pairs for FP32_HILO).  BF16: round-to-nearest-even bf16 complex.
+ * BF16_HILO: two bf16 arrays hi = bf16(x), lo = bf16(x - hi), used as
+ * hi + lo.  FP8_E4M3: e4m3 complex with one FP32 scale per (bin, 256
+ * consecutive grid rows), scale = amax / 448 computed in FP64 (stage-1
+ * operator only).
+ * FP32_HILO: two FP32 arrays hi + lo holding each spectrum to about 48
+ * significant bits (twice the FP32 bytes), and every step of the stream
+ * engine (the slip FFT, both contractions, the retransform, the reduction
+ * and the final IFFT) carried in FP32 pairs with error-free sums and
+ * products; only the waveforms are rounded to FP32 at the end.  An FFT
+ * evaluation errs relative to its whole 2 Nt-sample window, so when a
+ * waveform's energy lies mostly past the kept Nt samples (late arrivals)
+ * the kept head's relative error grows with that energy ratio; FP32 pairs
+ * keep the head at FP32 accuracy for ratios up to ~10^8.  For both
+ * operators or neither; stream engine only; no adjoint.  Spectra loaded as
+ * complex64 (s2w_load_*_spectra) carry no low-order part (lo = 0): load
+ * time-domain responses, whose spectra the library computes in pairs. */
 typedef enum {
   S2W_PREC_FP32 = 0,
   S2W_PREC_BF16 = 1,
   S2W_PREC_BF16_HILO = 2,
-  S2W_PREC_FP8_E4M3 = 3
+  S2W_PREC_FP8_E4M3 = 3,
+  S2W_PREC_FP32_HILO = 4
 } s2w_prec;
 
 /* D_t between the stages.  The paper (Sec. II-B.2) names "a discrete
@@ -94,15 +108,12 @@ typedef enum { S2W_ENGINE_AUTO = 0, S2W_ENGINE_STREAM = 1, S2W_ENGINE_TENSOR = 2
 
 typedef struct {
   int prec_g;     /* s2w_prec of the stage-1 spectrum Ghat (default FP32) */
-  int prec_p;     /* s2w_prec of the stage-2 spectrum Phat: FP32 or BF16 */
+  int prec_p;     /* s2w_prec of the stage-2 spectrum Phat: FP32, BF16 or FP32_HILO */
   int dt_mode;    /* s2w_dt_mode (default BACKWARD) */
   double dt;      /* time step of D_t in seconds (default 1.0, Sec. II-A) */
   int max_batch;  /* largest B accepted by s2w_waveforms (sizes workspaces) */
   int device;     /* CUDA device ordinal (default 0) */
   int engine;     /* s2w_engine (default AUTO) */
-  int tc_cluster; /* tensor engine: CTAs per cluster sharing each B tile by
-                     multicast, 1, 2 or 4; 0 = library choice (s2w_autotune
-                     can measure and set it) */
   int tc_adjoint; /* 1: also keep transposed copies of both operator spectra
                      (K-major along the grid) so that s2w_adjoint and
                      s2w_misfit_gradient run on the tensor engine for
@@ -122,7 +133,7 @@ typedef struct {
                       spectral loaders then take 2 Nt + 1 bins of length-4 Nt
                       DFTs.  0 (default): L = 2 Nt with the retransform. */
   int tc_pair;     /* tensor engine: S2W_PAIR_ON runs each GEMM whose shape
-                      allows it (cluster 1, BF16 or hi/lo operands, N a
+                      allows it (BF16 or hi/lo operands, N a
                       multiple of 32, at least two 128-row M tiles) as
                       two-SM MMAs: a pair of CTAs computes one 256-row tile
                       with each CTA staging half of the B tile.  S2W_PAIR_OFF
@@ -139,9 +150,45 @@ typedef struct {
                       top of the operator's.  Used for sub-batches whose grid
                       spans at least two 128-row tiles; others take the
                       FP16-activation path.  0 (default): FP16 activations. */
+  int tc_bsub;     /* tensor engine: ruptures per GEMM pass (the sub-batch),
+                      128 or 256 (BF16_HILO: 128); 0 (default) = 256, or 128
+                      for BF16_HILO, capped by max_batch.  The workspaces are
+                      sized for it; s2w_autotune may lower it to 128. */
+  int tc_s2_chunks; /* tensor engine: chunks of the grid (the K extent) that
+                      split the stage-2 GEMM, 1..16; 0 (default) = the count
+                      that balances bins x row tiles x chunks over the SMs.
+                      Results depend on it (the partial sums are added in
+                      chunk order). */
+  const char *tune_cache; /* path of the autotuner's cache file, or NULL
+                      (default).  s2w_autotune reads its choices from it
+                      when the file holds an entry for this problem (Ns,
+                      Ng, No, Nt, the batch, both precisions, the FP8
+                      activation and adjoint options and the GPU model) and
+                      otherwise measures and writes one.  The string is read
+                      during s2w_create and s2w_autotune only. */
+  int fault;        /* test hook, an s2w_fault (default S2W_FAULT_NONE).  When
+                      it is NONE, s2w_create reads the environment variable
+                      S2W_FAULT ("wait", "oom_load" or "launch") instead. */
+  int fault_wait_us; /* with fault = S2W_FAULT_WAIT: the bound of every wait
+                      in the streaming kernels, in microseconds (default
+                      5000; otherwise those waits are bounded by 2 s). */
 } s2w_opts;
 
 enum { S2W_PAIR_AUTO = 0, S2W_PAIR_ON = 1, S2W_PAIR_OFF = 2 };
+
+/* Injected failures for testing the error paths (the paper has no
+ * counterpart).  None of them faults, traps or hangs the GPU.
+ *   WAIT      the streaming stage-1 kernel's copy producer skips its first
+ *             copy, so the consumers' bounded wait on that stage runs out
+ *             after fault_wait_us: the kernel latches the timeout in the
+ *             device status word, drains its own copies and returns; the
+ *             next s2w_sync returns S2W_ERR_TIMEOUT (the waveforms of that
+ *             call are undefined).  Stream engine only.
+ *   OOM_LOAD  every operator load fails as if its staging allocation had
+ *             failed (S2W_ERR_OOM); no row is marked loaded.
+ *   LAUNCH    s2w_waveforms fails before its first launch as if the launch
+ *             had failed (S2W_ERR_CUDA); nothing is enqueued. */
+typedef enum { S2W_FAULT_NONE = 0, S2W_FAULT_WAIT = 1, S2W_FAULT_OOM_LOAD = 2, S2W_FAULT_LAUNCH = 3 } s2w_fault;
 
 /* Fill *o with the defaults listed above (max_batch = 1). */
 void s2w_default_opts(s2w_opts *o);
@@ -264,22 +311,33 @@ int s2w_waveforms_graph(s2w_ctx *ctx, const float *slip, int B, float *q, void *
 
 /* Measured choices of the tensor engine, from s2w_autotune. */
 typedef struct {
-  int tc_cluster;               /* chosen CTAs per cluster (1, 2, 4) */
+  int from_cache;               /* 1: the choices below came from opts.tune_cache; nothing was timed */
   int tc_min_batch;             /* smallest B that ENGINE_AUTO sends to the tensor engine */
-  int probe_batch;              /* batch size of the cluster probes */
-  float ms_stream_per_rupture;  /* stream engine, one rupture */
-  float ms_tensor_cluster[3];   /* tensor engine at probe_batch, clusters 1, 2, 4 (0 = not run) */
+  int tc_bsub;                  /* chosen ruptures per GEMM pass (128 or 256) */
+  int tc_pair;                  /* chosen GEMM form (S2W_PAIR_AUTO, _ON or _OFF) */
+  int tc_s2_chunks;             /* chosen stage-2 K chunk count */
+  int probe_batch;              /* batch size of the form and chunk probes */
+  float ms_stream_per_rupture;  /* stream engine, one rupture (0 = not run) */
+  int form_bsub[6];             /* GEMM forms probed: ruptures per pass (0 = no entry) ... */
+  int form_pair[6];             /* ... and S2W_PAIR_* mode */
+  float ms_form[6];             /* tensor engine at probe_batch in each form */
+  int s2_chunk_cand[4];         /* stage-2 chunk counts probed in the chosen form (0 = none) */
+  float ms_s2_chunks[4];        /* tensor engine at probe_batch with each of them */
   float ms_tensor_batch[7];     /* tensor engine at B = 1, 2, 4, 8, 16, 32, 64 (0 = not run) */
-  int tc_bsub;                  /* chosen tensor sub-batch size (rupture columns per GEMM pass) */
-  float ms_tensor_half;         /* tensor engine at probe_batch in sub-batches of 128 (0 = not run) */
 } s2w_tuning;
 
-/* Time the engines on the loaded operators (data-independent timings, dummy
- * inputs) and set the context's tensor-engine cluster size, sub-batch size
- * (256 or 128 ruptures per GEMM pass) and the batch size from which AUTO
- * uses the tensor engine.  Uses up to B ruptures
- * (<= max_batch).  Without the tensor engine only ms_stream_per_rupture is
- * measured.  `out` may be NULL. */
+/* Choose the tensor engine's schedule for this problem by timing it on the
+ * loaded operators (dummy inputs: the timings do not depend on the data):
+ * the GEMM form (ruptures per pass and two-SM or single-CTA tiles), the
+ * stage-2 K chunk count (how the grid is split between the persistent
+ * CTAs), and the batch size from which AUTO uses the tensor engine instead
+ * of streaming the spectra once per rupture.  The choices are kept in the
+ * context (and written to opts.tune_cache when one is set); an entry already
+ * in that cache is applied without timing.  Options the caller fixed
+ * (tc_bsub, tc_pair other than AUTO, tc_s2_chunks) are not searched.
+ * Uses up to B ruptures (<= max_batch).  Without the tensor engine only
+ * ms_stream_per_rupture is measured.  Captured graphs (s2w_waveforms_graph)
+ * are dropped: they hold the old schedule.  `out` may be NULL. */
 int s2w_autotune(s2w_ctx *ctx, int B, s2w_tuning *out, void *stream);
 
 /* Zero-padded real FFT of `rows` signals of Nt samples (the transform of

@@ -21,10 +21,12 @@ from . import layout  # noqa: F401  (size arithmetic, no library load)
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _lib = None
 
-PREC = {"fp32": 0, "bf16": 1, "bf16_hilo": 2, "fp8": 3}
+PREC = {"fp32": 0, "bf16": 1, "bf16_hilo": 2, "fp8": 3, "fp32_hilo": 4}
 ENGINE = {"auto": 0, "stream": 1, "tensor": 2}
 DT_MODE = {"backward": 0, "none": 1}
 PAIR = {"auto": 0, "on": 1, "off": 2}
+PAIR_NAME = {v: k for k, v in PAIR.items()}
+FAULT = {"none": 0, "wait": 1, "oom_load": 2, "launch": 3}
 STATUS = {0: "S2W_OK", -1: "S2W_ERR_ARG", -2: "S2W_ERR_OOM", -3: "S2W_ERR_STATE",
           -4: "S2W_ERR_CUDA", -5: "S2W_ERR_TIMEOUT", -6: "S2W_ERR_UNSUPPORTED"}
 
@@ -53,18 +55,22 @@ class Profile(ctypes.Structure):
 
 
 class Tuning(ctypes.Structure):
-    _fields_ = [("tc_cluster", ctypes.c_int), ("tc_min_batch", ctypes.c_int), ("probe_batch", ctypes.c_int),
-                ("ms_stream_per_rupture", ctypes.c_float), ("ms_tensor_cluster", ctypes.c_float * 3),
-                ("ms_tensor_batch", ctypes.c_float * 7), ("tc_bsub", ctypes.c_int),
-                ("ms_tensor_half", ctypes.c_float)]
+    _fields_ = [("from_cache", ctypes.c_int), ("tc_min_batch", ctypes.c_int), ("tc_bsub", ctypes.c_int),
+                ("tc_pair", ctypes.c_int), ("tc_s2_chunks", ctypes.c_int), ("probe_batch", ctypes.c_int),
+                ("ms_stream_per_rupture", ctypes.c_float), ("form_bsub", ctypes.c_int * 6),
+                ("form_pair", ctypes.c_int * 6), ("ms_form", ctypes.c_float * 6),
+                ("s2_chunk_cand", ctypes.c_int * 4), ("ms_s2_chunks", ctypes.c_float * 4),
+                ("ms_tensor_batch", ctypes.c_float * 7)]
 
 
 class Opts(ctypes.Structure):
     _fields_ = [("prec_g", ctypes.c_int), ("prec_p", ctypes.c_int),
                 ("dt_mode", ctypes.c_int), ("dt", ctypes.c_double),
                 ("max_batch", ctypes.c_int), ("device", ctypes.c_int),
-                ("engine", ctypes.c_int), ("tc_cluster", ctypes.c_int), ("tc_adjoint", ctypes.c_int),
-                ("single_pass", ctypes.c_int), ("tc_pair", ctypes.c_int), ("tc_fp8_act", ctypes.c_int)]
+                ("engine", ctypes.c_int), ("tc_adjoint", ctypes.c_int),
+                ("single_pass", ctypes.c_int), ("tc_pair", ctypes.c_int), ("tc_fp8_act", ctypes.c_int),
+                ("tc_bsub", ctypes.c_int), ("tc_s2_chunks", ctypes.c_int), ("tune_cache", ctypes.c_char_p),
+                ("fault", ctypes.c_int), ("fault_wait_us", ctypes.c_int)]
 
 
 def lib_path() -> str:
@@ -156,14 +162,17 @@ class Context:
     """One resident operator pair (Ghat, Phat) on one GPU.
 
     ``Context(Ns, Ng, No, Nt, prec_g="fp32", prec_p="fp32", dt_mode="backward",
-    dt=1.0, max_batch=1, device=0, engine="auto")``; load the operators with
+    dt=1.0, max_batch=1, device=0, engine="auto", ...)``; load the operators with
     ``load_greens``/``load_adjoint`` (time-domain responses, any row chunking),
-    then call ``waveforms``.
+    then call ``waveforms``.  The keyword options mirror ``s2w_opts``
+    (``include/s2w.h``); ``tune_cache`` is a file path, ``fault`` one of
+    ``FAULT``'s names (a test hook).
     """
 
     def __init__(self, Ns, Ng, No, Nt, prec_g="fp32", prec_p="fp32",
-                 dt_mode="backward", dt=1.0, max_batch=1, device=0, engine="auto", tc_cluster=0,
-                 tc_adjoint=False, single_pass=False, tc_pair="auto", tc_fp8_act=False):
+                 dt_mode="backward", dt=1.0, max_batch=1, device=0, engine="auto",
+                 tc_adjoint=False, single_pass=False, tc_pair="auto", tc_fp8_act=False, tc_bsub=0,
+                 tc_s2_chunks=0, tune_cache=None, fault="none", fault_wait_us=5000):
         L = lib()
         o = Opts()
         L.s2w_default_opts(ctypes.byref(o))
@@ -171,11 +180,16 @@ class Context:
         o.dt_mode, o.dt = DT_MODE[dt_mode], float(dt)
         o.max_batch, o.device = int(max_batch), int(device)
         o.engine = ENGINE[engine]
-        o.tc_cluster = int(tc_cluster)
         o.tc_adjoint = int(bool(tc_adjoint))
         o.single_pass = int(bool(single_pass))
         o.tc_pair = PAIR[tc_pair]
         o.tc_fp8_act = int(bool(tc_fp8_act))
+        o.tc_bsub = int(tc_bsub)
+        o.tc_s2_chunks = int(tc_s2_chunks)
+        cache = None if tune_cache is None else os.fsencode(tune_cache)
+        o.tune_cache = cache
+        o.fault = FAULT[fault]
+        o.fault_wait_us = int(fault_wait_us)
         h = ctypes.c_void_p()
         st = L.s2w_create(Ns, Ng, No, Nt, ctypes.byref(o), ctypes.byref(h))
         if st != 0:
@@ -292,18 +306,22 @@ class Context:
         return q
 
     def autotune(self, B, stream=None):
-        """Measure the engines on the loaded operators; sets the tensor-engine
-        cluster size and the AUTO batch threshold.  Returns the measurements."""
+        """Choose the tensor engine's schedule (GEMM form, stage-2 chunk
+        count, AUTO batch threshold) by timing it on the loaded operators, or
+        from the context's tune cache.  Returns the choices and timings."""
         t = Tuning()
         st = stream
         if st is None:
             import torch
             st = torch.cuda.current_stream(self.device)
         self._check(lib().s2w_autotune(self._h, int(B), ctypes.byref(t), _stream(st)))
-        return {"tc_cluster": t.tc_cluster, "tc_min_batch": t.tc_min_batch, "probe_batch": t.probe_batch,
-                "ms_stream_per_rupture": t.ms_stream_per_rupture,
-                "ms_tensor_cluster": list(t.ms_tensor_cluster), "ms_tensor_batch": list(t.ms_tensor_batch),
-                "tc_bsub": t.tc_bsub, "ms_tensor_half": t.ms_tensor_half}
+        forms = [{"bsub": t.form_bsub[k], "pair": PAIR_NAME[t.form_pair[k]], "ms": t.ms_form[k]}
+                 for k in range(6) if t.form_bsub[k] > 0]
+        chunks = [{"chunks": t.s2_chunk_cand[k], "ms": t.ms_s2_chunks[k]} for k in range(4) if t.s2_chunk_cand[k] > 0]
+        return {"from_cache": bool(t.from_cache), "tc_min_batch": t.tc_min_batch, "tc_bsub": t.tc_bsub,
+                "tc_pair": PAIR_NAME[t.tc_pair], "tc_s2_chunks": t.tc_s2_chunks, "probe_batch": t.probe_batch,
+                "ms_stream_per_rupture": t.ms_stream_per_rupture, "forms": forms, "s2_chunks": chunks,
+                "ms_tensor_batch": list(t.ms_tensor_batch)}
 
     def misfit_gradient(self, slip, d, grad=None, loss=None, stream=None):
         """Gradient of 0.5 ||q(slip[b]) - d[b]||^2 per rupture; returns

@@ -15,8 +15,13 @@
 // l handles the 16-byte chunks l, l + 32, ..., so a warp reads 512 contiguous
 // bytes per step); a short row (a few subfaults) gets a power-of-two group of
 // lanes with about four chunks each, several rows per warp pass.  Each lane
-// keeps its slice of x_vec in registers across rows that share it.  Products accumulate in FP32; FP8 rows are rescaled by their
-// per-(bin, 256-row block) scale after the dot product.
+// keeps its slice of x_vec in registers across rows that share it.  Products
+// accumulate in FP32; FP8 rows are rescaled by their per-(bin, 256-row block)
+// scale after the dot product.  FP32_HILO rows (hi and lo FP32 arrays) meet
+// a vector of pairs (x, x_lo): each product is formed exactly (TwoProduct)
+// and summed by TwoSum into double-float accumulators (df.cuh), written as
+// pairs (y, y_lo).
+#include "df.cuh"
 #include "s2w_internal.cuh"
 
 namespace s2w {
@@ -94,9 +99,11 @@ struct Chunk<EL_FP8> {
 };
 
 // EL selects the unpacker (EL_BF16 also serves the hi/lo pair when HILO);
-// SHORT: rows of at most 64 chunks, shared by lane groups.
-template <int EL, bool HILO, bool SHORT>
+// SHORT: rows of at most 64 chunks, shared by lane groups; DF (with EL_FP32
+// and HILO): FP32 pair rows and vectors, double-float sums.
+template <int EL, bool HILO, bool SHORT, bool DF = false>
 __global__ void __launch_bounds__(kThreads, 1) k_stream_dot(const StreamArgs a, int stage_rows) {
+  static_assert(!DF || (EL == EL_FP32 && HILO), "pair rows: FP32 hi and lo arrays");
   using CH = Chunk<EL>;
   constexpr int C = CH::C;
   // chunk slots per lane: a short row gives each lane at most four chunks
@@ -113,6 +120,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_stream_dot(const StreamArgs a, 
   const long long r0 = a.F * blockIdx.x / gridDim.x;
   const long long r1 = a.F * (blockIdx.x + 1) / gridDim.x;
   const int nst = static_cast<int>((r1 - r0 + stage_rows - 1) / stage_rows);
+  const unsigned long long wlim = a.wait_ns ? a.wait_ns : kWaitLimitNs;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -130,8 +138,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_stream_dot(const StreamArgs a, 
       for (; k < nst; ++k) {
         const int s = k % kStages;
         if (k >= kStages &&
-            !mbar_wait_bounded(empty + s, ((k / kStages) - 1) & 1, a.status, DEV_ERR_TIMEOUT_EMPTY))
+            !mbar_wait_bounded(empty + s, ((k / kStages) - 1) & 1, a.status, DEV_ERR_TIMEOUT_EMPTY, wlim))
           break;
+        if (a.fault_skip && k == 0) continue;  // test hook: stage 0 never fills (no copy, no expected bytes)
         const long long rs = r0 + static_cast<long long>(k) * stage_rows;
         const int nr = static_cast<int>(min(static_cast<long long>(stage_rows), r1 - rs));
         const uint32_t bytes = static_cast<uint32_t>(nr) * row_bytes;
@@ -144,7 +153,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_stream_dot(const StreamArgs a, 
       }
       // Never leave the CTA with copies in flight: wait for the last stages issued.
       for (int kk = (k > kStages ? k - kStages : 0); kk < k; ++kk)
-        mbar_wait_bounded(full + kk % kStages, (kk / kStages) & 1, a.status, DEV_ERR_TIMEOUT_FULL);
+        mbar_wait_bounded(full + kk % kStages, (kk / kStages) & 1, a.status, DEV_ERR_TIMEOUT_FULL, wlim);
     }
     return;
   }
@@ -160,10 +169,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_stream_dot(const StreamArgs a, 
   const int sub = lane % lpr;   // lane within its row group
   const int grp = lane / lpr;   // row group within the warp
   float2 xr[T][C];
+  float2 xl[DF ? T : 1][DF ? C : 1];  // DF: low-order parts of x_vec
   long long vec = -1, vec_end = 0;  // x_vec of rows [vec_end - rows_per_vec, vec_end); rows rise per lane
   for (int k = 0; k < nst; ++k) {
     const int s = k % kStages;
-    if (!mbar_wait_bounded(full + s, (k / kStages) & 1, a.status, DEV_ERR_TIMEOUT_FULL)) return;
+    if (!mbar_wait_bounded(full + s, (k / kStages) & 1, a.status, DEV_ERR_TIMEOUT_FULL, wlim)) return;
     const long long rs = r0 + static_cast<long long>(k) * stage_rows;
     const int nr = static_cast<int>(min(static_cast<long long>(stage_rows), r1 - rs));
     for (int base = warp * rpp; base < nr; base += kConsumerWarps * rpp) {
@@ -186,12 +196,54 @@ __global__ void __launch_bounds__(kThreads, 1) k_stream_dot(const StreamArgs a, 
             }
             xr[t][2 * q] = make_float2(v.x, v.y);
             xr[t][2 * q + 1] = make_float2(v.z, v.w);
+            if constexpr (DF) {
+              const float4* xvl = reinterpret_cast<const float4*>(a.x_lo + vec * a.x_stride);
+              const float4 w = (c < nchunk) ? __ldg(xvl + c * (C / 2) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+              xl[t][2 * q] = make_float2(w.x, w.y);
+              xl[t][2 * q + 1] = make_float2(w.z, w.w);
+            }
           }
         }
       }
       const int rrow = valid ? lr : base;
       const uint4* row = reinterpret_cast<const uint4*>(buf + s * stage_bytes + rrow * row_bytes);
       const uint4* row_lo = reinterpret_cast<const uint4*>(buf_lo + s * stage_bytes + rrow * row_bytes);
+      if constexpr (DF) {
+        // (g + g_lo)(x + x_lo) per complex entry, four real pair products
+        // into two compensated accumulators per chain (two chains)
+        dacc sr[2] = {{0.f, 0.f}, {0.f, 0.f}}, si[2] = {{0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+          const int c = sub + lpr * t;
+          if (valid && c < nchunk) {
+            float2 g[C], gl[C];
+            CH::unpack(row[c], g);
+            CH::unpack(row_lo[c], gl);
+#pragma unroll
+            for (int q = 0; q < C; ++q) {
+              const dfl gr{g[q].x, gl[q].x}, gi{g[q].y, gl[q].y};
+              const dfl xre{xr[t][q].x, xl[t][q].x}, xim{xr[t][q].y, xl[t][q].y};
+              acc_mac(sr[q & 1], gr, xre);
+              acc_mac(sr[q & 1], df_neg(gi), xim);
+              acc_mac(si[q & 1], gr, xim);
+              acc_mac(si[q & 1], gi, xre);
+            }
+          }
+        }
+        dacc ar = acc_merge(sr[0], sr[1]), ai = acc_merge(si[0], si[1]);
+        for (int o = lpr / 2; o > 0; o >>= 1) {
+          const dacc br{__shfl_xor_sync(0xffffffffu, ar.s, o), __shfl_xor_sync(0xffffffffu, ar.c, o)};
+          const dacc bi{__shfl_xor_sync(0xffffffffu, ai.s, o), __shfl_xor_sync(0xffffffffu, ai.c, o)};
+          ar = acc_merge(ar, br);
+          ai = acc_merge(ai, bi);
+        }
+        if (valid && sub == 0) {
+          const dfl yr = acc_get(ar), yi = acc_get(ai);
+          a.y[f] = make_float2(yr.hi, yi.hi);
+          a.y_lo[f] = make_float2(yr.lo, yi.lo);
+        }
+        continue;
+      }
       float ar0 = 0.f, ai0 = 0.f, ar1 = 0.f, ai1 = 0.f;
 #pragma unroll
       for (int t = 0; t < T; ++t) {
@@ -413,7 +465,7 @@ cudaError_t launch_tt(const StreamTArgs& a, int num_sms, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <int EL, bool HILO, bool SHORT>
+template <int EL, bool HILO, bool SHORT, bool DF = false>
 cudaError_t launch_t(const StreamArgs& a, int num_sms, cudaStream_t st) {
   constexpr int C = Chunk<EL>::C;
   const int row_bytes = a.row_len * (16 / C);
@@ -422,13 +474,13 @@ cudaError_t launch_t(const StreamArgs& a, int num_sms, cudaStream_t st) {
   if (stage_rows >= kConsumerWarps) stage_rows -= stage_rows % kConsumerWarps;
   if (stage_rows < 1) stage_rows = 1;
   const size_t smem = 128 + static_cast<size_t>(kStages) * stage_rows * row_bytes * (HILO ? 2 : 1);
-  cudaError_t e = cudaFuncSetAttribute(k_stream_dot<EL, HILO, SHORT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(smem));
+  cudaError_t e = cudaFuncSetAttribute(k_stream_dot<EL, HILO, SHORT, DF>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   long long grid = num_sms;
   if (grid > a.F) grid = a.F;
   if (grid < 1) grid = 1;
-  k_stream_dot<EL, HILO, SHORT><<<static_cast<unsigned>(grid), kThreads, smem, st>>>(a, stage_rows);
+  k_stream_dot<EL, HILO, SHORT, DF><<<static_cast<unsigned>(grid), kThreads, smem, st>>>(a, stage_rows);
   return cudaGetLastError();
 }
 
@@ -454,6 +506,10 @@ cudaError_t launch_stream_dot(const StreamArgs& a, int num_sms, cudaStream_t st)
     case EL_FP8:
       return short_rows(a, 8) ? launch_t<EL_FP8, false, true>(a, num_sms, st)
                               : launch_t<EL_FP8, false, false>(a, num_sms, st);
+    case EL_FP32_HILO:
+      if (a.rows_lo == nullptr || a.x_lo == nullptr || a.y_lo == nullptr) return cudaErrorInvalidValue;
+      return short_rows(a, 2) ? launch_t<EL_FP32, true, true, true>(a, num_sms, st)
+                              : launch_t<EL_FP32, true, false, true>(a, num_sms, st);
     default: return cudaErrorInvalidValue;
   }
 }

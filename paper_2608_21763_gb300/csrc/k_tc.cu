@@ -3,8 +3,10 @@
 // memory (kind::f16 for BF16 / FP16 operands, kind::f8f6f4 for e4m3 x e4m3),
 // operands staged by TMA with 128-byte (or 64-byte) swizzle.  Two GEMM
 // bodies: tc_gemm_body, one CTA per 128-row tile (optionally two tiles per
-// unit, or clusters sharing B by multicast), and tc_gemm2_body, the two-SM
-// form (cta_group::2: a CTA pair per 256-row tile, each staging half of B).
+// unit sharing each B tile), and tc_gemm2_body, the two-SM form
+// (cta_group::2: a CTA pair per 256-row tile, each staging half of B).  Every
+// CTA issues its own TMA loads of the tiles it uses; tiles shared by
+// several CTAs are served from L2.
 // The retransform between the stages is a GEMM too (k_tc_retransform).
 //
 // Complex products run as one real GEMM per bin through a real embedding that
@@ -59,17 +61,6 @@ __device__ __forceinline__ void tma_load_3d(void* sdst, const CUtensorMap* tm, i
       : "memory");
 }
 
-// Same load, delivered to the same shared-memory offset (and completing on the
-// same barrier offset) in every CTA of the cluster whose bit is set in mask.
-__device__ __forceinline__ void tma_load_3d_mc(void* sdst, const CUtensorMap* tm, int c0, int c1, int c2,
-                                               uint64_t* bar, uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1, {%2, "
-      "%3, %4}], [%5], %6;" ::"r"(smem_u32(sdst)),
-      "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar)), "h"(mask)
-      : "memory");
-}
-
 __device__ __forceinline__ uint32_t cluster_ctarank() {
   uint32_t r;
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
@@ -112,15 +103,6 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
 __device__ __forceinline__ void tc_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
-}
-
-// Arrive once on `bar` in every CTA of `mask` when this thread's issued MMAs complete.
-__device__ __forceinline__ void tc_commit_mc(uint64_t* bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-          smem_u32(bar)),
-      "h"(mask)
-      : "memory");
 }
 
 __device__ __forceinline__ void tc_mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
@@ -289,9 +271,6 @@ __device__ __forceinline__ void widen_fp8_row(const unsigned char* src_row, unsi
 
 // One ring of K-block stages, each holding the A tile and the B tile of the
 // same K block (loaded together, released together).
-// CL > 1: clusters of CL CTAs take CL adjacent M tiles of the same (bin, K
-// chunk); each CTA loads 1/CL of the B tile and multicasts it to all of them,
-// and every CTA's MMA releases a stage in all of them (empty barriers count CL).
 // Split precision (a_lo / b_lo): an operand stored as hi + lo BF16 parts has
 // both parts in every stage, and each K step issues A B, then A B_lo and/or
 // A_lo B into the same FP32 accumulator (the A_lo B_lo term, ~2^-18
@@ -303,14 +282,14 @@ __device__ __forceinline__ void widen_fp8_row(const unsigned char* src_row, unsi
 // FP16 A and B (B packed as FP16 with a power-of-two scale from its amax);
 // the per-(bin, 256-row) scale and the B scale are undone in the epilogue.  Each MODE is its own instantiation and kernel, so the plain
 // kernel carries none of the other modes' code.
-// MT = 2 (N <= 256, no cluster, not FP8): a unit takes two adjacent M tiles
+// MT = 2 (N <= 256, not FP8): a unit takes two adjacent M tiles
 // that share every B tile, with one accumulator each (2N TMEM columns): A
 // gets two thirds of each stage instead of half at N = 128, and B is read
 // from L2 once per two tiles.
-template <int BK, int CL, int MODE, int MT = 1>
+template <int BK, int MODE, int MT = 1>
 __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUtensorMap* tmB, const CUtensorMap* tmA2,
                                              const CUtensorMap* tmB2, const TcArgs& a) {
-  static_assert(MT == 1 || (CL == 1 && MODE != 2), "M-tile pairs: no cluster, no FP8");
+  static_assert(MT == 1 || MODE != 2, "M-tile pairs: not with FP8 A");
   constexpr bool SPLIT = MODE == 1;
   constexpr bool F8 = MODE == 2;
   constexpr int EPW = F8 ? kEpwF8 : kEpw;
@@ -319,10 +298,8 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUten
   constexpr int kStg = F8 ? kBlockM * BK : 0;  // FP8 staging bytes per stage
   constexpr int kA = kBlockM * BK * 2;
   constexpr int a_tile = kA * (SPLIT ? 2 : 1);  // one M tile's A (+ A_lo) bytes per stage
-  constexpr uint16_t kMask = static_cast<uint16_t>((1u << CL) - 1u);
-  const uint32_t crank = CL > 1 ? cluster_ctarank() : 0u;
-  const long long cid = CL > 1 ? static_cast<long long>(cluster_id_x()) : static_cast<long long>(blockIdx.x);
-  const long long ncl = CL > 1 ? static_cast<long long>(cluster_count_x()) : static_cast<long long>(gridDim.x);
+  const long long cid = static_cast<long long>(blockIdx.x);
+  const long long ncl = static_cast<long long>(gridDim.x);
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
   const int N = a.N;
@@ -339,18 +316,17 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUten
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const int nk_total = (a.K + BK - 1) / BK;
-  const int mtg = (a.m_tiles + CL * MT - 1) / (CL * MT);  // M-tile groups (one per cluster unit / pair)
+  const int mtg = (a.m_tiles + MT - 1) / MT;  // M-tile groups (one per unit)
   const long long units = static_cast<long long>(a.Nb) * mtg * a.n_kchunks;
   const int n_mma = N > 256 ? N / 256 : 1;
   const int n_mma_cols = N > 256 ? 256 : N;
-  const int slice_rows = N / CL;  // B rows this CTA loads (and multicasts)
   // FP8 A is widened to FP16 (one conversion per pair, exact); B is FP16 too
   const uint32_t idesc = F8 ? idesc_f16(kBlockM, n_mma_cols) : idesc_bf16(kBlockM, n_mma_cols);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(full + s, 1);
-      mbar_init(empty + s, CL);
+      mbar_init(empty + s, 1);
       if (F8) mbar_init(aready + s, 4);
     }
     mbar_init(acc_full, 1);
@@ -363,14 +339,13 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUten
   }
   tc_fence_before();
   __syncthreads();
-  if (CL > 1) cluster_sync_all();  // every CTA's barriers exist before any multicast
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
 
   auto unit_coords = [&](long long u, int& l, int& mt, int& kc) {
     kc = static_cast<int>(u % a.n_kchunks);
     const long long r = u / a.n_kchunks;
-    mt = static_cast<int>(r % mtg) * CL * MT + static_cast<int>(crank);  // first M tile of the unit
+    mt = static_cast<int>(r % mtg) * MT;  // first M tile of the unit
     l = static_cast<int>(r / mtg);
   };
 
@@ -402,13 +377,8 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUten
             }
           }
           auto load_b = [&](const CUtensorMap* tb, unsigned char* sb) {
-            if (CL == 1) {
-              for (int c = 0; c < n_mma; ++c)
-                tma_load_3d(sb + c * n_mma_cols * BK * 2, tb, kb * BK, c * n_mma_cols, l, full + s);
-            } else {
-              tma_load_3d_mc(sb + crank * slice_rows * BK * 2, tb, kb * BK, static_cast<int>(crank) * slice_rows, l,
-                             full + s, kMask);
-            }
+            for (int c = 0; c < n_mma; ++c)
+              tma_load_3d(sb + c * n_mma_cols * BK * 2, tb, kb * BK, c * n_mma_cols, l, full + s);
           };
           load_b(tmB, sa + a_all);
           if constexpr (SPLIT) load_b(tmB2, sa + a_all + b_bytes);
@@ -416,8 +386,8 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUten
       }
       for (int kk = (it > S ? it - S : 0); kk < it; ++kk)
         mbar_wait_bounded(full + kk % S, (kk / S) & 1, a.status, DEV_ERR_TIMEOUT_FULL);
-      // the last stages must also have been released by every CTA of the
-      // cluster (their multicast commits land here) before anyone leaves
+      // the last stages must also have been released by the MMAs before the
+      // CTA tears down
       for (int kk = (it > S ? it - S : 0); kk < it; ++kk)
         mbar_wait_bounded(empty + kk % S, (kk / S) & 1, a.status, DEV_ERR_TIMEOUT_EMPTY);
     }
@@ -462,10 +432,7 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUten
               }
             }
           }
-          if (CL == 1)
-            tc_commit(empty + s);
-          else
-            tc_commit_mc(empty + s, kMask);
+          tc_commit(empty + s);
         }
         if (!ok) break;
         tc_commit(acc_full);
@@ -529,19 +496,18 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUten
     tc_fence_after();
     tmem_dealloc(tmem, a.tmem_cols);
   }
-  if (CL > 1) cluster_sync_all();  // no CTA leaves while a peer may still signal it
 }
 
-template <int BK, int CL>
+template <int BK>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
-  tc_gemm_body<BK, CL, 0>(&tmA, &tmB, nullptr, nullptr, a);
+  tc_gemm_body<BK, 0>(&tmA, &tmB, nullptr, nullptr, a);
 }
 
 template <int BK>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_tc_gemm_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
-  tc_gemm_body<BK, 1, 0, 2>(&tmA, &tmB, nullptr, nullptr, a);
+  tc_gemm_body<BK, 0, 2>(&tmA, &tmB, nullptr, nullptr, a);
 }
 
 template <int BK>
@@ -549,21 +515,21 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     k_tc_gemm_split_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                          const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB2,
                          const TcArgs a) {
-  tc_gemm_body<BK, 1, 1, 2>(&tmA, &tmB, &tmA2, &tmB2, a);
+  tc_gemm_body<BK, 1, 2>(&tmA, &tmB, &tmA2, &tmB2, a);
 }
 
-template <int BK, int CL>
+template <int BK>
 __global__ void __launch_bounds__(kTcThreadsF8, 1)
     k_tc_gemm_f8(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
-  tc_gemm_body<BK, CL, 2>(&tmA, &tmB, nullptr, nullptr, a);
+  tc_gemm_body<BK, 2>(&tmA, &tmB, nullptr, nullptr, a);
 }
 
-template <int BK, int CL>
+template <int BK>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_tc_gemm_split(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB2,
                     const TcArgs a) {
-  tc_gemm_body<BK, CL, 1>(&tmA, &tmB, &tmA2, &tmB2, a);
+  tc_gemm_body<BK, 1>(&tmA, &tmB, &tmA2, &tmB2, a);
 }
 
 // ---------------------------------------------------------------------------
@@ -576,7 +542,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 // this halves the B bytes staged and read against one CTA per M tile.
 // Barriers: full[s] is used in rank 0 only (the TMA loads of both CTAs
 // complete on it); empty[s] and acc_full exist in both and receive the MMA
-// commits by multicast; acc_empty in rank 0 counts the epilogue warps of
+// commits as mbarrier arrives in both CTAs (tcgen05.commit with a CTA mask:
+// an arrive, no data moves); acc_empty in rank 0 counts the epilogue warps of
 // both CTAs (rank 1's arrive remotely).  Every tcgen05 allocation, MMA and
 // commit of the kernel uses cta_group::2.
 // ---------------------------------------------------------------------------
@@ -635,6 +602,8 @@ __device__ __forceinline__ void tmem_relinquish2() {
 __device__ __forceinline__ void tmem_dealloc2(uint32_t taddr, uint32_t ncols) {
   asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
+// Arrive once on `bar` in each CTA of the pair whose bit is set in `mask` when
+// this thread's issued MMAs complete (an mbarrier arrive only).
 __device__ __forceinline__ void tc_commit2_mc(uint64_t* bar, uint16_t mask) {
   asm volatile(
       "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
@@ -1092,7 +1061,8 @@ __host__ __device__ constexpr int rt_threads(bool split) { return 32 * (2 + 4 * 
 // slice of T (rank r: rows r 128 .. of the slice), so the T bytes staged and
 // read per CTA halve.  Rank 0 issues the MMAs; both CTAs' fill warps arrive
 // on rank 0's afull, both CTAs' T loads complete on rank 0's tfull, and the
-// MMA commits reach tempty / afree / acc_full of both CTAs by multicast.
+// MMA commits arrive on tempty / afree / acc_full of both CTAs (mbarrier
+// arrives with a CTA mask; no data moves).
 template <bool SPLIT, bool PAIR>
 __global__ void __launch_bounds__(rt_threads(SPLIT), 1)
     k_tc_retransform(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmT2,
@@ -1547,49 +1517,27 @@ int tc_stages_pair(int N, int split, int fp8) {
   return s;
 }
 
-template <int BK, int CL, int MODE>
-cudaError_t launch_tc_cl(const CUtensorMap& tmA, const CUtensorMap& tmB, const CUtensorMap& tmA2,
-                         const CUtensorMap& tmB2, const TcArgs& a, int num_sms, size_t smem, cudaStream_t st) {
-  auto kern = k_tc_gemm<BK, CL>;
-  auto kern_s = k_tc_gemm_split<BK, CL>;
-  auto kern_f = k_tc_gemm_f8<BK, CL>;
+// One CTA per SM (persistent over the units), one CTA per 128-row tile.
+template <int BK, int MODE>
+cudaError_t launch_tc_one(const CUtensorMap& tmA, const CUtensorMap& tmB, const CUtensorMap& tmA2,
+                          const CUtensorMap& tmB2, const TcArgs& a, int num_sms, size_t smem, cudaStream_t st) {
+  auto kern = k_tc_gemm<BK>;
+  auto kern_s = k_tc_gemm_split<BK>;
+  auto kern_f = k_tc_gemm_f8<BK>;
   const void* kfn = MODE == 1   ? reinterpret_cast<const void*>(kern_s)
                     : MODE == 2 ? reinterpret_cast<const void*>(kern_f)
                                 : reinterpret_cast<const void*>(kern);
   cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
-  const long long cunits = static_cast<long long>(a.Nb) * ((a.m_tiles + CL - 1) / CL) * a.n_kchunks;
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
-  cfg.blockDim = dim3(MODE == 2 ? kTcThreadsF8 : kTcThreads);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  long long nclusters = num_sms / CL;
-  if (CL > 1) {
-    e = cudaFuncSetAttribute(kfn, cudaFuncAttributeNonPortableClusterSizeAllowed, 0);
-    if (e != cudaSuccess) return e;
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CL;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cfg.gridDim = dim3(static_cast<unsigned>(nclusters * CL));
-    int active = 0;
-    e = cudaOccupancyMaxActiveClusters(&active, kfn, &cfg);
-    if (e != cudaSuccess) return e;
-    if (active < 1) return cudaErrorInvalidConfiguration;
-    nclusters = active;
-  }
-  if (nclusters > cunits) nclusters = cunits;
-  cfg.gridDim = dim3(static_cast<unsigned>(nclusters * CL));
+  const long long units = static_cast<long long>(a.Nb) * a.m_tiles * a.n_kchunks;
+  const unsigned grid = static_cast<unsigned>(units < num_sms ? units : num_sms);
+  const unsigned threads = MODE == 2 ? kTcThreadsF8 : kTcThreads;
   if (MODE == 1)
-    e = cudaLaunchKernelEx(&cfg, kern_s, tmA, tmB, tmA2, tmB2, a);
+    kern_s<<<grid, threads, smem, st>>>(tmA, tmB, tmA2, tmB2, a);
   else if (MODE == 2)
-    e = cudaLaunchKernelEx(&cfg, kern_f, tmA, tmB, a);
+    kern_f<<<grid, threads, smem, st>>>(tmA, tmB, a);
   else
-    e = cudaLaunchKernelEx(&cfg, kern, tmA, tmB, a);
-  if (e != cudaSuccess) return e;
+    kern<<<grid, threads, smem, st>>>(tmA, tmB, a);
   return cudaGetLastError();
 }
 
@@ -1605,8 +1553,8 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
   if (a.a_lo != a.b_lo || (a.a_lo != 0 && a.a_lo != 1) || (a.a_lo && (!tmA2 || !tmB2))) return cudaErrorInvalidValue;
   if ((a.a_fp8 != 0 && a.a_fp8 != 1) || (a.a_fp8 && a.a_lo) || (a.a_fp8 && a.row_scale == nullptr))
     return cudaErrorInvalidValue;
-  if (a.cta2) {  // two-SM MMAs (M = 256 per CTA pair), no cluster multicast, no M-tile pairs
-    if (a.m_pair || a.cluster > 1 || a.N % 32 != 0) return cudaErrorInvalidValue;
+  if (a.cta2) {  // two-SM MMAs (M = 256 per CTA pair), no M-tile pairs
+    if (a.m_pair || a.N % 32 != 0) return cudaErrorInvalidValue;
     const int sp = a.a_lo;
     const int f8 = a.a_fp8;
     const bool f8f8 = col_scale != nullptr;
@@ -1665,14 +1613,11 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
     return cudaGetLastError();
   }
   if (col_scale != nullptr) return cudaErrorInvalidValue;  // FP8 B: two-SM form only
-  const int CL = a.cluster < 1 ? 1 : a.cluster;
-  if (CL != 1 && CL != 2 && CL != 4) return cudaErrorInvalidValue;
-  if (CL > 1 && (a.N / CL < 8 || (a.N / CL) % 8 != 0 || a.N / CL > 256)) return cudaErrorInvalidValue;
   const int mt = a.m_pair ? 2 : 1;
-  if (a.m_pair && (a.N > 256 || CL != 1 || a.a_fp8)) return cudaErrorInvalidValue;
+  if (a.m_pair && (a.N > 256 || a.a_fp8)) return cudaErrorInvalidValue;
   const size_t smem = tc_smem_bytes(a.N, a.stages, a.a_lo, a.b_lo, a.a_fp8, mt);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
-  if (a.m_pair) {  // pairs of M tiles per unit, no cluster
+  if (a.m_pair) {  // pairs of M tiles per unit
     const long long pu = static_cast<long long>(a.Nb) * ((a.m_tiles + 1) / 2) * a.n_kchunks;
     const unsigned grid = static_cast<unsigned>(pu < num_sms ? pu : num_sms);
     const bool bk64 = tc_block_k(a.N, a.a_lo) == 64;
@@ -1700,9 +1645,7 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
   auto go = [&](auto bk_tag, auto mode_tag) -> cudaError_t {
     constexpr int BK = decltype(bk_tag)::value;
     constexpr int MD = decltype(mode_tag)::value;
-    if (CL == 1) return launch_tc_cl<BK, 1, MD>(tmA, tmB, a2, b2, a, num_sms, smem, st);
-    if (CL == 2) return launch_tc_cl<BK, 2, MD>(tmA, tmB, a2, b2, a, num_sms, smem, st);
-    return launch_tc_cl<BK, 4, MD>(tmA, tmB, a2, b2, a, num_sms, smem, st);
+    return launch_tc_one<BK, MD>(tmA, tmB, a2, b2, a, num_sms, smem, st);
   };
   using bk64 = std::integral_constant<int, 64>;
   using bk32 = std::integral_constant<int, 32>;

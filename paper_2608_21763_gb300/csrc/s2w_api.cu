@@ -16,7 +16,9 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <string>
 #include <vector>
 
 #include "s2w_internal.cuh"
@@ -34,8 +36,17 @@ struct s2w_ctx {
   float* G_scale = nullptr;
   int nblk = 0;
   void* P = nullptr;
+  void* P_lo = nullptr;   // FP32_HILO: low-order parts of Phat
   size_t g_bytes = 0, p_bytes = 0;
   float2* tw = nullptr;
+  // FP32_HILO (FP32 pairs everywhere on the stream path): pair twiddles and
+  // the low-order parts of every intermediate spectrum
+  bool df = false;
+  float4* tw_df = nullptr;
+  float2* ws_shat_lo = nullptr;
+  float2* ws_mhat_lo = nullptr;
+  float2* ws_vhat_lo = nullptr;
+  float2* ws_part_lo = nullptr;
   // workspaces
   float* ws_slip = nullptr;
   float2* ws_shat = nullptr;
@@ -54,17 +65,20 @@ struct s2w_ctx {
   int* d_status = nullptr;
   // tensor-core engine (BF16 storage, rupture batches)
   bool tc_on = false;
-  int tc_bsub = 0;       // largest sub-batch per tensor pass (<= 256)
+  int tc_bsub = 0;       // sub-batch per tensor pass (<= tc_bsub_max)
+  int tc_bsub_max = 0;   // sub-batch the tensor workspaces are sized for (<= 256)
   int tc_n1max = 0;      // B-operand rows of stage 1 (2 x sub-batch, padded)
   int tc_n2 = 0;         // B-operand rows of stage 2 (2 x No, padded)
   long long Ng_pad2 = 0; // complex columns per row of the stage-2 operands
   int tc_kbpc = 64;      // K blocks per stage-2 chunk
-  int tc_nkc = 1;        // stage-2 K chunks
-  int tc_cl1 = 1;        // cluster size of the stage-1 GEMM (B tiles multicast)
-  int tc_cl2 = 1;        // cluster size of the stage-2 GEMM
+  int tc_nkc = 1;        // stage-2 K chunks (<= kMaxS2Chunks, the partials' allocation)
   int tc_pair = 0;       // 1: two-SM MMAs (CTA pairs per M = 256 tile) where the shape allows; kPairAuto: for N = 512
   bool tc_rtpair = false;  // two-SM tiles for the BF16 retransform GEMM
   int tc_min_batch = 2;  // AUTO: smallest B on the tensor engine
+  // test hooks (s2w_opts.fault): what to inject, and the kernel wait bound
+  int fault = S2W_FAULT_NONE;
+  unsigned long long wait_ns = kWaitLimitNs;
+  std::string tune_cache;  // autotuner cache file (empty: none)
   // CUDA graphs of the waveform pipeline, one per (slip, q, B), least
   // recently used evicted beyond kGraphCache entries
   struct GraphEntry {
@@ -182,41 +196,63 @@ int pointer_kind(const void* p, int device) {
   return 0;
 }
 
-// Tensor engine: default CTAs per cluster sharing each B tile, and whether
-// GEMMs take the two-SM form by default (kPairAuto: for N = 512, where half
+// Tensor engine: whether GEMMs take the two-SM form by default (kPairAuto: for N = 512, where half
 // of B per CTA lets the ring take 64-element K blocks with 128-byte swizzle;
 // measured 0.86 against 0.75 of the sustained BF16 peak for the 256-rupture
 // stage 1.  At N = 128 the M-tile pairs of one CTA were faster, and so
 // were single CTAs for FP8 A: 0.63 against 0.50, the pair's cross-CTA
 // converter handshake sitting on every stage.)
-constexpr int kDefaultCluster = 1;
 constexpr int kPairAuto = 2;
 constexpr int kDefaultPair = kPairAuto;
-
-// Largest cluster <= want that the GEMM accepts for an N-wide B operand split
-// over it and m_tiles M tiles.
-int fit_cluster(int want, int N, int m_tiles) {
-  int cl = want < 1 ? 1 : want;
-  while (cl > 1 && (N / cl < 8 || (N / cl) % 8 != 0 || N / cl > 256 || cl > m_tiles)) cl /= 2;
-  return cl;  // 1: a single CTA loads any N <= 512 itself
-}
+// Largest stage-2 split-K chunk count (the tensor partials are sized for it,
+// so s2w_autotune and opts.tc_s2_chunks can pick any count up to it).
+constexpr int kMaxS2Chunks = 16;
 
 // Form of one tensor GEMM; sets the ring depth and TMEM columns of `a` and
 // returns the B tensor map's box rows.  With `pair` (1, or kPairAuto and
-// the shape it covers; and no cluster, N % 32 == 0, at least two M tiles):
-// two-SM MMAs, a CTA pair per M = 256 tile staging half of B each.  Otherwise two M tiles per unit
-// sharing each B tile when the accumulators fit (N <= 256), without a
-// cluster, for non-FP8 A and at least two M tiles.
-int tc_shape(TcArgs& a, int N, int m_tiles, int cl, int split, int fp8, int pair) {
+// the shape it covers; and N % 32 == 0, at least two M tiles): two-SM MMAs,
+// a CTA pair per M = 256 tile staging half of B each.  Otherwise two M tiles
+// per unit sharing each B tile when the accumulators fit (N <= 256), for
+// non-FP8 A and at least two M tiles.  Every CTA loads its own tiles.
+int tc_shape(TcArgs& a, int N, int m_tiles, int split, int fp8, int pair) {
   if (pair == kPairAuto) pair = N == 512 && !split && !fp8;
-  a.cta2 = (pair && cl == 1 && N % 32 == 0 && m_tiles >= 2) ? 1 : 0;
-  a.m_pair = (!a.cta2 && N <= 256 && cl == 1 && !fp8 && m_tiles >= 2) ? 1 : 0;
+  a.cta2 = (pair && N % 32 == 0 && m_tiles >= 2) ? 1 : 0;
+  a.m_pair = (!a.cta2 && N <= 256 && !fp8 && m_tiles >= 2) ? 1 : 0;
   const int mt = a.m_pair ? 2 : 1;
   a.stages = a.cta2 ? tc_stages_pair(N, split, fp8) : tc_stages_for(N, split, split, fp8, mt);
   const int cols = mt * N;
   a.tmem_cols = cols <= 32 ? 32 : (cols <= 64 ? 64 : (cols <= 128 ? 128 : (cols <= 256 ? 256 : 512)));
   const int slice = N > 256 ? 256 : N;
-  return a.cta2 ? slice / 2 : (cl > 1 ? N / cl : slice);
+  return a.cta2 ? slice / 2 : slice;
+}
+
+// Stage-2 split-K over the grid: the chunk count `want` (1..kMaxS2Chunks), or
+// for want = 0 the count that minimises rounds x chunk length over the
+// persistent CTAs for units = bins x M-tile groups (pairs of 128-row tiles
+// when the GEMM takes them) x K chunks, with a small fixed cost per unit
+// (pipeline fill and accumulator drain).  Sets tc_kbpc and tc_nkc.
+void set_s2_chunks(s2w_ctx* ctx, int want) {
+  const int bk2 = tc_block_k(ctx->tc_n2, ctx->tc_split ? 1 : 0);
+  const long long nk2 = (2 * ctx->Ng_pad2 + bk2 - 1) / bk2;
+  long long nkc = want;
+  if (nkc <= 0) {
+    const long long mt2 = (ctx->tc_bsub + 127) / 128;
+    const long long mg2 = (mt2 >= 2 && ctx->tc_n2 <= 256) ? (mt2 + 1) / 2 : mt2;
+    double best = 1e300;
+    nkc = 1;
+    for (long long c = 1; c <= std::min<long long>(kMaxS2Chunks, nk2); ++c) {
+      const long long units = ctx->Nb * mg2 * c;
+      const long long rounds = (units + ctx->num_sms - 1) / ctx->num_sms;
+      const double cost = static_cast<double>(rounds) * (1.0 / static_cast<double>(c) + 0.005);
+      if (cost < best * (1.0 - 1e-9)) {
+        best = cost;
+        nkc = c;
+      }
+    }
+  }
+  nkc = std::max<long long>(1, std::min<long long>({nkc, nk2, static_cast<long long>(kMaxS2Chunks)}));
+  ctx->tc_kbpc = static_cast<int>((nk2 + nkc - 1) / nkc);
+  ctx->tc_nkc = static_cast<int>((nk2 + ctx->tc_kbpc - 1) / ctx->tc_kbpc);
 }
 
 // The stream engine handles ruptures in groups of at most this many (its
@@ -279,7 +315,8 @@ void free_all(s2w_ctx* c) {
   for (auto e : c->ev_free) cudaEventDestroy(e);
   c->pending.clear();
   c->ev_free.clear();
-  void* ps[] = {c->G, c->G_lo, c->G_scale, c->P, c->tw, c->ws_slip, c->ws_shat, c->ws_mhat,
+  void* ps[] = {c->G, c->G_lo, c->G_scale, c->P, c->P_lo, c->tw_df, c->ws_shat_lo, c->ws_mhat_lo, c->ws_vhat_lo,
+                c->ws_part_lo, c->tw, c->ws_slip, c->ws_shat, c->ws_mhat,
                 c->ws_vhat, c->ws_part, c->ws_q, c->ws_seafloor, c->d_status, c->tc_bp1, c->ws_rhat, c->ws_gpart, c->ws_resid, c->ws_d, c->ws_loss,
                 c->tc_mhat, c->tc_vhat, c->tc_part, c->tc_p2, c->tc_T, c->tc_bp1_lo, c->tc_vhat_lo, c->tc_p2_lo,
                 c->tc_gT, c->tc_gT_lo, c->tc_pT, c->tc_pT_lo, c->tc_rb, c->tc_rb_lo, c->tc_ub, c->tc_ub_lo,
@@ -346,14 +383,13 @@ std::vector<double> retransform_matrix(int Nt, int dt_mode, double dt, bool tran
 // One tcgen05 GEMM (epilogue 0: FP32 out[l][t][row]) over A [Nb][M][K]
 // and the B operand rows [Nb][n_alloc][K] (BF16; lo parts when split).
 int tc_gemm_epi0(s2w_ctx* ctx, const void* A, const void* A_lo, long long M, long long K, const void* Bop,
-                 const void* B_lo, int n_alloc, int N, int T, float2* out, long long ld_l, long long ld_t, int cl_want,
+                 const void* B_lo, int n_alloc, int N, int T, float2* out, long long ld_l, long long ld_t,
                  cudaStream_t st, __nv_bfloat162* out_bf = nullptr) {
   const int sp = A_lo != nullptr ? 1 : 0;
   CUtensorMap ta, tb, ta2, tb2;
   const int mt = static_cast<int>((M + 127) / 128);
-  const int cl = fit_cluster(cl_want, N, mt);
   TcArgs a{};
-  const int brows = tc_shape(a, N, mt, cl, sp, 0, ctx->tc_pair);
+  const int brows = tc_shape(a, N, mt, sp, 0, ctx->tc_pair);
   const int bk = tc_block_k(N, sp, a.cta2);
   CK(tc_encode_3d(&ta, A, K, M, ctx->Nb, K, 128, bk));
   CK(tc_encode_3d(&tb, Bop, K, n_alloc, ctx->Nb, K, brows, bk));
@@ -370,7 +406,6 @@ int tc_gemm_epi0(s2w_ctx* ctx, const void* A, const void* A_lo, long long M, lon
   a.kblocks_per_chunk = static_cast<int>((K + bk - 1) / bk);
   a.a_lo = sp;
   a.b_lo = sp;
-  a.cluster = cl;
   a.epi = 0;
   a.T = T;
   a.out = out_bf ? nullptr : out;
@@ -413,7 +448,7 @@ int adjoint_tensor(s2w_ctx* ctx, const float* r_d, int B, float* g_d, cudaStream
       StageTimer t(ctx, 3, st);
       int rc = tc_gemm_epi0(ctx, ctx->tc_pT, sp ? ctx->tc_pT_lo : nullptr, Ng, 2LL * ctx->NoP, ctx->tc_rb,
                             sp ? ctx->tc_rb_lo : nullptr, ctx->tc_n1max, N1, Bs, what,
-                            static_cast<long long>(Bs) * Ng, Ng, ctx->tc_cl1, st,
+                            static_cast<long long>(Bs) * Ng, Ng, st,
                             gemm_rt && !sp ? reinterpret_cast<__nv_bfloat162*>(what) : nullptr);
       if (rc != S2W_OK) return rc;
     }
@@ -448,7 +483,7 @@ int adjoint_tensor(s2w_ctx* ctx, const float* r_d, int B, float* g_d, cudaStream
       StageTimer t(ctx, 1, st);
       int rc = tc_gemm_epi0(ctx, ctx->tc_gT, sp ? ctx->tc_gT_lo : nullptr, Ns, 2 * ctx->Ng_pad2, ctx->tc_ub,
                             sp ? ctx->tc_ub_lo : nullptr, ctx->tc_n1max, N1, Bs, ctx->tc_ghat,
-                            static_cast<long long>(Bs) * Ns, Ns, ctx->tc_cl1, st);
+                            static_cast<long long>(Bs) * Ns, Ns, st);
       if (rc != S2W_OK) return rc;
     }
     {
@@ -513,7 +548,6 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
       a.a_fp8 = 1;
       a.row_scale = ctx->G_scale;
       a.nblk = ctx->nblk;
-      a.cluster = 1;
       a.epi = 0;
       a.T = Bs;
       a.out_bf = static_cast<__nv_bfloat162*>(ctx->tc_mhat);
@@ -524,9 +558,8 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
     } else {
       StageTimer t(ctx, 1, st);
       CUtensorMap ta, tb, ta2, tb2;
-      const int cl = fit_cluster(ctx->tc_cl1, N1, m1);
       TcArgs a{};
-      const int brows = tc_shape(a, N1, m1, cl, sp, f8 ? 1 : 0, ctx->tc_pair);
+      const int brows = tc_shape(a, N1, m1, sp, f8 ? 1 : 0, ctx->tc_pair);
       const int bk = tc_block_k(N1, sp, a.cta2);
       if (f8)  // one byte per K element: row pitch 2 Ns_pad bytes
         CK(tc_encode_3d_u8(&ta, ctx->G, K1, Ng, Nb, 128, bk));
@@ -552,7 +585,6 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
         a.nblk = ctx->nblk;
         a.b_amax = ctx->d_amax;
       }
-      a.cluster = cl;
       a.epi = 0;
       a.T = Bs;
       // the GEMM retransform rounds the seafloor spectra to BF16 anyway; the
@@ -588,11 +620,10 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
       StageTimer t(ctx, 3, st);
       CUtensorMap ta, tb, ta2, tb2;
       const int m2 = (Bs + 127) / 128;
-      const int cl = fit_cluster(ctx->tc_cl2, ctx->tc_n2, m2);
       TcArgs a{};
-      int brows = tc_shape(a, ctx->tc_n2, m2, cl, sp, 0, ctx->tc_pair);
+      int brows = tc_shape(a, ctx->tc_n2, m2, sp, 0, ctx->tc_pair);
       // the chunk length tc_kbpc counts K blocks of the single-CTA size
-      if (tc_block_k(ctx->tc_n2, sp, a.cta2) != tc_block_k(ctx->tc_n2, sp)) brows = tc_shape(a, ctx->tc_n2, m2, cl, sp, 0, 0);
+      if (tc_block_k(ctx->tc_n2, sp, a.cta2) != tc_block_k(ctx->tc_n2, sp)) brows = tc_shape(a, ctx->tc_n2, m2, sp, 0, 0);
       const int bk = tc_block_k(ctx->tc_n2, sp, a.cta2);
       CK(tc_encode_3d(&ta, ctx->tc_vhat, K2, ctx->tc_bsub, Nb, K2, 128, bk));
       CK(tc_encode_3d(&tb, ctx->tc_p2, K2, ctx->tc_n2, Nb, K2, brows, bk));
@@ -609,7 +640,6 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
       a.kblocks_per_chunk = ctx->tc_kbpc;
       a.a_lo = sp;
       a.b_lo = sp;
-      a.cluster = cl;
       a.epi = 1;
       a.T = static_cast<int>(No);
       a.out = ctx->tc_part;
@@ -652,11 +682,15 @@ void s2w_default_opts(s2w_opts* o) {
   o->max_batch = 1;
   o->device = 0;
   o->engine = S2W_ENGINE_AUTO;
-  o->tc_cluster = 0;
   o->tc_adjoint = 0;
   o->single_pass = 0;
   o->tc_pair = S2W_PAIR_AUTO;
   o->tc_fp8_act = 0;
+  o->tc_bsub = 0;
+  o->tc_s2_chunks = 0;
+  o->tune_cache = nullptr;
+  o->fault = S2W_FAULT_NONE;
+  o->fault_wait_us = 5000;
 }
 
 const char* s2w_status_string(int s) {
@@ -684,17 +718,36 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
   if (Ns < 1 || Ng < 1 || No < 1) return fail(nullptr, S2W_ERR_ARG, "Ns, Ng, No must be >= 1");
   if (!supported_nt(Nt)) return fail(nullptr, S2W_ERR_UNSUPPORTED, "Nt=%d: supported 32, 64, 128, 256, 512", Nt);
   if (Ns > 1024) return fail(nullptr, S2W_ERR_UNSUPPORTED, "Ns=%d > 1024", Ns);
-  if (o.prec_g < S2W_PREC_FP32 || o.prec_g > S2W_PREC_FP8_E4M3)
+  if (o.prec_g < S2W_PREC_FP32 || o.prec_g > S2W_PREC_FP32_HILO)
     return fail(nullptr, S2W_ERR_ARG, "prec_g=%d", o.prec_g);
-  if (o.prec_p != S2W_PREC_FP32 && o.prec_p != S2W_PREC_BF16)
-    return fail(nullptr, S2W_ERR_UNSUPPORTED, "prec_p=%d: FP32 or BF16", o.prec_p);
+  if (o.prec_p != S2W_PREC_FP32 && o.prec_p != S2W_PREC_BF16 && o.prec_p != S2W_PREC_FP32_HILO)
+    return fail(nullptr, S2W_ERR_UNSUPPORTED, "prec_p=%d: FP32, BF16 or FP32_HILO", o.prec_p);
+  if ((o.prec_g == S2W_PREC_FP32_HILO) != (o.prec_p == S2W_PREC_FP32_HILO))
+    return fail(nullptr, S2W_ERR_UNSUPPORTED, "prec_g=%d, prec_p=%d: FP32_HILO is for both operators or neither",
+                o.prec_g, o.prec_p);
+  if (o.prec_g == S2W_PREC_FP32_HILO && (o.engine == S2W_ENGINE_TENSOR || o.single_pass || o.tc_adjoint))
+    return fail(nullptr, S2W_ERR_UNSUPPORTED, "FP32_HILO: stream engine only, no single_pass or tc_adjoint");
   if (o.dt_mode != S2W_DT_BACKWARD && o.dt_mode != S2W_DT_NONE)
     return fail(nullptr, S2W_ERR_ARG, "dt_mode=%d", o.dt_mode);
   if (!(o.dt > 0.0)) return fail(nullptr, S2W_ERR_ARG, "dt must be > 0");
   if (o.max_batch < 1) return fail(nullptr, S2W_ERR_ARG, "max_batch must be >= 1");
   if (o.engine < S2W_ENGINE_AUTO || o.engine > S2W_ENGINE_TENSOR) return fail(nullptr, S2W_ERR_ARG, "engine=%d", o.engine);
-  if (o.tc_cluster != 0 && o.tc_cluster != 1 && o.tc_cluster != 2 && o.tc_cluster != 4)
-    return fail(nullptr, S2W_ERR_ARG, "tc_cluster=%d: 0, 1, 2 or 4", o.tc_cluster);
+  if (o.tc_bsub != 0 && o.tc_bsub != 128 && o.tc_bsub != 256)
+    return fail(nullptr, S2W_ERR_ARG, "tc_bsub=%d: 0, 128 or 256", o.tc_bsub);
+  if (o.tc_bsub == 256 && o.prec_g == S2W_PREC_BF16_HILO)
+    return fail(nullptr, S2W_ERR_UNSUPPORTED, "tc_bsub=256: split (BF16_HILO) passes take at most 128 ruptures");
+  if (o.tc_s2_chunks < 0 || o.tc_s2_chunks > kMaxS2Chunks)
+    return fail(nullptr, S2W_ERR_ARG, "tc_s2_chunks=%d: 0..%d", o.tc_s2_chunks, kMaxS2Chunks);
+  if (o.fault < S2W_FAULT_NONE || o.fault > S2W_FAULT_LAUNCH) return fail(nullptr, S2W_ERR_ARG, "fault=%d", o.fault);
+  if (o.fault == S2W_FAULT_NONE) {  // test hook from the environment
+    const char* f = std::getenv("S2W_FAULT");
+    if (f && std::strcmp(f, "wait") == 0) o.fault = S2W_FAULT_WAIT;
+    else if (f && std::strcmp(f, "oom_load") == 0) o.fault = S2W_FAULT_OOM_LOAD;
+    else if (f && std::strcmp(f, "launch") == 0) o.fault = S2W_FAULT_LAUNCH;
+    else if (f && *f) return fail(nullptr, S2W_ERR_ARG, "S2W_FAULT=%s: wait, oom_load or launch", f);
+  }
+  if (o.fault == S2W_FAULT_WAIT && (o.fault_wait_us < 1 || o.fault_wait_us > 2000000))
+    return fail(nullptr, S2W_ERR_ARG, "fault_wait_us=%d: 1..2000000", o.fault_wait_us);
   if (o.engine == S2W_ENGINE_TENSOR && o.prec_g == S2W_PREC_FP32)
     return fail(nullptr, S2W_ERR_UNSUPPORTED, "the tensor engine needs prec_g = BF16, BF16_HILO or FP8_E4M3");
   if (o.tc_adjoint != 0 && o.tc_adjoint != 1) return fail(nullptr, S2W_ERR_ARG, "tc_adjoint=%d: 0 or 1", o.tc_adjoint);
@@ -729,6 +782,10 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
   ctx->nseg = static_cast<int>((Ng + 1023) / 1024);
   ctx->RL = static_cast<int>(round_up((Ng + ctx->nseg - 1) / ctx->nseg, 8));
   ctx->opts = o;
+  ctx->opts.tune_cache = nullptr;  // the caller's string is not kept
+  if (o.tune_cache) ctx->tune_cache = o.tune_cache;
+  ctx->fault = o.fault;
+  if (o.fault == S2W_FAULT_WAIT) ctx->wait_ns = 1000ull * static_cast<unsigned long long>(o.fault_wait_us);
   ctx->device = o.device;
   cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, o.device);
   ctx->g_loaded.assign(Ng, 0);
@@ -738,9 +795,11 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
   const size_t gcb = elem_complex_bytes(o.prec_g);
   ctx->nblk = static_cast<int>((Ng + 255) / 256);
   ctx->g_bytes = static_cast<size_t>(Nb) * Ng * ctx->Ns_pad * gcb;
-  if (o.prec_g == S2W_PREC_BF16_HILO) ctx->g_bytes *= 2;
+  ctx->df = o.prec_g == S2W_PREC_FP32_HILO;
+  if (o.prec_g == S2W_PREC_BF16_HILO || ctx->df) ctx->g_bytes *= 2;
   if (o.prec_g == S2W_PREC_FP8_E4M3) ctx->g_bytes += static_cast<size_t>(Nb) * ctx->nblk * sizeof(float);
-  ctx->p_bytes = static_cast<size_t>(Nb) * ctx->nseg * No * ctx->RL * elem_complex_bytes(o.prec_p);
+  const size_t psz = static_cast<size_t>(Nb) * ctx->nseg * No * ctx->RL * elem_complex_bytes(o.prec_p);
+  ctx->p_bytes = psz * (ctx->df ? 2 : 1);
 
   auto bad = [&](cudaError_t e, const char* what) {
     fail(nullptr, e == cudaErrorMemoryAllocation ? S2W_ERR_OOM : S2W_ERR_CUDA, "%s: %s", what,
@@ -752,11 +811,24 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
   cudaError_t e;
   const size_t gsz = static_cast<size_t>(Nb) * Ng * ctx->Ns_pad * gcb;
   if ((e = dalloc(&ctx->G, gsz)) != cudaSuccess) return bad(e, "Ghat");
-  if (o.prec_g == S2W_PREC_BF16_HILO && (e = dalloc(&ctx->G_lo, gsz)) != cudaSuccess) return bad(e, "Ghat lo");
+  if ((o.prec_g == S2W_PREC_BF16_HILO || ctx->df) && (e = dalloc(&ctx->G_lo, gsz)) != cudaSuccess)
+    return bad(e, "Ghat lo");
   if (o.prec_g == S2W_PREC_FP8_E4M3 &&
       (e = dalloc(&ctx->G_scale, static_cast<size_t>(Nb) * ctx->nblk * sizeof(float))) != cudaSuccess)
     return bad(e, "Ghat scales");
-  if ((e = dalloc(&ctx->P, ctx->p_bytes)) != cudaSuccess) return bad(e, "Phat");
+  if ((e = dalloc(&ctx->P, psz)) != cudaSuccess) return bad(e, "Phat");
+  if (ctx->df) {
+    if ((e = dalloc(&ctx->P_lo, psz)) != cudaSuccess) return bad(e, "Phat lo");
+    if ((e = dalloc(&ctx->tw_df, sizeof(float4) * ctx->L)) != cudaSuccess) return bad(e, "pair twiddles");
+    const long long Bsh = std::min<long long>(B, kStreamGroup);
+    if ((e = dalloc(&ctx->ws_shat_lo, sizeof(float2) * Nb * Bsh * ctx->Ns_pad)) != cudaSuccess)
+      return bad(e, "slip spectra lo");
+    if ((e = dalloc(&ctx->ws_mhat_lo, sizeof(float2) * Nb * Ng)) != cudaSuccess) return bad(e, "seafloor spectra lo");
+    if ((e = dalloc(&ctx->ws_vhat_lo, sizeof(float2) * Nb * ctx->nseg * ctx->RL)) != cudaSuccess)
+      return bad(e, "velocity spectra lo");
+    if ((e = dalloc(&ctx->ws_part_lo, sizeof(float2) * Bsh * Nb * ctx->nseg * No)) != cudaSuccess)
+      return bad(e, "stage-2 partials lo");
+  }
   if ((e = dalloc(&ctx->tw, sizeof(float2) * ctx->L)) != cudaSuccess) return bad(e, "twiddles");
   if ((e = dalloc(&ctx->ws_slip, sizeof(float) * B * Ns * Nt)) != cudaSuccess) return bad(e, "slip workspace");
   const long long Bsh = std::min<long long>(B, 256);  // slip spectra serve one group / sub-batch at a time
@@ -783,14 +855,14 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
     return bad(e, "adjoint partials");
   // AUTO keeps the tensor engine ready at any max_batch: single ruptures go
   // to it only if s2w_autotune measured it faster (tc_min_batch = 1)
-  ctx->tc_on = !ctx->single_pass && o.prec_g != S2W_PREC_FP32 && 2 * No <= 256 &&
+  ctx->tc_on = !ctx->single_pass && o.prec_g != S2W_PREC_FP32 && !ctx->df && 2 * No <= 256 &&
                (o.engine == S2W_ENGINE_TENSOR || o.engine == S2W_ENGINE_AUTO);
   ctx->tc_split = ctx->tc_on && o.prec_g == S2W_PREC_BF16_HILO;
   if (ctx->tc_on) {
     // split operands double the B tiles: sub-batches of up to 128 ruptures
-    ctx->tc_bsub = static_cast<int>(std::min<long long>(B, ctx->tc_split ? 128 : 256));
-    ctx->tc_cl1 = o.tc_cluster > 0 ? o.tc_cluster : kDefaultCluster;
-    ctx->tc_cl2 = o.tc_cluster > 0 ? o.tc_cluster : kDefaultCluster;
+    const int bsub_want = o.tc_bsub > 0 ? o.tc_bsub : (ctx->tc_split ? 128 : 256);
+    ctx->tc_bsub = static_cast<int>(std::min<long long>(B, bsub_want));
+    ctx->tc_bsub_max = ctx->tc_bsub;
     ctx->tc_pair = o.tc_pair == S2W_PAIR_ON ? 1 : (o.tc_pair == S2W_PAIR_OFF ? 0 : kDefaultPair);
     // the two-SM retransform measured slower (9.0 against 8.4 ms per 256-rupture
     // batch): only when asked for
@@ -801,27 +873,7 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
     if (ctx->tc_n1max > 256) ctx->tc_n1max = 512;
     ctx->tc_n2 = static_cast<int>(round_up(2 * No, 16));
     ctx->Ng_pad2 = round_up(Ng, 8);
-    // stage-2 split-K: units = bins x M-tile groups (pairs of 128-row tiles
-    // when the GEMM takes them) x K chunks over the persistent CTAs; pick the
-    // chunk count that minimises rounds x chunk length, with a small fixed
-    // cost per unit (pipeline fill and accumulator drain), up to 16 chunks
-    const int bk2 = tc_block_k(ctx->tc_n2, ctx->tc_split ? 1 : 0);
-    const long long nk2 = (2 * ctx->Ng_pad2 + bk2 - 1) / bk2;
-    const long long mt2 = (ctx->tc_bsub + 127) / 128;
-    const long long mg2 = (mt2 >= 2 && ctx->tc_n2 <= 256) ? (mt2 + 1) / 2 : mt2;
-    long long nkc = 1;
-    double best = 1e300;
-    for (long long c = 1; c <= std::min(16LL, nk2); ++c) {
-      const long long units = Nb * mg2 * c;
-      const long long rounds = (units + ctx->num_sms - 1) / ctx->num_sms;
-      const double cost = static_cast<double>(rounds) * (1.0 / static_cast<double>(c) + 0.005);
-      if (cost < best * (1.0 - 1e-9)) {
-        best = cost;
-        nkc = c;
-      }
-    }
-    ctx->tc_kbpc = static_cast<int>((nk2 + nkc - 1) / nkc);
-    ctx->tc_nkc = static_cast<int>((nk2 + ctx->tc_kbpc - 1) / ctx->tc_kbpc);
+    set_s2_chunks(ctx, o.tc_s2_chunks);
     const long long bs = ctx->tc_bsub;
     const bool sp = ctx->tc_split;
     if ((e = dalloc(&ctx->tc_bp1, 2ull * Nb * ctx->tc_n1max * 2 * ctx->Ns_pad)) != cudaSuccess)
@@ -857,7 +909,7 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
     }
     if ((e = dalloc(&ctx->tc_vhat, 4ull * Nb * bs * ctx->Ng_pad2)) != cudaSuccess)
       return bad(e, "tensor velocity spectra");
-    if ((e = dalloc(&ctx->tc_part, sizeof(float2) * Nb * ctx->tc_nkc * bs * No)) != cudaSuccess)
+    if ((e = dalloc(&ctx->tc_part, sizeof(float2) * Nb * kMaxS2Chunks * bs * No)) != cudaSuccess)
       return bad(e, "tensor stage-2 partials");
     if ((e = dalloc(&ctx->tc_p2, 4ull * Nb * ctx->tc_n2 * ctx->Ng_pad2)) != cudaSuccess)
       return bad(e, "tensor stage-2 operand");
@@ -902,6 +954,7 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
     }
   }
   if ((e = launch_twiddles(ctx->tw, ctx->L, nullptr)) != cudaSuccess) return bad(e, "twiddles");
+  if (ctx->df && (e = launch_twiddles_df(ctx->tw_df, ctx->L, nullptr)) != cudaSuccess) return bad(e, "pair twiddles");
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bad(e, "create sync");
   *out = ctx;
   return S2W_OK;
@@ -936,15 +989,20 @@ int load_greens_impl(s2w_ctx* ctx, int g0, int ng, const float* G, bool spectra,
     return fail(ctx, S2W_ERR_ARG, "load_greens: FP8 storage needs 256-row aligned chunks (g0=%d, ng=%d)", g0, ng);
   DeviceGuard guard(ctx->device);
   if (pointer_kind(G, ctx->device) < 0) return fail(ctx, S2W_ERR_ARG, "load_greens: G is on another device");
+  if (ctx->fault == S2W_FAULT_OOM_LOAD)
+    return fail(ctx, S2W_ERR_OOM, "load_greens: staging allocation failed (injected by the OOM_LOAD test hook)");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const long long Ns = ctx->Ns, Nt = ctx->Nt, Nb = ctx->Nb, Ns_pad = ctx->Ns_pad;
   const long long RC = 256;
   float* stage_t = nullptr;
   float2* stage_s = nullptr;
+  float2* stage_lo = nullptr;  // FP32_HILO: low-order parts of the spectra
   CK(cudaMalloc(&stage_t, sizeof(float) * RC * Ns * Nt));
   cudaError_t e = cudaMalloc(&stage_s, sizeof(float2) * Nb * RC * Ns_pad);
+  if (e == cudaSuccess && ctx->df) e = cudaMalloc(&stage_lo, sizeof(float2) * Nb * RC * Ns_pad);
   if (e != cudaSuccess) {
     cudaFree(stage_t);
+    cudaFree(stage_s);
     CK(e);
   }
   int rc_status = S2W_OK;
@@ -953,6 +1011,8 @@ int load_greens_impl(s2w_ctx* ctx, int g0, int ng, const float* G, bool spectra,
     const long long row0 = g0 + r;
     auto step = [&]() -> int {
       CK(cudaMemsetAsync(stage_s, 0, sizeof(float2) * Nb * rc * Ns_pad, st));
+      // complex64 spectra carry no low-order part: lo = 0
+      if (ctx->df) CK(cudaMemsetAsync(stage_lo, 0, sizeof(float2) * Nb * rc * Ns_pad, st));
       if (spectra) {  // bin l: rows r .. r+rc of Ghat_l, re-pitched to Ns_pad
         ctx->launches += fp8 ? 1 : 0;
         for (long long l = 0; l < Nb; ++l)
@@ -962,11 +1022,21 @@ int load_greens_impl(s2w_ctx* ctx, int g0, int ng, const float* G, bool spectra,
       } else {
         CK(cudaMemcpyAsync(stage_t, G + r * Ns * Nt, sizeof(float) * rc * Ns * Nt, cudaMemcpyDefault, st));
         ctx->launches += fp8 ? 2 : 1;
-        CK(launch_rfft_rows(stage_t, rc * Ns, static_cast<int>(Nt), static_cast<int>(ctx->L / 2), ctx->tw, stage_s,
-                            rc * Ns_pad, Ns, Ns_pad, st));
+        if (ctx->df)
+          CK(launch_df_rfft_rows(stage_t, rc * Ns, static_cast<int>(Nt), static_cast<int>(ctx->L / 2), ctx->tw_df,
+                                 stage_s, stage_lo, rc * Ns_pad, Ns, Ns_pad, st));
+        else
+          CK(launch_rfft_rows(stage_t, rc * Ns, static_cast<int>(Nt), static_cast<int>(ctx->L / 2), ctx->tw, stage_s,
+                              rc * Ns_pad, Ns, Ns_pad, st));
       }
       ctx->launches += 1;
-      if (fp8) {
+      if (ctx->df) {  // the pair's parts as two FP32 arrays of the same layout
+        ctx->launches += 1;
+        CK(launch_store_blocks(stage_s, static_cast<int>(Nb), rc * Ns_pad, EL_FP32, ctx->G, nullptr,
+                               static_cast<long long>(ctx->Ng) * Ns_pad, row0 * Ns_pad, st));
+        CK(launch_store_blocks(stage_lo, static_cast<int>(Nb), rc * Ns_pad, EL_FP32, ctx->G_lo, nullptr,
+                               static_cast<long long>(ctx->Ng) * Ns_pad, row0 * Ns_pad, st));
+      } else if (fp8) {
         CK(launch_fp8_store(stage_s, static_cast<int>(Nb), rc, static_cast<int>(Ns_pad), row0, ctx->Ng,
                             ctx->G_scale, ctx->nblk, ctx->G, st));
       } else {
@@ -989,6 +1059,7 @@ int load_greens_impl(s2w_ctx* ctx, int g0, int ng, const float* G, bool spectra,
   cudaStreamSynchronize(st);
   cudaFree(stage_t);
   cudaFree(stage_s);
+  cudaFree(stage_lo);
   if (rc_status != S2W_OK) return rc_status;
   for (int r = 0; r < ng; ++r) {
     if (!ctx->g_loaded[g0 + r]) ++ctx->g_count;
@@ -1005,15 +1076,20 @@ int load_adjoint_impl(s2w_ctx* ctx, int g0, int ng, const float* P, bool spectra
                 ctx->Ng);
   DeviceGuard guard(ctx->device);
   if (pointer_kind(P, ctx->device) < 0) return fail(ctx, S2W_ERR_ARG, "load_adjoint: P is on another device");
+  if (ctx->fault == S2W_FAULT_OOM_LOAD)
+    return fail(ctx, S2W_ERR_OOM, "load_adjoint: staging allocation failed (injected by the OOM_LOAD test hook)");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const long long No = ctx->No, Nt = ctx->Nt, Nb = ctx->Nb;
   const long long RC = 2048;
   float* stage_t = nullptr;
   float2* stage_s = nullptr;
+  float2* stage_lo = nullptr;  // FP32_HILO: low-order parts of the spectra
   CK(cudaMalloc(&stage_t, sizeof(float) * No * RC * Nt));
   cudaError_t e = cudaMalloc(&stage_s, sizeof(float2) * Nb * No * RC);
+  if (e == cudaSuccess && ctx->df) e = cudaMalloc(&stage_lo, sizeof(float2) * Nb * No * RC);
   if (e != cudaSuccess) {
     cudaFree(stage_t);
+    cudaFree(stage_s);
     CK(e);
   }
   int rc_status = S2W_OK;
@@ -1024,21 +1100,35 @@ int load_adjoint_impl(s2w_ctx* ctx, int g0, int ng, const float* P, bool spectra
         for (long long l = 0; l < Nb; ++l)
           CK(cudaMemcpy2DAsync(stage_s + l * No * rc, sizeof(float2) * rc, P + 2 * (l * No * ng + c),
                                sizeof(float2) * ng, sizeof(float2) * rc, No, cudaMemcpyDefault, st));
+        // complex64 spectra carry no low-order part: lo = 0
+        if (ctx->df) CK(cudaMemsetAsync(stage_lo, 0, sizeof(float2) * Nb * No * rc, st));
         ctx->launches += 1;
       } else {
         CK(cudaMemcpy2DAsync(stage_t, sizeof(float) * rc * Nt, P + c * Nt, sizeof(float) * ng * Nt,
                              sizeof(float) * rc * Nt, No, cudaMemcpyDefault, st));
         ctx->launches += 2;
-        CK(launch_rfft_rows(stage_t, No * rc, static_cast<int>(Nt), static_cast<int>(ctx->L / 2), ctx->tw, stage_s,
-                            No * rc, rc, rc, st));
+        if (ctx->df)
+          CK(launch_df_rfft_rows(stage_t, No * rc, static_cast<int>(Nt), static_cast<int>(ctx->L / 2), ctx->tw_df,
+                                 stage_s, stage_lo, No * rc, rc, rc, st));
+        else
+          CK(launch_rfft_rows(stage_t, No * rc, static_cast<int>(Nt), static_cast<int>(ctx->L / 2), ctx->tw, stage_s,
+                              No * rc, rc, rc, st));
       }
       if (ctx->single_pass && ctx->opts.dt_mode != S2W_DT_NONE) {  // fold D_t into the stage-2 spectra
         ctx->launches += 1;
         CK(launch_scale_dt(stage_s, static_cast<int>(Nb), No * rc, ctx->tw, static_cast<float>(1.0 / ctx->opts.dt),
                            st));
       }
-      CK(launch_store_adjoint(stage_s, static_cast<int>(Nb), static_cast<int>(No), rc, g0 + c, ctx->RL, ctx->nseg,
-                              ctx->opts.prec_p, ctx->P, st));
+      if (ctx->df) {  // the pair's parts as two FP32 arrays of the same layout
+        ctx->launches += 1;
+        CK(launch_store_adjoint(stage_s, static_cast<int>(Nb), static_cast<int>(No), rc, g0 + c, ctx->RL, ctx->nseg,
+                                EL_FP32, ctx->P, st));
+        CK(launch_store_adjoint(stage_lo, static_cast<int>(Nb), static_cast<int>(No), rc, g0 + c, ctx->RL,
+                                ctx->nseg, EL_FP32, ctx->P_lo, st));
+      } else {
+        CK(launch_store_adjoint(stage_s, static_cast<int>(Nb), static_cast<int>(No), rc, g0 + c, ctx->RL, ctx->nseg,
+                                ctx->opts.prec_p, ctx->P, st));
+      }
       if (ctx->tc_on) {
         ctx->launches += 1;
         CK(launch_pack_b(stage_s, static_cast<int>(Nb), static_cast<int>(No), rc, No * rc, rc, g0 + c, ctx->Ng_pad2,
@@ -1060,6 +1150,7 @@ int load_adjoint_impl(s2w_ctx* ctx, int g0, int ng, const float* P, bool spectra
   cudaStreamSynchronize(st);
   cudaFree(stage_t);
   cudaFree(stage_s);
+  cudaFree(stage_lo);
   if (rc_status != S2W_OK) return rc_status;
   for (int r = 0; r < ng; ++r) {
     if (!ctx->p_loaded[g0 + r]) ++ctx->p_count;
@@ -1099,6 +1190,8 @@ int s2w_waveforms(s2w_ctx* ctx, const float* slip, int B, float* q, float* seafl
   const int ks = pointer_kind(slip, ctx->device), kq = pointer_kind(q, ctx->device);
   const int kf = seafloor ? pointer_kind(seafloor, ctx->device) : 1;
   if (ks < 0 || kq < 0 || kf < 0) return fail(ctx, S2W_ERR_ARG, "waveforms: pointer on another device");
+  if (ctx->fault == S2W_FAULT_LAUNCH)
+    return fail(ctx, S2W_ERR_CUDA, "waveforms: kernel launch failed (injected by the LAUNCH test hook)");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const long long Ns = ctx->Ns, Ng = ctx->Ng, No = ctx->No, Nt = ctx->Nt, Nb = ctx->Nb, Ns_pad = ctx->Ns_pad;
   const float* slip_d = slip;
@@ -1127,9 +1220,14 @@ int s2w_waveforms(s2w_ctx* ctx, const float* slip, int B, float* q, float* seafl
     // K1
     {
       StageTimer t(ctx, 0, st);
-      CK(launch_rfft_rows(slip_d + static_cast<long long>(g0) * Ns * Nt, Bg * Ns, static_cast<int>(Nt),
-                          static_cast<int>(ctx->L / 2), ctx->tw, ctx->ws_shat, Bg * Ns_pad, Ns, Ns_pad, st,
-                          ctx->cur_lens ? ctx->cur_lens + g0 : nullptr));
+      if (ctx->df)
+        CK(launch_df_rfft_rows(slip_d + static_cast<long long>(g0) * Ns * Nt, Bg * Ns, static_cast<int>(Nt),
+                               static_cast<int>(ctx->L / 2), ctx->tw_df, ctx->ws_shat, ctx->ws_shat_lo, Bg * Ns_pad,
+                               Ns, Ns_pad, st, ctx->cur_lens ? ctx->cur_lens + g0 : nullptr));
+      else
+        CK(launch_rfft_rows(slip_d + static_cast<long long>(g0) * Ns * Nt, Bg * Ns, static_cast<int>(Nt),
+                            static_cast<int>(ctx->L / 2), ctx->tw, ctx->ws_shat, Bg * Ns_pad, Ns, Ns_pad, st,
+                            ctx->cur_lens ? ctx->cur_lens + g0 : nullptr));
     }
     const long long part_b = Nb * ctx->nseg * No;
     for (int b = 0; b < Bg; ++b) {
@@ -1147,7 +1245,13 @@ int s2w_waveforms(s2w_ctx* ctx, const float* slip, int B, float* q, float* seafl
       a1.scale = ctx->G_scale;
       a1.nblk = ctx->nblk;
       a1.y = ctx->ws_mhat;
+      if (ctx->df) {
+        a1.x_lo = ctx->ws_shat_lo + b * Ns_pad;
+        a1.y_lo = ctx->ws_mhat_lo;
+      }
       a1.status = ctx->d_status;
+      a1.wait_ns = ctx->wait_ns;
+      a1.fault_skip = ctx->fault == S2W_FAULT_WAIT ? 1 : 0;
       {
         StageTimer t(ctx, 1, st);
         CK(launch_stream_dot(a1, ctx->num_sms, st));
@@ -1159,6 +1263,11 @@ int s2w_waveforms(s2w_ctx* ctx, const float* slip, int B, float* q, float* seafl
         StageTimer t(ctx, 2, st, 0);
         CK(cudaMemcpy2DAsync(ctx->ws_vhat, sizeof(float2) * ctx->nseg * ctx->RL, ctx->ws_mhat, sizeof(float2) * Ng,
                              sizeof(float2) * Ng, Nb, cudaMemcpyDeviceToDevice, st));
+      } else if (ctx->df) {
+        StageTimer t(ctx, 2, st);
+        CK(launch_df_retransform(ctx->ws_mhat, ctx->ws_mhat_lo, Ng, Ng, static_cast<int>(Nt), ctx->tw_df,
+                                 1.0 / ctx->opts.dt, ctx->opts.dt_mode, ctx->ws_vhat, ctx->ws_vhat_lo,
+                                 static_cast<long long>(ctx->nseg) * ctx->RL, sf, st));
       } else {
         StageTimer t(ctx, 2, st);
         CK(launch_retransform(ctx->ws_mhat, Ng, Ng, static_cast<int>(Nt), ctx->tw,
@@ -1178,7 +1287,13 @@ int s2w_waveforms(s2w_ctx* ctx, const float* slip, int B, float* q, float* seafl
       a2.x_stride = ctx->RL;
       a2.rows_per_vec = No;
       a2.y = ctx->ws_part + b * part_b;
+      if (ctx->df) {
+        a2.rows_lo = ctx->P_lo;
+        a2.x_lo = ctx->ws_vhat_lo;
+        a2.y_lo = ctx->ws_part_lo + b * part_b;
+      }
       a2.status = ctx->d_status;
+      a2.wait_ns = ctx->wait_ns;
       {
         StageTimer t(ctx, 3, st);
         CK(launch_stream_dot(a2, ctx->num_sms, st));
@@ -1187,9 +1302,14 @@ int s2w_waveforms(s2w_ctx* ctx, const float* slip, int B, float* q, float* seafl
     // K5
     {
       StageTimer t(ctx, 4, st);
-      CK(launch_reduce_irfft(ctx->ws_part, Bg, static_cast<int>(No), ctx->nseg, static_cast<int>(ctx->L / 2), part_b,
-                             static_cast<long long>(ctx->nseg) * No, No, ctx->tw,
-                             q_d + static_cast<long long>(g0) * No * Nt, st, static_cast<int>(Nt)));
+      if (ctx->df)
+        CK(launch_df_reduce_irfft(ctx->ws_part, ctx->ws_part_lo, Bg, static_cast<int>(No), ctx->nseg,
+                                  static_cast<int>(ctx->L / 2), part_b, static_cast<long long>(ctx->nseg) * No, No,
+                                  ctx->tw_df, q_d + static_cast<long long>(g0) * No * Nt, st, static_cast<int>(Nt)));
+      else
+        CK(launch_reduce_irfft(ctx->ws_part, Bg, static_cast<int>(No), ctx->nseg, static_cast<int>(ctx->L / 2),
+                               part_b, static_cast<long long>(ctx->nseg) * No, No, ctx->tw,
+                               q_d + static_cast<long long>(g0) * No * Nt, st, static_cast<int>(Nt)));
     }
   }
   if (kq == 0) {
@@ -1225,6 +1345,7 @@ int s2w_waveforms_active(s2w_ctx* ctx, const float* slip, const int* active_len,
 int s2w_adjoint(s2w_ctx* ctx, const float* r, int B, float* grad_s, void* stream) {
   if (ctx && ctx->single_pass)
     return fail(ctx, S2W_ERR_UNSUPPORTED, "adjoint: not available in the single-pass variant");
+  if (ctx && ctx->df) return fail(ctx, S2W_ERR_UNSUPPORTED, "adjoint: not available with FP32_HILO storage");
   if (!ctx) return S2W_ERR_ARG;
   if (B < 0 || B > ctx->opts.max_batch)
     return fail(ctx, S2W_ERR_ARG, "adjoint: B=%d outside [0, max_batch=%d]", B, ctx->opts.max_batch);
@@ -1324,6 +1445,7 @@ int s2w_misfit_gradient(s2w_ctx* ctx, const float* slip, const float* d, int B, 
                         void* stream) {
   if (ctx && ctx->single_pass)
     return fail(ctx, S2W_ERR_UNSUPPORTED, "misfit_gradient: not available in the single-pass variant");
+  if (ctx && ctx->df) return fail(ctx, S2W_ERR_UNSUPPORTED, "misfit_gradient: not available with FP32_HILO storage");
   if (!ctx) return S2W_ERR_ARG;
   if (B < 0 || B > ctx->opts.max_batch)
     return fail(ctx, S2W_ERR_ARG, "misfit_gradient: B=%d outside [0, max_batch=%d]", B, ctx->opts.max_batch);
@@ -1445,6 +1567,85 @@ int s2w_waveforms_graph(s2w_ctx* ctx, const float* slip, int B, float* q, void* 
   return S2W_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Autotuner cache: one text line per problem,
+//   s2w-tune-1 <key> bsub=<n> pair=<n> s2c=<n> minb=<n>
+// with <key> naming everything the choices depend on.  A later entry for the
+// same key replaces the earlier one.
+std::string tune_key(const s2w_ctx* ctx, int B) {
+  cudaDeviceProp pr;
+  char name[256] = "unknown";
+  if (cudaGetDeviceProperties(&pr, ctx->device) == cudaSuccess) {
+    std::snprintf(name, sizeof(name), "%s", pr.name);
+    for (char* c = name; *c; ++c)
+      if (*c == ' ' || *c == '\t') *c = '_';
+  }
+  char k[512];
+  std::snprintf(k, sizeof(k), "Ns=%d,Ng=%d,No=%d,Nt=%d,B=%d,pg=%d,pp=%d,f8a=%d,adj=%d,bmax=%d,sms=%d,gpu=%s", ctx->Ns,
+                ctx->Ng, ctx->No, ctx->Nt, B, ctx->opts.prec_g, ctx->opts.prec_p, ctx->opts.tc_fp8_act,
+                ctx->opts.tc_adjoint, ctx->tc_bsub_max, ctx->num_sms, name);
+  return k;
+}
+
+bool tune_cache_read(const std::string& path, const std::string& key, int* bsub, int* pair, int* s2c, int* minb) {
+  FILE* f = std::fopen(path.c_str(), "r");
+  if (!f) return false;
+  char line[1024];
+  bool found = false;
+  while (std::fgets(line, sizeof(line), f)) {
+    char k[600];
+    int b, p, c, m;
+    if (std::sscanf(line, "s2w-tune-1 %599s bsub=%d pair=%d s2c=%d minb=%d", k, &b, &p, &c, &m) == 5 && key == k) {
+      *bsub = b;
+      *pair = p;
+      *s2c = c;
+      *minb = m;
+      found = true;  // keep reading: the last entry for the key wins
+    }
+  }
+  std::fclose(f);
+  return found;
+}
+
+// Rewrites the file with the entry for `key` replaced (written to a temporary
+// file next to it, then renamed over it).
+bool tune_cache_write(const std::string& path, const std::string& key, int bsub, int pair, int s2c, int minb) {
+  std::vector<std::string> keep;
+  if (FILE* f = std::fopen(path.c_str(), "r")) {
+    char line[1024];
+    while (std::fgets(line, sizeof(line), f)) {
+      char k[600];
+      if (std::sscanf(line, "s2w-tune-1 %599s", k) == 1 && key == k) continue;
+      keep.emplace_back(line);
+    }
+    std::fclose(f);
+  }
+  char tmp_name[64];
+  std::snprintf(tmp_name, sizeof(tmp_name), ".tmp%d", static_cast<int>(std::rand() & 0xffffff));
+  const std::string tmp = path + tmp_name;
+  FILE* f = std::fopen(tmp.c_str(), "w");
+  if (!f) return false;
+  for (const auto& l : keep) std::fputs(l.c_str(), f);
+  std::fprintf(f, "s2w-tune-1 %s bsub=%d pair=%d s2c=%d minb=%d\n", key.c_str(), bsub, pair, s2c, minb);
+  const bool ok = std::fclose(f) == 0;
+  if (!ok || std::rename(tmp.c_str(), path.c_str()) != 0) {
+    std::remove(tmp.c_str());
+    return false;
+  }
+  return true;
+}
+
+// GEMM-form knob of the tensor engine: the public S2W_PAIR_* value and the
+// internal tc_pair code it selects.
+int pair_code(int pub) { return pub == S2W_PAIR_ON ? 1 : (pub == S2W_PAIR_OFF ? 0 : kDefaultPair); }
+
+}  // namespace
+
+extern "C" {
+
 int s2w_autotune(s2w_ctx* ctx, int B, s2w_tuning* out, void* stream) {
   if (!ctx) return S2W_ERR_ARG;
   if (B < 1 || B > ctx->opts.max_batch)
@@ -1453,11 +1654,32 @@ int s2w_autotune(s2w_ctx* ctx, int B, s2w_tuning* out, void* stream) {
     return fail(ctx, S2W_ERR_STATE, "autotune: operators not fully loaded");
   DeviceGuard guard(ctx->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  // captured graphs hold the old engine choices
+  // captured graphs hold the old schedule
   CK(cudaStreamSynchronize(st));
   for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.exec);
   ctx->graphs.clear();
   s2w_tuning r{};
+  const bool tensor = ctx->tc_on && (ctx->tc_split || ctx->tc_T != nullptr);
+  const std::string key = tune_key(ctx, B);
+  // the public pair value of the current form (AUTO unless the caller fixed one)
+  int pair_pub = ctx->opts.tc_pair;
+  if (tensor && !ctx->tune_cache.empty()) {
+    int b = 0, p = 0, c = 0, m = 0;
+    if (tune_cache_read(ctx->tune_cache, key, &b, &p, &c, &m) && (b == 128 || b == 256) && b <= ctx->tc_bsub_max &&
+        (p == S2W_PAIR_AUTO || p == S2W_PAIR_ON || p == S2W_PAIR_OFF) && c >= 1 && c <= kMaxS2Chunks && m >= 1) {
+      ctx->tc_bsub = b;
+      ctx->tc_pair = pair_code(p);
+      set_s2_chunks(ctx, c);
+      ctx->tc_min_batch = m;
+      r.from_cache = 1;
+      r.tc_bsub = ctx->tc_bsub;
+      r.tc_pair = p;
+      r.tc_s2_chunks = ctx->tc_nkc;
+      r.tc_min_batch = m;
+      if (out) *out = r;
+      return S2W_OK;
+    }
+  }
   const bool prof = ctx->prof_on;
   ctx->prof_on = false;
   const long long l0 = ctx->launches;
@@ -1484,41 +1706,63 @@ int s2w_autotune(s2w_ctx* ctx, int B, s2w_tuning* out, void* stream) {
     return rc;
   };
   int rc = timed(1, S2W_ENGINE_STREAM, &r.ms_stream_per_rupture);
-  r.tc_cluster = ctx->tc_cl1;
   r.tc_min_batch = ctx->tc_min_batch;
-  if (rc == S2W_OK && ctx->tc_on && (ctx->tc_split || ctx->tc_T != nullptr)) {
-    r.probe_batch = std::min(B, ctx->tc_bsub);
-    const int cls[3] = {1, 2, 4};
+  r.tc_bsub = ctx->tc_bsub;
+  r.tc_pair = pair_pub;
+  r.tc_s2_chunks = ctx->tc_nkc;
+  if (rc == S2W_OK && tensor) {
+    r.probe_batch = std::min(B, ctx->tc_bsub_max);
+    // 1. the GEMM form: ruptures per pass x pair mode (fixed options are not searched)
+    // (the 128-rupture passes only when the probe batch needs two of them)
+    const int bsubs[2] = {ctx->tc_bsub_max, ctx->tc_bsub_max > 128 && r.probe_batch > 128 ? 128 : 0};
+    const int pairs[3] = {S2W_PAIR_AUTO, S2W_PAIR_OFF, S2W_PAIR_ON};
     float best = 1e30f;
-    int best_cl = ctx->tc_cl1;
-    for (int c = 0; c < 3 && rc == S2W_OK; ++c) {
-      ctx->tc_cl1 = ctx->tc_cl2 = cls[c];
-      rc = timed(r.probe_batch, S2W_ENGINE_TENSOR, &r.ms_tensor_cluster[c]);
-      if (rc == S2W_OK && r.ms_tensor_cluster[c] < best) {
-        best = r.ms_tensor_cluster[c];
-        best_cl = cls[c];
+    int best_b = ctx->tc_bsub, best_p = pair_pub, nf = 0;
+    for (int i = 0; i < 2 && rc == S2W_OK; ++i) {
+      if (bsubs[i] == 0 || (ctx->opts.tc_bsub != 0 && bsubs[i] != ctx->opts.tc_bsub)) continue;
+      for (int j = 0; j < 3 && rc == S2W_OK; ++j) {
+        if (ctx->opts.tc_pair != S2W_PAIR_AUTO && pairs[j] != ctx->opts.tc_pair) continue;
+        ctx->tc_bsub = bsubs[i];
+        ctx->tc_pair = pair_code(pairs[j]);
+        set_s2_chunks(ctx, ctx->opts.tc_s2_chunks);
+        r.form_bsub[nf] = bsubs[i];
+        r.form_pair[nf] = pairs[j];
+        rc = timed(r.probe_batch, S2W_ENGINE_TENSOR, &r.ms_form[nf]);
+        if (rc == S2W_OK && r.ms_form[nf] < best) {
+          best = r.ms_form[nf];
+          best_b = bsubs[i];
+          best_p = pairs[j];
+        }
+        ++nf;
       }
     }
-    ctx->tc_cl1 = ctx->tc_cl2 = best_cl;
-    r.tc_cluster = best_cl;
-    // sub-batch size: 256 ruptures (N = 512, one M tile per unit) or 128
-    // (N = 256, M-tile pairs; the spectra are streamed twice as often)
-    r.tc_bsub = ctx->tc_bsub;
-    if (rc == S2W_OK && ctx->tc_bsub > 128 && r.probe_batch > 128) {
-      const int full = ctx->tc_bsub;
-      ctx->tc_bsub = 128;
-      ctx->tc_cl1 = ctx->tc_cl2 = 1;  // the M-tile pairs need single CTAs
-      rc = timed(r.probe_batch, S2W_ENGINE_TENSOR, &r.ms_tensor_half);
-      if (rc == S2W_OK && r.ms_tensor_half < best) {
-        best = r.ms_tensor_half;
-        r.tc_cluster = 1;
-      } else {
-        ctx->tc_bsub = full;
-        ctx->tc_cl1 = ctx->tc_cl2 = best_cl;
+    ctx->tc_bsub = best_b;
+    ctx->tc_pair = pair_code(best_p);
+    set_s2_chunks(ctx, ctx->opts.tc_s2_chunks);
+    r.tc_bsub = best_b;
+    r.tc_pair = best_p;
+    // 2. the stage-2 K chunk count around the round-balance choice
+    int best_c = ctx->tc_nkc;
+    if (rc == S2W_OK && ctx->opts.tc_s2_chunks == 0) {
+      const int h = ctx->tc_nkc;
+      const int cand[4] = {h, std::max(1, h / 2), std::min(kMaxS2Chunks, 2 * h), 1};
+      float best_s2 = 1e30f;
+      for (int k = 0; k < 4 && rc == S2W_OK; ++k) {
+        bool dup = false;
+        for (int j = 0; j < k; ++j) dup = dup || r.s2_chunk_cand[j] == cand[k];
+        if (dup) continue;
+        set_s2_chunks(ctx, cand[k]);
+        r.s2_chunk_cand[k] = ctx->tc_nkc;
+        rc = timed(r.probe_batch, S2W_ENGINE_TENSOR, &r.ms_s2_chunks[k]);
+        if (rc == S2W_OK && r.ms_s2_chunks[k] < best_s2) {
+          best_s2 = r.ms_s2_chunks[k];
+          best_c = ctx->tc_nkc;
+        }
       }
-      r.tc_bsub = ctx->tc_bsub;
+      set_s2_chunks(ctx, best_c);
     }
-    // smallest batch whose tensor pass beats that many stream passes
+    r.tc_s2_chunks = ctx->tc_nkc;
+    // 3. the smallest batch whose tensor pass beats that many stream passes
     const int sizes[7] = {1, 2, 4, 8, 16, 32, 64};
     int min_b = 0;
     for (int k = 0; k < 7 && rc == S2W_OK; ++k) {
@@ -1535,6 +1779,9 @@ int s2w_autotune(s2w_ctx* ctx, int B, s2w_tuning* out, void* stream) {
   ctx->prof_on = prof;
   ctx->launches = l0;
   if (rc != S2W_OK) return rc;
+  if (tensor && !ctx->tune_cache.empty() &&
+      !tune_cache_write(ctx->tune_cache, key, r.tc_bsub, r.tc_pair, r.tc_s2_chunks, r.tc_min_batch))
+    return fail(ctx, S2W_ERR_ARG, "autotune: cannot write the cache file %s", ctx->tune_cache.c_str());
   if (out) *out = r;
   return S2W_OK;
 }
@@ -1647,12 +1894,22 @@ extern "C" int s2w_waveforms_noalloc(s2w_ctx* ctx, const float* slip, float* q, 
   if (!ctx) return S2W_ERR_ARG;
   if (!slip || !q) return fail(ctx, S2W_ERR_ARG, "waveforms_noalloc: slip and q must not be NULL");
   const long long Ns = ctx->Ns, Ng = ctx->Ng, No = ctx->No, Nt = ctx->Nt, Nb = ctx->Nb, Ns_pad = ctx->Ns_pad;
+  // the FFT half-length of the context (the single-pass variant, whose L is
+  // not 2 Nt, is rejected above)
+  const int Lh = static_cast<int>(ctx->L / 2);
   const long long seg_cols = static_cast<long long>(ctx->nseg) * ctx->RL;
-  const size_t off_s = 0;
-  const size_t off_m = align256(off_s + sizeof(float2) * Nb * Ns_pad);
-  const size_t off_v = align256(off_m + sizeof(float2) * Nb * Ng);
-  const size_t off_p = align256(off_v + sizeof(float2) * Nb * seg_cols);
-  const size_t need = off_p + sizeof(float2) * Nb * ctx->nseg * No;
+  // scratch regions (each 256-byte aligned); FP32_HILO adds a low-order
+  // region after each of them
+  const int parts = ctx->df ? 2 : 1;
+  const size_t sz_s = sizeof(float2) * Nb * Ns_pad, sz_m = sizeof(float2) * Nb * Ng;
+  const size_t sz_v = sizeof(float2) * Nb * seg_cols, sz_p = sizeof(float2) * Nb * ctx->nseg * No;
+  size_t off[4][2], need = 0;
+  const size_t sizes[4] = {sz_s, sz_m, sz_v, sz_p};
+  for (int r = 0; r < 4; ++r)
+    for (int h = 0; h < 2; ++h) {
+      off[r][h] = need;
+      if (h < parts) need = align256(need + sizes[r]);
+    }
   if (need > kNoAllocScratchBytes)
     return fail(ctx, S2W_ERR_UNSUPPORTED,
                 "waveforms_noalloc: this problem needs %zu bytes of scratch, more than the static %zu bytes "
@@ -1667,17 +1924,28 @@ extern "C" int s2w_waveforms_noalloc(s2w_ctx* ctx, const float* slip, float* q, 
   const int rs = noalloc_scratch(ctx, &base);
   if (rs != S2W_OK) return rs;
   unsigned char* sc = static_cast<unsigned char*>(base);
-  float2* shat = reinterpret_cast<float2*>(sc + off_s);
-  float2* mhat = reinterpret_cast<float2*>(sc + off_m);
-  float2* vhat = reinterpret_cast<float2*>(sc + off_v);
-  float2* part = reinterpret_cast<float2*>(sc + off_p);
+  auto region = [&](int r, int h) { return reinterpret_cast<float2*>(sc + off[r][h]); };
+  float2* shat = region(0, 0);
+  float2* mhat = region(1, 0);
+  float2* vhat = region(2, 0);
+  float2* part = region(3, 0);
+  float2* shat_lo = ctx->df ? region(0, 1) : nullptr;
+  float2* mhat_lo = ctx->df ? region(1, 1) : nullptr;
+  float2* vhat_lo = ctx->df ? region(2, 1) : nullptr;
+  float2* part_lo = ctx->df ? region(3, 1) : nullptr;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   // The array keeps the previous call's contents: zero the regions whose
   // padding entries are read (slip spectra columns >= Ns, velocity spectra
   // columns >= Ng); mhat and the partials are overwritten in full.
-  CK(cudaMemsetAsync(shat, 0, sizeof(float2) * Nb * Ns_pad, st));
-  CK(cudaMemsetAsync(vhat, 0, sizeof(float2) * Nb * seg_cols, st));
-  CK(launch_rfft_rows(slip, Ns, static_cast<int>(Nt), static_cast<int>(Nt), ctx->tw, shat, Ns_pad, Ns, Ns_pad, st));
+  CK(cudaMemsetAsync(shat, 0, sz_s, st));
+  CK(cudaMemsetAsync(vhat, 0, sz_v, st));
+  if (ctx->df) {
+    CK(cudaMemsetAsync(shat_lo, 0, sz_s, st));
+    CK(cudaMemsetAsync(vhat_lo, 0, sz_v, st));
+    CK(launch_df_rfft_rows(slip, Ns, static_cast<int>(Nt), Lh, ctx->tw_df, shat, shat_lo, Ns_pad, Ns, Ns_pad, st));
+  } else {
+    CK(launch_rfft_rows(slip, Ns, static_cast<int>(Nt), Lh, ctx->tw, shat, Ns_pad, Ns, Ns_pad, st));
+  }
   StreamArgs a1{};
   a1.rows = ctx->G;
   a1.rows_lo = ctx->G_lo;
@@ -1685,28 +1953,41 @@ extern "C" int s2w_waveforms_noalloc(s2w_ctx* ctx, const float* slip, float* q, 
   a1.row_len = static_cast<int>(Ns_pad);
   a1.el = ctx->opts.prec_g;
   a1.x = shat;
+  a1.x_lo = shat_lo;
   a1.x_stride = Ns_pad;
   a1.rows_per_vec = Ng;
   a1.scale = ctx->G_scale;
   a1.nblk = ctx->nblk;
   a1.y = mhat;
+  a1.y_lo = mhat_lo;
   a1.status = ctx->d_status;
   CK(launch_stream_dot(a1, ctx->num_sms, st));
-  CK(launch_retransform(mhat, Ng, Ng, static_cast<int>(Nt), ctx->tw, static_cast<float>(1.0 / ctx->opts.dt),
-                        ctx->opts.dt_mode, vhat, seg_cols, nullptr, st));
+  if (ctx->df)
+    CK(launch_df_retransform(mhat, mhat_lo, Ng, Ng, Lh, ctx->tw_df, 1.0 / ctx->opts.dt, ctx->opts.dt_mode, vhat,
+                             vhat_lo, seg_cols, nullptr, st));
+  else
+    CK(launch_retransform(mhat, Ng, Ng, Lh, ctx->tw, static_cast<float>(1.0 / ctx->opts.dt), ctx->opts.dt_mode, vhat,
+                          seg_cols, nullptr, st));
   StreamArgs a2{};
   a2.rows = ctx->P;
+  a2.rows_lo = ctx->P_lo;
   a2.F = Nb * ctx->nseg * No;
   a2.row_len = ctx->RL;
   a2.el = ctx->opts.prec_p;
   a2.x = vhat;
+  a2.x_lo = vhat_lo;
   a2.x_stride = ctx->RL;
   a2.rows_per_vec = No;
   a2.y = part;
+  a2.y_lo = part_lo;
   a2.status = ctx->d_status;
   CK(launch_stream_dot(a2, ctx->num_sms, st));
-  CK(launch_reduce_irfft(part, 1, static_cast<int>(No), ctx->nseg, static_cast<int>(Nt), Nb * ctx->nseg * No,
-                         static_cast<long long>(ctx->nseg) * No, No, ctx->tw, q, st));
+  if (ctx->df)
+    CK(launch_df_reduce_irfft(part, part_lo, 1, static_cast<int>(No), ctx->nseg, Lh, Nb * ctx->nseg * No,
+                              static_cast<long long>(ctx->nseg) * No, No, ctx->tw_df, q, st, static_cast<int>(Nt)));
+  else
+    CK(launch_reduce_irfft(part, 1, static_cast<int>(No), ctx->nseg, Lh, Nb * ctx->nseg * No,
+                           static_cast<long long>(ctx->nseg) * No, No, ctx->tw, q, st, static_cast<int>(Nt)));
   ctx->launches += 5;
   return S2W_OK;
 }

@@ -28,10 +28,11 @@ constexpr unsigned long long kWaitLimitNs = 2000000000ull;
 constexpr int kDtTranspose = 2;
 
 // Storage codes of the resident spectra (same values as S2W_PREC_*).
-enum Elem : int { EL_FP32 = 0, EL_BF16 = 1, EL_BF16_HILO = 2, EL_FP8 = 3 };
+enum Elem : int { EL_FP32 = 0, EL_BF16 = 1, EL_BF16_HILO = 2, EL_FP8 = 3, EL_FP32_HILO = 4 };
 
+// Bytes of one complex entry of one stored array (the hi/lo kinds keep two).
 __host__ __device__ inline int elem_complex_bytes(int el) {
-  return el == EL_FP32 ? 8 : (el == EL_FP8 ? 2 : 4);
+  return (el == EL_FP32 || el == EL_FP32_HILO) ? 8 : (el == EL_FP8 ? 2 : 4);
 }
 
 // ---------------------------------------------------------------------------
@@ -87,14 +88,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Wait for phase `parity` of `bar` to complete, for at most kWaitLimitNs.
-// On timeout, latch `code` into the device status word and return false.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* status, int code) {
+// Wait for phase `parity` of `bar` to complete, for at most `limit_ns`
+// (kWaitLimitNs by default).  On timeout, latch `code` into the device status
+// word and return false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* status, int code,
+                                                  unsigned long long limit_ns = kWaitLimitNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = globaltimer();
   for (uint32_t it = 1;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 255u) == 0u && globaltimer() - t0 > kWaitLimitNs) {
+    if ((it & 255u) == 0u && globaltimer() - t0 > limit_ns) {
       atomicOr(status, code);
       return false;
     }
@@ -159,23 +162,43 @@ cudaError_t launch_store_adjoint(const float2* src, int Nb, int No, long long nc
                                  int el, void* dst, cudaStream_t st);
 cudaError_t launch_fp8_store(const float2* spec, int Nb, long long rows, int Ns_pad, long long row0, long long Ng,
                              float* scale, int nblk, void* dst, cudaStream_t st);
+// k_df.cu (FP32_HILO: spectra and intermediates as FP32 pairs hi + lo):
+// tw[m] = exp(-2 pi i m / L) as (re hi, re lo, im hi, im lo), FP64-evaluated.
+cudaError_t launch_twiddles_df(float4* tw, int L, cudaStream_t st);
+// launch_rfft_rows with pair output (X hi, X_lo lo; same indexing).
+cudaError_t launch_df_rfft_rows(const float* x, long long rows, int n_in, int Nt, const float4* tw, float2* X,
+                                float2* X_lo, long long ld_l, long long rows_a, long long ld_a, cudaStream_t st,
+                                const int* lens = nullptr);
+// launch_retransform of one rupture with pairs in and out (dt_mode BACKWARD
+// or NONE; seafloor optional, rounded to FP32).
+cudaError_t launch_df_retransform(const float2* mhat, const float2* mhat_lo, long long Ng, long long ld_m, int Nt,
+                                  const float4* tw, double inv_dt, int dt_mode, float2* vhat, float2* vhat_lo,
+                                  long long ld_v, float* seafloor, cudaStream_t st);
+// launch_reduce_irfft with pair partials (FP32 output).
+cudaError_t launch_df_reduce_irfft(const float2* part, const float2* part_lo, int B, int No, int nseg, int Nt,
+                                   long long s_b, long long s_l, long long s_s, const float4* tw, float* q,
+                                   cudaStream_t st, int n_keep = 0);
 
 // k_stream.cu: y[f] = sum_c rows[f][c] * x_vec(f)[c] for f < F, with
 // x_vec(f) = x + (f / rows_per_vec) * x_stride.  Rows are contiguous,
 // row_len complex entries each, row_len a multiple of 8 and <= 1024.
 struct StreamArgs {
   const void* rows;
-  const void* rows_lo;        // BF16 hi/lo: the lo array (same layout), else nullptr
+  const void* rows_lo;        // BF16 / FP32 hi/lo: the lo array (same layout), else nullptr
   long long F;
   int row_len;
   int el;                     // Elem
   const float2* x;
+  const float2* x_lo;         // FP32_HILO: low-order parts of x (same layout)
   long long x_stride;         // complex entries between consecutive x vectors
   long long rows_per_vec;
   const float* scale;         // FP8: scale[(f / rows_per_vec) * nblk + (f % rows_per_vec) / 256]
   int nblk;
   float2* y;
+  float2* y_lo;                // FP32_HILO: low-order parts of y
   int* status;
+  unsigned long long wait_ns;  // bound of every wait (0: kWaitLimitNs)
+  int fault_skip;              // test hook: 1 = the producer skips its first copy (consumers' waits run out)
 };
 cudaError_t launch_stream_dot(const StreamArgs& a, int num_sms, cudaStream_t st);
 
@@ -210,7 +233,6 @@ struct TcArgs {
   int n_kchunks;          // split of the K blocks into chunks (stage 2)
   int kblocks_per_chunk;  // 64-element K blocks per chunk
   int stages;             // shared-memory ring depth
-  int cluster;            // CTAs per cluster sharing each B tile by multicast (1, 2, 4); B box rows = N / cluster
   int tmem_cols;          // power of two >= max(32, N)
   int epi;                // 0: out[l*ld_l + t*ld_t + row]; 1: out[((l*n_kchunks + kc)*M_total + row)*T + t]
   int T;                  // complex output columns (N / 2 live)
@@ -224,10 +246,10 @@ struct TcArgs {
   int a_fp8;               // 1: A is FP8 e4m3 (byte tensor map, row-major), widened to FP16 in shared memory;
                            //    needs row_scale; B is FP16 (launch_pack_b_f16) with its amax in b_amax
   const unsigned* b_amax;  // FP16 B operand: amax (float bits) that set its power-of-two scale
-  int m_pair;              // 1: two M tiles per unit sharing each B tile (N <= 256, cluster 1, not FP8;
+  int m_pair;              // 1: two M tiles per unit sharing each B tile (N <= 256, not FP8;
                            //    tmem_cols >= 2 N, stages from tc_stages_for(..., mt = 2))
   int cta2;                // 1: two-SM MMAs, a CTA pair per M = 256 tile, each staging half of B
-                           //    (N % 32 == 0, cluster 1, no m_pair; B box rows = min(N, 256) / 2,
+                           //    (N % 32 == 0, no m_pair; B box rows = min(N, 256) / 2,
                            //    K blocks tc_block_k(N, split, 1), stages from tc_stages_pair)
   int* status;
 };

@@ -6,14 +6,15 @@ import oracle
 
 
 def make_context(s2w, geom, Nt, prec_g="fp32", prec_p="fp32", dt_mode="backward",
-                 max_batch=1, chunk=4096, order=None, engine="auto", tc_cluster=0, tc_adjoint=False,
-                 single_pass=False, tc_pair="auto", tc_fp8_act=False):
+                 max_batch=1, chunk=4096, order=None, engine="auto", tc_adjoint=False,
+                 single_pass=False, tc_pair="auto", tc_fp8_act=False, **opts):
     """Context with both operators loaded from the generator, in row chunks
     (optionally in a permuted chunk order)."""
     Ng = geom.Ng
     ctx = s2w.Context(geom.Ns, Ng, geom.No, Nt, prec_g=prec_g, prec_p=prec_p,
-                      dt_mode=dt_mode, max_batch=max_batch, engine=engine, tc_cluster=tc_cluster,
-                      tc_adjoint=tc_adjoint, single_pass=single_pass, tc_pair=tc_pair, tc_fp8_act=tc_fp8_act)
+                      dt_mode=dt_mode, max_batch=max_batch, engine=engine,
+                      tc_adjoint=tc_adjoint, single_pass=single_pass, tc_pair=tc_pair, tc_fp8_act=tc_fp8_act,
+                      **opts)
     starts = list(range(0, Ng, chunk))
     if order is not None:
         starts = [starts[i] for i in order]
@@ -55,11 +56,14 @@ def window_norms(G, P, slip, dt_mode="backward"):
     return wn, wn / np.maximum(hn, 1e-300)
 
 
-def assert_parity(q, q_ref, wnorm, kappa, tol, strict=1e-5, kappa_max=10.0, label=""):
-    """Two bars, per rupture:
-    (1) ||q - q_ref|| <= tol * ||q_win||  (accuracy on the FFT window's scale);
-    (2) for FP32-class paths (tol <= 1e-5) on well-conditioned windows
-        (kappa <= kappa_max): the plain rel-L2 <= strict."""
+def assert_parity(q, q_ref, wnorm, kappa, tol, strict=1e-5, label=""):
+    """Per rupture, the plain relative L2 error over all No x Nt samples and
+    the error relative to the 2 Nt-sample FFT window (``window_norms``) are
+    printed, then:
+    FP32-class paths (tol <= 1e-5): plain rel-L2 <= strict (1e-5, the stated
+        target) for EVERY rupture, whatever its window/head ratio kappa;
+    reduced-precision paths: ||q - q_ref|| <= tol * ||q_win||, the path's
+        stated bound on the scale its FFT evaluation works on."""
     q = np.asarray(q, dtype=np.float64)
     q_ref = np.asarray(q_ref, dtype=np.float64)
     if q.ndim == 2:
@@ -68,8 +72,8 @@ def assert_parity(q, q_ref, wnorm, kappa, tol, strict=1e-5, kappa_max=10.0, labe
     rel = err / np.maximum(np.linalg.norm(q_ref.reshape(q.shape[0], -1), axis=1), 1e-300)
     win = err / np.maximum(wnorm, 1e-300)
     print(f"{label}: rel-L2 {rel}, error / window norm {win}, kappa {kappa}")
-    assert np.all(win <= tol), (label, win, tol)
     if tol <= 1e-5:
-        good = kappa <= kappa_max
-        assert np.all(rel[good] <= strict), (label, rel, kappa)
+        assert np.all(rel <= strict), (label, rel, kappa)
+    else:
+        assert np.all(win <= tol), (label, win, tol)
     return rel, win

@@ -32,12 +32,14 @@ def test_library_exports_every_declared_symbol():
     assert not missing, missing
 
 
-def test_library_is_built_for_sm_103a():
-    out = subprocess.run(["cuobjdump", "--list-elf", s2w.lib()._name],
-                         capture_output=True, text=True)
-    if out.returncode != 0:
-        pytest.skip("cuobjdump unavailable")
-    assert "sm_103a" in out.stdout
+def test_library_is_built_for_sm_103a_only():
+    """Every object is compiled with exactly one -gencode, sm_103a's, and
+    the link uses the same one."""
+    from paper_2608_21763_gb300 import _build
+    assert _build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+    flags = _build.NVCC_FLAGS
+    assert flags[:2] == _build.ARCH
+    assert flags.count("-gencode") == 1 and not any(f.startswith("-arch") for f in flags)
 
 
 def test_status_strings_and_default_opts():
@@ -64,21 +66,25 @@ def test_opts_layout_matches_the_header():
     larger than the binding's Opts, it must stop exactly at Opts' end (a
     field missing from the binding would be written past it) and leave the
     defaults of the last fields (two-SM tiles: library choice; FP8
-    activations off)."""
+    activations off; library sub-batch and stage-2 chunking; no tune cache;
+    no injected fault)."""
     L = s2w.lib()
     n = ctypes.sizeof(s2w.Opts)
     buf = (ctypes.c_ubyte * (n + 64))(*([0xAB] * (n + 64)))
     L.s2w_default_opts(ctypes.cast(buf, ctypes.POINTER(s2w.Opts)))
     assert all(b == 0xAB for b in buf[n:])
     o = s2w.Opts.from_buffer(buf)
-    assert (o.tc_cluster, o.tc_adjoint, o.single_pass, o.tc_pair, o.tc_fp8_act) == (0, 0, 0, 0, 0)
+    assert (o.tc_adjoint, o.single_pass, o.tc_pair, o.tc_fp8_act) == (0, 0, 0, 0)
+    assert (o.tc_bsub, o.tc_s2_chunks, o.tune_cache, o.fault, o.fault_wait_us) == (0, 0, None, 0, 5000)
 
 
 def test_create_rejects_bad_options_before_touching_a_device():
     L = s2w.lib()
     h = ctypes.c_void_p()
     for field, value, prec_g in [("tc_pair", 3, 1), ("tc_pair", -1, 1), ("tc_fp8_act", 2, 3),
-                                 ("tc_fp8_act", 1, 1), ("tc_fp8_act", 1, 0)]:
+                                 ("tc_fp8_act", 1, 1), ("tc_fp8_act", 1, 0), ("tc_bsub", 64, 1),
+                                 ("tc_bsub", -1, 1), ("tc_s2_chunks", 17, 1), ("tc_s2_chunks", -1, 1),
+                                 ("fault", 9, 0)]:
         o = s2w.Opts()
         L.s2w_default_opts(ctypes.byref(o))
         o.prec_g = prec_g
@@ -93,3 +99,29 @@ def test_null_context_is_an_argument_error():
     assert L.s2w_waveforms(None, None, 1, None, None, None) == -1
     assert L.s2w_sync(None) == -1
     assert L.s2w_destroy(None) == 0
+
+
+def test_split_passes_take_at_most_128_ruptures():
+    L = s2w.lib()
+    h = ctypes.c_void_p()
+    o = s2w.Opts()
+    L.s2w_default_opts(ctypes.byref(o))
+    o.prec_g, o.tc_bsub = s2w.PREC["bf16_hilo"], 256
+    assert L.s2w_create(16, 64, 4, 32, ctypes.byref(o), ctypes.byref(h)) == -6
+    assert b"tc_bsub=256" in L.s2w_last_error(None)
+
+
+def test_fault_environment_variable_is_checked(monkeypatch):
+    """S2W_FAULT selects a test hook at s2w_create; an unknown name is an
+    argument error before any device is touched."""
+    L = s2w.lib()
+    h = ctypes.c_void_p()
+    monkeypatch.setenv("S2W_FAULT", "segfault")
+    assert L.s2w_create(16, 64, 4, 32, None, ctypes.byref(h)) == -1
+    assert b"S2W_FAULT=segfault" in L.s2w_last_error(None)
+    o = s2w.Opts()
+    L.s2w_default_opts(ctypes.byref(o))
+    o.fault, o.fault_wait_us = s2w.FAULT["wait"], 0
+    monkeypatch.delenv("S2W_FAULT")
+    assert L.s2w_create(16, 64, 4, 32, ctypes.byref(o), ctypes.byref(h)) == -1
+    assert b"fault_wait_us" in L.s2w_last_error(None)

@@ -100,10 +100,15 @@ def test_autotune_choices_and_selected_path():
     ctx = make_context(s2w, geom, Nt, prec_g="bf16", max_batch=B)
     t = ctx.autotune(B)
     print("autotune:", t)
-    assert t["tc_cluster"] in (1, 2, 4)
+    assert not t["from_cache"]
     assert t["ms_stream_per_rupture"] > 0
     assert t["probe_batch"] == B
-    assert all(v > 0 for v in t["ms_tensor_cluster"])
+    # B = 40 fits one pass: the forms probed are the three pair modes at 40 ruptures per pass
+    assert [(f["bsub"], f["pair"]) for f in t["forms"]] == [(B, "auto"), (B, "off"), (B, "on")]
+    assert all(f["ms"] > 0 for f in t["forms"])
+    assert t["tc_pair"] in ("auto", "off", "on") and t["tc_bsub"] == B
+    assert len(t["s2_chunks"]) >= 2 and all(c["ms"] > 0 for c in t["s2_chunks"])
+    assert t["tc_s2_chunks"] in [c["chunks"] for c in t["s2_chunks"]]
     assert t["tc_min_batch"] >= 1
     sizes = [1, 2, 4, 8, 16, 32, 64]
     measured = [b for b, v in zip(sizes, t["ms_tensor_batch"]) if v > 0]
@@ -124,8 +129,50 @@ def test_autotune_without_tensor_engine():
     ctx = make_context(s2w, geom, wl.Nt, max_batch=4)  # FP32: stream engine only
     t = ctx.autotune(4)
     assert t["ms_stream_per_rupture"] > 0
-    assert t["ms_tensor_cluster"] == [0.0, 0.0, 0.0]
+    assert t["forms"] == [] and t["s2_chunks"] == []
+    assert t["ms_tensor_batch"] == [0.0] * 7
     ctx.sync()
+
+
+def test_autotune_cache_second_context(tmp_path):
+    """The tuned schedule is written to the cache file; a second context for
+    the same problem takes it from there without timing anything, and its
+    waveforms equal the first context's bit for bit (same schedule, same
+    kernels).  A third context given the same choices as explicit options
+    computes the same bits without any tuning."""
+    cache = str(tmp_path / "s2w_tune.txt")
+    geom = compact_box(24, 700, 6, seed=23)
+    Nt, B = 64, 40
+    s = slips(B, geom.Ns, Nt, 77)
+    x = torch.tensor(s, dtype=torch.float32, device="cuda")
+    ctx1 = make_context(s2w, geom, Nt, prec_g="bf16", max_batch=B, tune_cache=cache)
+    t1 = ctx1.autotune(B)
+    assert not t1["from_cache"]
+    text = open(cache).read()
+    assert text.count("s2w-tune-1 ") == 1 and f"Ng=700" in text
+    q1 = ctx1.waveforms(x).cpu().numpy()
+    ctx1.sync()
+    ctx2 = make_context(s2w, geom, Nt, prec_g="bf16", max_batch=B, tune_cache=cache)
+    t2 = ctx2.autotune(B)
+    assert t2["from_cache"]
+    assert t2["forms"] == [] and t2["s2_chunks"] == [] and t2["ms_stream_per_rupture"] == 0.0
+    for k in ("tc_bsub", "tc_pair", "tc_s2_chunks", "tc_min_batch"):
+        assert t2[k] == t1[k], k
+    q2 = ctx2.waveforms(x).cpu().numpy()
+    ctx2.sync()
+    assert np.array_equal(q1, q2)
+    ctx3 = make_context(s2w, geom, Nt, prec_g="bf16", max_batch=B, tc_bsub=0, tc_pair=t1["tc_pair"],
+                        tc_s2_chunks=t1["tc_s2_chunks"])
+    q3 = ctx3.waveforms(x).cpu().numpy()
+    ctx3.sync()
+    assert np.array_equal(q1, q3)
+    G = geom.greens_rows(0, geom.Ng, Nt)
+    P = geom.adjoint_cols(0, geom.Ng, Nt)
+    assert_parity(q2, oracle.waveforms(G, P, s), *window_norms(G, P, s), tol=1e-2, label="cached schedule")
+    # a different problem (another batch) is not in the cache: measured and appended
+    t4 = ctx2.autotune(B // 2)
+    assert not t4["from_cache"]
+    assert open(cache).read().count("s2w-tune-1 ") == 2
 
 
 def test_graph_cache_alternating_buffers_and_eviction():

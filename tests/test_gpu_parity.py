@@ -1,16 +1,20 @@
 """CUDA path against the FP64 oracle, element by element, through the C ABI.
 
-Two bars per rupture (tests/helpers.assert_parity):
-  (1) ||q - q_ref|| <= TOL * ||q_win||, with q_win the 2 Nt-sample window that
-      Alg. 2 computes before Truncate (oracle.fft_window).  Finite-precision
-      FFT convolution is accurate on that scale; when a record ends as the
-      signals arrive, most of the window's energy lies past Nt.
-        FP32 storage        1e-5
+Bars per rupture (tests/helpers.assert_parity):
+  FP32 class (FP32 pairs, and FP32 storage on inputs whose kept head is not
+  dwarfed by the rest of the FFT window): the plain relative L2 error over the
+  No x Nt samples <= 1e-5, every rupture.
+  Reduced precision: ||q - q_ref|| <= TOL * ||q_win||, with q_win the 2
+  Nt-sample window that Alg. 2 computes before Truncate (oracle.fft_window),
+  the scale on which a finite-precision FFT evaluation errs:
         BF16 hi/lo storage  2e-5  (hi + lo keeps ~17 bits: <= 2^-18 per entry)
         BF16 storage        5e-3  (8 significant bits: <= 2^-9 per entry)
         FP8 e4m3 storage    1e-1  (4 significant bits: <= 2^-4 per entry)
-  (2) FP32-class paths on well-conditioned windows (window/head norm ratio
-      <= 10): the plain relative L2 error over the No x Nt samples <= 1e-5.
+  (tests/test_error_model.py derives each bound from the rounding the path
+  makes.)  FP32 storage errs by up to ~1e-5 of that window too: on the tiny
+  workload, whose rupture 0 keeps 1/393 of its window's norm in the kept head,
+  that is 1.2e-4 of the head; the FP32 pair storage (fp32_hilo) takes the same
+  rupture to ~1e-9.
 """
 import numpy as np
 import pytest
@@ -24,7 +28,7 @@ pytestmark = pytest.mark.gpu
 
 import paper_2608_21763_gb300 as s2w  # noqa: E402
 
-TOL = {"fp32": 1e-5, "bf16_hilo": 2e-5, "bf16": 5e-3, "fp8": 1e-1}
+TOL = {"fp32": 1e-5, "fp32_hilo": 1e-5, "bf16_hilo": 2e-5, "bf16": 5e-3, "fp8": 1e-1}
 
 
 @pytest.fixture(scope="module")
@@ -81,22 +85,49 @@ def test_irfft_truncates_and_inverts(Nt):
 
 
 # ---------------------------------------------------------------- end to end
-@pytest.mark.parametrize("prec", ["fp32", "bf16_hilo", "bf16", "fp8"])
+@pytest.mark.parametrize("prec", ["fp32_hilo", "bf16_hilo", "bf16", "fp8"])
 def test_tiny_workload_against_oracle(tiny, tiny_window, prec):
     wl, geom, slip, q_ref, _ = tiny
     # stream engine: these bars are for the storage precisions alone
-    ctx = make_context(s2w, geom, wl.Nt, prec_g=prec, max_batch=3, chunk=256, engine="stream")
+    prec_p = "fp32_hilo" if prec == "fp32_hilo" else "fp32"
+    ctx = make_context(s2w, geom, wl.Nt, prec_g=prec, prec_p=prec_p, max_batch=3, chunk=256, engine="stream")
     q = ctx.waveforms(torch.tensor(slip, dtype=torch.float32, device="cuda")).cpu().numpy()
     assert_parity(q, q_ref, *tiny_window, tol=TOL[prec], label=f"tiny {prec}")
+    ctx.sync()
 
 
-def test_seafloor_field_against_oracle(tiny):
-    wl, geom, slip, _, m_ref = tiny
-    ctx = make_context(s2w, geom, wl.Nt, max_batch=3)
+def test_fp32_storage_errs_on_the_window_scale(tiny, tiny_window):
+    """FP32 (complex64) spectra on the tiny workload: every rupture within
+    1e-5 of its FFT window's norm, which for rupture 0 (kept head 1/393 of
+    the window) is not 1e-5 of the head; the FP32 pairs meet 1e-5 of the head
+    there with room to spare (the config's FP32 path)."""
+    wl, geom, slip, q_ref, _ = tiny
+    wn, kappa = tiny_window
+    out = {}
+    for prec in ("fp32", "fp32_hilo"):
+        ctx = make_context(s2w, geom, wl.Nt, prec_g=prec, prec_p=prec, max_batch=3, engine="stream")
+        out[prec] = ctx.waveforms(torch.tensor(slip, dtype=torch.float32, device="cuda")).cpu().numpy()
+        ctx.sync()
+    err = {k: np.linalg.norm((v - q_ref).reshape(3, -1), axis=1) for k, v in out.items()}
+    head = np.linalg.norm(q_ref.reshape(3, -1), axis=1)
+    print("fp32: rel", err["fp32"] / head, "window", err["fp32"] / wn, "kappa", kappa)
+    print("fp32_hilo: rel", err["fp32_hilo"] / head)
+    assert np.all(err["fp32"] <= 1e-5 * wn)
+    assert np.all(err["fp32_hilo"] <= 1e-5 * head)
+    assert err["fp32_hilo"][0] * 100 <= err["fp32"][0]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp32_hilo"])
+def test_seafloor_field_against_oracle(tiny, prec):
+    wl, geom, slip, q_ref, m_ref = tiny
+    ctx = make_context(s2w, geom, wl.Nt, prec_g=prec, prec_p=prec, max_batch=3)
     s = torch.tensor(slip, dtype=torch.float32, device="cuda")
     sf = torch.empty((3, geom.Ng, wl.Nt), dtype=torch.float32, device="cuda")
-    ctx.waveforms(s, seafloor=sf)
+    q = ctx.waveforms(s, seafloor=sf).cpu().numpy()
     assert np.all(rel_l2(sf.cpu().numpy(), m_ref) <= 1e-5)
+    if prec == "fp32_hilo":  # the seafloor output does not change the waveforms
+        assert np.all(rel_l2(q, q_ref) <= 1e-5)
+        assert np.array_equal(q, ctx.waveforms(s).cpu().numpy())
 
 
 def test_bf16_p_storage(tiny, tiny_window):
@@ -185,13 +216,14 @@ def test_stream_groups_of_ruptures():
     assert_parity(q, oracle.waveforms(G, P, slip), *window_norms(G, P, slip), tol=1e-5, label="stream groups")
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp32_hilo"])
 @pytest.mark.parametrize("Ns,Ng,No,Nt", [(5, 1000, 3, 64), (1, 37, 1, 32), (1024, 300, 2, 32),
                                          (7, 2100, 5, 128)])
-def test_ragged_shapes(Ns, Ng, No, Nt):
+def test_ragged_shapes(Ns, Ng, No, Nt, prec):
     geom = compact_box(Ns, Ng, No, seed=Ns + Ng)
     slip = np.random.default_rng(1).standard_normal((2, Ns, Nt))
     slip[:, :, Nt // 2:] = 0
-    ctx = make_context(s2w, geom, Nt, max_batch=2, chunk=512)
+    ctx = make_context(s2w, geom, Nt, prec_g=prec, prec_p=prec, max_batch=2, chunk=512)
     q = ctx.waveforms(torch.tensor(slip, dtype=torch.float32, device="cuda")).cpu().numpy()
     G = geom.greens_rows(0, Ng, Nt)
     P = geom.adjoint_cols(0, Ng, Nt)
@@ -246,8 +278,8 @@ def plain_reference():
     return wl, geom, slip, q_ref, wn, kappa
 
 
-@pytest.mark.parametrize("prec_g,prec_p", [("fp32", "fp32"), ("bf16_hilo", "fp32"), ("bf16", "bf16"),
-                                           ("fp8", "bf16")])
+@pytest.mark.parametrize("prec_g,prec_p", [("fp32", "fp32"), ("fp32_hilo", "fp32_hilo"), ("bf16_hilo", "fp32"),
+                                           ("bf16", "bf16"), ("fp8", "bf16")])
 def test_plain_workload_full_size(plain_reference, prec_g, prec_p):
     """The whole waveform set of the plain workload against the FP64 oracle,
     in every storage precision, at the size and launch configuration that
@@ -391,3 +423,38 @@ def test_single_pass_spectral_loads():
     q = ctx.waveforms(torch.tensor(slip, dtype=torch.float32, device="cuda")).cpu().numpy()
     ctx.sync()
     assert_parity(q, oracle.waveforms(G, P, slip), *window_norms(G, P, slip), tol=1e-5, label="single pass spectra")
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp32_hilo"])
+@pytest.mark.parametrize("Ns,Ng,No,Nt,B", [(96, 3000, 8, 256, 3), (60, 1500, 4, 128, 2), (33, 777, 5, 64, 2)])
+def test_paper_geometry_full_length_slip(prec, Ns, Ng, No, Nt, B):
+    """Ragged shapes on the paper-shaped geometry (subfaults on the dipping
+    1000 x 100 km plane, grid and observations over its surface projection)
+    with full-length von Karman ruptures (no zeroed tail, no shrunken box):
+    every rupture within 1e-5 of the oracle in plain relative L2."""
+    geom = synth.geometry_plane(Ns, Ng, No, seed=Ns + Nt)
+    slip = synth.slip_von_karman(geom, B, Nt, seed=Ng, mw_range=(8.0, 9.0))
+    ctx = make_context(s2w, geom, Nt, prec_g=prec, prec_p=prec, max_batch=B, chunk=1024)
+    q = ctx.waveforms(torch.tensor(slip, dtype=torch.float32, device="cuda")).cpu().numpy()
+    ctx.sync()
+    G = geom.greens_rows(0, Ng, Nt)
+    P = geom.adjoint_cols(0, Ng, Nt)
+    assert_parity(q, oracle.waveforms(G, P, slip), *window_norms(G, P, slip), tol=1e-5,
+                  label=f"plane {prec} {Ns}x{Ng}x{No}x{Nt}")
+
+
+def test_fp32_pairs_reject_what_they_do_not_support():
+    geom = compact_box(8, 200, 2, seed=3)
+    with pytest.raises(s2w.S2WError):   # both operators or neither
+        s2w.Context(8, 200, 2, 32, prec_g="fp32_hilo", prec_p="fp32")
+    with pytest.raises(s2w.S2WError):
+        s2w.Context(8, 200, 2, 32, prec_g="fp32_hilo", prec_p="fp32_hilo", engine="tensor")
+    ctx = make_context(s2w, geom, 32, prec_g="fp32_hilo", prec_p="fp32_hilo", max_batch=2)
+    with pytest.raises(s2w.S2WError) as e:
+        ctx.adjoint(torch.zeros((1, 2, 32), device="cuda"))
+    assert e.value.status == -6
+    g, p = ctx.operator_bytes()
+    c32 = make_context(s2w, geom, 32, max_batch=2)
+    g32, p32 = c32.operator_bytes()
+    assert (g, p) == (2 * g32, 2 * p32)
+    ctx.sync()

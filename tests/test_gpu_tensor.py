@@ -30,12 +30,13 @@ def compact_box(Ns, Ng, No, seed, scale=0.1):
                           g.strike * scale, g.dip * scale, "box")
 
 
-def run_case(geom, Nt, B, seed=5, engine="tensor", chunk=4096, tc_cluster=0, prec="bf16", tc_pair="auto"):
+def run_case(geom, Nt, B, seed=5, engine="tensor", chunk=4096, prec="bf16", tc_pair="auto", tc_bsub=0,
+             tc_s2_chunks=0):
     rng = np.random.default_rng(seed)
     slip = rng.standard_normal((B, geom.Ns, Nt))
     slip[:, :, Nt // 2:] = 0
     ctx = make_context(s2w, geom, Nt, prec_g=prec, max_batch=B, chunk=chunk, engine=engine,
-                       tc_cluster=tc_cluster, tc_pair=tc_pair)
+                       tc_pair=tc_pair, tc_bsub=tc_bsub, tc_s2_chunks=tc_s2_chunks)
     q = ctx.waveforms(torch.tensor(slip, dtype=torch.float32, device="cuda")).cpu().numpy()
     ctx.sync()
     G = geom.greens_rows(0, geom.Ng, Nt)
@@ -139,17 +140,23 @@ def test_gemm_retransform_record_lengths(Nt):
     assert_parity(q, q_ref, *wn, tol=TOL_TC, label=f"tensor Nt={Nt}")
 
 
-@pytest.mark.parametrize("cluster", [2, 4])
-@pytest.mark.parametrize("B", [3, 300])
-def test_multicast_clusters_match_single_cta(cluster, B):
-    """Clusters that share each B tile by TMA multicast compute exactly what
-    single CTAs compute (same MMAs, same accumulation order): bitwise equal,
-    including partial M-tile groups (700 rows = 5.5 tiles) and N = 16..512."""
+@pytest.mark.parametrize("prec", ["bf16", "bf16_hilo"])
+@pytest.mark.parametrize("knob", [{"tc_bsub": 128}, {"tc_s2_chunks": 1}, {"tc_s2_chunks": 3},
+                                  {"tc_s2_chunks": 16}])
+def test_schedule_knobs(prec, knob):
+    """The schedule options the autotuner searches (ruptures per GEMM pass,
+    stage-2 K chunks) change only the order of FP32 accumulation: each meets
+    the bar and agrees with the default schedule to accumulation rounding.
+    700 grid rows = 5.5 M tiles, B = 300 (two sub-batches)."""
+    if prec == "bf16_hilo" and "tc_bsub" in knob:
+        pytest.skip("split passes take 128 ruptures anyway")
     geom = compact_box(24, 700, 6, seed=12)
-    q1, q_ref, wn, _, _ = run_case(geom, 64, B, seed=13, tc_cluster=1)
-    qc, _, _, _, _ = run_case(geom, 64, B, seed=13, tc_cluster=cluster)
-    assert_parity(qc, q_ref, *wn, tol=TOL_TC, label=f"cluster {cluster} B={B}")
-    assert np.array_equal(q1, qc)
+    tol = TOL_SPLIT if prec == "bf16_hilo" else TOL_TC
+    q1, q_ref, wn, _, _ = run_case(geom, 64, 300, seed=13, prec=prec)
+    q2, _, _, _, _ = run_case(geom, 64, 300, seed=13, prec=prec, **knob)
+    assert_parity(q2, q_ref, *wn, tol=tol, label=f"{prec} {knob}")
+    d = np.linalg.norm((q2 - q1).ravel()) / np.linalg.norm(q1.ravel())
+    assert d < 1e-6, d
 
 
 @pytest.mark.parametrize("prec", ["bf16", "bf16_hilo"])
@@ -206,14 +213,6 @@ def test_split_precision_record_lengths(Nt):
     geom = compact_box(12, 300, 3, seed=Nt + 1)
     q, q_ref, wn, _, _ = run_case(geom, Nt, 6, prec="bf16_hilo")
     assert_parity(q, q_ref, *wn, tol=TOL_SPLIT, label=f"tensor split Nt={Nt}")
-
-
-def test_split_precision_clusters_bitwise():
-    geom = compact_box(24, 700, 6, seed=33)
-    q1, q_ref, wn, _, _ = run_case(geom, 64, 40, seed=34, prec="bf16_hilo", tc_cluster=1)
-    q2, _, _, _, _ = run_case(geom, 64, 40, seed=34, prec="bf16_hilo", tc_cluster=2)
-    assert_parity(q2, q_ref, *wn, tol=TOL_SPLIT, label="tensor split cluster 2")
-    assert np.array_equal(q1, q2)
 
 
 @pytest.mark.parametrize("B", [3, 7, 300])
@@ -297,14 +296,6 @@ def test_fp8_activations_reject_other_precisions():
     geom = compact_box(8, 300, 2, seed=5)
     with pytest.raises(s2w.S2WError):
         make_context(s2w, geom, 32, prec_g="bf16", max_batch=4, tc_fp8_act=True)
-
-
-def test_fp8_tensor_clusters_bitwise():
-    geom = compact_box(24, 700, 6, seed=63)
-    q1, q_ref, wn, _, _ = run_case(geom, 64, 40, seed=64, prec="fp8", tc_cluster=1, chunk=256)
-    q2, _, _, _, _ = run_case(geom, 64, 40, seed=64, prec="fp8", tc_cluster=2, chunk=256)
-    assert_parity(q2, q_ref, *wn, tol=1e-1, label="fp8 tensor cluster 2")
-    assert np.array_equal(q1, q2)
 
 
 def test_fp8_tensor_operand_range_is_scaled():
