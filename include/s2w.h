@@ -313,7 +313,7 @@ int s2w_waveforms_graph(s2w_ctx *ctx, const float *slip, int B, float *q, void *
 typedef struct {
   int from_cache;               /* 1: the choices below came from opts.tune_cache; nothing was timed */
   int tc_min_batch;             /* smallest B that ENGINE_AUTO sends to the tensor engine */
-  int tc_bsub;                  /* chosen ruptures per GEMM pass (128 or 256) */
+  int tc_bsub;                  /* chosen ruptures per GEMM pass (<= 256) */
   int tc_pair;                  /* chosen GEMM form (S2W_PAIR_AUTO, _ON or _OFF) */
   int tc_s2_chunks;             /* chosen stage-2 K chunk count */
   int probe_batch;              /* batch size of the form and chunk probes */

@@ -1665,7 +1665,7 @@ int s2w_autotune(s2w_ctx* ctx, int B, s2w_tuning* out, void* stream) {
   int pair_pub = ctx->opts.tc_pair;
   if (tensor && !ctx->tune_cache.empty()) {
     int b = 0, p = 0, c = 0, m = 0;
-    if (tune_cache_read(ctx->tune_cache, key, &b, &p, &c, &m) && (b == 128 || b == 256) && b <= ctx->tc_bsub_max &&
+    if (tune_cache_read(ctx->tune_cache, key, &b, &p, &c, &m) && b >= 1 && b <= ctx->tc_bsub_max &&
         (p == S2W_PAIR_AUTO || p == S2W_PAIR_ON || p == S2W_PAIR_OFF) && c >= 1 && c <= kMaxS2Chunks && m >= 1) {
       ctx->tc_bsub = b;
       ctx->tc_pair = pair_code(p);

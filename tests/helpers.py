@@ -4,6 +4,16 @@ import numpy as np
 
 import oracle
 
+# Error bars of the reduced-precision paths: ||q - q_ref|| <= bar * ||q_win||
+# per rupture (q_win: the 2 Nt-sample FFT window).  Each is about twice the
+# error that the path's own roundings produce in an otherwise exact FP64
+# evaluation (tests/error_model.py) on the worst rupture of the tiny workload
+# (8.6e-3 for the tensor BF16 path, 2.6e-3 for BF16 storage, 5.2e-2 for FP8,
+# 5.9e-6 / 1.7e-5 for the hi/lo splits); tests/test_error_model.py checks
+# that every bar lies between 1.5 and 4 times that modelled error.
+BARS = {"stream_bf16": 5e-3, "stream_bf16_hilo": 2e-5, "stream_fp8": 1e-1,
+        "tensor_bf16": 2e-2, "tensor_split": 3e-5, "tensor_fp8": 1e-1}
+
 
 def make_context(s2w, geom, Nt, prec_g="fp32", prec_p="fp32", dt_mode="backward",
                  max_batch=1, chunk=4096, order=None, engine="auto", tc_adjoint=False,

@@ -15,7 +15,7 @@ import pytest
 
 import oracle
 import synth
-from helpers import make_context, window_norms
+from helpers import BARS, make_context, window_norms
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -27,7 +27,8 @@ def call_noalloc(ctx, slip, q, stream):
     return s2w.lib().s2w_waveforms_noalloc(ctx._h, slip.data_ptr(), q.data_ptr(), stream.cuda_stream)
 
 
-TOL_WINDOW = {"fp32": 1e-5, "bf16_hilo": 2e-5, "bf16": 5e-3, "fp8": 1e-1}
+TOL_WINDOW = {"fp32": 1e-5, "bf16_hilo": BARS["stream_bf16_hilo"], "bf16": BARS["stream_bf16"],
+              "fp8": BARS["stream_fp8"]}
 
 
 @pytest.mark.parametrize("prec,max_batch", [("fp32", 1), ("fp32_hilo", 1), ("bf16", 1), ("bf16_hilo", 1),
