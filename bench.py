@@ -582,6 +582,39 @@ def run_reference(args, rank):
                     "d2h_bytes_per_step": 0}}
 
 
+def torch_conv_forward(W1, W2, x, tile):
+    """q = P * D_t (G * x) with two conv_transpose1d passes over grid tiles
+    (Eq. time-domain-conv twice, each truncated to Nt samples; dt = 1).
+    W1: [Ns][Ng][Nt] (the stage-1 weight, C_in x C_out x K), W2: [Ng][No][Nt],
+    x: [B][Ns][Nt], all of one dtype on one device."""
+    import torch
+    import torch.nn.functional as F
+    Ns, Ng, Nt = W1.shape
+    No = W2.shape[1]
+    m = torch.empty((x.shape[0], Ng, Nt), dtype=x.dtype, device=x.device)
+    for g0 in range(0, Ng, tile):
+        g1 = min(Ng, g0 + tile)
+        m[:, g0:g1] = F.conv_transpose1d(x, W1[:, g0:g1])[..., :Nt]
+    v = m - F.pad(m, (1, 0))[..., :Nt]                      # D_t, dt = 1
+    q = torch.zeros((x.shape[0], No, Nt), dtype=x.dtype, device=x.device)
+    for g0 in range(0, Ng, tile):
+        g1 = min(Ng, g0 + tile)
+        q += F.conv_transpose1d(v[:, g0:g1], W2[g0:g1])[..., :Nt]
+    return q
+
+
+def torch_conv_tile(Ns, Ng, No, Nt, B):
+    """Grid tile for torch_conv_forward: the largest power of two that keeps
+    every tensor handed to the backend below 2^30 elements (half its int32
+    indexing limit: a weight above it faulted inside the library instead of
+    raising), fixed from the shapes before any call."""
+    limit = 2 ** 30
+    tile = 1 << (Ng - 1).bit_length()
+    while tile > 1 and max(Ns * tile * Nt, B * tile * (2 * Nt - 1), tile * No * Nt) > limit:
+        tile //= 2
+    return tile
+
+
 def run_torch_conv(args, rank, local_rank):
     """Eq. time-domain-conv evaluated twice with conv_transpose1d (cuDNN), D_t
     between, as the paper's direct baseline does: m = G * s, v = D_t m,
@@ -614,25 +647,8 @@ def run_torch_conv(args, rank, local_rank):
     slip_np = wl.slip(geom, B=B)
     x = torch.tensor(slip_np, dtype=dtype, device=dev)
 
-    def forward(x, tile):
-        m = torch.empty((x.shape[0], Ng, Nt), dtype=dtype, device=dev)
-        for g0 in range(0, Ng, tile):
-            g1 = min(Ng, g0 + tile)
-            m[:, g0:g1] = F.conv_transpose1d(x, W1[:, g0:g1])[..., :Nt]
-        v = m - F.pad(m, (1, 0))[..., :Nt]                      # D_t, dt = 1
-        q = torch.zeros((x.shape[0], No, Nt), dtype=dtype, device=dev)
-        for g0 in range(0, Ng, tile):
-            g1 = min(Ng, g0 + tile)
-            q += F.conv_transpose1d(v[:, g0:g1], W2[g0:g1])[..., :Nt]
-        return q
-
-    # every tensor handed to the backend stays below 2^30 elements (half its int32
-    # indexing limit: a weight above it faulted inside the library instead of
-    # raising), so the grid tile is fixed from the shapes before any call
-    limit = 2 ** 30
-    tile = 1 << (Ng - 1).bit_length()
-    while tile > 1 and max(Ns * tile * Nt, B * tile * (2 * Nt - 1), tile * No * Nt) > limit:
-        tile //= 2
+    forward = lambda x, tile: torch_conv_forward(W1, W2, x, tile)
+    tile = torch_conv_tile(Ns, Ng, No, Nt, B)
     try:
         q = forward(x, tile)
         torch.cuda.synchronize(dev)

@@ -16,8 +16,13 @@
 // bytes per step); a short row (a few subfaults) gets a power-of-two group of
 // lanes with about four chunks each, several rows per warp pass.  Each lane
 // keeps its slice of x_vec in registers across rows that share it.  Products
-// accumulate in FP32; FP8 rows are rescaled by their per-(bin, 256-row block)
-// scale after the dot product.  FP32_HILO rows (hi and lo FP32 arrays) meet
+// accumulate in FP32; FP8 rows are widened exactly to FP16 pairs (one
+// conversion per complex entry) and multiplied by the vector held as FP16
+// pairs scaled by a power of two (its largest magnitude into [2, 4)), with
+// packed FP16 multiply-adds over 16-byte chunks of 8 entries flushed into FP32
+// every two chunks, so that a streamed byte costs about two instructions;
+// the per-(bin, 256-row block) scale and the power of two are undone after
+// the dot product.  FP32_HILO rows (hi and lo FP32 arrays) meet
 // a vector of pairs (x, x_lo): each product is formed exactly (TwoProduct)
 // and summed by TwoSum into double-float accumulators (df.cuh), written as
 // pairs (y, y_lo).
@@ -67,27 +72,9 @@ __device__ __forceinline__ float2 fp8x2_to_f2(unsigned short s) {
   return __half22float2(*reinterpret_cast<const __half2*>(&h));
 }
 
-// e4m3 -> f32 by moving bits: the sign to bit 31 and the 7 exponent+mantissa
-// bits to bits 26..20 gives an f32 whose value is the e4m3 value times
-// 2^-120 (exponent bias 127 - 7 = 120), exactly, subnormals included (the
-// e4m3 subnormals land on f32 subnormals).  The caller undoes the 2^-120:
-// 2^64 on the vector it multiplies, 2^56 on the sum.
-__device__ __forceinline__ float2 e4m3x2_scaled(unsigned w) {  // bytes 0 and 1 of w
-  return make_float2(__uint_as_float(((w << 24) & 0x80000000u) | ((w << 20) & 0x07f00000u)),
-                     __uint_as_float(((w << 16) & 0x80000000u) | ((w << 12) & 0x07f00000u)));
-}
-
 template <>
 struct Chunk<EL_FP8> {
   static constexpr int C = 8;
-  __device__ __forceinline__ static void unpack_scaled(const uint4& u, float2 (&g)[C]) {
-    const unsigned w[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      g[2 * k] = e4m3x2_scaled(w[k]);
-      g[2 * k + 1] = e4m3x2_scaled(w[k] >> 16);
-    }
-  }
   __device__ __forceinline__ static void unpack(const uint4& u, float2 (&g)[C]) {
     const unsigned w[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
@@ -168,8 +155,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_stream_dot(const StreamArgs a, 
   const int rpp = 32 / lpr;     // rows per warp pass
   const int sub = lane % lpr;   // lane within its row group
   const int grp = lane / lpr;   // row group within the warp
-  float2 xr[T][C];
+  constexpr bool F8 = EL == EL_FP8;
+  float2 xr[F8 ? 1 : T][F8 ? 1 : C];
   float2 xl[DF ? T : 1][DF ? C : 1];  // DF: low-order parts of x_vec
+  // FP8: x_vec times a power of two sx (max |component| into [2, 4)) as FP16
+  // pairs (Re, Re) and (Im, Im) for the packed products, and 1 / sx
+  __half2 xrr[F8 ? T : 1][F8 ? C : 1], xii[F8 ? T : 1][F8 ? C : 1];
+  float x_unscale = 1.f;
   long long vec = -1, vec_end = 0;  // x_vec of rows [vec_end - rows_per_vec, vec_end); rows rise per lane
   for (int k = 0; k < nst; ++k) {
     const int s = k % kStages;
@@ -184,23 +176,53 @@ __global__ void __launch_bounds__(kThreads, 1) k_stream_dot(const StreamArgs a, 
         vec = f / a.rows_per_vec;
         vec_end = (vec + 1) * a.rows_per_vec;
         const float4* xv = reinterpret_cast<const float4*>(a.x + vec * a.x_stride);
+        if constexpr (F8) {
+          // two passes over the lane's slice (cached loads): the largest
+          // magnitude over the row group's whole vector, then the scaled
+          // FP16 pairs; the lanes of one row group take this branch together
+          float amax = 0.f;
 #pragma unroll
-        for (int t = 0; t < T; ++t) {
-          const int c = sub + lpr * t;
+          for (int t = 0; t < T; ++t) {
+            const int c = sub + lpr * t;
 #pragma unroll
-          for (int q = 0; q < C / 2; ++q) {
-            float4 v = (c < nchunk) ? __ldg(xv + c * (C / 2) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
-            if (EL == EL_FP8) {  // 2^64: see e4m3x2_scaled
-              const float k64 = __uint_as_float((127u + 64u) << 23);
-              v = make_float4(v.x * k64, v.y * k64, v.z * k64, v.w * k64);
+            for (int q = 0; q < C / 2; ++q) {
+              const float4 v = (c < nchunk) ? __ldg(xv + c * (C / 2) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+              amax = fmaxf(amax, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
             }
-            xr[t][2 * q] = make_float2(v.x, v.y);
-            xr[t][2 * q + 1] = make_float2(v.z, v.w);
-            if constexpr (DF) {
-              const float4* xvl = reinterpret_cast<const float4*>(a.x_lo + vec * a.x_stride);
-              const float4 w = (c < nchunk) ? __ldg(xvl + c * (C / 2) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
-              xl[t][2 * q] = make_float2(w.x, w.y);
-              xl[t][2 * q + 1] = make_float2(w.z, w.w);
+          }
+          const unsigned gmask = lpr == 32 ? 0xffffffffu : ((1u << lpr) - 1u) << (grp * lpr);  // this row group
+          for (int o = lpr / 2; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(gmask, amax, o));
+          int e = 0;
+          frexpf(amax, &e);  // amax = m 2^e, m in [0.5, 1)
+          const float sx = amax > 0.f ? ldexpf(1.f, 2 - e) : 1.f;
+          x_unscale = amax > 0.f ? ldexpf(1.f, e - 2) : 1.f;
+#pragma unroll
+          for (int t = 0; t < T; ++t) {
+            const int c = sub + lpr * t;
+#pragma unroll
+            for (int q = 0; q < C / 2; ++q) {
+              const float4 v = (c < nchunk) ? __ldg(xv + c * (C / 2) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+              xrr[t][2 * q] = __float2half2_rn(v.x * sx);
+              xii[t][2 * q] = __float2half2_rn(v.y * sx);
+              xrr[t][2 * q + 1] = __float2half2_rn(v.z * sx);
+              xii[t][2 * q + 1] = __float2half2_rn(v.w * sx);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int t = 0; t < T; ++t) {
+            const int c = sub + lpr * t;
+#pragma unroll
+            for (int q = 0; q < C / 2; ++q) {
+              const float4 v = (c < nchunk) ? __ldg(xv + c * (C / 2) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+              xr[t][2 * q] = make_float2(v.x, v.y);
+              xr[t][2 * q + 1] = make_float2(v.z, v.w);
+              if constexpr (DF) {
+                const float4* xvl = reinterpret_cast<const float4*>(a.x_lo + vec * a.x_stride);
+                const float4 w = (c < nchunk) ? __ldg(xvl + c * (C / 2) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+                xl[t][2 * q] = make_float2(w.x, w.y);
+                xl[t][2 * q + 1] = make_float2(w.z, w.w);
+              }
             }
           }
         }
@@ -242,18 +264,58 @@ __global__ void __launch_bounds__(kThreads, 1) k_stream_dot(const StreamArgs a, 
           a.y[f] = make_float2(yr.hi, yi.hi);
           a.y_lo[f] = make_float2(yr.lo, yi.lo);
         }
-        continue;
-      }
+      } else if constexpr (F8) {
+        // e4m3 pairs (Re, Im) widen exactly to FP16 pairs (one cvt per
+        // complex entry); g * (xr, xr) and g * (xi, xi) accumulate as FP16
+        // pairs over two chunks (8 products per accumulator: |g| <= 448,
+        // |x sx| < 4, so |sum| < 2^14, inside the FP16 range), then into
+        // FP32; two accumulator pairs keep the FMA chains independent
+        float ar = 0.f, ai = 0.f;
+        __half2 ha[2], hb[2];
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+          if ((t & 1) == 0) ha[0] = ha[1] = hb[0] = hb[1] = __float2half2_rn(0.f);
+          const int c = sub + lpr * t;
+          if (valid && c < nchunk) {
+            const uint4 u = row[c];
+            const unsigned w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                const __half2_raw gr = __nv_cvt_fp8x2_to_halfraw2(
+                    static_cast<__nv_fp8x2_storage_t>((w[k] >> (16 * h)) & 0xffffu), __NV_E4M3);
+                const __half2 g = *reinterpret_cast<const __half2*>(&gr);
+                ha[h] = __hfma2(g, xrr[t][2 * k + h], ha[h]);  // (gr xr, gi xr)
+                hb[h] = __hfma2(g, xii[t][2 * k + h], hb[h]);  // (gr xi, gi xi)
+              }
+            }
+          }
+          if ((t & 1) == 1 || t == T - 1) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const float2 fa = __half22float2(ha[h]), fb = __half22float2(hb[h]);
+              ar += fa.x - fb.y;
+              ai += fb.x + fa.y;
+            }
+          }
+        }
+        for (int o = lpr / 2; o > 0; o >>= 1) {
+          ar += __shfl_xor_sync(0xffffffffu, ar, o);
+          ai += __shfl_xor_sync(0xffffffffu, ai, o);
+        }
+        if (valid && sub == 0) {
+          const float sc = a.scale[vec * a.nblk + (f - (vec_end - a.rows_per_vec)) / 256] * x_unscale;
+          a.y[f] = make_float2(ar * sc, ai * sc);
+        }
+      } else {
       float ar0 = 0.f, ai0 = 0.f, ar1 = 0.f, ai1 = 0.f;
 #pragma unroll
       for (int t = 0; t < T; ++t) {
         const int c = sub + lpr * t;
         if (valid && c < nchunk) {
           float2 g[C];
-          if constexpr (EL == EL_FP8)
-            CH::unpack_scaled(row[c], g);
-          else
-            CH::unpack(row[c], g);
+          CH::unpack(row[c], g);
           if (HILO) {
             float2 gl[C];
             CH::unpack(row_lo[c], gl);
@@ -278,14 +340,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_stream_dot(const StreamArgs a, 
         ar += __shfl_xor_sync(0xffffffffu, ar, o);
         ai += __shfl_xor_sync(0xffffffffu, ai, o);
       }
-      if (valid && sub == 0) {
-        if (EL == EL_FP8) {
-          const float sc = a.scale[vec * a.nblk + (f - (vec_end - a.rows_per_vec)) / 256] *
-                           __uint_as_float((127u + 56u) << 23);  // 2^56: see e4m3x2_scaled
-          ar *= sc;
-          ai *= sc;
-        }
-        a.y[f] = make_float2(ar, ai);
+      if (valid && sub == 0) a.y[f] = make_float2(ar, ai);
       }
     }
     __syncwarp();

@@ -1,0 +1,84 @@
+"""Full-size parity: the paper-shaped workloads at the sizes and launch
+configurations bench.py times, against the FP64 oracle's waveforms for
+sampled ruptures (every No x Nt sample of each), stored by
+tests/golden/make_full_size_oracle.py (which calls only oracle/ and synth/).
+
+  plain    963 x 20,000 x 64 x 256, one rupture per call, all 8 ruptures of
+           the bench's input pool: FP32 spectra (complex64, ~40 GB) and FP32
+           pairs, each rupture within 1e-5 plain relative L2.
+  batched  963 x 60,000 x 64 x 256, 256 ruptures with uneven durations in one
+           call, BF16 spectra on the tensor engine, and the hi/lo split;
+           16 sampled ruptures.
+  largest  963 x 150,000 x 64 x 256, 1,024 ruptures in one call, FP8 e4m3 Ghat
+           with per-(bin, 256-row) scales and BF16 Phat; 16 sampled ruptures.
+Reduced-precision paths are held to their bar (helpers.BARS) as a plain
+relative L2 error, which is stricter than the window-relative bar.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from helpers import BARS
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2608_21763_gb300 as s2w  # noqa: E402
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def golden(name):
+    p = os.path.join(GOLDEN, f"oracle_{name}.npz")
+    if not os.path.exists(p):
+        pytest.skip(f"no stored oracle waveforms for {name}")
+    d = np.load(p)
+    return d["q"], [int(i) for i in d["index"]], [int(x) for x in d["draw"]], d["checksum"]
+
+
+def run(name, prec_g, prec_p, chunk=2048, **opts):
+    """Waveforms of batch 0 of the bench's draw, and the stored reference."""
+    q_ref, idx, (B, pool), checksum = golden(name)
+    wl = synth.WORKLOADS[name]
+    geom = wl.geometry_obj()
+    slip = wl.slip(geom, B=pool * B).astype(np.float32)[:B]
+    s = slip[idx].astype(np.float64)
+    mine = np.stack([np.abs(s).sum(axis=(-2, -1)), (s * s).sum(axis=(-2, -1))], axis=-1)
+    assert np.allclose(mine, checksum, rtol=1e-9, atol=0.0), "the draw differs from the stored oracle's"
+    ctx = s2w.Context(wl.Ns, wl.Ng, wl.No, wl.Nt, prec_g=prec_g, prec_p=prec_p, max_batch=B, **opts)
+    for g0 in range(0, wl.Ng, chunk):
+        g1 = min(wl.Ng, g0 + chunk)
+        ctx.load_greens(g0, geom.greens_rows(g0, g1, wl.Nt, np.float32))
+        ctx.load_adjoint(g0, geom.adjoint_cols(g0, g1, wl.Nt, np.float32))
+    x = torch.tensor(slip, device="cuda")
+    q = ctx.waveforms(x).cpu().numpy()
+    ctx.sync()
+    ctx.close()
+    del x
+    torch.cuda.empty_cache()
+    q = q[idx].astype(np.float64)
+    err = np.linalg.norm((q - q_ref).reshape(len(idx), -1), axis=1)
+    rel = err / np.linalg.norm(q_ref.reshape(len(idx), -1), axis=1)
+    print(f"{name} {prec_g}/{prec_p}: rel-L2 max {rel.max():.3g} median {np.median(rel):.3g} over "
+          f"{len(idx)} ruptures x {q_ref.shape[1]} observations: {rel}")
+    return rel
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp32_hilo"])
+def test_plain_workload_every_rupture(prec):
+    rel = run("plain", prec, prec)
+    assert np.all(rel <= 1e-5), rel
+
+
+@pytest.mark.parametrize("prec_g,prec_p,bar", [("bf16", "bf16", "tensor_bf16"),
+                                               ("bf16_hilo", "fp32", "tensor_split")])
+def test_batched_workload_tensor_engine(prec_g, prec_p, bar):
+    rel = run("batched", prec_g, prec_p, engine="tensor")
+    assert np.all(rel <= BARS[bar]), rel
+
+
+def test_largest_workload_fp8():
+    rel = run("largest", "fp8", "bf16", chunk=4096, engine="tensor")
+    assert np.all(rel <= BARS["tensor_fp8"]), rel
