@@ -33,7 +33,7 @@ namespace s2w {
 
 namespace {
 
-constexpr int kConsumerWarps = 8;
+constexpr int kConsumerWarps = 8;  // the transposed kernel; k_stream_dot takes stream_warps(EL)
 constexpr int kStages = 3;
 constexpr int kThreads = 32 * (kConsumerWarps + 1);
 constexpr int kMaxRowLen = 1024;
@@ -88,8 +88,15 @@ struct Chunk<EL_FP8> {
 // EL selects the unpacker (EL_BF16 also serves the hi/lo pair when HILO);
 // SHORT: rows of at most 64 chunks, shared by lane groups; DF (with EL_FP32
 // and HILO): FP32 pair rows and vectors, double-float sums.
+// Consumer warps of k_stream_dot: FP8 rows carry half the bytes of BF16 ones,
+// so each warp spends more of its time on per-row work (the lane reduction,
+// the scale, the vector reload); twelve warps keep more rows in flight
+// (their registers, ~120 each, still fit one CTA per SM without spills).
+__host__ __device__ constexpr int stream_warps(int el) { return el == EL_FP8 ? 12 : 8; }
+
 template <int EL, bool HILO, bool SHORT, bool DF = false>
-__global__ void __launch_bounds__(kThreads, 1) k_stream_dot(const StreamArgs a, int stage_rows) {
+__global__ void __launch_bounds__(32 * (stream_warps(EL) + 1), 1) k_stream_dot(const StreamArgs a, int stage_rows) {
+  constexpr int kConsumerWarps = stream_warps(EL);
   static_assert(!DF || (EL == EL_FP32 && HILO), "pair rows: FP32 hi and lo arrays");
   using CH = Chunk<EL>;
   constexpr int C = CH::C;
@@ -526,7 +533,7 @@ cudaError_t launch_t(const StreamArgs& a, int num_sms, cudaStream_t st) {
   const int row_bytes = a.row_len * (16 / C);
   const int budget = HILO ? 32 * 1024 : 64 * 1024;
   int stage_rows = budget / row_bytes;
-  if (stage_rows >= kConsumerWarps) stage_rows -= stage_rows % kConsumerWarps;
+  if (stage_rows >= 8) stage_rows -= stage_rows % 8;
   if (stage_rows < 1) stage_rows = 1;
   const size_t smem = 128 + static_cast<size_t>(kStages) * stage_rows * row_bytes * (HILO ? 2 : 1);
   cudaError_t e = cudaFuncSetAttribute(k_stream_dot<EL, HILO, SHORT, DF>,
@@ -535,7 +542,8 @@ cudaError_t launch_t(const StreamArgs& a, int num_sms, cudaStream_t st) {
   long long grid = num_sms;
   if (grid > a.F) grid = a.F;
   if (grid < 1) grid = 1;
-  k_stream_dot<EL, HILO, SHORT, DF><<<static_cast<unsigned>(grid), kThreads, smem, st>>>(a, stage_rows);
+  k_stream_dot<EL, HILO, SHORT, DF><<<static_cast<unsigned>(grid), 32 * (stream_warps(EL) + 1), smem, st>>>(
+      a, stage_rows);
   return cudaGetLastError();
 }
 
