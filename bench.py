@@ -110,6 +110,8 @@ class ClockSampler:
         self.out = os.path.join("/tmp", f"s2w_clocks_{os.getpid()}.csv")
 
     def start(self):
+        """Start sampling and wait (up to 10 s) for the first sample, so that
+        nvidia-smi's start-up does not fall inside the timed region."""
         try:
             self.f = open(self.out, "w")
             self.proc = subprocess.Popen(
@@ -117,6 +119,12 @@ class ClockSampler:
                  "-lms", "200", "-i", str(self.gpu_index)], stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        t0 = time.time()
+        while time.time() - t0 < 10.0 and self.proc.poll() is None:
+            if os.path.getsize(self.out) > 0:
+                break
+            time.sleep(0.02)
 
     def stop(self):
         if self.proc is None:
@@ -184,10 +192,11 @@ def stage1_algorithmic_bytes(wl, prec_g, B, single_pass=False):
 
 
 def measured_traffic(wl, prec_g, tensor=False, bsub=256):
-    """DRAM bytes of one stage-1 launch from the committed ncu capture
-    (profiles/traffic.json: bytes per grid row of a smaller case of the same
-    kernel, scaled here by the grid rows), for the stream kernel (one
-    rupture) or the tensor GEMM (one sub-batch of 256 ruptures); None when
+    """DRAM bytes of one stage-1 launch from the committed ncu captures
+    (profiles/traffic.json: bytes per grid row, and a constant part, fitted
+    to captures of smaller cases of the same kernel, evaluated here at the
+    workload's grid), for the stream kernel (one rupture) or the tensor GEMM
+    (one sub-batch of 256 ruptures); None when
     the kernel's source changed since the capture or no capture exists for
     this storage precision and shape."""
     import hashlib
@@ -205,7 +214,8 @@ def measured_traffic(wl, prec_g, tensor=False, bsub=256):
     per_row = d.get(key_rows, {}).get(prec_g)
     if sha != d.get(key_sha) or per_row is None or wl.Ns != 963 or wl.Nt != 256 or (tensor and bsub != 256):
         return None
-    return int(per_row * wl.Ng)
+    const = d.get("tc_stage1_bytes_const" if tensor else "stage1_bytes_const", {}).get(prec_g, 0)
+    return int(per_row * wl.Ng + const)
 
 
 # ------------------------------------------------------------------ oracle legs

@@ -19,8 +19,9 @@
 // accumulate in FP32; FP8 rows are widened exactly to FP16 pairs (one
 // conversion per complex entry) and multiplied by the vector held as FP16
 // pairs scaled by a power of two (its largest magnitude into [2, 4)), with
-// packed FP16 multiply-adds over 16-byte chunks of 8 entries flushed into FP32
-// every two chunks, so that a streamed byte costs about two instructions;
+// packed FP16 multiply-adds (eight independent accumulators per lane, each
+// summing at most 8 products) flushed into FP32 at the end of the row, so
+// that a streamed byte costs about two instructions;
 // the per-(bin, 256-row block) scale and the power of two are undone after
 // the dot product.  FP32_HILO rows (hi and lo FP32 arrays) meet
 // a vector of pairs (x, x_lo): each product is formed exactly (TwoProduct)
@@ -274,14 +275,16 @@ __global__ void __launch_bounds__(32 * (stream_warps(EL) + 1), 1) k_stream_dot(c
       } else if constexpr (F8) {
         // e4m3 pairs (Re, Im) widen exactly to FP16 pairs (one cvt per
         // complex entry); g * (xr, xr) and g * (xi, xi) accumulate as FP16
-        // pairs over two chunks (8 products per accumulator: |g| <= 448,
-        // |x sx| < 4, so |sum| < 2^14, inside the FP16 range), then into
-        // FP32; two accumulator pairs keep the FMA chains independent
+        // pairs over the lane's T = 4 chunks of the row (eight independent
+        // accumulator chains of 8 products each: |g| <= 448, |x sx| < 4, so
+        // |sum| < 2^14, inside the FP16 range), then into FP32
+        static_assert(!F8 || T <= 4, "FP16 accumulation bound: at most 8 products per accumulator");
         float ar = 0.f, ai = 0.f;
-        __half2 ha[2], hb[2];
+        __half2 ha[4], hb[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) ha[k] = hb[k] = __float2half2_rn(0.f);
 #pragma unroll
         for (int t = 0; t < T; ++t) {
-          if ((t & 1) == 0) ha[0] = ha[1] = hb[0] = hb[1] = __float2half2_rn(0.f);
           const int c = sub + lpr * t;
           if (valid && c < nchunk) {
             const uint4 u = row[c];
@@ -293,19 +296,17 @@ __global__ void __launch_bounds__(32 * (stream_warps(EL) + 1), 1) k_stream_dot(c
                 const __half2_raw gr = __nv_cvt_fp8x2_to_halfraw2(
                     static_cast<__nv_fp8x2_storage_t>((w[k] >> (16 * h)) & 0xffffu), __NV_E4M3);
                 const __half2 g = *reinterpret_cast<const __half2*>(&gr);
-                ha[h] = __hfma2(g, xrr[t][2 * k + h], ha[h]);  // (gr xr, gi xr)
-                hb[h] = __hfma2(g, xii[t][2 * k + h], hb[h]);  // (gr xi, gi xi)
+                ha[k] = __hfma2(g, xrr[t][2 * k + h], ha[k]);  // (gr xr, gi xr)
+                hb[k] = __hfma2(g, xii[t][2 * k + h], hb[k]);  // (gr xi, gi xi)
               }
             }
           }
-          if ((t & 1) == 1 || t == T - 1) {
+        }
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const float2 fa = __half22float2(ha[h]), fb = __half22float2(hb[h]);
-              ar += fa.x - fb.y;
-              ai += fb.x + fa.y;
-            }
-          }
+        for (int k = 0; k < 4; ++k) {
+          const float2 fa = __half22float2(ha[k]), fb = __half22float2(hb[k]);
+          ar += fa.x - fb.y;
+          ai += fb.x + fa.y;
         }
         for (int o = lpr / 2; o > 0; o >>= 1) {
           ar += __shfl_xor_sync(0xffffffffu, ar, o);
