@@ -19,9 +19,10 @@
 // accumulate in FP32; FP8 rows are widened exactly to FP16 pairs (one
 // conversion per complex entry) and multiplied by the vector held as FP16
 // pairs scaled by a power of two (its largest magnitude into [2, 4)), with
-// packed FP16 multiply-adds (eight independent accumulators per lane, each
-// summing at most 8 products) flushed into FP32 at the end of the row, so
-// that a streamed byte costs about two instructions;
+// packed FP16 multiply-adds (independent accumulators per lane, each summing
+// at most 8 products) flushed into FP32 at the end of the row, so that a
+// streamed byte costs about two instructions; long FP8 rows go four per warp
+// pass with one butterfly reduction over the lanes for the four;
 // the per-(bin, 256-row block) scale and the power of two are undone after
 // the dot product.  FP32_HILO rows (hi and lo FP32 arrays) meet
 // a vector of pairs (x, x_lo): each product is formed exactly (TwoProduct)
@@ -89,15 +90,18 @@ struct Chunk<EL_FP8> {
 // EL selects the unpacker (EL_BF16 also serves the hi/lo pair when HILO);
 // SHORT: rows of at most 64 chunks, shared by lane groups; DF (with EL_FP32
 // and HILO): FP32 pair rows and vectors, double-float sums.
-// Consumer warps of k_stream_dot: FP8 rows carry half the bytes of BF16 ones,
-// so each warp spends more of its time on per-row work (the lane reduction,
-// the scale, the vector reload); twelve warps keep more rows in flight
-// (their registers, ~120 each, still fit one CTA per SM without spills).
-__host__ __device__ constexpr int stream_warps(int el) { return el == EL_FP8 ? 12 : 8; }
+// Consumer warps of k_stream_dot.  FP8 rows carry half the bytes of BF16
+// ones, so per-row work (the lane reduction, the scale) weighs more: long FP8
+// rows are taken four per warp pass (one reduction for the four), short ones
+// by twelve warps (more rows in flight; ~120 registers each, no spills).
+__host__ __device__ constexpr int stream_warps(int el, bool short_rows) {
+  return (el == EL_FP8 && short_rows) ? 12 : 8;
+}
 
 template <int EL, bool HILO, bool SHORT, bool DF = false>
-__global__ void __launch_bounds__(32 * (stream_warps(EL) + 1), 1) k_stream_dot(const StreamArgs a, int stage_rows) {
-  constexpr int kConsumerWarps = stream_warps(EL);
+__global__ void __launch_bounds__(32 * (stream_warps(EL, SHORT) + 1), 1)
+    k_stream_dot(const StreamArgs a, int stage_rows) {
+  constexpr int kConsumerWarps = stream_warps(EL, SHORT);
   static_assert(!DF || (EL == EL_FP32 && HILO), "pair rows: FP32 hi and lo arrays");
   using CH = Chunk<EL>;
   constexpr int C = CH::C;
@@ -171,6 +175,133 @@ __global__ void __launch_bounds__(32 * (stream_warps(EL) + 1), 1) k_stream_dot(c
   __half2 xrr[F8 ? T : 1][F8 ? C : 1], xii[F8 ? T : 1][F8 ? C : 1];
   float x_unscale = 1.f;
   long long vec = -1, vec_end = 0;  // x_vec of rows [vec_end - rows_per_vec, vec_end); rows rise per lane
+  if constexpr (F8 && !SHORT) {
+    // Long FP8 rows, four per warp pass, all 32 lanes on each: the lane's
+    // products of the four rows accumulate side by side (sixteen FP16 pair
+    // chains per kind), then one butterfly reduce-scatter over the lanes sums
+    // the 8 values (Re and Im of four rows) with 9 shuffles instead of 40;
+    // lanes 4v hold value v.  Rows of a pass that fall into the next bin are
+    // taken in a second round after the vector reload.
+    for (int k = 0; k < nst; ++k) {
+      const int s = k % kStages;
+      if (!mbar_wait_bounded(full + s, (k / kStages) & 1, a.status, DEV_ERR_TIMEOUT_FULL, wlim)) return;
+      const long long rs = r0 + static_cast<long long>(k) * stage_rows;
+      const int nr = static_cast<int>(min(static_cast<long long>(stage_rows), r1 - rs));
+      for (int base = warp * 4; base < nr; base += kConsumerWarps * 4) {
+        int j = 0;
+        while (j < 4 && base + j < nr) {
+          if (rs + base + j >= vec_end) {  // warp-uniform: every lane works on the same rows
+            vec = (rs + base + j) / a.rows_per_vec;
+            vec_end = (vec + 1) * a.rows_per_vec;
+            const float4* xv = reinterpret_cast<const float4*>(a.x + vec * a.x_stride);
+            float amax = 0.f;
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+              const int c = lane + 32 * t;
+#pragma unroll
+              for (int q = 0; q < C / 2; ++q) {
+                const float4 v = (c < nchunk) ? __ldg(xv + c * (C / 2) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+                amax = fmaxf(amax, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+              }
+            }
+            for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+            int e = 0;
+            frexpf(amax, &e);  // amax = m 2^e, m in [0.5, 1)
+            const float sx = amax > 0.f ? ldexpf(1.f, 2 - e) : 1.f;
+            x_unscale = amax > 0.f ? ldexpf(1.f, e - 2) : 1.f;
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+              const int c = lane + 32 * t;
+#pragma unroll
+              for (int q = 0; q < C / 2; ++q) {
+                const float4 v = (c < nchunk) ? __ldg(xv + c * (C / 2) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+                xrr[t][2 * q] = __float2half2_rn(v.x * sx);
+                xii[t][2 * q] = __float2half2_rn(v.y * sx);
+                xrr[t][2 * q + 1] = __float2half2_rn(v.z * sx);
+                xii[t][2 * q + 1] = __float2half2_rn(v.w * sx);
+              }
+            }
+          }
+          int je = j + 1;  // rows j .. je-1 of the pass share this bin's vector
+          while (je < 4 && base + je < nr && rs + base + je < vec_end) ++je;
+          __half2 ha[4][4], hb[4][4];
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) ha[r][q] = hb[r][q] = __float2half2_rn(0.f);
+#pragma unroll
+          for (int t = 0; t < T; ++t) {
+            const int c = lane + 32 * t;
+            if (c < nchunk) {
+#pragma unroll
+              for (int r = 0; r < 4; ++r) {
+                if (r >= j && r < je) {
+                  const uint4 u = reinterpret_cast<const uint4*>(buf + s * stage_bytes + (base + r) * row_bytes)[c];
+                  const unsigned w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                  for (int q = 0; q < 4; ++q) {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                      const __half2_raw gr = __nv_cvt_fp8x2_to_halfraw2(
+                          static_cast<__nv_fp8x2_storage_t>((w[q] >> (16 * h)) & 0xffffu), __NV_E4M3);
+                      const __half2 g = *reinterpret_cast<const __half2*>(&gr);
+                      ha[r][q] = __hfma2(g, xrr[t][2 * q + h], ha[r][q]);  // (gr xr, gi xr)
+                      hb[r][q] = __hfma2(g, xii[t][2 * q + h], hb[r][q]);  // (gr xi, gi xi)
+                    }
+                  }
+                }
+              }
+            }
+          }
+          float v[8];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            float ar = 0.f, ai = 0.f;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const float2 fa = __half22float2(ha[r][q]), fb = __half22float2(hb[r][q]);
+              ar += fa.x - fb.y;
+              ai += fb.x + fa.y;
+            }
+            v[2 * r] = ar;
+            v[2 * r + 1] = ai;
+          }
+          // reduce-scatter: after the step with lane bit b, the lane keeps the
+          // half of its values selected by that bit, summed with its partner's
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const bool up = lane & 16;
+            const float keep = up ? v[i + 4] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, up ? v[i] : v[i + 4], 16);
+          }
+#pragma unroll
+          for (int i = 0; i < 2; ++i) {
+            const bool up = lane & 8;
+            const float keep = up ? v[i + 2] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, up ? v[i] : v[i + 2], 8);
+          }
+          {
+            const bool up = lane & 4;
+            const float keep = up ? v[1] : v[0];
+            v[0] = keep + __shfl_xor_sync(0xffffffffu, up ? v[0] : v[1], 4);
+          }
+          v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
+          v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+          const int idx = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+          const int r = idx >> 1;
+          if ((lane & 3) == 0 && r >= j && r < je) {
+            const long long f = rs + base + r;
+            const float sc = a.scale[vec * a.nblk + (f - (vec_end - a.rows_per_vec)) / 256] * x_unscale;
+            reinterpret_cast<float*>(a.y + f)[idx & 1] = v[0] * sc;
+          }
+          j = je;
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(empty + s);
+    }
+    return;
+  }
   for (int k = 0; k < nst; ++k) {
     const int s = k % kStages;
     if (!mbar_wait_bounded(full + s, (k / kStages) & 1, a.status, DEV_ERR_TIMEOUT_FULL, wlim)) return;
@@ -543,7 +674,7 @@ cudaError_t launch_t(const StreamArgs& a, int num_sms, cudaStream_t st) {
   long long grid = num_sms;
   if (grid > a.F) grid = a.F;
   if (grid < 1) grid = 1;
-  k_stream_dot<EL, HILO, SHORT, DF><<<static_cast<unsigned>(grid), 32 * (stream_warps(EL) + 1), smem, st>>>(
+  k_stream_dot<EL, HILO, SHORT, DF><<<static_cast<unsigned>(grid), 32 * (stream_warps(EL, SHORT) + 1), smem, st>>>(
       a, stage_rows);
   return cudaGetLastError();
 }
