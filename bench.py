@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--fp8-act", action="store_true",
                     help="FP8 operator on the tensor engine: round the slip spectra to e4m3 too "
                          "(FP8 x FP8 stage-1 MMAs)")
+    ap.add_argument("--fp8-act-hilo", action="store_true",
+                    help="FP8 operator on the tensor engine: slip spectra as hi + lo e4m3 parts "
+                         "(two FP8 x FP8 MMAs per K step, FP16-class activation accuracy)")
     ap.add_argument("--mode", default="waveforms", choices=["waveforms", "gradient"],
                     help="gradient: one step = misfit gradients of the batch (forward + adjoint)")
     ap.add_argument("--batch", type=int, default=None, help="ruptures per step (default: the workload's)")
@@ -159,11 +162,12 @@ class ClockSampler:
 def tensor_dtype(args):
     """Arithmetic type of the tensor engine's stage-1 MMAs: BF16, three BF16
     MMAs per product (hi/lo split), FP16 (FP8 operator widened, FP16
-    activations) or e4m3 x e4m3 (FP8 activations); FP32 accumulation in all."""
+    activations), e4m3 x e4m3 (FP8 activations), or two e4m3 MMAs per product
+    (activations as hi + lo e4m3 parts); FP32 accumulation in all."""
     if args.prec_g == "bf16_hilo":
         return "bf16x3"
     if args.prec_g == "fp8":
-        return "e4m3" if args.fp8_act else "f16"
+        return "e4m3x2" if args.fp8_act_hilo else ("e4m3" if args.fp8_act else "f16")
     return "bf16"
 
 
@@ -364,7 +368,7 @@ def run_ours(args, rank, world, local_rank):
     tc_adj = args.mode == "gradient" and args.prec_g in ("bf16", "bf16_hilo") and args.engine != "stream"
     ctx = load_context(s2w, wl, geom, args.prec_g, args.prec_p, B, local_rank, args.engine,
                        tc_adjoint=tc_adj, single_pass=args.single_pass,
-                       tc_pair=args.tc_pair, tc_fp8_act=args.fp8_act)
+                       tc_pair=args.tc_pair, tc_fp8_act=2 if args.fp8_act_hilo else int(args.fp8_act))
     setup_s = time.perf_counter() - t_setup
     slip_d = torch.tensor(slip_np, device=dev)
     q_d = torch.empty((pool, B, wl.No, wl.Nt), dtype=torch.float32, device=dev)
@@ -496,12 +500,14 @@ def run_ours(args, rank, world, local_rank):
         split = args.prec_g == "bf16_hilo"
         bsub = min(B, tuning["tc_bsub"] if tuning else (128 if split else 256))
         flops = 8.0 * (wl.Nt + 1) * wl.Ng * wl.Ns * bsub
-        terms = 3 if split else 1
+        f8f8 = (args.fp8_act or args.fp8_act_hilo) and args.prec_g == "fp8"
+        terms = 3 if split else (2 if f8f8 and args.fp8_act_hilo else 1)
         achieved = terms * flops / per_launch_s / 1e12
-        f8f8 = args.fp8_act and args.prec_g == "fp8"
         # FP8 x FP8 MMAs: the measured BF16 peak times the nominal fp8 / bf16 ratio (4.5 / 2.25)
         peak = pk["bf16_tflops_sustained"] * (2.0 if f8f8 else 1.0)
-        kname = ("k_tc_gemm2_f8f8 (stage-1 per-bin GEMM, tcgen05 kind::f8f6f4)" if f8f8
+        kname = ("k_tc_gemm2_f8f8lo (stage-1 per-bin GEMM, two tcgen05 kind::f8f6f4 MMAs per K step)"
+                 if f8f8 and args.fp8_act_hilo else
+                 "k_tc_gemm2_f8f8 (stage-1 per-bin GEMM, tcgen05 kind::f8f6f4)" if f8f8
                  else "k_tc_gemm / k_tc_gemm2 (stage-1 per-bin GEMM, tcgen05 kind::f16)")
         roof = {"kernel": kname, "bound": "tensor",
                 "achieved": round(achieved, 1), "peak": peak, "unit": "TFLOP/s",
@@ -533,7 +539,8 @@ def run_ours(args, rank, world, local_rank):
            "data": "synthetic",
            "config": workload_config(wl, B, args),
            "engine": {"engine": "tensor" if tensor else "stream", "tc_pair": args.tc_pair,
-                      "fp8_activations": bool(args.fp8_act), "autotune": tuning, "cuda_graph": use_graph,
+                      "fp8_activations": "e4m3 hi + lo" if args.fp8_act_hilo else bool(args.fp8_act),
+                      "autotune": tuning, "cuda_graph": use_graph,
                       "single_pass": bool(args.single_pass), "parallelism": f"replicas{world}",
                       "l2": "inputs larger than L2 (every step streams the full operator spectra)",
                       "operator_gb": round(sum(ctx.operator_bytes()) / 1e9, 2), "setup_s": round(setup_s, 1)},

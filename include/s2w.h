@@ -140,16 +140,23 @@ typedef struct {
                       keeps one CTA per 128-row tile; S2W_PAIR_AUTO (0,
                       default) takes the two-SM form for the 512-column
                       GEMMs of BF16 operators (256-rupture sub-batches). */
-  int tc_fp8_act;  /* 1 (prec_g = FP8_E4M3 only): the tensor engine also rounds
-                      the slip spectra, stage 1's B operand, to e4m3 with one
-                      power-of-two scale per (bin, rupture) (amax to <= 448),
-                      and runs stage 1 as FP8 x FP8 MMAs (tcgen05
+  int tc_fp8_act;  /* prec_g = FP8_E4M3 only.  1: the tensor engine also
+                      rounds the slip spectra, stage 1's B operand, to e4m3
+                      with one power-of-two scale per (bin, rupture) (amax to
+                      <= 448), and runs stage 1 as FP8 x FP8 MMAs (tcgen05
                       kind::f8f6f4, two-SM tiles): twice the BF16 MMA rate
                       and no widening of the operator, at the cost of the
                       activation rounding (<= 2^-4 relative per entry) on
-                      top of the operator's.  Used for sub-batches whose grid
-                      spans at least two 128-row tiles; others take the
-                      FP16-activation path.  0 (default): FP16 activations. */
+                      top of the operator's.  2: the same with the slip
+                      spectra as hi + lo e4m3 parts in that frame (lo = the
+                      rounded remainder), two FP8 x FP8 MMAs per K step:
+                      activations kept to ~2^-8, the FP16 path's accuracy
+                      for these contractions, with both operands read as
+                      bytes straight from TMA.  Used for sub-batches whose
+                      grid spans at least two 128-row tiles; others take the
+                      FP16-activation path.  0 (default): the operator
+                      tiles widened exactly to FP16 in shared memory, FP16
+                      activations. */
   int tc_bsub;     /* tensor engine: ruptures per GEMM pass (the sub-batch),
                       128 or 256 (BF16_HILO: 128); 0 (default) = 256, or 128
                       for BF16_HILO, capped by max_batch.  The workspaces are

@@ -183,7 +183,7 @@ class Context:
         o.tc_adjoint = int(bool(tc_adjoint))
         o.single_pass = int(bool(single_pass))
         o.tc_pair = PAIR[tc_pair]
-        o.tc_fp8_act = int(bool(tc_fp8_act))
+        o.tc_fp8_act = int(tc_fp8_act)  # False / True / 2 (hi + lo e4m3 activations)
         o.tc_bsub = int(tc_bsub)
         o.tc_s2_chunks = int(tc_s2_chunks)
         cache = None if tune_cache is None else os.fsencode(tune_cache)

@@ -28,6 +28,8 @@
 // a vector of pairs (x, x_lo): each product is formed exactly (TwoProduct)
 // and summed by TwoSum into double-float accumulators (df.cuh), written as
 // pairs (y, y_lo).
+#include <type_traits>
+
 #include "df.cuh"
 #include "s2w_internal.cuh"
 
@@ -68,6 +70,20 @@ struct Chunk<EL_BF16> {
     g[3] = bf2_to_f2(u.w);
   }
 };
+
+// Two e4m3 values (bytes 0, 1 of a 16-bit word) widened exactly to an FP16
+// pair, and a 32-bit word's two such pairs.
+__device__ __forceinline__ __half2 e4m3x2_to_h2(unsigned short v) {
+  unsigned r;
+  asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(r) : "h"(v));
+  return *reinterpret_cast<const __half2*>(&r);
+}
+__device__ __forceinline__ void e4m3x4_to_h2(unsigned w, __half2& lo, __half2& hi) {
+  unsigned short l16, h16;
+  asm("mov.b32 {%0, %1}, %2;" : "=h"(l16), "=h"(h16) : "r"(w));
+  lo = e4m3x2_to_h2(l16);
+  hi = e4m3x2_to_h2(h16);
+}
 
 __device__ __forceinline__ float2 fp8x2_to_f2(unsigned short s) {
   const __half2_raw h = __nv_cvt_fp8x2_to_halfraw2(static_cast<__nv_fp8x2_storage_t>(s), __NV_E4M3);
@@ -229,30 +245,38 @@ __global__ void __launch_bounds__(32 * (stream_warps(EL, SHORT) + 1), 1)
           for (int r = 0; r < 4; ++r)
 #pragma unroll
             for (int q = 0; q < 4; ++q) ha[r][q] = hb[r][q] = __float2half2_rn(0.f);
+          // ALL: the four rows share the bin (the usual case): no per-row tests
+          auto accumulate = [&](auto all_tag) {
+            constexpr bool ALL = decltype(all_tag)::value;
 #pragma unroll
-          for (int t = 0; t < T; ++t) {
-            const int c = lane + 32 * t;
-            if (c < nchunk) {
+            for (int t = 0; t < T; ++t) {
+              const int c = lane + 32 * t;
+              if (c < nchunk) {
 #pragma unroll
-              for (int r = 0; r < 4; ++r) {
-                if (r >= j && r < je) {
-                  const uint4 u = reinterpret_cast<const uint4*>(buf + s * stage_bytes + (base + r) * row_bytes)[c];
-                  const unsigned w[4] = {u.x, u.y, u.z, u.w};
+                for (int r = 0; r < 4; ++r) {
+                  if (ALL || (r >= j && r < je)) {
+                    const uint4 u =
+                        reinterpret_cast<const uint4*>(buf + s * stage_bytes + (base + r) * row_bytes)[c];
+                    const unsigned w[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
-                  for (int q = 0; q < 4; ++q) {
+                    for (int q = 0; q < 4; ++q) {
+                      __half2 g[2];
+                      e4m3x4_to_h2(w[q], g[0], g[1]);
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                      const __half2_raw gr = __nv_cvt_fp8x2_to_halfraw2(
-                          static_cast<__nv_fp8x2_storage_t>((w[q] >> (16 * h)) & 0xffffu), __NV_E4M3);
-                      const __half2 g = *reinterpret_cast<const __half2*>(&gr);
-                      ha[r][q] = __hfma2(g, xrr[t][2 * q + h], ha[r][q]);  // (gr xr, gi xr)
-                      hb[r][q] = __hfma2(g, xii[t][2 * q + h], hb[r][q]);  // (gr xi, gi xi)
+                      for (int h = 0; h < 2; ++h) {
+                        ha[r][q] = __hfma2(g[h], xrr[t][2 * q + h], ha[r][q]);  // (gr xr, gi xr)
+                        hb[r][q] = __hfma2(g[h], xii[t][2 * q + h], hb[r][q]);  // (gr xi, gi xi)
+                      }
                     }
                   }
                 }
               }
             }
-          }
+          };
+          if (j == 0 && je == 4)
+            accumulate(std::true_type{});
+          else
+            accumulate(std::false_type{});
           float v[8];
 #pragma unroll
           for (int r = 0; r < 4; ++r) {
@@ -422,13 +446,12 @@ __global__ void __launch_bounds__(32 * (stream_warps(EL, SHORT) + 1), 1)
             const unsigned w[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
+              __half2 g[2];
+              e4m3x4_to_h2(w[k], g[0], g[1]);
 #pragma unroll
               for (int h = 0; h < 2; ++h) {
-                const __half2_raw gr = __nv_cvt_fp8x2_to_halfraw2(
-                    static_cast<__nv_fp8x2_storage_t>((w[k] >> (16 * h)) & 0xffffu), __NV_E4M3);
-                const __half2 g = *reinterpret_cast<const __half2*>(&gr);
-                ha[k] = __hfma2(g, xrr[t][2 * k + h], ha[k]);  // (gr xr, gi xr)
-                hb[k] = __hfma2(g, xii[t][2 * k + h], hb[k]);  // (gr xi, gi xi)
+                ha[k] = __hfma2(g[h], xrr[t][2 * k + h], ha[k]);  // (gr xr, gi xr)
+                hb[k] = __hfma2(g[h], xii[t][2 * k + h], hb[k]);  // (gr xi, gi xi)
               }
             }
           }

@@ -648,7 +648,8 @@ __device__ __forceinline__ void tc_gemm2_body(const CUtensorMap* tmA, const CUte
                                               const float* col_scale = nullptr, int col_ld = 0) {
   constexpr bool SPLIT = MODE == 1;
   constexpr bool F8 = MODE == 2;
-  constexpr bool F8F8 = MODE == 3;
+  constexpr bool F8F8 = MODE == 3 || MODE == 4;
+  constexpr bool BLO = MODE == 4;         // FP8 B as hi + lo e4m3 parts: two MMAs per K step
   constexpr int ES = F8F8 ? 1 : 2;        // operand bytes per element in shared memory
   constexpr int BKB = BK * ES;            // bytes per K-major row of a k-block
   constexpr int KI = F8F8 ? 32 : 16;      // K per MMA instruction (32 bytes either way)
@@ -670,7 +671,7 @@ __device__ __forceinline__ void tc_gemm2_body(const CUtensorMap* tmA, const CUte
   const int hb = hrows * BKB;
   const int bh_bytes = n_mma * hb;
   const int a_bytes = kA * (SPLIT ? 2 : 1);
-  const int b_all = bh_bytes * (SPLIT ? 2 : 1);
+  const int b_all = bh_bytes * ((SPLIT || BLO) ? 2 : 1);
   const int stage_bytes = a_bytes + b_all + kStg;
   const int S = a.stages;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * stage_bytes);
@@ -746,7 +747,7 @@ __device__ __forceinline__ void tc_gemm2_body(const CUtensorMap* tmA, const CUte
           for (int c = 0; c < n_mma; ++c) {
             const int row0 = c * n_mma_cols + static_cast<int>(crank) * hrows;
             tma_load_3d_pair(sb + c * hb, tmB, kb * BK, row0, l, fb);
-            if constexpr (SPLIT) tma_load_3d_pair(sb + bh_bytes + c * hb, tmB2, kb * BK, row0, l, fb);
+            if constexpr (SPLIT || BLO) tma_load_3d_pair(sb + bh_bytes + c * hb, tmB2, kb * BK, row0, l, fb);
           }
         }
       }
@@ -791,6 +792,7 @@ __device__ __forceinline__ void tc_gemm2_body(const CUtensorMap* tmA, const CUte
               const uint32_t dcol = tmem + c * n_mma_cols;
               if constexpr (F8F8) {
                 tc_mma2_f8f8(dcol, ad, bd, idesc, (kb > kb0 || k > 0) ? 1u : 0u);
+                if constexpr (BLO) tc_mma2_f8f8(dcol, ad, sdesc_sw<BKB / 2>(sb + bh_bytes + boff), idesc, 1u);
               } else {
                 tc_mma2_bf16(dcol, ad, bd, idesc, (kb > kb0 || k > 0) ? 1u : 0u);
               }
@@ -887,6 +889,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   tc_gemm2_body<BK, 3>(&tmA, &tmB, nullptr, nullptr, a, col_scale, col_ld);
 }
 
+// FP8 x (hi + lo FP8) MMAs: the slip spectra as two e4m3 parts in one
+// power-of-two frame, so the activations keep ~8 bits (as accurate as FP16
+// for this use) while both MMAs read 8-bit operands straight from TMA.
+template <int BK>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_tc_gemm2_f8f8lo(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                      const __grid_constant__ CUtensorMap tmB2, const TcArgs a, const float* col_scale, int col_ld) {
+  tc_gemm2_body<BK, 4>(&tmA, &tmB, nullptr, &tmB2, a, col_scale, col_ld);
+}
+
 template <int BK>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_tc_gemm2_split(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -961,7 +973,7 @@ __global__ void k_pack_b_f16(const float2* __restrict__ src, int Nb, int T, long
 // launch_pack_b_f8.
 __global__ void k_pack_b_f8(const float2* __restrict__ src, int Nb, int T, long long nc, long long s_l,
                             long long s_t, long long Kc, int N_alloc, int n_rows, float* __restrict__ col_scale,
-                            int col_ld, uint16_t* __restrict__ dst) {
+                            int col_ld, uint16_t* __restrict__ dst, uint16_t* __restrict__ dst_lo) {
   const int lane = threadIdx.x & 31;
   const int nt = n_rows / 2;
   const long long nw = static_cast<long long>(Nb) * nt;
@@ -971,8 +983,12 @@ __global__ void k_pack_b_f8(const float2* __restrict__ src, int Nb, int T, long 
     const int t = static_cast<int>(w % nt);
     uint16_t* r0 = dst + (l * N_alloc + 2 * t) * Kc;  // row 2t: (Re, -Im); row 2t + 1: (Im, Re)
     uint16_t* r1 = r0 + Kc;
+    uint16_t* q0 = dst_lo != nullptr ? dst_lo + (l * N_alloc + 2 * t) * Kc : nullptr;
     if (t >= T) {
-      for (long long c = lane; c < Kc; c += 32) r0[c] = r1[c] = 0;
+      for (long long c = lane; c < Kc; c += 32) {
+        r0[c] = r1[c] = 0;
+        if (q0 != nullptr) q0[c] = q0[Kc + c] = 0;
+      }
       if (lane == 0) col_scale[l * col_ld + t] = 0.f;
       continue;
     }
@@ -992,8 +1008,17 @@ __global__ void k_pack_b_f8(const float2* __restrict__ src, int Nb, int T, long 
     }
     for (long long c = lane; c < Kc; c += 32) {
       const float2 v = c < nc ? x[c] : make_float2(0.f, 0.f);
-      r0[c] = __nv_cvt_float2_to_fp8x2(make_float2(v.x * sc, -v.y * sc), __NV_SATFINITE, __NV_E4M3);
-      r1[c] = __nv_cvt_float2_to_fp8x2(make_float2(v.y * sc, v.x * sc), __NV_SATFINITE, __NV_E4M3);
+      const float2 p0 = make_float2(v.x * sc, -v.y * sc), p1 = make_float2(v.y * sc, v.x * sc);
+      const __nv_fp8x2_storage_t h0 = __nv_cvt_float2_to_fp8x2(p0, __NV_SATFINITE, __NV_E4M3);
+      const __nv_fp8x2_storage_t h1 = __nv_cvt_float2_to_fp8x2(p1, __NV_SATFINITE, __NV_E4M3);
+      r0[c] = h0;
+      r1[c] = h1;
+      if (q0 != nullptr) {  // low-order parts: the rounding remainders, rounded again (same frame)
+        const float2 b0 = __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2(h0, __NV_E4M3)));
+        const float2 b1 = __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2(h1, __NV_E4M3)));
+        q0[c] = __nv_cvt_float2_to_fp8x2(make_float2(p0.x - b0.x, p0.y - b0.y), __NV_SATFINITE, __NV_E4M3);
+        q0[Kc + c] = __nv_cvt_float2_to_fp8x2(make_float2(p1.x - b1.x, p1.y - b1.y), __NV_SATFINITE, __NV_E4M3);
+      }
     }
     if (lane == 0) col_scale[l * col_ld + t] = 1.f / sc;
   }
@@ -1454,7 +1479,8 @@ cudaError_t tc_encode_3d(CUtensorMap* out, const void* base, long long K, long l
 
 cudaError_t tc_encode_3d_u8(CUtensorMap* out, const void* base, long long K, long long rows, long long nbatch,
                             int box_rows, int bk, int sw128) {
-  if (sw128 && bk != 128) return cudaErrorInvalidValue;
+  // sw128 = 1: 128-byte swizzle (bk = 128); 2: 64-byte swizzle (bk = 64)
+  if ((sw128 == 1 && bk != 128) || (sw128 == 2 && bk != 64) || sw128 < 0 || sw128 > 2) return cudaErrorInvalidValue;
   if (g_encode == nullptr && resolve_encode() != cudaSuccess) return cudaErrorNotSupported;
   const cuuint64_t dims[3] = {static_cast<cuuint64_t>(K), static_cast<cuuint64_t>(rows),
                               static_cast<cuuint64_t>(nbatch)};
@@ -1462,7 +1488,9 @@ cudaError_t tc_encode_3d_u8(CUtensorMap* out, const void* base, long long K, lon
   const cuuint32_t box[3] = {static_cast<cuuint32_t>(bk), static_cast<cuuint32_t>(box_rows), 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = g_encode(out, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<void*>(base), dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, sw128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        sw128 == 1 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                   : (sw128 == 2 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_NONE),
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
@@ -1496,9 +1524,11 @@ size_t tc_smem_bytes(int N, int stages, int a_lo, int b_lo, int fp8, int mt) {
 namespace {
 // Two-SM form: per CTA, one A tile and half of the B tile (each part
 // doubled when split), plus the byte staging of an FP8 A tile.
-// fp8 = 2: FP8 A and B read directly (128-byte rows of 128 K elements).
+// fp8 = 2: FP8 A and B read directly (128-byte rows of 128 K elements);
+// fp8 = 3: the same with B as hi + lo parts (64-byte rows of 64 K elements).
 int tc2_stage_bytes(int N, int split, int fp8) {
   if (fp8 == 2) return (kBlockM + N / 2) * 128;
+  if (fp8 == 3) return (kBlockM + N) * 64;
   const int bk = tc_block_k(N, split, 1);
   return (kBlockM * bk * 2 + (N / 2) * bk * 2) * (1 + split) + (fp8 ? kBlockM * bk : 0);
 }
@@ -1558,11 +1588,13 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
     const int sp = a.a_lo;
     const int f8 = a.a_fp8;
     const bool f8f8 = col_scale != nullptr;
+    const bool f8lo = f8f8 && tmB2 != nullptr;  // B as hi + lo e4m3 parts
     if (f8f8 && (!a.a_fp8 || col_ld < a.T)) return cudaErrorInvalidValue;
-    const size_t smem = tc2_smem_bytes(a.N, a.stages, sp, f8f8 ? 2 : f8);
+    const size_t smem = tc2_smem_bytes(a.N, a.stages, sp, f8lo ? 3 : (f8f8 ? 2 : f8));
     if (smem > static_cast<size_t>(kSmemOptIn)) return cudaErrorInvalidValue;
     const bool bk64 = tc_block_k(a.N, sp, 1) == 64;
-    const void* kfn = f8f8 ? reinterpret_cast<const void*>(k_tc_gemm2_f8f8<128>)
+    const void* kfn = f8lo ? reinterpret_cast<const void*>(k_tc_gemm2_f8f8lo<64>)
+                      : f8f8 ? reinterpret_cast<const void*>(k_tc_gemm2_f8f8<128>)
                       : f8 ? (bk64 ? reinterpret_cast<const void*>(k_tc_gemm2_f8<64>)
                                    : reinterpret_cast<const void*>(k_tc_gemm2_f8<32>))
                       : sp ? (bk64 ? reinterpret_cast<const void*>(k_tc_gemm2_split<64>)
@@ -1591,7 +1623,9 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
     const long long pu = static_cast<long long>(a.Nb) * ((a.m_tiles + 1) / 2) * a.n_kchunks;
     if (nclusters > pu) nclusters = pu;
     cfg.gridDim = dim3(static_cast<unsigned>(nclusters * 2));
-    if (f8f8) {
+    if (f8lo) {
+      e = cudaLaunchKernelEx(&cfg, k_tc_gemm2_f8f8lo<64>, tmA, tmB, *tmB2, a, col_scale, col_ld);
+    } else if (f8f8) {
       e = cudaLaunchKernelEx(&cfg, k_tc_gemm2_f8f8<128>, tmA, tmB, a, col_scale, col_ld);
     } else if (f8) {
       if (bk64)
@@ -1735,7 +1769,7 @@ cudaError_t launch_pack_b(const float2* src, int Nb, int T, long long nc, long l
 }
 
 cudaError_t launch_pack_b_f8(const float2* src, int Nb, int T, long long nc, long long s_l, long long s_t,
-                             long long Kc, int N_alloc, int n_rows, float* col_scale, int col_ld, void* dst,
+                             long long Kc, int N_alloc, int n_rows, float* col_scale, int col_ld, void* dst, void* dst_lo,
                              cudaStream_t st) {
   if (n_rows % 2 != 0 || n_rows > N_alloc || 2 * T > n_rows || nc > Kc || col_ld < n_rows / 2)
     return cudaErrorInvalidValue;
@@ -1744,7 +1778,8 @@ cudaError_t launch_pack_b_f8(const float2* src, int Nb, int T, long long nc, lon
   long long blocks = (warps + 7) / 8;
   if (blocks > 152LL * 16) blocks = 152LL * 16;
   k_pack_b_f8<<<static_cast<unsigned>(blocks), 256, 0, st>>>(src, Nb, T, nc, s_l, s_t, Kc, N_alloc, n_rows,
-                                                                col_scale, col_ld, static_cast<uint16_t*>(dst));
+                                                                col_scale, col_ld, static_cast<uint16_t*>(dst),
+                                                                static_cast<uint16_t*>(dst_lo));
   return cudaGetLastError();
 }
 

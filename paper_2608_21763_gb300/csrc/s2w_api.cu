@@ -113,7 +113,8 @@ struct s2w_ctx {
   void* tc_vhat_lo = nullptr;
   void* tc_p2_lo = nullptr;
   void* tc_bp1 = nullptr;   // [Nb][tc_n1max][2 Ns_pad] bf16 (FP8 activations: bytes)
-  bool tc_f8act = false;    // FP8 operator x FP8 activations on stage 1 (opts.tc_fp8_act)
+  bool tc_f8act = false;    // FP8 operator x FP8 activations on stage 1 (opts.tc_fp8_act 1 or 2)
+  bool tc_f8lo = false;     // ... with the activations as hi + lo e4m3 parts (opts.tc_fp8_act = 2)
   float* tc_colscale = nullptr;  // [Nb][tc_n1max / 2] per-(bin, rupture) scales of the FP8 B operand
   void* tc_mhat = nullptr;  // [Nb][b][Ng] BF16 pairs (complex FP32 when split)
   void* tc_vhat = nullptr;  // [Nb][tc_bsub][Ng_pad2] bf16 pairs
@@ -517,10 +518,10 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
     }
     {
       StageTimer t(ctx, 6, st, f8 && !f8f8 ? 2 : 1);
-      if (f8f8)  // e4m3 operand, one power-of-two scale per (bin, rupture)
+      if (f8f8)  // e4m3 operand (+ lo parts), one power-of-two scale per (bin, rupture)
         CK(launch_pack_b_f8(ctx->ws_shat, static_cast<int>(Nb), Bs, Ns_pad, static_cast<long long>(Bs) * Ns_pad,
                             Ns_pad, Ns_pad, ctx->tc_n1max, N1, ctx->tc_colscale, ctx->tc_n1max / 2, ctx->tc_bp1,
-                            st));
+                            ctx->tc_f8lo ? ctx->tc_bp1_lo : nullptr, st));
       else if (f8)  // FP16 operand for the FP16 MMAs of the FP8 path, scaled by a power of two from its amax
         CK(launch_pack_b_f16(ctx->ws_shat, static_cast<int>(Nb), Bs, Ns_pad, static_cast<long long>(Bs) * Ns_pad,
                              Ns_pad, Ns_pad, ctx->tc_n1max, ctx->d_amax, ctx->tc_bp1, st));
@@ -530,10 +531,16 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
     }
     if (f8f8) {
       StageTimer t(ctx, 1, st);
-      CUtensorMap ta, tb;
-      // byte maps with 128-byte swizzle: K blocks of 128 e4m3 elements
-      CK(tc_encode_3d_u8(&ta, ctx->G, K1, Ng, Nb, 128, 128, 1));
-      CK(tc_encode_3d_u8(&tb, ctx->tc_bp1, K1, ctx->tc_n1max, Nb, (N1 > 256 ? 256 : N1) / 2, 128, 1));
+      CUtensorMap ta, tb, tb2;
+      // byte maps: K blocks of 128 e4m3 elements with 128-byte swizzle, or
+      // of 64 with 64-byte swizzle when B comes as hi + lo parts
+      const bool lo = ctx->tc_f8lo;
+      const int bkb = lo ? 64 : 128;
+      const int swz = lo ? 2 : 1;
+      const int brows = (N1 > 256 ? 256 : N1) / 2;
+      CK(tc_encode_3d_u8(&ta, ctx->G, K1, Ng, Nb, 128, bkb, swz));
+      CK(tc_encode_3d_u8(&tb, ctx->tc_bp1, K1, ctx->tc_n1max, Nb, brows, bkb, swz));
+      if (lo) CK(tc_encode_3d_u8(&tb2, ctx->tc_bp1_lo, K1, ctx->tc_n1max, Nb, brows, bkb, swz));
       TcArgs a{};
       a.N = N1;
       a.K = K1;
@@ -541,9 +548,9 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
       a.Nb = static_cast<int>(Nb);
       a.m_tiles = m1;
       a.n_kchunks = 1;
-      a.kblocks_per_chunk = (K1 + 127) / 128;
+      a.kblocks_per_chunk = (K1 + bkb - 1) / bkb;
       a.cta2 = 1;
-      a.stages = tc_stages_pair(N1, 0, 2);
+      a.stages = tc_stages_pair(N1, 0, lo ? 3 : 2);
       a.tmem_cols = N1 <= 32 ? 32 : (N1 <= 64 ? 64 : (N1 <= 128 ? 128 : (N1 <= 256 ? 256 : 512)));
       a.a_fp8 = 1;
       a.row_scale = ctx->G_scale;
@@ -554,7 +561,8 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
       a.ld_l = static_cast<long long>(Bs) * Ng;
       a.ld_t = Ng;
       a.status = ctx->d_status;
-      CK(launch_tc_gemm(ta, tb, a, ctx->num_sms, st, nullptr, nullptr, ctx->tc_colscale, ctx->tc_n1max / 2));
+      CK(launch_tc_gemm(ta, tb, a, ctx->num_sms, st, nullptr, lo ? &tb2 : nullptr, ctx->tc_colscale,
+                        ctx->tc_n1max / 2));
     } else {
       StageTimer t(ctx, 1, st);
       CUtensorMap ta, tb, ta2, tb2;
@@ -755,8 +763,8 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
     return fail(nullptr, S2W_ERR_ARG, "single_pass=%d: 0 or 1", o.single_pass);
   if (o.tc_pair != S2W_PAIR_AUTO && o.tc_pair != S2W_PAIR_ON && o.tc_pair != S2W_PAIR_OFF)
     return fail(nullptr, S2W_ERR_ARG, "tc_pair=%d: S2W_PAIR_AUTO, _ON or _OFF", o.tc_pair);
-  if (o.tc_fp8_act != 0 && o.tc_fp8_act != 1)
-    return fail(nullptr, S2W_ERR_ARG, "tc_fp8_act=%d: 0 or 1", o.tc_fp8_act);
+  if (o.tc_fp8_act < 0 || o.tc_fp8_act > 2)
+    return fail(nullptr, S2W_ERR_ARG, "tc_fp8_act=%d: 0, 1 or 2", o.tc_fp8_act);
   if (o.tc_fp8_act && o.prec_g != S2W_PREC_FP8_E4M3)
     return fail(nullptr, S2W_ERR_ARG, "tc_fp8_act needs prec_g = S2W_PREC_FP8_E4M3");
   if (o.single_pass && (Nt > 256 || o.engine == S2W_ENGINE_TENSOR || o.tc_adjoint))
@@ -868,6 +876,7 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
     // batch): only when asked for
     ctx->tc_rtpair = o.tc_pair == S2W_PAIR_ON;
     ctx->tc_f8act = o.tc_fp8_act != 0;
+    ctx->tc_f8lo = o.tc_fp8_act == 2;
     // FP8 B rows come in multiples of 32 (N % 32 for the two-SM tiles)
     ctx->tc_n1max = static_cast<int>(round_up(2 * ctx->tc_bsub, ctx->tc_f8act ? 32 : 16));
     if (ctx->tc_n1max > 256) ctx->tc_n1max = 512;
@@ -881,6 +890,8 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
     if (ctx->tc_f8act &&
         (e = dalloc(&ctx->tc_colscale, sizeof(float) * Nb * (ctx->tc_n1max / 2))) != cudaSuccess)
       return bad(e, "FP8 activation scales");
+    if (ctx->tc_f8lo && (e = dalloc(&ctx->tc_bp1_lo, 1ull * Nb * ctx->tc_n1max * 2 * ctx->Ns_pad)) != cudaSuccess)
+      return bad(e, "FP8 activation low-order parts");
     ctx->tc_adj = o.tc_adjoint != 0;
     // FP32 seafloor spectra for the split path, and for the adjoint's what
     const bool mhat32 = sp || ctx->tc_adj;

@@ -262,13 +262,17 @@ int tc_block_k(int N, int split = 0, int pair = 0);
 int tc_stages_for(int N, int a_lo = 0, int b_lo = 0, int fp8 = 0, int mt = 1);
 int tc_stages_pair(int N, int split, int fp8 = 0);
 // Byte tensor map for FP8 A tiles: [nbatch][rows][K] bytes, box bk x box_rows, no swizzle
-// (sw128: 128-byte swizzle, bk = 128, for operands the MMAs read directly).
+// (sw128 = 1: 128-byte swizzle, bk = 128; 2: 64-byte swizzle, bk = 64; for
+// operands the MMAs read directly).
 cudaError_t tc_encode_3d_u8(CUtensorMap* out, const void* base, long long K, long long rows, long long nbatch,
                             int box_rows, int bk, int sw128 = 0);
 // tmA2 / tmB2: tensor maps of the low-order parts when a.a_lo / a.b_lo.
 // col_scale (with a.a_fp8 and a.cta2): B is FP8 e4m3 too (launch_pack_b_f8),
 // byte tensor maps with 128-byte swizzle and 128-byte K boxes, kind::f8f6f4
-// MMAs; column t of bin l is scaled by col_scale[l * col_ld + t].  (Kept out
+// MMAs; column t of bin l is scaled by col_scale[l * col_ld + t].  With
+// col_scale and tmB2: B is hi + lo e4m3 parts (tmB, tmB2), 64-byte swizzle
+// and 64-byte K boxes for A and both B parts, two MMAs per K step
+// (a.stages from tc_stages_pair(N, 0, 3)).  (Kept out
 // of TcArgs: a larger argument block costs every GEMM kernel registers.)
 cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const TcArgs& a, int num_sms,
                            cudaStream_t st, const CUtensorMap* tmA2 = nullptr, const CUtensorMap* tmB2 = nullptr,
@@ -294,9 +298,11 @@ __device__ __forceinline__ float f16_unscale(unsigned amax_bits) { return 1.f / 
 // the K padding c >= nc), each pair of rows scaled by the power of two that
 // brings its amax to at most 448 (e4m3's largest finite value), rounded to
 // nearest even with saturation; col_scale[l * col_ld + t] = 1 / that scale.
+// dst_lo (optional): the low-order parts, e4m3 of (scaled value - its e4m3
+// rounding), in the same frame and layout.
 cudaError_t launch_pack_b_f8(const float2* src, int Nb, int T, long long nc, long long s_l, long long s_t,
                              long long Kc, int N_alloc, int n_rows, float* col_scale, int col_ld, void* dst,
-                             cudaStream_t st);
+                             void* dst_lo, cudaStream_t st);
 cudaError_t launch_pack_b_f16(const float2* src, int Nb, int T, long long nc, long long s_l, long long s_t,
                               long long Kc, int N_alloc, unsigned* amax, void* dst, cudaStream_t st);
 // A operand dst[(l*rows_total + r0 + r)*Kc + c0 + c] (BF16 pairs, hi and

@@ -81,7 +81,7 @@ def test_opts_layout_matches_the_header():
 def test_create_rejects_bad_options_before_touching_a_device():
     L = s2w.lib()
     h = ctypes.c_void_p()
-    for field, value, prec_g in [("tc_pair", 3, 1), ("tc_pair", -1, 1), ("tc_fp8_act", 2, 3),
+    for field, value, prec_g in [("tc_pair", 3, 1), ("tc_pair", -1, 1), ("tc_fp8_act", 3, 3),
                                  ("tc_fp8_act", 1, 1), ("tc_fp8_act", 1, 0), ("tc_bsub", 64, 1),
                                  ("tc_bsub", -1, 1), ("tc_s2_chunks", 17, 1), ("tc_s2_chunks", -1, 1),
                                  ("fault", 9, 0)]:

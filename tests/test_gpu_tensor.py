@@ -295,6 +295,36 @@ def test_fp8_activations_on_tensor_engine(Ng, B):
     assert np.array_equal(out[True], q2)
 
 
+@pytest.mark.parametrize("Ng,B", [(700, 3), (600, 300), (5000, 256)])
+def test_fp8_hilo_activations_match_fp16_activations(Ng, B):
+    """FP8 operator x FP8 activations as hi + lo e4m3 parts (tc_fp8_act = 2:
+    two kind::f8f6f4 MMAs per K step on two-SM tiles, 64-byte swizzle): at
+    the FP8 bar against the oracle, and within 2^-7 of the window norm of the
+    FP16-activation path (the hi + lo pair keeps ~2^-8 of each entry, FP16
+    2^-11; the operator's own e4m3 rounding is common to both)."""
+    geom = compact_box(24, Ng, 6, seed=Ng + B + 9)
+    rng = np.random.default_rng(B + 9)
+    Nt = 64
+    slip = rng.standard_normal((B, geom.Ns, Nt))
+    slip[:, :, Nt // 2:] = 0
+    st = torch.tensor(slip, dtype=torch.float32, device="cuda")
+    G = geom.greens_rows(0, geom.Ng, Nt)
+    P = geom.adjoint_cols(0, geom.Ng, Nt)
+    q_ref = oracle.waveforms(G, P, slip)
+    wn, kappa = window_norms(G, P, slip)
+    out = {}
+    for act in (0, 2):
+        ctx = make_context(s2w, geom, Nt, prec_g="fp8", max_batch=B, chunk=256, engine="tensor", tc_fp8_act=act)
+        out[act] = ctx.waveforms(st).cpu().numpy()
+        ctx.sync()
+        assert_parity(out[act], q_ref, wn, kappa, tol=TOL_F8, label=f"fp8 act={act} B={B}")
+    d = np.linalg.norm((out[2] - out[0]).reshape(B, -1), axis=1)
+    print("hi/lo vs FP16 activations, / window:", d / wn)
+    assert np.all(d <= 2.0 ** -7 * wn), d / wn
+    q2 = ctx.waveforms(st).cpu().numpy()
+    assert np.array_equal(out[2], q2)
+
+
 def test_fp8_activations_reject_other_precisions():
     geom = compact_box(8, 300, 2, seed=5)
     with pytest.raises(s2w.S2WError):
