@@ -63,12 +63,10 @@ def parse():
     ap.add_argument("--engine", default="auto", choices=["auto", "stream", "tensor"])
     ap.add_argument("--tc-pair", default="auto", choices=["auto", "on", "off"],
                     help="tensor engine: two-SM MMAs (a CTA pair per 256-row tile)")
-    ap.add_argument("--fp8-act", action="store_true",
-                    help="FP8 operator on the tensor engine: round the slip spectra to e4m3 too "
-                         "(FP8 x FP8 stage-1 MMAs)")
-    ap.add_argument("--fp8-act-hilo", action="store_true",
-                    help="FP8 operator on the tensor engine: slip spectra as hi + lo e4m3 parts "
-                         "(two FP8 x FP8 MMAs per K step, FP16-class activation accuracy)")
+    ap.add_argument("--fp8-act", default="hilo", choices=["hilo", "e4m3", "f16"],
+                    help="FP8 operator on the tensor engine, its activations (the slip spectra): hi + lo e4m3 "
+                         "parts (two FP8 x FP8 MMAs per K step, FP16-class accuracy; the library default), one "
+                         "e4m3 part (one FP8 x FP8 MMA), or FP16 (the operator widened to FP16 in shared memory)")
     ap.add_argument("--mode", default="waveforms", choices=["waveforms", "gradient"],
                     help="gradient: one step = misfit gradients of the batch (forward + adjoint)")
     ap.add_argument("--batch", type=int, default=None, help="ruptures per step (default: the workload's)")
@@ -167,13 +165,13 @@ def tensor_dtype(args):
     if args.prec_g == "bf16_hilo":
         return "bf16x3"
     if args.prec_g == "fp8":
-        return "e4m3x2" if args.fp8_act_hilo else ("e4m3" if args.fp8_act else "f16")
+        return {"hilo": "e4m3x2", "e4m3": "e4m3", "f16": "f16"}[args.fp8_act]
     return "bf16"
 
 
 # ------------------------------------------------------------------ setup
 def load_context(s2w, wl, geom, prec_g, prec_p, B, device, engine="auto", chunk=1024,
-                 tc_adjoint=False, single_pass=False, tc_pair="auto", tc_fp8_act=False):
+                 tc_adjoint=False, single_pass=False, tc_pair="auto", tc_fp8_act=None):
     ctx = s2w.Context(wl.Ns, wl.Ng, wl.No, wl.Nt, prec_g=prec_g, prec_p=prec_p,
                       max_batch=B, device=device, engine=engine, tc_adjoint=tc_adjoint,
                       single_pass=single_pass, tc_pair=tc_pair, tc_fp8_act=tc_fp8_act)
@@ -368,7 +366,7 @@ def run_ours(args, rank, world, local_rank):
     tc_adj = args.mode == "gradient" and args.prec_g in ("bf16", "bf16_hilo") and args.engine != "stream"
     ctx = load_context(s2w, wl, geom, args.prec_g, args.prec_p, B, local_rank, args.engine,
                        tc_adjoint=tc_adj, single_pass=args.single_pass,
-                       tc_pair=args.tc_pair, tc_fp8_act=2 if args.fp8_act_hilo else int(args.fp8_act))
+                       tc_pair=args.tc_pair, tc_fp8_act={"hilo": 2, "e4m3": 1, "f16": 0}[args.fp8_act])
     setup_s = time.perf_counter() - t_setup
     slip_d = torch.tensor(slip_np, device=dev)
     q_d = torch.empty((pool, B, wl.No, wl.Nt), dtype=torch.float32, device=dev)
@@ -500,13 +498,13 @@ def run_ours(args, rank, world, local_rank):
         split = args.prec_g == "bf16_hilo"
         bsub = min(B, tuning["tc_bsub"] if tuning else (128 if split else 256))
         flops = 8.0 * (wl.Nt + 1) * wl.Ng * wl.Ns * bsub
-        f8f8 = (args.fp8_act or args.fp8_act_hilo) and args.prec_g == "fp8"
-        terms = 3 if split else (2 if f8f8 and args.fp8_act_hilo else 1)
+        f8f8 = args.fp8_act != "f16" and args.prec_g == "fp8"
+        terms = 3 if split else (2 if f8f8 and args.fp8_act == "hilo" else 1)
         achieved = terms * flops / per_launch_s / 1e12
         # FP8 x FP8 MMAs: the measured BF16 peak times the nominal fp8 / bf16 ratio (4.5 / 2.25)
         peak = pk["bf16_tflops_sustained"] * (2.0 if f8f8 else 1.0)
         kname = ("k_tc_gemm2_f8f8lo (stage-1 per-bin GEMM, two tcgen05 kind::f8f6f4 MMAs per K step)"
-                 if f8f8 and args.fp8_act_hilo else
+                 if f8f8 and args.fp8_act == "hilo" else
                  "k_tc_gemm2_f8f8 (stage-1 per-bin GEMM, tcgen05 kind::f8f6f4)" if f8f8
                  else "k_tc_gemm / k_tc_gemm2 (stage-1 per-bin GEMM, tcgen05 kind::f16)")
         roof = {"kernel": kname, "bound": "tensor",
@@ -539,7 +537,8 @@ def run_ours(args, rank, world, local_rank):
            "data": "synthetic",
            "config": workload_config(wl, B, args),
            "engine": {"engine": "tensor" if tensor else "stream", "tc_pair": args.tc_pair,
-                      "fp8_activations": "e4m3 hi + lo" if args.fp8_act_hilo else bool(args.fp8_act),
+                      "fp8_activations": {"hilo": "e4m3 hi + lo", "e4m3": "e4m3", "f16": "f16"}[args.fp8_act]
+                      if args.prec_g == "fp8" else None,
                       "autotune": tuning, "cuda_graph": use_graph,
                       "single_pass": bool(args.single_pass), "parallelism": f"replicas{world}",
                       "l2": "inputs larger than L2 (every step streams the full operator spectra)",

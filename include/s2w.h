@@ -147,16 +147,17 @@ typedef struct {
                       kind::f8f6f4, two-SM tiles): twice the BF16 MMA rate
                       and no widening of the operator, at the cost of the
                       activation rounding (<= 2^-4 relative per entry) on
-                      top of the operator's.  2: the same with the slip
-                      spectra as hi + lo e4m3 parts in that frame (lo = the
-                      rounded remainder), two FP8 x FP8 MMAs per K step:
+                      top of the operator's.  2 (default): the same with the
+                      slip spectra as hi + lo e4m3 parts in that frame (lo =
+                      the rounded remainder), two FP8 x FP8 MMAs per K step:
                       activations kept to ~2^-8, the FP16 path's accuracy
                       for these contractions, with both operands read as
-                      bytes straight from TMA.  Used for sub-batches whose
+                      bytes straight from TMA.  0: the operator tiles
+                      widened exactly to FP16 in shared memory, FP16
+                      activations.  1 and 2 are used for sub-batches whose
                       grid spans at least two 128-row tiles; others take the
-                      FP16-activation path.  0 (default): the operator
-                      tiles widened exactly to FP16 in shared memory, FP16
-                      activations. */
+                      FP16-activation path.  With another prec_g the default
+                      2 is ignored and 1 is an argument error. */
   int tc_bsub;     /* tensor engine: ruptures per GEMM pass (the sub-batch),
                       128 or 256 (BF16_HILO: 128); 0 (default) = 256, or 128
                       for BF16_HILO, capped by max_batch.  The workspaces are

@@ -171,7 +171,7 @@ class Context:
 
     def __init__(self, Ns, Ng, No, Nt, prec_g="fp32", prec_p="fp32",
                  dt_mode="backward", dt=1.0, max_batch=1, device=0, engine="auto",
-                 tc_adjoint=False, single_pass=False, tc_pair="auto", tc_fp8_act=False, tc_bsub=0,
+                 tc_adjoint=False, single_pass=False, tc_pair="auto", tc_fp8_act=None, tc_bsub=0,
                  tc_s2_chunks=0, tune_cache=None, fault="none", fault_wait_us=5000):
         L = lib()
         o = Opts()
@@ -183,7 +183,8 @@ class Context:
         o.tc_adjoint = int(bool(tc_adjoint))
         o.single_pass = int(bool(single_pass))
         o.tc_pair = PAIR[tc_pair]
-        o.tc_fp8_act = int(tc_fp8_act)  # False / True / 2 (hi + lo e4m3 activations)
+        if tc_fp8_act is not None:  # 0 / False: FP16, 1 / True: e4m3, 2: hi + lo e4m3 (library default)
+            o.tc_fp8_act = int(tc_fp8_act)
         o.tc_bsub = int(tc_bsub)
         o.tc_s2_chunks = int(tc_s2_chunks)
         cache = None if tune_cache is None else os.fsencode(tune_cache)

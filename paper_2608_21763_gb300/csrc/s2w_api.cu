@@ -693,7 +693,7 @@ void s2w_default_opts(s2w_opts* o) {
   o->tc_adjoint = 0;
   o->single_pass = 0;
   o->tc_pair = S2W_PAIR_AUTO;
-  o->tc_fp8_act = 0;
+  o->tc_fp8_act = 2;
   o->tc_bsub = 0;
   o->tc_s2_chunks = 0;
   o->tune_cache = nullptr;
@@ -765,8 +765,10 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
     return fail(nullptr, S2W_ERR_ARG, "tc_pair=%d: S2W_PAIR_AUTO, _ON or _OFF", o.tc_pair);
   if (o.tc_fp8_act < 0 || o.tc_fp8_act > 2)
     return fail(nullptr, S2W_ERR_ARG, "tc_fp8_act=%d: 0, 1 or 2", o.tc_fp8_act);
-  if (o.tc_fp8_act && o.prec_g != S2W_PREC_FP8_E4M3)
-    return fail(nullptr, S2W_ERR_ARG, "tc_fp8_act needs prec_g = S2W_PREC_FP8_E4M3");
+  if (o.tc_fp8_act && o.prec_g != S2W_PREC_FP8_E4M3) {
+    if (!opts || o.tc_fp8_act == 2) o.tc_fp8_act = 0;  // the default applies to FP8 operators only
+    else return fail(nullptr, S2W_ERR_ARG, "tc_fp8_act needs prec_g = S2W_PREC_FP8_E4M3");
+  }
   if (o.single_pass && (Nt > 256 || o.engine == S2W_ENGINE_TENSOR || o.tc_adjoint))
     return fail(nullptr, S2W_ERR_UNSUPPORTED, "single_pass: stream engine only, Nt <= 256, no tc_adjoint");
   if (o.engine == S2W_ENGINE_TENSOR && 2 * No > 256)

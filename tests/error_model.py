@@ -13,7 +13,9 @@ or feeds to its MMAs in a narrower type, as the library's header documents:
                 stay FP32 and are split by the retransform;
   tensor FP8:   stage-1 operator as e4m3 with one scale per (bin, 256 grid
                 rows), slip spectra as FP16 (an exact power-of-two rescale
-                first), the rest as tensor BF16.
+                first), the rest as tensor BF16;
+  tensor FP8 hi/lo: the same with the slip spectra as hi + lo e4m3 parts in
+                one power-of-two frame per (bin, rupture) (amax <= 448).
 The FP32 arithmetic of the kernels is not modelled: the bars are set at
 about twice the modelled rounding error so that it fits beside it.
 """
@@ -63,6 +65,21 @@ def fp8_rows(Gh):
         amax = np.maximum(np.abs(blk.real).max(axis=(0, 1)), np.abs(blk.imag).max(axis=(0, 1)))
         sc = np.where(amax > 0, amax / 448.0, 1.0)
         out[g0:g0 + 256] = (e4m3(blk.real / sc) + 1j * e4m3(blk.imag / sc)) * sc
+    return out
+
+
+def e4m3_hilo_cols(sh):
+    """sh [B][Ns][Nb] as hi + lo e4m3 parts, both in the frame of the power of
+    two that brings each (rupture, bin)'s largest |Re|, |Im| to <= 448."""
+    out = np.empty_like(sh)
+    for b in range(sh.shape[0]):
+        for l in range(sh.shape[2]):
+            x = sh[b, :, l]
+            m = max(np.abs(x.real).max(), np.abs(x.imag).max())
+            sc = 2.0 ** np.floor(np.log2(448.0 / m)) if m > 0 else 1.0
+            xr, xi = x.real * sc, x.imag * sc
+            hr, hi = e4m3(xr), e4m3(xi)
+            out[b, :, l] = (hr + e4m3(xr - hr) + 1j * (hi + e4m3(xi - hi))) / sc
     return out
 
 
@@ -141,6 +158,10 @@ def model_waveforms(G, P, slip, path):
     elif path == "tensor_fp8":
         mh = bf16c(ein1(fp8_rows(Gh), f16c(sh / 2.0 ** np.ceil(np.log2(np.abs(sh).max()))) *
                         2.0 ** np.ceil(np.log2(np.abs(sh).max()))))
+        vh = bf16c(retransform(mh, bf16(T)))
+        qh = ein2(bf16c(Ph), vh)
+    elif path == "tensor_fp8_hilo":
+        mh = bf16c(ein1(fp8_rows(Gh), e4m3_hilo_cols(sh)))
         vh = bf16c(retransform(mh, bf16(T)))
         qh = ein2(bf16c(Ph), vh)
     elif path == "tensor_split":

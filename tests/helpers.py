@@ -17,7 +17,7 @@ BARS = {"stream_bf16": 5e-3, "stream_bf16_hilo": 2e-5, "stream_fp8": 1e-1,
 
 def make_context(s2w, geom, Nt, prec_g="fp32", prec_p="fp32", dt_mode="backward",
                  max_batch=1, chunk=4096, order=None, engine="auto", tc_adjoint=False,
-                 single_pass=False, tc_pair="auto", tc_fp8_act=False, **opts):
+                 single_pass=False, tc_pair="auto", tc_fp8_act=None, **opts):
     """Context with both operators loaded from the generator, in row chunks
     (optionally in a permuted chunk order)."""
     Ng = geom.Ng

@@ -65,16 +65,16 @@ def test_opts_layout_matches_the_header():
     """s2w_default_opts writes every field of s2w_opts: written into a buffer
     larger than the binding's Opts, it must stop exactly at Opts' end (a
     field missing from the binding would be written past it) and leave the
-    defaults of the last fields (two-SM tiles: library choice; FP8
-    activations off; library sub-batch and stage-2 chunking; no tune cache;
-    no injected fault)."""
+    defaults of the last fields (two-SM tiles: library choice; FP8 operators
+    take hi + lo e4m3 activations; library sub-batch and stage-2 chunking;
+    no tune cache; no injected fault)."""
     L = s2w.lib()
     n = ctypes.sizeof(s2w.Opts)
     buf = (ctypes.c_ubyte * (n + 64))(*([0xAB] * (n + 64)))
     L.s2w_default_opts(ctypes.cast(buf, ctypes.POINTER(s2w.Opts)))
     assert all(b == 0xAB for b in buf[n:])
     o = s2w.Opts.from_buffer(buf)
-    assert (o.tc_adjoint, o.single_pass, o.tc_pair, o.tc_fp8_act) == (0, 0, 0, 0)
+    assert (o.tc_adjoint, o.single_pass, o.tc_pair, o.tc_fp8_act) == (0, 0, 0, 2)
     assert (o.tc_bsub, o.tc_s2_chunks, o.tune_cache, o.fault, o.fault_wait_us) == (0, 0, None, 0, 5000)
 
 

@@ -15,7 +15,7 @@ from helpers import BARS
 
 MODEL_PATH = {"stream_bf16": ["stream_bf16"], "stream_bf16_hilo": ["stream_bf16_hilo"],
               "stream_fp8": ["stream_fp8", "stream_fp8_bf16p"], "tensor_bf16": ["tensor_bf16"],
-              "tensor_split": ["tensor_split"], "tensor_fp8": ["tensor_fp8"]}
+              "tensor_split": ["tensor_split"], "tensor_fp8": ["tensor_fp8", "tensor_fp8_hilo"]}
 
 
 def cases():

@@ -220,11 +220,11 @@ def test_split_precision_record_lengths(Nt):
 
 @pytest.mark.parametrize("B", [3, 7, 300])
 def test_fp8_operator_on_tensor_engine(B):
-    """FP8 e4m3 stage-1 spectra on the tensor engine: tiles widened to FP16
-    in shared memory (128-byte swizzle at N <= 256, 64-byte at N = 512),
+    """FP8 e4m3 stage-1 spectra on the tensor engine with the default
+    activations (hi + lo e4m3 parts on two-SM tiles; FP16 below two M tiles),
     per-(bin, 256-row) scales in the epilogue.  Against the oracle at the
     FP8 bar, and against the FP8 stream engine (same quantised operator; they
-    differ by the BF16 rounding of the activations)."""
+    differ by the rounding of the activations)."""
     geom = compact_box(24, 700, 6, seed=61)
     Nt = 64
     rng = np.random.default_rng(62)
@@ -331,9 +331,11 @@ def test_fp8_activations_reject_other_precisions():
         make_context(s2w, geom, 32, prec_g="bf16", max_batch=4, tc_fp8_act=True)
 
 
-def test_fp8_tensor_operand_range_is_scaled():
-    """The FP8 path's FP16 B operand carries a power-of-two scale from its
-    amax: slip scaled by 1e6 or 1e-6 (beyond / far inside the FP16 range)
+@pytest.mark.parametrize("act", [0, 2])
+def test_fp8_tensor_operand_range_is_scaled(act):
+    """The FP8 path's B operand (FP16, or hi + lo e4m3) carries a power-of-two
+    scale from its amax (the whole operand's, or each (bin, rupture)'s):
+    slip scaled by 1e6 or 1e-6 (beyond / far inside the FP16 and e4m3 ranges)
     gives the scaled waveforms, finite and within the tensor path's bar (a
     non-power-of-two rescale reshuffles the BF16 rounding of the later
     stages, ~2e-3 of the window; an overflow or underflow would be O(1))."""
@@ -342,7 +344,7 @@ def test_fp8_tensor_operand_range_is_scaled():
     rng = np.random.default_rng(66)
     slip = rng.standard_normal((B, geom.Ns, Nt))
     slip[:, :, Nt // 2:] = 0
-    ctx = make_context(s2w, geom, Nt, prec_g="fp8", max_batch=B, chunk=256, engine="tensor")
+    ctx = make_context(s2w, geom, Nt, prec_g="fp8", max_batch=B, chunk=256, engine="tensor", tc_fp8_act=act)
     q1 = ctx.waveforms(torch.tensor(slip, dtype=torch.float32, device="cuda")).cpu().numpy().astype(np.float64)
     G = geom.greens_rows(0, geom.Ng, Nt)
     P = geom.adjoint_cols(0, geom.Ng, Nt)

@@ -66,12 +66,14 @@ def test_single_rank_and_job_rate():
 
 def test_tensor_dtype_names_the_mma_type():
     """The bench line's dtype is the stage-1 MMA arithmetic: FP8 operators run
-    FP16 MMAs (operator widened) or e4m3 x e4m3 ones (FP8 activations)."""
+    two e4m3 x e4m3 MMAs per product (hi + lo activations, the default), one
+    (e4m3 activations), or FP16 MMAs (operator widened)."""
     import argparse
     sys.path.insert(0, ROOT)
     import bench
     ns = argparse.Namespace
-    assert bench.tensor_dtype(ns(prec_g="bf16", fp8_act=False)) == "bf16"
-    assert bench.tensor_dtype(ns(prec_g="bf16_hilo", fp8_act=False)) == "bf16x3"
-    assert bench.tensor_dtype(ns(prec_g="fp8", fp8_act=False)) == "f16"
-    assert bench.tensor_dtype(ns(prec_g="fp8", fp8_act=True)) == "e4m3"
+    assert bench.tensor_dtype(ns(prec_g="bf16", fp8_act="hilo")) == "bf16"
+    assert bench.tensor_dtype(ns(prec_g="bf16_hilo", fp8_act="hilo")) == "bf16x3"
+    assert bench.tensor_dtype(ns(prec_g="fp8", fp8_act="hilo")) == "e4m3x2"
+    assert bench.tensor_dtype(ns(prec_g="fp8", fp8_act="e4m3")) == "e4m3"
+    assert bench.tensor_dtype(ns(prec_g="fp8", fp8_act="f16")) == "f16"
