@@ -48,7 +48,7 @@ COMPLEX_BYTES = {"fp32": 8, "fp32_hilo": 16, "bf16": 4, "bf16_hilo": 8, "fp8": 2
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference", "torch_conv"],
                     help="torch_conv: the paper's comparison method (two direct convolutions with "
