@@ -511,7 +511,8 @@ def run_ours(args, rank, world, local_rank):
                 "achieved": round(achieved, 1), "peak": peak, "unit": "TFLOP/s",
                 "frac": round(achieved / peak, 4),
                 "peak_source": pk_kind + (" (bf16 sustained x 2, fp8 nominal ratio)" if f8f8 else " (bf16 sustained)"),
-                "traffic": measured_traffic(wl, args.prec_g, tensor=True, bsub=bsub) if not f8f8 else None,
+                "traffic": measured_traffic(wl, "fp8_hilo" if f8f8 and args.fp8_act == "hilo" else args.prec_g,
+                                            tensor=True, bsub=bsub),
                 "algorithmic_flops_per_launch": flops, "mma_terms": terms,
                 "launch_ms": round(per_launch_s * 1e3, 4)}
     else:
