@@ -164,7 +164,10 @@ typedef struct {
                       sized for it; s2w_autotune may lower it to 128. */
   int tc_s2_chunks; /* tensor engine: chunks of the grid (the K extent) that
                       split the stage-2 GEMM, 1..16; 0 (default) = the count
-                      that balances bins x row tiles x chunks over the SMs.
+                      that balances bins x row tiles x chunks over the SMs,
+                      and for BF16_HILO at least the count that keeps each
+                      chunk within 2,048 K elements (one FP32 accumulation
+                      each; longer ones cost that precision accuracy).
                       Results depend on it (the partial sums are added in
                       chunk order). */
   const char *tune_cache; /* path of the autotuner's cache file, or NULL
@@ -338,7 +341,9 @@ typedef struct {
  * loaded operators (dummy inputs: the timings do not depend on the data):
  * the GEMM form (ruptures per pass and two-SM or single-CTA tiles), the
  * stage-2 K chunk count (how the grid is split between the persistent
- * CTAs), and the batch size from which AUTO uses the tensor engine instead
+ * CTAs; with the BF16 hi/lo split, only counts at or above the default,
+ * since each chunk is one FP32 accumulation and a longer one costs that
+ * precision accuracy), and the batch size from which AUTO uses the tensor engine instead
  * of streaming the spectra once per rupture.  The choices are kept in the
  * context (and written to opts.tune_cache when one is set); an entry already
  * in that cache is applied without timing.  Options the caller fixed

@@ -1055,26 +1055,33 @@ __global__ void k_pack_a(const float2* __restrict__ src, int Nb, int rows, long 
 // Re, Im of bin l (0 < l < Nt).  With T[n][k] (built on the host in FP64 from
 // the definitions, rounded to BF16) every tile of 128 signals is
 //   V (128 x K) = M (128 x K) T^T,
-// one tcgen05 GEMM per tile.  The M tile is written into shared memory by
-// eight fill warps, one k-block each so that all of a tile's loads are in
-// flight together (coalesced loads of mhat[l][b][i0..i0+127], 128-byte
-// swizzled K-major layout, 16-byte stores), T streams through a ring by
-// TMA (it stays in L2), the accumulator rows go back out as BF16 velocity
+// one tcgen05 GEMM per tile, A K-major in 128-byte (BF16) or 64-byte
+// (split) swizzled k-block slots written by eight fill warps, one k-block
+// each so that all of a tile's loads are in flight together (coalesced loads
+// of mhat[l][b][i0 .. i0 + 127], 16-byte swizzled stores; split: the FP32
+// spectra split into hi + lo on the way).  T streams through a ring by TMA
+// (it stays in L2); the accumulator rows go back out as BF16 velocity
 // spectra in the stage-2 operand layout.
 // Warps: 0 TMA (T), 1 TMEM + MMA, then 4 RT_EPW epilogue warps (RT_EPW per
-// TMEM lane quadrant, each taking every RT_EPW-th 64-column chunk: the
-// 512-column accumulator fills tensor memory, so the MMAs of the next tile
-// wait for its drain), then 8 fill warps.  The split kernel keeps one
+// TMEM lane quadrant, each taking every RT_EPW-th 64-column chunk of an
+// accumulator unit), then the 8 fill warps.  The split kernel keeps one
 // epilogue warp per quadrant (its fill warps need the registers).
 // ---------------------------------------------------------------------------
 constexpr int kRtFillWarps = 8;
 __host__ __device__ constexpr int rt_epw(bool split) { return split ? 1 : 2; }
 __host__ __device__ constexpr int rt_threads(bool split) { return 32 * (2 + 4 * rt_epw(split) + kRtFillWarps); }
 
-
-// K blocks run outer and the (up to two) 256-column output halves inner, so a
-// k-block of the M tile is done once both halves have used it: the M tile
-// lives in a ring of RA k-block slots rather than whole in shared memory.
+// Schedule.  A tile's K = 2 Nt output columns are at most two 256-column MMA
+// halves.  BF16 runs the halves outer: each half is one accumulator unit of
+// 256 columns, tensor memory holds two units, and the epilogue drains one
+// unit while the MMAs fill the other (a whole 512-column tile would fill
+// tensor memory and make the next tile's MMAs wait for its drain).  The M
+// tile then stays whole in a ring of RA = 8 k-block slots (K / 64 <= 8) until
+// the second half has used it.  Split mode at Nt = 256 cannot hold its
+// doubled M tile whole: it runs the K blocks outer and both halves inner in
+// one 512-column unit, so each k-block slot is freed once both halves have
+// used it.  With a single half (Nt <= 128) both orders coincide and two
+// units of K columns fit.
 // SPLIT: the FP32 seafloor spectra are split by the fill warps into hi + lo
 // BF16 parts, T comes as hi + lo (both from the FP64 matrix), three MMAs per
 // K step (hi hi, hi lo, lo hi), and the epilogue writes hi + lo velocity
@@ -1106,6 +1113,11 @@ __global__ void __launch_bounds__(rt_threads(SPLIT), 1)
   const int KB = K / BK;          // k-blocks per tile
   const int n_half = K > 256 ? 2 : 1;   // MMA column halves (256 output columns each)
   const int ncols = K > 256 ? 256 : K;
+  const bool hout = !SPLIT || n_half == 1;  // halves outer (see the schedule above)
+  const int U = hout ? n_half : 1;          // accumulator units per tile
+  const int H = hout ? 1 : n_half;          // halves per unit
+  const int ucols = H * ncols;              // accumulator columns per unit
+  const int AS = 2 * ucols <= 512 ? 2 : 1;  // accumulator units in tensor memory
   const int trows = PAIR ? ncols / 2 : ncols;  // T rows this CTA stages per half
   const int t_part = trows * BK * 2;
   const int t_slot = t_part * (SPLIT ? 2 : 1);
@@ -1113,7 +1125,8 @@ __global__ void __launch_bounds__(rt_threads(SPLIT), 1)
   const bool lead = crank == 0;
   const long long cid = PAIR ? static_cast<long long>(cluster_id_x()) : static_cast<long long>(blockIdx.x);
   const long long ncl = PAIR ? static_cast<long long>(cluster_count_x()) : static_cast<long long>(gridDim.x);
-  // one A slot per fill warp: with KB a power of two, slot s = n % RA is only
+  // RA k-block slots (>= KB: the BF16 order keeps a whole M tile), one per
+  // fill warp: with KB a power of two, slot s = n % RA is only
   // ever filled by one warp (k-blocks kb = s mod KB, or s when KB >= RA), one
   // ring lap apart, so no parity wait can run a phase ahead
   constexpr int RA = kRtFillWarps;
@@ -1124,9 +1137,9 @@ __global__ void __launch_bounds__(rt_threads(SPLIT), 1)
   uint64_t* afree = afull + RA;
   uint64_t* tfull = afree + RA;
   uint64_t* tempty = tfull + RT;
-  uint64_t* acc_full = tempty + RT;
-  uint64_t* acc_empty = acc_full + 1;
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(acc_empty + 1);
+  uint64_t* acc_full = tempty + RT;        // [AS]
+  uint64_t* acc_empty = acc_full + 2;      // [AS]
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(acc_empty + 2);
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const int mtiles = (a.Ng + kBlockM - 1) / kBlockM;
@@ -1138,19 +1151,22 @@ __global__ void __launch_bounds__(rt_threads(SPLIT), 1)
     i0 = (static_cast<int>(u % mgroups) * (PAIR ? 2 : 1) + static_cast<int>(crank)) * kBlockM;
   };
   const uint32_t idesc = idesc_bf16(PAIR ? 2 * kBlockM : kBlockM, ncols);
-  const uint32_t tmem_cols = K <= 64 ? 64 : (K <= 128 ? 128 : (K <= 256 ? 256 : 512));
+  const int acols = AS * ucols;
+  const uint32_t tmem_cols = acols <= 64 ? 64 : (acols <= 128 ? 128 : (acols <= 256 ? 256 : 512));
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < RA; ++s) {
-      mbar_init(afull + s, PAIR ? 2 : 1);  // one fill warp per k-block (of each CTA)
+      mbar_init(afull + s, PAIR ? 2 : 1);  // the k-block's fill warp (of each CTA)
       mbar_init(afree + s, 1);
     }
     for (int s = 0; s < RT; ++s) {
       mbar_init(tfull + s, 1);
       mbar_init(tempty + s, 1);
     }
-    mbar_init(acc_full, 1);
-    mbar_init(acc_empty, (PAIR ? 2 : 1) * 4 * EPW);
+    for (int s = 0; s < AS; ++s) {
+      mbar_init(acc_full + s, 1);
+      mbar_init(acc_empty + s, (PAIR ? 2 : 1) * 4 * EPW);
+    }
     fence_mbar_init();
   }
   if (warp == 1) {
@@ -1169,27 +1185,30 @@ __global__ void __launch_bounds__(rt_threads(SPLIT), 1)
   const uint32_t tmem = *tmem_holder;
 
   if (warp == 0) {
-    // T slots in job order: tile, k-block, half
+    // T slots in job order: tile, unit, k-block, half within the unit
     if (lane == 0) {
       int it = 0;
       bool ok = true;
       const uint32_t tfull0 = PAIR ? cluster_addr(tfull, 0) : 0u;
       for (long long t = cid; t < tiles && ok; t += ncl) {
-        for (int kb = 0; kb < KB && ok; ++kb) {
-          for (int h = 0; h < n_half; ++h, ++it) {
-            const int s = it % RT;
-            if (it >= RT && !mbar_wait_bounded(tempty + s, ((it / RT) - 1) & 1, a.status, DEV_ERR_TIMEOUT_EMPTY)) {
-              ok = false;
-              break;
-            }
-            if constexpr (PAIR) {
-              if (lead) mbar_arrive_expect_tx(tfull + s, 2u * static_cast<uint32_t>(t_slot));
-              tma_load_3d_pair(sT + s * t_slot, &tmT, kb * BK, h * ncols + static_cast<int>(crank) * trows, 0,
-                               tfull0 + 8u * static_cast<uint32_t>(s));
-            } else {
-              mbar_arrive_expect_tx(tfull + s, t_slot);
-              tma_load_3d(sT + s * t_slot, &tmT, kb * BK, h * ncols, 0, tfull + s);
-              if constexpr (SPLIT) tma_load_3d(sT + s * t_slot + t_part, &tmT2, kb * BK, h * ncols, 0, tfull + s);
+        for (int u = 0; u < U && ok; ++u) {
+          for (int kb = 0; kb < KB && ok; ++kb) {
+            for (int hh = 0; hh < H; ++hh, ++it) {
+              const int h = hout ? u : hh;
+              const int s = it % RT;
+              if (it >= RT && !mbar_wait_bounded(tempty + s, ((it / RT) - 1) & 1, a.status, DEV_ERR_TIMEOUT_EMPTY)) {
+                ok = false;
+                break;
+              }
+              if constexpr (PAIR) {
+                if (lead) mbar_arrive_expect_tx(tfull + s, 2u * static_cast<uint32_t>(t_slot));
+                tma_load_3d_pair(sT + s * t_slot, &tmT, kb * BK, h * ncols + static_cast<int>(crank) * trows, 0,
+                                 tfull0 + 8u * static_cast<uint32_t>(s));
+              } else {
+                mbar_arrive_expect_tx(tfull + s, t_slot);
+                tma_load_3d(sT + s * t_slot, &tmT, kb * BK, h * ncols, 0, tfull + s);
+                if constexpr (SPLIT) tma_load_3d(sT + s * t_slot + t_part, &tmT2, kb * BK, h * ncols, 0, tfull + s);
+              }
             }
           }
         }
@@ -1213,66 +1232,70 @@ __global__ void __launch_bounds__(rt_threads(SPLIT), 1)
         else
           tc_commit(bar);
       };
-      int it = 0, tl = 0;
+      int it = 0, tl = 0, un = 0;  // T slot, tile and accumulator unit counters
       bool ok = true;
       for (long long t = cid; t < tiles && ok; t += ncl, ++tl) {
-        if (tl > 0 && !wait_x(acc_empty, (tl - 1) & 1, DEV_ERR_TIMEOUT_MMA)) {
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        for (int kb = 0; kb < KB && ok; ++kb) {
-          const long long n = static_cast<long long>(tl) * KB + kb;
-          const int sa = static_cast<int>(n % RA);
-          if (!wait_x(afull + sa, static_cast<int>((n / RA) & 1), DEV_ERR_TIMEOUT_FULL)) {
+        for (int u = 0; u < U && ok; ++u, ++un) {
+          const int as = un % AS;
+          if (un >= AS && !wait_x(acc_empty + as, ((un / AS) - 1) & 1, DEV_ERR_TIMEOUT_MMA)) {
             ok = false;
             break;
           }
-          for (int h = 0; h < n_half; ++h, ++it) {
-            const int s = it % RT;
-            if (!mbar_wait_bounded(tfull + s, (it / RT) & 1, a.status, DEV_ERR_TIMEOUT_FULL)) {
+          tc_fence_after();
+          const uint32_t dcol = tmem + static_cast<uint32_t>(as * ucols);
+          for (int kb = 0; kb < KB && ok; ++kb) {
+            const long long n = static_cast<long long>(tl) * KB + kb;
+            const int sa = static_cast<int>(n % RA);
+            if (u == 0 && !wait_x(afull + sa, static_cast<int>((n / RA) & 1), DEV_ERR_TIMEOUT_FULL)) {
               ok = false;
               break;
             }
-            tc_fence_after();
-            const uint32_t ua = smem_u32(sA + sa * a_slot);
-            const uint32_t ub = smem_u32(sT + s * t_slot);
-#pragma unroll
-            for (int k = 0; k < BK / 16; ++k) {
-              const uint64_t ad = sdesc_sw<BK>(ua + k * 32);
-              const uint64_t bd = sdesc_sw<BK>(ub + k * 32);
-              if constexpr (PAIR)
-                tc_mma2_bf16(tmem + h * ncols, ad, bd, idesc, (kb > 0 || k > 0) ? 1u : 0u);
-              else
-                tc_mma_bf16(tmem + h * ncols, ad, bd, idesc, (kb > 0 || k > 0) ? 1u : 0u);
-              if constexpr (SPLIT) {
-                tc_mma_bf16(tmem + h * ncols, ad, sdesc_sw<BK>(ub + t_part + k * 32), idesc, 1u);
-                tc_mma_bf16(tmem + h * ncols, sdesc_sw<BK>(ua + kAs + k * 32), bd, idesc, 1u);
+            for (int hh = 0; hh < H; ++hh, ++it) {
+              const int s = it % RT;
+              if (!mbar_wait_bounded(tfull + s, (it / RT) & 1, a.status, DEV_ERR_TIMEOUT_FULL)) {
+                ok = false;
+                break;
               }
+              tc_fence_after();
+              const uint32_t ua = smem_u32(sA + sa * a_slot);
+              const uint32_t ub = smem_u32(sT + s * t_slot);
+              const uint32_t d = dcol + static_cast<uint32_t>(hh * ncols);
+#pragma unroll
+              for (int k = 0; k < BK / 16; ++k) {
+                const uint64_t ad = sdesc_sw<BK>(ua + k * 32);
+                const uint64_t bd = sdesc_sw<BK>(ub + k * 32);
+                if constexpr (PAIR)
+                  tc_mma2_bf16(d, ad, bd, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+                else
+                  tc_mma_bf16(d, ad, bd, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+                if constexpr (SPLIT) {
+                  tc_mma_bf16(d, ad, sdesc_sw<BK>(ub + t_part + k * 32), idesc, 1u);
+                  tc_mma_bf16(d, sdesc_sw<BK>(ua + kAs + k * 32), bd, idesc, 1u);
+                }
+              }
+              commit(tempty + s);
             }
-            commit(tempty + s);
+            if (!ok) break;
+            if (u == U - 1) commit(afree + sa);  // the last unit has used this k-block
           }
           if (!ok) break;
-          commit(afree + sa);
+          commit(acc_full + as);
         }
-        if (!ok) break;
-        commit(acc_full);
       }
-      if (tl > 0) wait_x(acc_empty, (tl - 1) & 1, DEV_ERR_TIMEOUT_MMA);
+      // the epilogue's releases of the last units (from both CTAs) have landed
+      for (int k = (un > AS ? un - AS : 0); k < un; ++k) wait_x(acc_empty + k % AS, (k / AS) & 1, DEV_ERR_TIMEOUT_MMA);
     }
   } else if (warp < kFill0) {
     // epilogue: accumulator row = signal, columns = output degrees of freedom
     const int q = warp & 3;
     const int g = (warp - 2) >> 2;  // column group of the quadrant
     const uint32_t acc_empty0 = PAIR ? cluster_addr(acc_empty, 0) : 0u;
-    int tl = 0;
-    for (long long t = cid; t < tiles; t += ncl, ++tl) {
+    int un = 0;
+    bool ok = true;
+    for (long long t = cid; t < tiles && ok; t += ncl) {
       int b, i0;
       unit_tile(t, b, i0);
       const int i = i0 + q * 32 + lane;
-      if (!mbar_wait_bounded(acc_full, tl & 1, a.status, DEV_ERR_TIMEOUT_MMA)) break;
-      tc_fence_after();
-      const uint32_t tbase = tmem + (static_cast<uint32_t>(q * 32) << 16);
       __nv_bfloat162* out = a.vhat + static_cast<long long>(b) * a.vld_b + i;
       __nv_bfloat162* out_lo = SPLIT ? a.vhat_lo + static_cast<long long>(b) * a.vld_b + i : nullptr;
       auto put1 = [&](long long off, float re, float im) {
@@ -1284,38 +1307,121 @@ __global__ void __launch_bounds__(rt_threads(SPLIT), 1)
         put1(off, re, im);
         if (a.conj_row > 0) put1(off + a.conj_row, im, -re);  // row 2b + 1 of the conjugate embedding
       };
-      // K = 2 Nt is a multiple of 64 for every supported Nt (32..256)
-      for (int c0 = 64 * g; c0 < K; c0 += 64 * EPW) {
-        float v[64];
-        tmem_ld64(tbase + c0, v);
-        if (i >= a.Ng) continue;
+      for (int u = 0; u < U; ++u, ++un) {
+        const int as = un % AS;
+        if (!mbar_wait_bounded(acc_full + as, (un / AS) & 1, a.status, DEV_ERR_TIMEOUT_MMA)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t tbase = tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(as * ucols);
+        const int cb = hout ? u * ncols : 0;  // first output column of the unit
+        // K = 2 Nt is a multiple of 64 for every supported Nt (32..256)
+        for (int c0 = 64 * g; c0 < ucols; c0 += 64 * EPW) {
+          float v[64];
+          tmem_ld64(tbase + c0, v);
+          if (i >= a.Ng) continue;
+          const int oc = cb + c0;
 #pragma unroll
-        for (int k = 0; k < 32; ++k) {
-          const int l = c0 / 2 + k;
-          if (l == 0) {
-            put(0, v[0], 0.f);
-            put(static_cast<long long>(Nt) * a.vld_l, v[1], 0.f);
-          } else {
-            put(static_cast<long long>(l) * a.vld_l, v[2 * k], v[2 * k + 1]);
+          for (int k = 0; k < 32; ++k) {
+            const int l = oc / 2 + k;
+            if (l == 0) {
+              put(0, v[0], 0.f);
+              put(static_cast<long long>(Nt) * a.vld_l, v[1], 0.f);
+            } else {
+              put(static_cast<long long>(l) * a.vld_l, v[2 * k], v[2 * k + 1]);
+            }
           }
         }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) {
+          if constexpr (PAIR)
+            mbar_arrive_cluster(acc_empty0 + 8u * static_cast<uint32_t>(as));
+          else
+            mbar_arrive(acc_empty + as);
+        }
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) {
-        if constexpr (PAIR)
-          mbar_arrive_cluster(acc_empty0);
-        else
-          mbar_arrive(acc_empty);
+    }
+  } else if constexpr (!SPLIT) {
+    // fill warps (BF16): warp f fills k-blocks f, f + 8, ... of every tile
+    // (k-block kb holds bins 32 kb .. 32 kb + 31 for 128 signals; K slot 1
+    // of bin 0 carries Re(bin Nt)), two batches of 16 bins each with 64
+    // loads in flight per lane.  The first batch is loaded before the wait
+    // for the slot, so its HBM latency overlaps the MMAs that still read the
+    // slot; 16-byte chunks are stored in the TMA 128-byte swizzle pattern
+    // (chunk ^ (row & 7)).
+    const int f = warp - kFill0;
+    const uint32_t afull0 = PAIR ? cluster_addr(afull, 0) : 0u;
+    int tl = 0;
+    bool ok = true;
+    for (long long t = cid; t < tiles && ok; t += ncl, ++tl) {
+      int b, i0;
+      unit_tile(t, b, i0);
+      const unsigned* mbb = reinterpret_cast<const unsigned*>(a.mhat_bf) + static_cast<long long>(b) * a.ld_b;
+      for (int kb = f; kb < KB && ok; kb += kRtFillWarps) {
+        const long long n = static_cast<long long>(tl) * KB + kb;
+        const int sa = static_cast<int>(n % RA);
+        unsigned raw[16][4];
+        auto load = [&](int hh) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const long long lo = static_cast<long long>(kb * kBins + 16 * hh + j) * a.ld_l;
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+              const int i = i0 + 32 * g + lane;
+              raw[j][g] = i < a.Ng ? __ldg(mbb + lo + i) : 0u;
+            }
+          }
+        };
+        unsigned char* slot = sA + sa * a_slot;
+        auto store = [&](int hh) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+              const int row = 32 * g + lane;
+              *reinterpret_cast<uint4*>(slot + row * 128 + (((4 * hh + c) ^ (row & 7)) << 4)) =
+                  make_uint4(raw[4 * c][g], raw[4 * c + 1][g], raw[4 * c + 2][g], raw[4 * c + 3][g]);
+            }
+          }
+        };
+        load(0);
+        if (kb == 0) {
+#pragma unroll
+          for (int g = 0; g < 4; ++g) {
+            const int i = i0 + 32 * g + lane;
+            const unsigned rn = i < a.Ng ? __ldg(mbb + static_cast<long long>(Nt) * a.ld_l + i) : 0u;
+            raw[0][g] = (raw[0][g] & 0xffffu) | (rn << 16);  // K slot 1: Re(bin Nt)
+          }
+        }
+        if (n >= RA &&
+            !mbar_wait_bounded(afree + sa, static_cast<int>(((n / RA) - 1) & 1), a.status, DEV_ERR_TIMEOUT_EMPTY)) {
+          ok = false;
+          break;
+        }
+        store(0);
+#pragma unroll
+        for (int hh = 1; hh < kBins / 16; ++hh) {
+          load(hh);
+          store(hh);
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          if constexpr (PAIR)
+            mbar_arrive_cluster(afull0 + 8u * static_cast<uint32_t>(sa));
+          else
+            mbar_arrive(afull + sa);
+        }
       }
     }
   } else {
-    // fill warps: warp f fills k-blocks f, f + 8, ... of every tile (k-block
-    // kb holds bins kBins kb .. kBins kb + kBins - 1 for 128 signals; K slot 1
-    // of bin 0 carries Re(bin Nt)); all of a tile's loads are in flight
-    // together; 16-byte chunks are stored in the TMA swizzle pattern
+    // fill warps (split): warp f fills k-blocks f, f + 8, ... of every tile
+    // (k-block kb holds bins kBins kb .. kBins kb + kBins - 1 for 128 signals;
+    // K slot 1 of bin 0 carries Re(bin Nt)); all of a tile's loads are in
+    // flight together; 16-byte chunks are stored in the TMA swizzle pattern
     const int f = warp - kFill0;
-    const uint32_t afull0 = PAIR ? cluster_addr(afull, 0) : 0u;
     int tl = 0;
     bool ok = true;
     for (long long t = cid; t < tiles && ok; t += ncl, ++tl) {
@@ -1330,100 +1436,57 @@ __global__ void __launch_bounds__(rt_threads(SPLIT), 1)
           break;
         }
         unsigned char* slot = sA + sa * a_slot;
-        auto chunk_off = [&](int row, int chunk) {  // 16-byte chunk `chunk` of K-major row `row`
-          return BK == 64 ? row * 128 + ((chunk ^ (row & 7)) << 4) : row * 64 + ((chunk ^ ((row >> 1) & 3)) << 4);
+        auto chunk_off = [&](int row, int chunk) {  // 16-byte chunk `chunk` of K-major row `row` (64-byte swizzle)
+          return row * 64 + ((chunk ^ ((row >> 1) & 3)) << 4);
         };
-        if constexpr (!SPLIT) {
-          const unsigned* mbb = reinterpret_cast<const unsigned*>(a.mhat_bf) + static_cast<long long>(b) * a.ld_b;
-          unsigned rawn[4] = {0u, 0u, 0u, 0u};
-          if (kb == 0) {
+        const float2* mb = a.mhat32 + static_cast<long long>(b) * a.ld_b;
+        float rawn[4] = {0.f, 0.f, 0.f, 0.f};
+        if (kb == 0) {
+#pragma unroll
+          for (int g = 0; g < 4; ++g) {
+            const int i = i0 + 32 * g + lane;
+            rawn[g] = i < a.Ng ? __ldg(mb + static_cast<long long>(Nt) * a.ld_l + i).x : 0.f;
+          }
+        }
+#pragma unroll
+        for (int hh = 0; hh < kBins / 8; ++hh) {  // 8 bins per batch, 32 float2 loads in flight
+          float2 raw[8][4];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const long long lo = static_cast<long long>(kb * kBins + 8 * hh + j) * a.ld_l;
 #pragma unroll
             for (int g = 0; g < 4; ++g) {
               const int i = i0 + 32 * g + lane;
-              rawn[g] = i < a.Ng ? __ldg(mbb + static_cast<long long>(Nt) * a.ld_l + i) : 0u;
+              raw[j][g] = i < a.Ng ? __ldg(mb + lo + i) : make_float2(0.f, 0.f);
             }
           }
+          if (kb == 0 && hh == 0) {
 #pragma unroll
-          for (int hh = 0; hh < kBins / 16; ++hh) {  // 16 bins per batch, 64 loads in flight
-            unsigned raw[16][4];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const long long lo = static_cast<long long>(kb * kBins + 16 * hh + j) * a.ld_l;
-#pragma unroll
-              for (int g = 0; g < 4; ++g) {
-                const int i = i0 + 32 * g + lane;
-                raw[j][g] = i < a.Ng ? __ldg(mbb + lo + i) : 0u;
-              }
-            }
-            if (kb == 0 && hh == 0) {
-#pragma unroll
-              for (int g = 0; g < 4; ++g) raw[0][g] = (raw[0][g] & 0xffffu) | (rawn[g] << 16);
-            }
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-#pragma unroll
-              for (int g = 0; g < 4; ++g) {
-                const int row = 32 * g + lane;
-                *reinterpret_cast<uint4*>(slot + chunk_off(row, 4 * hh + c)) =
-                    make_uint4(raw[4 * c][g], raw[4 * c + 1][g], raw[4 * c + 2][g], raw[4 * c + 3][g]);
-              }
-            }
+            for (int g = 0; g < 4; ++g) raw[0][g].y = rawn[g];  // K slot 1: Re(bin Nt)
           }
-        } else {
-          const float2* mb = a.mhat32 + static_cast<long long>(b) * a.ld_b;
-          float rawn[4] = {0.f, 0.f, 0.f, 0.f};
-          if (kb == 0) {
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {  // chunk 2 hh + c = bins 8 hh + 4 c .. + 3
 #pragma unroll
             for (int g = 0; g < 4; ++g) {
-              const int i = i0 + 32 * g + lane;
-              rawn[g] = i < a.Ng ? __ldg(mb + static_cast<long long>(Nt) * a.ld_l + i).x : 0.f;
-            }
-          }
+              const int row = 32 * g + lane;
+              unsigned hw[4], lw[4];
 #pragma unroll
-          for (int hh = 0; hh < kBins / 8; ++hh) {  // 8 bins per batch, 32 float2 loads in flight
-            float2 raw[8][4];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              const long long lo = static_cast<long long>(kb * kBins + 8 * hh + j) * a.ld_l;
-#pragma unroll
-              for (int g = 0; g < 4; ++g) {
-                const int i = i0 + 32 * g + lane;
-                raw[j][g] = i < a.Ng ? __ldg(mb + lo + i) : make_float2(0.f, 0.f);
+              for (int e = 0; e < 4; ++e) {
+                const float2 x = raw[4 * c + e][g];
+                const __nv_bfloat162 h2 = __floats2bfloat162_rn(x.x, x.y);
+                const __nv_bfloat162 l2 = __floats2bfloat162_rn(x.x - __low2float(h2), x.y - __high2float(h2));
+                hw[e] = *reinterpret_cast<const unsigned*>(&h2);
+                lw[e] = *reinterpret_cast<const unsigned*>(&l2);
               }
-            }
-            if (kb == 0 && hh == 0) {
-#pragma unroll
-              for (int g = 0; g < 4; ++g) raw[0][g].y = rawn[g];  // K slot 1: Re(bin Nt)
-            }
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {  // chunk 2 hh + c = bins 8 hh + 4 c .. + 3
-#pragma unroll
-              for (int g = 0; g < 4; ++g) {
-                const int row = 32 * g + lane;
-                unsigned hw[4], lw[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                  const float2 x = raw[4 * c + e][g];
-                  const __nv_bfloat162 h2 = __floats2bfloat162_rn(x.x, x.y);
-                  const __nv_bfloat162 l2 = __floats2bfloat162_rn(x.x - __low2float(h2), x.y - __high2float(h2));
-                  hw[e] = *reinterpret_cast<const unsigned*>(&h2);
-                  lw[e] = *reinterpret_cast<const unsigned*>(&l2);
-                }
-                const int off = chunk_off(row, 2 * hh + c);
-                *reinterpret_cast<uint4*>(slot + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                *reinterpret_cast<uint4*>(slot + kAs + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-              }
+              const int off = chunk_off(row, 2 * hh + c);
+              *reinterpret_cast<uint4*>(slot + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+              *reinterpret_cast<uint4*>(slot + kAs + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
             }
           }
         }
         fence_proxy_async_smem();
         __syncwarp();
-        if (lane == 0) {
-          if constexpr (PAIR)
-            mbar_arrive_cluster(afull0 + 8u * static_cast<uint32_t>(sa));
-          else
-            mbar_arrive(afull + sa);
-        }
+        if (lane == 0) mbar_arrive(afull + sa);
       }
     }
   }
@@ -1697,7 +1760,7 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
 
 cudaError_t launch_tc_retransform(const CUtensorMap& tmT, const CUtensorMap* tmT2, const TcRtArgs& a, int num_sms,
                                   cudaStream_t st, const CUtensorMap* tmTp) {
-  if (a.Nt < 32 || a.Nt > 256) return cudaErrorInvalidValue;
+  if (a.Nt < 32 || a.Nt > 256 || a.Nt % 32 != 0) return cudaErrorInvalidValue;
   const int mtiles = (a.Ng + kBlockM - 1) / kBlockM;
   const long long tiles = static_cast<long long>(a.Bs) * mtiles;
   if (tiles <= 0) return cudaSuccess;
@@ -1711,14 +1774,12 @@ cudaError_t launch_tc_retransform(const CUtensorMap& tmT, const CUtensorMap* tmT
   const size_t a_slot = static_cast<size_t>(kBlockM) * BK * 2 * (split ? 2 : 1);
   const size_t t_slot = static_cast<size_t>(pair ? ncols / 2 : ncols) * BK * 2 * (split ? 2 : 1);
   TcRtArgs aa = a;
-  aa.ra = kRtFillWarps;  // one A slot per fill warp (see the kernel)
-  // T slots fill the opt-in shared memory left by the A ring: three at
-  // Nt = 256 (two within 200 KB; the split kernel's 256-rupture batch went
-  // 24.4 -> 20.8 ms, BF16 unchanged)
-  aa.rt = static_cast<int>((kSmemOptInLimit - 1024 - 8 * (2 * 8 + 2 * 4 + 2) - 16 - aa.ra * a_slot) / t_slot);
+  aa.ra = kRtFillWarps;  // k-block slots of A: a whole tile (BF16), one per fill warp (split)
+  // T slots fill the opt-in shared memory left by the A ring (up to four)
+  aa.rt = static_cast<int>((kSmemOptInLimit - 1024 - (8 * (2 * aa.ra + 2 * 4 + 4) + 16) - aa.ra * a_slot) / t_slot);
   if (aa.rt > 4) aa.rt = 4;
   if (aa.rt < 2) return cudaErrorInvalidValue;
-  const size_t smem = 1024 + aa.ra * a_slot + aa.rt * t_slot + 8 * (2 * aa.ra + 2 * aa.rt + 2) + 16;
+  const size_t smem = 1024 + aa.ra * a_slot + aa.rt * t_slot + 8 * (2 * aa.ra + 2 * aa.rt + 4) + 16;
   if (pair) {
     const void* kfn = reinterpret_cast<const void*>(k_tc_retransform<false, true>);
     cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));

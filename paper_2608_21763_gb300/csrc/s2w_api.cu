@@ -71,7 +71,9 @@ struct s2w_ctx {
   int tc_n2 = 0;         // B-operand rows of stage 2 (2 x No, padded)
   long long Ng_pad2 = 0; // complex columns per row of the stage-2 operands
   int tc_kbpc = 64;      // K blocks per stage-2 chunk
-  int tc_nkc = 1;        // stage-2 K chunks (<= kMaxS2Chunks, the partials' allocation)
+  int tc_nkc = 1;        // stage-2 K chunks (<= s2_max_chunks, the partials' allocation)
+  int s2_min_chunks = 1;  // fewest stage-2 chunks the default and the autotuner take (split: kSplitChunkK)
+  int s2_max_chunks = 0;  // stage-2 chunks the partials are sized for
   int tc_pair = 0;       // 1: two-SM MMAs (CTA pairs per M = 256 tile) where the shape allows; kPairAuto: for N = 512
   bool tc_rtpair = false;  // two-SM tiles for the BF16 retransform GEMM
   int tc_min_batch = 2;  // AUTO: smallest B on the tensor engine
@@ -116,7 +118,7 @@ struct s2w_ctx {
   bool tc_f8act = false;    // FP8 operator x FP8 activations on stage 1 (opts.tc_fp8_act 1 or 2)
   bool tc_f8lo = false;     // ... with the activations as hi + lo e4m3 parts (opts.tc_fp8_act = 2)
   float* tc_colscale = nullptr;  // [Nb][tc_n1max / 2] per-(bin, rupture) scales of the FP8 B operand
-  void* tc_mhat = nullptr;  // [Nb][b][Ng] BF16 pairs (complex FP32 when split)
+  void* tc_mhat = nullptr;  // BF16: [Nb][b][Ng_pad2] (Re, Im) pairs; split (and the adjoint): [Nb][b][Ng] complex FP32
   void* tc_vhat = nullptr;  // [Nb][tc_bsub][Ng_pad2] bf16 pairs
   float2* tc_part = nullptr;  // [Nb][nkc][b][No] complex FP32
   void* tc_p2 = nullptr;    // [Nb][tc_n2][Ng_pad2] bf16 pairs
@@ -208,6 +210,13 @@ constexpr int kDefaultPair = kPairAuto;
 // Largest stage-2 split-K chunk count (the tensor partials are sized for it,
 // so s2w_autotune and opts.tc_s2_chunks can pick any count up to it).
 constexpr int kMaxS2Chunks = 16;
+// The split precision's stage-2 chunks hold at most this many K elements by
+// default: each chunk is one FP32 accumulation in tensor memory, and at the
+// split's error level the length of that accumulation shows (963 x 60,000 x
+// 64 x 256, 256 ruptures: one chunk of 120,000 K elements 9.9e-5 rel-L2,
+// seven 2.0e-5, against 5.2e-6 from the rounding of the split operands
+// alone).  Its partials are sized for the chunk count this takes.
+constexpr long long kSplitChunkK = 2048;
 
 // Form of one tensor GEMM; sets the ring depth and TMEM columns of `a` and
 // returns the B tensor map's box rows.  With `pair` (1, or kPairAuto and
@@ -227,21 +236,22 @@ int tc_shape(TcArgs& a, int N, int m_tiles, int split, int fp8, int pair) {
   return a.cta2 ? slice / 2 : slice;
 }
 
-// Stage-2 split-K over the grid: the chunk count `want` (1..kMaxS2Chunks), or
-// for want = 0 the count that minimises rounds x chunk length over the
-// persistent CTAs for units = bins x M-tile groups (pairs of 128-row tiles
-// when the GEMM takes them) x K chunks, with a small fixed cost per unit
-// (pipeline fill and accumulator drain).  Sets tc_kbpc and tc_nkc.
+// Stage-2 split-K over the grid: the chunk count `want` (1..s2_max_chunks), or
+// for want = 0 the count from s2_min_chunks up that minimises rounds x chunk
+// length over the persistent CTAs for units = bins x M-tile groups (pairs of
+// 128-row tiles when the GEMM takes them) x K chunks, with a small fixed cost
+// per unit (pipeline fill and accumulator drain).  Sets tc_kbpc and tc_nkc.
 void set_s2_chunks(s2w_ctx* ctx, int want) {
   const int bk2 = tc_block_k(ctx->tc_n2, ctx->tc_split ? 1 : 0);
   const long long nk2 = (2 * ctx->Ng_pad2 + bk2 - 1) / bk2;
+  const long long cmax = std::min<long long>(ctx->s2_max_chunks, nk2);
   long long nkc = want;
   if (nkc <= 0) {
     const long long mt2 = (ctx->tc_bsub + 127) / 128;
     const long long mg2 = (mt2 >= 2 && ctx->tc_n2 <= 256) ? (mt2 + 1) / 2 : mt2;
     double best = 1e300;
     nkc = 1;
-    for (long long c = 1; c <= std::min<long long>(kMaxS2Chunks, nk2); ++c) {
+    for (long long c = std::min<long long>(ctx->s2_min_chunks, cmax); c <= cmax; ++c) {
       const long long units = ctx->Nb * mg2 * c;
       const long long rounds = (units + ctx->num_sms - 1) / ctx->num_sms;
       const double cost = static_cast<double>(rounds) * (1.0 / static_cast<double>(c) + 0.005);
@@ -251,7 +261,7 @@ void set_s2_chunks(s2w_ctx* ctx, int want) {
       }
     }
   }
-  nkc = std::max<long long>(1, std::min<long long>({nkc, nk2, static_cast<long long>(kMaxS2Chunks)}));
+  nkc = std::max<long long>(1, std::min<long long>(nkc, cmax));
   ctx->tc_kbpc = static_cast<int>((nk2 + nkc - 1) / nkc);
   ctx->tc_nkc = static_cast<int>((nk2 + ctx->tc_kbpc - 1) / ctx->tc_kbpc);
 }
@@ -383,9 +393,18 @@ std::vector<double> retransform_matrix(int Nt, int dt_mode, double dt, bool tran
 //   -> tcgen05 stage 2 over grid chunks -> partials -> reduce + IFFT -> q.
 // One tcgen05 GEMM (epilogue 0: FP32 out[l][t][row]) over A [Nb][M][K]
 // and the B operand rows [Nb][n_alloc][K] (BF16; lo parts when split).
+// Stage-1 epilogue writing the BF16 (Re, Im) pairs the GEMM retransform
+// reads to `dst`, [Nb][Bs][Ng_pad2], for Bs ruptures.
+void set_pairs(s2w_ctx* ctx, TcArgs& a, int Bs, void* dst) {
+  a.out = nullptr;
+  a.out_bf = static_cast<__nv_bfloat162*>(dst);
+  a.ld_t = ctx->Ng_pad2;
+  a.ld_l = static_cast<long long>(Bs) * ctx->Ng_pad2;
+}
+
 int tc_gemm_epi0(s2w_ctx* ctx, const void* A, const void* A_lo, long long M, long long K, const void* Bop,
                  const void* B_lo, int n_alloc, int N, int T, float2* out, long long ld_l, long long ld_t,
-                 cudaStream_t st, __nv_bfloat162* out_bf = nullptr) {
+                 cudaStream_t st, bool pairs = false) {
   const int sp = A_lo != nullptr ? 1 : 0;
   CUtensorMap ta, tb, ta2, tb2;
   const int mt = static_cast<int>((M + 127) / 128);
@@ -409,10 +428,13 @@ int tc_gemm_epi0(s2w_ctx* ctx, const void* A, const void* A_lo, long long M, lon
   a.b_lo = sp;
   a.epi = 0;
   a.T = T;
-  a.out = out_bf ? nullptr : out;
-  a.out_bf = out_bf;
-  a.ld_l = ld_l;
-  a.ld_t = ld_t;
+  if (pairs) {
+    set_pairs(ctx, a, T, out);
+  } else {
+    a.out = out;
+    a.ld_l = ld_l;
+    a.ld_t = ld_t;
+  }
   a.status = ctx->d_status;
   CK(launch_tc_gemm(ta, tb, a, ctx->num_sms, st, sp ? &ta2 : nullptr, sp ? &tb2 : nullptr));
   return S2W_OK;
@@ -449,19 +471,21 @@ int adjoint_tensor(s2w_ctx* ctx, const float* r_d, int B, float* g_d, cudaStream
       StageTimer t(ctx, 3, st);
       int rc = tc_gemm_epi0(ctx, ctx->tc_pT, sp ? ctx->tc_pT_lo : nullptr, Ng, 2LL * ctx->NoP, ctx->tc_rb,
                             sp ? ctx->tc_rb_lo : nullptr, ctx->tc_n1max, N1, Bs, what,
-                            static_cast<long long>(Bs) * Ng, Ng, st,
-                            gemm_rt && !sp ? reinterpret_cast<__nv_bfloat162*>(what) : nullptr);
+                            static_cast<long long>(Bs) * Ng, Ng, st, gemm_rt && !sp);
       if (rc != S2W_OK) return rc;
     }
     if (gemm_rt) {  // uhat as the conjugate-embedding B operand: rows 2b, 2b+1 of [l][n1max][Ng_pad2]
       StageTimer t(ctx, 2, st);
       TcRtArgs r{};
-      if (sp)
+      if (sp) {
         r.mhat32 = what;
-      else
+        r.ld_l = static_cast<long long>(Bs) * Ng;
+        r.ld_b = Ng;
+      } else {
         r.mhat_bf = reinterpret_cast<const __nv_bfloat162*>(what);
-      r.ld_l = static_cast<long long>(Bs) * Ng;
-      r.ld_b = Ng;
+        r.ld_l = static_cast<long long>(Bs) * ctx->Ng_pad2;
+        r.ld_b = ctx->Ng_pad2;
+      }
       r.Ng = static_cast<int>(Ng);
       r.Bs = Bs;
       r.Nt = static_cast<int>(Nt);
@@ -557,9 +581,7 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
       a.nblk = ctx->nblk;
       a.epi = 0;
       a.T = Bs;
-      a.out_bf = static_cast<__nv_bfloat162*>(ctx->tc_mhat);
-      a.ld_l = static_cast<long long>(Bs) * Ng;
-      a.ld_t = Ng;
+      set_pairs(ctx, a, Bs, ctx->tc_mhat);
       a.status = ctx->d_status;
       CK(launch_tc_gemm(ta, tb, a, ctx->num_sms, st, nullptr, lo ? &tb2 : nullptr, ctx->tc_colscale,
                         ctx->tc_n1max / 2));
@@ -595,25 +617,32 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
       }
       a.epi = 0;
       a.T = Bs;
-      // the GEMM retransform rounds the seafloor spectra to BF16 anyway; the
-      // split path keeps them in FP32 and splits them into hi + lo itself
-      a.out = sp ? static_cast<float2*>(ctx->tc_mhat) : nullptr;
-      a.out_bf = sp ? nullptr : static_cast<__nv_bfloat162*>(ctx->tc_mhat);
-      a.ld_l = static_cast<long long>(Bs) * Ng;
-      a.ld_t = Ng;
+      // the GEMM retransform rounds the seafloor spectra to BF16 anyway (BF16
+      // pairs, its TMA operand); the split path keeps them in FP32 and
+      // splits them into hi + lo itself
+      if (sp) {
+        a.out = static_cast<float2*>(ctx->tc_mhat);
+        a.ld_l = static_cast<long long>(Bs) * Ng;
+        a.ld_t = Ng;
+      } else {
+        set_pairs(ctx, a, Bs, ctx->tc_mhat);
+      }
       a.status = ctx->d_status;
       CK(launch_tc_gemm(ta, tb, a, ctx->num_sms, st, sp ? &ta2 : nullptr, sp ? &tb2 : nullptr));
     }
     {
       StageTimer t(ctx, 2, st);
       TcRtArgs r{};
-      if (sp)
+      if (sp) {
         r.mhat32 = static_cast<const float2*>(ctx->tc_mhat);
-      else
+        r.ld_l = static_cast<long long>(Bs) * Ng;
+        r.ld_b = Ng;
+      } else {
         r.mhat_bf = reinterpret_cast<const __nv_bfloat162*>(ctx->tc_mhat);
+        r.ld_l = static_cast<long long>(Bs) * ctx->Ng_pad2;
+        r.ld_b = ctx->Ng_pad2;
+      }
       r.vhat_lo = static_cast<__nv_bfloat162*>(ctx->tc_vhat_lo);
-      r.ld_l = static_cast<long long>(Bs) * Ng;
-      r.ld_b = Ng;
       r.Ng = static_cast<int>(Ng);
       r.Bs = Bs;
       r.Nt = static_cast<int>(Nt);
@@ -884,6 +913,13 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
     if (ctx->tc_n1max > 256) ctx->tc_n1max = 512;
     ctx->tc_n2 = static_cast<int>(round_up(2 * No, 16));
     ctx->Ng_pad2 = round_up(Ng, 8);
+    ctx->s2_max_chunks = kMaxS2Chunks;
+    if (ctx->tc_split) {
+      const int bk2 = tc_block_k(ctx->tc_n2, 1);
+      const long long k2 = (2 * ctx->Ng_pad2 + bk2 - 1) / bk2 * bk2;
+      ctx->s2_min_chunks = static_cast<int>((k2 + kSplitChunkK - 1) / kSplitChunkK);
+      ctx->s2_max_chunks = std::max(kMaxS2Chunks, ctx->s2_min_chunks);
+    }
     set_s2_chunks(ctx, o.tc_s2_chunks);
     const long long bs = ctx->tc_bsub;
     const bool sp = ctx->tc_split;
@@ -897,7 +933,8 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
     ctx->tc_adj = o.tc_adjoint != 0;
     // FP32 seafloor spectra for the split path, and for the adjoint's what
     const bool mhat32 = sp || ctx->tc_adj;
-    if ((e = dalloc(&ctx->tc_mhat, (mhat32 ? sizeof(float2) : sizeof(__nv_bfloat162)) * Nb * bs * Ng)) !=
+    const size_t mh_pairs = sizeof(__nv_bfloat162) * Nb * bs * ctx->Ng_pad2;  // the BF16 retransform's TMA operand
+    if ((e = dalloc(&ctx->tc_mhat, std::max<size_t>((mhat32 ? sizeof(float2) * Nb * bs * Ng : 0), mh_pairs))) !=
         cudaSuccess)
       return bad(e, "tensor seafloor spectra");
     if (ctx->tc_adj) {
@@ -922,7 +959,7 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
     }
     if ((e = dalloc(&ctx->tc_vhat, 4ull * Nb * bs * ctx->Ng_pad2)) != cudaSuccess)
       return bad(e, "tensor velocity spectra");
-    if ((e = dalloc(&ctx->tc_part, sizeof(float2) * Nb * kMaxS2Chunks * bs * No)) != cudaSuccess)
+    if ((e = dalloc(&ctx->tc_part, sizeof(float2) * Nb * ctx->s2_max_chunks * bs * No)) != cudaSuccess)
       return bad(e, "tensor stage-2 partials");
     if ((e = dalloc(&ctx->tc_p2, 4ull * Nb * ctx->tc_n2 * ctx->Ng_pad2)) != cudaSuccess)
       return bad(e, "tensor stage-2 operand");
@@ -1679,7 +1716,8 @@ int s2w_autotune(s2w_ctx* ctx, int B, s2w_tuning* out, void* stream) {
   if (tensor && !ctx->tune_cache.empty()) {
     int b = 0, p = 0, c = 0, m = 0;
     if (tune_cache_read(ctx->tune_cache, key, &b, &p, &c, &m) && b >= 1 && b <= ctx->tc_bsub_max &&
-        (p == S2W_PAIR_AUTO || p == S2W_PAIR_ON || p == S2W_PAIR_OFF) && c >= 1 && c <= kMaxS2Chunks && m >= 1) {
+        (p == S2W_PAIR_AUTO || p == S2W_PAIR_ON || p == S2W_PAIR_OFF) && c >= 1 && c <= ctx->s2_max_chunks &&
+        m >= 1) {
       ctx->tc_bsub = b;
       ctx->tc_pair = pair_code(p);
       set_s2_chunks(ctx, c);
@@ -1754,11 +1792,15 @@ int s2w_autotune(s2w_ctx* ctx, int B, s2w_tuning* out, void* stream) {
     set_s2_chunks(ctx, ctx->opts.tc_s2_chunks);
     r.tc_bsub = best_b;
     r.tc_pair = best_p;
-    // 2. the stage-2 K chunk count around the round-balance choice
+    // 2. the stage-2 K chunk count around the round-balance choice.  The
+    // split precision tries no count below it (it starts at the chunk
+    // length kSplitChunkK: see there)
     int best_c = ctx->tc_nkc;
     if (rc == S2W_OK && ctx->opts.tc_s2_chunks == 0) {
       const int h = ctx->tc_nkc;
-      const int cand[4] = {h, std::max(1, h / 2), std::min(kMaxS2Chunks, 2 * h), 1};
+      const bool longer_ok = !ctx->tc_split;
+      const int cand[4] = {h, longer_ok ? std::max(1, h / 2) : h, std::min(ctx->s2_max_chunks, 2 * h),
+                           longer_ok ? 1 : h};
       float best_s2 = 1e30f;
       for (int k = 0; k < 4 && rc == S2W_OK; ++k) {
         bool dup = false;

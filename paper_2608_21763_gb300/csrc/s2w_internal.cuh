@@ -314,7 +314,7 @@ cudaError_t launch_pack_a(const float2* src, int Nb, int rows, long long nc, lon
 // reads mhat[l*ld_l + b*ld_b + i], writes vhat[l*vld_l + b*vld_b + i] (BF16
 // pairs); tmT: T[n][k], 2 Nt x 2 Nt BF16, K-major.  32 <= Nt <= 256.
 struct TcRtArgs {
-  const __nv_bfloat162* mhat_bf;  // seafloor spectra, BF16 (re, im) pairs
+  const __nv_bfloat162* mhat_bf;  // seafloor spectra, BF16 (re, im) pairs [l][b][i]
   const float2* mhat32;           // split: seafloor spectra, FP32 (same indexing)
   long long ld_l, ld_b;
   int Ng, Bs, Nt;
@@ -332,6 +332,5 @@ struct TcRtArgs {
 // which selects two-SM tiles when the grid spans at least two M tiles.
 cudaError_t launch_tc_retransform(const CUtensorMap& tmT, const CUtensorMap* tmT2, const TcRtArgs& a, int num_sms,
                                   cudaStream_t st, const CUtensorMap* tmTp = nullptr);
-
 
 }  // namespace s2w

@@ -23,14 +23,23 @@ import numpy as np
 
 
 def bf16(x):
-    x = np.asarray(x, np.float64).astype(np.float32)
-    u = x.view(np.uint32).astype(np.uint64)
-    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
-    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+    """Round to BF16 (nearest even) through FP32, as the kernels round FP32
+    values: add 0x7FFF plus the kept part's last bit to the FP32 pattern and
+    clear the low 16 bits (no carry past bit 31 for finite values)."""
+    f = np.array(x, np.float64).astype(np.float32)
+    u = f.view(np.uint32)
+    u += (u >> 16) & np.uint32(1)
+    u += np.uint32(0x7FFF)
+    u &= np.uint32(0xFFFF0000)
+    return f.astype(np.float64)
 
 
 def cplx(f, z):
-    return f(z.real) + 1j * f(z.imag)
+    """f applied to the real and the imaginary parts (the memory layout of z kept)."""
+    out = np.empty_like(z)
+    out.real = f(z.real)
+    out.imag = f(z.imag)
+    return out
 
 
 def bf16c(z):
@@ -117,24 +126,40 @@ def to_dofs(X, Nt):
     return u
 
 
+def ein1(g, s):
+    """m[b][i][l] = sum_j g[i][j][l] s[b][j][l]: stage 1 per bin (BLAS over bins)."""
+    return np.matmul(g.transpose(2, 0, 1), s.transpose(2, 1, 0)).transpose(2, 1, 0)
+
+
+def ein2(p, v):
+    """q[b][o][l] = sum_i p[o][i][l] v[b][i][l]: stage 2 per bin."""
+    return np.matmul(p.transpose(2, 0, 1), v.transpose(2, 1, 0)).transpose(2, 1, 0)
+
+
 def model_waveforms(G, P, slip, path):
     """q [B][No][Nt] of the FFT pipeline with `path`'s roundings (see the
     module docstring); G [Ng][Ns][Nt], P [No][Ng][Nt], slip [B][Ns][Nt], all
     FP32-representable inputs as the library receives them."""
     Nt = G.shape[2]
     L = 2 * Nt
-    Gh = np.fft.rfft(G, L, axis=-1)           # [Ng][Ns][Nb]
-    Ph = np.fft.rfft(P, L, axis=-1)           # [No][Ng][Nb]
-    sh = np.fft.rfft(slip, L, axis=-1)        # [B][Ns][Nb]
-    ein1 = lambda g, s: np.einsum('ijl,bjl->bil', g, s)
-    ein2 = lambda p, v: np.einsum('oil,bil->bol', p, v)
+    qh = model_spectra(np.fft.rfft(G, L, axis=-1), np.fft.rfft(P, L, axis=-1), np.fft.rfft(slip, L, axis=-1),
+                       path, retransform_matrix(Nt))
+    return np.fft.irfft(qh, L, axis=-1)[..., :Nt]
 
-    def split_prod(ein, a, b):  # hi*hi + hi*lo + lo*hi of BF16 parts
+
+def model_spectra(Gh, Ph, sh, path, T):
+    """Stage-2 spectra qh [B][No][Nb] of `path` from the operator spectra
+    Gh [Ng][Ns][Nb], Ph [No][Ng][Nb], the slip spectra sh [B][Ns][Nb] and the
+    retransform matrix T.  Except for the FP8 operator's per-(bin, 256-row)
+    scales and the FP16 activations' global scale, every rounding is per
+    element or per signal, so for the other paths the result over a grid is
+    the sum of the results over its row chunks."""
+    Nt = (Gh.shape[2] - 1)
+
+    def split_prod(ein, a, b):  # hi*hi + hi*lo + lo*hi of BF16 parts (lo*lo dropped)
         ah, al = hilo(a)
         bh, bl = hilo(b)
-        return ein(ah, bh) + ein(ah, bl) + ein(al, bh)
-
-    T = retransform_matrix(Nt)
+        return ein(ah, bh + bl) + ein(al, bh)
 
     def retransform(mh, T_used):
         return to_bins(to_dofs(mh, Nt) @ T_used.T, Nt)
@@ -150,28 +175,26 @@ def model_waveforms(G, P, slip, path):
                 Ph = bf16c(Ph)
         mh = ein1(Gh, sh)
         vh = retransform(mh, T)
-        qh = ein2(Ph, vh)
-    elif path == "tensor_bf16":
+        return ein2(Ph, vh)
+    if path == "tensor_bf16":
         mh = bf16c(ein1(bf16c(Gh), bf16c(sh)))
         vh = bf16c(retransform(mh, bf16(T)))
-        qh = ein2(bf16c(Ph), vh)
-    elif path == "tensor_fp8":
-        mh = bf16c(ein1(fp8_rows(Gh), f16c(sh / 2.0 ** np.ceil(np.log2(np.abs(sh).max()))) *
-                        2.0 ** np.ceil(np.log2(np.abs(sh).max()))))
+        return ein2(bf16c(Ph), vh)
+    if path == "tensor_fp8":
+        sc = 2.0 ** np.ceil(np.log2(np.abs(sh).max()))
+        mh = bf16c(ein1(fp8_rows(Gh), f16c(sh / sc) * sc))
         vh = bf16c(retransform(mh, bf16(T)))
-        qh = ein2(bf16c(Ph), vh)
-    elif path == "tensor_fp8_hilo":
+        return ein2(bf16c(Ph), vh)
+    if path == "tensor_fp8_hilo":
         mh = bf16c(ein1(fp8_rows(Gh), e4m3_hilo_cols(sh)))
         vh = bf16c(retransform(mh, bf16(T)))
-        qh = ein2(bf16c(Ph), vh)
-    elif path == "tensor_split":
+        return ein2(bf16c(Ph), vh)
+    if path == "tensor_split":
         mh = split_prod(ein1, Gh, sh)
         Th, Tl = bf16(T), bf16(T - bf16(T))
         mh_h, mh_l = hilo(mh)
         d_h, d_l = to_dofs(mh_h, Nt), to_dofs(mh_l, Nt)
         vh = to_bins(d_h @ Th.T + d_h @ Tl.T + d_l @ Th.T, Nt)
         vh = sum(hilo(vh))
-        qh = split_prod(ein2, Ph, vh)
-    else:
-        raise ValueError(path)
-    return np.fft.irfft(qh, L, axis=-1)[..., :Nt]
+        return split_prod(ein2, Ph, vh)
+    raise ValueError(path)

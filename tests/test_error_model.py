@@ -80,3 +80,21 @@ def test_bar_is_derived_from_the_path_rounding(prepared, bar):
             worst = max(worst, float(e.max()))
     print(f"{bar}: modelled worst error / window {worst:.3g}, bar {BARS[bar]:.3g} ({BARS[bar] / worst:.2f}x)")
     assert 1.5 * worst <= BARS[bar] <= 4.0 * worst
+
+
+def test_full_size_model_is_the_oracle():
+    """The model without rounding, run over the full batched workload's grid
+    in chunks (tests/golden/make_full_size_model.py, operator spectra by an
+    FP64 DFT matrix), gives the FP64 oracle's stored waveforms of the same
+    ruptures: the full-size bars come from a model of the same map."""
+    import os
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    m = np.load(os.path.join(here, "model_batched.npz"))
+    o = np.load(os.path.join(here, "oracle_batched.npz"))
+    assert np.array_equal(m["index"], o["index"]) and np.array_equal(m["draw"], o["draw"])
+    assert np.allclose(m["checksum"], o["checksum"], rtol=1e-12, atol=0.0)
+    n = len(m["index"])
+    rel = np.linalg.norm((m["q_exact"] - o["q"]).reshape(n, -1), axis=1) / np.linalg.norm(o["q"].reshape(n, -1), axis=1)
+    assert rel.max() <= 1e-12, rel
+    for k in ("rel_tensor_bf16", "rel_tensor_split"):
+        assert m[k].shape == (n,) and np.all(m[k] > 0)

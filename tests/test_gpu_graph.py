@@ -125,6 +125,25 @@ def test_autotune_choices_and_selected_path():
     ctx.sync()
 
 
+def test_autotune_split_keeps_short_accumulations():
+    """With the BF16 hi/lo split the autotuner probes no stage-2 chunk count
+    below the round-balance default (the first candidate): fewer chunks mean
+    longer FP32 accumulations, which the split's error level shows."""
+    geom = compact_box(24, 700, 6, seed=24)
+    Nt, B = 64, 40
+    ctx = make_context(s2w, geom, Nt, prec_g="bf16_hilo", prec_p="fp32", max_batch=B)
+    t = ctx.autotune(B)
+    probed = [c["chunks"] for c in t["s2_chunks"]]
+    print("split autotune chunks:", t["s2_chunks"], "chosen", t["tc_s2_chunks"])
+    assert probed and min(probed) == probed[0] and t["tc_s2_chunks"] >= probed[0]
+    s = slips(B, geom.Ns, Nt, 31)
+    G = geom.greens_rows(0, geom.Ng, Nt)
+    P = geom.adjoint_cols(0, geom.Ng, Nt)
+    q = ctx.waveforms(torch.tensor(s, dtype=torch.float32, device="cuda")).cpu().numpy()
+    assert_parity(q, oracle.waveforms(G, P, s), *window_norms(G, P, s), tol=BARS["tensor_split"], label="autotuned split")
+    ctx.sync()
+
+
 def test_autotune_without_tensor_engine():
     wl = synth.WORKLOADS["tiny"]
     geom = wl.geometry_obj()
