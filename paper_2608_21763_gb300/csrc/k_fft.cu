@@ -210,6 +210,20 @@ __global__ void __launch_bounds__(kThreads) k_reduce_irfft(const float2* __restr
                      tw, fl, threadIdx.x, scr);
 }
 
+// part[l][s][e] (l < Nb, s < nseg, e < per): part[l][0][e] becomes the sum
+// over s in increasing order (the order k_reduce_irfft adds them in), read
+// coalesced along e, so that the reduction reads one segment.
+__global__ void k_sum_chunks(float2* __restrict__ part, int Nb, int nseg, long long per) {
+  const long long total = static_cast<long long>(Nb) * per;
+  for (long long e = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    float2* p = part + (e / per) * nseg * per + e % per;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int s = 0; s < nseg; ++s) acc = cadd(acc, p[static_cast<long long>(s) * per]);
+    p[0] = acc;
+  }
+}
+
 // X[l][r] *= (1 - W_L^l) / dt for l <= L/2, r < per_bin: the spectrum of the
 // backward difference, folded into the stage-2 spectra of the single-pass
 // variant (no retransform between the stages; L = 4 Nt leaves no wrap).
@@ -427,6 +441,11 @@ cudaError_t launch_reduce_irfft(const float2* part, int B, int No, int nseg, int
     const size_t sm = sizeof(float2) * (64 * P + 32 * P + 1 + 32 * P);
     k_reduce_irfft<P><<<static_cast<unsigned>(n), kThreads, sm, st>>>(part, No, nseg, s_b, s_l, s_s, tw, q, n_keep);
   });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sum_chunks(float2* part, int Nb, int nseg, long long per, cudaStream_t st) {
+  k_sum_chunks<<<grid_for(Nb * per, 256), 256, 0, st>>>(part, Nb, nseg, per);
   return cudaGetLastError();
 }
 

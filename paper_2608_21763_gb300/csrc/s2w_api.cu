@@ -685,7 +685,14 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
     }
     {
       StageTimer t(ctx, 4, st);
-      CK(launch_reduce_irfft(ctx->tc_part, Bs, static_cast<int>(No), ctx->tc_nkc, static_cast<int>(Nt), No,
+      // many chunks (the split precision): add them up first along the
+      // contiguous (rupture, observation) rows, in the same order
+      int nseg = ctx->tc_nkc;
+      if (nseg > 8) {
+        CK(launch_sum_chunks(ctx->tc_part, static_cast<int>(Nb), nseg, static_cast<long long>(Bs) * No, st));
+        nseg = 1;
+      }
+      CK(launch_reduce_irfft(ctx->tc_part, Bs, static_cast<int>(No), nseg, static_cast<int>(Nt), No,
                              static_cast<long long>(ctx->tc_nkc) * Bs * No, static_cast<long long>(Bs) * No, ctx->tw,
                              q_d + static_cast<long long>(b0) * No * Nt, st));
     }

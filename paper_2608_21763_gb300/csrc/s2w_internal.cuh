@@ -152,6 +152,9 @@ cudaError_t launch_retransform(const float2* mhat, long long Ng, long long ld_m,
 // the first n_keep (0: Nt) samples of the length-2Nt IFFT, rows n_keep apart.
 cudaError_t launch_reduce_irfft(const float2* part, int B, int No, int nseg, int Nt, long long s_b, long long s_l,
                                 long long s_s, const float2* tw, float* q, cudaStream_t st, int n_keep = 0);
+// Partials part[l][s][e] (e < per): part[l][0][e] = sum over s < nseg, in
+// increasing s (the order launch_reduce_irfft adds segments in).
+cudaError_t launch_sum_chunks(float2* part, int Nb, int nseg, long long per, cudaStream_t st);
 // Spectra X[l][r] (l < Nb, r < per_bin) times (1 - W_L^l) / dt, W_L^l = tw[l].
 cudaError_t launch_scale_dt(float2* X, int Nb, long long per_bin, const float2* tw, float inv_dt, cudaStream_t st);
 // r = q - d in place (B blocks of n_per_b floats); loss[b] = 0.5 sum r^2 (optional).

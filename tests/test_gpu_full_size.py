@@ -12,7 +12,12 @@ tests/golden/make_full_size_oracle.py (which calls only oracle/ and synth/).
   largest  963 x 150,000 x 64 x 256, 1,024 ruptures in one call, FP8 e4m3 Ghat
            with per-(bin, 256-row) scales and BF16 Phat; 16 sampled ruptures.
 Reduced-precision paths are held to their bar (helpers.BARS) as a plain
-relative L2 error, which is stricter than the window-relative bar.
+relative L2 error, which is stricter than the window-relative bar.  The
+batched workload also has the rounding model at full size
+(tests/golden/make_full_size_model.py): the BF16 tensor path's measured
+error must be its modelled rounding error (within 0.5x .. 2x per rupture),
+and the split path's at least half its model (the model holds only the
+operand roundings; the FP32 accumulations add to them) and within its bar.
 """
 import os
 
@@ -77,11 +82,24 @@ def test_plain_workload_every_rupture(prec):
     assert np.all(rel <= 1e-5), rel
 
 
+def model(name, path):
+    p = os.path.join(GOLDEN, f"model_{name}.npz")
+    if not os.path.exists(p):
+        pytest.skip(f"no stored rounding model for {name}")
+    return np.load(p)[f"rel_{path}"]
+
+
 @pytest.mark.parametrize("prec_g,prec_p,bar", [("bf16", "bf16", "tensor_bf16"),
                                                ("bf16_hilo", "fp32", "tensor_split")])
 def test_batched_workload_tensor_engine(prec_g, prec_p, bar):
     rel = run("batched", prec_g, prec_p, engine="tensor")
     assert np.all(rel <= BARS[bar]), rel
+    m = model("batched", bar)
+    print(f"modelled rounding error per rupture: {m}")
+    if bar == "tensor_bf16":
+        assert np.all(rel <= 2.0 * m) and np.all(rel >= 0.5 * m), rel / m
+    else:
+        assert np.all(rel >= 0.5 * m), rel / m
 
 
 def test_largest_workload_fp8():
