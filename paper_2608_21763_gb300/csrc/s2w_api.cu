@@ -92,6 +92,10 @@ struct s2w_ctx {
     unsigned long long last_use;
   };
   cudaStream_t cap_stream = nullptr;
+  // host-buffer calls on the tensor engine: copies of one sub-batch overlap
+  // the GEMMs of another (copy stream, one event pair per sub-batch)
+  cudaStream_t copy_stream = nullptr;
+  std::vector<cudaEvent_t> ev_in, ev_out;
   std::vector<GraphEntry> graphs;
   unsigned long long graph_clock = 0;
   // tensor-engine adjoint: transposed spectra, K-major along the grid
@@ -319,6 +323,12 @@ void free_all(s2w_ctx* c) {
   c->graphs.clear();
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   c->cap_stream = nullptr;
+  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+  c->copy_stream = nullptr;
+  for (cudaEvent_t e : c->ev_in) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->ev_out) cudaEventDestroy(e);
+  c->ev_in.clear();
+  c->ev_out.clear();
   for (auto& p : c->pending) {
     cudaEventDestroy(p.a);
     cudaEventDestroy(p.b);
@@ -1234,6 +1244,61 @@ int s2w_load_adjoint_spectra(s2w_ctx* ctx, int g0, int ng, const float* Phat, vo
   return load_adjoint_impl(ctx, g0, ng, Phat, true, stream);
 }
 
+namespace {
+// Tensor engine with host slip and host q, several sub-batches: sub-batch k's
+// slip goes up on the copy stream while sub-batch k - 1 computes on `st`,
+// and its waveforms come down while sub-batch k + 1 computes; the call
+// returns when the last copy has landed.  Same kernels, launch shapes and
+// results as the device-pointer path.
+int waveforms_tensor_host(s2w_ctx* ctx, const float* slip, int B, float* q, cudaStream_t st) {
+  const long long per_in = ctx->Ns * ctx->Nt, per_out = ctx->No * ctx->Nt;
+  const int nsub = (B + ctx->tc_bsub - 1) / ctx->tc_bsub;
+  if (!ctx->copy_stream) CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+  while (static_cast<int>(ctx->ev_in.size()) < nsub) {
+    cudaEvent_t a, b;
+    CK(cudaEventCreateWithFlags(&a, cudaEventDisableTiming));
+    if (cudaEventCreateWithFlags(&b, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventDestroy(a);
+      return fail(ctx, S2W_ERR_CUDA, "waveforms: event creation failed");
+    }
+    ctx->ev_in.push_back(a);
+    ctx->ev_out.push_back(b);
+  }
+  cudaStream_t cs = ctx->copy_stream;
+  // the copy stream starts after the caller's earlier work (the workspaces)
+  CK(cudaEventRecord(ctx->ev_out[0], st));
+  CK(cudaStreamWaitEvent(cs, ctx->ev_out[0], 0));
+  for (int k = 0; k < nsub; ++k) {
+    const long long b0 = static_cast<long long>(k) * ctx->tc_bsub;
+    const int Bs = static_cast<int>(std::min<long long>(ctx->tc_bsub, B - b0));
+    CK(cudaMemcpyAsync(ctx->ws_slip + b0 * per_in, slip + b0 * per_in, sizeof(float) * Bs * per_in,
+                       cudaMemcpyHostToDevice, cs));
+    CK(cudaEventRecord(ctx->ev_in[k], cs));
+  }
+  const int* lens = ctx->cur_lens;
+  int rc = S2W_OK;
+  for (int k = 0; k < nsub && rc == S2W_OK; ++k) {
+    const long long b0 = static_cast<long long>(k) * ctx->tc_bsub;
+    const int Bs = static_cast<int>(std::min<long long>(ctx->tc_bsub, B - b0));
+    CK(cudaStreamWaitEvent(st, ctx->ev_in[k], 0));
+    ctx->cur_lens = lens ? lens + b0 : nullptr;
+    rc = waveforms_tensor(ctx, ctx->ws_slip + b0 * per_in, Bs, ctx->ws_q + b0 * per_out, st);
+    ctx->cur_lens = lens;
+    if (rc != S2W_OK) break;
+    CK(cudaEventRecord(ctx->ev_out[k], st));
+    CK(cudaStreamWaitEvent(cs, ctx->ev_out[k], 0));
+    CK(cudaMemcpyAsync(q + b0 * per_out, ctx->ws_q + b0 * per_out, sizeof(float) * Bs * per_out,
+                       cudaMemcpyDeviceToHost, cs));
+  }
+  // the caller's stream continues after the copies (workspace reuse), and
+  // the host after the last one
+  CK(cudaEventRecord(ctx->ev_in[0], cs));
+  CK(cudaStreamWaitEvent(st, ctx->ev_in[0], 0));
+  CK(cudaStreamSynchronize(cs));
+  return rc;
+}
+}  // namespace
+
 int s2w_waveforms(s2w_ctx* ctx, const float* slip, int B, float* q, float* seafloor, void* stream) {
   if (!ctx) return S2W_ERR_ARG;
   if (B < 0 || B > ctx->opts.max_batch)
@@ -1251,17 +1316,18 @@ int s2w_waveforms(s2w_ctx* ctx, const float* slip, int B, float* q, float* seafl
     return fail(ctx, S2W_ERR_CUDA, "waveforms: kernel launch failed (injected by the LAUNCH test hook)");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const long long Ns = ctx->Ns, Ng = ctx->Ng, No = ctx->No, Nt = ctx->Nt, Nb = ctx->Nb, Ns_pad = ctx->Ns_pad;
+  if (ctx->single_pass && seafloor != nullptr)
+    return fail(ctx, S2W_ERR_UNSUPPORTED, "waveforms: no seafloor output in the single-pass variant");
+  const bool use_tc = ctx->tc_on && seafloor == nullptr && (ctx->tc_split || ctx->tc_T != nullptr) &&
+                      (ctx->opts.engine == S2W_ENGINE_TENSOR || B >= ctx->tc_min_batch);
+  if (use_tc && ks == 0 && kq == 0 && B > ctx->tc_bsub) return waveforms_tensor_host(ctx, slip, B, q, st);
   const float* slip_d = slip;
   if (ks == 0) {
     StageTimer t(ctx, 5, st, 0);
     CK(cudaMemcpyAsync(ctx->ws_slip, slip, sizeof(float) * B * Ns * Nt, cudaMemcpyHostToDevice, st));
     slip_d = ctx->ws_slip;
   }
-  if (ctx->single_pass && seafloor != nullptr)
-    return fail(ctx, S2W_ERR_UNSUPPORTED, "waveforms: no seafloor output in the single-pass variant");
   float* q_d = kq == 1 ? q : ctx->ws_q;
-  const bool use_tc = ctx->tc_on && seafloor == nullptr && (ctx->tc_split || ctx->tc_T != nullptr) &&
-                      (ctx->opts.engine == S2W_ENGINE_TENSOR || B >= ctx->tc_min_batch);
   if (use_tc) {
     int rc = waveforms_tensor(ctx, slip_d, B, q_d, st);
     if (rc != S2W_OK) return rc;

@@ -77,6 +77,21 @@ def test_full_width_batch_and_sub_batches():
     # deterministic: same inputs, same bits
     q2 = ctx.waveforms(torch.tensor(slip, dtype=torch.float32, device="cuda")).cpu().numpy()
     assert np.array_equal(q, q2)
+    # host buffers: the sub-batches' copies overlap the other sub-batches'
+    # GEMMs on an internal stream; same kernels, same bits
+    s32 = np.ascontiguousarray(slip, dtype=np.float32)
+    assert np.array_equal(q, ctx.waveforms(s32))
+    # ... with per-rupture active lengths (each sub-batch gets its own)
+    lens = np.random.default_rng(41).integers(1, 65, size=300)
+    cut = s32.copy()
+    for b, n in enumerate(lens):
+        cut[b, :, n:] = 0
+    want = ctx.waveforms(torch.tensor(cut, device="cuda")).cpu().numpy()
+    junk = cut.copy()
+    for b, n in enumerate(lens):
+        junk[b, :, n:] = 1e30  # never read
+    assert np.array_equal(want, ctx.waveforms_active(junk, lens))
+    ctx.sync()
 
 
 def test_split_k_over_grid_chunks():
