@@ -212,7 +212,9 @@ __device__ __forceinline__ void tc_store_cols(const TcArgs& a, const float* v, i
     for (int k = 0; k < NC; ++k)
       if (k < nt) {
         const float sk = CS ? scale * cs[t0 + k] : scale;
-        p[k * ld] = make_float2(v[2 * k] * sk, v[2 * k + 1] * sk);
+        float2 o = make_float2(v[2 * k] * sk, v[2 * k + 1] * sk);
+        if (a.acc_out) o = cadd(p[k * ld], o);  // K chunk after the first: add into the output
+        p[k * ld] = o;
       }
   }
 }
@@ -356,7 +358,7 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUten
       for (long long u = cid; u < units && ok; u += ncl) {
         int l, mt, kc;
         unit_coords(u, l, mt, kc);
-        const int kb0 = kc * a.kblocks_per_chunk;
+        const int kb0 = a.kb_off + kc * a.kblocks_per_chunk;
         const int kb1 = min(nk_total, kb0 + a.kblocks_per_chunk);
         for (int kb = kb0; kb < kb1; ++kb, ++it) {
           const int s = it % S;
@@ -398,7 +400,7 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUten
       for (long long u = cid; u < units && ok; u += ncl) {
         int l, mt, kc;
         unit_coords(u, l, mt, kc);
-        const int kb0 = kc * a.kblocks_per_chunk;
+        const int kb0 = a.kb_off + kc * a.kblocks_per_chunk;
         const int kb1 = min(nk_total, kb0 + a.kblocks_per_chunk);
         if (acc_it > 0 && !mbar_wait_bounded(acc_empty, (acc_it - 1) & 1, a.status, DEV_ERR_TIMEOUT_MMA)) {
           ok = false;
@@ -449,7 +451,7 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUten
     for (long long u = cid; u < units && ok; u += ncl) {
       int l, mt, kc;
       unit_coords(u, l, mt, kc);
-      const int kb0 = kc * a.kblocks_per_chunk;
+      const int kb0 = a.kb_off + kc * a.kblocks_per_chunk;
       const int kb1 = min(nk_total, kb0 + a.kblocks_per_chunk);
       for (int kb = kb0; kb < kb1; ++kb, ++it) {
         const int s = it % S;
@@ -723,7 +725,7 @@ __device__ __forceinline__ void tc_gemm2_body(const CUtensorMap* tmA, const CUte
       for (long long u = cid; u < units && ok; u += ncl) {
         int l, mt, kc;
         unit_coords(u, l, mt, kc);
-        const int kb0 = kc * a.kblocks_per_chunk;
+        const int kb0 = a.kb_off + kc * a.kblocks_per_chunk;
         const int kb1 = min(nk_total, kb0 + a.kblocks_per_chunk);
         for (int kb = kb0; kb < kb1; ++kb, ++it) {
           const int s = it % S;
@@ -765,7 +767,7 @@ __device__ __forceinline__ void tc_gemm2_body(const CUtensorMap* tmA, const CUte
       for (long long u = cid; u < units && ok; u += ncl) {
         int l, mt, kc;
         unit_coords(u, l, mt, kc);
-        const int kb0 = kc * a.kblocks_per_chunk;
+        const int kb0 = a.kb_off + kc * a.kblocks_per_chunk;
         const int kb1 = min(nk_total, kb0 + a.kblocks_per_chunk);
         if (acc_it > 0 && !mbar_wait_bounded_cl(acc_empty, (acc_it - 1) & 1, a.status, DEV_ERR_TIMEOUT_MMA)) {
           ok = false;
@@ -820,7 +822,7 @@ __device__ __forceinline__ void tc_gemm2_body(const CUtensorMap* tmA, const CUte
     for (long long u = cid; u < units && ok; u += ncl) {
       int l, mt, kc;
       unit_coords(u, l, mt, kc);
-      const int kb0 = kc * a.kblocks_per_chunk;
+      const int kb0 = a.kb_off + kc * a.kblocks_per_chunk;
       const int kb1 = min(nk_total, kb0 + a.kblocks_per_chunk);
       for (int kb = kb0; kb < kb1; ++kb, ++it) {
         const int s = it % S;

@@ -221,6 +221,14 @@ constexpr int kMaxS2Chunks = 16;
 // seven 2.0e-5, against 5.2e-6 from the rounding of the split operands
 // alone).  Its partials are sized for the chunk count this takes.
 constexpr long long kSplitChunkK = 2048;
+// The tensor adjoint's last GEMM (K = the grid) at the split precision runs
+// in launches of at most this many K elements, each adding its FP32 partial
+// into the output: longer accumulations than stage 2's chunks (each launch
+// re-reads and rewrites the output, so fewer of them), short enough for the
+// split's error level (963 x 40,000, rel-L2 of the adjoint: one accumulation
+// ~2e-4; launches of 8,192 elements 2.9e-5 at +4 % gradient time, of 4,096
+// 1.6e-5 at +9 %, of 2,048 9.8e-6 at +21 %).
+constexpr long long kSplitAdjChunkK = 4096;
 
 // Form of one tensor GEMM; sets the ring depth and TMEM columns of `a` and
 // returns the B tensor map's box rows.  With `pair` (1, or kPairAuto and
@@ -412,9 +420,13 @@ void set_pairs(s2w_ctx* ctx, TcArgs& a, int Bs, void* dst) {
   a.ld_l = static_cast<long long>(Bs) * ctx->Ng_pad2;
 }
 
+// chunk_k > 0 (FP32 out): the K extent in launches of at most chunk_k
+// elements each, in order, the first storing and the others adding their
+// FP32 partial into `out` (each launch one FP32 accumulation of chunk_k
+// terms at most).
 int tc_gemm_epi0(s2w_ctx* ctx, const void* A, const void* A_lo, long long M, long long K, const void* Bop,
                  const void* B_lo, int n_alloc, int N, int T, float2* out, long long ld_l, long long ld_t,
-                 cudaStream_t st, bool pairs = false) {
+                 cudaStream_t st, bool pairs = false, long long chunk_k = 0) {
   const int sp = A_lo != nullptr ? 1 : 0;
   CUtensorMap ta, tb, ta2, tb2;
   const int mt = static_cast<int>((M + 127) / 128);
@@ -446,7 +458,14 @@ int tc_gemm_epi0(s2w_ctx* ctx, const void* A, const void* A_lo, long long M, lon
     a.ld_t = ld_t;
   }
   a.status = ctx->d_status;
-  CK(launch_tc_gemm(ta, tb, a, ctx->num_sms, st, sp ? &ta2 : nullptr, sp ? &tb2 : nullptr));
+  const int nk = a.kblocks_per_chunk;
+  const int per = chunk_k > 0 && !pairs ? static_cast<int>(std::max<long long>(1, chunk_k / bk)) : nk;
+  for (int kb = 0; kb < nk; kb += per) {
+    a.kb_off = kb;
+    a.kblocks_per_chunk = std::min(per, nk - kb);
+    a.acc_out = kb > 0 ? 1 : 0;
+    CK(launch_tc_gemm(ta, tb, a, ctx->num_sms, st, sp ? &ta2 : nullptr, sp ? &tb2 : nullptr));
+  }
   return S2W_OK;
 }
 
@@ -516,9 +535,11 @@ int adjoint_tensor(s2w_ctx* ctx, const float* r_d, int B, float* g_d, cudaStream
     }
     {
       StageTimer t(ctx, 1, st);
+      // K = the grid: the split precision keeps each FP32 accumulation
+      // within kSplitAdjChunkK terms
       int rc = tc_gemm_epi0(ctx, ctx->tc_gT, sp ? ctx->tc_gT_lo : nullptr, Ns, 2 * ctx->Ng_pad2, ctx->tc_ub,
                             sp ? ctx->tc_ub_lo : nullptr, ctx->tc_n1max, N1, Bs, ctx->tc_ghat,
-                            static_cast<long long>(Bs) * Ns, Ns, st);
+                            static_cast<long long>(Bs) * Ns, Ns, st, false, sp ? kSplitAdjChunkK : 0);
       if (rc != S2W_OK) return rc;
     }
     {

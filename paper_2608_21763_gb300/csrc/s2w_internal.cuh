@@ -235,6 +235,9 @@ struct TcArgs {
   int m_tiles;            // ceil(M_total / 128)
   int n_kchunks;          // split of the K blocks into chunks (stage 2)
   int kblocks_per_chunk;  // 64-element K blocks per chunk
+  int kb_off;             // first K block (a launch over one K range: chunk kc covers blocks
+                          //   kb_off + kc kblocks_per_chunk ...)
+  int acc_out;            // epi 0, FP32 out: add into out instead of storing (K ranges in turn)
   int stages;             // shared-memory ring depth
   int tmem_cols;          // power of two >= max(32, N)
   int epi;                // 0: out[l*ld_l + t*ld_t + row]; 1: out[((l*n_kchunks + kc)*M_total + row)*T + t]
