@@ -28,7 +28,10 @@
 //              64-column chunk), scale, store.  Four warps per lane quadrant
 //              cut the time the MMAs wait for the accumulator to drain
 //              (with N = 512 it fills tensor memory, so it cannot be
-//              double-buffered); FP8 kernels keep two per quadrant.
+//              double-buffered); FP8 kernels keep two per quadrant.  The
+//              two-SM FP8 x (hi + lo FP8) kernel at N = 512 instead splits
+//              the columns into two 256-column units (n_split) whose
+//              accumulators alternate, so the drain overlaps the MMAs.
 // Every mbarrier wait is bounded (s2w_internal.cuh); on expiry a status bit
 // is latched and the CTA drains and exits.
 #include <cuda.h>
@@ -196,8 +199,8 @@ __host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
 // CS: per-column scales of this bin (FP8 B operand), cs[t].
 template <int NC, bool CS>
 __device__ __forceinline__ void tc_store_cols(const TcArgs& a, const float* v, int t0, long long obase, long long ld,
-                                              bool bf, float scale, const float* cs) {
-  const int nt = a.T - t0;  // live complex columns from t0 (all NC when >= NC)
+                                              bool bf, float scale, const float* cs, int T) {
+  const int nt = T - t0;  // live complex columns from t0 (all NC when >= NC)
   if (bf) {
     __nv_bfloat162* p = a.out_bf + obase + t0 * ld;
 #pragma unroll
@@ -221,22 +224,26 @@ __device__ __forceinline__ void tc_store_cols(const TcArgs& a, const float* v, i
 
 template <int EPW, bool CS = false>
 __device__ __forceinline__ void tc_epilogue_tile(const TcArgs& a, uint32_t tbase, int N, int g, int l, int kc,
-                                                 int row, bool live, float scale, const float* cs = nullptr) {
+                                                 int row, bool live, float scale, const float* cs = nullptr,
+                                                 int t_off = 0) {
   const bool bf = a.epi == 0 && a.out_bf != nullptr;
   const long long ld = a.epi == 0 ? a.ld_t : 1;
-  const long long obase = a.epi == 0
-                              ? static_cast<long long>(l) * a.ld_l + row
-                              : ((static_cast<long long>(l) * a.n_kchunks + kc) * a.M_total + row) * a.T;
+  const long long obase =
+      (a.epi == 0 ? static_cast<long long>(l) * a.ld_l + row
+                  : ((static_cast<long long>(l) * a.n_kchunks + kc) * a.M_total + row) * a.T) +
+      static_cast<long long>(t_off) * ld;
+  const int T = a.T - t_off;  // live complex columns of this accumulator
+  if (CS) cs += t_off;
   const int n64 = N / 64 * 64;
   for (int c0 = 64 * g; c0 < n64; c0 += 64 * EPW) {
     float v[64];
     tmem_ld64(tbase + c0, v);
-    if (live && c0 / 2 < a.T) tc_store_cols<32, CS>(a, v, c0 / 2, obase, ld, bf, scale, cs);
+    if (live && c0 / 2 < T) tc_store_cols<32, CS>(a, v, c0 / 2, obase, ld, bf, scale, cs, T);
   }
   for (int c0 = n64 + 16 * g; c0 < N; c0 += 16 * EPW) {
     float v[16];
     tmem_ld16(tbase + c0, v);
-    if (live && c0 / 2 < a.T) tc_store_cols<8, CS>(a, v, c0 / 2, obase, ld, bf, scale, cs);
+    if (live && c0 / 2 < T) tc_store_cols<8, CS>(a, v, c0 / 2, obase, ld, bf, scale, cs, T);
   }
 }
 
@@ -640,10 +647,19 @@ __device__ __forceinline__ void tc_mma2_f8f8(uint32_t d_tmem, uint64_t a_desc, u
 // CTA, FP16 B.  Stage layout per CTA: A [A_lo] B-halves [B_lo-halves]
 // [FP8 staging].  FP8: each CTA's staging load completes on its own full[s],
 // and rank 0's full[s] also takes both CTAs' B halves; the converters of
-// both CTAs then arrive on rank 0's aready[s], which the MMAs wait for.  3: FP8 e4m3 A and B (kind::f8f6f4, no widening): BK counts
-// bytes = elements, 128-byte rows with 128-byte swizzle, K = 32 per MMA; the
-// per-(bin, 256-row) A scales and per-(bin, column) B scales are applied in
-// the epilogue.
+// both CTAs then arrive on rank 0's aready[s], which the MMAs wait for.
+// 3: FP8 e4m3 A and B (kind::f8f6f4, no widening): BK counts bytes =
+// elements, K = 32 per MMA; the per-(bin, 256-row) A scales and per-(bin,
+// column) B scales are applied in the epilogue.  4: the same with B as hi +
+// lo e4m3 parts, two MMAs per K step.  MODE 4 with a.n_split = 2
+// (N = 512): a unit is one 256-column half of an M = 256 tile (the two
+// halves are adjacent units, taken by neighbouring CTA pairs at about the
+// same time, so A comes from HBM about once), its
+// accumulator one of two alternating 256-column slots of tensor memory: the
+// epilogue drains one while the MMAs fill the other (with one 512-column
+// accumulator the MMAs waited ~20 % of each unit for the drain).  MODE 3
+// reads half the B bytes per K step, and there the second A read of each
+// tile cost more than the overlap gained (measured), so it keeps N = 512.
 template <int BK, int MODE>
 __device__ __forceinline__ void tc_gemm2_body(const CUtensorMap* tmA, const CUtensorMap* tmB, const CUtensorMap* tmA2,
                                               const CUtensorMap* tmB2, const TcArgs& a,
@@ -667,8 +683,14 @@ __device__ __forceinline__ void tc_gemm2_body(const CUtensorMap* tmA, const CUte
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
   const int N = a.N;
-  const int n_mma = N > 256 ? N / 256 : 1;
-  const int n_mma_cols = N > 256 ? 256 : N;
+  // F8F8 with n_split = 2 (N = 512): a unit takes one 256-column half of the
+  // columns, and two such accumulators alternate in tensor memory, so the
+  // MMAs of the next unit run while the epilogue drains the last one
+  const int NS = (BLO && a.n_split == 2) ? 2 : 1;
+  const int NU = N / NS;       // accumulator columns per unit
+  const int AS = NS;           // accumulators in tensor memory
+  const int n_mma = NU > 256 ? NU / 256 : 1;
+  const int n_mma_cols = NU > 256 ? 256 : NU;
   const int hrows = n_mma_cols / 2;  // B rows this CTA stages per MMA slice
   const int hb = hrows * BKB;
   const int bh_bytes = n_mma * hb;
@@ -679,14 +701,15 @@ __device__ __forceinline__ void tc_gemm2_body(const CUtensorMap* tmA, const CUte
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * stage_bytes);
   uint64_t* empty = full + S;
   uint64_t* aready = empty + S;  // F8, rank 0: both CTAs' A slots widened
+  constexpr int kAccBars = BLO ? 2 : 1;  // hi + lo B may alternate two accumulators
   uint64_t* acc_full = aready + (F8 ? S : 0);
-  uint64_t* acc_empty = acc_full + 1;
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(acc_empty + 1);
+  uint64_t* acc_empty = acc_full + kAccBars;
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(acc_empty + kAccBars);
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const int nk_total = (a.K + BK - 1) / BK;
   const int mpairs = (a.m_tiles + 1) / 2;
-  const long long units = static_cast<long long>(a.Nb) * mpairs * a.n_kchunks;
+  const long long units = static_cast<long long>(a.Nb) * mpairs * NS * a.n_kchunks;
   // FP16 (F8) and e4m3 (F8F8, kind::f8f6f4) both encode as type 0
   const uint32_t idesc = (F8 || F8F8) ? idesc_f16(2 * kBlockM, n_mma_cols) : idesc_bf16(2 * kBlockM, n_mma_cols);
 
@@ -696,8 +719,10 @@ __device__ __forceinline__ void tc_gemm2_body(const CUtensorMap* tmA, const CUte
       mbar_init(empty + s, 1);
       if (F8) mbar_init(aready + s, 8);  // 4 converter warps of each CTA
     }
-    mbar_init(acc_full, 1);
-    mbar_init(acc_empty, 2 * kEpiWarps);
+    for (int s = 0; s < kAccBars; ++s) {
+      mbar_init(acc_full + s, 1);
+      mbar_init(acc_empty + s, 2 * kEpiWarps);
+    }
     fence_mbar_init();
   }
   if (warp == 1) {  // one warp of each CTA allocates the pair's tensor memory together
@@ -710,9 +735,11 @@ __device__ __forceinline__ void tc_gemm2_body(const CUtensorMap* tmA, const CUte
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
 
-  auto unit_coords = [&](long long u, int& l, int& mt, int& kc) {
+  auto unit_coords = [&](long long u, int& l, int& mt, int& nh, int& kc) {
     kc = static_cast<int>(u % a.n_kchunks);
-    const long long r = u / a.n_kchunks;
+    long long r = u / a.n_kchunks;
+    nh = static_cast<int>(r % NS);  // column half (n_split)
+    r /= NS;
     mt = static_cast<int>(r % mpairs) * 2 + static_cast<int>(crank);  // this CTA's M tile
     l = static_cast<int>(r / mpairs);
   };
@@ -723,8 +750,8 @@ __device__ __forceinline__ void tc_gemm2_body(const CUtensorMap* tmA, const CUte
       int it = 0;
       bool ok = true;
       for (long long u = cid; u < units && ok; u += ncl) {
-        int l, mt, kc;
-        unit_coords(u, l, mt, kc);
+        int l, mt, nh, kc;
+        unit_coords(u, l, mt, nh, kc);
         const int kb0 = a.kb_off + kc * a.kblocks_per_chunk;
         const int kb1 = min(nk_total, kb0 + a.kblocks_per_chunk);
         for (int kb = kb0; kb < kb1; ++kb, ++it) {
@@ -747,7 +774,7 @@ __device__ __forceinline__ void tc_gemm2_body(const CUtensorMap* tmA, const CUte
           }
           unsigned char* sb = sa + a_bytes;
           for (int c = 0; c < n_mma; ++c) {
-            const int row0 = c * n_mma_cols + static_cast<int>(crank) * hrows;
+            const int row0 = nh * NU + c * n_mma_cols + static_cast<int>(crank) * hrows;
             tma_load_3d_pair(sb + c * hb, tmB, kb * BK, row0, l, fb);
             if constexpr (SPLIT || BLO) tma_load_3d_pair(sb + bh_bytes + c * hb, tmB2, kb * BK, row0, l, fb);
           }
@@ -765,11 +792,13 @@ __device__ __forceinline__ void tc_gemm2_body(const CUtensorMap* tmA, const CUte
       int it = 0, acc_it = 0;
       bool ok = true;
       for (long long u = cid; u < units && ok; u += ncl) {
-        int l, mt, kc;
-        unit_coords(u, l, mt, kc);
+        int l, mt, nh, kc;
+        unit_coords(u, l, mt, nh, kc);
         const int kb0 = a.kb_off + kc * a.kblocks_per_chunk;
         const int kb1 = min(nk_total, kb0 + a.kblocks_per_chunk);
-        if (acc_it > 0 && !mbar_wait_bounded_cl(acc_empty, (acc_it - 1) & 1, a.status, DEV_ERR_TIMEOUT_MMA)) {
+        const int as = acc_it % AS;
+        if (acc_it >= AS &&
+            !mbar_wait_bounded_cl(acc_empty + as, ((acc_it / AS) - 1) & 1, a.status, DEV_ERR_TIMEOUT_MMA)) {
           ok = false;
           break;
         }
@@ -791,7 +820,7 @@ __device__ __forceinline__ void tc_gemm2_body(const CUtensorMap* tmA, const CUte
             for (int c = 0; c < n_mma; ++c) {
               const uint32_t boff = c * hb + k * 32;
               const uint64_t bd = sdesc_sw<BKB / 2>(sb + boff);
-              const uint32_t dcol = tmem + c * n_mma_cols;
+              const uint32_t dcol = tmem + static_cast<uint32_t>(as * NU + c * n_mma_cols);
               if constexpr (F8F8) {
                 tc_mma2_f8f8(dcol, ad, bd, idesc, (kb > kb0 || k > 0) ? 1u : 0u);
                 if constexpr (BLO) tc_mma2_f8f8(dcol, ad, sdesc_sw<BKB / 2>(sb + bh_bytes + boff), idesc, 1u);
@@ -807,11 +836,12 @@ __device__ __forceinline__ void tc_gemm2_body(const CUtensorMap* tmA, const CUte
           tc_commit2_mc(empty + s, 0x3);
         }
         if (!ok) break;
-        tc_commit2_mc(acc_full, 0x3);
+        tc_commit2_mc(acc_full + as, 0x3);
         ++acc_it;
       }
-      // both CTAs' epilogues consume the last accumulator before teardown
-      if (acc_it > 0) mbar_wait_bounded_cl(acc_empty, (acc_it - 1) & 1, a.status, DEV_ERR_TIMEOUT_MMA);
+      // both CTAs' epilogues consume the last accumulators before teardown
+      for (int k = (acc_it > AS ? acc_it - AS : 0); k < acc_it; ++k)
+        mbar_wait_bounded_cl(acc_empty + k % AS, (k / AS) & 1, a.status, DEV_ERR_TIMEOUT_MMA);
     }
   } else if (F8 && warp >= kConvWarp0) {
     // converter warps of both CTAs: thread t widens row t of this CTA's FP8 A tile
@@ -820,8 +850,8 @@ __device__ __forceinline__ void tc_gemm2_body(const CUtensorMap* tmA, const CUte
     int it = 0;
     bool ok = true;
     for (long long u = cid; u < units && ok; u += ncl) {
-      int l, mt, kc;
-      unit_coords(u, l, mt, kc);
+      int l, mt, nh, kc;
+      unit_coords(u, l, mt, nh, kc);
       const int kb0 = a.kb_off + kc * a.kblocks_per_chunk;
       const int kb1 = min(nk_total, kb0 + a.kblocks_per_chunk);
       for (int kb = kb0; kb < kb1; ++kb, ++it) {
@@ -844,21 +874,22 @@ __device__ __forceinline__ void tc_gemm2_body(const CUtensorMap* tmA, const CUte
     const uint32_t acc_empty0 = cluster_addr(acc_empty, 0);
     int acc_it = 0;
     for (long long u = cid; u < units; u += ncl) {
-      int l, mt, kc;
-      unit_coords(u, l, mt, kc);
-      if (!mbar_wait_bounded(acc_full, acc_it & 1, a.status, DEV_ERR_TIMEOUT_MMA)) break;
+      int l, mt, nh, kc;
+      unit_coords(u, l, mt, nh, kc);
+      const int as = acc_it % AS;
+      if (!mbar_wait_bounded(acc_full + as, (acc_it / AS) & 1, a.status, DEV_ERR_TIMEOUT_MMA)) break;
       tc_fence_after();
       const int row = mt * kBlockM + q * 32 + lane;
-      const uint32_t tbase = tmem + (static_cast<uint32_t>(q * 32) << 16);
+      const uint32_t tbase = tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(as * NU);
       const bool live = row < a.M_total && mt < a.m_tiles;
       float scale = 1.f;
       if (a.row_scale != nullptr && live) scale = a.row_scale[static_cast<long long>(l) * a.nblk + row / 256];
       if (a.b_amax != nullptr) scale *= f16_unscale(*a.b_amax);  // undo the FP16 B operand's power-of-two scale
-      tc_epilogue_tile<EPW, F8F8>(a, tbase, N, g, l, kc, row, live, scale,  // F8F8: per-column B scales
-                                  F8F8 ? col_scale + static_cast<long long>(l) * col_ld : nullptr);
+      tc_epilogue_tile<EPW, F8F8>(a, tbase, NU, g, l, kc, row, live, scale,  // F8F8: per-column B scales
+                                  F8F8 ? col_scale + static_cast<long long>(l) * col_ld : nullptr, nh * NU / 2);
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive_cluster(acc_empty0);
+      if (lane == 0) mbar_arrive_cluster(acc_empty0 + 8u * static_cast<uint32_t>(as));
       ++acc_it;
     }
   }
@@ -1588,12 +1619,15 @@ size_t tc_smem_bytes(int N, int stages, int a_lo, int b_lo, int fp8, int mt) {
 
 namespace {
 // Two-SM form: per CTA, one A tile and half of the B tile (each part
-// doubled when split), plus the byte staging of an FP8 A tile.
+// doubled when split), plus the byte staging of an FP8 A tile.  N: the
+// columns of one unit (N / 2 with n_split = 2).
 // fp8 = 2: FP8 A and B read directly (128-byte rows of 128 K elements);
-// fp8 = 3: the same with B as hi + lo parts (64-byte rows of 64 K elements).
+// fp8 = 3: the same with B as hi + lo parts (64-byte rows of 64 K elements);
+// fp8 = 4: hi + lo B parts in 128-byte rows of 128 K elements (n_split).
 int tc2_stage_bytes(int N, int split, int fp8) {
   if (fp8 == 2) return (kBlockM + N / 2) * 128;
   if (fp8 == 3) return (kBlockM + N) * 64;
+  if (fp8 == 4) return (kBlockM + N) * 128;
   const int bk = tc_block_k(N, split, 1);
   return (kBlockM * bk * 2 + (N / 2) * bk * 2) * (1 + split) + (fp8 ? kBlockM * bk : 0);
 }
@@ -1655,10 +1689,14 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
     const bool f8f8 = col_scale != nullptr;
     const bool f8lo = f8f8 && tmB2 != nullptr;  // B as hi + lo e4m3 parts
     if (f8f8 && (!a.a_fp8 || col_ld < a.T)) return cudaErrorInvalidValue;
-    const size_t smem = tc2_smem_bytes(a.N, a.stages, sp, f8lo ? 3 : (f8f8 ? 2 : f8));
+    const bool nsp = a.n_split == 2;  // FP8 x (hi + lo FP8) at N = 512 only
+    if ((a.n_split != 0 && a.n_split != 1 && !nsp) || (nsp && (!f8lo || a.N != 512))) return cudaErrorInvalidValue;
+    const size_t smem =
+        tc2_smem_bytes(nsp ? a.N / 2 : a.N, a.stages, sp, f8lo ? (nsp ? 4 : 3) : (f8f8 ? 2 : f8));
     if (smem > static_cast<size_t>(kSmemOptIn)) return cudaErrorInvalidValue;
     const bool bk64 = tc_block_k(a.N, sp, 1) == 64;
-    const void* kfn = f8lo ? reinterpret_cast<const void*>(k_tc_gemm2_f8f8lo<64>)
+    const void* kfn = f8lo ? (nsp ? reinterpret_cast<const void*>(k_tc_gemm2_f8f8lo<128>)
+                                  : reinterpret_cast<const void*>(k_tc_gemm2_f8f8lo<64>))
                       : f8f8 ? reinterpret_cast<const void*>(k_tc_gemm2_f8f8<128>)
                       : f8 ? (bk64 ? reinterpret_cast<const void*>(k_tc_gemm2_f8<64>)
                                    : reinterpret_cast<const void*>(k_tc_gemm2_f8<32>))
@@ -1685,11 +1723,14 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
     if (e != cudaSuccess) return e;
     if (active < 1) return cudaErrorInvalidConfiguration;
     long long nclusters = active;
-    const long long pu = static_cast<long long>(a.Nb) * ((a.m_tiles + 1) / 2) * a.n_kchunks;
+    const long long pu = static_cast<long long>(a.Nb) * ((a.m_tiles + 1) / 2) * a.n_kchunks * (nsp ? 2 : 1);
     if (nclusters > pu) nclusters = pu;
     cfg.gridDim = dim3(static_cast<unsigned>(nclusters * 2));
     if (f8lo) {
-      e = cudaLaunchKernelEx(&cfg, k_tc_gemm2_f8f8lo<64>, tmA, tmB, *tmB2, a, col_scale, col_ld);
+      if (nsp)
+        e = cudaLaunchKernelEx(&cfg, k_tc_gemm2_f8f8lo<128>, tmA, tmB, *tmB2, a, col_scale, col_ld);
+      else
+        e = cudaLaunchKernelEx(&cfg, k_tc_gemm2_f8f8lo<64>, tmA, tmB, *tmB2, a, col_scale, col_ld);
     } else if (f8f8) {
       e = cudaLaunchKernelEx(&cfg, k_tc_gemm2_f8f8<128>, tmA, tmB, a, col_scale, col_ld);
     } else if (f8) {

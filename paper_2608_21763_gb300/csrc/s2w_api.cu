@@ -588,10 +588,13 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
       StageTimer t(ctx, 1, st);
       CUtensorMap ta, tb, tb2;
       // byte maps: K blocks of 128 e4m3 elements with 128-byte swizzle, or
-      // of 64 with 64-byte swizzle when B comes as hi + lo parts
+      // of 64 with 64-byte swizzle when B comes as hi + lo parts of up to
+      // 256 columns; hi + lo at N = 512: each unit takes one 256-column
+      // half (n_split), and two accumulators alternate in tensor memory
       const bool lo = ctx->tc_f8lo;
-      const int bkb = lo ? 64 : 128;
-      const int swz = lo ? 2 : 1;
+      const bool nsp = lo && N1 == 512;
+      const int bkb = lo && !nsp ? 64 : 128;
+      const int swz = lo && !nsp ? 2 : 1;
       const int brows = (N1 > 256 ? 256 : N1) / 2;
       CK(tc_encode_3d_u8(&ta, ctx->G, K1, Ng, Nb, 128, bkb, swz));
       CK(tc_encode_3d_u8(&tb, ctx->tc_bp1, K1, ctx->tc_n1max, Nb, brows, bkb, swz));
@@ -605,7 +608,8 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
       a.n_kchunks = 1;
       a.kblocks_per_chunk = (K1 + bkb - 1) / bkb;
       a.cta2 = 1;
-      a.stages = tc_stages_pair(N1, 0, lo ? 3 : 2);
+      a.stages = tc_stages_pair(nsp ? N1 / 2 : N1, 0, lo ? (nsp ? 4 : 3) : 2);
+      a.n_split = nsp ? 2 : 1;
       a.tmem_cols = N1 <= 32 ? 32 : (N1 <= 64 ? 64 : (N1 <= 128 ? 128 : (N1 <= 256 ? 256 : 512)));
       a.a_fp8 = 1;
       a.row_scale = ctx->G_scale;

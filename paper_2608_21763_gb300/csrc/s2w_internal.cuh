@@ -254,6 +254,9 @@ struct TcArgs {
   const unsigned* b_amax;  // FP16 B operand: amax (float bits) that set its power-of-two scale
   int m_pair;              // 1: two M tiles per unit sharing each B tile (N <= 256, not FP8;
                            //    tmem_cols >= 2 N, stages from tc_stages_for(..., mt = 2))
+  int n_split;             // 2 (FP8 x hi + lo FP8 two-SM, N = 512): units of 256 columns, two
+                           //    accumulators alternating in tensor memory; 128-element K blocks,
+                           //    stages from tc_stages_pair(N / 2, 0, 4)
   int cta2;                // 1: two-SM MMAs, a CTA pair per M = 256 tile, each staging half of B
                            //    (N % 32 == 0, no m_pair; B box rows = min(N, 256) / 2,
                            //    K blocks tc_block_k(N, split, 1), stages from tc_stages_pair)
@@ -276,9 +279,10 @@ cudaError_t tc_encode_3d_u8(CUtensorMap* out, const void* base, long long K, lon
 // col_scale (with a.a_fp8 and a.cta2): B is FP8 e4m3 too (launch_pack_b_f8),
 // byte tensor maps with 128-byte swizzle and 128-byte K boxes, kind::f8f6f4
 // MMAs; column t of bin l is scaled by col_scale[l * col_ld + t].  With
-// col_scale and tmB2: B is hi + lo e4m3 parts (tmB, tmB2), 64-byte swizzle
-// and 64-byte K boxes for A and both B parts, two MMAs per K step
-// (a.stages from tc_stages_pair(N, 0, 3)).  (Kept out
+// col_scale and tmB2: B is hi + lo e4m3 parts (tmB, tmB2), two MMAs per K
+// step; at N <= 256 with 64-byte swizzle and 64-byte K boxes for A and both
+// B parts (a.stages from tc_stages_pair(N, 0, 3)), at N = 512 with
+// a.n_split = 2 and 128-byte boxes.  (Kept out
 // of TcArgs: a larger argument block costs every GEMM kernel registers.)
 cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const TcArgs& a, int num_sms,
                            cudaStream_t st, const CUtensorMap* tmA2 = nullptr, const CUtensorMap* tmB2 = nullptr,
