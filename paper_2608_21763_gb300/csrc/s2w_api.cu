@@ -1789,6 +1789,12 @@ bool tune_cache_write(const std::string& path, const std::string& key, int bsub,
 // GEMM-form knob of the tensor engine: the public S2W_PAIR_* value and the
 // internal tc_pair code it selects.
 int pair_code(int pub) { return pub == S2W_PAIR_ON ? 1 : (pub == S2W_PAIR_OFF ? 0 : kDefaultPair); }
+// The GEMM form of a public pair value: S2W_PAIR_ON also runs the BF16
+// retransform GEMM on two-SM tiles, as when the caller sets it.
+void apply_pair_mode(s2w_ctx* ctx, int pub) {
+  ctx->tc_pair = pair_code(pub);
+  ctx->tc_rtpair = pub == S2W_PAIR_ON;
+}
 
 }  // namespace
 
@@ -1817,7 +1823,7 @@ int s2w_autotune(s2w_ctx* ctx, int B, s2w_tuning* out, void* stream) {
         (p == S2W_PAIR_AUTO || p == S2W_PAIR_ON || p == S2W_PAIR_OFF) && c >= 1 && c <= ctx->s2_max_chunks &&
         m >= 1) {
       ctx->tc_bsub = b;
-      ctx->tc_pair = pair_code(p);
+      apply_pair_mode(ctx, p);
       set_s2_chunks(ctx, c);
       ctx->tc_min_batch = m;
       r.from_cache = 1;
@@ -1872,7 +1878,7 @@ int s2w_autotune(s2w_ctx* ctx, int B, s2w_tuning* out, void* stream) {
       for (int j = 0; j < 3 && rc == S2W_OK; ++j) {
         if (ctx->opts.tc_pair != S2W_PAIR_AUTO && pairs[j] != ctx->opts.tc_pair) continue;
         ctx->tc_bsub = bsubs[i];
-        ctx->tc_pair = pair_code(pairs[j]);
+        apply_pair_mode(ctx, pairs[j]);
         set_s2_chunks(ctx, ctx->opts.tc_s2_chunks);
         r.form_bsub[nf] = bsubs[i];
         r.form_pair[nf] = pairs[j];
@@ -1886,7 +1892,7 @@ int s2w_autotune(s2w_ctx* ctx, int B, s2w_tuning* out, void* stream) {
       }
     }
     ctx->tc_bsub = best_b;
-    ctx->tc_pair = pair_code(best_p);
+    apply_pair_mode(ctx, best_p);
     set_s2_chunks(ctx, ctx->opts.tc_s2_chunks);
     r.tc_bsub = best_b;
     r.tc_pair = best_p;
