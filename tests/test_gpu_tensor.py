@@ -310,12 +310,13 @@ def test_fp8_activations_on_tensor_engine(Ng, B):
     assert np.array_equal(out[True], q2)
 
 
-@pytest.mark.parametrize("Ng,B", [(700, 3), (600, 300), (5000, 256)])
+@pytest.mark.parametrize("Ng,B", [(700, 3), (600, 300), (5000, 256), (700, 150)])
 def test_fp8_hilo_activations_match_fp16_activations(Ng, B):
     """FP8 operator x FP8 activations as hi + lo e4m3 parts (tc_fp8_act = 2:
     two kind::f8f6f4 MMAs per K step on two-SM tiles; 64-byte swizzle up to
-    N = 256, and at N = 512 (B = 256, and the first sub-batch of B = 300)
-    two 256-column units per tile with alternating accumulators): at
+    N = 256, and at N = 512 (B = 256, the first sub-batch of B = 300, and
+    B = 150, whose second column half holds 22 live ruptures) two 256-column
+    units per tile with alternating accumulators): at
     the FP8 bar against the oracle, and within 2^-7 of the window norm of the
     FP16-activation path (the hi + lo pair keeps ~2^-8 of each entry, FP16
     2^-11; the operator's own e4m3 rounding is common to both)."""
