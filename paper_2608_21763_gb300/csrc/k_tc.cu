@@ -247,6 +247,40 @@ __device__ __forceinline__ void tc_epilogue_tile(const TcArgs& a, uint32_t tbase
   }
 }
 
+// Epilogue with a half-stored B (TcArgs::b_half): accumulator columns t and
+// N / 2 + t hold the real and imaginary parts of complex column t (B rows
+// t = (Re, -Im) and N / 2 + t = (Im, Re) of one column of the embedding).
+// Group g of EPW takes the 16-column chunks g, g + EPW, ... of the first
+// half; N / 2 is a multiple of 16.  FP32 pairs out (epi 0 or 1).
+template <int EPW>
+__device__ __forceinline__ void tc_epilogue_half(const TcArgs& a, uint32_t tbase, int N, int g, int l, int kc,
+                                                 int row, bool live, float scale) {
+  const int nh = N / 2;
+  const long long ld = a.epi == 0 ? a.ld_t : 1;
+  const long long obase = a.epi == 0
+                              ? static_cast<long long>(l) * a.ld_l + row
+                              : ((static_cast<long long>(l) * a.n_kchunks + kc) * a.M_total + row) * a.T;
+  for (int t0 = 16 * g; t0 < nh; t0 += 16 * EPW) {
+    float re[16], im[16];
+    tmem_ld16(tbase + t0, re);
+    tmem_ld16(tbase + nh + t0, im);
+    if (!live || t0 >= a.T) continue;
+    float2* p = a.out + obase + t0 * ld;
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+      if (t0 + k < a.T) {
+        float2 o = make_float2(re[k] * scale, im[k] * scale);
+        if (a.acc_out) o = cadd(p[k * ld], o);
+        p[k * ld] = o;
+      }
+  }
+}
+
+// Row t of the embedding's second half from row t of the first: each BF16
+// pair (a, b) becomes (-b, a) -- the halves swapped and the sign bit of the
+// new low half flipped (exact).
+__device__ __forceinline__ unsigned rot_pair_bf16(unsigned w) { return __funnelshift_l(w, w, 16) ^ 0x8000u; }
+
 // Widens row t of an FP8 e4m3 A tile (BK bytes at src, as TMA wrote it
 // without swizzle) exactly to FP16 (one cvt per pair) and stores the BK * 2
 // bytes at dst in the TMA swizzle pattern of a BK-element K-major row
@@ -301,9 +335,11 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUten
   static_assert(MT == 1 || MODE != 2, "M-tile pairs: not with FP8 A");
   constexpr bool SPLIT = MODE == 1;
   constexpr bool F8 = MODE == 2;
-  constexpr int EPW = F8 ? kEpwF8 : kEpw;
+  constexpr bool BH = MODE == 5;    // B stored as its first N / 2 rows (TcArgs::b_half)
+  constexpr bool CONV = F8 || BH;   // 4 converter warps complete each stage
+  constexpr int EPW = CONV ? kEpwF8 : kEpw;
   constexpr int kEpiWarps = 4 * EPW;
-  constexpr int kConvWarp0 = 2 + kEpiWarps;  // FP8: first of the 4 converter warps
+  constexpr int kConvWarp0 = 2 + kEpiWarps;  // first of the 4 converter warps
   constexpr int kStg = F8 ? kBlockM * BK : 0;  // FP8 staging bytes per stage
   constexpr int kA = kBlockM * BK * 2;
   constexpr int a_tile = kA * (SPLIT ? 2 : 1);  // one M tile's A (+ A_lo) bytes per stage
@@ -318,8 +354,8 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUten
   const int S = a.stages;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * stage_bytes);
   uint64_t* empty = full + S;
-  uint64_t* aready = empty + S;  // F8: A slot widened (count 4 converter warps)
-  uint64_t* acc_full = aready + (F8 ? S : 0);
+  uint64_t* aready = empty + S;  // F8 / BH: the stage completed (count 4 converter warps)
+  uint64_t* acc_full = aready + (CONV ? S : 0);
   uint64_t* acc_empty = acc_full + 1;
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(acc_empty + 1);
   const int warp = threadIdx.x >> 5;
@@ -336,7 +372,7 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUten
     for (int s = 0; s < S; ++s) {
       mbar_init(full + s, 1);
       mbar_init(empty + s, 1);
-      if (F8) mbar_init(aready + s, 4);
+      if (CONV) mbar_init(aready + s, 4);
     }
     mbar_init(acc_full, 1);
     mbar_init(acc_empty, kEpiWarps);
@@ -374,7 +410,8 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUten
             break;
           }
           unsigned char* sa = smem + s * stage_bytes;
-          mbar_arrive_expect_tx(full + s, stage_bytes - (F8 ? kA : 0));  // F8: the A slot is not TMA's
+          // F8: the A slot is not TMA's; BH: nor the second half of B
+          mbar_arrive_expect_tx(full + s, stage_bytes - (F8 ? kA : 0) - (BH ? b_bytes / 2 : 0));
           if constexpr (F8) {
             tma_load_3d(sa + a_all + b_bytes, tmA, kb * BK, mt * kBlockM, l, full + s);
           } else {
@@ -389,7 +426,10 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUten
             for (int c = 0; c < n_mma; ++c)
               tma_load_3d(sb + c * n_mma_cols * BK * 2, tb, kb * BK, c * n_mma_cols, l, full + s);
           };
-          load_b(tmB, sa + a_all);
+          if constexpr (BH)
+            tma_load_3d(sa + a_all, tmB, kb * BK, 0, l, full + s);  // box: the N / 2 stored rows
+          else
+            load_b(tmB, sa + a_all);
           if constexpr (SPLIT) load_b(tmB2, sa + a_all + b_bytes);
         }
       }
@@ -416,7 +456,7 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUten
         tc_fence_after();
         for (int kb = kb0; kb < kb1; ++kb, ++it) {
           const int s = it % S;
-          if (!mbar_wait_bounded(F8 ? aready + s : full + s, (it / S) & 1, a.status, DEV_ERR_TIMEOUT_FULL)) {
+          if (!mbar_wait_bounded(CONV ? aready + s : full + s, (it / S) & 1, a.status, DEV_ERR_TIMEOUT_FULL)) {
             ok = false;
             break;
           }
@@ -450,8 +490,11 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUten
       // the epilogue consumes the last accumulator; wait for it before teardown
       if (acc_it > 0) mbar_wait_bounded(acc_empty, (acc_it - 1) & 1, a.status, DEV_ERR_TIMEOUT_MMA);
     }
-  } else if (F8 && warp >= kConvWarp0) {
-    // converter warps: thread t widens row t of each FP8 A tile
+  } else if (CONV && warp >= kConvWarp0) {
+    // converter warps.  F8: thread t widens row t of each FP8 A tile.  BH:
+    // the B tile's second half, row by row from the first (rows N / 2 + r
+    // and r share the 128-byte swizzle phase, N / 2 being a multiple of 8,
+    // so the bytes copy straight across), 16 bytes per thread and step
     const int t = threadIdx.x - 32 * kConvWarp0;
     int it = 0;
     bool ok = true;
@@ -467,7 +510,16 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUten
           break;
         }
         unsigned char* sa = smem + s * stage_bytes;
-        widen_fp8_row<BK>(sa + a_all + b_bytes + t * BK, sa + t * (BK * 2), t);
+        if constexpr (F8) {
+          widen_fp8_row<BK>(sa + a_all + b_bytes + t * BK, sa + t * (BK * 2), t);
+        } else {
+          const uint4* src = reinterpret_cast<const uint4*>(sa + a_all);
+          uint4* dst = reinterpret_cast<uint4*>(sa + a_all + b_bytes / 2);
+          for (int i = t; i < b_bytes / 32; i += 128) {
+            const uint4 w = src[i];
+            dst[i] = make_uint4(rot_pair_bf16(w.x), rot_pair_bf16(w.y), rot_pair_bf16(w.z), rot_pair_bf16(w.w));
+          }
+        }
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(aready + s);
@@ -491,7 +543,10 @@ __device__ __forceinline__ void tc_gemm_body(const CUtensorMap* tmA, const CUten
         float scale = 1.f;
         if (a.row_scale != nullptr && live) scale = a.row_scale[static_cast<long long>(l) * a.nblk + row / 256];
         if (a.b_amax != nullptr) scale *= f16_unscale(*a.b_amax);  // undo the FP16 B operand's power-of-two scale
-        tc_epilogue_tile<EPW>(a, tbase, N, g, l, kc, row, live, scale);
+        if constexpr (BH)
+          tc_epilogue_half<EPW>(a, tbase, N, g, l, kc, row, live, scale);
+        else
+          tc_epilogue_tile<EPW>(a, tbase, N, g, l, kc, row, live, scale);
       }  // M tiles of the unit
       tc_fence_before();
       __syncwarp();
@@ -517,6 +572,21 @@ template <int BK>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_tc_gemm_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
   tc_gemm_body<BK, 0, 2>(&tmA, &tmB, nullptr, nullptr, a);
+}
+
+// BF16 operands with B stored as the first half of its rows (b_half): the
+// stage-2 GEMM on the adjoint spectra stored once, (Re, -Im) per observation.
+template <int BK>
+__global__ void __launch_bounds__(kTcThreadsF8, 1)
+    k_tc_gemm_h(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
+  tc_gemm_body<BK, 5>(&tmA, &tmB, nullptr, nullptr, a);
+}
+
+template <int BK>
+__global__ void __launch_bounds__(kTcThreadsF8, 1)
+    k_tc_gemm_pair_h(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                     const TcArgs a) {
+  tc_gemm_body<BK, 5, 2>(&tmA, &tmB, nullptr, nullptr, a);
 }
 
 template <int BK>
@@ -956,6 +1026,13 @@ __global__ void k_pack_b(const float2* __restrict__ src, int Nb, int T, long lon
     const long long t = (e / nc) % T;
     const long long l = e / (nc * T);
     const float2 v = src[l * s_l + t * s_t + c];
+    if (conj == 2) {  // first half of the plain embedding only: row t = (Re, -Im)
+      const long long o = (l * N_alloc + t) * Kc + c0 + c;
+      const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, -v.y);
+      hi[o] = h;
+      if (lo != nullptr) lo[o] = __floats2bfloat162_rn(v.x - __low2float(h), -v.y - __high2float(h));
+      continue;
+    }
     const float2 r0 = conj ? make_float2(v.x, v.y) : make_float2(v.x, -v.y);
     const float2 r1 = conj ? make_float2(v.y, -v.x) : make_float2(v.y, v.x);
     const long long o0 = (l * N_alloc + 2 * t) * Kc + c0 + c;
@@ -1682,6 +1759,25 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
   if (a.a_lo != a.b_lo || (a.a_lo != 0 && a.a_lo != 1) || (a.a_lo && (!tmA2 || !tmB2))) return cudaErrorInvalidValue;
   if ((a.a_fp8 != 0 && a.a_fp8 != 1) || (a.a_fp8 && a.a_lo) || (a.a_fp8 && a.row_scale == nullptr))
     return cudaErrorInvalidValue;
+  if (a.b_half) {  // B as its first N / 2 rows; the converter warps build the rest
+    if (a.cta2 || a.a_lo || a.b_lo || a.a_fp8 || col_scale != nullptr || a.N > 256 || a.N % 32 != 0 ||
+        tc_block_k(a.N, 0) != 64)
+      return cudaErrorInvalidValue;
+    const int mt = a.m_pair ? 2 : 1;
+    const size_t smem = tc_smem_bytes(a.N, a.stages, 0, 0, 0, mt);
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    const long long pu = static_cast<long long>(a.Nb) * ((a.m_tiles + mt - 1) / mt) * a.n_kchunks;
+    const unsigned grid = static_cast<unsigned>(pu < num_sms ? pu : num_sms);
+    const void* kfn = a.m_pair ? reinterpret_cast<const void*>(k_tc_gemm_pair_h<64>)
+                               : reinterpret_cast<const void*>(k_tc_gemm_h<64>);
+    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    if (a.m_pair)
+      k_tc_gemm_pair_h<64><<<grid, kTcThreadsF8, smem, st>>>(tmA, tmB, a);
+    else
+      k_tc_gemm_h<64><<<grid, kTcThreadsF8, smem, st>>>(tmA, tmB, a);
+    return cudaGetLastError();
+  }
   if (a.cta2) {  // two-SM MMAs (M = 256 per CTA pair), no M-tile pairs
     if (a.m_pair || a.N % 32 != 0) return cudaErrorInvalidValue;
     const int sp = a.a_lo;

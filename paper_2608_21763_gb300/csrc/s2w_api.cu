@@ -69,6 +69,7 @@ struct s2w_ctx {
   int tc_bsub_max = 0;   // sub-batch the tensor workspaces are sized for (<= 256)
   int tc_n1max = 0;      // B-operand rows of stage 1 (2 x sub-batch, padded)
   int tc_n2 = 0;         // B-operand rows of stage 2 (2 x No, padded)
+  bool tc_p2h = false;   // stage-2 operand stored as rows (Re, -Im) only (TcArgs::b_half): tc_n2 / 2 rows
   long long Ng_pad2 = 0; // complex columns per row of the stage-2 operands
   int tc_kbpc = 64;      // K blocks per stage-2 chunk
   int tc_nkc = 1;        // stage-2 K chunks (<= s2_max_chunks, the partials' allocation)
@@ -125,7 +126,7 @@ struct s2w_ctx {
   void* tc_mhat = nullptr;  // BF16: [Nb][b][Ng_pad2] (Re, Im) pairs; split (and the adjoint): [Nb][b][Ng] complex FP32
   void* tc_vhat = nullptr;  // [Nb][tc_bsub][Ng_pad2] bf16 pairs
   float2* tc_part = nullptr;  // [Nb][nkc][b][No] complex FP32
-  void* tc_p2 = nullptr;    // [Nb][tc_n2][Ng_pad2] bf16 pairs
+  void* tc_p2 = nullptr;    // [Nb][tc_n2 (tc_n2 / 2 when tc_p2h)][Ng_pad2] bf16 pairs
   void* tc_T = nullptr;     // [2 Nt][2 Nt] bf16: retransform as a real-linear map
   void* tc_T_lo = nullptr;  // split: its low-order part
   CUtensorMap tc_tmT, tc_tmT2;
@@ -693,12 +694,15 @@ int waveforms_tensor(s2w_ctx* ctx, const float* slip_d, int B, float* q_d, cudaS
       CUtensorMap ta, tb, ta2, tb2;
       const int m2 = (Bs + 127) / 128;
       TcArgs a{};
-      int brows = tc_shape(a, ctx->tc_n2, m2, sp, 0, ctx->tc_pair);
+      // the half-stored operand runs on one CTA per tile (or M-tile pair)
+      int brows = tc_shape(a, ctx->tc_n2, m2, sp, 0, ctx->tc_p2h ? 0 : ctx->tc_pair);
       // the chunk length tc_kbpc counts K blocks of the single-CTA size
       if (tc_block_k(ctx->tc_n2, sp, a.cta2) != tc_block_k(ctx->tc_n2, sp)) brows = tc_shape(a, ctx->tc_n2, m2, sp, 0, 0);
       const int bk = tc_block_k(ctx->tc_n2, sp, a.cta2);
+      const int p2rows = ctx->tc_p2h ? ctx->tc_n2 / 2 : ctx->tc_n2;
+      a.b_half = ctx->tc_p2h ? 1 : 0;
       CK(tc_encode_3d(&ta, ctx->tc_vhat, K2, ctx->tc_bsub, Nb, K2, 128, bk));
-      CK(tc_encode_3d(&tb, ctx->tc_p2, K2, ctx->tc_n2, Nb, K2, brows, bk));
+      CK(tc_encode_3d(&tb, ctx->tc_p2, K2, p2rows, Nb, K2, ctx->tc_p2h ? p2rows : brows, bk));
       if (sp) {
         CK(tc_encode_3d(&ta2, ctx->tc_vhat_lo, K2, ctx->tc_bsub, Nb, K2, 128, bk));
         CK(tc_encode_3d(&tb2, ctx->tc_p2_lo, K2, ctx->tc_n2, Nb, K2, brows, bk));
@@ -953,7 +957,11 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
     // FP8 B rows come in multiples of 32 (N % 32 for the two-SM tiles)
     ctx->tc_n1max = static_cast<int>(round_up(2 * ctx->tc_bsub, ctx->tc_f8act ? 32 : 16));
     if (ctx->tc_n1max > 256) ctx->tc_n1max = 512;
-    ctx->tc_n2 = static_cast<int>(round_up(2 * No, 16));
+    // BF16 stage 2 stores each adjoint spectrum once (b_half: the converter
+    // warps build the embedding's second row per stage); the split keeps
+    // both rows of hi and lo
+    ctx->tc_p2h = !ctx->tc_split;
+    ctx->tc_n2 = static_cast<int>(ctx->tc_p2h ? 2 * round_up(No, 16) : round_up(2 * No, 16));
     ctx->Ng_pad2 = round_up(Ng, 8);
     ctx->s2_max_chunks = kMaxS2Chunks;
     if (ctx->tc_split) {
@@ -1003,7 +1011,8 @@ int s2w_create(int Ns, int Ng, int No, int Nt, const s2w_opts* opts, s2w_ctx** o
       return bad(e, "tensor velocity spectra");
     if ((e = dalloc(&ctx->tc_part, sizeof(float2) * Nb * ctx->s2_max_chunks * bs * No)) != cudaSuccess)
       return bad(e, "tensor stage-2 partials");
-    if ((e = dalloc(&ctx->tc_p2, 4ull * Nb * ctx->tc_n2 * ctx->Ng_pad2)) != cudaSuccess)
+    if ((e = dalloc(&ctx->tc_p2, 4ull * Nb * (ctx->tc_p2h ? ctx->tc_n2 / 2 : ctx->tc_n2) * ctx->Ng_pad2)) !=
+        cudaSuccess)
       return bad(e, "tensor stage-2 operand");
     if (sp) {
       if ((e = dalloc(&ctx->tc_bp1_lo, 2ull * Nb * ctx->tc_n1max * 2 * ctx->Ns_pad)) != cudaSuccess)
@@ -1224,7 +1233,8 @@ int load_adjoint_impl(s2w_ctx* ctx, int g0, int ng, const float* P, bool spectra
       if (ctx->tc_on) {
         ctx->launches += 1;
         CK(launch_pack_b(stage_s, static_cast<int>(Nb), static_cast<int>(No), rc, No * rc, rc, g0 + c, ctx->Ng_pad2,
-                         ctx->tc_n2, 0, ctx->tc_p2, ctx->tc_p2_lo, st));
+                         ctx->tc_p2h ? ctx->tc_n2 / 2 : ctx->tc_n2, ctx->tc_p2h ? 2 : 0, ctx->tc_p2, ctx->tc_p2_lo,
+                         st));
       }
       if (ctx->tc_adj) {  // Phat_l^T[g0 + c + r][o] (transposing copy; observations along K)
         ctx->launches += 1;

@@ -254,6 +254,11 @@ struct TcArgs {
   const unsigned* b_amax;  // FP16 B operand: amax (float bits) that set its power-of-two scale
   int m_pair;              // 1: two M tiles per unit sharing each B tile (N <= 256, not FP8;
                            //    tmem_cols >= 2 N, stages from tc_stages_for(..., mt = 2))
+  int b_half;              // 1: B holds rows 2t = (Re, -Im) of the plain embedding only, as rows
+                           //    t < N / 2 (tensor map box N / 2 rows); four converter warps build
+                           //    rows N / 2 + t = (Im, Re) per stage; output column t pairs
+                           //    accumulator columns t and N / 2 + t.  BF16, one CTA per tile (or
+                           //    M-tile pair), N <= 256 with N / 2 a multiple of 16, FP32 out
   int n_split;             // 2 (FP8 x hi + lo FP8 two-SM, N = 512): units of 256 columns, two
                            //    accumulators alternating in tensor memory; 128-element K blocks,
                            //    stages from tc_stages_pair(N / 2, 0, 4)
@@ -289,7 +294,9 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
                            const float* col_scale = nullptr, int col_ld = 0);
 // B operand rows 2t / 2t+1 of dst[l][N_alloc][2 Kc] (BF16 pairs, hi and
 // optional lo) from complex FP32 src[l*s_l + t*s_t + c], t < T, c < nc, at
-// complex columns c0 + c; conj selects the embedding of conj(A) x.
+// complex columns c0 + c; conj = 1 selects the embedding of conj(A) x;
+// conj = 2 writes row 2t of the plain embedding, (Re, -Im), as row t only
+// (the half-stored B of TcArgs::b_half).
 cudaError_t launch_pack_b(const float2* src, int Nb, int T, long long nc, long long s_l, long long s_t, long long c0,
                           long long Kc, int N_alloc, int conj, void* hi, void* lo, cudaStream_t st);
 // FP16 B operands: the power-of-two scale that keeps |x| * scale <= 2^14
