@@ -75,3 +75,27 @@ def test_retransform_matrix_rejects_bad_arguments():
     assert L.s2w_retransform_matrix(32, BACKWARD, 0.0, 0, T) == -1
     assert L.s2w_retransform_matrix(32, BACKWARD, 1.0, 2, T) == -1
     assert L.s2w_retransform_matrix(32, BACKWARD, 1.0, 0, None) == -1
+
+
+def test_embedding_second_row_is_a_pair_rotation_of_the_first():
+    """The stage-2 GEMM stores only row 2t = (Re P, -Im P) of the real
+    embedding of each adjoint spectrum and builds row 2t + 1 = (Im P, Re P)
+    in shared memory by rotating each 32-bit BF16 pair by 16 bits and
+    flipping bit 15 (the sign of the new low half).  That is exact because
+    round-to-nearest-even is odd-symmetric, bf16(-x) = -bf16(x), signed
+    zeros included: checked here on the bit patterns, with the pair's first
+    element in the low half as the BF16x2 layout has it."""
+    from error_model import bf16
+    rng = np.random.default_rng(3)
+    re = np.concatenate([rng.standard_normal(4000) * 10.0 ** rng.integers(-30, 30, 4000),
+                         [0.0, -0.0, 0.0, -0.0, 1.0 + 2.0 ** -8, -(1.0 + 3 * 2.0 ** -8), 3.0e38]])
+    im = np.concatenate([rng.standard_normal(4000) * 10.0 ** rng.integers(-30, 30, 4000),
+                         [0.0, 0.0, -0.0, -0.0, -(1.0 + 2.0 ** -8), 1.0 + 3 * 2.0 ** -8, -3.0e38]])
+
+    def bits(x):
+        return (np.asarray(bf16(x), np.float32).view(np.uint32) >> np.uint32(16)).astype(np.uint32)
+
+    row_a = bits(re) | (bits(-im) << np.uint32(16))       # (Re, -Im), as stored
+    rot = ((row_a << np.uint32(16)) | (row_a >> np.uint32(16))) ^ np.uint32(0x8000)
+    row_b = bits(im) | (bits(re) << np.uint32(16))        # (Im, Re), as the embedding needs
+    assert np.array_equal(rot, row_b)
