@@ -32,6 +32,10 @@
 //              two-SM FP8 x (hi + lo FP8) kernel at N = 512 instead splits
 //              the columns into two 256-column units (n_split) whose
 //              accumulators alternate, so the drain overlaps the MMAs.
+//   warps 10-13 (448-thread kernels: FP8 A widened to FP16, and the
+//              stage-2 GEMM on the half-stored adjoint operand) complete
+//              each stage in shared memory before the MMAs read it; these
+//              kernels keep two epilogue warps per quadrant (warps 2-9).
 // Every mbarrier wait is bounded (s2w_internal.cuh); on expiry a status bit
 // is latched and the CTA drains and exits.
 #include <cuda.h>
@@ -320,11 +324,16 @@ __device__ __forceinline__ void widen_fp8_row(const unsigned char* src_row, unsi
 // relative, is dropped).
 // MODE: 0 BF16 operands; 1 split (hi/lo parts of both operands); 2 FP8 e4m3
 // A: TMA brings the FP8 tile (row-major, one byte per K element) into a
-// staging slot of the stage, warps 6-9 widen it exactly to FP16 (one
+// staging slot of the stage, warps 10-13 widen it exactly to FP16 (one
 // cvt per pair) into the swizzled A slot and signal `aready`; the MMAs take
 // FP16 A and B (B packed as FP16 with a power-of-two scale from its amax);
-// the per-(bin, 256-row) scale and the B scale are undone in the epilogue.  Each MODE is its own instantiation and kernel, so the plain
-// kernel carries none of the other modes' code.
+// the per-(bin, 256-row) scale and the B scale are undone in the epilogue.
+// 5 BF16 with B stored as its first N / 2 rows (TcArgs::b_half): TMA loads
+// those into the first half of the stage's B tile, warps 10-13 write the
+// second half (rot_pair_bf16 of each word) and signal `aready`, and the
+// epilogue pairs accumulator columns t and N / 2 + t (tc_epilogue_half).
+// Each MODE is its own instantiation and kernel, so the plain kernel carries
+// none of the other modes' code.
 // MT = 2 (N <= 256, not FP8): a unit takes two adjacent M tiles
 // that share every B tile, with one accumulator each (2N TMEM columns): A
 // gets two thirds of each stage instead of half at N = 128, and B is read
