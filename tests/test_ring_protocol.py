@@ -5,7 +5,10 @@ parity of the previous lap.  A parity wait can only be trusted if the
 waiting warp's consecutive uses of a slot are exactly one lap apart and no
 other warp fills the slot in between; this checks that ownership rule for
 every K-block count the kernel meets (BF16: 64-element k-blocks, split:
-32-element, Nt = 32 .. 256), with the kernel's own index formulas."""
+32-element, Nt = 32 .. 256), with the kernel's own index formulas.  Then the
+tensor-memory accumulator hand-off between the MMA role and the epilogue
+warps (one slot, or two alternating slots), on a model of the mbarrier's
+parity waits under random interleavings."""
 import pytest
 
 RA = 8           # A slots = fill warps
@@ -34,3 +37,87 @@ def test_every_k_block_of_every_tile_is_filled_once():
         filled = [(tile, kb) for tile in range(4) for f in range(FILL_WARPS)
                   for kb in range(f, KB, FILL_WARPS)]
         assert sorted(filled) == [(t, k) for t in range(4) for k in range(KB)]
+
+
+class Barrier:
+    """An mbarrier as the kernels use it: a phase completes when its arrival
+    count is reached, and a parity wait for P passes once the phase with
+    parity P has completed, i.e. while the current phase number has the
+    other parity (so a waiter two phases behind or ahead is not told apart)."""
+
+    def __init__(self, count):
+        self.count, self.arrived, self.phase = count, 0, 0
+
+    def arrive(self):
+        self.arrived += 1
+        if self.arrived == self.count:
+            self.arrived, self.phase = 0, self.phase + 1
+
+    def ready(self, parity):
+        return (self.phase & 1) != parity
+
+
+@pytest.mark.parametrize("AS", [1, 2])
+@pytest.mark.parametrize("seed", range(20))
+def test_alternating_accumulators_are_never_overwritten_or_read_early(AS, seed):
+    """The accumulator hand-off of the tensor-memory GEMMs with AS slots
+    (AS = 2: the column-split FP8 stage-1 GEMM and the retransform GEMM,
+    AS = 1: the other GEMMs): the MMA role fills use u into slot u % AS
+    after waiting on that slot's acc_empty with parity ((u / AS) - 1) & 1
+    (from u >= AS on) and commits acc_full; the epilogue waits on acc_full
+    with parity (u / AS) & 1, reads, and arrives on acc_empty.  Under random
+    interleavings (several epilogue warps arriving one by one), no use is
+    started over a slot whose last use has not been drained, no epilogue
+    warp reads a use before it is complete, and the MMA role's final waits
+    on the last AS uses end only once every warp has drained them."""
+    import random
+    rnd = random.Random(seed)
+    U, WARPS = 23, 3
+    full = [Barrier(1) for _ in range(AS)]
+    empty = [Barrier(WARPS) for _ in range(AS)]
+    slot_use = [None] * AS              # use held by each slot (None: free)
+    drained = [set() for _ in range(U)]  # epilogue warps done with use u
+    mma = {"u": 0, "writing": None, "final": 0}
+    epi = [0] * WARPS                   # next use of each epilogue warp
+    steps = 0
+    while True:
+        steps += 1
+        assert steps < 100000, "no progress"
+        actors = []
+        if mma["u"] < U or mma["writing"] is not None or mma["final"] < min(AS, U):
+            actors.append("mma")
+        actors += [w for w in range(WARPS) if epi[w] < U]
+        if not actors:
+            break
+        a = rnd.choice(actors)
+        if a == "mma":
+            if mma["writing"] is not None:          # commit the use being filled
+                u = mma["writing"]
+                full[u % AS].arrive()
+                mma["writing"] = None
+                mma["u"] += 1
+            elif mma["u"] < U:
+                u = mma["u"]
+                s = u % AS
+                if u >= AS and not empty[s].ready(((u // AS) - 1) & 1):
+                    continue
+                prev = slot_use[s]
+                assert prev is None or len(drained[prev]) == WARPS, (u, prev)
+                slot_use[s] = u
+                mma["writing"] = u
+            else:                                   # the final waits on the last AS uses
+                k = U - min(AS, U) + mma["final"]
+                if empty[k % AS].ready((k // AS) & 1):
+                    assert len(drained[k]) == WARPS, k
+                    mma["final"] += 1
+        else:
+            w = a
+            u = epi[w]
+            s = u % AS
+            if not full[s].ready((u // AS) & 1):
+                continue
+            assert slot_use[s] == u and mma["writing"] != u, (w, u, slot_use[s])
+            drained[u].add(w)
+            empty[s].arrive()
+            epi[w] += 1
+    assert all(len(d) == WARPS for d in drained)
