@@ -121,3 +121,59 @@ def test_alternating_accumulators_are_never_overwritten_or_read_early(AS, seed):
             empty[s].arrive()
             epi[w] += 1
     assert all(len(d) == WARPS for d in drained)
+
+
+@pytest.mark.parametrize("S", [2, 4])
+@pytest.mark.parametrize("seed", range(20))
+def test_converter_stage_ring(S, seed):
+    """The K-block ring of the GEMMs whose stages are completed in shared
+    memory (FP8 A widened to FP16; B's second half built from its first):
+    the producer waits on empty[s] with parity ((n / S) - 1) & 1 from n >= S
+    on and issues the TMA (which completes full[s]); each of 4 converter
+    warps waits on full[s] with parity (n / S) & 1, writes its part and
+    arrives on aready[s]; the MMA role waits on aready[s] with parity
+    (n / S) & 1, reads, and commits empty[s].  Under random interleavings no
+    TMA lands in a stage still being converted or read, no converter works
+    on a stage before its TMA or while the MMAs read it, and the MMAs read
+    only fully converted stages."""
+    import random
+    rnd = random.Random(1000 + seed)
+    NK, CONV = 29, 4
+    full = [Barrier(1) for _ in range(S)]
+    aready = [Barrier(CONV) for _ in range(S)]
+    empty = [Barrier(1) for _ in range(S)]
+    state = [None] * S                 # (use n, 'loaded' | 'converting' | 'converted' | 'read')
+    converted = [set() for _ in range(NK)]
+    prod, mma = 0, 0
+    conv = [0] * CONV
+    steps = 0
+    while prod < NK or mma < NK or min(conv) < NK:
+        steps += 1
+        assert steps < 200000, "no progress"
+        a = rnd.choice(["prod", "mma"] + list(range(CONV)))
+        if a == "prod" and prod < NK:
+            s = prod % S
+            if prod >= S and not empty[s].ready(((prod // S) - 1) & 1):
+                continue
+            assert state[s] is None or state[s][1] == "read", (prod, state[s])
+            state[s] = (prod, "loaded")
+            full[s].arrive()
+            prod += 1
+        elif a == "mma" and mma < NK:
+            s = mma % S
+            if not aready[s].ready((mma // S) & 1):
+                continue
+            assert state[s] == (mma, "converted") and len(converted[mma]) == CONV, (mma, state[s])
+            state[s] = (mma, "read")
+            empty[s].arrive()
+            mma += 1
+        elif isinstance(a, int) and conv[a] < NK:
+            n = conv[a]
+            s = n % S
+            if not full[s].ready((n // S) & 1):
+                continue
+            assert state[s] is not None and state[s][0] == n and state[s][1] in ("loaded", "converting"), (a, n, state[s])
+            converted[n].add(a)
+            state[s] = (n, "converted" if len(converted[n]) == CONV else "converting")
+            aready[s].arrive()
+            conv[a] += 1
