@@ -139,7 +139,11 @@ typedef struct {
                       with each CTA staging half of the B tile.  S2W_PAIR_OFF
                       keeps one CTA per 128-row tile; S2W_PAIR_AUTO (0,
                       default) takes the two-SM form for the 512-column
-                      GEMMs of BF16 operators (256-rupture sub-batches). */
+                      GEMMs of BF16 operators (256-rupture sub-batches).
+                      The BF16 stage-2 GEMM, whose adjoint operand is stored
+                      once (the embedding's second rows are built in shared
+                      memory), runs on one CTA per tile in every mode; the
+                      FP8-activation stage-1 GEMM is always two-SM. */
   int tc_fp8_act;  /* prec_g = FP8_E4M3 only.  1: the tensor engine also
                       rounds the slip spectra, stage 1's B operand, to e4m3
                       with one power-of-two scale per (bin, rupture) (amax to
