@@ -99,3 +99,38 @@ def test_embedding_second_row_is_a_pair_rotation_of_the_first():
     rot = ((row_a << np.uint32(16)) | (row_a >> np.uint32(16))) ^ np.uint32(0x8000)
     row_b = bits(im) | (bits(re) << np.uint32(16))        # (Im, Re), as the embedding needs
     assert np.array_equal(rot, row_b)
+
+
+def _offblock_rank1_residual(M, rows_bin, cols_bin):
+    """Relative residual of the best rank-one fit (alternating least squares)
+    to the entries of M whose row and column belong to different bins."""
+    off = rows_bin[:, None] != cols_bin[None, :]
+    Moff = np.where(off, M, 0.0)
+    u = np.ones(M.shape[0])
+    v = np.ones(M.shape[1])
+    for _ in range(100):
+        v = (Moff * u[:, None]).sum(0) / np.maximum((off * u[:, None] ** 2).sum(0), 1e-300)
+        u = (Moff * v[None, :]).sum(1) / np.maximum((off * v[None, :] ** 2).sum(1), 1e-300)
+    return np.abs(np.where(off, M - np.outer(u, v), 0.0)).max() / np.abs(M).max()
+
+
+@pytest.mark.parametrize("Nt", [32, 256])
+def test_parity_blocks_of_the_retransform_are_block_diagonal_plus_rank_one(Nt):
+    """With the degrees of freedom grouped by bin parity, the even-to-even
+    and odd-to-odd blocks of the retransform matrix are a per-bin (2 x 2)
+    block diagonal plus a rank-one term: the even bins of the zero-padded
+    2Nt-point transform are the Nt-point transform of the kept samples, the
+    odd bins that of the samples times exp(-i pi n / Nt); under either a
+    circular (or anti-circular) difference is diagonal, and the causal D_t
+    differs from it by the wrap-around term of sample 0 only.  The cross
+    blocks are not
+    of that form (the structure is what a GEMM with half the MMAs would
+    use)."""
+    T = lib_matrix(Nt, BACKWARD, 1.0, 0)
+    bins = np.array([0, Nt] + [k // 2 for k in range(2, 2 * Nt)])
+    ev = np.where(bins % 2 == 0)[0]
+    od = np.where(bins % 2 == 1)[0]
+    for r, c in ((ev, ev), (od, od)):
+        assert _offblock_rank1_residual(T[np.ix_(r, c)], bins[r], bins[c]) <= 1e-12
+    for r, c in ((ev, od), (od, ev)):
+        assert _offblock_rank1_residual(T[np.ix_(r, c)], bins[r], bins[c]) > 1e-2
